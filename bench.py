@@ -1,0 +1,389 @@
+"""Benchmark: move-scenario evaluations per second on the 50k-block workload.
+
+One step = one pass of the whole hot path over one batch of moves resident in
+HBM: mm_eval_moves (decode, exact feasibility, per-scenario NPV delta,
+mean - lambda*std) -> mm_topk -> mm_apply_best (the best feasible move applied
+on the device, FP64 accumulators updated).  Workload: 50x50x20 = 50,000 blocks,
+S = 100 lognormal grade scenarios, T = 20 periods, 262,144 moves (half shifts,
+half swaps), synthetic and seeded.  The value rows (21 MB) fit in L2, so L2 is
+flushed (a 256 MB write, outside the per-step events) before every timed step.
+
+Prints one JSON line (rank 0).  Arms:
+  default           the CUDA path (value: device-timed; e2e: host buffers through
+                    the C ABI, copies inside the timed region);
+  --impl reference  the FP64 CPU oracle on the host cores (the only reference
+                    arm available: the paper publishes no code).
+Multi-GPU (torchrun): every rank evaluates its own independent batch on its own
+GPU (no data-path collective); value = all ranks' evaluations / max rank time.
+"""
+
+from __future__ import annotations
+
+import argparse
+import csv
+import hashlib
+import io
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "plain_50k"
+METRIC = "move-scenario evals/sec at 50k blocks, S=100; % of HBM roofline vs plain form"
+UNIT = "move-scenario evals/s"
+TOPK = 32
+FLUSH_BYTES = 256 << 20
+EVAL_KERNEL = "k_eval_uniform"
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k_eval_uniform_plain_50k.md")
+EVAL_SOURCES = ["paper_2511_18296_b300/csrc/mm_eval.cu", "paper_2511_18296_b300/csrc/mm_move.cuh",
+                "paper_2511_18296_b300/csrc/mm_internal.cuh"]
+
+
+def algorithmic_bytes(moves: np.ndarray, S: int) -> float:
+    """Bytes a move batch must touch at minimum: 8 (move) + 5 (score + flag) +
+    per moved block (11 + 4S + S/8): its period byte and ten neighbour period
+    bytes, an FP32 value row and an ore bit row."""
+    n_swap = int((moves[:, 1] >= 0).sum())
+    n_shift = moves.shape[0] - n_swap
+    per_block = 11 + 4 * S + S / 8
+    return n_shift * (13 + per_block) + n_swap * (13 + 2 * per_block)
+
+
+def source_sha() -> str:
+    h = hashlib.sha256()
+    for f in EVAL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the evaluator from the committed ncu summary,
+    or None when absent or taken on another version of the kernel source."""
+    try:
+        txt = open(PROFILE_SUMMARY).read()
+    except OSError:
+        return None
+    vals = {}
+    for line in txt.splitlines():
+        if ":" in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("source_sha256_16") != source_sha():
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def mark(self):
+        return time.time()
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc is not None:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                self.out = ""
+
+    def summary(self, t0: float, t1: float):
+        rows = []
+        for r in csv.reader(io.StringIO(self.out)):
+            if len(r) < 10:
+                continue
+            try:
+                ts = time.mktime(time.strptime(r[0].strip().split(".")[0], "%Y/%m/%d %H:%M:%S"))
+                ts += float("0." + r[0].strip().split(".")[1]) if "." in r[0] else 0.0
+            except Exception:
+                continue
+            rows.append((ts, [x.strip() for x in r]))
+        inside = [r for ts, r in rows if t0 - 0.05 <= ts <= t1 + 0.05] or [r for _, r in rows]
+        if not inside:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        sm = [float(r[2]) for r in inside if r[2].replace(".", "").isdigit()]
+        mx = [float(r[3]) for r in inside if r[3].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in inside for i in range(4) if r[6 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(inside),
+                "power_w_max": max((float(r[4]) for r in inside if r[4].replace(".", "").isdigit()), default=None)}
+
+
+# ----------------------------------------------------------------- CPU oracle
+
+
+def cpu_baseline(p, budget_s: float = 12.0):
+    """The FP64 oracle as it stands, on the host cores: the incremental
+    evaluator over whole batches and the brute-force definition on a sample."""
+    import oracle as O
+    om = O.OracleModel(p)
+    cores = O.num_threads()
+    n = p.moves.shape[0]
+    om.eval_incremental(p.x0, p.moves[:1024])
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        om.eval_incremental(p.x0, p.moves)
+        reps += 1
+        if time.perf_counter() - t0 > budget_s * 0.6:
+            break
+    inc_rate = reps * n * p.S / (time.perf_counter() - t0)
+    nb = 8
+    t0 = time.perf_counter()
+    done = 0
+    while time.perf_counter() - t0 < budget_s * 0.4:
+        om.eval_bruteforce(p.x0, p.moves[done % n:done % n + nb], want_delta=False)
+        done += nb
+    bf_rate = done * p.S / (time.perf_counter() - t0)
+    return {"value": inc_rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"incremental FP64 evaluator: {reps} full batches of {n} moves x {p.S} scenarios; "
+                      f"brute force (full NPV recompute per move): {done} moves",
+            "bruteforce_value": bf_rate}
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle as O
+    import workloads as W
+    p = W.config(WORKLOAD)
+    om = O.OracleModel(p)
+    cores = O.num_threads()
+    n_all = p.moves.shape[0]
+    # size each step so that warm-up + timed steps take about a minute
+    t0 = time.perf_counter()
+    om.eval_incremental(p.x0, p.moves[:16384])
+    per_move = (time.perf_counter() - t0) / 16384
+    n = int(min(n_all, max(1024, 60.0 / max(args.steps + args.warmup, 1) / max(per_move, 1e-9))))
+    x = p.x0.copy()
+
+    def step(j):
+        lo = (j * n) % n_all
+        mv = p.moves[lo:lo + n] if lo + n <= n_all else np.concatenate([p.moves[lo:], p.moves[:lo + n - n_all]])
+        r = om.eval_incremental(x, mv)
+        idx, _ = O.topk(r["score"], r["flag"], TOPK)
+        if idx.size:
+            om.apply(x, mv[idx[0]])
+
+    for j in range(args.warmup):
+        step(j)
+    t0 = time.perf_counter()
+    for j in range(args.steps):
+        step(args.warmup + j)
+    el = time.perf_counter() - t0
+    value = args.steps * n * p.S / el
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded lognormal Gaussian-random-field grades; no public dataset)",
+            "config": {"workload": "50x50x20 blocks, S=100, T=20, 262,144 moves (50% shifts)",
+                       "moves_per_step": n, "topk": TOPK},
+            "cpu_baseline": {"kind": "oracle", "cores": cores, "value": value, "unit": UNIT,
+                             "sample": f"{n} moves per step (incremental FP64 evaluator + top-k + apply)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm
+
+
+def gpu_arm(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2511_18296_b300 as mm
+    import workloads as W
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    p = W.config(WORKLOAD)
+    if rank > 0:  # weak scaling: every rank its own independent batch of moves
+        rng = np.random.default_rng(np.random.SeedSequence([1, rank]))
+        p.moves = W.random_moves(p.x0, p.T, p.moves.shape[0], 0.5, rng)
+    n, S = p.moves.shape[0], p.S
+    m = mm.Model.from_problem(p)
+    assert m.schedule_set(p.x0)
+    moves_d = torch.as_tensor(p.moves, device=dev)
+    score = torch.empty(n, dtype=torch.float32, device=dev)
+    feas = torch.empty(n, dtype=torch.uint8, device=dev)
+    idx = torch.empty(TOPK, dtype=torch.int32, device=dev)
+    top = torch.empty(TOPK, dtype=torch.float32, device=dev)
+    cnt = torch.empty(1, dtype=torch.int32, device=dev)
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    launches_per_step = 5  # eval, 2 x top-k, apply, NPV statistics
+
+    def step():
+        m.eval_moves(moves_d, score=score, feas=feas, want_mean=False)
+        m.topk(score, feas, TOPK, idx=idx, top=top, count=cnt)
+        m.apply_best(moves_d, idx, cnt)
+
+    for _ in range(max(args.warmup, 3)):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    m.schedule_set(p.x0)  # every timed run starts from the same schedule
+
+    K = args.steps
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
+    with ClockSampler(local) as clk:
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t_start = time.time()
+        for k in range(K):
+            flush.zero_()
+            ev[k][0].record()
+            m.eval_moves(moves_d, score=score, feas=feas, want_mean=False)
+            ev[k][1].record()
+            m.topk(score, feas, TOPK, idx=idx, top=top, count=cnt)
+            m.apply_best(moves_d, idx, cnt)
+            ev[k][2].record()
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        t_end = time.time()
+    step_ms = [e[0].elapsed_time(e[2]) for e in ev]
+    eval_ms = [e[0].elapsed_time(e[1]) for e in ev]
+    total_ms = float(sum(step_ms))
+    eval_avg_ms = float(sum(eval_ms)) / K
+    applied, npv_mean, _ = m.last_apply()
+
+    # end to end through the public API with host buffers
+    K2 = max(20, min(200, K))
+    moves_h = torch.from_numpy(p.moves).pin_memory()
+    idx_h = torch.empty(TOPK, dtype=torch.int32).pin_memory()
+    top_h = torch.empty(TOPK, dtype=torch.float32).pin_memory()
+    cnt_h = torch.empty(1, dtype=torch.int32).pin_memory()
+    moves_np = p.moves
+    m.schedule_set(p.x0)
+    e2e_s = []
+    for k in range(K2 + 3):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        moves_d.copy_(moves_h, non_blocking=True)
+        m.eval_moves(moves_d, score=score, feas=feas, want_mean=False)
+        m.topk(score, feas, TOPK, idx=idx, top=top, count=cnt)
+        idx_h.copy_(idx, non_blocking=True)
+        top_h.copy_(top, non_blocking=True)
+        cnt_h.copy_(cnt, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+        if int(cnt_h[0]) > 0:
+            try:
+                m.apply_move(tuple(moves_np[int(idx_h[0])]))
+            except mm.MMError:
+                pass
+        t1 = time.perf_counter()
+        if k >= 3:
+            e2e_s.append(t1 - t0)
+    e2e_avg = sum(e2e_s) / len(e2e_s)
+
+    # max over ranks
+    local_vals = torch.tensor([total_ms, eval_avg_ms, e2e_avg], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(local_vals, op=dist.ReduceOp.MAX)
+    total_ms, eval_avg_ms, e2e_avg = [float(v) for v in local_vals.cpu()]
+
+    evals_per_step = n * S
+    value = world * evals_per_step * K / (total_ms * 1e-3)
+    alg = algorithmic_bytes(p.moves, S)
+    peaks, which = measured_peaks()
+    achieved_gbs = alg / (eval_avg_ms * 1e-3) / 1e9
+    clocks = clk.summary(t_start, t_end)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
+        "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic (seeded lognormal Gaussian-random-field grades; no public dataset)",
+        "config": {"workload": "50x50x20 = 50,000 blocks, S=100, T=20, 262,144 moves (50% shifts, 50% swaps)",
+                   "step": "mm_eval_moves + mm_topk(k=32) + mm_apply_best", "topk": TOPK,
+                   "l2": "flushed before every step (256 MB write outside the step events)",
+                   "per_rank_moves": n, "parallelism": f"independent batches x{world}"},
+        "roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": achieved_gbs / peaks["hbm_gbs"], "traffic": profiled_traffic(),
+                     "kernel": EVAL_KERNEL, "kernel_ms": eval_avg_ms,
+                     "algorithmic_bytes_per_launch": alg, "peak_source": f"{which} (MEASURED_PEAKS.json hbm_gbs)"},
+        "e2e": {"value": evals_per_step * world / e2e_avg, "unit": UNIT,
+                "h2d_bytes_per_step": int(p.moves.nbytes), "d2h_bytes_per_step": TOPK * 8 + 4 + 16,
+                "ms_per_step": e2e_avg * 1e3,
+                "path": "pinned host moves -> mm_eval_moves -> mm_topk -> top-k to host -> mm_apply_move"},
+        "gpu_launches": launches_per_step * K,
+        "clocks": clocks,
+        "check": {"last_apply": applied, "npv_mean": npv_mean},
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(p, budget_s=args.cpu_budget)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=12.0)
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return reference_arm(args)
+    return gpu_arm(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,210 @@
+/*
+ * mm.h - C ABI of the B300 move-evaluation engine for stochastic open-pit
+ * mine scheduling.
+ *
+ * The engine evaluates batches of candidate schedule moves (single-block
+ * period shifts and block-pair swaps) against S geological grade scenarios.
+ * Problem statement: Section 5.6 of the paper, Eq. 14 (objective: discounted
+ * mining cost plus scenario-averaged processing value), Eq. 15 (a block is
+ * mined no earlier than its direct predecessors), Eq. 16 (mined tonnage per
+ * period within capacity M_t), with the second stage (Eq. 17-21) read as a
+ * single processing mode: a block is ore in a scenario when processing beats
+ * dumping it (Eq. 18, zero processed mass = waste), and the mill's ore tonnage
+ * per period is held to a target Q_t by piecewise-linear shortfall/excess
+ * penalties.  Cash flows and penalties are discounted per period by
+ * d_t = (1 + r)^-t, t = 0..T-1 (Algorithm 5; Section 7.1.2).  The candidate
+ * moves are those of Algorithms 4-5 (assign block b* to period t*).
+ *
+ * Conventions for every call:
+ *   - Pointers named *_dev are device pointers owned by the caller; *_host are
+ *     host pointers owned by the caller.  The library owns all model state on
+ *     the device and frees it in mm_model_destroy.
+ *   - Asynchronous calls (mm_eval_*, mm_topk, mm_apply_best) only enqueue work
+ *     on the model's stream and return MM_OK unless an argument is invalid or a
+ *     launch fails.  Synchronising calls (mm_schedule_set/get, mm_apply_move,
+ *     mm_npv, mm_get_*) wait for the stream.
+ *   - A bad move inside a batch (block id or period out of range) does not fail
+ *     the batch: its flag is 0, its score -INFINITY, and the next synchronising
+ *     call returns MM_ERR_BAD_MOVE once (sticky bit, then cleared).
+ *   - Errors: every call returns an mm_status; mm_last_error() gives a message
+ *     for the last failing call on the calling thread.  No call aborts, traps or
+ *     falls back to the CPU.
+ *   - A model is not thread-safe: one host thread at a time.
+ *
+ * Limits: 1 <= T <= 254 (period byte; value T means "unmined"), 1 <= S <= 1024,
+ * B < 2^31, total block mass < 2^62 t, top-k k <= 1024.
+ */
+#ifndef MM_H
+#define MM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MM_OK = 0,
+    MM_ERR_INVALID_ARG = 1, /* a NULL pointer, size or value out of range */
+    MM_ERR_CUDA = 2,        /* a CUDA runtime call failed */
+    MM_ERR_OOM = 3,         /* device allocation failed or over the model's memory cap */
+    MM_ERR_OVERFLOW = 4,    /* tonnage sums would overflow 2^62 */
+    MM_ERR_INFEASIBLE = 5,  /* mm_apply_move: the move's feasibility flag is 0; nothing changed */
+    MM_ERR_BAD_MOVE = 6,    /* a move referenced a block or period out of range */
+    MM_ERR_TIMEOUT = 7,     /* a bounded device wait ran out */
+    MM_ERR_STATE = 8        /* call out of order (e.g. eval before mm_schedule_set) */
+} mm_status;
+
+/* Opaque model: block model, scenarios, schedule and derived device state. */
+typedef struct mm_model mm_model;
+
+/* One candidate move (8 bytes; arrays of moves are [n] of these).
+ *   arg >= 0 : swap the periods of blocks b1 and arg;
+ *   arg <  0 : shift block b1 to period -arg-1 (0..T; T = leave unmined).
+ * A shift to the block's own period, a swap of a block with itself or of two
+ * blocks in the same period changes nothing (delta 0). */
+typedef struct {
+    int32_t b1;
+    int32_t arg;
+} mm_move;
+
+/* Model description (Section 5.6 parameter table: blocks, n_s scenarios,
+ * n_T periods, m_b, M_t, direct predecessors; economics of Eq. 14/17). */
+typedef struct {
+    int32_t n_blocks, n_scenarios, n_periods; /* B, S, T */
+    /* Precedence: either a grid for the 1-5 pattern (nx*ny*nz == B, block
+     * b = x + nx*(y + ny*z), z = 0 on top; the predecessors of (x,y,z) are
+     * (x,y,z-1), (x+-1,y,z-1), (x,y+-1,z-1), clipped at the boundary), or
+     * nx = ny = nz = 0 and a CSR of direct predecessors (host arrays,
+     * pred_ptr[B+1], pred_idx[pred_ptr[B]]; must describe a DAG). */
+    int32_t nx, ny, nz;
+    const int32_t *pred_ptr, *pred_idx;
+    const uint32_t *mass_t;         /* [B] host, block mass m_b in tonnes, > 0 */
+    const double *grade;            /* [B][S] host, g/t, scenario fastest, finite, >= 0 */
+    const uint64_t *cap_t;          /* [T] host, mining capacity M_t in tonnes */
+    const uint64_t *mill_target_t;  /* [T] host, mill ore target Q_t in tonnes */
+    double price, recovery;         /* $/g, recovered fraction */
+    double mining_cost, proc_cost;  /* $/t mined, $/t processed */
+    double shortfall_pen, excess_pen; /* $/t below / above Q_t */
+    double discount_rate;           /* r, per period */
+    double lambda;                  /* risk weight of score = mean - lambda*std */
+    void *cuda_stream;              /* cudaStream_t for all work (NULL = default stream) */
+} mm_model_desc;
+
+/* Create a model: copies the inputs to the device, classifies every
+ * (block, scenario) as ore or waste in FP64 with the rule
+ * (g*price)*recovery > proc_cost (strict), and builds the FP32 per-block
+ * value rows v[b][s] = ore ? m((g*price)*recovery - pc) - m*mc : -m*mc and the
+ * ore bitmask.  The model has no schedule yet.  Synchronising.
+ * Errors: MM_ERR_INVALID_ARG (NULL, sizes, non-finite or negative grade, zero
+ * mass, bad CSR), MM_ERR_OVERFLOW, MM_ERR_OOM, MM_ERR_CUDA. */
+mm_status mm_model_create(const mm_model_desc *desc, mm_model **out);
+
+/* Free all device state of the model.  NULL is ignored. */
+void mm_model_destroy(mm_model *m);
+
+/* Use another stream for subsequent calls (NULL = default stream). */
+mm_status mm_set_stream(mm_model *m, void *cuda_stream);
+
+/* Install a schedule: period_host[B] in 0..T (T = unmined).  Rebuilds, from
+ * scratch, the per-period mined tonnage, per-(period, scenario) ore tonnage
+ * (int64, exact), metal (FP64), the per-scenario NPV (FP64) and the tables the
+ * move evaluator reads; this also discards any drift accumulated by applies.
+ * *base_feasible_out (nullable) receives 1 when the schedule satisfies Eq. 15
+ * on every arc and Eq. 16 in every period.  Synchronising. */
+mm_status mm_schedule_set(mm_model *m, const uint8_t *period_host, int *base_feasible_out);
+
+/* Copy the current schedule to period_host[B].  Synchronising. */
+mm_status mm_schedule_get(mm_model *m, uint8_t *period_host);
+
+/* Evaluate n moves against the current schedule (Algorithm 5's candidate
+ * evaluation, per scenario).  For move i and scenario s:
+ *   delta_s  = NPV_s(x') - NPV_s(x)  (value change plus discounted change of
+ *              the mill-deviation penalties of the affected periods);
+ *   score[i] = mean_s delta_s - lambda * std_s delta_s (population std);
+ *   feasible[i] = 1 iff every precedence arc with an end in a moved block holds
+ *              in x' and every period a moved block leaves or enters is within
+ *              capacity in x' (exact integer test; equals full feasibility of x'
+ *              when x is feasible);
+ *   mean[i]  = mean_s delta_s (mean_dev may be NULL).
+ * moves_dev[n] (8-byte aligned), score_dev[n], feasible_dev[n], mean_dev[n]:
+ * device memory.  n = 0 is allowed.  Asynchronous. */
+mm_status mm_eval_moves(mm_model *m, const mm_move *moves_dev, int64_t n, float *score_dev,
+                        uint8_t *feasible_dev, float *mean_dev);
+
+/* Tile shape of the move evaluator (chosen by the autotuner or by hand):
+ * team = lanes that evaluate one move (4, 8, 16 or 32; 0 = built-in choice),
+ * ctas_per_sm = resident CTAs per SM of the persistent grid (0 = occupancy
+ * maximum).  team must leave at most 8 scenario quads per lane
+ * (ceil(ceil(S/4)/team) <= 8), else MM_ERR_INVALID_ARG. */
+mm_status mm_set_tile(mm_model *m, int32_t team, int32_t ctas_per_sm);
+
+/* Evaluation options for mm_eval_moves_ex. */
+enum {
+    MM_EVAL_PLAIN = 0,     /* FP32 scenario sums, tree reduction */
+    MM_EVAL_KAHAN = 1      /* compensated (TwoSum) scenario sums for mean and variance */
+};
+
+/* mm_eval_moves with options and an optional per-scenario output:
+ * delta_dev[n][S] (FP32, row i = move i; may be NULL). */
+mm_status mm_eval_moves_ex(mm_model *m, const mm_move *moves_dev, int64_t n, float *score_dev,
+                           uint8_t *feasible_dev, float *mean_dev, float *delta_dev, int32_t options);
+
+/* The k feasible moves with the largest score, ties to the lower move index
+ * (replaces the paper's atomic per-CTA best-move reduction, Algorithm 5 and
+ * Section 6 Phase 5, with an exact, deterministic selection).  Reads
+ * score_dev[n], feasible_dev[n]; writes idx_dev[k] (move indices, best first),
+ * topscore_dev[k] and *count_dev = min(k, number of feasible moves with a
+ * non-NaN score).  -0.0 and +0.0 compare equal.  1 <= k <= 1024.
+ * Device memory; asynchronous.  Uses model-owned scratch, grown on demand
+ * (the first call with a larger n allocates). */
+mm_status mm_topk(mm_model *m, const float *score_dev, const uint8_t *feasible_dev, int64_t n,
+                  int32_t k, int32_t *idx_dev, float *topscore_dev, int32_t *count_dev);
+
+/* Apply one move (Algorithm 4: assign S[b*] <- t*) if its feasibility flag is
+ * 1: updates the schedule, the integer tonnages, the FP64 metal accumulators,
+ * the per-scenario NPV and the evaluator's tables for the affected periods.
+ * Returns the new NPV mean and std over scenarios (FP64; pointers nullable).
+ * MM_ERR_INFEASIBLE or MM_ERR_BAD_MOVE: nothing changed.  Synchronising. */
+mm_status mm_apply_move(mm_model *m, mm_move move, double *npv_mean_out, double *npv_std_out);
+
+/* Device-side apply of the best move of a batch, for search loops that never
+ * leave the GPU: if *count_dev > 0, applies moves_dev[idx_dev[0]] exactly as
+ * mm_apply_move does (re-checking feasibility on the device).  The outcome
+ * (applied 0/1, NPV mean and std) is kept on the device and returned by the
+ * next mm_last_apply call.  moves_dev[n] is the batch idx_dev indexes; an
+ * index outside 0..n-1 is treated as a bad move (nothing applied, sticky
+ * MM_ERR_BAD_MOVE).  Asynchronous. */
+mm_status mm_apply_best(mm_model *m, const mm_move *moves_dev, int64_t n, const int32_t *idx_dev,
+                        const int32_t *count_dev);
+
+/* Outcome of the last mm_apply_best: *applied (1 if a move was applied),
+ * NPV mean and std after it.  Pointers nullable.  Synchronising. */
+mm_status mm_last_apply(mm_model *m, int32_t *applied, double *npv_mean_out, double *npv_std_out);
+
+/* Per-scenario NPV of the current schedule (FP64, [S], nullable) and its mean
+ * and population std (nullable).  Synchronising. */
+mm_status mm_npv(mm_model *m, double *npv_per_scenario_host, double *mean, double *std);
+
+/* Sizes: any pointer may be NULL.  s_pad = row stride of the value rows (S
+ * rounded up to a multiple of 8). */
+mm_status mm_model_info(const mm_model *m, int32_t *B, int32_t *S, int32_t *T, int32_t *s_pad);
+
+/* Inspection (synchronising; host outputs):
+ *   ore_host[B][ceil(S/32)]  bit (s % 32) of word s / 32 = ore flag of (b, s);
+ *   value_host[B][S]         FP32 value rows;
+ *   mined_host[T], ore_t_host[T][S]  integer tonnages of the current schedule;
+ *   metal_host[T][S]         FP64 metal accumulators (grams in situ of ore). */
+mm_status mm_get_ore(mm_model *m, uint32_t *ore_host);
+mm_status mm_get_values(mm_model *m, float *value_host);
+mm_status mm_get_tonnage(mm_model *m, int64_t *mined_host, int64_t *ore_t_host);
+mm_status mm_get_metal(mm_model *m, double *metal_host);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char *mm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MM_H */

@@ -1,0 +1,281 @@
+"""Python binding of the B300 move-evaluation engine (libmm.so, C ABI in mm.h).
+
+Argument marshalling only: every step of the evaluation runs in the CUDA
+library.  PyTorch supplies device memory and the stream.  If the library is
+missing the import fails loudly; there is no CPU fallback.
+
+Typical use::
+
+    m = Model.from_problem(prob)          # grades, masses, economics -> device
+    m.schedule_set(prob.x0)
+    moves = torch.as_tensor(prob.moves, device="cuda")
+    score, feas, mean = m.eval_moves(moves)
+    idx, top, count = m.topk(score, feas, k=32)
+    m.apply_move(tuple(prob.moves[int(idx[0])]))
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Tuple
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libmm.so")
+
+MM_OK = 0
+STATUS = {0: "MM_OK", 1: "MM_ERR_INVALID_ARG", 2: "MM_ERR_CUDA", 3: "MM_ERR_OOM", 4: "MM_ERR_OVERFLOW",
+          5: "MM_ERR_INFEASIBLE", 6: "MM_ERR_BAD_MOVE", 7: "MM_ERR_TIMEOUT", 8: "MM_ERR_STATE"}
+MM_EVAL_PLAIN = 0
+MM_EVAL_KAHAN = 1
+TOPK_MAX = 1024
+
+
+class MMError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class MMModelDesc(C.Structure):
+    _fields_ = [
+        ("n_blocks", C.c_int32), ("n_scenarios", C.c_int32), ("n_periods", C.c_int32),
+        ("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
+        ("pred_ptr", C.c_void_p), ("pred_idx", C.c_void_p),
+        ("mass_t", C.c_void_p), ("grade", C.c_void_p),
+        ("cap_t", C.c_void_p), ("mill_target_t", C.c_void_p),
+        ("price", C.c_double), ("recovery", C.c_double),
+        ("mining_cost", C.c_double), ("proc_cost", C.c_double),
+        ("shortfall_pen", C.c_double), ("excess_pen", C.c_double),
+        ("discount_rate", C.c_double), ("lam", C.c_double),
+        ("cuda_stream", C.c_void_p),
+    ]
+
+
+class MMMove(C.Structure):
+    _fields_ = [("b1", C.c_int32), ("arg", C.c_int32)]
+
+
+_lib = None
+
+# (name, restype, argtypes): every entry point declared in include/mm.h
+P, I32, I64, D = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+SIGNATURES = [
+    ("mm_model_create", C.c_int, [P, P]),
+    ("mm_model_destroy", None, [P]),
+    ("mm_set_stream", C.c_int, [P, P]),
+    ("mm_schedule_set", C.c_int, [P, P, P]),
+    ("mm_schedule_get", C.c_int, [P, P]),
+    ("mm_eval_moves", C.c_int, [P, P, I64, P, P, P]),
+    ("mm_eval_moves_ex", C.c_int, [P, P, I64, P, P, P, P, I32]),
+    ("mm_set_tile", C.c_int, [P, I32, I32]),
+    ("mm_topk", C.c_int, [P, P, P, I64, I32, P, P, P]),
+    ("mm_apply_move", C.c_int, [P, MMMove, P, P]),
+    ("mm_apply_best", C.c_int, [P, P, I64, P, P]),
+    ("mm_last_apply", C.c_int, [P, P, P, P]),
+    ("mm_npv", C.c_int, [P, P, P, P]),
+    ("mm_model_info", C.c_int, [P, P, P, P, P]),
+    ("mm_get_ore", C.c_int, [P, P]),
+    ("mm_get_values", C.c_int, [P, P]),
+    ("mm_get_tonnage", C.c_int, [P, P, P]),
+    ("mm_get_metal", C.c_int, [P, P]),
+    ("mm_last_error", C.c_char_p, []),
+]
+
+
+def lib():
+    """Load libmm.so (built by build.py); raise if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"CUDA library not built: {LIB_PATH} is missing (run paper_2511_18296_b300/build.py)")
+    l = C.CDLL(LIB_PATH)
+    for name, res, args in SIGNATURES:
+        f = getattr(l, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = l
+    return l
+
+
+def _check(st: int):
+    if st != MM_OK:
+        raise MMError(st, lib().mm_last_error().decode())
+
+
+def _ptr(t) -> int:
+    return 0 if t is None else int(t.data_ptr())
+
+
+def _np(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def _stream_handle(stream) -> int:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+class Model:
+    """One block model on the device (owns an mm_model*)."""
+
+    def __init__(self, B: int, S: int, T: int, mass, grade, cap, target, price: float, recovery: float,
+                 mining_cost: float, proc_cost: float, shortfall_pen: float, excess_pen: float,
+                 discount_rate: float, lam: float, grid: Optional[Tuple[int, int, int]] = None,
+                 preds: Optional[Tuple[np.ndarray, np.ndarray]] = None, stream=None):
+        L = lib()
+        self._keep = dict(mass=_np(mass, np.uint32), grade=_np(grade, np.float64).reshape(B, S),
+                          cap=_np(cap, np.uint64), target=_np(target, np.uint64))
+        nx = ny = nz = 0
+        pp = pi = None
+        if grid is not None:
+            nx, ny, nz = grid
+        else:
+            self._keep["pp"] = pp = _np(preds[0], np.int32)
+            self._keep["pi"] = pi = _np(preds[1] if len(preds[1]) else np.zeros(1), np.int32)
+        k = self._keep
+        self.desc = MMModelDesc(B, S, T, nx, ny, nz,
+                                pp.ctypes.data if pp is not None else None,
+                                pi.ctypes.data if pi is not None else None,
+                                k["mass"].ctypes.data, k["grade"].ctypes.data, k["cap"].ctypes.data,
+                                k["target"].ctypes.data, price, recovery, mining_cost, proc_cost, shortfall_pen,
+                                excess_pen, discount_rate, lam, _stream_handle(stream))
+        h = C.c_void_p()
+        _check(L.mm_model_create(C.byref(self.desc), C.byref(h)))
+        self.h = h
+        self.B, self.S, self.T = B, S, T
+        self._keep = None  # the library copied everything it needs
+        sp = C.c_int32()
+        _check(L.mm_model_info(self.h, None, None, None, C.byref(sp)))
+        self.S_pad = sp.value
+
+    @classmethod
+    def from_problem(cls, p, preds=None, stream=None) -> "Model":
+        """From a workloads.Problem (1-5 grid unless a predecessor CSR is given)."""
+        return cls(p.B, p.S, p.T, p.mass, p.grade, p.cap, p.target, p.price, p.recovery, p.mining_cost,
+                   p.proc_cost, p.shortfall_pen, p.excess_pen, p.discount_rate, p.lam,
+                   grid=None if preds is not None else (p.nx, p.ny, p.nz), preds=preds, stream=stream)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().mm_model_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_tile(self, team: int = 0, ctas_per_sm: int = 0):
+        _check(lib().mm_set_tile(self.h, team, ctas_per_sm))
+
+    def set_stream(self, stream=None):
+        _check(lib().mm_set_stream(self.h, _stream_handle(stream)))
+
+    # -- schedule -------------------------------------------------------
+    def schedule_set(self, period) -> bool:
+        x = _np(period, np.uint8)
+        assert x.shape == (self.B,)
+        feas = C.c_int()
+        _check(lib().mm_schedule_set(self.h, x.ctypes.data, C.byref(feas)))
+        return bool(feas.value)
+
+    def schedule_get(self) -> np.ndarray:
+        x = np.zeros(self.B, np.uint8)
+        _check(lib().mm_schedule_get(self.h, x.ctypes.data))
+        return x
+
+    # -- evaluation -----------------------------------------------------
+    def eval_moves(self, moves, score=None, feas=None, mean=None, want_mean=True, delta=None,
+                   kahan: bool = False):
+        """moves: int32 CUDA tensor [n, 2].  Returns (score f32, feasible u8, mean f32 or None)."""
+        import torch
+        assert moves.is_cuda and moves.dtype == torch.int32 and moves.is_contiguous()
+        n = moves.shape[0]
+        dev = moves.device
+        if score is None:
+            score = torch.empty(n, dtype=torch.float32, device=dev)
+        if feas is None:
+            feas = torch.empty(n, dtype=torch.uint8, device=dev)
+        if mean is None and want_mean:
+            mean = torch.empty(n, dtype=torch.float32, device=dev)
+        L = lib()
+        if delta is None and not kahan:
+            _check(L.mm_eval_moves(self.h, _ptr(moves), n, _ptr(score), _ptr(feas), _ptr(mean)))
+        else:
+            _check(L.mm_eval_moves_ex(self.h, _ptr(moves), n, _ptr(score), _ptr(feas), _ptr(mean), _ptr(delta),
+                                      MM_EVAL_KAHAN if kahan else MM_EVAL_PLAIN))
+        return score, feas, mean
+
+    def eval_deltas(self, moves, kahan: bool = False):
+        """Per-scenario deltas [n, S] as well (parity/debug path)."""
+        import torch
+        delta = torch.empty((moves.shape[0], self.S), dtype=torch.float32, device=moves.device)
+        score, feas, mean = self.eval_moves(moves, delta=delta, kahan=kahan)
+        return score, feas, mean, delta
+
+    def topk(self, score, feas, k: int, idx=None, top=None, count=None):
+        import torch
+        n = score.shape[0]
+        dev = score.device
+        if idx is None:
+            idx = torch.empty(k, dtype=torch.int32, device=dev)
+        if top is None:
+            top = torch.empty(k, dtype=torch.float32, device=dev)
+        if count is None:
+            count = torch.empty(1, dtype=torch.int32, device=dev)
+        _check(lib().mm_topk(self.h, _ptr(score), _ptr(feas), n, k, _ptr(idx), _ptr(top), _ptr(count)))
+        return idx, top, count
+
+    # -- apply ----------------------------------------------------------
+    def apply_move(self, move) -> Tuple[float, float]:
+        """Apply (b1, arg); returns the NPV (mean, std).  Raises MMError with
+        MM_ERR_INFEASIBLE / MM_ERR_BAD_MOVE (nothing changed)."""
+        mean, sd = C.c_double(), C.c_double()
+        _check(lib().mm_apply_move(self.h, MMMove(int(move[0]), int(move[1])), C.byref(mean), C.byref(sd)))
+        return mean.value, sd.value
+
+    def apply_best(self, moves, idx, count):
+        _check(lib().mm_apply_best(self.h, _ptr(moves), int(moves.shape[0]), _ptr(idx), _ptr(count)))
+
+    def last_apply(self):
+        a, mean, sd = C.c_int32(), C.c_double(), C.c_double()
+        _check(lib().mm_last_apply(self.h, C.byref(a), C.byref(mean), C.byref(sd)))
+        return a.value, mean.value, sd.value
+
+    # -- inspection -----------------------------------------------------
+    def npv(self):
+        v = np.zeros(self.S, np.float64)
+        mean, sd = C.c_double(), C.c_double()
+        _check(lib().mm_npv(self.h, v.ctypes.data, C.byref(mean), C.byref(sd)))
+        return v, mean.value, sd.value
+
+    def ore_bits(self) -> np.ndarray:
+        """uint8 [B][S] ore flags unpacked from the device bitmask."""
+        W = (self.S + 31) // 32
+        w = np.zeros((self.B, W), np.uint32)
+        _check(lib().mm_get_ore(self.h, w.ctypes.data))
+        bits = np.unpackbits(w.view(np.uint8).reshape(self.B, W * 4), axis=1, bitorder="little")
+        return bits[:, :self.S]
+
+    def values(self) -> np.ndarray:
+        v = np.zeros((self.B, self.S), np.float32)
+        _check(lib().mm_get_values(self.h, v.ctypes.data))
+        return v
+
+    def tonnage(self):
+        mined = np.zeros(self.T, np.int64)
+        oreT = np.zeros((self.T, self.S), np.int64)
+        _check(lib().mm_get_tonnage(self.h, mined.ctypes.data, oreT.ctypes.data))
+        return mined, oreT
+
+    def metal(self) -> np.ndarray:
+        m = np.zeros((self.T, self.S), np.float64)
+        _check(lib().mm_get_metal(self.h, m.ctypes.data))
+        return m

@@ -1,0 +1,121 @@
+// Internal definitions of the move-evaluation engine (device state, launch
+// helpers).  Not part of the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "mm.h"
+
+namespace mm {
+
+constexpr int kMaxS = 1024;       // scenarios per model
+constexpr int kMaxT = 254;        // periods; the period byte value T means unmined
+constexpr int kTopkMax = 1024;    // largest k of mm_topk
+constexpr int kHistBits = 16;     // top-k coarse histogram over the score's top bits
+constexpr int kHistBins = 1 << kHistBits;
+
+// Sticky device status bits, read and cleared by synchronising calls.
+enum : uint32_t { kStBadMove = 1u, kStTimeout = 2u };
+
+// Outcome of an apply, written by the device.
+struct ApplyResult {
+    int32_t applied;   // 1 if the move was applied
+    int32_t status;    // mm_status of the apply
+    double mean, std;  // NPV mean / population std over scenarios after it
+};
+
+// Packed per-block schedule word read by the evaluator with one 4-byte load:
+//   bits 0-7 period x_b, bits 8-15 lo_b = max period over direct predecessors
+//   (0 if none), bits 16-23 hi_b = min period over direct successors (T if none).
+// A shift of b to t' satisfies every arc at b iff lo_b <= t' <= hi_b.
+__host__ __device__ inline uint32_t blk_pack(uint32_t t, uint32_t lo, uint32_t hi) {
+    return t | (lo << 8) | (hi << 16);
+}
+__host__ __device__ inline uint32_t blk_period(uint32_t w) { return w & 0xffu; }
+__host__ __device__ inline uint32_t blk_lo(uint32_t w) { return (w >> 8) & 0xffu; }
+__host__ __device__ inline uint32_t blk_hi(uint32_t w) { return (w >> 16) & 0xffu; }
+
+// Top-k scratch owned by a model (or by the caller-free static variant).
+struct TopkScratch {
+    uint32_t *hist = nullptr;      // [kHistBins] coarse histogram, zero between calls
+    uint64_t *sure = nullptr;      // [kTopkMax] keys above the cut-off bin
+    uint64_t *maybe = nullptr;     // [cap_maybe] keys inside the cut-off bin
+    uint32_t *ctl = nullptr;       // [8] tickets, counters, cut-off
+    int64_t cap_maybe = 0;
+};
+
+}  // namespace mm
+
+struct mm_model {
+    int32_t B = 0, S = 0, T = 0, S_pad = 0, W = 0;
+    int32_t nx = 0, ny = 0, nz = 0;   // grid of the 1-5 pattern, or 0 (CSR)
+    int32_t uniform_mass = 0;
+    uint32_t m_uniform = 0;
+    double price = 0, recovery = 0, mining_cost = 0, proc_cost = 0;
+    double shortfall_pen = 0, excess_pen = 0, discount_rate = 0, lambda = 0;
+    cudaStream_t stream = nullptr;
+    int has_schedule = 0;
+    int num_sms = 148;
+    int team = 0;          // evaluator tile: lanes per move (0 = default)
+    int ctas_per_sm = 0;   // evaluator grid: CTAs per SM (0 = occupancy maximum)
+
+    std::vector<double> h_disc;      // [T+1] d_t in FP64, d_T = 0
+    std::vector<uint64_t> h_cap;     // [T]
+    std::vector<uint64_t> h_target;  // [T]
+
+    // device state
+    uint32_t *mass = nullptr;    // [B]
+    double *grade = nullptr;     // [B][S]
+    float *val = nullptr;        // [B][S_pad] FP32 value rows (padding 0)
+    uint32_t *ore = nullptr;     // [B][W] ore bits
+    uint32_t *blk = nullptr;     // [B] packed period / lo / hi
+    int32_t *pred_ptr = nullptr, *pred_idx = nullptr;  // CSR (device) when nx == 0
+    int32_t *succ_ptr = nullptr, *succ_idx = nullptr;
+    int32_t *order = nullptr;    // [B] blocks sorted by period (schedule_set)
+    int32_t *porder = nullptr;   // [T+2] offsets of each period in order
+    int64_t *minedT = nullptr;   // [T+1]
+    int64_t *oreT = nullptr;     // [T+1][S]  (row T stays 0)
+    double *metal = nullptr;     // [T][S]    grams in situ of ore
+    double *npv = nullptr;       // [S]
+    float *tab = nullptr;        // [2][T+1][S_pad]  Pout, Pin
+    float *ddt = nullptr;        // [(T+1)*(T+1)]    d_{t'} - d_t  (index t*(T+1)+t')
+    double *disc = nullptr;      // [T+1]
+    uint64_t *cap = nullptr;     // [T+1]  cap[T] = max
+    uint64_t *target = nullptr;  // [T+1]
+    uint32_t *status = nullptr;  // sticky bits
+    mm::ApplyResult *apply_res = nullptr;       // device
+    mm::ApplyResult *apply_res_host = nullptr;  // pinned host mirror
+    uint32_t *status_host = nullptr;            // pinned
+    mm::TopkScratch topk;
+};
+
+namespace mm {
+
+// Thread-local error message and status helpers.
+mm_status set_error(mm_status st, const char *fmt, ...);
+mm_status cuda_status(cudaError_t e, const char *what);
+mm_status check_launch(const char *what);
+mm_status read_sticky(mm_model *m);  // synchronises, clears and maps the sticky bits
+
+// Kernels and launchers shared between translation units.
+mm_status rebuild_tables(mm_model *m);                     // Pout/Pin from oreT
+mm_status eval_launch(mm_model *m, const mm_move *moves, int64_t n, float *score, uint8_t *feas, float *mean,
+                      float *delta, int32_t options, int team, int ctas_per_sm);
+int default_team(int S);
+mm_status topk_launch(const float *score, const uint8_t *feas, int64_t n, int32_t k, int32_t *idx,
+                      float *top, int32_t *count, TopkScratch &scr, int num_sms, cudaStream_t st);
+mm_status topk_scratch_reserve(TopkScratch &scr, int64_t n);
+void topk_scratch_free(TopkScratch &scr);
+
+}  // namespace mm
+
+#define MM_CUDA_TRY(expr, what)                              \
+    do {                                                     \
+        cudaError_t e_ = (expr);                             \
+        if (e_ != cudaSuccess) return mm::cuda_status(e_, what); \
+    } while (0)

@@ -1,0 +1,852 @@
+// Model store, schedule state and the apply-move kernel.
+//
+// Device layout (per model):
+//   val   FP32 [B][S_pad]   per-block value rows, scenario fastest, 32-byte rows
+//   ore   u32  [B][W]       ore bits, W = ceil(S/32)
+//   blk   u32  [B]          packed period | lo << 8 | hi << 16
+//   grade FP64 [B][S]       kept for the FP64 metal accumulators
+//   minedT i64 [T+1], oreT i64 [T+1][S], metal FP64 [T][S], npv FP64 [S]
+//   tab   FP32 [2][T+1][S_pad]  NPV change of removing / adding one block of ore
+//                               in period t, scenario s (uniform block mass)
+#include <cmath>
+#include <cstdarg>
+#include <cstring>
+#include <limits>
+#include <numeric>
+
+#include "mm_internal.cuh"
+#include "mm_move.cuh"
+
+namespace mm {
+
+static thread_local char g_err[512] = "";
+
+mm_status set_error(mm_status st, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+mm_status cuda_status(cudaError_t e, const char *what) {
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return set_error(MM_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
+    }
+    return set_error(MM_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+mm_status check_launch(const char *what) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_status(e, what);
+    return MM_OK;
+}
+
+mm_status read_sticky(mm_model *m) {
+    MM_CUDA_TRY(cudaMemcpyAsync(m->status_host, m->status, sizeof(uint32_t), cudaMemcpyDeviceToHost, m->stream),
+                "read status");
+    MM_CUDA_TRY(cudaStreamSynchronize(m->stream), "synchronize");
+    uint32_t st = *m->status_host;
+    if (st) {
+        MM_CUDA_TRY(cudaMemsetAsync(m->status, 0, sizeof(uint32_t), m->stream), "clear status");
+        if (st & kStTimeout) return set_error(MM_ERR_TIMEOUT, "a bounded device wait ran out");
+        if (st & kStBadMove) return set_error(MM_ERR_BAD_MOVE, "a batch contained a move with a block or period out of range");
+    }
+    return MM_OK;
+}
+
+static Topo topo_of(const mm_model *m) {
+    Topo tp;
+    tp.B = m->B; tp.T = m->T; tp.nx = m->nx; tp.ny = m->ny; tp.nz = m->nz;
+    tp.pred_ptr = m->pred_ptr; tp.pred_idx = m->pred_idx; tp.succ_ptr = m->succ_ptr; tp.succ_idx = m->succ_idx;
+    return tp;
+}
+
+// ---------------------------------------------------------------- kernels
+
+// Ore/waste and FP32 value rows.  One thread per (block, ore word): 32
+// scenarios.  FP64 with explicit round-to-nearest operations in the order
+// ((g*price)*recovery) > proc_cost; value = m*(rev - pc) - m*mc or -(m*mc).
+__global__ void k_classify(const double *__restrict__ grade, const uint32_t *__restrict__ mass, int32_t B, int32_t S,
+                           int32_t S_pad, int32_t W, double price, double recovery, double pc, double mc,
+                           float *__restrict__ val, uint32_t *__restrict__ ore) {
+    int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= (int64_t)B * W) return;
+    int32_t b = (int32_t)(gid / W), w = (int32_t)(gid % W);
+    double m = (double)mass[b];
+    uint32_t bits = 0;
+    for (int j = 0; j < 32; j++) {
+        int s = w * 32 + j;
+        if (s >= S_pad) break;
+        float v = 0.0f;
+        if (s < S) {
+            double g = grade[(int64_t)b * S + s];
+            double rev = __dmul_rn(__dmul_rn(g, price), recovery);
+            bool o = rev > pc;
+            double vv = o ? __dsub_rn(__dmul_rn(m, __dsub_rn(rev, pc)), __dmul_rn(m, mc)) : -__dmul_rn(m, mc);
+            v = __double2float_rn(vv);
+            bits |= (o ? 1u : 0u) << j;
+        }
+        val[(int64_t)b * S_pad + s] = v;
+    }
+    ore[gid] = bits;
+}
+
+// Packed period/lo/hi word of every block.
+__global__ void k_blk_build(Topo tp, const uint8_t *__restrict__ period, uint32_t *__restrict__ blk) {
+    int32_t b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= tp.B) return;
+    blk[b] = block_bounds(tp, b, [&](int32_t j) { return (uint32_t)period[j]; });
+}
+
+// Base feasibility: every arc p -> b with x_p <= x_b (checked from lo_b).
+__global__ void k_base_arcs(int32_t B, const uint32_t *__restrict__ blk, uint32_t *__restrict__ bad) {
+    int32_t b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    uint32_t w = blk[b];
+    if (blk_lo(w) > blk_period(w)) atomicOr(bad, 1u);
+}
+
+// Per-period sums in a fixed order (blocks of period t sorted by id):
+// minedT[t], oreT[t][s], metal[t][s].  Grid (T, ceil(S/32)); block of 32 x 8:
+// lanes over scenarios, 8 slices over the period's blocks, combined in slice order.
+__global__ void k_accum(const int32_t *__restrict__ order, const int32_t *__restrict__ porder,
+                        const uint32_t *__restrict__ mass, const uint32_t *__restrict__ ore,
+                        const double *__restrict__ grade, int32_t S, int32_t W, int32_t T,
+                        int64_t *__restrict__ minedT, int64_t *__restrict__ oreT, double *__restrict__ metal) {
+    int t = blockIdx.x;
+    int s = blockIdx.y * 32 + threadIdx.x;
+    int slice = threadIdx.y;
+    int32_t beg = porder[t], end = porder[t + 1];
+    __shared__ int64_t s_ore[8][32];
+    __shared__ double s_met[8][32];
+    __shared__ int64_t s_mass[8][32];
+    int64_t o = 0, mt = 0;
+    double g = 0.0;
+    for (int32_t k = beg + slice; k < end; k += 8) {
+        int32_t b = order[k];
+        uint32_t mb = mass[b];
+        if (blockIdx.y == 0 && threadIdx.x == 0) mt += mb;  // one lane per slice counts mass
+        if (s < S && ((ore[(int64_t)b * W + (s >> 5)] >> (s & 31)) & 1u)) {
+            o += mb;
+            g = __dadd_rn(g, __dmul_rn((double)mb, grade[(int64_t)b * S + s]));
+        }
+    }
+    s_ore[slice][threadIdx.x] = o;
+    s_met[slice][threadIdx.x] = g;
+    s_mass[slice][threadIdx.x] = mt;
+    __syncthreads();
+    if (slice == 0) {
+        int64_t oo = 0;
+        double gg = 0.0;
+        for (int k = 0; k < 8; k++) {
+            oo += s_ore[k][threadIdx.x];
+            gg = __dadd_rn(gg, s_met[k][threadIdx.x]);
+        }
+        if (s < S) {
+            oreT[(int64_t)t * S + s] = oo;
+            metal[(int64_t)t * S + s] = gg;
+        }
+        if (blockIdx.y == 0 && threadIdx.x == 0) {
+            int64_t mm_ = 0;
+            for (int k = 0; k < 8; k++)
+                for (int l = 0; l < 32; l++) mm_ += s_mass[k][l];
+            minedT[t] = mm_;
+        }
+    }
+}
+
+// pen(x0) - pen(x1) for excess x = O - Q (exact integer parts, then FP64).
+__device__ __forceinline__ double pen_diff(int64_t x0, int64_t x1, double a, double e) {
+    int64_t s0 = x0 < 0 ? -x0 : 0, s1 = x1 < 0 ? -x1 : 0;
+    int64_t e0 = x0 > 0 ? x0 : 0, e1 = x1 > 0 ? x1 : 0;
+    return __dadd_rn(__dmul_rn(a, (double)(s0 - s1)), __dmul_rn(e, (double)(e0 - e1)));
+}
+
+__device__ __forceinline__ double pen_of(int64_t x, double a, double e) {
+    return x < 0 ? __dmul_rn(a, (double)(-x)) : __dmul_rn(e, (double)x);
+}
+
+// Pout[t][s] = d_t (pen(x) - pen(x - m)), Pin[t][s] = d_t (pen(x) - pen(x + m))
+// with x = oreT[t][s] - Q_t; zero for t = T and for padding scenarios.
+__device__ __forceinline__ void table_entry(int t, int s, int32_t S, int32_t S_pad, int32_t T, const int64_t *oreT,
+                                            const uint64_t *target, const double *disc, int64_t m, double a,
+                                            double e, float *tab) {
+    float po = 0.0f, pi = 0.0f;
+    if (t < T && s < S) {
+        int64_t x = oreT[(int64_t)t * S + s] - (int64_t)target[t];
+        double d = disc[t];
+        po = __double2float_rn(__dmul_rn(d, pen_diff(x, x - m, a, e)));
+        pi = __double2float_rn(__dmul_rn(d, pen_diff(x, x + m, a, e)));
+    }
+    tab[(int64_t)t * S_pad + s] = po;
+    tab[(int64_t)(T + 1) * S_pad + (int64_t)t * S_pad + s] = pi;
+}
+
+__global__ void k_tables(int32_t S, int32_t S_pad, int32_t T, const int64_t *__restrict__ oreT,
+                         const uint64_t *__restrict__ target, const double *__restrict__ disc, int64_t m, double a,
+                         double e, float *__restrict__ tab) {
+    int t = blockIdx.x;
+    for (int s = threadIdx.x; s < S_pad; s += blockDim.x) table_entry(t, s, S, S_pad, T, oreT, target, disc, m, a, e, tab);
+}
+
+// NPV_s = sum_t d_t (price*rec*metal - pc*oreT - mc*minedT - pen_t(oreT)).
+__device__ __forceinline__ double npv_of(int s, int32_t S, int32_t T, const double *disc, const double *metal,
+                                         const int64_t *oreT, const int64_t *minedT, const uint64_t *target,
+                                         double pr, double pc, double mc, double a, double e) {
+    double acc = 0.0;
+    for (int t = 0; t < T; t++) {
+        int64_t o = oreT[(int64_t)t * S + s];
+        double cash = __dsub_rn(__dsub_rn(__dmul_rn(pr, metal[(int64_t)t * S + s]), __dmul_rn(pc, (double)o)),
+                                __dmul_rn(mc, (double)minedT[t]));
+        double p = pen_of(o - (int64_t)target[t], a, e);
+        acc = __dadd_rn(acc, __dmul_rn(disc[t], __dsub_rn(cash, p)));
+    }
+    return acc;
+}
+
+__global__ void k_npv(int32_t S, int32_t T, const double *__restrict__ disc, const double *__restrict__ metal,
+                      const int64_t *__restrict__ oreT, const int64_t *__restrict__ minedT,
+                      const uint64_t *__restrict__ target, double pr, double pc, double mc, double a, double e,
+                      double *__restrict__ npv) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S) return;
+    npv[s] = npv_of(s, S, T, disc, metal, oreT, minedT, target, pr, pc, mc, a, e);
+}
+
+// Block-wide FP64 mean and population std of npv[0..S) (two passes).
+__device__ void npv_stats(const double *npv, int32_t S, double *mean, double *std) {
+    __shared__ double red[32];
+    double acc = 0.0;
+    for (int s = threadIdx.x; s < S; s += blockDim.x) acc += npv[s];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += red[w];
+        red[31] = t / S;
+    }
+    __syncthreads();
+    double mu = red[31];
+    __syncthreads();
+    double v = 0.0;
+    for (int s = threadIdx.x; s < S; s += blockDim.x) v += (npv[s] - mu) * (npv[s] - mu);
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += red[w];
+        *mean = mu;
+        *std = sqrt(t / S);
+    }
+}
+
+struct ApplyArgs {
+    Topo tp;
+    int32_t S, S_pad, W, T;
+    uint32_t m_uniform;
+    int32_t uniform;
+    const uint32_t *mass;
+    const uint32_t *ore;
+    const double *grade;
+    uint32_t *blk;
+    int64_t *minedT;
+    int64_t *oreT;
+    double *metal;
+    double *npv;
+    float *tab;
+    const double *disc;
+    const uint64_t *cap;
+    const uint64_t *target;
+    double pr, pc, mc, a, e;
+    ApplyResult *res;
+    uint32_t *status;
+};
+
+// Apply one move on a single CTA: exact re-check, period update, integer
+// tonnages, FP64 metal, lo/hi of the neighbourhood, tables of the affected
+// periods, then NPV_s from the accumulators and its mean/std.
+// The move comes either by value (from_dev = 0) or as moves[idx[0]] when
+// *count > 0 (from_dev = 1).
+__global__ void k_apply(ApplyArgs A, int2 mv_val, const int2 *moves, int64_t n_moves, const int32_t *idx,
+                        const int32_t *count, int from_dev) {
+    __shared__ MoveView sv;
+    __shared__ int s_go;
+    __shared__ int32_t s_nb[32];
+    __shared__ int s_nnb;
+    if (threadIdx.x == 0) {
+        int2 mv = mv_val;
+        int have = 1;
+        if (from_dev) {
+            have = *count > 0;
+            if (have) {
+                int32_t j = idx[0];
+                if (j >= 0 && (int64_t)j < n_moves) {
+                    mv = moves[j];
+                } else {
+                    mv = make_int2(-1, -1);  // decodes as a bad move
+                    atomicOr(A.status, kStBadMove);
+                }
+            }
+        }
+        MoveView v;
+        if (have) {
+            v = decode_move(
+                mv, A.tp, [&](int32_t b) { return A.blk[b]; },
+                [&](int32_t b) { return A.uniform ? A.m_uniform : A.mass[b]; },
+                [&](uint32_t t) { return A.minedT[t]; }, [&](uint32_t t) { return A.cap[t]; });
+        } else {
+            v.valid = true;
+            v.feasible = false;
+            v.noop = true;
+        }
+        sv = v;
+        int go = have && v.valid && v.feasible && !v.noop;
+        s_go = go;
+        if (!go) {
+            A.res->applied = (have && v.valid && v.feasible) ? 1 : 0;  // a feasible no-op counts as applied
+            A.res->status = !have ? MM_OK : (!v.valid ? MM_ERR_BAD_MOVE : (!v.feasible ? MM_ERR_INFEASIBLE : MM_OK));
+        } else {
+            // periods and mined tonnage
+            int64_t dm1 = v.m1, dm2 = v.swap ? (int64_t)v.m2 : 0;
+            if (v.t1 < (uint32_t)A.T) A.minedT[v.t1] += -dm1 + dm2;
+            if (v.t2 < (uint32_t)A.T) A.minedT[v.t2] += dm1 - dm2;
+            A.blk[v.b1] = (A.blk[v.b1] & ~0xffu) | v.t2;
+            if (v.swap) A.blk[v.b2] = (A.blk[v.b2] & ~0xffu) | v.t1;
+            // neighbourhood whose lo/hi may change: moved blocks and their neighbours
+            int n = 0;
+            int32_t mb[2] = {v.b1, v.swap ? v.b2 : -1};
+            for (int q = 0; q < 2; q++) {
+                int32_t b = mb[q];
+                if (b < 0) continue;
+                s_nb[n++] = b;
+                if (A.tp.nx > 0) {
+                    int32_t nxy = A.tp.nx * A.tp.ny;
+                    int32_t x = b % A.tp.nx, y = (b / A.tp.nx) % A.tp.ny, z = b / nxy;
+                    const int dx[5] = {0, -1, 1, 0, 0};
+                    const int dy[5] = {0, 0, 0, -1, 1};
+                    for (int k = 0; k < 5; k++) {
+                        int32_t px = x + dx[k], py = y + dy[k];
+                        if (px < 0 || px >= A.tp.nx || py < 0 || py >= A.tp.ny) continue;
+                        if (z > 0) s_nb[n++] = px + A.tp.nx * (py + A.tp.ny * (z - 1));
+                        if (z + 1 < A.tp.nz) s_nb[n++] = px + A.tp.nx * (py + A.tp.ny * (z + 1));
+                    }
+                }
+            }
+            s_nnb = n;
+        }
+    }
+    __syncthreads();
+    if (!s_go) return;
+    MoveView v = sv;
+    // scenario-parallel tonnage and metal updates
+    for (int s = threadIdx.x; s < A.S; s += blockDim.x) {
+        uint32_t o1 = (A.ore[(int64_t)v.b1 * A.W + (s >> 5)] >> (s & 31)) & 1u;
+        int64_t om1 = o1 ? (int64_t)v.m1 : 0;
+        double g1 = o1 ? __dmul_rn((double)v.m1, A.grade[(int64_t)v.b1 * A.S + s]) : 0.0;
+        int64_t om2 = 0;
+        double g2 = 0.0;
+        if (v.swap) {
+            uint32_t o2 = (A.ore[(int64_t)v.b2 * A.W + (s >> 5)] >> (s & 31)) & 1u;
+            om2 = o2 ? (int64_t)v.m2 : 0;
+            g2 = o2 ? __dmul_rn((double)v.m2, A.grade[(int64_t)v.b2 * A.S + s]) : 0.0;
+        }
+        if (v.t1 < (uint32_t)A.T) {
+            A.oreT[(int64_t)v.t1 * A.S + s] += om2 - om1;
+            double &mt = A.metal[(int64_t)v.t1 * A.S + s];
+            mt = __dadd_rn(__dsub_rn(mt, g1), g2);
+        }
+        if (v.t2 < (uint32_t)A.T) {
+            A.oreT[(int64_t)v.t2 * A.S + s] += om1 - om2;
+            double &mt = A.metal[(int64_t)v.t2 * A.S + s];
+            mt = __dadd_rn(__dsub_rn(mt, g2), g1);
+        }
+    }
+    // lo/hi of the neighbourhood (CSR: the moved blocks' own lists)
+    if (A.tp.nx > 0) {
+        if (threadIdx.x < (unsigned)s_nnb) {
+            int32_t b = s_nb[threadIdx.x];
+            A.blk[b] = block_bounds(A.tp, b, [&](int32_t j) { return blk_period(A.blk[j]); });
+        }
+    } else if (threadIdx.x < 2) {
+        int32_t b = threadIdx.x == 0 ? v.b1 : (v.swap ? v.b2 : -1);
+        if (b >= 0) {
+            // moved block: its own bounds; its neighbours are refreshed below
+            A.blk[b] = block_bounds(A.tp, b, [&](int32_t j) { return blk_period(A.blk[j]); });
+        }
+    }
+    __syncthreads();
+    if (A.tp.nx == 0) {
+        // CSR: refresh every predecessor and successor of the moved blocks
+        for (int q = 0; q < 2; q++) {
+            int32_t b = q == 0 ? v.b1 : (v.swap ? v.b2 : -1);
+            if (b < 0) continue;
+            int32_t np = A.tp.pred_ptr[b + 1] - A.tp.pred_ptr[b];
+            int32_t ns = A.tp.succ_ptr[b + 1] - A.tp.succ_ptr[b];
+            for (int k = threadIdx.x; k < np + ns; k += blockDim.x) {
+                int32_t j = k < np ? A.tp.pred_idx[A.tp.pred_ptr[b] + k] : A.tp.succ_idx[A.tp.succ_ptr[b] + k - np];
+                A.blk[j] = block_bounds(A.tp, j, [&](int32_t i) { return blk_period(A.blk[i]); });
+            }
+            __syncthreads();
+        }
+    }
+    __syncthreads();
+    // tables of the affected periods
+    if (A.uniform) {
+        uint32_t rows[2] = {v.t1, v.t2};
+        for (int q = 0; q < 2; q++) {
+            int t = (int)rows[q];
+            if (t >= A.T) continue;
+            for (int s = threadIdx.x; s < A.S_pad; s += blockDim.x)
+                table_entry(t, s, A.S, A.S_pad, A.T, A.oreT, A.target, A.disc, (int64_t)A.m_uniform, A.a, A.e, A.tab);
+        }
+    }
+    // NPV from the accumulators
+    for (int s = threadIdx.x; s < A.S; s += blockDim.x)
+        A.npv[s] = npv_of(s, A.S, A.T, A.disc, A.metal, A.oreT, A.minedT, A.target, A.pr, A.pc, A.mc, A.a, A.e);
+    __syncthreads();
+    double mean = 0, sd = 0;
+    npv_stats(A.npv, A.S, &mean, &sd);
+    if (threadIdx.x == 0) {
+        A.res->applied = 1;
+        A.res->status = MM_OK;
+        A.res->mean = mean;
+        A.res->std = sd;
+    }
+}
+
+__global__ void k_npv_stats(const double *npv, int32_t S, ApplyResult *res) {
+    double mean = 0, sd = 0;
+    npv_stats(npv, S, &mean, &sd);
+    if (threadIdx.x == 0) {
+        res->mean = mean;
+        res->std = sd;
+    }
+}
+
+// ------------------------------------------------------------------ host
+
+mm_status rebuild_tables(mm_model *m) {
+    if (!m->uniform_mass) return MM_OK;
+    k_tables<<<m->T + 1, 128, 0, m->stream>>>(m->S, m->S_pad, m->T, m->oreT, m->target, m->disc, (int64_t)m->m_uniform,
+                                              m->shortfall_pen, m->excess_pen, m->tab);
+    return check_launch("k_tables");
+}
+
+static ApplyArgs apply_args(mm_model *m) {
+    ApplyArgs A;
+    A.tp = topo_of(m);
+    A.S = m->S; A.S_pad = m->S_pad; A.W = m->W; A.T = m->T;
+    A.m_uniform = m->m_uniform; A.uniform = m->uniform_mass;
+    A.mass = m->mass; A.ore = m->ore; A.grade = m->grade; A.blk = m->blk;
+    A.minedT = m->minedT; A.oreT = m->oreT; A.metal = m->metal; A.npv = m->npv; A.tab = m->tab;
+    A.disc = m->disc; A.cap = m->cap; A.target = m->target;
+    A.pr = m->price * m->recovery; A.pc = m->proc_cost; A.mc = m->mining_cost;
+    A.a = m->shortfall_pen; A.e = m->excess_pen;
+    A.res = m->apply_res;
+    A.status = m->status;
+    return A;
+}
+
+static int apply_threads(int S) {
+    int t = ((S + 31) / 32) * 32;
+    if (t < 64) t = 64;
+    if (t > 1024) t = 1024;
+    return t;
+}
+
+}  // namespace mm
+
+using namespace mm;
+
+template <typename T>
+static mm_status dalloc(T **p, size_t count, const char *what) {
+    size_t bytes = count * sizeof(T);
+    if (bytes == 0) bytes = sizeof(T);
+    cudaError_t e = cudaMalloc((void **)p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return cuda_status(e, what);
+    }
+    return MM_OK;
+}
+
+extern "C" {
+
+const char *mm_last_error(void) { return g_err; }
+
+void mm_model_destroy(mm_model *m) {
+    if (!m) return;
+    if (m->stream) cudaStreamSynchronize(m->stream);
+    cudaFree(m->mass); cudaFree(m->grade); cudaFree(m->val); cudaFree(m->ore); cudaFree(m->blk);
+    cudaFree(m->pred_ptr); cudaFree(m->pred_idx); cudaFree(m->succ_ptr); cudaFree(m->succ_idx);
+    cudaFree(m->order); cudaFree(m->porder);
+    cudaFree(m->minedT); cudaFree(m->oreT); cudaFree(m->metal); cudaFree(m->npv); cudaFree(m->tab);
+    cudaFree(m->ddt); cudaFree(m->disc); cudaFree(m->cap); cudaFree(m->target); cudaFree(m->status);
+    cudaFree(m->apply_res);
+    if (m->apply_res_host) cudaFreeHost(m->apply_res_host);
+    if (m->status_host) cudaFreeHost(m->status_host);
+    topk_scratch_free(m->topk);
+    delete m;
+}
+
+mm_status mm_model_create(const mm_model_desc *d, mm_model **out) {
+    g_err[0] = 0;
+    if (!d || !out) return set_error(MM_ERR_INVALID_ARG, "mm_model_create: NULL argument");
+    *out = nullptr;
+    const int32_t B = d->n_blocks, S = d->n_scenarios, T = d->n_periods;
+    if (B <= 0 || S <= 0 || T <= 0) return set_error(MM_ERR_INVALID_ARG, "B, S and T must be positive");
+    if (S > kMaxS) return set_error(MM_ERR_INVALID_ARG, "S = %d exceeds the limit %d", S, kMaxS);
+    if (T > kMaxT) return set_error(MM_ERR_INVALID_ARG, "T = %d exceeds the limit %d", T, kMaxT);
+    if (!d->mass_t || !d->grade || !d->cap_t || !d->mill_target_t)
+        return set_error(MM_ERR_INVALID_ARG, "mass, grade, capacity and mill target are required");
+    bool grid = d->nx > 0 || d->ny > 0 || d->nz > 0;
+    if (grid) {
+        if (d->nx <= 0 || d->ny <= 0 || d->nz <= 0 || (int64_t)d->nx * d->ny * d->nz != B)
+            return set_error(MM_ERR_INVALID_ARG, "grid %d x %d x %d does not hold %d blocks", d->nx, d->ny, d->nz, B);
+    } else if (!d->pred_ptr || !d->pred_idx) {
+        return set_error(MM_ERR_INVALID_ARG, "either a grid or a predecessor CSR is required");
+    }
+    const double econ[] = {d->price, d->recovery, d->mining_cost, d->proc_cost, d->shortfall_pen, d->excess_pen,
+                           d->discount_rate, d->lambda};
+    for (double v : econ)
+        if (!std::isfinite(v)) return set_error(MM_ERR_INVALID_ARG, "economic parameters must be finite");
+    if (d->discount_rate <= -1.0) return set_error(MM_ERR_INVALID_ARG, "discount rate must exceed -1");
+    uint64_t total = 0;
+    for (int32_t b = 0; b < B; b++) {
+        if (d->mass_t[b] == 0) return set_error(MM_ERR_INVALID_ARG, "block %d has zero mass", b);
+        total += d->mass_t[b];
+    }
+    if (total >= (1ull << 62)) return set_error(MM_ERR_OVERFLOW, "total block mass exceeds 2^62 t");
+    for (int32_t t = 0; t < T; t++)
+        if (d->cap_t[t] >= (1ull << 62) || d->mill_target_t[t] >= (1ull << 62))
+            return set_error(MM_ERR_OVERFLOW, "capacity or mill target of period %d exceeds 2^62 t", t);
+    for (int64_t i = 0; i < (int64_t)B * S; i++)
+        if (!std::isfinite(d->grade[i]) || d->grade[i] < 0.0)
+            return set_error(MM_ERR_INVALID_ARG, "grade[%lld] is negative or not finite", (long long)i);
+    std::vector<int32_t> sptr, sidx;
+    if (!grid) {
+        if (d->pred_ptr[0] != 0) return set_error(MM_ERR_INVALID_ARG, "pred_ptr[0] must be 0");
+        for (int32_t b = 0; b < B; b++)
+            if (d->pred_ptr[b + 1] < d->pred_ptr[b]) return set_error(MM_ERR_INVALID_ARG, "pred_ptr is not monotone");
+        int32_t E = d->pred_ptr[B];
+        for (int32_t k = 0; k < E; k++)
+            if (d->pred_idx[k] < 0 || d->pred_idx[k] >= B)
+                return set_error(MM_ERR_INVALID_ARG, "pred_idx[%d] out of range", k);
+        for (int32_t b = 0; b < B; b++)
+            for (int32_t k = d->pred_ptr[b]; k < d->pred_ptr[b + 1]; k++)
+                if (d->pred_idx[k] == b) return set_error(MM_ERR_INVALID_ARG, "block %d is its own predecessor", b);
+        sptr.assign(B + 1, 0);
+        for (int32_t k = 0; k < E; k++) sptr[d->pred_idx[k] + 1]++;
+        for (int32_t b = 0; b < B; b++) sptr[b + 1] += sptr[b];
+        sidx.assign(E > 0 ? E : 1, 0);
+        std::vector<int32_t> fill(sptr.begin(), sptr.end() - 1);
+        for (int32_t b = 0; b < B; b++)
+            for (int32_t k = d->pred_ptr[b]; k < d->pred_ptr[b + 1]; k++) sidx[fill[d->pred_idx[k]]++] = b;
+    }
+
+    mm_model *m = new mm_model();
+    m->B = B; m->S = S; m->T = T;
+    m->S_pad = (S + 7) / 8 * 8;
+    m->W = (S + 31) / 32;
+    m->nx = grid ? d->nx : 0; m->ny = grid ? d->ny : 0; m->nz = grid ? d->nz : 0;
+    m->price = d->price; m->recovery = d->recovery; m->mining_cost = d->mining_cost; m->proc_cost = d->proc_cost;
+    m->shortfall_pen = d->shortfall_pen; m->excess_pen = d->excess_pen; m->discount_rate = d->discount_rate;
+    m->lambda = d->lambda;
+    m->stream = (cudaStream_t)d->cuda_stream;
+    m->uniform_mass = 1;
+    m->m_uniform = d->mass_t[0];
+    for (int32_t b = 1; b < B; b++)
+        if (d->mass_t[b] != m->m_uniform) { m->uniform_mass = 0; break; }
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&m->num_sms, cudaDevAttrMultiProcessorCount, dev);
+
+    m->h_disc.resize(T + 1);
+    for (int t = 0; t < T; t++) m->h_disc[t] = std::pow(1.0 + d->discount_rate, -(double)t);
+    m->h_disc[T] = 0.0;
+    m->h_cap.assign(d->cap_t, d->cap_t + T);
+    m->h_target.assign(d->mill_target_t, d->mill_target_t + T);
+
+    mm_status st = MM_OK;
+#define ALLOC(ptr, n) \
+    if (st == MM_OK) st = dalloc(&m->ptr, (size_t)(n), "allocate " #ptr)
+    ALLOC(mass, B);
+    ALLOC(grade, (int64_t)B * S);
+    ALLOC(val, (int64_t)B * m->S_pad);
+    ALLOC(ore, (int64_t)B * m->W);
+    ALLOC(blk, B);
+    ALLOC(order, B);
+    ALLOC(porder, T + 2);
+    ALLOC(minedT, T + 1);
+    ALLOC(oreT, (int64_t)(T + 1) * S);
+    ALLOC(metal, (int64_t)T * S);
+    ALLOC(npv, S);
+    ALLOC(tab, (int64_t)2 * (T + 1) * m->S_pad);
+    ALLOC(ddt, (int64_t)(T + 1) * (T + 1));
+    ALLOC(disc, T + 1);
+    ALLOC(cap, T + 1);
+    ALLOC(target, T + 1);
+    ALLOC(status, 1);
+    ALLOC(apply_res, 1);
+    if (!grid) {
+        ALLOC(pred_ptr, B + 1);
+        ALLOC(pred_idx, d->pred_ptr[B] > 0 ? d->pred_ptr[B] : 1);
+        ALLOC(succ_ptr, B + 1);
+        ALLOC(succ_idx, sidx.size());
+    }
+#undef ALLOC
+    if (st == MM_OK && cudaMallocHost((void **)&m->apply_res_host, sizeof(ApplyResult)) != cudaSuccess)
+        st = set_error(MM_ERR_OOM, "pinned host allocation failed");
+    if (st == MM_OK && cudaMallocHost((void **)&m->status_host, sizeof(uint32_t)) != cudaSuccess)
+        st = set_error(MM_ERR_OOM, "pinned host allocation failed");
+    if (st != MM_OK) {
+        mm_model_destroy(m);
+        return st;
+    }
+    auto fail = [&](mm_status s) {
+        mm_model_destroy(m);
+        return s;
+    };
+    cudaStream_t s = m->stream;
+#define TRY(expr, what)                                   \
+    do {                                                  \
+        cudaError_t e_ = (expr);                          \
+        if (e_ != cudaSuccess) return fail(cuda_status(e_, what)); \
+    } while (0)
+    TRY(cudaMemcpyAsync(m->mass, d->mass_t, sizeof(uint32_t) * B, cudaMemcpyHostToDevice, s), "copy mass");
+    TRY(cudaMemcpyAsync(m->grade, d->grade, sizeof(double) * (size_t)B * S, cudaMemcpyHostToDevice, s), "copy grade");
+    std::vector<uint64_t> capx(T + 1), tgtx(T + 1);
+    for (int t = 0; t < T; t++) capx[t] = d->cap_t[t], tgtx[t] = d->mill_target_t[t];
+    capx[T] = std::numeric_limits<uint64_t>::max();
+    tgtx[T] = 0;
+    std::vector<float> ddt((size_t)(T + 1) * (T + 1));
+    for (int t = 0; t <= T; t++)
+        for (int u = 0; u <= T; u++) ddt[(size_t)t * (T + 1) + u] = (float)(m->h_disc[u] - m->h_disc[t]);
+    TRY(cudaMemcpyAsync(m->cap, capx.data(), sizeof(uint64_t) * (T + 1), cudaMemcpyHostToDevice, s), "copy cap");
+    TRY(cudaMemcpyAsync(m->target, tgtx.data(), sizeof(uint64_t) * (T + 1), cudaMemcpyHostToDevice, s), "copy target");
+    TRY(cudaMemcpyAsync(m->disc, m->h_disc.data(), sizeof(double) * (T + 1), cudaMemcpyHostToDevice, s), "copy disc");
+    TRY(cudaMemcpyAsync(m->ddt, ddt.data(), sizeof(float) * ddt.size(), cudaMemcpyHostToDevice, s), "copy ddt");
+    TRY(cudaMemsetAsync(m->status, 0, sizeof(uint32_t), s), "clear status");
+    TRY(cudaMemsetAsync(m->oreT, 0, sizeof(int64_t) * (size_t)(T + 1) * S, s), "clear oreT");
+    TRY(cudaMemsetAsync(m->minedT, 0, sizeof(int64_t) * (T + 1), s), "clear minedT");
+    TRY(cudaMemsetAsync(m->apply_res, 0, sizeof(ApplyResult), s), "clear apply result");
+    if (!grid) {
+        TRY(cudaMemcpyAsync(m->pred_ptr, d->pred_ptr, sizeof(int32_t) * (B + 1), cudaMemcpyHostToDevice, s), "copy CSR");
+        if (d->pred_ptr[B] > 0)
+            TRY(cudaMemcpyAsync(m->pred_idx, d->pred_idx, sizeof(int32_t) * d->pred_ptr[B], cudaMemcpyHostToDevice, s),
+                "copy CSR");
+        TRY(cudaMemcpyAsync(m->succ_ptr, sptr.data(), sizeof(int32_t) * (B + 1), cudaMemcpyHostToDevice, s), "copy CSR");
+        TRY(cudaMemcpyAsync(m->succ_idx, sidx.data(), sizeof(int32_t) * sidx.size(), cudaMemcpyHostToDevice, s),
+            "copy CSR");
+    }
+    int64_t nthreads = (int64_t)B * m->W;
+    k_classify<<<(unsigned)((nthreads + 255) / 256), 256, 0, s>>>(m->grade, m->mass, B, S, m->S_pad, m->W, m->price,
+                                                                  m->recovery, m->proc_cost, m->mining_cost, m->val,
+                                                                  m->ore);
+    mm_status ls = check_launch("k_classify");
+    if (ls != MM_OK) return fail(ls);
+    TRY(cudaStreamSynchronize(s), "synchronize after create");
+#undef TRY
+    *out = m;
+    return MM_OK;
+}
+
+mm_status mm_set_stream(mm_model *m, void *stream) {
+    if (!m) return set_error(MM_ERR_INVALID_ARG, "NULL model");
+    m->stream = (cudaStream_t)stream;
+    return MM_OK;
+}
+
+mm_status mm_model_info(const mm_model *m, int32_t *B, int32_t *S, int32_t *T, int32_t *s_pad) {
+    if (!m) return set_error(MM_ERR_INVALID_ARG, "NULL model");
+    if (B) *B = m->B;
+    if (S) *S = m->S;
+    if (T) *T = m->T;
+    if (s_pad) *s_pad = m->S_pad;
+    return MM_OK;
+}
+
+mm_status mm_schedule_set(mm_model *m, const uint8_t *period, int *base_feasible_out) {
+    if (!m || !period) return set_error(MM_ERR_INVALID_ARG, "mm_schedule_set: NULL argument");
+    const int32_t B = m->B, T = m->T, S = m->S;
+    std::vector<int32_t> cnt(T + 2, 0);
+    for (int32_t b = 0; b < B; b++) {
+        if (period[b] > T) return set_error(MM_ERR_INVALID_ARG, "period[%d] = %d exceeds T = %d", b, period[b], T);
+        cnt[period[b] + 1]++;
+    }
+    for (int t = 0; t <= T; t++) cnt[t + 1] += cnt[t];
+    std::vector<int32_t> order(B), fill(cnt.begin(), cnt.end() - 1);
+    for (int32_t b = 0; b < B; b++) order[fill[period[b]]++] = b;
+    cudaStream_t s = m->stream;
+    uint8_t *d_period = nullptr;
+    mm_status st = dalloc(&d_period, B, "allocate period staging");
+    if (st != MM_OK) return st;
+    auto done = [&](mm_status r) {
+        cudaStreamSynchronize(s);
+        cudaFree(d_period);
+        return r;
+    };
+#define TRY(expr, what)                                   \
+    do {                                                  \
+        cudaError_t e_ = (expr);                          \
+        if (e_ != cudaSuccess) return done(cuda_status(e_, what)); \
+    } while (0)
+    TRY(cudaMemcpyAsync(d_period, period, B, cudaMemcpyHostToDevice, s), "copy schedule");
+    TRY(cudaMemcpyAsync(m->order, order.data(), sizeof(int32_t) * B, cudaMemcpyHostToDevice, s), "copy order");
+    TRY(cudaMemcpyAsync(m->porder, cnt.data(), sizeof(int32_t) * (T + 2), cudaMemcpyHostToDevice, s), "copy order");
+    Topo tp = topo_of(m);
+    k_blk_build<<<(B + 255) / 256, 256, 0, s>>>(tp, d_period, m->blk);
+    if ((st = check_launch("k_blk_build")) != MM_OK) return done(st);
+    TRY(cudaMemsetAsync(m->oreT, 0, sizeof(int64_t) * (size_t)(T + 1) * S, s), "clear oreT");
+    TRY(cudaMemsetAsync(m->minedT, 0, sizeof(int64_t) * (T + 1), s), "clear minedT");
+    dim3 grid(T, (S + 31) / 32), block(32, 8);
+    k_accum<<<grid, block, 0, s>>>(m->order, m->porder, m->mass, m->ore, m->grade, S, m->W, T, m->minedT, m->oreT,
+                                   m->metal);
+    if ((st = check_launch("k_accum")) != MM_OK) return done(st);
+    if ((st = rebuild_tables(m)) != MM_OK) return done(st);
+    k_npv<<<(S + 127) / 128, 128, 0, s>>>(S, T, m->disc, m->metal, m->oreT, m->minedT, m->target,
+                                           m->price * m->recovery, m->proc_cost, m->mining_cost, m->shortfall_pen,
+                                           m->excess_pen, m->npv);
+    if ((st = check_launch("k_npv")) != MM_OK) return done(st);
+    // base feasibility: arcs (device) + capacity (host, from minedT)
+    uint32_t *d_bad = m->status_host ? nullptr : nullptr;
+    TRY(cudaMemsetAsync(m->apply_res, 0, sizeof(ApplyResult), s), "clear apply result");
+    d_bad = (uint32_t *)&m->apply_res->status;  // reuse as a scratch word
+    k_base_arcs<<<(B + 255) / 256, 256, 0, s>>>(B, m->blk, d_bad);
+    if ((st = check_launch("k_base_arcs")) != MM_OK) return done(st);
+    std::vector<int64_t> mined(T + 1);
+    TRY(cudaMemcpyAsync(mined.data(), m->minedT, sizeof(int64_t) * (T + 1), cudaMemcpyDeviceToHost, s), "read minedT");
+    TRY(cudaMemcpyAsync(m->apply_res_host, m->apply_res, sizeof(ApplyResult), cudaMemcpyDeviceToHost, s),
+        "read feasibility");
+    TRY(cudaStreamSynchronize(s), "synchronize");
+    int feas = m->apply_res_host->status == 0;
+    for (int t = 0; t < T; t++)
+        if ((uint64_t)mined[t] > m->h_cap[t]) feas = 0;
+    TRY(cudaMemsetAsync(m->apply_res, 0, sizeof(ApplyResult), s), "clear apply result");
+#undef TRY
+    if (base_feasible_out) *base_feasible_out = feas;
+    m->has_schedule = 1;
+    return done(MM_OK);
+}
+
+mm_status mm_schedule_get(mm_model *m, uint8_t *period) {
+    if (!m || !period) return set_error(MM_ERR_INVALID_ARG, "mm_schedule_get: NULL argument");
+    if (!m->has_schedule) return set_error(MM_ERR_STATE, "no schedule installed");
+    std::vector<uint32_t> w(m->B);
+    MM_CUDA_TRY(cudaMemcpyAsync(w.data(), m->blk, sizeof(uint32_t) * m->B, cudaMemcpyDeviceToHost, m->stream),
+                "read schedule");
+    MM_CUDA_TRY(cudaStreamSynchronize(m->stream), "synchronize");
+    for (int32_t b = 0; b < m->B; b++) period[b] = (uint8_t)blk_period(w[b]);
+    return read_sticky(m);
+}
+
+mm_status mm_apply_move(mm_model *m, mm_move mv, double *mean, double *sd) {
+    if (!m) return set_error(MM_ERR_INVALID_ARG, "NULL model");
+    if (!m->has_schedule) return set_error(MM_ERR_STATE, "no schedule installed");
+    ApplyArgs A = apply_args(m);
+    k_apply<<<1, apply_threads(m->S), 0, m->stream>>>(A, make_int2(mv.b1, mv.arg), nullptr, 0, nullptr, nullptr, 0);
+    mm_status st = check_launch("k_apply");
+    if (st != MM_OK) return st;
+    MM_CUDA_TRY(cudaMemcpyAsync(m->apply_res_host, m->apply_res, sizeof(ApplyResult), cudaMemcpyDeviceToHost, m->stream),
+                "read apply result");
+    MM_CUDA_TRY(cudaStreamSynchronize(m->stream), "synchronize");
+    ApplyResult r = *m->apply_res_host;
+    mm_status sticky = read_sticky(m);
+    if (r.status == MM_ERR_BAD_MOVE) return set_error(MM_ERR_BAD_MOVE, "move (%d, %d) is out of range", mv.b1, mv.arg);
+    if (r.status == MM_ERR_INFEASIBLE) return set_error(MM_ERR_INFEASIBLE, "move (%d, %d) is infeasible", mv.b1, mv.arg);
+    if (mean || sd) {
+        // a no-op leaves the state as it was: report the current statistics
+        k_npv_stats<<<1, apply_threads(m->S), 0, m->stream>>>(m->npv, m->S, m->apply_res);
+        if ((st = check_launch("k_npv_stats")) != MM_OK) return st;
+        MM_CUDA_TRY(cudaMemcpyAsync(m->apply_res_host, m->apply_res, sizeof(ApplyResult), cudaMemcpyDeviceToHost,
+                                    m->stream), "read apply result");
+        MM_CUDA_TRY(cudaStreamSynchronize(m->stream), "synchronize");
+        if (mean) *mean = m->apply_res_host->mean;
+        if (sd) *sd = m->apply_res_host->std;
+    }
+    return sticky;
+}
+
+mm_status mm_apply_best(mm_model *m, const mm_move *moves, int64_t n, const int32_t *idx, const int32_t *count) {
+    if (!m || !moves || !idx || !count) return set_error(MM_ERR_INVALID_ARG, "mm_apply_best: NULL argument");
+    if (n < 0) return set_error(MM_ERR_INVALID_ARG, "negative move count");
+    if (!m->has_schedule) return set_error(MM_ERR_STATE, "no schedule installed");
+    ApplyArgs A = apply_args(m);
+    k_apply<<<1, apply_threads(m->S), 0, m->stream>>>(A, make_int2(0, 0), (const int2 *)moves, n, idx, count, 1);
+    mm_status st = check_launch("k_apply");
+    if (st != MM_OK) return st;
+    k_npv_stats<<<1, apply_threads(m->S), 0, m->stream>>>(m->npv, m->S, m->apply_res);
+    return check_launch("k_npv_stats");
+}
+
+mm_status mm_last_apply(mm_model *m, int32_t *applied, double *mean, double *sd) {
+    if (!m) return set_error(MM_ERR_INVALID_ARG, "NULL model");
+    MM_CUDA_TRY(cudaMemcpyAsync(m->apply_res_host, m->apply_res, sizeof(ApplyResult), cudaMemcpyDeviceToHost, m->stream),
+                "read apply result");
+    MM_CUDA_TRY(cudaStreamSynchronize(m->stream), "synchronize");
+    if (applied) *applied = m->apply_res_host->applied;
+    if (mean) *mean = m->apply_res_host->mean;
+    if (sd) *sd = m->apply_res_host->std;
+    return read_sticky(m);
+}
+
+mm_status mm_npv(mm_model *m, double *npv_host, double *mean, double *sd) {
+    if (!m) return set_error(MM_ERR_INVALID_ARG, "NULL model");
+    if (!m->has_schedule) return set_error(MM_ERR_STATE, "no schedule installed");
+    std::vector<double> v(m->S);
+    MM_CUDA_TRY(cudaMemcpyAsync(v.data(), m->npv, sizeof(double) * m->S, cudaMemcpyDeviceToHost, m->stream), "read npv");
+    MM_CUDA_TRY(cudaStreamSynchronize(m->stream), "synchronize");
+    if (npv_host) std::memcpy(npv_host, v.data(), sizeof(double) * m->S);
+    double mu = 0.0;
+    for (double x : v) mu += x;
+    mu /= m->S;
+    double var = 0.0;
+    for (double x : v) var += (x - mu) * (x - mu);
+    if (mean) *mean = mu;
+    if (sd) *sd = std::sqrt(var / m->S);
+    return read_sticky(m);
+}
+
+mm_status mm_get_ore(mm_model *m, uint32_t *ore_host) {
+    if (!m || !ore_host) return set_error(MM_ERR_INVALID_ARG, "NULL argument");
+    MM_CUDA_TRY(cudaMemcpyAsync(ore_host, m->ore, sizeof(uint32_t) * (size_t)m->B * m->W, cudaMemcpyDeviceToHost,
+                                m->stream), "read ore");
+    MM_CUDA_TRY(cudaStreamSynchronize(m->stream), "synchronize");
+    return MM_OK;
+}
+
+mm_status mm_get_values(mm_model *m, float *value_host) {
+    if (!m || !value_host) return set_error(MM_ERR_INVALID_ARG, "NULL argument");
+    MM_CUDA_TRY(cudaMemcpy2DAsync(value_host, sizeof(float) * m->S, m->val, sizeof(float) * m->S_pad, sizeof(float) * m->S,
+                                  m->B, cudaMemcpyDeviceToHost, m->stream), "read values");
+    MM_CUDA_TRY(cudaStreamSynchronize(m->stream), "synchronize");
+    return MM_OK;
+}
+
+mm_status mm_get_tonnage(mm_model *m, int64_t *mined_host, int64_t *ore_t_host) {
+    if (!m) return set_error(MM_ERR_INVALID_ARG, "NULL model");
+    if (!m->has_schedule) return set_error(MM_ERR_STATE, "no schedule installed");
+    if (mined_host)
+        MM_CUDA_TRY(cudaMemcpyAsync(mined_host, m->minedT, sizeof(int64_t) * m->T, cudaMemcpyDeviceToHost, m->stream),
+                    "read mined");
+    if (ore_t_host)
+        MM_CUDA_TRY(cudaMemcpyAsync(ore_t_host, m->oreT, sizeof(int64_t) * (size_t)m->T * m->S, cudaMemcpyDeviceToHost,
+                                    m->stream), "read ore tonnage");
+    MM_CUDA_TRY(cudaStreamSynchronize(m->stream), "synchronize");
+    return MM_OK;
+}
+
+mm_status mm_get_metal(mm_model *m, double *metal_host) {
+    if (!m || !metal_host) return set_error(MM_ERR_INVALID_ARG, "NULL argument");
+    if (!m->has_schedule) return set_error(MM_ERR_STATE, "no schedule installed");
+    MM_CUDA_TRY(cudaMemcpyAsync(metal_host, m->metal, sizeof(double) * (size_t)m->T * m->S, cudaMemcpyDeviceToHost,
+                                m->stream), "read metal");
+    MM_CUDA_TRY(cudaStreamSynchronize(m->stream), "synchronize");
+    return MM_OK;
+}
+
+}  // extern "C"

@@ -54,3 +54,28 @@ def all_moves(B, T):
     mv = [(b, -(t + 1)) for b in range(B) for t in range(T + 1)]
     mv += [(b1, b2) for b1 in range(B) for b2 in range(B)]
     return np.asarray(mv, np.int32)
+
+
+REL_TOL = 1e-5  # relative error bound on FP32 deltas and scores vs the FP64 oracle
+
+
+def assert_close_floor(gpu, ref, floor, rel=REL_TOL, what=""):
+    """|gpu - ref| <= rel * max(|ref|, floor), elementwise.
+
+    ``floor`` is the oracle's per-move (or per-scenario) scale of the terms
+    that were summed, so that cancellation near zero is judged against the size
+    of what cancelled.  Where ref and floor are both 0 (a no-op move) the GPU
+    value must be exactly 0; equal infinities (bad moves) match."""
+    g = np.asarray(gpu, np.float64)
+    r = np.asarray(ref, np.float64)
+    f = np.broadcast_to(np.asarray(floor, np.float64), r.shape)
+    both_inf = np.isinf(g) & np.isinf(r) & (np.sign(g) == np.sign(r))
+    with np.errstate(invalid="ignore"):
+        err = np.where(both_inf, 0.0, np.abs(g - r))
+    tol = rel * np.maximum(np.abs(np.where(both_inf, 0.0, r)), f)
+    bad = ~(err <= tol)
+    if bad.any():
+        k = np.argmax(np.where(bad, err / np.maximum(tol, 1e-300), 0))
+        idx = np.unravel_index(k, r.shape)
+        raise AssertionError(f"{what}: {int(bad.sum())} of {bad.size} outside tolerance; worst at {idx}: "
+                             f"gpu={g[idx]!r} ref={r[idx]!r} floor={f[idx]!r}")

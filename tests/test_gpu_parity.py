@@ -1,0 +1,215 @@
+"""CUDA path vs the FP64 oracle, element by element (needs a B300).
+
+Bars: ore bits, feasibility flags and integer tonnages bit-exact; FP32 value
+rows equal to the FP64 oracle value rounded to FP32; per-scenario deltas,
+means and scores within 1e-5 relative of the oracle (with the oracle's term
+magnitude as the floor near cancellation); no-op moves exactly zero.
+"""
+
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from helpers import REL_TOL, all_moves, assert_close_floor, tiny_problem
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    import paper_2511_18296_b300  # noqa: F401  (fails loudly if the library is missing)
+
+
+def gpu_model(p, preds=None):
+    import paper_2511_18296_b300 as mm
+    m = mm.Model.from_problem(p, preds=preds)
+    assert m.schedule_set(p.x0) == O.OracleModel(p, preds=preds).feasible(p.x0)
+    return m
+
+
+def run_eval(m, moves, kahan=False, deltas=True):
+    mv = torch.as_tensor(np.ascontiguousarray(moves, np.int32), device="cuda")
+    if deltas:
+        score, feas, mean, delta = m.eval_deltas(mv, kahan=kahan)
+    else:
+        score, feas, mean = m.eval_moves(mv, kahan=kahan)
+        delta = None
+    torch.cuda.synchronize()
+    out = dict(score=score.cpu().numpy(), flag=feas.cpu().numpy(), mean=mean.cpu().numpy())
+    if delta is not None:
+        out["delta"] = delta.cpu().numpy()
+    return out
+
+
+def check_against(gpu, ref, inc, what, delta_rows=None):
+    assert np.array_equal(gpu["flag"], ref["flag"]), f"{what}: flags differ"
+    assert_close_floor(gpu["score"], ref["score"], inc["floor"], what=f"{what} score")
+    assert_close_floor(gpu["mean"], ref["mean"], inc["floor"], what=f"{what} mean")
+    if "delta" in gpu and ref.get("delta") is not None:
+        rows = slice(None) if delta_rows is None else delta_rows
+        assert_close_floor(gpu["delta"][rows], ref["delta"][rows], inc["floor_s"][rows], what=f"{what} delta")
+
+
+@pytest.mark.parametrize("name", ["plain_4k", "plain_50k"])
+def test_classify_and_state(name):
+    p = W.config(name, n_moves=0)
+    om = O.OracleModel(p)
+    m = gpu_model(p)
+    assert np.array_equal(m.ore_bits(), om.ore)
+    assert np.array_equal(m.values(), om.value.astype(np.float32))
+    mined, oreT = m.tonnage()
+    rmined, roreT = om.tonnage(p.x0)
+    assert np.array_equal(mined, rmined) and np.array_equal(oreT, roreT)
+    npv, mean, sd = m.npv()
+    ref = om.npv(p.x0)
+    np.testing.assert_allclose(npv, ref, rtol=1e-12)
+    assert mean == pytest.approx(ref.mean(), rel=1e-12)
+    assert sd == pytest.approx(ref.std(), rel=1e-9)
+    assert np.array_equal(m.schedule_get(), p.x0)
+
+
+def test_plain_4k_full_batch_vs_bruteforce():
+    p = W.config("plain_4k")
+    om = O.OracleModel(p)
+    m = gpu_model(p)
+    g = run_eval(m, p.moves)
+    ref = om.eval_bruteforce(p.x0, p.moves)
+    inc = om.eval_incremental(p.x0, p.moves, want_floor_s=True)
+    check_against(g, ref, inc, "plain_4k")
+
+
+@pytest.mark.parametrize("kahan", [False, True])
+def test_plain_50k_full_batch(kahan):
+    p = W.config("plain_50k")
+    om = O.OracleModel(p)
+    m = gpu_model(p)
+    g = run_eval(m, p.moves, kahan=kahan, deltas=False)
+    inc = om.eval_incremental(p.x0, p.moves)
+    check_against(g, inc, inc, f"plain_50k kahan={kahan}")
+    # per-scenario deltas on a ragged slice and brute force on a sample
+    sl = slice(1000, 1000 + 3001)
+    gd = run_eval(m, p.moves[sl], kahan=kahan)
+    incd = om.eval_incremental(p.x0, p.moves[sl], want_delta=True, want_floor_s=True)
+    check_against(gd, incd, incd, "plain_50k deltas")
+    sample = np.random.default_rng(7).choice(p.moves.shape[0], 96, replace=False)
+    bf = om.eval_bruteforce(p.x0, p.moves[sample])
+    gs = {k: v[sample] for k, v in g.items()}
+    inc_s = {k: (v[sample] if v is not None else None) for k, v in inc.items()}
+    check_against(gs, bf, inc_s, "plain_50k brute-force sample")
+
+
+@pytest.mark.parametrize("S", [1, 3, 4, 5, 13, 33, 100])
+@pytest.mark.parametrize("T", [1, 3])
+def test_tiny_exhaustive(S, T):
+    """Every shift (to every period, unmined included) and every ordered swap,
+    no-ops and partner-adjacent swaps included, on a 3x3x3 model."""
+    p = tiny_problem(3, 3, 3, S=S, T=T, seed=S * 7 + T, target_blocks=4)
+    om = O.OracleModel(p)
+    m = gpu_model(p)
+    mv = all_moves(p.B, T)
+    bad = np.array([[p.B, -1], [0, -(T + 2)], [-1, 0], [0, p.B]], np.int32)
+    mv = np.concatenate([mv, bad])
+    for kahan in (False, True):
+        g = run_eval(m, mv, kahan=kahan)
+        ref = om.eval_bruteforce(p.x0, mv)
+        inc = om.eval_incremental(p.x0, mv, want_floor_s=True)
+        check_against(g, ref, inc, f"tiny S={S} T={T} kahan={kahan}")
+        noop = inc["floor"] == 0
+        assert np.all(g["score"][noop & (ref["score"] == 0)] == 0.0)
+    import paper_2511_18296_b300 as mm
+    with pytest.raises(mm.MMError) as e:
+        m.npv()  # the sticky bad-move status surfaces at the next synchronising call
+    assert e.value.status == 6
+    m.npv()  # and is cleared
+
+
+def test_moves_on_a_moved_schedule():
+    """A base schedule with blocks pushed down and some unmined."""
+    p = tiny_problem(4, 3, 3, S=7, T=4, seed=3, cap_blocks=12)
+    om = O.OracleModel(p)
+    x = p.x0.copy()
+    rng = np.random.default_rng(1)
+    for _ in range(200):
+        b = int(rng.integers(p.B))
+        tn = int(rng.integers(p.T + 1))
+        y = x.copy()
+        y[b] = tn
+        if om.feasible(y):
+            x = y
+    p.x0 = x
+    m = gpu_model(p)
+    mv = all_moves(p.B, p.T)
+    g = run_eval(m, mv)
+    ref = om.eval_bruteforce(x, mv)
+    inc = om.eval_incremental(x, mv, want_floor_s=True)
+    check_against(g, ref, inc, "moved schedule")
+
+
+def test_nonuniform_mass_general_kernel():
+    rng = np.random.default_rng(11)
+    B = 4 * 4 * 3
+    mass = rng.integers(6_000, 14_000, size=B).astype(np.uint32)
+    x0 = W.greedy_schedule(mass, np.full(4, 150_000, np.uint64), 4)
+    p = tiny_problem(4, 4, 3, S=37, T=4, mass=mass, x0=x0, cap_blocks=15, target_blocks=5)
+    om = O.OracleModel(p)
+    m = gpu_model(p)
+    mv = all_moves(B, 4)
+    g = run_eval(m, mv)
+    ref = om.eval_bruteforce(x0, mv)
+    inc = om.eval_incremental(x0, mv, want_floor_s=True)
+    check_against(g, ref, inc, "non-uniform mass")
+
+
+def test_general_dag_csr():
+    rng = np.random.default_rng(5)
+    B, T = 40, 4
+    preds = [sorted(set(rng.integers(0, b, size=min(b, 3)).tolist())) if b > 0 else [] for b in range(B)]
+    ptr = np.zeros(B + 1, np.int32)
+    ptr[1:] = np.cumsum([len(q) for q in preds])
+    idx = np.array([j for q in preds for j in q] or [0], np.int32)
+    x0 = np.minimum(np.arange(B) // 12, T).astype(np.uint8)
+    p = tiny_problem(B, 1, 1, S=9, T=T, x0=x0, cap_blocks=13, seed=8)
+    om = O.OracleModel(p, preds=(ptr, idx))
+    assert om.feasible(x0)
+    m = gpu_model(p, preds=(ptr, idx[:ptr[-1]]))
+    mv = all_moves(B, T)
+    g = run_eval(m, mv)
+    ref = om.eval_bruteforce(x0, mv)
+    inc = om.eval_incremental(x0, mv, want_floor_s=True)
+    check_against(g, ref, inc, "CSR DAG")
+
+
+def test_max_scenarios_and_empty_batch():
+    p = tiny_problem(3, 2, 2, S=1024, T=3, seed=2)
+    om = O.OracleModel(p)
+    m = gpu_model(p)
+    mv = all_moves(p.B, p.T)
+    g = run_eval(m, mv)
+    ref = om.eval_bruteforce(p.x0, mv)
+    inc = om.eval_incremental(p.x0, mv, want_floor_s=True)
+    check_against(g, ref, inc, "S=1024")
+    empty = torch.zeros((0, 2), dtype=torch.int32, device="cuda")
+    s, f, mn = m.eval_moves(empty)
+    assert s.numel() == 0
+
+
+def test_team_sizes_agree():
+    """Every team width gives the same flags and scores within tolerance."""
+    import ctypes
+    import paper_2511_18296_b300 as mm
+    p = W.config("plain_4k")
+    om = O.OracleModel(p)
+    m = gpu_model(p)
+    inc = om.eval_incremental(p.x0, p.moves)
+    mv = torch.as_tensor(p.moves, device="cuda")
+    for team in (4, 8, 16, 32):
+        if not hasattr(mm.lib(), "mm_set_tile"):
+            pytest.skip("tile selection not exported")
+        assert mm.lib().mm_set_tile(m.h, team, 0) == 0
+        s, f, mean = m.eval_moves(mv)
+        torch.cuda.synchronize()
+        assert np.array_equal(f.cpu().numpy(), inc["flag"])
+        assert_close_floor(s.cpu().numpy(), inc["score"], inc["floor"], what=f"team {team}")
