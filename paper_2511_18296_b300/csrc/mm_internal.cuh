@@ -6,6 +6,7 @@
 
 #include <cstdint>
 #include <cstdio>
+#include <set>
 #include <string>
 #include <vector>
 
@@ -16,7 +17,7 @@ namespace mm {
 constexpr int kMaxS = 1024;       // scenarios per model
 constexpr int kMaxT = 254;        // periods; the period byte value T means unmined
 constexpr int kTopkMax = 1024;    // largest k of mm_topk
-constexpr int kHistBits = 16;     // top-k coarse histogram over the score's top bits
+constexpr int kHistBits = 12;     // top-k coarse histogram over the key's top bits
 constexpr int kHistBins = 1 << kHistBits;
 
 // Sticky device status bits, read and cleared by synchronising calls.
@@ -63,6 +64,7 @@ struct mm_model {
     int num_sms = 148;
     int team = 0;          // evaluator tile: lanes per move (0 = default)
     int ctas_per_sm = 0;   // evaluator grid: CTAs per SM (0 = occupancy maximum)
+    std::set<const void *> smem_attr_set;  // kernels whose shared-memory limit was raised
 
     std::vector<double> h_disc;      // [T+1] d_t in FP64, d_T = 0
     std::vector<uint64_t> h_cap;     // [T]
@@ -71,8 +73,8 @@ struct mm_model {
     // device state
     uint32_t *mass = nullptr;    // [B]
     double *grade = nullptr;     // [B][S]
-    float *val = nullptr;        // [B][S_pad] FP32 value rows (padding 0)
-    uint32_t *ore = nullptr;     // [B][W] ore bits
+    float *val = nullptr;        // [B+1][S_pad] FP32 value rows (padding 0; row B all 0)
+    uint32_t *ore = nullptr;     // [B+1][W] ore bits (row B all 0)
     uint32_t *blk = nullptr;     // [B] packed period / lo / hi
     int32_t *pred_ptr = nullptr, *pred_idx = nullptr;  // CSR (device) when nx == 0
     int32_t *succ_ptr = nullptr, *succ_idx = nullptr;
@@ -82,6 +84,7 @@ struct mm_model {
     int64_t *oreT = nullptr;     // [T+1][S]  (row T stays 0)
     double *metal = nullptr;     // [T][S]    grams in situ of ore
     double *npv = nullptr;       // [S]
+    double *contrib = nullptr;   // [T][S]    d_t (cash - penalty) per period
     float *tab = nullptr;        // [2][T+1][S_pad]  Pout, Pin
     float *ddt = nullptr;        // [(T+1)*(T+1)]    d_{t'} - d_t  (index t*(T+1)+t')
     double *disc = nullptr;      // [T+1]

@@ -1,11 +1,13 @@
 // Model store, schedule state and the apply-move kernel.
 //
 // Device layout (per model):
-//   val   FP32 [B][S_pad]   per-block value rows, scenario fastest, 32-byte rows
-//   ore   u32  [B][W]       ore bits, W = ceil(S/32)
+//   val   FP32 [B+1][S_pad] per-block value rows, scenario fastest, 32-byte rows;
+//                           row B is all zeros (the stand-in partner of a shift)
+//   ore   u32  [B+1][W]     ore bits, W = ceil(S/32); row B zero
 //   blk   u32  [B]          packed period | lo << 8 | hi << 16
 //   grade FP64 [B][S]       kept for the FP64 metal accumulators
 //   minedT i64 [T+1], oreT i64 [T+1][S], metal FP64 [T][S], npv FP64 [S]
+//   contrib FP64 [T][S]     d_t (cash_t,s - pen_t,s): NPV_s = sum_t contrib[t][s]
 //   tab   FP32 [2][T+1][S_pad]  NPV change of removing / adding one block of ore
 //                               in period t, scenario s (uniform block mass)
 #include <cmath>
@@ -191,28 +193,32 @@ __global__ void k_tables(int32_t S, int32_t S_pad, int32_t T, const int64_t *__r
     for (int s = threadIdx.x; s < S_pad; s += blockDim.x) table_entry(t, s, S, S_pad, T, oreT, target, disc, m, a, e, tab);
 }
 
-// NPV_s = sum_t d_t (price*rec*metal - pc*oreT - mc*minedT - pen_t(oreT)).
-__device__ __forceinline__ double npv_of(int s, int32_t S, int32_t T, const double *disc, const double *metal,
-                                         const int64_t *oreT, const int64_t *minedT, const uint64_t *target,
-                                         double pr, double pc, double mc, double a, double e) {
-    double acc = 0.0;
-    for (int t = 0; t < T; t++) {
-        int64_t o = oreT[(int64_t)t * S + s];
-        double cash = __dsub_rn(__dsub_rn(__dmul_rn(pr, metal[(int64_t)t * S + s]), __dmul_rn(pc, (double)o)),
-                                __dmul_rn(mc, (double)minedT[t]));
-        double p = pen_of(o - (int64_t)target[t], a, e);
-        acc = __dadd_rn(acc, __dmul_rn(disc[t], __dsub_rn(cash, p)));
-    }
-    return acc;
+// Discounted net cash of period t in scenario s:
+//   d_t (price*rec*metal - pc*oreT - mc*minedT - pen_t(oreT)).
+__device__ __forceinline__ double contrib_of(int t, int s, int32_t S, const double *disc, const double *metal,
+                                             const int64_t *oreT, const int64_t *minedT, const uint64_t *target,
+                                             double pr, double pc, double mc, double a, double e) {
+    int64_t o = oreT[(int64_t)t * S + s];
+    double cash = __dsub_rn(__dsub_rn(__dmul_rn(pr, metal[(int64_t)t * S + s]), __dmul_rn(pc, (double)o)),
+                            __dmul_rn(mc, (double)minedT[t]));
+    double p = pen_of(o - (int64_t)target[t], a, e);
+    return __dmul_rn(disc[t], __dsub_rn(cash, p));
 }
 
+// contrib[t][s] for every period, and NPV_s = their sum in period order.
 __global__ void k_npv(int32_t S, int32_t T, const double *__restrict__ disc, const double *__restrict__ metal,
                       const int64_t *__restrict__ oreT, const int64_t *__restrict__ minedT,
                       const uint64_t *__restrict__ target, double pr, double pc, double mc, double a, double e,
-                      double *__restrict__ npv) {
+                      double *__restrict__ contrib, double *__restrict__ npv) {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= S) return;
-    npv[s] = npv_of(s, S, T, disc, metal, oreT, minedT, target, pr, pc, mc, a, e);
+    double acc = 0.0;
+    for (int t = 0; t < T; t++) {
+        double c = contrib_of(t, s, S, disc, metal, oreT, minedT, target, pr, pc, mc, a, e);
+        contrib[(int64_t)t * S + s] = c;
+        acc = __dadd_rn(acc, c);
+    }
+    npv[s] = acc;
 }
 
 // Block-wide FP64 mean and population std of npv[0..S) (two passes).
@@ -257,6 +263,7 @@ struct ApplyArgs {
     int64_t *oreT;
     double *metal;
     double *npv;
+    double *contrib;
     float *tab;
     const double *disc;
     const uint64_t *cap;
@@ -267,8 +274,9 @@ struct ApplyArgs {
 };
 
 // Apply one move on a single CTA: exact re-check, period update, integer
-// tonnages, FP64 metal, lo/hi of the neighbourhood, tables of the affected
-// periods, then NPV_s from the accumulators and its mean/std.
+// tonnages, FP64 metal, lo/hi of the neighbourhood, tables and NPV
+// contributions of the affected periods (NPV_s += new - old), then the FP64
+// mean/std of NPV over scenarios (computed whether or not the move applied).
 // The move comes either by value (from_dev = 0) or as moves[idx[0]] when
 // *count > 0 (from_dev = 1).
 __global__ void k_apply(ApplyArgs A, int2 mv_val, const int2 *moves, int64_t n_moves, const int32_t *idx,
@@ -306,11 +314,9 @@ __global__ void k_apply(ApplyArgs A, int2 mv_val, const int2 *moves, int64_t n_m
         sv = v;
         int go = have && v.valid && v.feasible && !v.noop;
         s_go = go;
-        if (!go) {
-            A.res->applied = (have && v.valid && v.feasible) ? 1 : 0;  // a feasible no-op counts as applied
-            A.res->status = !have ? MM_OK : (!v.valid ? MM_ERR_BAD_MOVE : (!v.feasible ? MM_ERR_INFEASIBLE : MM_OK));
-        } else {
-            // periods and mined tonnage
+        A.res->applied = (have && v.valid && v.feasible) ? 1 : 0;  // a feasible no-op counts as applied
+        A.res->status = !have ? MM_OK : (!v.valid ? MM_ERR_BAD_MOVE : (!v.feasible ? MM_ERR_INFEASIBLE : MM_OK));
+        if (go) {
             int64_t dm1 = v.m1, dm2 = v.swap ? (int64_t)v.m2 : 0;
             if (v.t1 < (uint32_t)A.T) A.minedT[v.t1] += -dm1 + dm2;
             if (v.t2 < (uint32_t)A.T) A.minedT[v.t2] += dm1 - dm2;
@@ -340,90 +346,71 @@ __global__ void k_apply(ApplyArgs A, int2 mv_val, const int2 *moves, int64_t n_m
         }
     }
     __syncthreads();
-    if (!s_go) return;
-    MoveView v = sv;
-    // scenario-parallel tonnage and metal updates
-    for (int s = threadIdx.x; s < A.S; s += blockDim.x) {
-        uint32_t o1 = (A.ore[(int64_t)v.b1 * A.W + (s >> 5)] >> (s & 31)) & 1u;
-        int64_t om1 = o1 ? (int64_t)v.m1 : 0;
-        double g1 = o1 ? __dmul_rn((double)v.m1, A.grade[(int64_t)v.b1 * A.S + s]) : 0.0;
-        int64_t om2 = 0;
-        double g2 = 0.0;
-        if (v.swap) {
-            uint32_t o2 = (A.ore[(int64_t)v.b2 * A.W + (s >> 5)] >> (s & 31)) & 1u;
-            om2 = o2 ? (int64_t)v.m2 : 0;
-            g2 = o2 ? __dmul_rn((double)v.m2, A.grade[(int64_t)v.b2 * A.S + s]) : 0.0;
-        }
-        if (v.t1 < (uint32_t)A.T) {
-            A.oreT[(int64_t)v.t1 * A.S + s] += om2 - om1;
-            double &mt = A.metal[(int64_t)v.t1 * A.S + s];
-            mt = __dadd_rn(__dsub_rn(mt, g1), g2);
-        }
-        if (v.t2 < (uint32_t)A.T) {
-            A.oreT[(int64_t)v.t2 * A.S + s] += om1 - om2;
-            double &mt = A.metal[(int64_t)v.t2 * A.S + s];
-            mt = __dadd_rn(__dsub_rn(mt, g2), g1);
-        }
-    }
-    // lo/hi of the neighbourhood (CSR: the moved blocks' own lists)
-    if (A.tp.nx > 0) {
-        if (threadIdx.x < (unsigned)s_nnb) {
+    if (s_go) {
+        const MoveView v = sv;
+        // lo/hi of the neighbourhood (1-5 pattern); CSR handled below
+        if (A.tp.nx > 0 && threadIdx.x < (unsigned)s_nnb) {
             int32_t b = s_nb[threadIdx.x];
             A.blk[b] = block_bounds(A.tp, b, [&](int32_t j) { return blk_period(A.blk[j]); });
         }
-    } else if (threadIdx.x < 2) {
-        int32_t b = threadIdx.x == 0 ? v.b1 : (v.swap ? v.b2 : -1);
-        if (b >= 0) {
-            // moved block: its own bounds; its neighbours are refreshed below
-            A.blk[b] = block_bounds(A.tp, b, [&](int32_t j) { return blk_period(A.blk[j]); });
+        // per scenario: tonnage, metal, contributions, NPV, table rows
+        for (int s = threadIdx.x; s < A.S; s += blockDim.x) {
+            uint32_t o1 = (A.ore[(int64_t)v.b1 * A.W + (s >> 5)] >> (s & 31)) & 1u;
+            int64_t om1 = o1 ? (int64_t)v.m1 : 0;
+            double g1 = o1 ? __dmul_rn((double)v.m1, A.grade[(int64_t)v.b1 * A.S + s]) : 0.0;
+            int64_t om2 = 0;
+            double g2 = 0.0;
+            if (v.swap) {
+                uint32_t o2 = (A.ore[(int64_t)v.b2 * A.W + (s >> 5)] >> (s & 31)) & 1u;
+                om2 = o2 ? (int64_t)v.m2 : 0;
+                g2 = o2 ? __dmul_rn((double)v.m2, A.grade[(int64_t)v.b2 * A.S + s]) : 0.0;
+            }
+            double dnpv = 0.0;
+            const uint32_t rows[2] = {v.t1, v.t2};
+            for (int q = 0; q < 2; q++) {
+                const int t = (int)rows[q];
+                if (t >= A.T) continue;
+                const int64_t dO = q == 0 ? om2 - om1 : om1 - om2;
+                A.oreT[(int64_t)t * A.S + s] += dO;
+                double &mt = A.metal[(int64_t)t * A.S + s];
+                mt = q == 0 ? __dadd_rn(__dsub_rn(mt, g1), g2) : __dadd_rn(__dsub_rn(mt, g2), g1);
+                double c = contrib_of(t, s, A.S, A.disc, A.metal, A.oreT, A.minedT, A.target, A.pr, A.pc, A.mc,
+                                      A.a, A.e);
+                double &cr = A.contrib[(int64_t)t * A.S + s];
+                dnpv = __dadd_rn(dnpv, __dsub_rn(c, cr));
+                cr = c;
+                if (A.uniform)
+                    table_entry(t, s, A.S, A.S_pad, A.T, A.oreT, A.target, A.disc, (int64_t)A.m_uniform, A.a, A.e,
+                                A.tab);
+            }
+            A.npv[s] = __dadd_rn(A.npv[s], dnpv);
         }
-    }
-    __syncthreads();
-    if (A.tp.nx == 0) {
-        // CSR: refresh every predecessor and successor of the moved blocks
-        for (int q = 0; q < 2; q++) {
-            int32_t b = q == 0 ? v.b1 : (v.swap ? v.b2 : -1);
-            if (b < 0) continue;
-            int32_t np = A.tp.pred_ptr[b + 1] - A.tp.pred_ptr[b];
-            int32_t ns = A.tp.succ_ptr[b + 1] - A.tp.succ_ptr[b];
-            for (int k = threadIdx.x; k < np + ns; k += blockDim.x) {
-                int32_t j = k < np ? A.tp.pred_idx[A.tp.pred_ptr[b] + k] : A.tp.succ_idx[A.tp.succ_ptr[b] + k - np];
-                A.blk[j] = block_bounds(A.tp, j, [&](int32_t i) { return blk_period(A.blk[i]); });
+        if (A.tp.nx == 0) {
+            // CSR: the moved blocks first, then every predecessor and successor
+            if (threadIdx.x < 2) {
+                int32_t b = threadIdx.x == 0 ? v.b1 : (v.swap ? v.b2 : -1);
+                if (b >= 0) A.blk[b] = block_bounds(A.tp, b, [&](int32_t j) { return blk_period(A.blk[j]); });
             }
             __syncthreads();
+            for (int q = 0; q < 2; q++) {
+                int32_t b = q == 0 ? v.b1 : (v.swap ? v.b2 : -1);
+                if (b < 0) continue;
+                int32_t np = A.tp.pred_ptr[b + 1] - A.tp.pred_ptr[b];
+                int32_t ns = A.tp.succ_ptr[b + 1] - A.tp.succ_ptr[b];
+                for (int k = threadIdx.x; k < np + ns; k += blockDim.x) {
+                    int32_t j = k < np ? A.tp.pred_idx[A.tp.pred_ptr[b] + k] : A.tp.succ_idx[A.tp.succ_ptr[b] + k - np];
+                    A.blk[j] = block_bounds(A.tp, j, [&](int32_t i) { return blk_period(A.blk[i]); });
+                }
+                __syncthreads();
+            }
         }
     }
-    __syncthreads();
-    // tables of the affected periods
-    if (A.uniform) {
-        uint32_t rows[2] = {v.t1, v.t2};
-        for (int q = 0; q < 2; q++) {
-            int t = (int)rows[q];
-            if (t >= A.T) continue;
-            for (int s = threadIdx.x; s < A.S_pad; s += blockDim.x)
-                table_entry(t, s, A.S, A.S_pad, A.T, A.oreT, A.target, A.disc, (int64_t)A.m_uniform, A.a, A.e, A.tab);
-        }
-    }
-    // NPV from the accumulators
-    for (int s = threadIdx.x; s < A.S; s += blockDim.x)
-        A.npv[s] = npv_of(s, A.S, A.T, A.disc, A.metal, A.oreT, A.minedT, A.target, A.pr, A.pc, A.mc, A.a, A.e);
     __syncthreads();
     double mean = 0, sd = 0;
     npv_stats(A.npv, A.S, &mean, &sd);
     if (threadIdx.x == 0) {
-        A.res->applied = 1;
-        A.res->status = MM_OK;
         A.res->mean = mean;
         A.res->std = sd;
-    }
-}
-
-__global__ void k_npv_stats(const double *npv, int32_t S, ApplyResult *res) {
-    double mean = 0, sd = 0;
-    npv_stats(npv, S, &mean, &sd);
-    if (threadIdx.x == 0) {
-        res->mean = mean;
-        res->std = sd;
     }
 }
 
@@ -442,7 +429,8 @@ static ApplyArgs apply_args(mm_model *m) {
     A.S = m->S; A.S_pad = m->S_pad; A.W = m->W; A.T = m->T;
     A.m_uniform = m->m_uniform; A.uniform = m->uniform_mass;
     A.mass = m->mass; A.ore = m->ore; A.grade = m->grade; A.blk = m->blk;
-    A.minedT = m->minedT; A.oreT = m->oreT; A.metal = m->metal; A.npv = m->npv; A.tab = m->tab;
+    A.minedT = m->minedT; A.oreT = m->oreT; A.metal = m->metal; A.npv = m->npv; A.contrib = m->contrib;
+    A.tab = m->tab;
     A.disc = m->disc; A.cap = m->cap; A.target = m->target;
     A.pr = m->price * m->recovery; A.pc = m->proc_cost; A.mc = m->mining_cost;
     A.a = m->shortfall_pen; A.e = m->excess_pen;
@@ -484,7 +472,8 @@ void mm_model_destroy(mm_model *m) {
     cudaFree(m->mass); cudaFree(m->grade); cudaFree(m->val); cudaFree(m->ore); cudaFree(m->blk);
     cudaFree(m->pred_ptr); cudaFree(m->pred_idx); cudaFree(m->succ_ptr); cudaFree(m->succ_idx);
     cudaFree(m->order); cudaFree(m->porder);
-    cudaFree(m->minedT); cudaFree(m->oreT); cudaFree(m->metal); cudaFree(m->npv); cudaFree(m->tab);
+    cudaFree(m->minedT); cudaFree(m->oreT); cudaFree(m->metal); cudaFree(m->npv); cudaFree(m->contrib);
+    cudaFree(m->tab);
     cudaFree(m->ddt); cudaFree(m->disc); cudaFree(m->cap); cudaFree(m->target); cudaFree(m->status);
     cudaFree(m->apply_res);
     if (m->apply_res_host) cudaFreeHost(m->apply_res_host);
@@ -576,8 +565,8 @@ mm_status mm_model_create(const mm_model_desc *d, mm_model **out) {
     if (st == MM_OK) st = dalloc(&m->ptr, (size_t)(n), "allocate " #ptr)
     ALLOC(mass, B);
     ALLOC(grade, (int64_t)B * S);
-    ALLOC(val, (int64_t)B * m->S_pad);
-    ALLOC(ore, (int64_t)B * m->W);
+    ALLOC(val, (int64_t)(B + 1) * m->S_pad);
+    ALLOC(ore, (int64_t)(B + 1) * m->W);
     ALLOC(blk, B);
     ALLOC(order, B);
     ALLOC(porder, T + 2);
@@ -585,6 +574,7 @@ mm_status mm_model_create(const mm_model_desc *d, mm_model **out) {
     ALLOC(oreT, (int64_t)(T + 1) * S);
     ALLOC(metal, (int64_t)T * S);
     ALLOC(npv, S);
+    ALLOC(contrib, (int64_t)T * S);
     ALLOC(tab, (int64_t)2 * (T + 1) * m->S_pad);
     ALLOC(ddt, (int64_t)(T + 1) * (T + 1));
     ALLOC(disc, T + 1);
@@ -631,6 +621,8 @@ mm_status mm_model_create(const mm_model_desc *d, mm_model **out) {
     TRY(cudaMemcpyAsync(m->disc, m->h_disc.data(), sizeof(double) * (T + 1), cudaMemcpyHostToDevice, s), "copy disc");
     TRY(cudaMemcpyAsync(m->ddt, ddt.data(), sizeof(float) * ddt.size(), cudaMemcpyHostToDevice, s), "copy ddt");
     TRY(cudaMemsetAsync(m->status, 0, sizeof(uint32_t), s), "clear status");
+    TRY(cudaMemsetAsync(m->val + (size_t)B * m->S_pad, 0, sizeof(float) * m->S_pad, s), "clear zero row");
+    TRY(cudaMemsetAsync(m->ore + (size_t)B * m->W, 0, sizeof(uint32_t) * m->W, s), "clear zero row");
     TRY(cudaMemsetAsync(m->oreT, 0, sizeof(int64_t) * (size_t)(T + 1) * S, s), "clear oreT");
     TRY(cudaMemsetAsync(m->minedT, 0, sizeof(int64_t) * (T + 1), s), "clear minedT");
     TRY(cudaMemsetAsync(m->apply_res, 0, sizeof(ApplyResult), s), "clear apply result");
@@ -710,7 +702,7 @@ mm_status mm_schedule_set(mm_model *m, const uint8_t *period, int *base_feasible
     if ((st = rebuild_tables(m)) != MM_OK) return done(st);
     k_npv<<<(S + 127) / 128, 128, 0, s>>>(S, T, m->disc, m->metal, m->oreT, m->minedT, m->target,
                                            m->price * m->recovery, m->proc_cost, m->mining_cost, m->shortfall_pen,
-                                           m->excess_pen, m->npv);
+                                           m->excess_pen, m->contrib, m->npv);
     if ((st = check_launch("k_npv")) != MM_OK) return done(st);
     // base feasibility: arcs (device) + capacity (host, from minedT)
     uint32_t *d_bad = m->status_host ? nullptr : nullptr;
@@ -758,16 +750,8 @@ mm_status mm_apply_move(mm_model *m, mm_move mv, double *mean, double *sd) {
     mm_status sticky = read_sticky(m);
     if (r.status == MM_ERR_BAD_MOVE) return set_error(MM_ERR_BAD_MOVE, "move (%d, %d) is out of range", mv.b1, mv.arg);
     if (r.status == MM_ERR_INFEASIBLE) return set_error(MM_ERR_INFEASIBLE, "move (%d, %d) is infeasible", mv.b1, mv.arg);
-    if (mean || sd) {
-        // a no-op leaves the state as it was: report the current statistics
-        k_npv_stats<<<1, apply_threads(m->S), 0, m->stream>>>(m->npv, m->S, m->apply_res);
-        if ((st = check_launch("k_npv_stats")) != MM_OK) return st;
-        MM_CUDA_TRY(cudaMemcpyAsync(m->apply_res_host, m->apply_res, sizeof(ApplyResult), cudaMemcpyDeviceToHost,
-                                    m->stream), "read apply result");
-        MM_CUDA_TRY(cudaStreamSynchronize(m->stream), "synchronize");
-        if (mean) *mean = m->apply_res_host->mean;
-        if (sd) *sd = m->apply_res_host->std;
-    }
+    if (mean) *mean = r.mean;
+    if (sd) *sd = r.std;
     return sticky;
 }
 
@@ -777,10 +761,7 @@ mm_status mm_apply_best(mm_model *m, const mm_move *moves, int64_t n, const int3
     if (!m->has_schedule) return set_error(MM_ERR_STATE, "no schedule installed");
     ApplyArgs A = apply_args(m);
     k_apply<<<1, apply_threads(m->S), 0, m->stream>>>(A, make_int2(0, 0), (const int2 *)moves, n, idx, count, 1);
-    mm_status st = check_launch("k_apply");
-    if (st != MM_OK) return st;
-    k_npv_stats<<<1, apply_threads(m->S), 0, m->stream>>>(m->npv, m->S, m->apply_res);
-    return check_launch("k_npv_stats");
+    return check_launch("k_apply");
 }
 
 mm_status mm_last_apply(mm_model *m, int32_t *applied, double *mean, double *sd) {

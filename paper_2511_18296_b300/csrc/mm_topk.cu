@@ -4,14 +4,14 @@
 // its FP32 score (-0 folded into +0) in the high word and the complement of its
 // move index in the low word, so larger keys are better and equal scores prefer
 // the lower index.  Selection runs in two launches:
-//   k_topk_hist    every CTA adds its candidates to a 65,536-bin histogram of
-//                  the key's top 16 bits (global atomics); the last CTA to
+//   k_topk_hist    every CTA builds a 4,096-bin shared-memory histogram of the
+//                  key's top 12 bits and adds it to a global one; the last CTA to
 //                  finish (ticket counter, no waiting) finds the cut-off bin
 //                  that holds the k-th best key and clears the histogram.
 //   k_topk_collect every CTA appends keys above the cut-off bin to a "sure"
 //                  list (< k keys) and keys inside it to a "maybe" list; the
 //                  last CTA radix-selects the missing keys from the maybe list
-//                  on the remaining 48 bits, sorts the k keys (bitonic, in
+//                  on the remaining 52 bits, sorts the k keys (bitonic, in
 //                  shared memory) and writes indices, scores and the count.
 // Integer keys make the result independent of thread scheduling.
 #include "mm_internal.cuh"
@@ -34,11 +34,17 @@ __device__ __forceinline__ bool make_key(const float *score, const uint8_t *feas
 __global__ void __launch_bounds__(256) k_topk_hist(const float *__restrict__ score, const uint8_t *__restrict__ feas,
                                                    int64_t n, int32_t k, uint32_t *__restrict__ hist,
                                                    uint32_t *__restrict__ ctl) {
+    __shared__ uint32_t s_h[kHistBins];
+    for (int j = threadIdx.x; j < kHistBins; j += blockDim.x) s_h[j] = 0;
+    __syncthreads();
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         uint64_t key;
-        if (make_key(score, feas, i, key)) atomicAdd(hist + (key >> 48), 1u);
+        if (make_key(score, feas, i, key)) atomicAdd(&s_h[key >> (64 - kHistBits)], 1u);
     }
+    __syncthreads();
+    for (int j = threadIdx.x; j < kHistBins; j += blockDim.x)
+        if (s_h[j]) atomicAdd(hist + j, s_h[j]);
     __threadfence();
     __shared__ uint32_t s_last;
     __syncthreads();
@@ -46,14 +52,22 @@ __global__ void __launch_bounds__(256) k_topk_hist(const float *__restrict__ sco
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    // last CTA: bins are scanned from the top; thread t owns bins
-    // [65535 - 256 t - 255, 65535 - 256 t].
+    // last CTA: bins scanned from the top; thread t owns the 16 bins
+    // [4095 - 16 t - 15, 4095 - 16 t], read as four 16-byte loads.
+    static_assert(kHistBins == 16 * 256, "one thread per 16 bins");
     __shared__ uint32_t s_part[256];
     __shared__ uint32_t s_sel[2];  // owner thread, count before it
     const int t = threadIdx.x;
-    const int hi_bin = kHistBins - 1 - 256 * t;
+    const int lo_bin = kHistBins - 16 * (t + 1);
+    uint32_t h[16];
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        uint4 v = __ldcg(reinterpret_cast<const uint4 *>(hist + lo_bin) + q);
+        h[4 * q] = v.x; h[4 * q + 1] = v.y; h[4 * q + 2] = v.z; h[4 * q + 3] = v.w;
+    }
     uint32_t local = 0;
-    for (int j = 0; j < 256; j++) local += __ldcg(hist + hi_bin - j);
+#pragma unroll
+    for (int j = 0; j < 16; j++) local += h[j];
     s_part[t] = local;
     __syncthreads();
     if (t == 0) {
@@ -76,17 +90,16 @@ __global__ void __launch_bounds__(256) k_topk_hist(const float *__restrict__ sco
     __syncthreads();
     if (s_sel[0] == (uint32_t)t) {
         uint32_t cum = s_sel[1];
-        for (int j = 0; j < 256; j++) {
-            uint32_t h = __ldcg(hist + hi_bin - j);
-            if (cum + h >= (uint32_t)k) {
-                ctl[kCtlCut] = (uint32_t)(hi_bin - j);
+        for (int j = 15; j >= 0; j--) {
+            if (cum + h[j] >= (uint32_t)k) {
+                ctl[kCtlCut] = (uint32_t)(lo_bin + j);
                 break;
             }
-            cum += h;
+            cum += h[j];
         }
     }
-    __syncthreads();
-    for (int j = 0; j < 256; j++) hist[hi_bin - j] = 0u;
+#pragma unroll
+    for (int q = 0; q < 4; q++) reinterpret_cast<uint4 *>(hist + lo_bin)[q] = make_uint4(0, 0, 0, 0);
     if (t == 0) ctl[kCtlTicket1] = 0;
 }
 
@@ -124,7 +137,7 @@ __global__ void __launch_bounds__(256) k_topk_collect(const float *__restrict__ 
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_round; i += stride) {
         uint64_t key = 0;
         bool ok = i < n && make_key(score, feas, i, key);
-        uint32_t bin = (uint32_t)(key >> 48);
+        uint32_t bin = (uint32_t)(key >> (64 - kHistBits));
         bool is_sure = ok && (take_all || bin > cut);
         bool is_maybe = ok && !take_all && bin == cut;
         uint32_t ms = __ballot_sync(0xffffffffu, is_sure);
@@ -178,15 +191,17 @@ __global__ void __launch_bounds__(256) k_topk_collect(const float *__restrict__ 
             __syncthreads();
             if (threadIdx.x == 0) s_n = ns + (uint32_t)nm;
         } else {
-            // radix select of the `need` largest maybe keys on bits 47..0
-            int shift = 40;
-            for (; shift >= 0; shift -= 8) {
+            // radix select of the `need` largest maybe keys on bits 51..0
+            // (digits of 8 bits at shifts 44, 36, ..., 4, then 4 bits at 0)
+            int shift = 64 - kHistBits - 8;
+            for (; shift > -8; shift -= 8) {
+                const int sh = shift < 0 ? 0 : shift;
                 for (int j = threadIdx.x; j < 256; j += blockDim.x) s_hist[j] = 0;
                 __syncthreads();
                 const uint64_t mask = s_mask, prefix = s_prefix;
                 for (uint64_t j = threadIdx.x; j < nm; j += blockDim.x) {
                     uint64_t key = __ldcg(maybe + j);
-                    if ((key & mask) == prefix) atomicAdd(&s_hist[(key >> shift) & 0xffu], 1u);
+                    if ((key & mask) == prefix) atomicAdd(&s_hist[(key >> sh) & 0xffu], 1u);
                 }
                 __syncthreads();
                 if (threadIdx.x == 0) {
@@ -197,8 +212,8 @@ __global__ void __launch_bounds__(256) k_topk_collect(const float *__restrict__ 
                         cum += s_hist[b];
                     }
                     s_need = r - cum;
-                    s_prefix = prefix | ((uint64_t)dgt << shift);
-                    s_mask = mask | (0xffull << shift);
+                    s_prefix = prefix | ((uint64_t)dgt << sh);
+                    s_mask = mask | ((0xffull << sh) & ((1ull << (64 - kHistBits)) - 1));
                     s_done = (s_hist[dgt] == s_need) ? 1u : 0u;
                 }
                 __syncthreads();
