@@ -135,9 +135,13 @@ mm_status mm_eval_moves(mm_model *m, const mm_move *moves_dev, int64_t n, float 
 /* Tile shape of the move evaluator (chosen by the autotuner or by hand):
  * team = lanes that evaluate one move (4, 8, 16 or 32; 0 = built-in choice),
  * ctas_per_sm = resident CTAs per SM of the persistent grid (0 = occupancy
- * maximum).  team must leave at most 8 scenario quads per lane
- * (ceil(ceil(S/4)/team) <= 8), else MM_ERR_INVALID_ARG. */
-mm_status mm_set_tile(mm_model *m, int32_t team, int32_t ctas_per_sm);
+ * maximum), stages = how block rows reach the lanes: 0 = direct global loads,
+ * 1..4 = bulk copies into shared memory with that many batches in flight per
+ * warp, -1 = built-in choice; prefetch = with direct loads, how many batches
+ * ahead the rows are prefetched into L1 (0..8, -1 = built-in choice).  team must
+ * leave at most 8 scenario quads per lane (ceil(ceil(S/4)/team) <= 8), else
+ * MM_ERR_INVALID_ARG. */
+mm_status mm_set_tile(mm_model *m, int32_t team, int32_t ctas_per_sm, int32_t stages, int32_t prefetch);
 
 /* Evaluation options for mm_eval_moves_ex. */
 enum {
@@ -186,8 +190,8 @@ mm_status mm_last_apply(mm_model *m, int32_t *applied, double *npv_mean_out, dou
  * and population std (nullable).  Synchronising. */
 mm_status mm_npv(mm_model *m, double *npv_per_scenario_host, double *mean, double *std);
 
-/* Sizes: any pointer may be NULL.  s_pad = row stride of the value rows (S
- * rounded up to a multiple of 8). */
+/* Sizes: any pointer may be NULL.  s_pad = row stride, in 4-byte words, of the
+ * per-block device rows (S FP32 values, then the ore words; a multiple of 8). */
 mm_status mm_model_info(const mm_model *m, int32_t *B, int32_t *S, int32_t *T, int32_t *s_pad);
 
 /* Inspection (synchronising; host outputs):

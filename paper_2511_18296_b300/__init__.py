@@ -70,7 +70,7 @@ SIGNATURES = [
     ("mm_schedule_get", C.c_int, [P, P]),
     ("mm_eval_moves", C.c_int, [P, P, I64, P, P, P]),
     ("mm_eval_moves_ex", C.c_int, [P, P, I64, P, P, P, P, I32]),
-    ("mm_set_tile", C.c_int, [P, I32, I32]),
+    ("mm_set_tile", C.c_int, [P, I32, I32, I32, I32]),
     ("mm_topk", C.c_int, [P, P, P, I64, I32, P, P, P]),
     ("mm_apply_move", C.c_int, [P, MMMove, P, P]),
     ("mm_apply_best", C.c_int, [P, P, I64, P, P]),
@@ -172,8 +172,8 @@ class Model:
         except Exception:
             pass
 
-    def set_tile(self, team: int = 0, ctas_per_sm: int = 0):
-        _check(lib().mm_set_tile(self.h, team, ctas_per_sm))
+    def set_tile(self, team: int = 0, ctas_per_sm: int = 0, stages: int = -1, prefetch: int = -1):
+        _check(lib().mm_set_tile(self.h, team, ctas_per_sm, stages, prefetch))
 
     def set_stream(self, stream=None):
         _check(lib().mm_set_stream(self.h, _stream_handle(stream)))

@@ -29,8 +29,8 @@
 namespace mm {
 
 using EvalFn = void (*)(EvalArgs);
-EvalFn pick_tiled_plain(int team, int qmax, bool delta, bool tsm);
-EvalFn pick_tiled_kahan(int team, int qmax, bool delta, bool tsm);
+EvalFn pick_tiled_plain(int team, int qmax, bool delta, bool tsm, bool tma);
+EvalFn pick_tiled_kahan(int team, int qmax, bool delta, bool tsm, bool tma);
 
 // General evaluator (unequal block masses): one warp per move, one lane per
 // scenario, penalty change from the exact integer ore tonnages:
@@ -47,7 +47,7 @@ __global__ void __launch_bounds__(256) k_eval_general(EvalArgs A) {
     const int lane = threadIdx.x & 31;
     const int64_t warp_gid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int S = A.S, S_pad = A.S_pad, W = A.W, T1 = A.T + 1;
+    const int S = A.S, T1 = A.T + 1;
     for (int64_t i = warp_gid; i < A.n; i += nwarps) {
         const int2 mv = __ldg(A.moves + i);
         const MoveView v = decode_move(
@@ -62,13 +62,15 @@ __global__ void __launch_bounds__(256) k_eval_general(EvalArgs A) {
             const int s = lane + 32 * k;
             float x = 0.0f;
             if (work && s < S) {
-                const uint32_t o1 = (__ldg(A.ore + (int64_t)v.b1 * W + (s >> 5)) >> (s & 31)) & 1u;
-                const float v1 = __ldg(A.val + (int64_t)v.b1 * S_pad + s);
+                const float *row1 = A.val + (int64_t)v.b1 * A.R;
+                const uint32_t o1 = (__ldg(reinterpret_cast<const uint32_t *>(row1 + A.ore_off) + (s >> 5)) >> (s & 31)) & 1u;
+                const float v1 = __ldg(row1 + s);
                 uint32_t o2 = 0;
                 float v2 = 0.0f;
                 if (v.swap) {
-                    o2 = (__ldg(A.ore + (int64_t)v.b2 * W + (s >> 5)) >> (s & 31)) & 1u;
-                    v2 = __ldg(A.val + (int64_t)v.b2 * S_pad + s);
+                    const float *row2 = A.val + (int64_t)v.b2 * A.R;
+                    o2 = (__ldg(reinterpret_cast<const uint32_t *>(row2 + A.ore_off) + (s >> 5)) >> (s & 31)) & 1u;
+                    v2 = __ldg(row2 + s);
                 }
                 const int64_t dO = (int64_t)(o2 ? v.m2 : 0) - (int64_t)(o1 ? v.m1 : 0);
                 double p = 0.0;
@@ -131,19 +133,21 @@ int default_team(int S) {
 }
 
 mm_status eval_launch(mm_model *m, const mm_move *moves, int64_t n, float *score, uint8_t *feas, float *mean,
-                      float *delta, int32_t options, int team, int ctas_per_sm) {
+                      float *delta, int32_t options, int team, int ctas_per_sm, int stages) {
     EvalArgs A;
     A.moves = reinterpret_cast<const int2 *>(moves);
     A.n = n;
     A.score = score; A.feas = feas; A.mean = mean; A.delta = delta;
-    A.val = m->val; A.ore = m->ore; A.blk = m->blk; A.mass = m->mass;
+    A.val = m->val; A.blk = m->blk; A.mass = m->mass;
     A.tab = m->tab; A.ddt = m->ddt; A.minedT = m->minedT; A.cap = m->cap;
     A.oreT = m->oreT; A.target = m->target; A.disc = m->disc;
     A.status = m->status;
     A.tp.B = m->B; A.tp.T = m->T; A.tp.nx = m->nx; A.tp.ny = m->ny; A.tp.nz = m->nz;
     A.tp.pred_ptr = m->pred_ptr; A.tp.pred_idx = m->pred_idx; A.tp.succ_ptr = m->succ_ptr; A.tp.succ_idx = m->succ_idx;
-    A.S = m->S; A.S_pad = m->S_pad; A.W = m->W; A.T = m->T;
+    A.S = m->S; A.S_pad = m->S_pad; A.W = m->W; A.T = m->T; A.R = m->R; A.ore_off = m->ore_off;
     A.m_uniform = m->m_uniform;
+    A.nstage = 0;
+    A.prefetch = m->prefetch < 0 ? kDefaultPrefetch : m->prefetch;
     A.lambda = (float)m->lambda;
     A.a = m->shortfall_pen; A.e = m->excess_pen;
     A.qpl = 0;
@@ -168,13 +172,29 @@ mm_status eval_launch(mm_model *m, const mm_move *moves, int64_t n, float *score
     const size_t tab_bytes = (size_t)2 * T1 * m->S_pad * sizeof(float);
     const size_t small = (((size_t)T1 * T1 * sizeof(float) + 15) & ~(size_t)15) + 2 * (size_t)T1 * sizeof(int64_t);
     const bool tsm = tab_bytes <= 64 * 1024;
-    const size_t smem = (tsm ? tab_bytes : 0) + small;
-    EvalFn fn = kahan ? pick_tiled_kahan(team, qmax, want_delta, tsm) : pick_tiled_plain(team, qmax, want_delta, tsm);
+    if (stages < 0) stages = kDefaultStages;
+    if (stages > kMaxStages) stages = kMaxStages;
+    const bool tma = stages > 0;
+    A.nstage = stages;
+    size_t smem = (tsm ? tab_bytes : 0) + small;
+    if (tma) {
+        // the static shared arrays of the kernel take ~12 KB; keep a margin
+        const size_t base = ((smem + 127) & ~(size_t)127);
+        const size_t per_stage = (size_t)(kEvalThreads / 32) * (32 / team) * 2 * m->R * sizeof(float);
+        while (stages > 1 && base + stages * per_stage + 16 * 1024 > (size_t)m->max_smem_optin) stages--;
+        if (base + stages * per_stage + 16 * 1024 > (size_t)m->max_smem_optin) stages = 0;
+        if (stages > 0) smem = base + stages * per_stage;
+    }
+    const bool use_tma = stages > 0;
+    A.nstage = stages;
+    EvalFn fn = kahan ? pick_tiled_kahan(team, qmax, want_delta, tsm, use_tma)
+                      : pick_tiled_plain(team, qmax, want_delta, tsm, use_tma);
     if (!fn) return set_error(MM_ERR_INVALID_ARG, "no evaluator for team %d with %d quads per lane", team, qpl);
-    if (smem > 48 * 1024 && m->smem_attr_set.count((const void *)fn) == 0) {
+    // the 48 KB default covers static + dynamic shared memory (~12 KB static here)
+    if (smem + 16 * 1024 > 48 * 1024 && m->smem_attr[(const void *)fn] < smem) {
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return cuda_status(e, "set evaluator shared memory");
-        m->smem_attr_set.insert((const void *)fn);
+        m->smem_attr[(const void *)fn] = smem;
     }
     int per_sm = ctas_per_sm;
     if (per_sm <= 0) {
@@ -220,18 +240,22 @@ extern "C" {
 mm_status mm_eval_moves(mm_model *m, const mm_move *moves, int64_t n, float *score, uint8_t *feas, float *mean) {
     mm_status st = eval_check(m, moves, n, score, feas);
     if (st != MM_OK || n == 0) return st;
-    return eval_launch(m, moves, n, score, feas, mean, nullptr, MM_EVAL_PLAIN, m->team, m->ctas_per_sm);
+    return eval_launch(m, moves, n, score, feas, mean, nullptr, MM_EVAL_PLAIN, m->team, m->ctas_per_sm, m->stages);
 }
 
-mm_status mm_set_tile(mm_model *m, int32_t team, int32_t ctas_per_sm) {
+mm_status mm_set_tile(mm_model *m, int32_t team, int32_t ctas_per_sm, int32_t stages, int32_t prefetch) {
     if (!m) return set_error(MM_ERR_INVALID_ARG, "NULL model");
     if (team != 0 && team != 4 && team != 8 && team != 16 && team != 32)
         return set_error(MM_ERR_INVALID_ARG, "team must be 0, 4, 8, 16 or 32");
     if (team != 0 && ((m->S + 3) / 4 + team - 1) / team > 8)
         return set_error(MM_ERR_INVALID_ARG, "team %d leaves more than 8 quads per lane at S = %d", team, m->S);
     if (ctas_per_sm < 0 || ctas_per_sm > 32) return set_error(MM_ERR_INVALID_ARG, "ctas_per_sm out of range");
+    if (stages < -1 || stages > kMaxStages) return set_error(MM_ERR_INVALID_ARG, "stages must be -1..%d", kMaxStages);
     m->team = team;
     m->ctas_per_sm = ctas_per_sm;
+    if (prefetch < -1 || prefetch > 8) return set_error(MM_ERR_INVALID_ARG, "prefetch must be -1..8");
+    m->stages = stages;
+    m->prefetch = prefetch;
     return MM_OK;
 }
 
@@ -240,7 +264,7 @@ mm_status mm_eval_moves_ex(mm_model *m, const mm_move *moves, int64_t n, float *
     mm_status st = eval_check(m, moves, n, score, feas);
     if (st != MM_OK || n == 0) return st;
     if (options & ~MM_EVAL_KAHAN) return set_error(MM_ERR_INVALID_ARG, "unknown option bits 0x%x", options);
-    return eval_launch(m, moves, n, score, feas, mean, delta, options, m->team, m->ctas_per_sm);
+    return eval_launch(m, moves, n, score, feas, mean, delta, options, m->team, m->ctas_per_sm, m->stages);
 }
 
 }  // extern "C"

@@ -7,28 +7,32 @@ namespace mm {
 using EvalFn = void (*)(EvalArgs);
 
 template <int TEAM, int QMAX>
-static EvalFn pick2(bool delta, bool tsm) {
+static EvalFn pick2(bool delta, bool tsm, bool tma) {
+    if (tma) {
+        if (delta) return tsm ? k_eval_tma<TEAM, QMAX, true, true, true> : k_eval_tma<TEAM, QMAX, true, true, false>;
+        return tsm ? k_eval_tma<TEAM, QMAX, true, false, true> : k_eval_tma<TEAM, QMAX, true, false, false>;
+    }
     if (delta) return tsm ? k_eval_tiled<TEAM, QMAX, true, true, true> : k_eval_tiled<TEAM, QMAX, true, true, false>;
     return tsm ? k_eval_tiled<TEAM, QMAX, true, false, true> : k_eval_tiled<TEAM, QMAX, true, false, false>;
 }
 
 template <int TEAM>
-static EvalFn pick1(int qmax, bool delta, bool tsm) {
+static EvalFn pick1(int qmax, bool delta, bool tsm, bool tma) {
     switch (qmax) {
-        case 1: return pick2<TEAM, 1>(delta, tsm);
-        case 2: return pick2<TEAM, 2>(delta, tsm);
-        case 4: return pick2<TEAM, 4>(delta, tsm);
-        case 8: return pick2<TEAM, 8>(delta, tsm);
+        case 1: return pick2<TEAM, 1>(delta, tsm, tma);
+        case 2: return pick2<TEAM, 2>(delta, tsm, tma);
+        case 4: return pick2<TEAM, 4>(delta, tsm, tma);
+        case 8: return pick2<TEAM, 8>(delta, tsm, tma);
     }
     return nullptr;
 }
 
-EvalFn pick_tiled_kahan(int team, int qmax, bool delta, bool tsm) {
+EvalFn pick_tiled_kahan(int team, int qmax, bool delta, bool tsm, bool tma) {
     switch (team) {
-        case 4: return pick1<4>(qmax, delta, tsm);
-        case 8: return pick1<8>(qmax, delta, tsm);
-        case 16: return pick1<16>(qmax, delta, tsm);
-        case 32: return pick1<32>(qmax, delta, tsm);
+        case 4: return pick1<4>(qmax, delta, tsm, tma);
+        case 8: return pick1<8>(qmax, delta, tsm, tma);
+        case 16: return pick1<16>(qmax, delta, tsm, tma);
+        case 32: return pick1<32>(qmax, delta, tsm, tma);
     }
     return nullptr;
 }

@@ -38,8 +38,7 @@ struct EvalArgs {
     uint8_t *feas;
     float *mean;
     float *delta;
-    const float *val;      // [B+1][S_pad], row B = zeros (stand-in partner of a shift)
-    const uint32_t *ore;   // [B+1][W],     row B = zeros
+    const float *val;      // [B+1][R] combined rows (values, then ore words), row B = zeros
     const uint32_t *blk;
     const uint32_t *mass;
     const float *tab;
@@ -51,9 +50,11 @@ struct EvalArgs {
     const double *disc;
     uint32_t *status;
     Topo tp;
-    int32_t S, S_pad, W, T;
+    int32_t S, S_pad, W, T, R, ore_off;
     uint32_t m_uniform;
     int32_t qpl;           // quads per lane actually used (<= QMAX)
+    int32_t nstage;        // bulk-copy pipeline depth per warp (TMA path)
+    int32_t prefetch;      // direct-load path: batches whose rows are prefetched into L1 ahead
     float lambda;
     double a, e;
 };
@@ -97,24 +98,28 @@ __device__ __forceinline__ float4 ld_tab(const float *p) {
     return __ldg(reinterpret_cast<const float4 *>(p));
 }
 
-// Ore bits of quad q (scenarios 4q..4q+3) of an ore row.
-template <int TEAM>
-__device__ __forceinline__ uint32_t ore_nibble(const uint32_t *orow, int q) {
-    return (__ldg(orow + (q >> 3)) >> ((q & 7) * 4)) & 0xfu;
+// Loads from a block row that lives in global memory (read-only path) or in
+// shared memory (staged by a bulk copy).
+template <bool SROW>
+__device__ __forceinline__ float4 ld_row4(const float *row, int q) {
+    if (SROW) return reinterpret_cast<const float4 *>(row)[q];
+    return __ldg(reinterpret_cast<const float4 *>(row) + q);
+}
+template <bool SROW>
+__device__ __forceinline__ uint32_t ld_ore_word(const float *row, int ore_off, int w) {
+    if (SROW) return reinterpret_cast<const uint32_t *>(row + ore_off)[w];
+    return __ldg(reinterpret_cast<const uint32_t *>(row + ore_off) + w);
 }
 
 // Per-move scenario loop + reduction for one team.  SWAP selects the move
-// type at compile time.  Returns the mean; writes the deltas to d[][].
-template <int TEAM, int QMAX, bool SWAP, bool KAHAN>
+// type at compile time, SROW where the two block rows live.  Writes the
+// deltas to d[][], the mean to mu and the population std to sd.
+template <int TEAM, int QMAX, bool SWAP, bool KAHAN, bool SROW>
 __device__ __forceinline__ void team_eval(const EvalArgs &A, const float *tab, const float4 *lut, int tl, bool act,
-                                          int32_t b1, int32_t b2, uint32_t t1, uint32_t t2, float dd, int NQ,
-                                          int rem, float invS, size_t pin_off, float (&d)[QMAX][4], float &mu,
+                                          const float *row1, const float *row2, uint32_t t1, uint32_t t2, float dd,
+                                          int NQ, int rem, float invS, size_t pin_off, float (&d)[QMAX][4], float &mu,
                                           float &sd) {
-    const int S_pad = A.S_pad, W = A.W;
-    const float *vrow1 = A.val + (size_t)b1 * S_pad;
-    const float *vrow2 = A.val + (size_t)b2 * S_pad;
-    const uint32_t *orow1 = A.ore + (size_t)b1 * W;
-    const uint32_t *orow2 = A.ore + (size_t)b2 * W;
+    const int S_pad = A.S_pad, ore_off = A.ore_off;
     const int pout1 = (int)t1 * S_pad, pout2 = (int)t2 * S_pad;
     const int pin1 = (int)pin_off + pout1, pin2 = (int)pin_off + pout2;
     const int nq = act ? NQ : 0;
@@ -122,33 +127,38 @@ __device__ __forceinline__ void team_eval(const EvalArgs &A, const float *tab, c
 #pragma unroll
     for (int k = 0; k < QMAX; k++) {
         const int q = tl + k * TEAM;
-#pragma unroll
-        for (int j = 0; j < 4; j++) d[k][j] = 0.0f;
-        if (k < A.qpl && q < nq) {
-            const float4 a = __ldg(reinterpret_cast<const float4 *>(vrow1) + q);
-            const float4 pa = ld_tab<true>(tab + pout1 + 4 * q);
-            const float4 pb = ld_tab<true>(tab + pin2 + 4 * q);
-            if (SWAP) {
-                const float4 b = __ldg(reinterpret_cast<const float4 *>(vrow2) + q);
-                const uint32_t n1 = ore_nibble<TEAM>(orow1, q);
-                const uint32_t n2 = ore_nibble<TEAM>(orow2, q);
-                const float4 m1 = lut[n1 & ~n2];
-                const float4 m2 = lut[n2 & ~n1];
-                const float4 pc = ld_tab<true>(tab + pin1 + 4 * q);
-                const float4 pd = ld_tab<true>(tab + pout2 + 4 * q);
-                d[k][0] = fmaf(a.x - b.x, dd, fmaf(m2.x, pc.x + pd.x, m1.x * (pa.x + pb.x)));
-                d[k][1] = fmaf(a.y - b.y, dd, fmaf(m2.y, pc.y + pd.y, m1.y * (pa.y + pb.y)));
-                d[k][2] = fmaf(a.z - b.z, dd, fmaf(m2.z, pc.z + pd.z, m1.z * (pa.z + pb.z)));
-                d[k][3] = fmaf(a.w - b.w, dd, fmaf(m2.w, pc.w + pd.w, m1.w * (pa.w + pb.w)));
-            } else {
-                const float4 m1 = lut[ore_nibble<TEAM>(orow1, q)];
-                d[k][0] = fmaf(a.x, dd, m1.x * (pa.x + pb.x));
-                d[k][1] = fmaf(a.y, dd, m1.y * (pa.y + pb.y));
-                d[k][2] = fmaf(a.z, dd, m1.z * (pa.z + pb.z));
-                d[k][3] = fmaf(a.w, dd, m1.w * (pa.w + pb.w));
-            }
-            // padding scenarios (s >= S) have zero rows and zero ore bits: d = 0 there
+        // loads are unconditional and in bounds (quad index clamped) so the
+        // compiler can issue every quad's loads before the first use; lanes
+        // past the last quad, inactive teams and k >= qpl are masked to 0.
+        const int qc = q < NQ ? q : NQ - 1;
+        const bool live = (k < A.qpl) && (q < nq);
+        const float4 a = ld_row4<SROW>(row1, qc);
+        const uint32_t sh = (qc & 7) * 4;
+        const float4 pa = ld_tab<true>(tab + pout1 + 4 * qc);
+        const float4 pb = ld_tab<true>(tab + pin2 + 4 * qc);
+        float x[4];
+        if (SWAP) {
+            const float4 b = ld_row4<SROW>(row2, qc);
+            const uint32_t n1 = (ld_ore_word<SROW>(row1, ore_off, qc >> 3) >> sh) & 0xfu;
+            const uint32_t n2 = (ld_ore_word<SROW>(row2, ore_off, qc >> 3) >> sh) & 0xfu;
+            const float4 m1 = lut[n1 & ~n2];
+            const float4 m2 = lut[n2 & ~n1];
+            const float4 pc = ld_tab<true>(tab + pin1 + 4 * qc);
+            const float4 pd = ld_tab<true>(tab + pout2 + 4 * qc);
+            x[0] = fmaf(a.x - b.x, dd, fmaf(m2.x, pc.x + pd.x, m1.x * (pa.x + pb.x)));
+            x[1] = fmaf(a.y - b.y, dd, fmaf(m2.y, pc.y + pd.y, m1.y * (pa.y + pb.y)));
+            x[2] = fmaf(a.z - b.z, dd, fmaf(m2.z, pc.z + pd.z, m1.z * (pa.z + pb.z)));
+            x[3] = fmaf(a.w - b.w, dd, fmaf(m2.w, pc.w + pd.w, m1.w * (pa.w + pb.w)));
+        } else {
+            const float4 m1 = lut[(ld_ore_word<SROW>(row1, ore_off, qc >> 3) >> sh) & 0xfu];
+            x[0] = fmaf(a.x, dd, m1.x * (pa.x + pb.x));
+            x[1] = fmaf(a.y, dd, m1.y * (pa.y + pb.y));
+            x[2] = fmaf(a.z, dd, m1.z * (pa.z + pb.z));
+            x[3] = fmaf(a.w, dd, m1.w * (pa.w + pb.w));
         }
+        // padding scenarios (s >= S) have zero values and zero ore bits: d = 0 there
+#pragma unroll
+        for (int j = 0; j < 4; j++) d[k][j] = live ? x[j] : 0.0f;
         if (KAHAN) {
 #pragma unroll
             for (int j = 0; j < 4; j++) comp_add(sum, csum, d[k][j]);
@@ -191,12 +201,43 @@ __device__ __forceinline__ void team_eval(const EvalArgs &A, const float *tab, c
     sd = sqrtf(var * invS);
 }
 
+// Per-scenario deltas of one move to delta[i][0..S).
+template <int TEAM, int QMAX>
+__device__ __forceinline__ void write_deltas(const EvalArgs &A, int64_t i, int tl, int NQ, int rem,
+                                             const float (&d)[QMAX][4]) {
+    float *drow = A.delta + i * (int64_t)A.S;
+#pragma unroll
+    for (int k = 0; k < QMAX; k++) {
+        const int q = tl + k * TEAM;
+        if (k < A.qpl && q < NQ) {
+            const int nv = (q == NQ - 1) ? rem : 4;
+#pragma unroll
+            for (int j = 0; j < 4; j++)
+                if (j < nv) drow[4 * q + j] = d[k][j];
+        }
+    }
+}
+
+// Non-binding prefetch of one 128-byte line into L1.
+__device__ __forceinline__ void prefetch_l1(const void *p) {
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
+
+// The lanes of a team prefetch the 128-byte lines of one block row.
+template <int TEAM>
+__device__ __forceinline__ void prefetch_row(const float *row, uint32_t row_bytes, int tl) {
+    const uintptr_t beg = reinterpret_cast<uintptr_t>(row) & ~(uintptr_t)127;
+    const uintptr_t end = reinterpret_cast<uintptr_t>(row) + row_bytes;
+    for (uintptr_t a = beg + (uintptr_t)tl * 128; a < end; a += (uintptr_t)TEAM * 128)
+        prefetch_l1(reinterpret_cast<const void *>(a));
+}
+
 template <int TEAM, int QMAX, bool KAHAN, bool DELTA, bool TSM>
 __global__ void __launch_bounds__(kEvalThreads, MM_EVAL_MINB) k_eval_tiled(EvalArgs A) {
     constexpr int CH = kChunk;              // moves per warp chunk (2 per lane)
     constexpr int NW = kEvalThreads / 32;   // warps per CTA
     constexpr int TPW = 32 / TEAM;          // teams per warp
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(128) unsigned char smem[];
     __shared__ float4 s_lut[16];
     __shared__ int32_t s_b1[NW][CH], s_b2[NW][CH];
     __shared__ uint32_t s_tt[NW][CH];
@@ -286,49 +327,307 @@ __global__ void __launch_bounds__(kEvalThreads, MM_EVAL_MINB) k_eval_tiled(EvalA
             nsw += __popc(msw);
         }
         __syncwarp();
-        // ---- compute: teams over the shift list, then the swap list ----
+        // ---- compute: batches of TPW list entries, shifts first, then swaps;
+        //      the rows of batch j + prefetch are pulled into L1 meanwhile ----
+        const int nbs = (nsh + TPW - 1) / TPW, nb = nbs + (nsw + TPW - 1) / TPW;
+        const uint32_t row_bytes = (uint32_t)A.R * 4u;
+        auto prefetch_batch = [&](int j) {
+            if (j >= nb) return;
+            const bool sw = j >= nbs;
+            const int e = (sw ? j - nbs : j) * TPW + tw;
+            if (e < (sw ? nsw : nsh)) {
+                const int slot = (sw ? s_lsw[warp] : s_lsh[warp])[e];
+                prefetch_row<TEAM>(A.val + (size_t)s_b1[warp][slot] * A.R, row_bytes, tl);
+                if (sw) prefetch_row<TEAM>(A.val + (size_t)s_b2[warp][slot] * A.R, row_bytes, tl);
+            }
+        };
+        for (int j = 0; j < A.prefetch && j < nb; j++) prefetch_batch(j);
 #pragma unroll 1
-        for (int pass = 0; pass < 2; pass++) {
-            const int nl = pass == 0 ? nsh : nsw;
-            const uint8_t *list = pass == 0 ? s_lsh[warp] : s_lsw[warp];
-#pragma unroll 1
-            for (int eb = 0; eb < nl; eb += TPW) {
-                const int e = eb + tw;
-                const bool act = e < nl;
-                const int slot = act ? list[e] : 0;
-                const int32_t b1 = act ? s_b1[warp][slot] : 0;
-                const int32_t b2 = act ? s_b2[warp][slot] : 0;
-                const uint32_t tt = act ? s_tt[warp][slot] : 0;
-                const uint32_t t1 = tt & 0xffu, t2 = tt >> 8;
-                const float dd = s_dd[t1 * T1 + t2];
-                float d[QMAX][4];
-                float mu, sd;
-                if (pass == 0)
-                    team_eval<TEAM, QMAX, false, KAHAN>(A, tab, s_lut, tl, act, b1, b2, t1, t2, dd, NQ, rem, invS,
-                                                        pin_off, d, mu, sd);
-                else
-                    team_eval<TEAM, QMAX, true, KAHAN>(A, tab, s_lut, tl, act, b1, b2, t1, t2, dd, NQ, rem, invS,
-                                                       pin_off, d, mu, sd);
-                if (act) {
-                    if (tl == 0) {
-                        s_score[warp][slot] = mu - A.lambda * sd;
-                        s_mean[warp][slot] = mu;
-                    }
-                    if (DELTA) {
-                        float *drow = A.delta + (c0 + slot) * (int64_t)S;
+        for (int j = 0; j < nb; j++) {
+            if (A.prefetch > 0) prefetch_batch(j + A.prefetch);
+            const bool sw = j >= nbs;
+            const int e = (sw ? j - nbs : j) * TPW + tw;
+            const int nl = sw ? nsw : nsh;
+            const bool act = e < nl;
+            const int slot = act ? (sw ? s_lsw[warp] : s_lsh[warp])[e] : 0;
+            const int32_t b1 = act ? s_b1[warp][slot] : 0;
+            const int32_t b2 = act ? s_b2[warp][slot] : 0;
+            const uint32_t tt = act ? s_tt[warp][slot] : 0;
+            const uint32_t t1 = tt & 0xffu, t2 = tt >> 8;
+            const float dd = s_dd[t1 * T1 + t2];
+            float d[QMAX][4];
+            float mu, sd;
+            const float *row1 = A.val + (size_t)b1 * A.R;
+            const float *row2 = A.val + (size_t)b2 * A.R;
+            if (!sw)
+                team_eval<TEAM, QMAX, false, KAHAN, false>(A, tab, s_lut, tl, act, row1, row2, t1, t2, dd, NQ, rem,
+                                                           invS, pin_off, d, mu, sd);
+            else
+                team_eval<TEAM, QMAX, true, KAHAN, false>(A, tab, s_lut, tl, act, row1, row2, t1, t2, dd, NQ, rem,
+                                                          invS, pin_off, d, mu, sd);
+            if (act) {
+                if (tl == 0) {
+                    s_score[warp][slot] = mu - A.lambda * sd;
+                    s_mean[warp][slot] = mu;
+                }
+                if (DELTA) write_deltas<TEAM, QMAX>(A, c0 + slot, tl, NQ, rem, d);
+            }
+        }
+        __syncwarp();
+        // ---- store (coalesced) ----
 #pragma unroll
-                        for (int k = 0; k < QMAX; k++) {
-                            const int q = tl + k * TEAM;
-                            if (k < A.qpl && q < NQ) {
-                                const int nv = (q == NQ - 1) ? rem : 4;
+        for (int h = 0; h < 2; h++) {
+            const int slot = h * 32 + lane;
+            const int64_t i = c0 + slot;
+            if (i < r1) {
+                A.score[i] = s_score[warp][slot];
+                if (A.mean) A.mean[i] = s_mean[warp][slot];
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// ----------------------------------------------------------------------------
+// Bulk-copy (TMA) staged evaluator.  Same decode / list / team structure as
+// k_eval_tiled, but the value rows of the next batches of moves are copied
+// into shared memory by cp.async.bulk (one 1-D copy per moved block row,
+// values and ore bits together), tracked by one mbarrier per pipeline stage,
+// so the gathers of several batches are in flight while a batch is computed.
+// A batch is TPW = 32 / TEAM list entries (one per team).  Lane 0 of the warp
+// is the producer.  Every wait is bounded: on expiry the kernel raises the
+// sticky timeout bit, drains its own copies (again bounded) and returns.
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+// Order this thread's earlier generic-proxy shared-memory accesses before its
+// later async-proxy (bulk copy) accesses to the same buffers.
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz: far beyond any legitimate copy latency
+
+// Bounded wait for a pipeline stage (uniform across the warp).
+__device__ __forceinline__ bool stage_wait(uint64_t *bar, uint32_t parity) {
+    bool ok = mbar_try_wait(bar, parity);
+    if (!ok) {
+        const long long t0 = clock64();
+        while (!(ok = mbar_try_wait(bar, parity)))
+            if (clock64() - t0 > kWaitCycles) break;
+    }
+    return __all_sync(0xffffffffu, ok);
+}
+
+constexpr int kMaxStages = 4;
+constexpr int kDefaultStages = 0;    // direct loads measured faster than bulk copies of 416-byte rows
+constexpr int kDefaultPrefetch = 0;
+
+template <int TEAM, int QMAX, bool KAHAN, bool DELTA, bool TSM>
+__global__ void __launch_bounds__(kEvalThreads, 1) k_eval_tma(EvalArgs A) {
+    constexpr int CH = kChunk;
+    constexpr int NWMAX = kEvalThreads / 32;
+    constexpr int TPW = 32 / TEAM;
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ float4 s_lut[16];
+    __shared__ int32_t s_b1[NWMAX][CH], s_b2[NWMAX][CH];
+    __shared__ uint32_t s_tt[NWMAX][CH];
+    __shared__ uint8_t s_lsh[NWMAX][CH], s_lsw[NWMAX][CH];
+    __shared__ float s_score[NWMAX][CH], s_mean[NWMAX][CH];
+    __shared__ __align__(8) uint64_t s_bar[NWMAX][kMaxStages];
+
+    const int NW = blockDim.x >> 5;
+    const int NS = A.nstage;
+    const int T1 = A.T + 1;
+    const int R = A.R;
+    const size_t tab_floats = (size_t)2 * T1 * A.S_pad;
+    float *s_tab = reinterpret_cast<float *>(smem);                            // [2][T+1][S_pad] if TSM
+    float *s_dd = s_tab + (TSM ? tab_floats : 0);                              // [(T+1)^2]
+    size_t off = ((TSM ? tab_floats : 0) + (size_t)T1 * T1) * sizeof(float);
+    off = (off + 15) & ~(size_t)15;
+    int64_t *s_mined = reinterpret_cast<int64_t *>(smem + off);                // [T+1]
+    uint64_t *s_cap = reinterpret_cast<uint64_t *>(s_mined + T1);              // [T+1]
+    off += 2 * (size_t)T1 * sizeof(int64_t);
+    off = (off + 127) & ~(size_t)127;
+    float *s_stage_all = reinterpret_cast<float *>(smem + off);                // [NW][NS][TPW][2][R]
+
+    const int tid = threadIdx.x;
+    if (TSM) {
+        const float4 *src = reinterpret_cast<const float4 *>(A.tab);
+        float4 *dst = reinterpret_cast<float4 *>(s_tab);
+        for (int i = tid; i < (int)(tab_floats / 4); i += blockDim.x) dst[i] = __ldg(src + i);
+    }
+    for (int i = tid; i < T1 * T1; i += blockDim.x) s_dd[i] = __ldg(A.ddt + i);
+    for (int i = tid; i < T1; i += blockDim.x) {
+        s_mined[i] = A.minedT[i];
+        s_cap[i] = A.cap[i];
+    }
+    if (tid < 16)
+        s_lut[tid] = make_float4((float)(tid & 1), (float)((tid >> 1) & 1), (float)((tid >> 2) & 1),
+                                 (float)((tid >> 3) & 1));
+    const int lane = tid & 31, warp = tid >> 5;
+    if (lane == 0)
+        for (int st = 0; st < NS; st++) mbar_init(&s_bar[warp][st], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    __syncthreads();
+    const float *tab = TSM ? s_tab : A.tab;
+
+    const int tl = lane % TEAM, tw = lane / TEAM;
+    const int S = A.S;
+    const int NQ = (S + 3) >> 2;
+    const int rem = S - 4 * (NQ - 1);
+    const float invS = 1.0f / (float)S;
+    const size_t pin_off = (size_t)T1 * A.S_pad;
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    const uint32_t row_bytes = (uint32_t)R * 4u;
+    float *stage0 = s_stage_all + (size_t)warp * NS * TPW * 2 * R;
+    const int64_t nwarps = (int64_t)gridDim.x * NW;
+    const int64_t gw = (int64_t)blockIdx.x * NW + warp;
+    const int64_t r0 = gw * A.n / nwarps, r1 = (gw + 1) * A.n / nwarps;
+    uint32_t parity = 0;  // bit st: parity of the next completion of stage st
+    uint32_t cnt = 0;     // batches issued (== consumed at chunk boundaries) by this warp
+
+    int2 mv[2];
 #pragma unroll
-                                for (int j = 0; j < 4; j++)
-                                    if (j < nv) drow[4 * q + j] = d[k][j];
-                            }
-                        }
-                    }
+    for (int h = 0; h < 2; h++) {
+        const int64_t i = r0 + h * 32 + lane;
+        mv[h] = i < r1 ? __ldg(A.moves + i) : make_int2(0, -1);
+    }
+    for (int64_t c0 = r0; c0 < r1; c0 += CH) {
+        // ---- decode: two moves per lane ----
+        int nsh = 0, nsw = 0;
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            const int slot = h * 32 + lane;
+            const int64_t i = c0 + slot;
+            const bool active = i < r1;
+            const MoveView v = decode_move(
+                mv[h], A.tp, [&](int32_t b) { return __ldg(A.blk + b); }, [&](int32_t) { return A.m_uniform; },
+                [&](uint32_t t) { return s_mined[t]; }, [&](uint32_t t) { return s_cap[t]; });
+            const int64_t ni = i + CH;
+            mv[h] = ni < r1 ? __ldg(A.moves + ni) : make_int2(0, -1);
+            const bool work = active && v.valid && !v.noop;
+            if (active) {
+                A.feas[i] = v.feasible ? 1 : 0;
+                if (!v.valid) atomicOr(A.status, kStBadMove);
+                if (DELTA && !work) {
+                    float *drow = A.delta + i * (int64_t)S;
+                    for (int s2 = 0; s2 < S; s2++) drow[s2] = 0.0f;
                 }
             }
+            s_score[warp][slot] = v.valid ? 0.0f : -INFINITY;
+            s_mean[warp][slot] = 0.0f;
+            if (work) {
+                s_b1[warp][slot] = v.b1;
+                s_b2[warp][slot] = v.swap ? v.b2 : A.tp.B;
+                s_tt[warp][slot] = v.t1 | (v.t2 << 8);
+            }
+            const bool is_sh = work && !v.swap, is_sw = work && v.swap;
+            const uint32_t msh = __ballot_sync(0xffffffffu, is_sh);
+            const uint32_t msw = __ballot_sync(0xffffffffu, is_sw);
+            if (is_sh) s_lsh[warp][nsh + __popc(msh & lt_mask)] = (uint8_t)slot;
+            if (is_sw) s_lsw[warp][nsw + __popc(msw & lt_mask)] = (uint8_t)slot;
+            nsh += __popc(msh);
+            nsw += __popc(msw);
+        }
+        __syncwarp();
+        const int nbs = (nsh + TPW - 1) / TPW, nbw = (nsw + TPW - 1) / TPW, nb = nbs + nbw;
+        // producer: issue batch j of this chunk into stage (cnt0 + j) % NS
+        const uint32_t cnt0 = cnt;
+        auto issue = [&](int j) {
+            if (lane == 0) {
+                const bool sw = j >= nbs;
+                const uint8_t *list = sw ? s_lsw[warp] : s_lsh[warp];
+                const int e0 = (sw ? j - nbs : j) * TPW, nl = sw ? nsw : nsh;
+                const int st = (int)((cnt0 + (uint32_t)j) % (uint32_t)NS);
+                float *buf = stage0 + (size_t)st * TPW * 2 * R;
+                int ne = nl - e0 < TPW ? nl - e0 : TPW;
+                fence_proxy_async();
+                mbar_arrive_expect_tx(&s_bar[warp][st], (uint32_t)ne * row_bytes * (sw ? 2u : 1u));
+                for (int t = 0; t < ne; t++) {
+                    const int slot = list[e0 + t];
+                    bulk_copy_g2s(buf + (size_t)t * 2 * R, A.val + (size_t)s_b1[warp][slot] * R, row_bytes,
+                                  &s_bar[warp][st]);
+                    if (sw)
+                        bulk_copy_g2s(buf + (size_t)t * 2 * R + R, A.val + (size_t)s_b2[warp][slot] * R, row_bytes,
+                                      &s_bar[warp][st]);
+                }
+            }
+        };
+        for (int j = 0; j < nb && j < NS; j++) issue(j);
+        cnt += (uint32_t)nb;
+        bool timed_out = false;
+#pragma unroll 1
+        for (int j = 0; j < nb; j++) {
+            const int st = (int)((cnt0 + (uint32_t)j) % (uint32_t)NS);
+            if (!stage_wait(&s_bar[warp][st], (parity >> st) & 1u)) {
+                timed_out = true;
+                // drain this warp's copies in flight (bounded), then leave
+                for (int jj = j; jj < nb && jj < j + NS; jj++) {
+                    const int st2 = (int)((cnt0 + (uint32_t)jj) % (uint32_t)NS);
+                    stage_wait(&s_bar[warp][st2], (parity >> st2) & 1u);
+                }
+                break;
+            }
+            parity ^= 1u << st;
+            const bool sw = j >= nbs;
+            const uint8_t *list = sw ? s_lsw[warp] : s_lsh[warp];
+            const int e = (sw ? j - nbs : j) * TPW + tw;
+            const int nl = sw ? nsw : nsh;
+            const bool act = e < nl;
+            const int slot = act ? list[e] : 0;
+            const uint32_t tt = act ? s_tt[warp][slot] : 0;
+            const uint32_t t1 = tt & 0xffu, t2 = tt >> 8;
+            const float dd = s_dd[t1 * T1 + t2];
+            const float *row1 = stage0 + ((size_t)st * TPW + tw) * 2 * R;
+            const float *row2 = row1 + R;
+            float d[QMAX][4];
+            float mu, sd;
+            if (!sw)
+                team_eval<TEAM, QMAX, false, KAHAN, true>(A, tab, s_lut, tl, act, row1, row2, t1, t2, dd, NQ, rem,
+                                                          invS, pin_off, d, mu, sd);
+            else
+                team_eval<TEAM, QMAX, true, KAHAN, true>(A, tab, s_lut, tl, act, row1, row2, t1, t2, dd, NQ, rem,
+                                                         invS, pin_off, d, mu, sd);
+            if (act) {
+                if (tl == 0) {
+                    s_score[warp][slot] = mu - A.lambda * sd;
+                    s_mean[warp][slot] = mu;
+                }
+                if (DELTA) write_deltas<TEAM, QMAX>(A, c0 + slot, tl, NQ, rem, d);
+            }
+            __syncwarp();
+            if (j + NS < nb) issue(j + NS);
+        }
+        if (timed_out) {
+            if (lane == 0) atomicOr(A.status, kStTimeout);
+            return;
         }
         __syncwarp();
         // ---- store (coalesced) ----

@@ -6,7 +6,7 @@
 
 #include <cstdint>
 #include <cstdio>
-#include <set>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -54,6 +54,8 @@ struct TopkScratch {
 
 struct mm_model {
     int32_t B = 0, S = 0, T = 0, S_pad = 0, W = 0;
+    int32_t R = 0;        // row stride (floats) of the combined value/ore rows
+    int32_t ore_off = 0;  // float index of the first ore word in a row (4 * ceil(S/4))
     int32_t nx = 0, ny = 0, nz = 0;   // grid of the 1-5 pattern, or 0 (CSR)
     int32_t uniform_mass = 0;
     uint32_t m_uniform = 0;
@@ -62,9 +64,12 @@ struct mm_model {
     cudaStream_t stream = nullptr;
     int has_schedule = 0;
     int num_sms = 148;
+    int max_smem_optin = 227 * 1024;  // per-CTA shared-memory limit (opt-in)
     int team = 0;          // evaluator tile: lanes per move (0 = default)
     int ctas_per_sm = 0;   // evaluator grid: CTAs per SM (0 = occupancy maximum)
-    std::set<const void *> smem_attr_set;  // kernels whose shared-memory limit was raised
+    int stages = -1;       // evaluator row staging: -1 default, 0 direct loads, 1..4 bulk-copy pipeline depth
+    int prefetch = -1;     // direct loads: batches prefetched into L1 ahead (-1 default)
+    std::map<const void *, size_t> smem_attr;  // dynamic shared-memory limit raised per kernel
 
     std::vector<double> h_disc;      // [T+1] d_t in FP64, d_T = 0
     std::vector<uint64_t> h_cap;     // [T]
@@ -73,8 +78,7 @@ struct mm_model {
     // device state
     uint32_t *mass = nullptr;    // [B]
     double *grade = nullptr;     // [B][S]
-    float *val = nullptr;        // [B+1][S_pad] FP32 value rows (padding 0; row B all 0)
-    uint32_t *ore = nullptr;     // [B+1][W] ore bits (row B all 0)
+    float *val = nullptr;        // [B+1][R] rows: S FP32 values, 0 up to ore_off, W ore words, 0 (row B all 0)
     uint32_t *blk = nullptr;     // [B] packed period / lo / hi
     int32_t *pred_ptr = nullptr, *pred_idx = nullptr;  // CSR (device) when nx == 0
     int32_t *succ_ptr = nullptr, *succ_idx = nullptr;
@@ -108,7 +112,7 @@ mm_status read_sticky(mm_model *m);  // synchronises, clears and maps the sticky
 // Kernels and launchers shared between translation units.
 mm_status rebuild_tables(mm_model *m);                     // Pout/Pin from oreT
 mm_status eval_launch(mm_model *m, const mm_move *moves, int64_t n, float *score, uint8_t *feas, float *mean,
-                      float *delta, int32_t options, int team, int ctas_per_sm);
+                      float *delta, int32_t options, int team, int ctas_per_sm, int stages);
 int default_team(int S);
 mm_status topk_launch(const float *score, const uint8_t *feas, int64_t n, int32_t k, int32_t *idx,
                       float *top, int32_t *count, TopkScratch &scr, int num_sms, cudaStream_t st);

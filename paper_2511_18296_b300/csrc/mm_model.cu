@@ -1,9 +1,12 @@
 // Model store, schedule state and the apply-move kernel.
 //
 // Device layout (per model):
-//   val   FP32 [B+1][S_pad] per-block value rows, scenario fastest, 32-byte rows;
+//   val   [B+1][R]          one combined row per block, R = roundup(4*ceil(S/4) + W, 8)
+//                           floats (32-byte multiple): S FP32 values (scenario
+//                           fastest), zeros up to ore_off = 4*ceil(S/4), then
+//                           W = ceil(S/32) ore words (bit s%32 of word s/32), zeros;
+//                           a moved block is one contiguous gather (one bulk copy);
 //                           row B is all zeros (the stand-in partner of a shift)
-//   ore   u32  [B+1][W]     ore bits, W = ceil(S/32); row B zero
 //   blk   u32  [B]          packed period | lo << 8 | hi << 16
 //   grade FP64 [B][S]       kept for the FP64 metal accumulators
 //   minedT i64 [T+1], oreT i64 [T+1][S], metal FP64 [T][S], npv FP64 [S]
@@ -71,28 +74,29 @@ static Topo topo_of(const mm_model *m) {
 // scenarios.  FP64 with explicit round-to-nearest operations in the order
 // ((g*price)*recovery) > proc_cost; value = m*(rev - pc) - m*mc or -(m*mc).
 __global__ void k_classify(const double *__restrict__ grade, const uint32_t *__restrict__ mass, int32_t B, int32_t S,
-                           int32_t S_pad, int32_t W, double price, double recovery, double pc, double mc,
-                           float *__restrict__ val, uint32_t *__restrict__ ore) {
+                           int32_t R, int32_t ore_off, int32_t W, double price, double recovery, double pc,
+                           double mc, float *__restrict__ val) {
     int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (gid >= (int64_t)B * W) return;
     int32_t b = (int32_t)(gid / W), w = (int32_t)(gid % W);
     double m = (double)mass[b];
+    float *row = val + (int64_t)b * R;
     uint32_t bits = 0;
     for (int j = 0; j < 32; j++) {
         int s = w * 32 + j;
-        if (s >= S_pad) break;
-        float v = 0.0f;
-        if (s < S) {
-            double g = grade[(int64_t)b * S + s];
-            double rev = __dmul_rn(__dmul_rn(g, price), recovery);
-            bool o = rev > pc;
-            double vv = o ? __dsub_rn(__dmul_rn(m, __dsub_rn(rev, pc)), __dmul_rn(m, mc)) : -__dmul_rn(m, mc);
-            v = __double2float_rn(vv);
-            bits |= (o ? 1u : 0u) << j;
-        }
-        val[(int64_t)b * S_pad + s] = v;
+        if (s >= S) break;
+        double g = grade[(int64_t)b * S + s];
+        double rev = __dmul_rn(__dmul_rn(g, price), recovery);
+        bool o = rev > pc;
+        double vv = o ? __dsub_rn(__dmul_rn(m, __dsub_rn(rev, pc)), __dmul_rn(m, mc)) : -__dmul_rn(m, mc);
+        row[s] = __double2float_rn(vv);
+        bits |= (o ? 1u : 0u) << j;
     }
-    ore[gid] = bits;
+    reinterpret_cast<uint32_t *>(row + ore_off)[w] = bits;
+}
+
+__device__ __forceinline__ uint32_t ore_bit(const float *val, int32_t R, int32_t ore_off, int32_t b, int s) {
+    return (reinterpret_cast<const uint32_t *>(val + (int64_t)b * R + ore_off)[s >> 5] >> (s & 31)) & 1u;
 }
 
 // Packed period/lo/hi word of every block.
@@ -114,8 +118,8 @@ __global__ void k_base_arcs(int32_t B, const uint32_t *__restrict__ blk, uint32_
 // minedT[t], oreT[t][s], metal[t][s].  Grid (T, ceil(S/32)); block of 32 x 8:
 // lanes over scenarios, 8 slices over the period's blocks, combined in slice order.
 __global__ void k_accum(const int32_t *__restrict__ order, const int32_t *__restrict__ porder,
-                        const uint32_t *__restrict__ mass, const uint32_t *__restrict__ ore,
-                        const double *__restrict__ grade, int32_t S, int32_t W, int32_t T,
+                        const uint32_t *__restrict__ mass, const float *__restrict__ val, int32_t R, int32_t ore_off,
+                        const double *__restrict__ grade, int32_t S, int32_t T,
                         int64_t *__restrict__ minedT, int64_t *__restrict__ oreT, double *__restrict__ metal) {
     int t = blockIdx.x;
     int s = blockIdx.y * 32 + threadIdx.x;
@@ -130,7 +134,7 @@ __global__ void k_accum(const int32_t *__restrict__ order, const int32_t *__rest
         int32_t b = order[k];
         uint32_t mb = mass[b];
         if (blockIdx.y == 0 && threadIdx.x == 0) mt += mb;  // one lane per slice counts mass
-        if (s < S && ((ore[(int64_t)b * W + (s >> 5)] >> (s & 31)) & 1u)) {
+        if (s < S && ore_bit(val, R, ore_off, b, s)) {
             o += mb;
             g = __dadd_rn(g, __dmul_rn((double)mb, grade[(int64_t)b * S + s]));
         }
@@ -252,11 +256,11 @@ __device__ void npv_stats(const double *npv, int32_t S, double *mean, double *st
 
 struct ApplyArgs {
     Topo tp;
-    int32_t S, S_pad, W, T;
+    int32_t S, S_pad, W, T, R, ore_off;
     uint32_t m_uniform;
     int32_t uniform;
     const uint32_t *mass;
-    const uint32_t *ore;
+    const float *val;
     const double *grade;
     uint32_t *blk;
     int64_t *minedT;
@@ -355,13 +359,13 @@ __global__ void k_apply(ApplyArgs A, int2 mv_val, const int2 *moves, int64_t n_m
         }
         // per scenario: tonnage, metal, contributions, NPV, table rows
         for (int s = threadIdx.x; s < A.S; s += blockDim.x) {
-            uint32_t o1 = (A.ore[(int64_t)v.b1 * A.W + (s >> 5)] >> (s & 31)) & 1u;
+            uint32_t o1 = ore_bit(A.val, A.R, A.ore_off, v.b1, s);
             int64_t om1 = o1 ? (int64_t)v.m1 : 0;
             double g1 = o1 ? __dmul_rn((double)v.m1, A.grade[(int64_t)v.b1 * A.S + s]) : 0.0;
             int64_t om2 = 0;
             double g2 = 0.0;
             if (v.swap) {
-                uint32_t o2 = (A.ore[(int64_t)v.b2 * A.W + (s >> 5)] >> (s & 31)) & 1u;
+                uint32_t o2 = ore_bit(A.val, A.R, A.ore_off, v.b2, s);
                 om2 = o2 ? (int64_t)v.m2 : 0;
                 g2 = o2 ? __dmul_rn((double)v.m2, A.grade[(int64_t)v.b2 * A.S + s]) : 0.0;
             }
@@ -426,9 +430,9 @@ mm_status rebuild_tables(mm_model *m) {
 static ApplyArgs apply_args(mm_model *m) {
     ApplyArgs A;
     A.tp = topo_of(m);
-    A.S = m->S; A.S_pad = m->S_pad; A.W = m->W; A.T = m->T;
+    A.S = m->S; A.S_pad = m->S_pad; A.W = m->W; A.T = m->T; A.R = m->R; A.ore_off = m->ore_off;
     A.m_uniform = m->m_uniform; A.uniform = m->uniform_mass;
-    A.mass = m->mass; A.ore = m->ore; A.grade = m->grade; A.blk = m->blk;
+    A.mass = m->mass; A.val = m->val; A.grade = m->grade; A.blk = m->blk;
     A.minedT = m->minedT; A.oreT = m->oreT; A.metal = m->metal; A.npv = m->npv; A.contrib = m->contrib;
     A.tab = m->tab;
     A.disc = m->disc; A.cap = m->cap; A.target = m->target;
@@ -469,7 +473,7 @@ const char *mm_last_error(void) { return g_err; }
 void mm_model_destroy(mm_model *m) {
     if (!m) return;
     if (m->stream) cudaStreamSynchronize(m->stream);
-    cudaFree(m->mass); cudaFree(m->grade); cudaFree(m->val); cudaFree(m->ore); cudaFree(m->blk);
+    cudaFree(m->mass); cudaFree(m->grade); cudaFree(m->val); cudaFree(m->blk);
     cudaFree(m->pred_ptr); cudaFree(m->pred_idx); cudaFree(m->succ_ptr); cudaFree(m->succ_idx);
     cudaFree(m->order); cudaFree(m->porder);
     cudaFree(m->minedT); cudaFree(m->oreT); cudaFree(m->metal); cudaFree(m->npv); cudaFree(m->contrib);
@@ -541,6 +545,8 @@ mm_status mm_model_create(const mm_model_desc *d, mm_model **out) {
     m->B = B; m->S = S; m->T = T;
     m->S_pad = (S + 7) / 8 * 8;
     m->W = (S + 31) / 32;
+    m->ore_off = 4 * ((S + 3) / 4);
+    m->R = (m->ore_off + m->W + 7) / 8 * 8;
     m->nx = grid ? d->nx : 0; m->ny = grid ? d->ny : 0; m->nz = grid ? d->nz : 0;
     m->price = d->price; m->recovery = d->recovery; m->mining_cost = d->mining_cost; m->proc_cost = d->proc_cost;
     m->shortfall_pen = d->shortfall_pen; m->excess_pen = d->excess_pen; m->discount_rate = d->discount_rate;
@@ -553,6 +559,7 @@ mm_status mm_model_create(const mm_model_desc *d, mm_model **out) {
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&m->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&m->max_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
 
     m->h_disc.resize(T + 1);
     for (int t = 0; t < T; t++) m->h_disc[t] = std::pow(1.0 + d->discount_rate, -(double)t);
@@ -565,8 +572,7 @@ mm_status mm_model_create(const mm_model_desc *d, mm_model **out) {
     if (st == MM_OK) st = dalloc(&m->ptr, (size_t)(n), "allocate " #ptr)
     ALLOC(mass, B);
     ALLOC(grade, (int64_t)B * S);
-    ALLOC(val, (int64_t)(B + 1) * m->S_pad);
-    ALLOC(ore, (int64_t)(B + 1) * m->W);
+    ALLOC(val, (int64_t)(B + 1) * m->R);
     ALLOC(blk, B);
     ALLOC(order, B);
     ALLOC(porder, T + 2);
@@ -621,8 +627,7 @@ mm_status mm_model_create(const mm_model_desc *d, mm_model **out) {
     TRY(cudaMemcpyAsync(m->disc, m->h_disc.data(), sizeof(double) * (T + 1), cudaMemcpyHostToDevice, s), "copy disc");
     TRY(cudaMemcpyAsync(m->ddt, ddt.data(), sizeof(float) * ddt.size(), cudaMemcpyHostToDevice, s), "copy ddt");
     TRY(cudaMemsetAsync(m->status, 0, sizeof(uint32_t), s), "clear status");
-    TRY(cudaMemsetAsync(m->val + (size_t)B * m->S_pad, 0, sizeof(float) * m->S_pad, s), "clear zero row");
-    TRY(cudaMemsetAsync(m->ore + (size_t)B * m->W, 0, sizeof(uint32_t) * m->W, s), "clear zero row");
+    TRY(cudaMemsetAsync(m->val, 0, sizeof(float) * (size_t)(B + 1) * m->R, s), "clear rows");
     TRY(cudaMemsetAsync(m->oreT, 0, sizeof(int64_t) * (size_t)(T + 1) * S, s), "clear oreT");
     TRY(cudaMemsetAsync(m->minedT, 0, sizeof(int64_t) * (T + 1), s), "clear minedT");
     TRY(cudaMemsetAsync(m->apply_res, 0, sizeof(ApplyResult), s), "clear apply result");
@@ -636,9 +641,9 @@ mm_status mm_model_create(const mm_model_desc *d, mm_model **out) {
             "copy CSR");
     }
     int64_t nthreads = (int64_t)B * m->W;
-    k_classify<<<(unsigned)((nthreads + 255) / 256), 256, 0, s>>>(m->grade, m->mass, B, S, m->S_pad, m->W, m->price,
-                                                                  m->recovery, m->proc_cost, m->mining_cost, m->val,
-                                                                  m->ore);
+    k_classify<<<(unsigned)((nthreads + 255) / 256), 256, 0, s>>>(m->grade, m->mass, B, S, m->R, m->ore_off, m->W,
+                                                                  m->price, m->recovery, m->proc_cost, m->mining_cost,
+                                                                  m->val);
     mm_status ls = check_launch("k_classify");
     if (ls != MM_OK) return fail(ls);
     TRY(cudaStreamSynchronize(s), "synchronize after create");
@@ -658,7 +663,7 @@ mm_status mm_model_info(const mm_model *m, int32_t *B, int32_t *S, int32_t *T, i
     if (B) *B = m->B;
     if (S) *S = m->S;
     if (T) *T = m->T;
-    if (s_pad) *s_pad = m->S_pad;
+    if (s_pad) *s_pad = m->R;
     return MM_OK;
 }
 
@@ -696,8 +701,8 @@ mm_status mm_schedule_set(mm_model *m, const uint8_t *period, int *base_feasible
     TRY(cudaMemsetAsync(m->oreT, 0, sizeof(int64_t) * (size_t)(T + 1) * S, s), "clear oreT");
     TRY(cudaMemsetAsync(m->minedT, 0, sizeof(int64_t) * (T + 1), s), "clear minedT");
     dim3 grid(T, (S + 31) / 32), block(32, 8);
-    k_accum<<<grid, block, 0, s>>>(m->order, m->porder, m->mass, m->ore, m->grade, S, m->W, T, m->minedT, m->oreT,
-                                   m->metal);
+    k_accum<<<grid, block, 0, s>>>(m->order, m->porder, m->mass, m->val, m->R, m->ore_off, m->grade, S, T, m->minedT,
+                                   m->oreT, m->metal);
     if ((st = check_launch("k_accum")) != MM_OK) return done(st);
     if ((st = rebuild_tables(m)) != MM_OK) return done(st);
     k_npv<<<(S + 127) / 128, 128, 0, s>>>(S, T, m->disc, m->metal, m->oreT, m->minedT, m->target,
@@ -794,15 +799,15 @@ mm_status mm_npv(mm_model *m, double *npv_host, double *mean, double *sd) {
 
 mm_status mm_get_ore(mm_model *m, uint32_t *ore_host) {
     if (!m || !ore_host) return set_error(MM_ERR_INVALID_ARG, "NULL argument");
-    MM_CUDA_TRY(cudaMemcpyAsync(ore_host, m->ore, sizeof(uint32_t) * (size_t)m->B * m->W, cudaMemcpyDeviceToHost,
-                                m->stream), "read ore");
+    MM_CUDA_TRY(cudaMemcpy2DAsync(ore_host, sizeof(uint32_t) * m->W, m->val + m->ore_off, sizeof(float) * m->R,
+                                  sizeof(uint32_t) * m->W, m->B, cudaMemcpyDeviceToHost, m->stream), "read ore");
     MM_CUDA_TRY(cudaStreamSynchronize(m->stream), "synchronize");
     return MM_OK;
 }
 
 mm_status mm_get_values(mm_model *m, float *value_host) {
     if (!m || !value_host) return set_error(MM_ERR_INVALID_ARG, "NULL argument");
-    MM_CUDA_TRY(cudaMemcpy2DAsync(value_host, sizeof(float) * m->S, m->val, sizeof(float) * m->S_pad, sizeof(float) * m->S,
+    MM_CUDA_TRY(cudaMemcpy2DAsync(value_host, sizeof(float) * m->S, m->val, sizeof(float) * m->R, sizeof(float) * m->S,
                                   m->B, cudaMemcpyDeviceToHost, m->stream), "read values");
     MM_CUDA_TRY(cudaStreamSynchronize(m->stream), "synchronize");
     return MM_OK;

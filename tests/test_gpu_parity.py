@@ -112,13 +112,15 @@ def test_tiny_exhaustive(S, T):
     mv = all_moves(p.B, T)
     bad = np.array([[p.B, -1], [0, -(T + 2)], [-1, 0], [0, p.B]], np.int32)
     mv = np.concatenate([mv, bad])
-    for kahan in (False, True):
-        g = run_eval(m, mv, kahan=kahan)
-        ref = om.eval_bruteforce(p.x0, mv)
-        inc = om.eval_incremental(p.x0, mv, want_floor_s=True)
-        check_against(g, ref, inc, f"tiny S={S} T={T} kahan={kahan}")
-        noop = inc["floor"] == 0
-        assert np.all(g["score"][noop & (ref["score"] == 0)] == 0.0)
+    ref = om.eval_bruteforce(p.x0, mv)
+    inc = om.eval_incremental(p.x0, mv, want_floor_s=True)
+    for stages in (0, 2):  # direct loads with L1 prefetch; bulk copies into shared memory
+        m.set_tile(0, 0, stages, -1)
+        for kahan in (False, True):
+            g = run_eval(m, mv, kahan=kahan)
+            check_against(g, ref, inc, f"tiny S={S} T={T} stages={stages} kahan={kahan}")
+            noop = inc["floor"] == 0
+            assert np.all(g["score"][noop & (ref["score"] == 0)] == 0.0)
     import paper_2511_18296_b300 as mm
     with pytest.raises(mm.MMError) as e:
         m.npv()  # the sticky bad-move status surfaces at the next synchronising call
@@ -206,10 +208,10 @@ def test_team_sizes_agree():
     inc = om.eval_incremental(p.x0, p.moves)
     mv = torch.as_tensor(p.moves, device="cuda")
     for team in (4, 8, 16, 32):
-        if not hasattr(mm.lib(), "mm_set_tile"):
-            pytest.skip("tile selection not exported")
-        assert mm.lib().mm_set_tile(m.h, team, 0) == 0
-        s, f, mean = m.eval_moves(mv)
-        torch.cuda.synchronize()
-        assert np.array_equal(f.cpu().numpy(), inc["flag"])
-        assert_close_floor(s.cpu().numpy(), inc["score"], inc["floor"], what=f"team {team}")
+        for stages, pf in ((0, 0), (0, 1), (0, 3), (1, 0), (2, 0), (3, 0), (4, 0)):
+            m.set_tile(team, 0, stages, pf)
+            s, f, mean = m.eval_moves(mv)
+            torch.cuda.synchronize()
+            assert np.array_equal(f.cpu().numpy(), inc["flag"])
+            assert_close_floor(s.cpu().numpy(), inc["score"], inc["floor"], what=f"team {team} stages {stages}")
+    m.set_tile(0, 0, -1, -1)
