@@ -165,6 +165,28 @@ mm_status mm_eval_moves_ex(mm_model *m, const mm_move *moves_dev, int64_t n, flo
 mm_status mm_topk(mm_model *m, const float *score_dev, const uint8_t *feasible_dev, int64_t n,
                   int32_t k, int32_t *idx_dev, float *topscore_dev, int32_t *count_dev);
 
+/* mm_topk for callers that must not allocate device memory, such as code
+ * that runs while a CUDA stream is being captured into a graph (cudaMalloc may
+ * not be called then), code that owns a fixed memory budget or pool and must
+ * not grow it, or a loop that must never block the device the way cudaMalloc
+ * and cudaFree can.  The paper has no counterpart: it is an interface
+ * convenience of this library.  It needs no model: it selects, from
+ * score_dev[n] / feasible_dev[n], the k feasible moves with the largest score
+ * exactly as mm_topk does (same outputs, ties to the lower index) and enqueues
+ * the work on cuda_stream (NULL = default stream).
+ * Scratch: one fixed device array inside this library (about 8 MiB, held on
+ * every GPU that loads the library until the process exits); n must be at
+ * most 1,048,576 (else MM_ERR_INVALID_ARG) and 1 <= k <= 1024.  No call
+ * allocates: each clears the parts of the array that must start at zero with
+ * an asynchronous memset on cuda_stream.  The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before capturing a stream into a graph.  All calls
+ * share the one array, so two calls that may run at the same time on the GPU
+ * (different streams, or the same device from two threads) race: serialise
+ * them.  Asynchronous. */
+mm_status mm_topk_noalloc(const float *score_dev, const uint8_t *feasible_dev, int64_t n, int32_t k,
+                          int32_t *idx_dev, float *topscore_dev, int32_t *count_dev, void *cuda_stream);
+
 /* Apply one move (Algorithm 4: assign S[b*] <- t*) if its feasibility flag is
  * 1: updates the schedule, the integer tonnages, the FP64 metal accumulators,
  * the per-scenario NPV and the evaluator's tables for the affected periods.

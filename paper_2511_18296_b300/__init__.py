@@ -72,6 +72,7 @@ SIGNATURES = [
     ("mm_eval_moves_ex", C.c_int, [P, P, I64, P, P, P, P, I32]),
     ("mm_set_tile", C.c_int, [P, I32, I32, I32, I32]),
     ("mm_topk", C.c_int, [P, P, P, I64, I32, P, P, P]),
+    ("mm_topk_noalloc", C.c_int, [P, P, I64, I32, P, P, P, P]),
     ("mm_apply_move", C.c_int, [P, MMMove, P, P]),
     ("mm_apply_best", C.c_int, [P, P, I64, P, P]),
     ("mm_last_apply", C.c_int, [P, P, P, P]),
@@ -119,6 +120,14 @@ def _stream_handle(stream) -> int:
     if stream is None:
         stream = torch.cuda.current_stream()
     return int(stream.cuda_stream)
+
+
+def topk_noalloc(score, feas, k: int, idx, top, count, stream=None):
+    """mm_topk_noalloc: top-k without any device allocation (caller passes
+    every output buffer; the scratch is a fixed array inside the library)."""
+    _check(lib().mm_topk_noalloc(_ptr(score), _ptr(feas), int(score.shape[0]), int(k), _ptr(idx), _ptr(top),
+                                 _ptr(count), _stream_handle(stream)))
+    return idx, top, count
 
 
 class Model:

@@ -14,6 +14,8 @@
 //                  on the remaining 52 bits, sorts the k keys (bitonic, in
 //                  shared memory) and writes indices, scores and the count.
 // Integer keys make the result independent of thread scheduling.
+#include <mutex>
+
 #include "mm_internal.cuh"
 
 namespace mm {
@@ -313,4 +315,72 @@ extern "C" mm_status mm_topk(mm_model *m, const float *score, const uint8_t *fea
     mm_status st = topk_scratch_reserve(m->topk, n);
     if (st != MM_OK) return st;
     return topk_launch(score, feas, n, k, idx, top, count, m->topk, m->num_sms, m->stream);
+}
+
+// ---------------------------------------------------------------------------
+// Caller-free variant.  Its scratch is one file-scope device array, so a call
+// allocates nothing: the array exists on every GPU that loads this library
+// until the process exits.  Layout inside the array (byte offsets):
+//   [0, 8 MiB)            keys inside the cut-off bin (kNoAllocMaxN x 8 bytes)
+//   [8 MiB, +16 KiB)      coarse histogram
+//   [+16 KiB, +24 KiB)    keys above the cut-off bin
+//   [+24 KiB, +24.25 KiB) counters and tickets
+namespace mm {
+
+constexpr int64_t kNoAllocMaxN = int64_t(1) << 20;  // largest batch mm_topk_noalloc accepts
+constexpr size_t kNaMaybeOff = 0;
+constexpr size_t kNaHistOff = kNaMaybeOff + sizeof(uint64_t) * (size_t)kNoAllocMaxN;
+constexpr size_t kNaSureOff = kNaHistOff + sizeof(uint32_t) * kHistBins;
+constexpr size_t kNaCtlOff = kNaSureOff + sizeof(uint64_t) * kTopkMax;
+constexpr size_t kNaBytes = kNaCtlOff + 256;
+
+static __device__ __align__(256) unsigned char g_topk_noalloc_scratch[kNaBytes];
+
+constexpr int kNaMaxDevices = 64;
+static std::mutex g_na_mu;
+static unsigned char *g_na_base[kNaMaxDevices];  // device address of the array, per device
+static int g_na_sms[kNaMaxDevices];
+
+}  // namespace mm
+
+extern "C" mm_status mm_topk_noalloc(const float *score, const uint8_t *feas, int64_t n, int32_t k, int32_t *idx,
+                                     float *top, int32_t *count, void *cuda_stream) {
+    if (n < 0 || n > kNoAllocMaxN)
+        return set_error(MM_ERR_INVALID_ARG, "mm_topk_noalloc: n = %lld is outside 0..%lld (the fixed scratch size)",
+                         (long long)n, (long long)kNoAllocMaxN);
+    if (k < 1 || k > kTopkMax) return set_error(MM_ERR_INVALID_ARG, "k = %d outside 1..%d", k, kTopkMax);
+    if (!count || (n > 0 && (!score || !feas || !idx || !top))) return set_error(MM_ERR_INVALID_ARG, "NULL pointer");
+    int dev = 0;
+    MM_CUDA_TRY(cudaGetDevice(&dev), "cudaGetDevice");
+    if (dev < 0 || dev >= kNaMaxDevices) return set_error(MM_ERR_INVALID_ARG, "device %d not supported", dev);
+    unsigned char *base;
+    int sms;
+    {
+        // once per device, with that device current: the host-side symbol is not
+        // a device address, so ask the runtime for the array's device address
+        std::lock_guard<std::mutex> lock(g_na_mu);
+        if (!g_na_base[dev]) {
+            void *p = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&p, g_topk_noalloc_scratch);
+            if (e != cudaSuccess) return cuda_status(e, "cudaGetSymbolAddress(top-k scratch)");
+            int nsm = 0;
+            e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+            if (e != cudaSuccess) return cuda_status(e, "cudaDeviceGetAttribute");
+            g_na_sms[dev] = nsm;
+            g_na_base[dev] = static_cast<unsigned char *>(p);
+        }
+        base = g_na_base[dev];
+        sms = g_na_sms[dev];
+    }
+    TopkScratch scr;
+    scr.maybe = reinterpret_cast<uint64_t *>(base + kNaMaybeOff);
+    scr.hist = reinterpret_cast<uint32_t *>(base + kNaHistOff);
+    scr.sure = reinterpret_cast<uint64_t *>(base + kNaSureOff);
+    scr.ctl = reinterpret_cast<uint32_t *>(base + kNaCtlOff);
+    scr.cap_maybe = kNoAllocMaxN;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    // the array keeps the previous call's contents: the histogram and the
+    // counters must start at zero
+    MM_CUDA_TRY(cudaMemsetAsync(scr.hist, 0, kNaCtlOff + 256 - kNaHistOff, st), "clear top-k scratch");
+    return topk_launch(score, feas, n, k, idx, top, count, scr, sms, st);
 }
