@@ -30,6 +30,7 @@ STATUS = {0: "MM_OK", 1: "MM_ERR_INVALID_ARG", 2: "MM_ERR_CUDA", 3: "MM_ERR_OOM"
           5: "MM_ERR_INFEASIBLE", 6: "MM_ERR_BAD_MOVE", 7: "MM_ERR_TIMEOUT", 8: "MM_ERR_STATE"}
 MM_EVAL_PLAIN = 0
 MM_EVAL_KAHAN = 1
+MM_EVAL_GENERIC = 2
 TOPK_MAX = 1024
 
 
@@ -202,7 +203,7 @@ class Model:
 
     # -- evaluation -----------------------------------------------------
     def eval_moves(self, moves, score=None, feas=None, mean=None, want_mean=True, delta=None,
-                   kahan: bool = False):
+                   kahan: bool = False, generic: bool = False):
         """moves: int32 CUDA tensor [n, 2].  Returns (score f32, feasible u8, mean f32 or None)."""
         import torch
         assert moves.is_cuda and moves.dtype == torch.int32 and moves.is_contiguous()
@@ -215,18 +216,19 @@ class Model:
         if mean is None and want_mean:
             mean = torch.empty(n, dtype=torch.float32, device=dev)
         L = lib()
-        if delta is None and not kahan:
+        opts = (MM_EVAL_KAHAN if kahan else MM_EVAL_PLAIN) | (MM_EVAL_GENERIC if generic else 0)
+        if delta is None and opts == 0:
             _check(L.mm_eval_moves(self.h, _ptr(moves), n, _ptr(score), _ptr(feas), _ptr(mean)))
         else:
             _check(L.mm_eval_moves_ex(self.h, _ptr(moves), n, _ptr(score), _ptr(feas), _ptr(mean), _ptr(delta),
-                                      MM_EVAL_KAHAN if kahan else MM_EVAL_PLAIN))
+                                      opts))
         return score, feas, mean
 
-    def eval_deltas(self, moves, kahan: bool = False):
+    def eval_deltas(self, moves, kahan: bool = False, generic: bool = False):
         """Per-scenario deltas [n, S] as well (parity/debug path)."""
         import torch
         delta = torch.empty((moves.shape[0], self.S), dtype=torch.float32, device=moves.device)
-        score, feas, mean = self.eval_moves(moves, delta=delta, kahan=kahan)
+        score, feas, mean = self.eval_moves(moves, delta=delta, kahan=kahan, generic=generic)
         return score, feas, mean, delta
 
     def topk(self, score, feas, k: int, idx=None, top=None, count=None):

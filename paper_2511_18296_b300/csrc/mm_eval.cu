@@ -31,6 +31,8 @@ namespace mm {
 using EvalFn = void (*)(EvalArgs);
 EvalFn pick_tiled_plain(int team, int qmax, bool delta, bool tsm, bool tma);
 EvalFn pick_tiled_kahan(int team, int qmax, bool delta, bool tsm, bool tma);
+EvalFn pick_fast_plain(int team, int kf, bool tail, bool delta, bool tsm);
+EvalFn pick_fast_kahan(int team, int kf, bool tail, bool delta, bool tsm);
 
 // General evaluator (unequal block masses): one warp per move, one lane per
 // scenario, penalty change from the exact integer ore tonnages:
@@ -187,8 +189,18 @@ mm_status eval_launch(mm_model *m, const mm_move *moves, int64_t n, float *score
     }
     const bool use_tma = stages > 0;
     A.nstage = stages;
-    EvalFn fn = kahan ? pick_tiled_kahan(team, qmax, want_delta, tsm, use_tma)
-                      : pick_tiled_plain(team, qmax, want_delta, tsm, use_tma);
+    EvalFn fn = nullptr;
+    if (!use_tma && m->S % 4 == 0 && !(options & MM_EVAL_GENERIC)) {
+        // fast form: floor(NQ / team) full quad iterations known at compile time
+        const int kf = nq / team;
+        const bool tail = nq % team != 0;
+        if (kf >= 1 && kf <= 4)
+            fn = kahan ? pick_fast_kahan(team, kf, tail, want_delta, tsm)
+                       : pick_fast_plain(team, kf, tail, want_delta, tsm);
+    }
+    if (!fn)
+        fn = kahan ? pick_tiled_kahan(team, qmax, want_delta, tsm, use_tma)
+                   : pick_tiled_plain(team, qmax, want_delta, tsm, use_tma);
     if (!fn) return set_error(MM_ERR_INVALID_ARG, "no evaluator for team %d with %d quads per lane", team, qpl);
     // the 48 KB default covers static + dynamic shared memory (~12 KB static here)
     if (smem + 16 * 1024 > 48 * 1024 && m->smem_attr[(const void *)fn] < smem) {
@@ -263,7 +275,8 @@ mm_status mm_eval_moves_ex(mm_model *m, const mm_move *moves, int64_t n, float *
                            float *delta, int32_t options) {
     mm_status st = eval_check(m, moves, n, score, feas);
     if (st != MM_OK || n == 0) return st;
-    if (options & ~MM_EVAL_KAHAN) return set_error(MM_ERR_INVALID_ARG, "unknown option bits 0x%x", options);
+    if (options & ~(MM_EVAL_KAHAN | MM_EVAL_GENERIC))
+        return set_error(MM_ERR_INVALID_ARG, "unknown option bits 0x%x", options);
     return eval_launch(m, moves, n, score, feas, mean, delta, options, m->team, m->ctas_per_sm, m->stages);
 }
 

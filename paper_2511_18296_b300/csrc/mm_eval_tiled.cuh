@@ -201,6 +201,108 @@ __device__ __forceinline__ void team_eval(const EvalArgs &A, const float *tab, c
     sd = sqrtf(var * invS);
 }
 
+// Fast form of team_eval for S % 4 == 0: the team runs KF = floor(NQ / TEAM)
+// full quad iterations, fixed at compile time (every lane of every team owns
+// a real quad, offsets are compile-time immediates from per-lane bases, no
+// masking), then, if TAIL, one iteration in which only the first
+// NQ - KF * TEAM lanes hold a quad.  d[KF] holds the tail quad.
+template <int TEAM, int KF, bool TAIL, bool SWAP, bool KAHAN>
+__device__ __forceinline__ void team_eval_fast(const EvalArgs &A, const float *tab, const float4 *lut, int tl,
+                                               const float *row1, const float *row2, uint32_t t1, uint32_t t2,
+                                               float dd, int ntail, float invS, size_t pin_off,
+                                               float (&d)[KF + 1][4], float &mu, float &sd) {
+    const int S_pad = A.S_pad, ore_off = A.ore_off;
+    const float4 *r1 = reinterpret_cast<const float4 *>(row1) + tl;
+    const float4 *r2 = reinterpret_cast<const float4 *>(row2) + tl;
+    const uint32_t *w1 = reinterpret_cast<const uint32_t *>(row1 + ore_off);
+    const uint32_t *w2 = reinterpret_cast<const uint32_t *>(row2 + ore_off);
+    const float4 *po1 = reinterpret_cast<const float4 *>(tab + (size_t)t1 * S_pad) + tl;
+    const float4 *po2 = reinterpret_cast<const float4 *>(tab + (size_t)t2 * S_pad) + tl;
+    const float4 *pi1 = reinterpret_cast<const float4 *>(tab + pin_off + (size_t)t1 * S_pad) + tl;
+    const float4 *pi2 = reinterpret_cast<const float4 *>(tab + pin_off + (size_t)t2 * S_pad) + tl;
+    float sum = 0.0f, csum = 0.0f;
+    auto quad = [&](int k, float (&x)[4]) {
+        const int q = tl + k * TEAM;
+        const int wi = q >> 3;
+        const uint32_t sh = (uint32_t)(q & 7) * 4u;
+        const float4 a = __ldg(r1 + k * TEAM);
+        const float4 pa = po1[k * TEAM];
+        const float4 pb = pi2[k * TEAM];
+        if (SWAP) {
+            const float4 b = __ldg(r2 + k * TEAM);
+            const uint32_t n1 = (__ldg(w1 + wi) >> sh) & 0xfu;
+            const uint32_t n2 = (__ldg(w2 + wi) >> sh) & 0xfu;
+            const float4 m1 = lut[n1 & ~n2];
+            const float4 m2 = lut[n2 & ~n1];
+            const float4 pc = pi1[k * TEAM];
+            const float4 pd = po2[k * TEAM];
+            x[0] = fmaf(a.x - b.x, dd, fmaf(m2.x, pc.x + pd.x, m1.x * (pa.x + pb.x)));
+            x[1] = fmaf(a.y - b.y, dd, fmaf(m2.y, pc.y + pd.y, m1.y * (pa.y + pb.y)));
+            x[2] = fmaf(a.z - b.z, dd, fmaf(m2.z, pc.z + pd.z, m1.z * (pa.z + pb.z)));
+            x[3] = fmaf(a.w - b.w, dd, fmaf(m2.w, pc.w + pd.w, m1.w * (pa.w + pb.w)));
+        } else {
+            const float4 m1 = lut[(__ldg(w1 + wi) >> sh) & 0xfu];
+            x[0] = fmaf(a.x, dd, m1.x * (pa.x + pb.x));
+            x[1] = fmaf(a.y, dd, m1.y * (pa.y + pb.y));
+            x[2] = fmaf(a.z, dd, m1.z * (pa.z + pb.z));
+            x[3] = fmaf(a.w, dd, m1.w * (pa.w + pb.w));
+        }
+    };
+    auto acc = [&](const float (&x)[4]) {
+        if (KAHAN) {
+#pragma unroll
+            for (int j = 0; j < 4; j++) comp_add(sum, csum, x[j]);
+        } else {
+            sum += (x[0] + x[1]) + (x[2] + x[3]);
+        }
+    };
+#pragma unroll
+    for (int k = 0; k < KF; k++) {
+        quad(k, d[k]);
+        acc(d[k]);
+    }
+#pragma unroll
+    for (int j = 0; j < 4; j++) d[KF][j] = 0.0f;
+    if (TAIL && tl < ntail) {
+        quad(KF, d[KF]);
+        acc(d[KF]);
+    }
+    if (KAHAN) {
+        team_sum_comp<TEAM>(sum, csum);
+        mu = (sum + csum) * invS;
+    } else {
+        mu = team_sum<TEAM>(sum) * invS;
+    }
+    float var = 0.0f, cvar = 0.0f;
+    auto vacc = [&](const float (&x)[4]) {
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const float dv = x[j] - mu;
+            if (KAHAN) comp_add(var, cvar, dv * dv);
+            else var = fmaf(dv, dv, var);
+        }
+    };
+#pragma unroll
+    for (int k = 0; k < KF; k++) vacc(d[k]);
+    if (TAIL && tl < ntail) vacc(d[KF]);
+    if (KAHAN) {
+        team_sum_comp<TEAM>(var, cvar);
+        var = var + cvar;
+    } else {
+        var = team_sum<TEAM>(var);
+    }
+    sd = sqrtf(var * invS);
+}
+
+template <int TEAM, int KF>
+__device__ __forceinline__ void write_deltas_fast(const EvalArgs &A, int64_t i, int tl, int ntail,
+                                                  const float (&d)[KF + 1][4]) {
+    float4 *drow = reinterpret_cast<float4 *>(A.delta + i * (int64_t)A.S);
+#pragma unroll
+    for (int k = 0; k < KF; k++) drow[tl + k * TEAM] = make_float4(d[k][0], d[k][1], d[k][2], d[k][3]);
+    if (tl < ntail) drow[tl + KF * TEAM] = make_float4(d[KF][0], d[KF][1], d[KF][2], d[KF][3]);
+}
+
 // Per-scenario deltas of one move to delta[i][0..S).
 template <int TEAM, int QMAX>
 __device__ __forceinline__ void write_deltas(const EvalArgs &A, int64_t i, int tl, int NQ, int rem,
@@ -232,7 +334,7 @@ __device__ __forceinline__ void prefetch_row(const float *row, uint32_t row_byte
         prefetch_l1(reinterpret_cast<const void *>(a));
 }
 
-template <int TEAM, int QMAX, bool KAHAN, bool DELTA, bool TSM>
+template <int TEAM, int QMAX, bool KAHAN, bool DELTA, bool TSM, int KF = 0, bool TAIL = false>
 __global__ void __launch_bounds__(kEvalThreads, MM_EVAL_MINB) k_eval_tiled(EvalArgs A) {
     constexpr int CH = kChunk;              // moves per warp chunk (2 per lane)
     constexpr int NW = kEvalThreads / 32;   // warps per CTA
@@ -355,22 +457,33 @@ __global__ void __launch_bounds__(kEvalThreads, MM_EVAL_MINB) k_eval_tiled(EvalA
             const uint32_t tt = act ? s_tt[warp][slot] : 0;
             const uint32_t t1 = tt & 0xffu, t2 = tt >> 8;
             const float dd = s_dd[t1 * T1 + t2];
-            float d[QMAX][4];
             float mu, sd;
             const float *row1 = A.val + (size_t)b1 * A.R;
             const float *row2 = A.val + (size_t)b2 * A.R;
-            if (!sw)
-                team_eval<TEAM, QMAX, false, KAHAN, false>(A, tab, s_lut, tl, act, row1, row2, t1, t2, dd, NQ, rem,
-                                                           invS, pin_off, d, mu, sd);
-            else
-                team_eval<TEAM, QMAX, true, KAHAN, false>(A, tab, s_lut, tl, act, row1, row2, t1, t2, dd, NQ, rem,
-                                                          invS, pin_off, d, mu, sd);
-            if (act) {
-                if (tl == 0) {
-                    s_score[warp][slot] = mu - A.lambda * sd;
-                    s_mean[warp][slot] = mu;
-                }
-                if (DELTA) write_deltas<TEAM, QMAX>(A, c0 + slot, tl, NQ, rem, d);
+            if constexpr (KF > 0) {
+                // fast form: S % 4 == 0, KF full quad iterations, optional tail
+                const int ntail = NQ - KF * TEAM;
+                float d[KF + 1][4];
+                if (!sw)
+                    team_eval_fast<TEAM, KF, TAIL, false, KAHAN>(A, tab, s_lut, tl, row1, row2, t1, t2, dd, ntail,
+                                                                 invS, pin_off, d, mu, sd);
+                else
+                    team_eval_fast<TEAM, KF, TAIL, true, KAHAN>(A, tab, s_lut, tl, row1, row2, t1, t2, dd, ntail,
+                                                                invS, pin_off, d, mu, sd);
+                if (act && DELTA) write_deltas_fast<TEAM, KF>(A, c0 + slot, tl, ntail, d);
+            } else {
+                float d[QMAX][4];
+                if (!sw)
+                    team_eval<TEAM, QMAX, false, KAHAN, false>(A, tab, s_lut, tl, act, row1, row2, t1, t2, dd, NQ,
+                                                               rem, invS, pin_off, d, mu, sd);
+                else
+                    team_eval<TEAM, QMAX, true, KAHAN, false>(A, tab, s_lut, tl, act, row1, row2, t1, t2, dd, NQ,
+                                                              rem, invS, pin_off, d, mu, sd);
+                if (act && DELTA) write_deltas<TEAM, QMAX>(A, c0 + slot, tl, NQ, rem, d);
+            }
+            if (act && tl == 0) {
+                s_score[warp][slot] = mu - A.lambda * sd;
+                s_mean[warp][slot] = mu;
             }
         }
         __syncwarp();

@@ -30,12 +30,12 @@ def gpu_model(p, preds=None):
     return m
 
 
-def run_eval(m, moves, kahan=False, deltas=True):
+def run_eval(m, moves, kahan=False, deltas=True, generic=False):
     mv = torch.as_tensor(np.ascontiguousarray(moves, np.int32), device="cuda")
     if deltas:
-        score, feas, mean, delta = m.eval_deltas(mv, kahan=kahan)
+        score, feas, mean, delta = m.eval_deltas(mv, kahan=kahan, generic=generic)
     else:
-        score, feas, mean = m.eval_moves(mv, kahan=kahan)
+        score, feas, mean = m.eval_moves(mv, kahan=kahan, generic=generic)
         delta = None
     torch.cuda.synchronize()
     out = dict(score=score.cpu().numpy(), flag=feas.cpu().numpy(), mean=mean.cpu().numpy())
@@ -86,9 +86,16 @@ def test_plain_50k_full_batch(kahan):
     p = W.config("plain_50k")
     om = O.OracleModel(p)
     m = gpu_model(p)
-    g = run_eval(m, p.moves, kahan=kahan, deltas=False)
     inc = om.eval_incremental(p.x0, p.moves)
-    check_against(g, inc, inc, f"plain_50k kahan={kahan}")
+    # 8-lane teams (the default at S = 100), 32-lane teams, 16-lane teams with
+    # L1 prefetch, and bulk-copy staging
+    for tile, generic in (((8, 0, 0, 0), False), ((8, 0, 0, 0), True), ((32, 0, 0, 0), False),
+                          ((16, 0, 0, 2), True), ((8, 0, 2, 0), False)):
+        m.set_tile(*tile)
+        g = run_eval(m, p.moves, kahan=kahan, deltas=False, generic=generic)
+        check_against(g, inc, inc, f"plain_50k kahan={kahan} tile={tile} generic={generic}")
+    m.set_tile(0, 0, -1, -1)
+    g = run_eval(m, p.moves, kahan=kahan, deltas=False)
     # per-scenario deltas on a ragged slice and brute force on a sample
     sl = slice(1000, 1000 + 3001)
     gd = run_eval(m, p.moves[sl], kahan=kahan)
@@ -114,11 +121,13 @@ def test_tiny_exhaustive(S, T):
     mv = np.concatenate([mv, bad])
     ref = om.eval_bruteforce(p.x0, mv)
     inc = om.eval_incremental(p.x0, mv, want_floor_s=True)
-    for stages in (0, 2):  # direct loads with L1 prefetch; bulk copies into shared memory
+    # direct loads (compile-time-shaped where S % 4 == 0, and the run-time-shaped
+    # form), and bulk copies into shared memory
+    for stages, generic in ((0, False), (0, True), (2, False)):
         m.set_tile(0, 0, stages, -1)
         for kahan in (False, True):
-            g = run_eval(m, mv, kahan=kahan)
-            check_against(g, ref, inc, f"tiny S={S} T={T} stages={stages} kahan={kahan}")
+            g = run_eval(m, mv, kahan=kahan, generic=generic)
+            check_against(g, ref, inc, f"tiny S={S} T={T} stages={stages} generic={generic} kahan={kahan}")
             noop = inc["floor"] == 0
             assert np.all(g["score"][noop & (ref["score"] == 0)] == 0.0)
     import paper_2511_18296_b300 as mm
