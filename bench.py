@@ -43,8 +43,8 @@ FLUSH_BYTES = 256 << 20
 EVAL_KERNEL = "k_eval_tiled"
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k_eval_tiled_plain_50k.md")
 EVAL_SOURCES = ["paper_2511_18296_b300/csrc/mm_eval.cu", "paper_2511_18296_b300/csrc/mm_eval_tiled.cuh",
-                "paper_2511_18296_b300/csrc/mm_eval_plain.cu", "paper_2511_18296_b300/csrc/mm_move.cuh",
-                "paper_2511_18296_b300/csrc/mm_internal.cuh"]
+                "paper_2511_18296_b300/csrc/mm_eval_plain.cu", "paper_2511_18296_b300/csrc/mm_eval_fast_plain.cu",
+                "paper_2511_18296_b300/csrc/mm_move.cuh", "paper_2511_18296_b300/csrc/mm_internal.cuh"]
 
 
 def algorithmic_bytes(moves: np.ndarray, S: int) -> float:
