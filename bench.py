@@ -40,10 +40,11 @@ METRIC = "move-scenario evals/sec at 50k blocks, S=100; % of HBM roofline vs pla
 UNIT = "move-scenario evals/s"
 TOPK = 32
 FLUSH_BYTES = 256 << 20
-EVAL_KERNEL = "k_eval_tiled"
-PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k_eval_tiled_plain_50k.md")
+EVAL_KERNEL = "k_eval_tiled"  # the fused step is k_eval_tiled's top-k variant
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k_eval_tiled_step_plain_50k.md")
 EVAL_SOURCES = ["paper_2511_18296_b300/csrc/mm_eval.cu", "paper_2511_18296_b300/csrc/mm_eval_tiled.cuh",
                 "paper_2511_18296_b300/csrc/mm_eval_plain.cu", "paper_2511_18296_b300/csrc/mm_eval_fast_plain.cu",
+                "paper_2511_18296_b300/csrc/mm_step.cu", "paper_2511_18296_b300/csrc/mm_apply.cuh",
                 "paper_2511_18296_b300/csrc/mm_move.cuh", "paper_2511_18296_b300/csrc/mm_internal.cuh"]
 
 
@@ -260,62 +261,76 @@ def gpu_arm(args):
     top = torch.empty(TOPK, dtype=torch.float32, device=dev)
     cnt = torch.empty(1, dtype=torch.int32, device=dev)
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    launches_per_step = 4  # eval, 2 x top-k, apply
 
-    # All work runs on one stream; the step is captured in two CUDA graphs
-    # (evaluation; top-k + apply) so that host launch overhead never shows up
-    # as idle time inside the per-step events.
+    # All work runs on one stream; steps are replayed from CUDA graphs so that
+    # host launch overhead never shows up as idle time inside the step events.
     stream = torch.cuda.Stream(device=dev)
     m.set_stream(stream)
 
-    def step():
+    def fused():
+        m.search_step(moves_d, k=TOPK, apply=True, score=score, feas=feas, idx=idx, top=top, count=cnt)
+
+    def plain_eval():
         m.eval_moves(moves_d, score=score, feas=feas, want_mean=False)
+
+    def plain_rest():
         m.topk(score, feas, TOPK, idx=idx, top=top, count=cnt)
         m.apply_best(moves_d, idx, cnt)
 
     with torch.cuda.stream(stream):
         for _ in range(max(args.warmup, 3)):
             flush.zero_()
-            step()
+            fused()
+            plain_eval()
+            plain_rest()
     stream.synchronize()
-    g_eval, g_rest = torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()
-    with torch.cuda.graph(g_eval, stream=stream):
-        m.eval_moves(moves_d, score=score, feas=feas, want_mean=False)
-    with torch.cuda.graph(g_rest, stream=stream):
-        m.topk(score, feas, TOPK, idx=idx, top=top, count=cnt)
-        m.apply_best(moves_d, idx, cnt)
-    with torch.cuda.stream(stream):
-        for _ in range(3):
-            flush.zero_()
-            g_eval.replay()
-            g_rest.replay()
-    stream.synchronize()
-    m.schedule_set(p.x0)  # every timed run starts from the same schedule
 
+    def capture(fn):
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            fn()
+        return g
+
+    g_step, g_eval, g_rest = capture(fused), capture(plain_eval), capture(plain_rest)
+    g_kahan = capture(lambda: m.eval_moves(moves_d, score=score, feas=feas, want_mean=False, kahan=True))
+
+    def timed(graphs, K):
+        """Per-step device times (ms) of the given graphs replayed in order,
+        L2 flushed before every step; returns [step][graph]."""
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(graphs) + 1)] for _ in range(K)]
+        with torch.cuda.stream(stream):
+            for k in range(K):
+                flush.zero_()
+                ev[k][0].record(stream)
+                for j, g in enumerate(graphs):
+                    g.replay()
+                    ev[k][j + 1].record(stream)
+        torch.cuda.synchronize()
+        return [[ev[k][j].elapsed_time(ev[k][j + 1]) for j in range(len(graphs))] for k in range(K)]
+
+    timed([g_step], 3)
+    m.schedule_set(p.x0)  # every timed run starts from the same schedule
     K = args.steps
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
     with ClockSampler(local) as clk:
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
         t_start = time.time()
-        with torch.cuda.stream(stream):
-            for k in range(K):
-                flush.zero_()
-                ev[k][0].record(stream)
-                g_eval.replay()
-                ev[k][1].record(stream)
-                g_rest.replay()
-                ev[k][2].record(stream)
-        torch.cuda.synchronize()
+        step_t = timed([g_step], K)
         if world > 1:
             dist.barrier()
         t_end = time.time()
-    step_ms = [e[0].elapsed_time(e[2]) for e in ev]
-    eval_ms = [e[0].elapsed_time(e[1]) for e in ev]
-    total_ms = float(sum(step_ms))
-    eval_avg_ms = float(sum(eval_ms)) / K
+    total_ms = float(sum(t[0] for t in step_t))
+    step_avg_ms = total_ms / K
     applied, npv_mean, _ = m.last_apply()
+    # the plain form (one launch per call) and the compensated-sum evaluator, same workload
+    m.schedule_set(p.x0)
+    Kp = max(20, min(K, 500))
+    plain_t = timed([g_eval, g_rest], Kp)
+    plain_eval_ms = float(np.mean([t[0] for t in plain_t]))
+    plain_step_ms = float(np.mean([t[0] + t[1] for t in plain_t]))
+    m.schedule_set(p.x0)
+    kahan_eval_ms = float(np.mean([t[0] for t in timed([g_kahan], Kp)]))
 
     # end to end through the public API with host buffers
     K2 = max(20, min(200, K))
@@ -324,7 +339,6 @@ def gpu_arm(args):
     idx_h = torch.empty(TOPK, dtype=torch.int32).pin_memory()
     top_h = torch.empty(TOPK, dtype=torch.float32).pin_memory()
     cnt_h = torch.empty(1, dtype=torch.int32).pin_memory()
-    moves_np = p.moves
     m.schedule_set(p.x0)
     e2e_s = []
     for k in range(K2 + 3):
@@ -332,51 +346,56 @@ def gpu_arm(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         moves_d.copy_(moves_h, non_blocking=True)
-        m.eval_moves(moves_d, score=score, feas=feas, want_mean=False)
-        m.topk(score, feas, TOPK, idx=idx, top=top, count=cnt)
+        m.search_step(moves_d, k=TOPK, apply=True, score=score, feas=feas, idx=idx, top=top, count=cnt)
         idx_h.copy_(idx, non_blocking=True)
         top_h.copy_(top, non_blocking=True)
         cnt_h.copy_(cnt, non_blocking=True)
-        stream.synchronize()
-        if int(cnt_h[0]) > 0:
-            try:
-                m.apply_move(tuple(moves_np[int(idx_h[0])]))
-            except mm.MMError:
-                pass
+        _, e2e_mean, _ = m.last_apply()  # synchronises; NPV after the applied move
         t1 = time.perf_counter()
         if k >= 3:
             e2e_s.append(t1 - t0)
     e2e_avg = sum(e2e_s) / len(e2e_s)
 
     # max over ranks
-    local_vals = torch.tensor([total_ms, eval_avg_ms, e2e_avg], dtype=torch.float64, device=dev)
+    local_vals = torch.tensor([total_ms, step_avg_ms, e2e_avg, plain_step_ms, plain_eval_ms], dtype=torch.float64,
+                              device=dev)
     if world > 1:
         dist.all_reduce(local_vals, op=dist.ReduceOp.MAX)
-    total_ms, eval_avg_ms, e2e_avg = [float(v) for v in local_vals.cpu()]
+    total_ms, step_avg_ms, e2e_avg, plain_step_ms, plain_eval_ms = [float(v) for v in local_vals.cpu()]
 
     evals_per_step = n * S
     value = world * evals_per_step * K / (total_ms * 1e-3)
     alg = algorithmic_bytes(p.moves, S)
     peaks, which = measured_peaks()
-    achieved_gbs = alg / (eval_avg_ms * 1e-3) / 1e9
+    achieved_gbs = alg / (step_avg_ms * 1e-3) / 1e9
+    plain_gbs = alg / (plain_eval_ms * 1e-3) / 1e9
     clocks = clk.summary(t_start, t_end)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
         "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic (seeded lognormal Gaussian-random-field grades; no public dataset)",
         "config": {"workload": "50x50x20 = 50,000 blocks, S=100, T=20, 262,144 moves (50% shifts, 50% swaps)",
-                   "step": "mm_eval_moves + mm_topk(k=32) + mm_apply_best (two CUDA graphs)", "topk": TOPK,
+                   "step": "mm_search_step: evaluate + top-32 + apply the best move, one launch (CUDA graph)",
+                   "topk": TOPK,
                    "l2": "flushed before every step (256 MB write outside the step events)",
                    "per_rank_moves": n, "parallelism": f"independent batches x{world}"},
         "roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved_gbs / peaks["hbm_gbs"], "traffic": profiled_traffic(),
-                     "kernel": EVAL_KERNEL, "kernel_ms": eval_avg_ms,
+                     "kernel": EVAL_KERNEL + " (fused search step: evaluation + top-k + apply)",
+                     "kernel_ms": step_avg_ms,
                      "algorithmic_bytes_per_launch": alg, "peak_source": f"{which} (MEASURED_PEAKS.json hbm_gbs)"},
+        "plain_form": {"desc": "mm_eval_moves, then mm_topk + mm_apply_best: one launch per call, same workload",
+                       "value": evals_per_step * world / (plain_step_ms * 1e-3), "unit": UNIT,
+                       "ms_per_step": plain_step_ms, "eval_kernel_ms": plain_eval_ms,
+                       "eval_roofline_frac": plain_gbs / peaks["hbm_gbs"], "eval_achieved_gbs": plain_gbs},
+        "precision_form": {"desc": "mm_eval_moves_ex with compensated scenario sums (MM_EVAL_KAHAN)",
+                           "eval_kernel_ms": kahan_eval_ms,
+                           "eval_roofline_frac": alg / (kahan_eval_ms * 1e-3) / 1e9 / peaks["hbm_gbs"]},
         "e2e": {"value": evals_per_step * world / e2e_avg, "unit": UNIT,
-                "h2d_bytes_per_step": int(p.moves.nbytes), "d2h_bytes_per_step": TOPK * 8 + 4 + 16,
+                "h2d_bytes_per_step": int(p.moves.nbytes), "d2h_bytes_per_step": TOPK * 8 + 4 + 24 + 4,
                 "ms_per_step": e2e_avg * 1e3,
-                "path": "pinned host moves -> mm_eval_moves -> mm_topk -> top-k to host -> mm_apply_move"},
-        "gpu_launches": launches_per_step * K,
+                "path": "pinned host moves -> mm_search_step (apply on device) -> top-k and NPV to host"},
+        "gpu_launches": K,
         "clocks": clocks,
         "check": {"last_apply": applied, "npv_mean": npv_mean},
     }

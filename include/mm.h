@@ -168,6 +168,19 @@ mm_status mm_eval_moves_ex(mm_model *m, const mm_move *moves_dev, int64_t n, flo
 mm_status mm_topk(mm_model *m, const float *score_dev, const uint8_t *feasible_dev, int64_t n,
                   int32_t k, int32_t *idx_dev, float *topscore_dev, int32_t *count_dev);
 
+/* One local-search step in a single launch (Algorithm 4's evaluate-then-assign
+ * loop body with Algorithm 5's candidate evaluation): evaluates the n moves
+ * exactly as mm_eval_moves (score_dev[n], feasible_dev[n]), selects the k best
+ * feasible ones exactly as mm_topk (idx_dev[k], topscore_dev[k], *count_dev;
+ * 1 <= k <= 32), and, if apply != 0, applies the best one on the device exactly
+ * as mm_apply_best (outcome via mm_last_apply).  The per-batch selection keeps
+ * each warp's 32 best keys in registers (warp shuffles) and merges them at the
+ * end of the launch.  Needs equal block masses (else MM_ERR_INVALID_ARG; use
+ * the separate calls).  Asynchronous. */
+mm_status mm_search_step(mm_model *m, const mm_move *moves_dev, int64_t n, int32_t k, int32_t apply,
+                         float *score_dev, uint8_t *feasible_dev, int32_t *idx_dev, float *topscore_dev,
+                         int32_t *count_dev);
+
 /* mm_topk for callers that must not allocate device memory, such as code
  * that runs while a CUDA stream is being captured into a graph (cudaMalloc may
  * not be called then), code that owns a fixed memory budget or pool and must

@@ -74,6 +74,7 @@ SIGNATURES = [
     ("mm_set_tile", C.c_int, [P, I32, I32, I32, I32]),
     ("mm_topk", C.c_int, [P, P, P, I64, I32, P, P, P]),
     ("mm_topk_noalloc", C.c_int, [P, P, I64, I32, P, P, P, P]),
+    ("mm_search_step", C.c_int, [P, P, I64, I32, I32, P, P, P, P, P]),
     ("mm_apply_move", C.c_int, [P, MMMove, P, P]),
     ("mm_apply_best", C.c_int, [P, P, I64, P, P]),
     ("mm_last_apply", C.c_int, [P, P, P, P]),
@@ -243,6 +244,26 @@ class Model:
             count = torch.empty(1, dtype=torch.int32, device=dev)
         _check(lib().mm_topk(self.h, _ptr(score), _ptr(feas), n, k, _ptr(idx), _ptr(top), _ptr(count)))
         return idx, top, count
+
+    def search_step(self, moves, k: int = 32, apply: bool = True, score=None, feas=None, idx=None, top=None,
+                    count=None):
+        """Evaluate + top-k (k <= 32) + optional device apply of the best move, one launch."""
+        import torch
+        n = moves.shape[0]
+        dev = moves.device
+        if score is None:
+            score = torch.empty(n, dtype=torch.float32, device=dev)
+        if feas is None:
+            feas = torch.empty(n, dtype=torch.uint8, device=dev)
+        if idx is None:
+            idx = torch.empty(k, dtype=torch.int32, device=dev)
+        if top is None:
+            top = torch.empty(k, dtype=torch.float32, device=dev)
+        if count is None:
+            count = torch.empty(1, dtype=torch.int32, device=dev)
+        _check(lib().mm_search_step(self.h, _ptr(moves), n, k, 1 if apply else 0, _ptr(score), _ptr(feas), _ptr(idx),
+                                    _ptr(top), _ptr(count)))
+        return score, feas, idx, top, count
 
     # -- apply ----------------------------------------------------------
     def apply_move(self, move) -> Tuple[float, float]:

@@ -33,6 +33,8 @@ EvalFn pick_tiled_plain(int team, int qmax, bool delta, bool tsm, bool tma);
 EvalFn pick_tiled_kahan(int team, int qmax, bool delta, bool tsm, bool tma);
 EvalFn pick_fast_plain(int team, int kf, bool tail, bool delta, bool tsm);
 EvalFn pick_fast_kahan(int team, int kf, bool tail, bool delta, bool tsm);
+EvalFn pick_step(int team, bool fast, int kf, bool tail, int qmax, bool tsm);
+ApplyArgs apply_args(mm_model *m);
 
 // General evaluator (unequal block masses): one warp per move, one lane per
 // scenario, penalty change from the exact integer ore tonnages:
@@ -135,7 +137,7 @@ int default_team(int S) {
 }
 
 mm_status eval_launch(mm_model *m, const mm_move *moves, int64_t n, float *score, uint8_t *feas, float *mean,
-                      float *delta, int32_t options, int team, int ctas_per_sm, int stages) {
+                      float *delta, int32_t options, int team, int ctas_per_sm, int stages, const StepOut *step) {
     EvalArgs A;
     A.moves = reinterpret_cast<const int2 *>(moves);
     A.n = n;
@@ -153,6 +155,16 @@ mm_status eval_launch(mm_model *m, const mm_move *moves, int64_t n, float *score
     A.lambda = (float)m->lambda;
     A.a = m->shortfall_pen; A.e = m->excess_pen;
     A.qpl = 0;
+    A.k = 0; A.do_apply = 0; A.idx_out = nullptr; A.top_out = nullptr; A.count_out = nullptr;
+    A.step_cta = m->step_cta;
+    if (step) {
+        A.k = step->k;
+        A.do_apply = step->apply;
+        A.idx_out = step->idx;
+        A.top_out = step->top;
+        A.count_out = step->count;
+        stages = 0;  // the fused step runs on direct loads
+    }
     const bool kahan = (options & MM_EVAL_KAHAN) != 0;
     const bool want_delta = delta != nullptr;
     if (!m->uniform_mass) {
@@ -190,17 +202,20 @@ mm_status eval_launch(mm_model *m, const mm_move *moves, int64_t n, float *score
     const bool use_tma = stages > 0;
     A.nstage = stages;
     EvalFn fn = nullptr;
-    if (!use_tma && m->S % 4 == 0 && !(options & MM_EVAL_GENERIC)) {
+    const int kf = nq / team;
+    const bool tail = nq % team != 0;
+    const bool fast_ok = !use_tma && m->S % 4 == 0 && !(options & MM_EVAL_GENERIC) && kf >= 1 && kf <= 4;
+    if (step) {
+        fn = pick_step(team, fast_ok, kf, tail, qmax, tsm);
+    } else {
         // fast form: floor(NQ / team) full quad iterations known at compile time
-        const int kf = nq / team;
-        const bool tail = nq % team != 0;
-        if (kf >= 1 && kf <= 4)
+        if (fast_ok)
             fn = kahan ? pick_fast_kahan(team, kf, tail, want_delta, tsm)
                        : pick_fast_plain(team, kf, tail, want_delta, tsm);
+        if (!fn)
+            fn = kahan ? pick_tiled_kahan(team, qmax, want_delta, tsm, use_tma)
+                       : pick_tiled_plain(team, qmax, want_delta, tsm, use_tma);
     }
-    if (!fn)
-        fn = kahan ? pick_tiled_kahan(team, qmax, want_delta, tsm, use_tma)
-                   : pick_tiled_plain(team, qmax, want_delta, tsm, use_tma);
     if (!fn) return set_error(MM_ERR_INVALID_ARG, "no evaluator for team %d with %d quads per lane", team, qpl);
     // the 48 KB default covers static + dynamic shared memory (~12 KB static here)
     if (smem + 16 * 1024 > 48 * 1024 && m->smem_attr[(const void *)fn] < smem) {
@@ -227,9 +242,11 @@ mm_status eval_launch(mm_model *m, const mm_move *moves, int64_t n, float *score
     }
     const int64_t chunks = (n + kChunk - 1) / kChunk;
     int64_t blocks = (chunks + kEvalThreads / 32 - 1) / (kEvalThreads / 32);
-    const int64_t grid_cap = (int64_t)m->num_sms * per_sm;
+    int64_t grid_cap = (int64_t)m->num_sms * per_sm;
+    if (step && grid_cap > m->step_max_ctas) grid_cap = m->step_max_ctas;
     if (blocks > grid_cap) blocks = grid_cap;
     if (blocks < 1) blocks = 1;
+    if (step) const_cast<StepOut *>(step)->grid = (int)blocks;
     fn<<<(unsigned)blocks, kEvalThreads, smem, m->stream>>>(A);
     return check_launch("k_eval_tiled");
 }
@@ -252,7 +269,8 @@ extern "C" {
 mm_status mm_eval_moves(mm_model *m, const mm_move *moves, int64_t n, float *score, uint8_t *feas, float *mean) {
     mm_status st = eval_check(m, moves, n, score, feas);
     if (st != MM_OK || n == 0) return st;
-    return eval_launch(m, moves, n, score, feas, mean, nullptr, MM_EVAL_PLAIN, m->team, m->ctas_per_sm, m->stages);
+    return eval_launch(m, moves, n, score, feas, mean, nullptr, MM_EVAL_PLAIN, m->team, m->ctas_per_sm, m->stages,
+                       nullptr);
 }
 
 mm_status mm_set_tile(mm_model *m, int32_t team, int32_t ctas_per_sm, int32_t stages, int32_t prefetch) {
@@ -277,7 +295,8 @@ mm_status mm_eval_moves_ex(mm_model *m, const mm_move *moves, int64_t n, float *
     if (st != MM_OK || n == 0) return st;
     if (options & ~(MM_EVAL_KAHAN | MM_EVAL_GENERIC))
         return set_error(MM_ERR_INVALID_ARG, "unknown option bits 0x%x", options);
-    return eval_launch(m, moves, n, score, feas, mean, delta, options, m->team, m->ctas_per_sm, m->stages);
+    return eval_launch(m, moves, n, score, feas, mean, delta, options, m->team, m->ctas_per_sm, m->stages, nullptr);
 }
 
 }  // extern "C"
+

@@ -19,8 +19,8 @@
 // per-scenario work is four (shift) or seven (swap) FP32 operations.
 #pragma once
 
-#include "mm_internal.cuh"
-#include "mm_move.cuh"
+#include "mm_apply.cuh"
+#include "mm_sort.cuh"
 
 namespace mm {
 
@@ -57,7 +57,87 @@ struct EvalArgs {
     int32_t prefetch;      // direct-load path: batches whose rows are prefetched into L1 ahead
     float lambda;
     double a, e;
+    // fused search step (TOPK kernels only)
+    int32_t k;             // top-k size, 1..32
+    int32_t do_apply;      // apply the best feasible move at the end
+    int32_t *idx_out;      // [k]
+    float *top_out;        // [k]
+    int32_t *count_out;    // [1]
+    uint64_t *step_cta;    // [grid][32] per-CTA top-32 keys
 };
+
+// ---------------------------------------------------------------- warp top-k
+// A warp keeps its 32 best candidate keys, one per lane, sorted best-first
+// across lanes.  Keys are unique 64-bit integers: the order-preserving bits of
+// the FP32 score (-0 folded into +0) above the complement of the move index,
+// so larger is better and equal scores prefer the lower index; 0 = empty.
+
+__device__ __forceinline__ uint64_t score_key(float f, int64_t i) {
+    uint32_t u = __float_as_uint(f);
+    if ((u << 1) == 0) u = 0;  // -0 -> +0
+    const uint32_t ord = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+    return ((uint64_t)ord << 32) | (uint32_t)(~(uint32_t)i);
+}
+
+__device__ __forceinline__ uint64_t umax64(uint64_t a, uint64_t b) { return a > b ? a : b; }
+__device__ __forceinline__ uint64_t umin64(uint64_t a, uint64_t b) { return a < b ? a : b; }
+
+// Bitonic sort of the 32 lane values, largest in lane 0.
+__device__ __forceinline__ uint64_t warp_sort_desc(uint64_t x) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int size = 2; size <= 32; size <<= 1) {
+#pragma unroll
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            const uint64_t y = __shfl_xor_sync(0xffffffffu, x, stride);
+            const bool lower = (lane & stride) == 0;
+            const bool desc = (lane & size) == 0;
+            x = (lower == desc) ? umax64(x, y) : umin64(x, y);
+        }
+    }
+    return x;
+}
+
+// Top 32 of the union of two best-first lists.
+__device__ __forceinline__ uint64_t warp_merge_sorted(uint64_t t, uint64_t c) {
+    const int lane = threadIdx.x & 31;
+    uint64_t m = umax64(t, __shfl_sync(0xffffffffu, c, 31 - lane));  // bitonic: holds the top 32
+#pragma unroll
+    for (int stride = 16; stride > 0; stride >>= 1) {
+        const uint64_t y = __shfl_xor_sync(0xffffffffu, m, stride);
+        m = ((lane & stride) == 0) ? umax64(m, y) : umin64(m, y);
+    }
+    return m;
+}
+
+// Insert one candidate per lane (0 = none).  Candidates that beat the
+// current 32nd key are inserted one by one (find the rank with a ballot,
+// shift the tail of the list down one lane); more than 8 at once go through
+// a full sort and merge instead.
+__device__ __forceinline__ uint64_t warp_topk_insert(uint64_t t, uint64_t c) {
+    const int lane = threadIdx.x & 31;
+    uint32_t msk = __ballot_sync(0xffffffffu, c > __shfl_sync(0xffffffffu, t, 31));
+    if (msk == 0) return t;
+    if (__popc(msk) > 8) return warp_merge_sorted(t, warp_sort_desc(c));
+    while (msk) {
+        const int src = __ffs(msk) - 1;
+        msk &= msk - 1;
+        const uint64_t x = __shfl_sync(0xffffffffu, c, src);
+        const int pos = __popc(__ballot_sync(0xffffffffu, t > x));  // entries better than x
+        const uint64_t up = __shfl_up_sync(0xffffffffu, t, 1);
+        if (pos < 32) t = lane < pos ? t : (lane == pos ? x : up);
+    }
+    return t;
+}
+
+// Merge another best-first list into t, skipped when it cannot contribute.
+__device__ __forceinline__ uint64_t warp_topk_merge(uint64_t t, uint64_t c_sorted) {
+    const uint64_t thr = __shfl_sync(0xffffffffu, t, 31);
+    const uint64_t best = __shfl_sync(0xffffffffu, c_sorted, 0);
+    if (best <= thr) return t;
+    return warp_merge_sorted(t, c_sorted);
+}
+
 
 // Neumaier-compensated accumulation: (s, c) += x.
 __device__ __forceinline__ void comp_add(float &s, float &c, float x) {
@@ -334,7 +414,24 @@ __device__ __forceinline__ void prefetch_row(const float *row, uint32_t row_byte
         prefetch_l1(reinterpret_cast<const void *>(a));
 }
 
-template <int TEAM, int QMAX, bool KAHAN, bool DELTA, bool TSM, int KF = 0, bool TAIL = false>
+// End of the evaluation part of a fused search step: warp 0 merges the
+// warps' lists (skipping lists that cannot contribute) and publishes the
+// CTA's 32 best keys.  Every key of the batch's top k is among the 32 best of
+// the CTA that evaluated it; k_step_finish selects from these lists.
+__device__ __forceinline__ void step_publish(const EvalArgs &A, uint64_t wtk) {
+    constexpr int NW = kEvalThreads / 32;
+    __shared__ uint64_t s_wtk[NW][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    s_wtk[warp][lane] = wtk;
+    __syncthreads();
+    if (warp == 0) {
+        uint64_t t = s_wtk[0][lane];
+        for (int w = 1; w < NW; w++) t = warp_topk_merge(t, s_wtk[w][lane]);
+        A.step_cta[(size_t)blockIdx.x * 32 + lane] = t;
+    }
+}
+
+template <int TEAM, int QMAX, bool KAHAN, bool DELTA, bool TSM, int KF = 0, bool TAIL = false, bool TOPK = false>
 __global__ void __launch_bounds__(kEvalThreads, MM_EVAL_MINB) k_eval_tiled(EvalArgs A) {
     constexpr int CH = kChunk;              // moves per warp chunk (2 per lane)
     constexpr int NW = kEvalThreads / 32;   // warps per CTA
@@ -345,6 +442,7 @@ __global__ void __launch_bounds__(kEvalThreads, MM_EVAL_MINB) k_eval_tiled(EvalA
     __shared__ uint32_t s_tt[NW][CH];
     __shared__ uint8_t s_lsh[NW][CH], s_lsw[NW][CH];
     __shared__ float s_score[NW][CH], s_mean[NW][CH];
+    __shared__ uint8_t s_flag[NW][CH];
 
     const int T1 = A.T + 1;
     const size_t tab_floats = (size_t)2 * T1 * A.S_pad;
@@ -385,6 +483,7 @@ __global__ void __launch_bounds__(kEvalThreads, MM_EVAL_MINB) k_eval_tiled(EvalA
     const int64_t gw = (int64_t)blockIdx.x * NW + warp;
     const int64_t r0 = gw * A.n / nwarps, r1 = (gw + 1) * A.n / nwarps;
 
+    uint64_t wtk = 0;  // this warp's best 32 candidate keys (TOPK)
     int2 mv[2];
 #pragma unroll
     for (int h = 0; h < 2; h++) {
@@ -415,6 +514,7 @@ __global__ void __launch_bounds__(kEvalThreads, MM_EVAL_MINB) k_eval_tiled(EvalA
             }
             s_score[warp][slot] = v.valid ? 0.0f : -INFINITY;
             s_mean[warp][slot] = 0.0f;
+            if (TOPK) s_flag[warp][slot] = (active && v.feasible) ? 1 : 0;
             if (work) {
                 s_b1[warp][slot] = v.b1;
                 s_b2[warp][slot] = v.swap ? v.b2 : A.tp.B;
@@ -496,9 +596,18 @@ __global__ void __launch_bounds__(kEvalThreads, MM_EVAL_MINB) k_eval_tiled(EvalA
                 A.score[i] = s_score[warp][slot];
                 if (A.mean) A.mean[i] = s_mean[warp][slot];
             }
+            if (TOPK) {
+                uint64_t key = 0;
+                if (i < r1 && s_flag[warp][slot]) {
+                    const float f = s_score[warp][slot];
+                    if (!isnan(f)) key = score_key(f, i);
+                }
+                wtk = warp_topk_insert(wtk, key);
+            }
         }
         __syncwarp();
     }
+    if constexpr (TOPK) step_publish(A, wtk);
 }
 
 // ----------------------------------------------------------------------------

@@ -99,6 +99,8 @@ struct mm_model {
     mm::ApplyResult *apply_res_host = nullptr;  // pinned host mirror
     uint32_t *status_host = nullptr;            // pinned
     mm::TopkScratch topk;
+    uint64_t *step_cta = nullptr;    // fused search step: [step_max_ctas][32] published keys
+    int step_max_ctas = 0;
 };
 
 namespace mm {
@@ -111,8 +113,16 @@ mm_status read_sticky(mm_model *m);  // synchronises, clears and maps the sticky
 
 // Kernels and launchers shared between translation units.
 mm_status rebuild_tables(mm_model *m);                     // Pout/Pin from oreT
+// Outputs of the fused search step (top-k of the batch, optional apply).
+struct StepOut {
+    int32_t k, apply;
+    int32_t *idx;
+    float *top;
+    int32_t *count;
+    int grid;  // set by eval_launch: CTAs that publish a list
+};
 mm_status eval_launch(mm_model *m, const mm_move *moves, int64_t n, float *score, uint8_t *feas, float *mean,
-                      float *delta, int32_t options, int team, int ctas_per_sm, int stages);
+                      float *delta, int32_t options, int team, int ctas_per_sm, int stages, const StepOut *step);
 int default_team(int S);
 mm_status topk_launch(const float *score, const uint8_t *feas, int64_t n, int32_t k, int32_t *idx,
                       float *top, int32_t *count, TopkScratch &scr, int num_sms, cudaStream_t st);

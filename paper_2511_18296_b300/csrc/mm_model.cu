@@ -19,8 +19,7 @@
 #include <limits>
 #include <numeric>
 
-#include "mm_internal.cuh"
-#include "mm_move.cuh"
+#include "mm_apply.cuh"
 
 namespace mm {
 
@@ -95,10 +94,6 @@ __global__ void k_classify(const double *__restrict__ grade, const uint32_t *__r
     reinterpret_cast<uint32_t *>(row + ore_off)[w] = bits;
 }
 
-__device__ __forceinline__ uint32_t ore_bit(const float *val, int32_t R, int32_t ore_off, int32_t b, int s) {
-    return (reinterpret_cast<const uint32_t *>(val + (int64_t)b * R + ore_off)[s >> 5] >> (s & 31)) & 1u;
-}
-
 // Packed period/lo/hi word of every block.
 __global__ void k_blk_build(Topo tp, const uint8_t *__restrict__ period, uint32_t *__restrict__ blk) {
     int32_t b = blockIdx.x * blockDim.x + threadIdx.x;
@@ -163,50 +158,11 @@ __global__ void k_accum(const int32_t *__restrict__ order, const int32_t *__rest
     }
 }
 
-// pen(x0) - pen(x1) for excess x = O - Q (exact integer parts, then FP64).
-__device__ __forceinline__ double pen_diff(int64_t x0, int64_t x1, double a, double e) {
-    int64_t s0 = x0 < 0 ? -x0 : 0, s1 = x1 < 0 ? -x1 : 0;
-    int64_t e0 = x0 > 0 ? x0 : 0, e1 = x1 > 0 ? x1 : 0;
-    return __dadd_rn(__dmul_rn(a, (double)(s0 - s1)), __dmul_rn(e, (double)(e0 - e1)));
-}
-
-__device__ __forceinline__ double pen_of(int64_t x, double a, double e) {
-    return x < 0 ? __dmul_rn(a, (double)(-x)) : __dmul_rn(e, (double)x);
-}
-
-// Pout[t][s] = d_t (pen(x) - pen(x - m)), Pin[t][s] = d_t (pen(x) - pen(x + m))
-// with x = oreT[t][s] - Q_t; zero for t = T and for padding scenarios.
-__device__ __forceinline__ void table_entry(int t, int s, int32_t S, int32_t S_pad, int32_t T, const int64_t *oreT,
-                                            const uint64_t *target, const double *disc, int64_t m, double a,
-                                            double e, float *tab) {
-    float po = 0.0f, pi = 0.0f;
-    if (t < T && s < S) {
-        int64_t x = oreT[(int64_t)t * S + s] - (int64_t)target[t];
-        double d = disc[t];
-        po = __double2float_rn(__dmul_rn(d, pen_diff(x, x - m, a, e)));
-        pi = __double2float_rn(__dmul_rn(d, pen_diff(x, x + m, a, e)));
-    }
-    tab[(int64_t)t * S_pad + s] = po;
-    tab[(int64_t)(T + 1) * S_pad + (int64_t)t * S_pad + s] = pi;
-}
-
 __global__ void k_tables(int32_t S, int32_t S_pad, int32_t T, const int64_t *__restrict__ oreT,
                          const uint64_t *__restrict__ target, const double *__restrict__ disc, int64_t m, double a,
                          double e, float *__restrict__ tab) {
     int t = blockIdx.x;
     for (int s = threadIdx.x; s < S_pad; s += blockDim.x) table_entry(t, s, S, S_pad, T, oreT, target, disc, m, a, e, tab);
-}
-
-// Discounted net cash of period t in scenario s:
-//   d_t (price*rec*metal - pc*oreT - mc*minedT - pen_t(oreT)).
-__device__ __forceinline__ double contrib_of(int t, int s, int32_t S, const double *disc, const double *metal,
-                                             const int64_t *oreT, const int64_t *minedT, const uint64_t *target,
-                                             double pr, double pc, double mc, double a, double e) {
-    int64_t o = oreT[(int64_t)t * S + s];
-    double cash = __dsub_rn(__dsub_rn(__dmul_rn(pr, metal[(int64_t)t * S + s]), __dmul_rn(pc, (double)o)),
-                            __dmul_rn(mc, (double)minedT[t]));
-    double p = pen_of(o - (int64_t)target[t], a, e);
-    return __dmul_rn(disc[t], __dsub_rn(cash, p));
 }
 
 // contrib[t][s] for every period, and NPV_s = their sum in period order.
@@ -225,197 +181,26 @@ __global__ void k_npv(int32_t S, int32_t T, const double *__restrict__ disc, con
     npv[s] = acc;
 }
 
-// Block-wide FP64 mean and population std of npv[0..S) (two passes).
-__device__ void npv_stats(const double *npv, int32_t S, double *mean, double *std) {
-    __shared__ double red[32];
-    double acc = 0.0;
-    for (int s = threadIdx.x; s < S; s += blockDim.x) acc += npv[s];
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += red[w];
-        red[31] = t / S;
-    }
-    __syncthreads();
-    double mu = red[31];
-    __syncthreads();
-    double v = 0.0;
-    for (int s = threadIdx.x; s < S; s += blockDim.x) v += (npv[s] - mu) * (npv[s] - mu);
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += red[w];
-        *mean = mu;
-        *std = sqrt(t / S);
-    }
-}
-
-struct ApplyArgs {
-    Topo tp;
-    int32_t S, S_pad, W, T, R, ore_off;
-    uint32_t m_uniform;
-    int32_t uniform;
-    const uint32_t *mass;
-    const float *val;
-    const double *grade;
-    uint32_t *blk;
-    int64_t *minedT;
-    int64_t *oreT;
-    double *metal;
-    double *npv;
-    double *contrib;
-    float *tab;
-    const double *disc;
-    const uint64_t *cap;
-    const uint64_t *target;
-    double pr, pc, mc, a, e;
-    ApplyResult *res;
-    uint32_t *status;
-};
-
-// Apply one move on a single CTA: exact re-check, period update, integer
-// tonnages, FP64 metal, lo/hi of the neighbourhood, tables and NPV
-// contributions of the affected periods (NPV_s += new - old), then the FP64
-// mean/std of NPV over scenarios (computed whether or not the move applied).
-// The move comes either by value (from_dev = 0) or as moves[idx[0]] when
-// *count > 0 (from_dev = 1).
+// Apply kernel: the move comes either by value (from_dev = 0) or as
+// moves[idx[0]] when *count > 0 (from_dev = 1; an index outside the batch is a
+// bad move).
 __global__ void k_apply(ApplyArgs A, int2 mv_val, const int2 *moves, int64_t n_moves, const int32_t *idx,
                         const int32_t *count, int from_dev) {
-    __shared__ MoveView sv;
-    __shared__ int s_go;
-    __shared__ int32_t s_nb[32];
-    __shared__ int s_nnb;
-    if (threadIdx.x == 0) {
-        int2 mv = mv_val;
-        int have = 1;
-        if (from_dev) {
-            have = *count > 0;
-            if (have) {
-                int32_t j = idx[0];
-                if (j >= 0 && (int64_t)j < n_moves) {
-                    mv = moves[j];
-                } else {
-                    mv = make_int2(-1, -1);  // decodes as a bad move
-                    atomicOr(A.status, kStBadMove);
-                }
-            }
-        }
-        MoveView v;
+    int2 mv = mv_val;
+    int have = 1;
+    if (from_dev) {
+        have = *count > 0;
         if (have) {
-            v = decode_move(
-                mv, A.tp, [&](int32_t b) { return A.blk[b]; },
-                [&](int32_t b) { return A.uniform ? A.m_uniform : A.mass[b]; },
-                [&](uint32_t t) { return A.minedT[t]; }, [&](uint32_t t) { return A.cap[t]; });
-        } else {
-            v.valid = true;
-            v.feasible = false;
-            v.noop = true;
-        }
-        sv = v;
-        int go = have && v.valid && v.feasible && !v.noop;
-        s_go = go;
-        A.res->applied = (have && v.valid && v.feasible) ? 1 : 0;  // a feasible no-op counts as applied
-        A.res->status = !have ? MM_OK : (!v.valid ? MM_ERR_BAD_MOVE : (!v.feasible ? MM_ERR_INFEASIBLE : MM_OK));
-        if (go) {
-            int64_t dm1 = v.m1, dm2 = v.swap ? (int64_t)v.m2 : 0;
-            if (v.t1 < (uint32_t)A.T) A.minedT[v.t1] += -dm1 + dm2;
-            if (v.t2 < (uint32_t)A.T) A.minedT[v.t2] += dm1 - dm2;
-            A.blk[v.b1] = (A.blk[v.b1] & ~0xffu) | v.t2;
-            if (v.swap) A.blk[v.b2] = (A.blk[v.b2] & ~0xffu) | v.t1;
-            // neighbourhood whose lo/hi may change: moved blocks and their neighbours
-            int n = 0;
-            int32_t mb[2] = {v.b1, v.swap ? v.b2 : -1};
-            for (int q = 0; q < 2; q++) {
-                int32_t b = mb[q];
-                if (b < 0) continue;
-                s_nb[n++] = b;
-                if (A.tp.nx > 0) {
-                    int32_t nxy = A.tp.nx * A.tp.ny;
-                    int32_t x = b % A.tp.nx, y = (b / A.tp.nx) % A.tp.ny, z = b / nxy;
-                    const int dx[5] = {0, -1, 1, 0, 0};
-                    const int dy[5] = {0, 0, 0, -1, 1};
-                    for (int k = 0; k < 5; k++) {
-                        int32_t px = x + dx[k], py = y + dy[k];
-                        if (px < 0 || px >= A.tp.nx || py < 0 || py >= A.tp.ny) continue;
-                        if (z > 0) s_nb[n++] = px + A.tp.nx * (py + A.tp.ny * (z - 1));
-                        if (z + 1 < A.tp.nz) s_nb[n++] = px + A.tp.nx * (py + A.tp.ny * (z + 1));
-                    }
-                }
-            }
-            s_nnb = n;
-        }
-    }
-    __syncthreads();
-    if (s_go) {
-        const MoveView v = sv;
-        // lo/hi of the neighbourhood (1-5 pattern); CSR handled below
-        if (A.tp.nx > 0 && threadIdx.x < (unsigned)s_nnb) {
-            int32_t b = s_nb[threadIdx.x];
-            A.blk[b] = block_bounds(A.tp, b, [&](int32_t j) { return blk_period(A.blk[j]); });
-        }
-        // per scenario: tonnage, metal, contributions, NPV, table rows
-        for (int s = threadIdx.x; s < A.S; s += blockDim.x) {
-            uint32_t o1 = ore_bit(A.val, A.R, A.ore_off, v.b1, s);
-            int64_t om1 = o1 ? (int64_t)v.m1 : 0;
-            double g1 = o1 ? __dmul_rn((double)v.m1, A.grade[(int64_t)v.b1 * A.S + s]) : 0.0;
-            int64_t om2 = 0;
-            double g2 = 0.0;
-            if (v.swap) {
-                uint32_t o2 = ore_bit(A.val, A.R, A.ore_off, v.b2, s);
-                om2 = o2 ? (int64_t)v.m2 : 0;
-                g2 = o2 ? __dmul_rn((double)v.m2, A.grade[(int64_t)v.b2 * A.S + s]) : 0.0;
-            }
-            double dnpv = 0.0;
-            const uint32_t rows[2] = {v.t1, v.t2};
-            for (int q = 0; q < 2; q++) {
-                const int t = (int)rows[q];
-                if (t >= A.T) continue;
-                const int64_t dO = q == 0 ? om2 - om1 : om1 - om2;
-                A.oreT[(int64_t)t * A.S + s] += dO;
-                double &mt = A.metal[(int64_t)t * A.S + s];
-                mt = q == 0 ? __dadd_rn(__dsub_rn(mt, g1), g2) : __dadd_rn(__dsub_rn(mt, g2), g1);
-                double c = contrib_of(t, s, A.S, A.disc, A.metal, A.oreT, A.minedT, A.target, A.pr, A.pc, A.mc,
-                                      A.a, A.e);
-                double &cr = A.contrib[(int64_t)t * A.S + s];
-                dnpv = __dadd_rn(dnpv, __dsub_rn(c, cr));
-                cr = c;
-                if (A.uniform)
-                    table_entry(t, s, A.S, A.S_pad, A.T, A.oreT, A.target, A.disc, (int64_t)A.m_uniform, A.a, A.e,
-                                A.tab);
-            }
-            A.npv[s] = __dadd_rn(A.npv[s], dnpv);
-        }
-        if (A.tp.nx == 0) {
-            // CSR: the moved blocks first, then every predecessor and successor
-            if (threadIdx.x < 2) {
-                int32_t b = threadIdx.x == 0 ? v.b1 : (v.swap ? v.b2 : -1);
-                if (b >= 0) A.blk[b] = block_bounds(A.tp, b, [&](int32_t j) { return blk_period(A.blk[j]); });
-            }
-            __syncthreads();
-            for (int q = 0; q < 2; q++) {
-                int32_t b = q == 0 ? v.b1 : (v.swap ? v.b2 : -1);
-                if (b < 0) continue;
-                int32_t np = A.tp.pred_ptr[b + 1] - A.tp.pred_ptr[b];
-                int32_t ns = A.tp.succ_ptr[b + 1] - A.tp.succ_ptr[b];
-                for (int k = threadIdx.x; k < np + ns; k += blockDim.x) {
-                    int32_t j = k < np ? A.tp.pred_idx[A.tp.pred_ptr[b] + k] : A.tp.succ_idx[A.tp.succ_ptr[b] + k - np];
-                    A.blk[j] = block_bounds(A.tp, j, [&](int32_t i) { return blk_period(A.blk[i]); });
-                }
-                __syncthreads();
+            const int32_t j = idx[0];
+            if (j >= 0 && (int64_t)j < n_moves) {
+                mv = moves[j];
+            } else {
+                mv = make_int2(-1, -1);  // decodes as a bad move
+                if (threadIdx.x == 0) atomicOr(A.status, kStBadMove);
             }
         }
     }
-    __syncthreads();
-    double mean = 0, sd = 0;
-    npv_stats(A.npv, A.S, &mean, &sd);
-    if (threadIdx.x == 0) {
-        A.res->mean = mean;
-        A.res->std = sd;
-    }
+    apply_block(A, mv, have);
 }
 
 // ------------------------------------------------------------------ host
@@ -427,7 +212,7 @@ mm_status rebuild_tables(mm_model *m) {
     return check_launch("k_tables");
 }
 
-static ApplyArgs apply_args(mm_model *m) {
+ApplyArgs apply_args(mm_model *m) {
     ApplyArgs A;
     A.tp = topo_of(m);
     A.S = m->S; A.S_pad = m->S_pad; A.W = m->W; A.T = m->T; A.R = m->R; A.ore_off = m->ore_off;
@@ -480,6 +265,7 @@ void mm_model_destroy(mm_model *m) {
     cudaFree(m->tab);
     cudaFree(m->ddt); cudaFree(m->disc); cudaFree(m->cap); cudaFree(m->target); cudaFree(m->status);
     cudaFree(m->apply_res);
+    cudaFree(m->step_cta);
     if (m->apply_res_host) cudaFreeHost(m->apply_res_host);
     if (m->status_host) cudaFreeHost(m->status_host);
     topk_scratch_free(m->topk);
@@ -588,6 +374,8 @@ mm_status mm_model_create(const mm_model_desc *d, mm_model **out) {
     ALLOC(target, T + 1);
     ALLOC(status, 1);
     ALLOC(apply_res, 1);
+    m->step_max_ctas = m->num_sms * 8;  // 256-thread CTAs: at most 8 resident per SM
+    ALLOC(step_cta, (size_t)m->step_max_ctas * 32);
     if (!grid) {
         ALLOC(pred_ptr, B + 1);
         ALLOC(pred_idx, d->pred_ptr[B] > 0 ? d->pred_ptr[B] : 1);

@@ -1,0 +1,184 @@
+// The fused search step: instantiations of the evaluator's top-k variant
+// (plain FP32 sums, no per-scenario output), the one-CTA finisher that selects
+// the batch's top k and applies the best move, and the entry point.
+#include "mm_eval_tiled.cuh"
+
+namespace mm {
+
+using EvalFn = void (*)(EvalArgs);
+ApplyArgs apply_args(mm_model *m);
+
+template <int TEAM, int KF, bool TAIL>
+static EvalFn step_fast3(bool tsm) {
+    if (tsm) return k_eval_tiled<TEAM, 1, false, false, true, KF, TAIL, true>;
+    if constexpr (TEAM == 32) return k_eval_tiled<TEAM, 1, false, false, false, KF, TAIL, true>;
+    return nullptr;
+}
+
+template <int TEAM>
+static EvalFn step_fast2(int kf, bool tail, bool tsm) {
+    switch (kf) {
+        case 1: return tail ? step_fast3<TEAM, 1, true>(tsm) : step_fast3<TEAM, 1, false>(tsm);
+        case 2: return tail ? step_fast3<TEAM, 2, true>(tsm) : step_fast3<TEAM, 2, false>(tsm);
+        case 3: return tail ? step_fast3<TEAM, 3, true>(tsm) : step_fast3<TEAM, 3, false>(tsm);
+        case 4: return tail ? step_fast3<TEAM, 4, true>(tsm) : step_fast3<TEAM, 4, false>(tsm);
+    }
+    return nullptr;
+}
+
+template <int TEAM, int QMAX>
+static EvalFn step_gen2(bool tsm) {
+    return tsm ? k_eval_tiled<TEAM, QMAX, false, false, true, 0, false, true>
+               : k_eval_tiled<TEAM, QMAX, false, false, false, 0, false, true>;
+}
+
+template <int TEAM>
+static EvalFn step_gen1(int qmax, bool tsm) {
+    switch (qmax) {
+        case 1: return step_gen2<TEAM, 1>(tsm);
+        case 2: return step_gen2<TEAM, 2>(tsm);
+        case 4: return step_gen2<TEAM, 4>(tsm);
+        case 8: return step_gen2<TEAM, 8>(tsm);
+    }
+    return nullptr;
+}
+
+EvalFn pick_step(int team, bool fast, int kf, bool tail, int qmax, bool tsm) {
+    if (fast) {
+        switch (team) {
+            case 4: return step_fast2<4>(kf, tail, tsm);
+            case 8: return step_fast2<8>(kf, tail, tsm);
+            case 16: return step_fast2<16>(kf, tail, tsm);
+            case 32: return step_fast2<32>(kf, tail, tsm);
+        }
+        return nullptr;
+    }
+    switch (team) {
+        case 4: return step_gen1<4>(qmax, tsm);
+        case 8: return step_gen1<8>(qmax, tsm);
+        case 16: return step_gen1<16>(qmax, tsm);
+        case 32: return step_gen1<32>(qmax, tsm);
+    }
+    return nullptr;
+}
+
+// Arguments of the one-CTA finisher of a fused search step.
+struct StepFinishArgs {
+    const uint64_t *keys;  // [nkeys] published CTA lists (0 = empty)
+    int32_t nkeys;
+    int64_t n;             // moves in the batch (decoded indices must be < n)
+    uint32_t *status;      // sticky status bits
+    int32_t k;
+    int32_t do_apply;
+    const float *score;
+    const int2 *moves;
+    int32_t *idx_out;
+    float *top_out;
+    int32_t *count_out;
+};
+
+// Selection of the k largest keys among the published lists (each sorted
+// best-first, 0 = empty; keys are unique): warp w merges lists w, w + 32, ...
+// with pruned warp merges (a list whose best key does not beat the running
+// 32nd is skipped), four lists' loads in flight at a time; a five-level tree
+// merges the 32 warp results; warp 0 writes the top k and the CTA applies the
+// best move when asked.
+__global__ void __launch_bounds__(1024) k_step_finish(StepFinishArgs F, ApplyArgs AP) {
+    __shared__ uint64_t s_wl[32][32];
+    __shared__ int s_best;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nw = blockDim.x >> 5;  // 32
+    const int nlists = F.nkeys / 32;
+    uint64_t t = 0;
+    for (int l0 = warp; l0 < nlists; l0 += 4 * nw) {
+        uint64_t c[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const int l = l0 + u * nw;
+            c[u] = l < nlists ? __ldcg(F.keys + (size_t)l * 32 + lane) : 0ull;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) t = warp_topk_merge(t, c[u]);
+    }
+    s_wl[warp][lane] = t;
+    __syncthreads();
+    for (int stride = nw / 2; stride > 0; stride >>= 1) {
+        if (warp < stride) {
+            t = warp_topk_merge(t, s_wl[warp + stride][lane]);
+            s_wl[warp][lane] = t;
+        }
+        __syncthreads();
+    }
+    if (warp == 0) {
+        const uint32_t valid = __ballot_sync(0xffffffffu, t != 0ull);
+        int cnt = min(__popc(valid), F.k);
+        const uint32_t id = ~(uint32_t)(t & 0xffffffffull);
+        // a key always decodes to a move of this batch; check anyway so that a
+        // corrupted list can never turn into an out-of-range access
+        const bool ok = (uint64_t)id < (uint64_t)F.n;
+        const uint32_t bad = __ballot_sync(0xffffffffu, lane < cnt && !ok);
+        if (bad) {
+            cnt = __ffs(bad) - 1;
+            if (lane == 0) atomicOr(F.status, kStBadMove);
+        }
+        const uint32_t id0 = __shfl_sync(0xffffffffu, id, 0);
+        if (lane < cnt) {
+            F.idx_out[lane] = (int32_t)id;
+            F.top_out[lane] = __ldcg(F.score + id);
+        }
+        if (lane == 0) {
+            *F.count_out = cnt;
+            s_best = cnt > 0 ? (int)id0 : -1;
+        }
+    }
+    __syncthreads();
+    if (F.do_apply) {
+        const int b = s_best;
+        const int2 mv = b >= 0 ? __ldg(F.moves + b) : make_int2(0, -1);
+        apply_block(AP, mv, b >= 0 ? 1 : 0);
+    }
+}
+
+}  // namespace mm
+
+using namespace mm;
+
+static mm_status step_check(mm_model *m, const mm_move *moves, int64_t n, float *score, uint8_t *feas) {
+    if (!m) return set_error(MM_ERR_INVALID_ARG, "NULL model");
+    if (!m->has_schedule) return set_error(MM_ERR_STATE, "no schedule installed");
+    if (n < 0 || n > 0x7fffffffLL) return set_error(MM_ERR_INVALID_ARG, "move count out of range");
+    if (n > 0 && (!moves || !score || !feas)) return set_error(MM_ERR_INVALID_ARG, "NULL output or move pointer");
+    if (((uintptr_t)moves & 7u) != 0) return set_error(MM_ERR_INVALID_ARG, "moves must be 8-byte aligned");
+    return MM_OK;
+}
+
+extern "C" mm_status mm_search_step(mm_model *m, const mm_move *moves, int64_t n, int32_t k, int32_t apply,
+                                    float *score, uint8_t *feas, int32_t *idx, float *top, int32_t *count) {
+    mm_status st = step_check(m, moves, n, score, feas);
+    if (st != MM_OK) return st;
+    if (k < 1 || k > 32) return set_error(MM_ERR_INVALID_ARG, "mm_search_step: k = %d outside 1..32", k);
+    if (!idx || !top || !count) return set_error(MM_ERR_INVALID_ARG, "NULL top-k output");
+    if (!m->uniform_mass)
+        return set_error(MM_ERR_INVALID_ARG, "mm_search_step needs equal block masses (use the separate calls)");
+    if (n == 0) {
+        MM_CUDA_TRY(cudaMemsetAsync(count, 0, sizeof(int32_t), m->stream), "clear count");
+        return apply ? mm_apply_best(m, moves, 0, idx, count) : MM_OK;
+    }
+    StepOut so{k, apply ? 1 : 0, idx, top, count, 0};
+    st = eval_launch(m, moves, n, score, feas, nullptr, nullptr, MM_EVAL_PLAIN, m->team, m->ctas_per_sm, 0, &so);
+    if (st != MM_OK) return st;
+    StepFinishArgs F;
+    F.keys = m->step_cta;
+    F.nkeys = so.grid * 32;
+    F.n = n;
+    F.status = m->status;
+    F.k = k;
+    F.do_apply = apply ? 1 : 0;
+    F.score = score;
+    F.moves = reinterpret_cast<const int2 *>(moves);
+    F.idx_out = idx;
+    F.top_out = top;
+    F.count_out = count;
+    k_step_finish<<<1, 1024, 0, m->stream>>>(F, apply_args(m));
+    return check_launch("k_step_finish");
+}

@@ -17,6 +17,7 @@
 #include <mutex>
 
 #include "mm_internal.cuh"
+#include "mm_sort.cuh"
 
 namespace mm {
 
@@ -103,26 +104,6 @@ __global__ void __launch_bounds__(256) k_topk_hist(const float *__restrict__ sco
 #pragma unroll
     for (int q = 0; q < 4; q++) reinterpret_cast<uint4 *>(hist + lo_bin)[q] = make_uint4(0, 0, 0, 0);
     if (t == 0) ctl[kCtlTicket1] = 0;
-}
-
-// Descending bitonic sort of s[0..N), N a power of two <= 1024.
-__device__ void bitonic_desc(uint64_t *s, int N) {
-    for (int size = 2; size <= N; size <<= 1) {
-        for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            __syncthreads();
-            for (int i = threadIdx.x; i < N / 2; i += blockDim.x) {
-                int lo = 2 * i - (i & (stride - 1));
-                int hi = lo + stride;
-                bool desc = ((lo & size) == 0);
-                uint64_t a = s[lo], b = s[hi];
-                if (desc ? (a < b) : (a > b)) {
-                    s[lo] = b;
-                    s[hi] = a;
-                }
-            }
-        }
-    }
-    __syncthreads();
 }
 
 __global__ void __launch_bounds__(256) k_topk_collect(const float *__restrict__ score,

@@ -1,0 +1,109 @@
+"""Fused search step (mm_search_step) vs the separate calls it fuses.
+
+One launch evaluates the batch, keeps each warp's best 32 keys with warp
+shuffles, merges them at the end of the launch and applies the best move.
+It must reproduce mm_eval_moves + mm_topk + mm_apply_best exactly: same scores
+and flags bit for bit, same top-k, same schedule and NPV after every step.
+"""
+
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from helpers import all_moves, tiny_problem
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+
+
+def _pair(p):
+    import paper_2511_18296_b300 as mm
+    a = mm.Model.from_problem(p)
+    b = mm.Model.from_problem(p)
+    a.schedule_set(p.x0)
+    b.schedule_set(p.x0)
+    return a, b
+
+
+def _separate(m, mv, k, apply):
+    s, f, _ = m.eval_moves(mv, want_mean=False)
+    idx, top, cnt = m.topk(s, f, k)
+    if apply:
+        m.apply_best(mv, idx, cnt)
+    return s, f, idx, top, cnt
+
+
+def _compare(ra, rb, k):
+    torch.cuda.synchronize()
+    sa, fa, ia, ta, ca = (x.cpu().numpy() for x in ra)
+    sb, fb, ib, tb, cb = (x.cpu().numpy() for x in rb)
+    assert np.array_equal(fa, fb)
+    assert np.array_equal(sa.view(np.uint32), sb.view(np.uint32))
+    assert ca[0] == cb[0]
+    c = int(ca[0])
+    assert np.array_equal(ia[:c], ib[:c]) and np.array_equal(ta[:c], tb[:c])
+    return c
+
+
+@pytest.mark.parametrize("name,steps,k", [("plain_4k", 12, 32), ("plain_50k", 4, 8)])
+def test_step_matches_separate_calls(name, steps, k):
+    p = W.config(name)
+    a, b = _pair(p)
+    mv = torch.as_tensor(p.moves, device="cuda")
+    for _ in range(steps):
+        ra = a.search_step(mv, k=k, apply=True)
+        rb = _separate(b, mv, k, True)
+        _compare(ra, rb, k)
+        la, lb = a.last_apply(), b.last_apply()
+        assert la == lb
+    assert np.array_equal(a.schedule_get(), b.schedule_get())
+    na, nb = a.npv(), b.npv()
+    assert np.array_equal(na[0], nb[0])
+
+
+@pytest.mark.parametrize("n", [1, 63, 64, 65, 1000, 20_000])
+@pytest.mark.parametrize("k", [1, 7, 32])
+def test_step_sizes_and_k(n, k):
+    p = W.config("plain_4k", n_moves=max(n, 2))
+    a, b = _pair(p)
+    mv = torch.as_tensor(p.moves[:n], device="cuda")
+    ra = a.search_step(mv, k=k, apply=False)
+    rb = _separate(b, mv, k, False)
+    c = _compare(ra, rb, k)
+    # no apply: the schedule is unchanged
+    assert np.array_equal(a.schedule_get(), p.x0)
+    # and the selection is the oracle's on the GPU's own scores
+    s, f = ra[0].cpu().numpy(), ra[1].cpu().numpy()
+    ri, _ = O.topk(s.astype(np.float64), f, k)
+    assert np.array_equal(ra[2].cpu().numpy()[:c], ri)
+
+
+def test_step_run_time_shaped_loop():
+    """S = 13 (not a multiple of 4) runs the run-time-shaped evaluator."""
+    p = tiny_problem(3, 3, 3, S=13, T=3, seed=4)
+    a, b = _pair(p)
+    mv = torch.as_tensor(all_moves(p.B, p.T), device="cuda")
+    for _ in range(3):
+        _compare(a.search_step(mv, k=5, apply=True), _separate(b, mv, 5, True), 5)
+    assert np.array_equal(a.schedule_get(), b.schedule_get())
+
+
+def test_step_nothing_feasible_and_errors():
+    import paper_2511_18296_b300 as mm
+    p = W.config("plain_4k")
+    a, _ = _pair(p)
+    inc = O.OracleModel(p).eval_incremental(p.x0, p.moves)
+    bad = torch.as_tensor(p.moves[inc["flag"] == 0][:500], device="cuda")
+    s, f, idx, top, cnt = a.search_step(bad, k=4, apply=True)
+    torch.cuda.synchronize()
+    assert int(cnt.cpu()[0]) == 0
+    assert a.last_apply()[0] == 0
+    assert np.array_equal(a.schedule_get(), p.x0)
+    with pytest.raises(mm.MMError):
+        a.search_step(bad, k=33)
