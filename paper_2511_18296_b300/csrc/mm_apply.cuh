@@ -81,6 +81,7 @@ struct ApplyArgs {
     double *npv;
     double *contrib;
     float *tab;
+    float *ctab;  // nullptr when the period-pair table is not kept
     const double *disc;
     const uint64_t *cap;
     const uint64_t *target;
@@ -242,6 +243,27 @@ static __device__ __noinline__ void apply_block(const ApplyArgs &A, int2 mv, int
             }
             my_npv = __dadd_rn(my_npv, dnpv);
             A.npv[s] = my_npv;
+        }
+        if (A.ctab) {
+            // period-pair table: rows and columns of the changed periods
+            __syncthreads();  // the new Pout / Pin entries of t1 and t2 are written
+            const uint32_t T = (uint32_t)A.T, T1 = T + 1;
+            const bool c1 = v.t1 < T, c2 = v.t2 < T && v.t2 != v.t1;
+            if (c1 || c2) {
+                const uint32_t ra = c1 ? v.t1 : v.t2, rb = c2 ? v.t2 : ra;
+                const size_t sp = (size_t)A.S_pad, pin = (size_t)T1 * sp;
+                const float *tb = A.tab;
+                for (int j = threadIdx.x; j < (int)T1 * A.S; j += blockDim.x) {
+                    const uint32_t b = (uint32_t)(j / A.S), s2 = (uint32_t)(j - (int)b * A.S);
+                    const float pob = tb[b * sp + s2], pib = tb[pin + b * sp + s2];
+                    const float poa = tb[ra * sp + s2], pia = tb[pin + ra * sp + s2];
+                    const float por = tb[rb * sp + s2], pir = tb[pin + rb * sp + s2];
+                    A.ctab[((size_t)ra * T1 + b) * sp + s2] = poa + pib;
+                    A.ctab[((size_t)b * T1 + ra) * sp + s2] = pob + pia;
+                    A.ctab[((size_t)rb * T1 + b) * sp + s2] = por + pib;
+                    A.ctab[((size_t)b * T1 + rb) * sp + s2] = pob + pir;
+                }
+            }
         }
         if (A.tp.nx == 0) {
             // CSR: the moved blocks first, then every predecessor and successor

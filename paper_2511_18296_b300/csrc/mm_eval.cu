@@ -31,8 +31,8 @@ namespace mm {
 using EvalFn = void (*)(EvalArgs);
 EvalFn pick_tiled_plain(int team, int qmax, bool delta, bool tsm, bool tma);
 EvalFn pick_tiled_kahan(int team, int qmax, bool delta, bool tsm, bool tma);
-EvalFn pick_fast_plain(int team, int kf, bool tail, bool delta, bool tsm);
-EvalFn pick_fast_kahan(int team, int kf, bool tail, bool delta, bool tsm);
+EvalFn pick_fast_plain(int team, int kf, bool tail, bool delta);
+EvalFn pick_fast_kahan(int team, int kf, bool tail, bool delta);
 EvalFn pick_step(int team, bool fast, int kf, bool tail, int qmax, bool tsm);
 ApplyArgs apply_args(mm_model *m);
 
@@ -143,7 +143,7 @@ mm_status eval_launch(mm_model *m, const mm_move *moves, int64_t n, float *score
     A.n = n;
     A.score = score; A.feas = feas; A.mean = mean; A.delta = delta;
     A.val = m->val; A.blk = m->blk; A.mass = m->mass;
-    A.tab = m->tab; A.ddt = m->ddt; A.minedT = m->minedT; A.cap = m->cap;
+    A.tab = m->tab; A.ctab = m->ctab; A.ddt = m->ddt; A.minedT = m->minedT; A.cap = m->cap;
     A.oreT = m->oreT; A.target = m->target; A.disc = m->disc;
     A.status = m->status;
     A.tp.B = m->B; A.tp.T = m->T; A.tp.nx = m->nx; A.tp.ny = m->ny; A.tp.nz = m->nz;
@@ -185,10 +185,16 @@ mm_status eval_launch(mm_model *m, const mm_move *moves, int64_t n, float *score
     const int T1 = m->T + 1;
     const size_t tab_bytes = (size_t)2 * T1 * m->S_pad * sizeof(float);
     const size_t small = (((size_t)T1 * T1 * sizeof(float) + 15) & ~(size_t)15) + 2 * (size_t)T1 * sizeof(int64_t);
-    const bool tsm = tab_bytes <= 64 * 1024;
     if (stages < 0) stages = kDefaultStages;
     if (stages > kMaxStages) stages = kMaxStages;
     const bool tma = stages > 0;
+    // fast form: S % 4 == 0, floor(NQ / team) full quad iterations known at
+    // compile time, period-pair table read from global memory
+    const int kf = nq / team;
+    const bool tail = nq % team != 0;
+    const bool fast_ok = !tma && m->ctab && m->S % 4 == 0 && !(options & MM_EVAL_GENERIC) && kf >= 1 && kf <= 4;
+    // otherwise the Pout / Pin tables are staged in shared memory when small
+    const bool tsm = !fast_ok && tab_bytes <= 64 * 1024;
     A.nstage = stages;
     size_t smem = (tsm ? tab_bytes : 0) + small;
     if (tma) {
@@ -202,16 +208,11 @@ mm_status eval_launch(mm_model *m, const mm_move *moves, int64_t n, float *score
     const bool use_tma = stages > 0;
     A.nstage = stages;
     EvalFn fn = nullptr;
-    const int kf = nq / team;
-    const bool tail = nq % team != 0;
-    const bool fast_ok = !use_tma && m->S % 4 == 0 && !(options & MM_EVAL_GENERIC) && kf >= 1 && kf <= 4;
     if (step) {
         fn = pick_step(team, fast_ok, kf, tail, qmax, tsm);
     } else {
-        // fast form: floor(NQ / team) full quad iterations known at compile time
         if (fast_ok)
-            fn = kahan ? pick_fast_kahan(team, kf, tail, want_delta, tsm)
-                       : pick_fast_plain(team, kf, tail, want_delta, tsm);
+            fn = kahan ? pick_fast_kahan(team, kf, tail, want_delta) : pick_fast_plain(team, kf, tail, want_delta);
         if (!fn)
             fn = kahan ? pick_tiled_kahan(team, qmax, want_delta, tsm, use_tma)
                        : pick_tiled_plain(team, qmax, want_delta, tsm, use_tma);

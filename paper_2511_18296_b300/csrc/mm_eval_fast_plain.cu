@@ -7,30 +7,27 @@ namespace mm {
 using EvalFn = void (*)(EvalArgs);
 
 template <int TEAM, int KF, bool TAIL>
-static EvalFn fast3(bool delta, bool tsm) {
-    if (tsm) return delta ? k_eval_tiled<TEAM, 1, false, true, true, KF, TAIL> : k_eval_tiled<TEAM, 1, false, false, true, KF, TAIL>;
-    if constexpr (TEAM == 32)
-        return delta ? k_eval_tiled<TEAM, 1, false, true, false, KF, TAIL> : k_eval_tiled<TEAM, 1, false, false, false, KF, TAIL>;
-    return nullptr;
+static EvalFn fast3(bool delta) {
+    return delta ? k_eval_tiled<TEAM, 1, false, true, false, KF, TAIL> : k_eval_tiled<TEAM, 1, false, false, false, KF, TAIL>;
 }
 
 template <int TEAM>
-static EvalFn fast2(int kf, bool tail, bool delta, bool tsm) {
+static EvalFn fast2(int kf, bool tail, bool delta) {
     switch (kf) {
-        case 1: return tail ? fast3<TEAM, 1, true>(delta, tsm) : fast3<TEAM, 1, false>(delta, tsm);
-        case 2: return tail ? fast3<TEAM, 2, true>(delta, tsm) : fast3<TEAM, 2, false>(delta, tsm);
-        case 3: return tail ? fast3<TEAM, 3, true>(delta, tsm) : fast3<TEAM, 3, false>(delta, tsm);
-        case 4: return tail ? fast3<TEAM, 4, true>(delta, tsm) : fast3<TEAM, 4, false>(delta, tsm);
+        case 1: return tail ? fast3<TEAM, 1, true>(delta) : fast3<TEAM, 1, false>(delta);
+        case 2: return tail ? fast3<TEAM, 2, true>(delta) : fast3<TEAM, 2, false>(delta);
+        case 3: return tail ? fast3<TEAM, 3, true>(delta) : fast3<TEAM, 3, false>(delta);
+        case 4: return tail ? fast3<TEAM, 4, true>(delta) : fast3<TEAM, 4, false>(delta);
     }
     return nullptr;
 }
 
-EvalFn pick_fast_plain(int team, int kf, bool tail, bool delta, bool tsm) {
+EvalFn pick_fast_plain(int team, int kf, bool tail, bool delta) {
     switch (team) {
-        case 4: return fast2<4>(kf, tail, delta, tsm);
-        case 8: return fast2<8>(kf, tail, delta, tsm);
-        case 16: return fast2<16>(kf, tail, delta, tsm);
-        case 32: return fast2<32>(kf, tail, delta, tsm);
+        case 4: return fast2<4>(kf, tail, delta);
+        case 8: return fast2<8>(kf, tail, delta);
+        case 16: return fast2<16>(kf, tail, delta);
+        case 32: return fast2<32>(kf, tail, delta);
     }
     return nullptr;
 }

@@ -42,6 +42,7 @@ struct EvalArgs {
     const uint32_t *blk;
     const uint32_t *mass;
     const float *tab;
+    const float *ctab;  // [T+1][T+1][S_pad] Pout[a] + Pin[b] (the fast form reads only this)
     const float *ddt;
     const int64_t *minedT;
     const uint64_t *cap;
@@ -287,45 +288,42 @@ __device__ __forceinline__ void team_eval(const EvalArgs &A, const float *tab, c
 // masking), then, if TAIL, one iteration in which only the first
 // NQ - KF * TEAM lanes hold a quad.  d[KF] holds the tail quad.
 template <int TEAM, int KF, bool TAIL, bool SWAP, bool KAHAN>
-__device__ __forceinline__ void team_eval_fast(const EvalArgs &A, const float *tab, const float4 *lut, int tl,
-                                               const float *row1, const float *row2, uint32_t t1, uint32_t t2,
-                                               float dd, int ntail, float invS, size_t pin_off,
-                                               float (&d)[KF + 1][4], float &mu, float &sd) {
+__device__ __forceinline__ void team_eval_fast(const EvalArgs &A, const float4 *lut, int tl, const float *row1,
+                                               const float *row2, uint32_t t1, uint32_t t2, float dd, int ntail,
+                                               float invS, float (&d)[KF + 1][4], float &mu, float &sd) {
     const int S_pad = A.S_pad, ore_off = A.ore_off;
+    const uint32_t T1 = (uint32_t)A.T + 1u;
     const float4 *r1 = reinterpret_cast<const float4 *>(row1) + tl;
     const float4 *r2 = reinterpret_cast<const float4 *>(row2) + tl;
     const uint32_t *w1 = reinterpret_cast<const uint32_t *>(row1 + ore_off);
     const uint32_t *w2 = reinterpret_cast<const uint32_t *>(row2 + ore_off);
-    const float4 *po1 = reinterpret_cast<const float4 *>(tab + (size_t)t1 * S_pad) + tl;
-    const float4 *po2 = reinterpret_cast<const float4 *>(tab + (size_t)t2 * S_pad) + tl;
-    const float4 *pi1 = reinterpret_cast<const float4 *>(tab + pin_off + (size_t)t1 * S_pad) + tl;
-    const float4 *pi2 = reinterpret_cast<const float4 *>(tab + pin_off + (size_t)t2 * S_pad) + tl;
+    // period-pair rows: p12 = Pout[t1] + Pin[t2] (ore leaving t1 for t2), p21 the reverse
+    const float4 *p12 = reinterpret_cast<const float4 *>(A.ctab + ((size_t)t1 * T1 + t2) * S_pad) + tl;
+    const float4 *p21 = reinterpret_cast<const float4 *>(A.ctab + ((size_t)t2 * T1 + t1) * S_pad) + tl;
     float sum = 0.0f, csum = 0.0f;
     auto quad = [&](int k, float (&x)[4]) {
         const int q = tl + k * TEAM;
         const int wi = q >> 3;
         const uint32_t sh = (uint32_t)(q & 7) * 4u;
         const float4 a = __ldg(r1 + k * TEAM);
-        const float4 pa = po1[k * TEAM];
-        const float4 pb = pi2[k * TEAM];
+        const float4 pa = __ldg(p12 + k * TEAM);
         if (SWAP) {
             const float4 b = __ldg(r2 + k * TEAM);
             const uint32_t n1 = (__ldg(w1 + wi) >> sh) & 0xfu;
             const uint32_t n2 = (__ldg(w2 + wi) >> sh) & 0xfu;
             const float4 m1 = lut[n1 & ~n2];
             const float4 m2 = lut[n2 & ~n1];
-            const float4 pc = pi1[k * TEAM];
-            const float4 pd = po2[k * TEAM];
-            x[0] = fmaf(a.x - b.x, dd, fmaf(m2.x, pc.x + pd.x, m1.x * (pa.x + pb.x)));
-            x[1] = fmaf(a.y - b.y, dd, fmaf(m2.y, pc.y + pd.y, m1.y * (pa.y + pb.y)));
-            x[2] = fmaf(a.z - b.z, dd, fmaf(m2.z, pc.z + pd.z, m1.z * (pa.z + pb.z)));
-            x[3] = fmaf(a.w - b.w, dd, fmaf(m2.w, pc.w + pd.w, m1.w * (pa.w + pb.w)));
+            const float4 pb = __ldg(p21 + k * TEAM);
+            x[0] = fmaf(a.x - b.x, dd, fmaf(m2.x, pb.x, m1.x * pa.x));
+            x[1] = fmaf(a.y - b.y, dd, fmaf(m2.y, pb.y, m1.y * pa.y));
+            x[2] = fmaf(a.z - b.z, dd, fmaf(m2.z, pb.z, m1.z * pa.z));
+            x[3] = fmaf(a.w - b.w, dd, fmaf(m2.w, pb.w, m1.w * pa.w));
         } else {
             const float4 m1 = lut[(__ldg(w1 + wi) >> sh) & 0xfu];
-            x[0] = fmaf(a.x, dd, m1.x * (pa.x + pb.x));
-            x[1] = fmaf(a.y, dd, m1.y * (pa.y + pb.y));
-            x[2] = fmaf(a.z, dd, m1.z * (pa.z + pb.z));
-            x[3] = fmaf(a.w, dd, m1.w * (pa.w + pb.w));
+            x[0] = fmaf(a.x, dd, m1.x * pa.x);
+            x[1] = fmaf(a.y, dd, m1.y * pa.y);
+            x[2] = fmaf(a.z, dd, m1.z * pa.z);
+            x[3] = fmaf(a.w, dd, m1.w * pa.w);
         }
     };
     auto acc = [&](const float (&x)[4]) {
@@ -565,11 +563,11 @@ __global__ void __launch_bounds__(kEvalThreads, MM_EVAL_MINB) k_eval_tiled(EvalA
                 const int ntail = NQ - KF * TEAM;
                 float d[KF + 1][4];
                 if (!sw)
-                    team_eval_fast<TEAM, KF, TAIL, false, KAHAN>(A, tab, s_lut, tl, row1, row2, t1, t2, dd, ntail,
-                                                                 invS, pin_off, d, mu, sd);
+                    team_eval_fast<TEAM, KF, TAIL, false, KAHAN>(A, s_lut, tl, row1, row2, t1, t2, dd, ntail, invS,
+                                                                 d, mu, sd);
                 else
-                    team_eval_fast<TEAM, KF, TAIL, true, KAHAN>(A, tab, s_lut, tl, row1, row2, t1, t2, dd, ntail,
-                                                                invS, pin_off, d, mu, sd);
+                    team_eval_fast<TEAM, KF, TAIL, true, KAHAN>(A, s_lut, tl, row1, row2, t1, t2, dd, ntail, invS, d,
+                                                                mu, sd);
                 if (act && DELTA) write_deltas_fast<TEAM, KF>(A, c0 + slot, tl, ntail, d);
             } else {
                 float d[QMAX][4];

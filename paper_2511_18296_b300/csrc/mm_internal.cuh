@@ -16,6 +16,7 @@ namespace mm {
 
 constexpr int kMaxS = 1024;       // scenarios per model
 constexpr int kMaxT = 254;        // periods; the period byte value T means unmined
+constexpr int kCtabMaxT = 64;     // the period-pair table is kept for T <= this
 constexpr int kTopkMax = 1024;    // largest k of mm_topk
 constexpr int kHistBits = 12;     // top-k coarse histogram over the key's top bits
 constexpr int kHistBins = 1 << kHistBits;
@@ -90,6 +91,7 @@ struct mm_model {
     double *npv = nullptr;       // [S]
     double *contrib = nullptr;   // [T][S]    d_t (cash - penalty) per period
     float *tab = nullptr;        // [2][T+1][S_pad]  Pout, Pin
+    float *ctab = nullptr;       // [T+1][T+1][S_pad] Pout[a] + Pin[b] (FP32 sum); T <= kCtabMaxT only
     float *ddt = nullptr;        // [(T+1)*(T+1)]    d_{t'} - d_t  (index t*(T+1)+t')
     double *disc = nullptr;      // [T+1]
     uint64_t *cap = nullptr;     // [T+1]  cap[T] = max

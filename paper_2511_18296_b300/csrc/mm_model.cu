@@ -12,6 +12,8 @@
 //   minedT i64 [T+1], oreT i64 [T+1][S], metal FP64 [T][S], npv FP64 [S]
 //   contrib FP64 [T][S]     d_t (cash_t,s - pen_t,s): NPV_s = sum_t contrib[t][s]
 //   tab   FP32 [2][T+1][S_pad]  NPV change of removing / adding one block of ore
+//   ctab  FP32 [T+1][T+1][S_pad] Pout[a] + Pin[b]: the penalty change of moving one
+//         block of ore from period a to period b (kept while T <= kCtabMaxT)
 //                               in period t, scenario s (uniform block mass)
 #include <cmath>
 #include <cstdarg>
@@ -165,6 +167,16 @@ __global__ void k_tables(int32_t S, int32_t S_pad, int32_t T, const int64_t *__r
     for (int s = threadIdx.x; s < S_pad; s += blockDim.x) table_entry(t, s, S, S_pad, T, oreT, target, disc, m, a, e, tab);
 }
 
+// ctab[a][b][s] = Pout[a][s] + Pin[b][s], the FP32 sum the evaluator would form.
+__global__ void k_ctab(int32_t S_pad, int32_t T, const float *__restrict__ tab, float *__restrict__ ctab) {
+    const int T1 = T + 1;
+    const int a = blockIdx.x / T1, b = blockIdx.x % T1;
+    const float *po = tab + (int64_t)a * S_pad;
+    const float *pi = tab + (int64_t)T1 * S_pad + (int64_t)b * S_pad;
+    float *dst = ctab + (int64_t)blockIdx.x * S_pad;
+    for (int s = threadIdx.x; s < S_pad; s += blockDim.x) dst[s] = po[s] + pi[s];
+}
+
 // contrib[t][s] for every period, and NPV_s = their sum in period order.
 __global__ void k_npv(int32_t S, int32_t T, const double *__restrict__ disc, const double *__restrict__ metal,
                       const int64_t *__restrict__ oreT, const int64_t *__restrict__ minedT,
@@ -209,7 +221,10 @@ mm_status rebuild_tables(mm_model *m) {
     if (!m->uniform_mass) return MM_OK;
     k_tables<<<m->T + 1, 128, 0, m->stream>>>(m->S, m->S_pad, m->T, m->oreT, m->target, m->disc, (int64_t)m->m_uniform,
                                               m->shortfall_pen, m->excess_pen, m->tab);
-    return check_launch("k_tables");
+    mm_status st = check_launch("k_tables");
+    if (st != MM_OK || !m->ctab) return st;
+    k_ctab<<<(m->T + 1) * (m->T + 1), 128, 0, m->stream>>>(m->S_pad, m->T, m->tab, m->ctab);
+    return check_launch("k_ctab");
 }
 
 ApplyArgs apply_args(mm_model *m) {
@@ -220,6 +235,7 @@ ApplyArgs apply_args(mm_model *m) {
     A.mass = m->mass; A.val = m->val; A.grade = m->grade; A.blk = m->blk;
     A.minedT = m->minedT; A.oreT = m->oreT; A.metal = m->metal; A.npv = m->npv; A.contrib = m->contrib;
     A.tab = m->tab;
+    A.ctab = m->ctab;
     A.disc = m->disc; A.cap = m->cap; A.target = m->target;
     A.pr = m->price * m->recovery; A.pc = m->proc_cost; A.mc = m->mining_cost;
     A.a = m->shortfall_pen; A.e = m->excess_pen;
@@ -228,9 +244,10 @@ ApplyArgs apply_args(mm_model *m) {
     return A;
 }
 
-static int apply_threads(int S) {
-    int t = ((S + 31) / 32) * 32;
+static int apply_threads(const mm_model *m) {
+    int t = ((m->S + 31) / 32) * 32;
     if (t < 64) t = 64;
+    if (m->ctab && t < 512) t = 512;  // the period-pair rows are rebuilt by the whole CTA
     if (t > 1024) t = 1024;
     return t;
 }
@@ -263,6 +280,7 @@ void mm_model_destroy(mm_model *m) {
     cudaFree(m->order); cudaFree(m->porder);
     cudaFree(m->minedT); cudaFree(m->oreT); cudaFree(m->metal); cudaFree(m->npv); cudaFree(m->contrib);
     cudaFree(m->tab);
+    cudaFree(m->ctab);
     cudaFree(m->ddt); cudaFree(m->disc); cudaFree(m->cap); cudaFree(m->target); cudaFree(m->status);
     cudaFree(m->apply_res);
     cudaFree(m->step_cta);
@@ -368,6 +386,7 @@ mm_status mm_model_create(const mm_model_desc *d, mm_model **out) {
     ALLOC(npv, S);
     ALLOC(contrib, (int64_t)T * S);
     ALLOC(tab, (int64_t)2 * (T + 1) * m->S_pad);
+    if (T <= kCtabMaxT && m->uniform_mass) ALLOC(ctab, (int64_t)(T + 1) * (T + 1) * m->S_pad);
     ALLOC(ddt, (int64_t)(T + 1) * (T + 1));
     ALLOC(disc, T + 1);
     ALLOC(cap, T + 1);
@@ -533,7 +552,7 @@ mm_status mm_apply_move(mm_model *m, mm_move mv, double *mean, double *sd) {
     if (!m) return set_error(MM_ERR_INVALID_ARG, "NULL model");
     if (!m->has_schedule) return set_error(MM_ERR_STATE, "no schedule installed");
     ApplyArgs A = apply_args(m);
-    k_apply<<<1, apply_threads(m->S), 0, m->stream>>>(A, make_int2(mv.b1, mv.arg), nullptr, 0, nullptr, nullptr, 0);
+    k_apply<<<1, apply_threads(m), 0, m->stream>>>(A, make_int2(mv.b1, mv.arg), nullptr, 0, nullptr, nullptr, 0);
     mm_status st = check_launch("k_apply");
     if (st != MM_OK) return st;
     MM_CUDA_TRY(cudaMemcpyAsync(m->apply_res_host, m->apply_res, sizeof(ApplyResult), cudaMemcpyDeviceToHost, m->stream),
@@ -553,7 +572,7 @@ mm_status mm_apply_best(mm_model *m, const mm_move *moves, int64_t n, const int3
     if (n < 0) return set_error(MM_ERR_INVALID_ARG, "negative move count");
     if (!m->has_schedule) return set_error(MM_ERR_STATE, "no schedule installed");
     ApplyArgs A = apply_args(m);
-    k_apply<<<1, apply_threads(m->S), 0, m->stream>>>(A, make_int2(0, 0), (const int2 *)moves, n, idx, count, 1);
+    k_apply<<<1, apply_threads(m), 0, m->stream>>>(A, make_int2(0, 0), (const int2 *)moves, n, idx, count, 1);
     return check_launch("k_apply");
 }
 

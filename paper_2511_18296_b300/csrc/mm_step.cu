@@ -9,19 +9,17 @@ using EvalFn = void (*)(EvalArgs);
 ApplyArgs apply_args(mm_model *m);
 
 template <int TEAM, int KF, bool TAIL>
-static EvalFn step_fast3(bool tsm) {
-    if (tsm) return k_eval_tiled<TEAM, 1, false, false, true, KF, TAIL, true>;
-    if constexpr (TEAM == 32) return k_eval_tiled<TEAM, 1, false, false, false, KF, TAIL, true>;
-    return nullptr;
+static EvalFn step_fast3() {
+    return k_eval_tiled<TEAM, 1, false, false, false, KF, TAIL, true>;
 }
 
 template <int TEAM>
-static EvalFn step_fast2(int kf, bool tail, bool tsm) {
+static EvalFn step_fast2(int kf, bool tail) {
     switch (kf) {
-        case 1: return tail ? step_fast3<TEAM, 1, true>(tsm) : step_fast3<TEAM, 1, false>(tsm);
-        case 2: return tail ? step_fast3<TEAM, 2, true>(tsm) : step_fast3<TEAM, 2, false>(tsm);
-        case 3: return tail ? step_fast3<TEAM, 3, true>(tsm) : step_fast3<TEAM, 3, false>(tsm);
-        case 4: return tail ? step_fast3<TEAM, 4, true>(tsm) : step_fast3<TEAM, 4, false>(tsm);
+        case 1: return tail ? step_fast3<TEAM, 1, true>() : step_fast3<TEAM, 1, false>();
+        case 2: return tail ? step_fast3<TEAM, 2, true>() : step_fast3<TEAM, 2, false>();
+        case 3: return tail ? step_fast3<TEAM, 3, true>() : step_fast3<TEAM, 3, false>();
+        case 4: return tail ? step_fast3<TEAM, 4, true>() : step_fast3<TEAM, 4, false>();
     }
     return nullptr;
 }
@@ -46,10 +44,10 @@ static EvalFn step_gen1(int qmax, bool tsm) {
 EvalFn pick_step(int team, bool fast, int kf, bool tail, int qmax, bool tsm) {
     if (fast) {
         switch (team) {
-            case 4: return step_fast2<4>(kf, tail, tsm);
-            case 8: return step_fast2<8>(kf, tail, tsm);
-            case 16: return step_fast2<16>(kf, tail, tsm);
-            case 32: return step_fast2<32>(kf, tail, tsm);
+            case 4: return step_fast2<4>(kf, tail);
+            case 8: return step_fast2<8>(kf, tail);
+            case 16: return step_fast2<16>(kf, tail);
+            case 32: return step_fast2<32>(kf, tail);
         }
         return nullptr;
     }
