@@ -75,6 +75,7 @@ SIGNATURES = [
     ("mm_topk", C.c_int, [P, P, P, I64, I32, P, P, P]),
     ("mm_topk_noalloc", C.c_int, [P, P, I64, I32, P, P, P, P]),
     ("mm_search_step", C.c_int, [P, P, I64, I32, I32, P, P, P, P, P]),
+    ("mm_set_step_event", C.c_int, [P, P]),
     ("mm_apply_move", C.c_int, [P, MMMove, P, P]),
     ("mm_apply_best", C.c_int, [P, P, I64, P, P]),
     ("mm_last_apply", C.c_int, [P, P, P, P]),
@@ -264,6 +265,18 @@ class Model:
         _check(lib().mm_search_step(self.h, _ptr(moves), n, k, 1 if apply else 0, _ptr(score), _ptr(feas), _ptr(idx),
                                     _ptr(top), _ptr(count)))
         return score, feas, idx, top, count
+
+    def set_step_event(self, event=None):
+        """Timing hook: record `event` (a timing-enabled torch.cuda.Event that
+        has been recorded once, or a raw cudaEvent_t) between the two launches
+        of every later search_step; None turns it off."""
+        h = None
+        if event is not None:
+            h = event.cuda_event if hasattr(event, "cuda_event") else int(event)
+            if not h:
+                raise ValueError("the event has no CUDA handle yet (record it once first)")
+        self._step_event = event  # keep the caller's event alive while it is in use
+        _check(lib().mm_set_step_event(self.h, h))
 
     # -- apply ----------------------------------------------------------
     def apply_move(self, move) -> Tuple[float, float]:

@@ -416,7 +416,7 @@ __device__ __forceinline__ void prefetch_row(const float *row, uint32_t row_byte
 // warps' lists (skipping lists that cannot contribute) and publishes the
 // CTA's 32 best keys.  Every key of the batch's top k is among the 32 best of
 // the CTA that evaluated it; k_step_finish selects from these lists.
-__device__ __forceinline__ void step_publish(const EvalArgs &A, uint64_t wtk) {
+__device__ __forceinline__ void step_publish(uint64_t *lists, uint64_t wtk) {
     constexpr int NW = kEvalThreads / 32;
     __shared__ uint64_t s_wtk[NW][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -425,7 +425,7 @@ __device__ __forceinline__ void step_publish(const EvalArgs &A, uint64_t wtk) {
     if (warp == 0) {
         uint64_t t = s_wtk[0][lane];
         for (int w = 1; w < NW; w++) t = warp_topk_merge(t, s_wtk[w][lane]);
-        A.step_cta[(size_t)blockIdx.x * 32 + lane] = t;
+        lists[(size_t)blockIdx.x * 32 + lane] = t;
     }
 }
 
@@ -605,7 +605,7 @@ __global__ void __launch_bounds__(kEvalThreads, MM_EVAL_MINB) k_eval_tiled(EvalA
         }
         __syncwarp();
     }
-    if constexpr (TOPK) step_publish(A, wtk);
+    if constexpr (TOPK) step_publish(A.step_cta, wtk);
 }
 
 // ----------------------------------------------------------------------------

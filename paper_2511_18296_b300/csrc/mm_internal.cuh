@@ -103,6 +103,7 @@ struct mm_model {
     mm::TopkScratch topk;
     uint64_t *step_cta = nullptr;    // fused search step: [step_max_ctas][32] published keys
     int step_max_ctas = 0;
+    void *step_event = nullptr;      // cudaEvent_t recorded between the step's two launches (timing hook)
 };
 
 namespace mm {
@@ -126,6 +127,9 @@ struct StepOut {
 mm_status eval_launch(mm_model *m, const mm_move *moves, int64_t n, float *score, uint8_t *feas, float *mean,
                       float *delta, int32_t options, int team, int ctas_per_sm, int stages, const StepOut *step);
 int default_team(int S);
+// Top-k for k <= 32 through per-CTA warp lists and the step finisher.
+mm_status topk_small_launch(mm_model *m, const float *score, const uint8_t *feas, int64_t n, int32_t k, int32_t *idx,
+                            float *top, int32_t *count);
 mm_status topk_launch(const float *score, const uint8_t *feas, int64_t n, int32_t k, int32_t *idx,
                       float *top, int32_t *count, TopkScratch &scr, int num_sms, cudaStream_t st);
 mm_status topk_scratch_reserve(TopkScratch &scr, int64_t n);

@@ -137,6 +137,59 @@ __global__ void __launch_bounds__(1024) k_step_finish(StepFinishArgs F, ApplyArg
     }
 }
 
+// Standalone top-k for k <= 32: the same per-CTA lists as the fused step,
+// built from stored scores and flags (four 32-key rounds in flight per warp).
+__global__ void __launch_bounds__(kEvalThreads) k_topk_lists(const float *__restrict__ score,
+                                                             const uint8_t *__restrict__ feas, int64_t n,
+                                                             uint64_t *__restrict__ lists) {
+    constexpr int NW = kEvalThreads / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t nwarps = (int64_t)gridDim.x * NW, gw = (int64_t)blockIdx.x * NW + warp;
+    const int64_t r0 = gw * n / nwarps, r1 = (gw + 1) * n / nwarps;
+    uint64_t wtk = 0;
+    for (int64_t c = r0; c < r1; c += 4 * 32) {
+        float f[4];
+        uint8_t ok[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const int64_t i = c + u * 32 + lane;
+            ok[u] = i < r1 ? __ldg(feas + i) : 0;
+            f[u] = i < r1 ? __ldg(score + i) : 0.0f;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const int64_t i = c + u * 32 + lane;
+            wtk = warp_topk_insert(wtk, (ok[u] && !isnan(f[u])) ? score_key(f[u], i) : 0ull);
+        }
+    }
+    step_publish(lists, wtk);
+}
+
+mm_status topk_small_launch(mm_model *m, const float *score, const uint8_t *feas, int64_t n, int32_t k, int32_t *idx,
+                            float *top, int32_t *count) {
+    int64_t blocks = (n + 2047) / 2048;
+    if (blocks > (int64_t)m->num_sms * 2) blocks = (int64_t)m->num_sms * 2;
+    if (blocks > m->step_max_ctas) blocks = m->step_max_ctas;
+    if (blocks < 1) blocks = 1;
+    k_topk_lists<<<(unsigned)blocks, kEvalThreads, 0, m->stream>>>(score, feas, n, m->step_cta);
+    mm_status st = check_launch("k_topk_lists");
+    if (st != MM_OK) return st;
+    StepFinishArgs F;
+    F.keys = m->step_cta;
+    F.nkeys = (int32_t)blocks * 32;
+    F.n = n;
+    F.status = m->status;
+    F.k = k;
+    F.do_apply = 0;
+    F.score = score;
+    F.moves = nullptr;
+    F.idx_out = idx;
+    F.top_out = top;
+    F.count_out = count;
+    k_step_finish<<<1, 1024, 0, m->stream>>>(F, apply_args(m));
+    return check_launch("k_step_finish");
+}
+
 }  // namespace mm
 
 using namespace mm;
@@ -165,6 +218,14 @@ extern "C" mm_status mm_search_step(mm_model *m, const mm_move *moves, int64_t n
     StepOut so{k, apply ? 1 : 0, idx, top, count, 0};
     st = eval_launch(m, moves, n, score, feas, nullptr, nullptr, MM_EVAL_PLAIN, m->team, m->ctas_per_sm, 0, &so);
     if (st != MM_OK) return st;
+    if (m->step_event) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        MM_CUDA_TRY(cudaStreamIsCapturing(m->stream, &cs), "query stream capture");
+        cudaEvent_t ev = static_cast<cudaEvent_t>(m->step_event);
+        MM_CUDA_TRY(cs == cudaStreamCaptureStatusActive ? cudaEventRecordWithFlags(ev, m->stream, cudaEventRecordExternal)
+                                                        : cudaEventRecord(ev, m->stream),
+                    "record the step event");
+    }
     StepFinishArgs F;
     F.keys = m->step_cta;
     F.nkeys = so.grid * 32;
@@ -179,4 +240,10 @@ extern "C" mm_status mm_search_step(mm_model *m, const mm_move *moves, int64_t n
     F.count_out = count;
     k_step_finish<<<1, 1024, 0, m->stream>>>(F, apply_args(m));
     return check_launch("k_step_finish");
+}
+
+extern "C" mm_status mm_set_step_event(mm_model *m, void *cuda_event) {
+    if (!m) return set_error(MM_ERR_INVALID_ARG, "NULL model");
+    m->step_event = cuda_event;
+    return MM_OK;
 }

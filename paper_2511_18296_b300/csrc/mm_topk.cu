@@ -293,6 +293,7 @@ extern "C" mm_status mm_topk(mm_model *m, const float *score, const uint8_t *fea
     if (k < 1 || k > kTopkMax) return set_error(MM_ERR_INVALID_ARG, "k = %d outside 1..%d", k, kTopkMax);
     if (!count || (n > 0 && (!score || !feas || !idx || !top)))
         return set_error(MM_ERR_INVALID_ARG, "NULL pointer");
+    if (k <= 32 && n > 0) return topk_small_launch(m, score, feas, n, k, idx, top, count);
     mm_status st = topk_scratch_reserve(m->topk, n);
     if (st != MM_OK) return st;
     return topk_launch(score, feas, n, k, idx, top, count, m->topk, m->num_sms, m->stream);

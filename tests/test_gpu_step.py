@@ -107,3 +107,46 @@ def test_step_nothing_feasible_and_errors():
     assert np.array_equal(a.schedule_get(), p.x0)
     with pytest.raises(mm.MMError):
         a.search_step(bad, k=33)
+
+
+def test_step_event_splits_the_two_launches():
+    """The timing hook records the caller's event between the evaluation and
+    the finisher, eagerly and as an external node of a captured graph; the
+    step's results do not change."""
+    p = W.config("plain_4k")
+    a, b = _pair(p)
+    st = torch.cuda.Stream()
+    a.set_stream(st)
+    mv = torch.as_tensor(p.moves, device="cuda")
+    out = [torch.empty(p.moves.shape[0], device="cuda"), torch.empty(p.moves.shape[0], dtype=torch.uint8, device="cuda"),
+           torch.empty(32, dtype=torch.int32, device="cuda"), torch.empty(32, device="cuda"),
+           torch.empty(1, dtype=torch.int32, device="cuda")]
+    mid = torch.cuda.Event(enable_timing=True)
+    with pytest.raises(ValueError):
+        a.set_step_event(mid)  # not recorded yet: no handle
+    mid.record(st)
+    a.set_step_event(mid)
+
+    def step():
+        a.search_step(mv, k=32, apply=True, score=out[0], feas=out[1], idx=out[2], top=out[3], count=out[4])
+
+    with torch.cuda.stream(st):
+        step()  # eager
+    st.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=st):
+        step()
+    a.set_step_event(None)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(st):
+        e0.record(st)
+        g.replay()
+        e1.record(st)
+    e1.synchronize()
+    t_eval, t_fin = e0.elapsed_time(mid), mid.elapsed_time(e1)
+    assert t_eval > 0 and t_fin > 0 and t_eval + t_fin == pytest.approx(e0.elapsed_time(e1), rel=1e-3, abs=1e-3)
+    # two steps through the hook agree with two plain steps
+    for _ in range(2):
+        rb = b.search_step(mv, k=32, apply=True)
+    _compare(out, rb, 32)
+    assert np.array_equal(a.schedule_get(), b.schedule_get())
