@@ -244,7 +244,7 @@ __device__ __forceinline__ void team_eval(const EvalArgs &A, const float *tab, c
 #pragma unroll
             for (int j = 0; j < 4; j++) comp_add(sum, csum, d[k][j]);
         } else {
-            sum += (d[k][0] + d[k][1]) + (d[k][2] + d[k][3]);
+            sum += (d[k][0] + d[k][2]) + (d[k][1] + d[k][3]);  // the fast form's order
         }
     }
     if (KAHAN) {
@@ -282,6 +282,39 @@ __device__ __forceinline__ void team_eval(const EvalArgs &A, const float *tab, c
     sd = sqrtf(var * invS);
 }
 
+// Two FP32 values in one 64-bit register pair and the sm_100-family paired
+// instructions on them.  Each lane of fma.rn / mul.rn / add.rn / sub.rn .f32x2
+// is rounded exactly like the scalar instruction, so paired and scalar code
+// give the same bits; the pairing halves the issued arithmetic instructions.
+__device__ __forceinline__ uint64_t f2_pack(float lo, float hi) {
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void f2_unpack(uint64_t r, float &lo, float &hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(r));
+}
+__device__ __forceinline__ uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c) {
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ uint64_t f2_mul(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t f2_add(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t f2_sub(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
 // Fast form of team_eval for S % 4 == 0: the team runs KF = floor(NQ / TEAM)
 // full quad iterations, fixed at compile time (every lane of every team owns
 // a real quad, offsets are compile-time immediates from per-lane bases, no
@@ -301,6 +334,7 @@ __device__ __forceinline__ void team_eval_fast(const EvalArgs &A, const float4 *
     const float4 *p12 = reinterpret_cast<const float4 *>(A.ctab + ((size_t)t1 * T1 + t2) * S_pad) + tl;
     const float4 *p21 = reinterpret_cast<const float4 *>(A.ctab + ((size_t)t2 * T1 + t1) * S_pad) + tl;
     float sum = 0.0f, csum = 0.0f;
+    const uint64_t dd2 = f2_pack(dd, dd);
     auto quad = [&](int k, float (&x)[4]) {
         const int q = tl + k * TEAM;
         const int wi = q >> 3;
@@ -314,16 +348,22 @@ __device__ __forceinline__ void team_eval_fast(const EvalArgs &A, const float4 *
             const float4 m1 = lut[n1 & ~n2];
             const float4 m2 = lut[n2 & ~n1];
             const float4 pb = __ldg(p21 + k * TEAM);
-            x[0] = fmaf(a.x - b.x, dd, fmaf(m2.x, pb.x, m1.x * pa.x));
-            x[1] = fmaf(a.y - b.y, dd, fmaf(m2.y, pb.y, m1.y * pa.y));
-            x[2] = fmaf(a.z - b.z, dd, fmaf(m2.z, pb.z, m1.z * pa.z));
-            x[3] = fmaf(a.w - b.w, dd, fmaf(m2.w, pb.w, m1.w * pa.w));
+            // x = (a - b) dd + (m2 pb + m1 pa), scenario by scenario, in pairs
+            const uint64_t lo = f2_fma(f2_sub(f2_pack(a.x, a.y), f2_pack(b.x, b.y)), dd2,
+                                       f2_fma(f2_pack(m2.x, m2.y), f2_pack(pb.x, pb.y),
+                                              f2_mul(f2_pack(m1.x, m1.y), f2_pack(pa.x, pa.y))));
+            const uint64_t hi = f2_fma(f2_sub(f2_pack(a.z, a.w), f2_pack(b.z, b.w)), dd2,
+                                       f2_fma(f2_pack(m2.z, m2.w), f2_pack(pb.z, pb.w),
+                                              f2_mul(f2_pack(m1.z, m1.w), f2_pack(pa.z, pa.w))));
+            f2_unpack(lo, x[0], x[1]);
+            f2_unpack(hi, x[2], x[3]);
         } else {
             const float4 m1 = lut[(__ldg(w1 + wi) >> sh) & 0xfu];
-            x[0] = fmaf(a.x, dd, m1.x * pa.x);
-            x[1] = fmaf(a.y, dd, m1.y * pa.y);
-            x[2] = fmaf(a.z, dd, m1.z * pa.z);
-            x[3] = fmaf(a.w, dd, m1.w * pa.w);
+            // x = a dd + m1 pa
+            const uint64_t lo = f2_fma(f2_pack(a.x, a.y), dd2, f2_mul(f2_pack(m1.x, m1.y), f2_pack(pa.x, pa.y)));
+            const uint64_t hi = f2_fma(f2_pack(a.z, a.w), dd2, f2_mul(f2_pack(m1.z, m1.w), f2_pack(pa.z, pa.w)));
+            f2_unpack(lo, x[0], x[1]);
+            f2_unpack(hi, x[2], x[3]);
         }
     };
     auto acc = [&](const float (&x)[4]) {
@@ -331,7 +371,10 @@ __device__ __forceinline__ void team_eval_fast(const EvalArgs &A, const float4 *
 #pragma unroll
             for (int j = 0; j < 4; j++) comp_add(sum, csum, x[j]);
         } else {
-            sum += (x[0] + x[1]) + (x[2] + x[3]);
+            // (x0 + x2) + (x1 + x3), the first level as one paired add
+            float u, v;
+            f2_unpack(f2_add(f2_pack(x[0], x[1]), f2_pack(x[2], x[3])), u, v);
+            sum += u + v;
         }
     };
 #pragma unroll
@@ -352,12 +395,15 @@ __device__ __forceinline__ void team_eval_fast(const EvalArgs &A, const float4 *
         mu = team_sum<TEAM>(sum) * invS;
     }
     float var = 0.0f, cvar = 0.0f;
+    const uint64_t mu2 = f2_pack(mu, mu);
     auto vacc = [&](const float (&x)[4]) {
+        float dv[4];
+        f2_unpack(f2_sub(f2_pack(x[0], x[1]), mu2), dv[0], dv[1]);
+        f2_unpack(f2_sub(f2_pack(x[2], x[3]), mu2), dv[2], dv[3]);
 #pragma unroll
         for (int j = 0; j < 4; j++) {
-            const float dv = x[j] - mu;
-            if (KAHAN) comp_add(var, cvar, dv * dv);
-            else var = fmaf(dv, dv, var);
+            if (KAHAN) comp_add(var, cvar, dv[j] * dv[j]);
+            else var = fmaf(dv[j], dv[j], var);
         }
     };
 #pragma unroll

@@ -86,6 +86,18 @@ __global__ void __launch_bounds__(1024) k_step_finish(StepFinishArgs F, ApplyArg
     __shared__ int s_best;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nw = blockDim.x >> 5;  // 32
+    if (F.do_apply) {
+        // the apply's per-period state was evicted by the evaluation's row
+        // traffic: pull it back into L2 while the lists are merged
+        const size_t ts = (size_t)AP.T * AP.S;
+        const size_t tab_bytes = (size_t)2 * (AP.T + 1) * AP.S_pad * sizeof(float);
+        const char *regions[5] = {(const char *)AP.oreT, (const char *)AP.metal, (const char *)AP.contrib,
+                                  (const char *)AP.tab, (const char *)AP.npv};
+        const size_t bytes[5] = {ts * 8, ts * 8, ts * 8, tab_bytes, (size_t)AP.S * 8};
+        for (int r = 0; r < 5; r++)
+            for (size_t o = (size_t)tid * 128; o < bytes[r]; o += (size_t)blockDim.x * 128)
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(regions[r] + o));
+    }
     const int nlists = F.nkeys / 32;
     uint64_t t = 0;
     for (int l0 = warp; l0 < nlists; l0 += 4 * nw) {
