@@ -191,6 +191,66 @@ mm_status mm_search_step(mm_model *m, const mm_move *moves_dev, int64_t n, int32
  * NULL turns the hook off.  A failed record is MM_ERR_CUDA. */
 mm_status mm_set_step_event(mm_model *m, void *cuda_event);
 
+/* ---- Batched multi-chain evaluation (many search chains, one launch) ----
+ *
+ * The paper's search runs a population of independent chains (Table 3: a
+ * population of 100; Section 6's candidate chunks).  A batch evaluates one
+ * move batch per chain -- chains with different block models, scenario counts
+ * and batch sizes -- in ONE persistent launch fed by a device work queue of
+ * (chain, move range) items, each chain's result exactly what mm_search_step
+ * gives for that chain alone (scores, flags, top k; the best move applied when
+ * apply != 0; the chain runs with the team width the single-model path picks
+ * by default, whatever mm_set_tile says).
+ *
+ * A chain names its model (schedule installed, equal block masses, T <= 64;
+ * S <= 256 when applying; no two chains share a model) and the caller's device
+ * buffers: moves_dev[n_moves], score_dev[n_moves], feasible_dev[n_moves],
+ * idx_dev[k], topscore_dev[k], count_dev[1].  The buffers are fixed at
+ * creation; a caller changes a chain's moves by rewriting moves_dev (n_moves is
+ * fixed).  The batch owns its queue and list storage (allocated at creation and
+ * on a tile change).  mm_batch_run is asynchronous on cuda_stream, allocates
+ * nothing and never synchronises, so it can be captured into a CUDA graph;
+ * work on the chains' own model streams must be ordered before it by the
+ * caller.  Bad moves: feasible = 0 and the chain's model raises its sticky
+ * MM_ERR_BAD_MOVE.  There are no device-side waits (each chain is finished by
+ * the CTA that completes its last item, by ticket). */
+typedef struct {
+    mm_model *model;
+    const mm_move *moves_dev;
+    int64_t n_moves;
+    float *score_dev;
+    uint8_t *feasible_dev;
+    int32_t *idx_dev;
+    float *topscore_dev;
+    int32_t *count_dev;
+} mm_chain;
+
+typedef struct mm_batch mm_batch;
+
+/* 1 <= k <= 32.  MM_ERR_INVALID_ARG / MM_ERR_STATE on a chain that breaks the
+ * rules above (the message names the chain), MM_ERR_CUDA on allocation. */
+mm_status mm_batch_create(const mm_chain *chains, int32_t n_chains, int32_t k, int32_t apply,
+                          void *cuda_stream, mm_batch **out);
+void      mm_batch_destroy(mm_batch *b);
+
+/* One evaluation of every chain (plus the applies): asynchronous. */
+mm_status mm_batch_run(mm_batch *b);
+
+/* Tile shape: moves per queue item (a multiple of 64) and resident CTAs per SM
+ * of the persistent grid (0 = the occupancy maximum).  Rebuilds the queue
+ * (synchronous; not while a run or a graph replay is in flight). */
+mm_status mm_batch_set_tile(mm_batch *b, int32_t moves_per_item, int32_t ctas_per_sm);
+mm_status mm_batch_get_tile(const mm_batch *b, int32_t *moves_per_item, int32_t *ctas_per_sm,
+                            int32_t *n_items);
+
+/* Autotuner: times `reps` runs of every candidate tile shape (moves per item
+ * 512 .. 16384 x CTAs per SM {max, max - 1}) with CUDA events on the batch's
+ * stream, keeps the fastest and returns it (outputs may be NULL).  Synchronous;
+ * only for batches created with apply = 0 (MM_ERR_STATE otherwise), since it
+ * runs the batch many times. */
+mm_status mm_batch_autotune(mm_batch *b, int32_t reps, int32_t *moves_per_item, int32_t *ctas_per_sm,
+                            float *best_ms);
+
 /* mm_topk for callers that must not allocate device memory, such as code
  * that runs while a CUDA stream is being captured into a graph (cudaMalloc may
  * not be called then), code that owns a fixed memory budget or pool and must

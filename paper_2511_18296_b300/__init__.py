@@ -59,6 +59,12 @@ class MMMove(C.Structure):
     _fields_ = [("b1", C.c_int32), ("arg", C.c_int32)]
 
 
+class MMChain(C.Structure):
+    _fields_ = [("model", C.c_void_p), ("moves_dev", C.c_void_p), ("n_moves", C.c_int64),
+                ("score_dev", C.c_void_p), ("feasible_dev", C.c_void_p), ("idx_dev", C.c_void_p),
+                ("topscore_dev", C.c_void_p), ("count_dev", C.c_void_p)]
+
+
 _lib = None
 
 # (name, restype, argtypes): every entry point declared in include/mm.h
@@ -76,6 +82,12 @@ SIGNATURES = [
     ("mm_topk_noalloc", C.c_int, [P, P, I64, I32, P, P, P, P]),
     ("mm_search_step", C.c_int, [P, P, I64, I32, I32, P, P, P, P, P]),
     ("mm_set_step_event", C.c_int, [P, P]),
+    ("mm_batch_create", C.c_int, [P, I32, I32, I32, P, P]),
+    ("mm_batch_destroy", None, [P]),
+    ("mm_batch_run", C.c_int, [P]),
+    ("mm_batch_set_tile", C.c_int, [P, I32, I32]),
+    ("mm_batch_get_tile", C.c_int, [P, P, P, P]),
+    ("mm_batch_autotune", C.c_int, [P, I32, P, P, P]),
     ("mm_apply_move", C.c_int, [P, MMMove, P, P]),
     ("mm_apply_best", C.c_int, [P, P, I64, P, P]),
     ("mm_last_apply", C.c_int, [P, P, P, P]),
@@ -324,3 +336,62 @@ class Model:
         m = np.zeros((self.T, self.S), np.float64)
         _check(lib().mm_get_metal(self.h, m.ctypes.data))
         return m
+
+
+class Batch:
+    """Many chains evaluated in one persistent launch (mm_batch_*).
+
+    chains: list of (model, moves) with moves an int32 [n, 2] CUDA tensor; the
+    batch allocates each chain's outputs (score, feas, idx, top, count) and
+    keeps references to every buffer it was given."""
+
+    def __init__(self, chains, k: int = 32, apply: bool = False, stream=None):
+        import torch
+        self.k = k
+        self.models = [m for m, _ in chains]
+        self.moves = [mv for _, mv in chains]
+        self.out = []
+        arr = (MMChain * len(chains))()
+        for i, (m, mv) in enumerate(chains):
+            n = int(mv.shape[0])
+            dev = mv.device
+            o = dict(score=torch.empty(n, dtype=torch.float32, device=dev),
+                     feas=torch.empty(n, dtype=torch.uint8, device=dev),
+                     idx=torch.empty(k, dtype=torch.int32, device=dev),
+                     top=torch.empty(k, dtype=torch.float32, device=dev),
+                     count=torch.empty(1, dtype=torch.int32, device=dev))
+            self.out.append(o)
+            mh = m.h.value if isinstance(m.h, C.c_void_p) else m.h
+            arr[i] = MMChain(mh, _ptr(mv), n, _ptr(o["score"]), _ptr(o["feas"]), _ptr(o["idx"]), _ptr(o["top"]),
+                             _ptr(o["count"]))
+        self.stream = stream
+        h = C.c_void_p()
+        _check(lib().mm_batch_create(arr, len(chains), k, 1 if apply else 0, _stream_handle(stream), C.byref(h)))
+        self.h = h
+
+    def run(self):
+        _check(lib().mm_batch_run(self.h))
+
+    def set_tile(self, moves_per_item: int, ctas_per_sm: int = 0):
+        _check(lib().mm_batch_set_tile(self.h, moves_per_item, ctas_per_sm))
+
+    def tile(self):
+        a, b, c = C.c_int32(), C.c_int32(), C.c_int32()
+        _check(lib().mm_batch_get_tile(self.h, C.byref(a), C.byref(b), C.byref(c)))
+        return a.value, b.value, c.value
+
+    def autotune(self, reps: int = 3):
+        a, b, ms = C.c_int32(), C.c_int32(), C.c_float()
+        _check(lib().mm_batch_autotune(self.h, reps, C.byref(a), C.byref(b), C.byref(ms)))
+        return a.value, b.value, ms.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().mm_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -136,8 +136,10 @@ int default_team(int S) {
     return 32;
 }
 
-mm_status eval_launch(mm_model *m, const mm_move *moves, int64_t n, float *score, uint8_t *feas, float *mean,
-                      float *delta, int32_t options, int team, int ctas_per_sm, int stages, const StepOut *step) {
+// Evaluator arguments for a batch of n moves on model m (the step fields
+// cleared).
+EvalArgs eval_args(mm_model *m, const mm_move *moves, int64_t n, float *score, uint8_t *feas, float *mean,
+                   float *delta) {
     EvalArgs A;
     A.moves = reinterpret_cast<const int2 *>(moves);
     A.n = n;
@@ -157,6 +159,12 @@ mm_status eval_launch(mm_model *m, const mm_move *moves, int64_t n, float *score
     A.qpl = 0;
     A.k = 0; A.do_apply = 0; A.idx_out = nullptr; A.top_out = nullptr; A.count_out = nullptr;
     A.step_cta = m->step_cta;
+    return A;
+}
+
+mm_status eval_launch(mm_model *m, const mm_move *moves, int64_t n, float *score, uint8_t *feas, float *mean,
+                      float *delta, int32_t options, int team, int ctas_per_sm, int stages, const StepOut *step) {
+    EvalArgs A = eval_args(m, moves, n, score, feas, mean, delta);
     if (step) {
         A.k = step->k;
         A.do_apply = step->apply;

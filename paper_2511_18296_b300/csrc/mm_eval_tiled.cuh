@@ -459,10 +459,10 @@ __device__ __forceinline__ void prefetch_row(const float *row, uint32_t row_byte
 }
 
 // End of the evaluation part of a fused search step: warp 0 merges the
-// warps' lists (skipping lists that cannot contribute) and publishes the
-// CTA's 32 best keys.  Every key of the batch's top k is among the 32 best of
-// the CTA that evaluated it; k_step_finish selects from these lists.
-__device__ __forceinline__ void step_publish(uint64_t *lists, uint64_t wtk) {
+// warps' lists (skipping lists that cannot contribute) and writes the CTA's 32
+// best keys to out32[0..32).  Every key of the batch's top k is among the 32
+// best of the CTA that evaluated it; the finisher selects from these lists.
+__device__ __forceinline__ void step_publish(uint64_t *out32, uint64_t wtk) {
     constexpr int NW = kEvalThreads / 32;
     __shared__ uint64_t s_wtk[NW][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -471,50 +471,94 @@ __device__ __forceinline__ void step_publish(uint64_t *lists, uint64_t wtk) {
     if (warp == 0) {
         uint64_t t = s_wtk[0][lane];
         for (int w = 1; w < NW; w++) t = warp_topk_merge(t, s_wtk[w][lane]);
-        lists[(size_t)blockIdx.x * 32 + lane] = t;
+        out32[lane] = t;
     }
 }
 
-template <int TEAM, int QMAX, bool KAHAN, bool DELTA, bool TSM, int KF = 0, bool TAIL = false, bool TOPK = false>
-__global__ void __launch_bounds__(kEvalThreads, MM_EVAL_MINB) k_eval_tiled(EvalArgs A) {
-    constexpr int CH = kChunk;              // moves per warp chunk (2 per lane)
-    constexpr int NW = kEvalThreads / 32;   // warps per CTA
-    constexpr int TPW = 32 / TEAM;          // teams per warp
-    extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ float4 s_lut[16];
-    __shared__ int32_t s_b1[NW][CH], s_b2[NW][CH];
-    __shared__ uint32_t s_tt[NW][CH];
-    __shared__ uint8_t s_lsh[NW][CH], s_lsw[NW][CH];
-    __shared__ float s_score[NW][CH], s_mean[NW][CH];
-    __shared__ uint8_t s_flag[NW][CH];
-
-    const int T1 = A.T + 1;
-    const size_t tab_floats = (size_t)2 * T1 * A.S_pad;
-    float *s_tab = reinterpret_cast<float *>(smem);                            // [2][T+1][S_pad] if TSM
-    float *s_dd = s_tab + (TSM ? tab_floats : 0);                              // [(T+1)^2]
-    size_t off = ((TSM ? tab_floats : 0) + (size_t)T1 * T1) * sizeof(float);
-    off = (off + 15) & ~(size_t)15;
-    int64_t *s_mined = reinterpret_cast<int64_t *>(smem + off);                // [T+1]
-    uint64_t *s_cap = reinterpret_cast<uint64_t *>(s_mined + T1);              // [T+1]
-
-    const int tid = threadIdx.x;
-    if (TSM) {
-        const float4 *src = reinterpret_cast<const float4 *>(A.tab);
-        float4 *dst = reinterpret_cast<float4 *>(s_tab);
-        for (int i = tid; i < (int)(tab_floats / 4); i += kEvalThreads) dst[i] = __ldg(src + i);
+// Selection of the 32 largest keys among nlists published lists (each sorted
+// best-first, 0 = empty; keys unique) by the whole CTA (NW warps, NW a power of
+// two): warp w merges lists w, w + NW, ... with pruned warp merges, four
+// lists' loads in flight at a time, then a tree over the warps.  Every thread
+// must call it; the result is valid in warp 0 (sorted, lane 0 best).
+template <int NW>
+__device__ __forceinline__ uint64_t block_merge_lists(const uint64_t *lists, int nlists, uint64_t (*s_wl)[32]) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint64_t t = 0;
+    for (int l0 = warp; l0 < nlists; l0 += 4 * NW) {
+        uint64_t c[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const int l = l0 + u * NW;
+            c[u] = l < nlists ? __ldcg(lists + (size_t)l * 32 + lane) : 0ull;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) t = warp_topk_merge(t, c[u]);
     }
-    for (int i = tid; i < T1 * T1; i += kEvalThreads) s_dd[i] = __ldg(A.ddt + i);
-    for (int i = tid; i < T1; i += kEvalThreads) {
-        s_mined[i] = A.minedT[i];
-        s_cap[i] = A.cap[i];
-    }
-    if (tid < 16)
-        s_lut[tid] = make_float4((float)(tid & 1), (float)((tid >> 1) & 1), (float)((tid >> 2) & 1),
-                                 (float)((tid >> 3) & 1));
+    s_wl[warp][lane] = t;
     __syncthreads();
-    const float *tab = TSM ? s_tab : A.tab;
+#pragma unroll
+    for (int stride = NW / 2; stride > 0; stride >>= 1) {
+        if (warp < stride) {
+            t = warp_topk_merge(t, s_wl[warp + stride][lane]);
+            s_wl[warp][lane] = t;
+        }
+        __syncthreads();
+    }
+    return t;
+}
 
-    const int lane = tid & 31, warp = tid >> 5;
+// Called by one full warp with the merged list t: writes the top k (move
+// indices, their scores read back from score[], the count) and returns the
+// best move's index in every lane, -1 when nothing is feasible.  A key always
+// decodes to a move of the batch; the range check (< n) makes sure a corrupted
+// list can never turn into an out-of-range access (it raises the bad-move bit).
+__device__ __forceinline__ int warp_write_topk(uint64_t t, int k, int64_t n, uint32_t *status, const float *score,
+                                               int32_t *idx_out, float *top_out, int32_t *count_out) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t valid = __ballot_sync(0xffffffffu, t != 0ull);
+    int cnt = min(__popc(valid), k);
+    const uint32_t id = ~(uint32_t)(t & 0xffffffffull);
+    const bool ok = (uint64_t)id < (uint64_t)n;
+    const uint32_t bad = __ballot_sync(0xffffffffu, lane < cnt && !ok);
+    if (bad) {
+        cnt = __ffs(bad) - 1;
+        if (lane == 0) atomicOr(status, kStBadMove);
+    }
+    const uint32_t id0 = __shfl_sync(0xffffffffu, id, 0);
+    if (lane < cnt) {
+        idx_out[lane] = (int32_t)id;
+        top_out[lane] = __ldcg(score + id);
+    }
+    if (lane == 0) *count_out = cnt;
+    return cnt > 0 ? (int)id0 : -1;
+}
+
+// Evaluator arguments for a batch of n moves on model m (mm_eval.cu).
+EvalArgs eval_args(mm_model *m, const mm_move *moves, int64_t n, float *score, uint8_t *feas, float *mean,
+                   float *delta);
+
+// Per-warp lists and staging of the evaluator (static shared memory).
+struct EvalShared {
+    int32_t b1[kEvalThreads / 32][kChunk], b2[kEvalThreads / 32][kChunk];
+    uint32_t tt[kEvalThreads / 32][kChunk];
+    uint8_t lsh[kEvalThreads / 32][kChunk], lsw[kEvalThreads / 32][kChunk];
+    float score[kEvalThreads / 32][kChunk], mean[kEvalThreads / 32][kChunk];
+    uint8_t flag[kEvalThreads / 32][kChunk];
+};
+
+// The evaluator proper: the calling warp evaluates moves [r0, r1) of A in
+// chunks of 64 (decode two per lane, shift / swap lists by ballot, teams of
+// TEAM lanes per move, coalesced stores) and, if TOPK, inserts every feasible
+// move's key into its register list wtk.  tab, s_dd, s_mined and s_cap are
+// the CTA's staged tables; s_lut the 16 ore-nibble masks.
+template <int TEAM, int QMAX, bool KAHAN, bool DELTA, int KF, bool TAIL, bool TOPK>
+__device__ __forceinline__ void eval_warp_range(const EvalArgs &A, EvalShared &sh, const float4 *s_lut,
+                                                const float *tab, const float *s_dd, const int64_t *s_mined,
+                                                const uint64_t *s_cap, int64_t r0, int64_t r1, uint64_t &wtk) {
+    constexpr int CH = kChunk;
+    constexpr int TPW = 32 / TEAM;
+    const int T1 = A.T + 1;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int tl = lane % TEAM, tw = lane / TEAM;
     const int S = A.S;
     const int NQ = (S + 3) >> 2;
@@ -522,12 +566,6 @@ __global__ void __launch_bounds__(kEvalThreads, MM_EVAL_MINB) k_eval_tiled(EvalA
     const float invS = 1.0f / (float)S;
     const size_t pin_off = (size_t)T1 * A.S_pad;
     const uint32_t lt_mask = (1u << lane) - 1u;
-    // contiguous, balanced range of moves for this warp
-    const int64_t nwarps = (int64_t)gridDim.x * NW;
-    const int64_t gw = (int64_t)blockIdx.x * NW + warp;
-    const int64_t r0 = gw * A.n / nwarps, r1 = (gw + 1) * A.n / nwarps;
-
-    uint64_t wtk = 0;  // this warp's best 32 candidate keys (TOPK)
     int2 mv[2];
 #pragma unroll
     for (int h = 0; h < 2; h++) {
@@ -556,19 +594,19 @@ __global__ void __launch_bounds__(kEvalThreads, MM_EVAL_MINB) k_eval_tiled(EvalA
                     for (int s2 = 0; s2 < S; s2++) drow[s2] = 0.0f;
                 }
             }
-            s_score[warp][slot] = v.valid ? 0.0f : -INFINITY;
-            s_mean[warp][slot] = 0.0f;
-            if (TOPK) s_flag[warp][slot] = (active && v.feasible) ? 1 : 0;
+            sh.score[warp][slot] = v.valid ? 0.0f : -INFINITY;
+            sh.mean[warp][slot] = 0.0f;
+            if (TOPK) sh.flag[warp][slot] = (active && v.feasible) ? 1 : 0;
             if (work) {
-                s_b1[warp][slot] = v.b1;
-                s_b2[warp][slot] = v.swap ? v.b2 : A.tp.B;
-                s_tt[warp][slot] = v.t1 | (v.t2 << 8);
+                sh.b1[warp][slot] = v.b1;
+                sh.b2[warp][slot] = v.swap ? v.b2 : A.tp.B;
+                sh.tt[warp][slot] = v.t1 | (v.t2 << 8);
             }
             const bool is_sh = work && !v.swap, is_sw = work && v.swap;
             const uint32_t msh = __ballot_sync(0xffffffffu, is_sh);
             const uint32_t msw = __ballot_sync(0xffffffffu, is_sw);
-            if (is_sh) s_lsh[warp][nsh + __popc(msh & lt_mask)] = (uint8_t)slot;
-            if (is_sw) s_lsw[warp][nsw + __popc(msw & lt_mask)] = (uint8_t)slot;
+            if (is_sh) sh.lsh[warp][nsh + __popc(msh & lt_mask)] = (uint8_t)slot;
+            if (is_sw) sh.lsw[warp][nsw + __popc(msw & lt_mask)] = (uint8_t)slot;
             nsh += __popc(msh);
             nsw += __popc(msw);
         }
@@ -582,9 +620,9 @@ __global__ void __launch_bounds__(kEvalThreads, MM_EVAL_MINB) k_eval_tiled(EvalA
             const bool sw = j >= nbs;
             const int e = (sw ? j - nbs : j) * TPW + tw;
             if (e < (sw ? nsw : nsh)) {
-                const int slot = (sw ? s_lsw[warp] : s_lsh[warp])[e];
-                prefetch_row<TEAM>(A.val + (size_t)s_b1[warp][slot] * A.R, row_bytes, tl);
-                if (sw) prefetch_row<TEAM>(A.val + (size_t)s_b2[warp][slot] * A.R, row_bytes, tl);
+                const int slot = (sw ? sh.lsw[warp] : sh.lsh[warp])[e];
+                prefetch_row<TEAM>(A.val + (size_t)sh.b1[warp][slot] * A.R, row_bytes, tl);
+                if (sw) prefetch_row<TEAM>(A.val + (size_t)sh.b2[warp][slot] * A.R, row_bytes, tl);
             }
         };
         for (int j = 0; j < A.prefetch && j < nb; j++) prefetch_batch(j);
@@ -595,10 +633,10 @@ __global__ void __launch_bounds__(kEvalThreads, MM_EVAL_MINB) k_eval_tiled(EvalA
             const int e = (sw ? j - nbs : j) * TPW + tw;
             const int nl = sw ? nsw : nsh;
             const bool act = e < nl;
-            const int slot = act ? (sw ? s_lsw[warp] : s_lsh[warp])[e] : 0;
-            const int32_t b1 = act ? s_b1[warp][slot] : 0;
-            const int32_t b2 = act ? s_b2[warp][slot] : 0;
-            const uint32_t tt = act ? s_tt[warp][slot] : 0;
+            const int slot = act ? (sw ? sh.lsw[warp] : sh.lsh[warp])[e] : 0;
+            const int32_t b1 = act ? sh.b1[warp][slot] : 0;
+            const int32_t b2 = act ? sh.b2[warp][slot] : 0;
+            const uint32_t tt = act ? sh.tt[warp][slot] : 0;
             const uint32_t t1 = tt & 0xffu, t2 = tt >> 8;
             const float dd = s_dd[t1 * T1 + t2];
             float mu, sd;
@@ -626,8 +664,8 @@ __global__ void __launch_bounds__(kEvalThreads, MM_EVAL_MINB) k_eval_tiled(EvalA
                 if (act && DELTA) write_deltas<TEAM, QMAX>(A, c0 + slot, tl, NQ, rem, d);
             }
             if (act && tl == 0) {
-                s_score[warp][slot] = mu - A.lambda * sd;
-                s_mean[warp][slot] = mu;
+                sh.score[warp][slot] = mu - A.lambda * sd;
+                sh.mean[warp][slot] = mu;
             }
         }
         __syncwarp();
@@ -637,13 +675,13 @@ __global__ void __launch_bounds__(kEvalThreads, MM_EVAL_MINB) k_eval_tiled(EvalA
             const int slot = h * 32 + lane;
             const int64_t i = c0 + slot;
             if (i < r1) {
-                A.score[i] = s_score[warp][slot];
-                if (A.mean) A.mean[i] = s_mean[warp][slot];
+                A.score[i] = sh.score[warp][slot];
+                if (A.mean) A.mean[i] = sh.mean[warp][slot];
             }
             if (TOPK) {
                 uint64_t key = 0;
-                if (i < r1 && s_flag[warp][slot]) {
-                    const float f = s_score[warp][slot];
+                if (i < r1 && sh.flag[warp][slot]) {
+                    const float f = sh.score[warp][slot];
                     if (!isnan(f)) key = score_key(f, i);
                 }
                 wtk = warp_topk_insert(wtk, key);
@@ -651,7 +689,49 @@ __global__ void __launch_bounds__(kEvalThreads, MM_EVAL_MINB) k_eval_tiled(EvalA
         }
         __syncwarp();
     }
-    if constexpr (TOPK) step_publish(A.step_cta, wtk);
+}
+
+template <int TEAM, int QMAX, bool KAHAN, bool DELTA, bool TSM, int KF = 0, bool TAIL = false, bool TOPK = false>
+__global__ void __launch_bounds__(kEvalThreads, MM_EVAL_MINB) k_eval_tiled(EvalArgs A) {
+    constexpr int NW = kEvalThreads / 32;   // warps per CTA
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ float4 s_lut[16];
+    __shared__ EvalShared sh;
+
+    const int T1 = A.T + 1;
+    const size_t tab_floats = (size_t)2 * T1 * A.S_pad;
+    float *s_tab = reinterpret_cast<float *>(smem);                            // [2][T+1][S_pad] if TSM
+    float *s_dd = s_tab + (TSM ? tab_floats : 0);                              // [(T+1)^2]
+    size_t off = ((TSM ? tab_floats : 0) + (size_t)T1 * T1) * sizeof(float);
+    off = (off + 15) & ~(size_t)15;
+    int64_t *s_mined = reinterpret_cast<int64_t *>(smem + off);                // [T+1]
+    uint64_t *s_cap = reinterpret_cast<uint64_t *>(s_mined + T1);              // [T+1]
+
+    const int tid = threadIdx.x;
+    if (TSM) {
+        const float4 *src = reinterpret_cast<const float4 *>(A.tab);
+        float4 *dst = reinterpret_cast<float4 *>(s_tab);
+        for (int i = tid; i < (int)(tab_floats / 4); i += kEvalThreads) dst[i] = __ldg(src + i);
+    }
+    for (int i = tid; i < T1 * T1; i += kEvalThreads) s_dd[i] = __ldg(A.ddt + i);
+    for (int i = tid; i < T1; i += kEvalThreads) {
+        s_mined[i] = A.minedT[i];
+        s_cap[i] = A.cap[i];
+    }
+    if (tid < 16)
+        s_lut[tid] = make_float4((float)(tid & 1), (float)((tid >> 1) & 1), (float)((tid >> 2) & 1),
+                                 (float)((tid >> 3) & 1));
+    __syncthreads();
+    const float *tab = TSM ? s_tab : A.tab;
+
+    // contiguous, balanced range of moves for each warp
+    const int warp = tid >> 5;
+    const int64_t nwarps = (int64_t)gridDim.x * NW;
+    const int64_t gw = (int64_t)blockIdx.x * NW + warp;
+    const int64_t r0 = gw * A.n / nwarps, r1 = (gw + 1) * A.n / nwarps;
+    uint64_t wtk = 0;  // this warp's best 32 candidate keys (TOPK)
+    eval_warp_range<TEAM, QMAX, KAHAN, DELTA, KF, TAIL, TOPK>(A, sh, s_lut, tab, s_dd, s_mined, s_cap, r0, r1, wtk);
+    if constexpr (TOPK) step_publish(A.step_cta + (size_t)blockIdx.x * 32, wtk);
 }
 
 // ----------------------------------------------------------------------------

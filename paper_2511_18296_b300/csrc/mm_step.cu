@@ -75,17 +75,13 @@ struct StepFinishArgs {
     int32_t *count_out;
 };
 
-// Selection of the k largest keys among the published lists (each sorted
-// best-first, 0 = empty; keys are unique): warp w merges lists w, w + 32, ...
-// with pruned warp merges (a list whose best key does not beat the running
-// 32nd is skipped), four lists' loads in flight at a time; a five-level tree
-// merges the 32 warp results; warp 0 writes the top k and the CTA applies the
-// best move when asked.
+// The finisher of a fused step: selects the k largest keys among the
+// published CTA lists (block_merge_lists over 32 warps), warp 0 writes the top
+// k, and the CTA applies the best move when asked.
 __global__ void __launch_bounds__(1024) k_step_finish(StepFinishArgs F, ApplyArgs AP) {
     __shared__ uint64_t s_wl[32][32];
     __shared__ int s_best;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int nw = blockDim.x >> 5;  // 32
+    const int tid = threadIdx.x, warp = tid >> 5;
     if (F.do_apply) {
         // the apply's per-period state was evicted by the evaluation's row
         // traffic: pull it back into L2 while the lists are merged
@@ -98,48 +94,10 @@ __global__ void __launch_bounds__(1024) k_step_finish(StepFinishArgs F, ApplyArg
             for (size_t o = (size_t)tid * 128; o < bytes[r]; o += (size_t)blockDim.x * 128)
                 asm volatile("prefetch.global.L2 [%0];" ::"l"(regions[r] + o));
     }
-    const int nlists = F.nkeys / 32;
-    uint64_t t = 0;
-    for (int l0 = warp; l0 < nlists; l0 += 4 * nw) {
-        uint64_t c[4];
-#pragma unroll
-        for (int u = 0; u < 4; u++) {
-            const int l = l0 + u * nw;
-            c[u] = l < nlists ? __ldcg(F.keys + (size_t)l * 32 + lane) : 0ull;
-        }
-#pragma unroll
-        for (int u = 0; u < 4; u++) t = warp_topk_merge(t, c[u]);
-    }
-    s_wl[warp][lane] = t;
-    __syncthreads();
-    for (int stride = nw / 2; stride > 0; stride >>= 1) {
-        if (warp < stride) {
-            t = warp_topk_merge(t, s_wl[warp + stride][lane]);
-            s_wl[warp][lane] = t;
-        }
-        __syncthreads();
-    }
+    const uint64_t t = block_merge_lists<32>(F.keys, F.nkeys / 32, s_wl);
     if (warp == 0) {
-        const uint32_t valid = __ballot_sync(0xffffffffu, t != 0ull);
-        int cnt = min(__popc(valid), F.k);
-        const uint32_t id = ~(uint32_t)(t & 0xffffffffull);
-        // a key always decodes to a move of this batch; check anyway so that a
-        // corrupted list can never turn into an out-of-range access
-        const bool ok = (uint64_t)id < (uint64_t)F.n;
-        const uint32_t bad = __ballot_sync(0xffffffffu, lane < cnt && !ok);
-        if (bad) {
-            cnt = __ffs(bad) - 1;
-            if (lane == 0) atomicOr(F.status, kStBadMove);
-        }
-        const uint32_t id0 = __shfl_sync(0xffffffffu, id, 0);
-        if (lane < cnt) {
-            F.idx_out[lane] = (int32_t)id;
-            F.top_out[lane] = __ldcg(F.score + id);
-        }
-        if (lane == 0) {
-            *F.count_out = cnt;
-            s_best = cnt > 0 ? (int)id0 : -1;
-        }
+        const int best = warp_write_topk(t, F.k, F.n, F.status, F.score, F.idx_out, F.top_out, F.count_out);
+        if ((tid & 31) == 0) s_best = best;
     }
     __syncthreads();
     if (F.do_apply) {
@@ -174,7 +132,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_topk_lists(const float *__rest
             wtk = warp_topk_insert(wtk, (ok[u] && !isnan(f[u])) ? score_key(f[u], i) : 0ull);
         }
     }
-    step_publish(lists, wtk);
+    step_publish(lists + (size_t)blockIdx.x * 32, wtk);
 }
 
 mm_status topk_small_launch(mm_model *m, const float *score, const uint8_t *feas, int64_t n, int32_t k, int32_t *idx,

@@ -1,0 +1,205 @@
+"""Batched multi-chain evaluation (mm_batch_*) against the per-model calls.
+
+Every chain of a batch -- different block models, scenario counts and batch
+sizes, evaluated together in one persistent launch -- must get exactly what
+the single-model path gives it: the same score and flag bits, the same top k,
+and (with apply) the same schedule and NPV afterwards.  Two chains are also
+checked against the FP64 oracle.
+"""
+
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from helpers import assert_close_floor
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+
+
+def mm():
+    import paper_2511_18296_b300 as m
+    return m
+
+
+# (side, S, n_moves): every compiled shape (S = 16, 32, 48, 64, 100) and the
+# run-time-shaped one (S = 13, 36), ragged batch sizes, one empty chain
+SMALL = [(10, 16, 1000), (12, 32, 3333), (9, 48, 700), (11, 64, 2500), (13, 100, 4100), (8, 13, 999),
+         (10, 36, 64), (9, 100, 0), (14, 16, 6000)]
+
+
+def small_chains(seed0=500):
+    specs = W.batched_chain_specs(len(SMALL), base_seed=seed0)
+    probs = []
+    for spec, (side, S, n) in zip(specs, SMALL):
+        spec = dict(spec, nx=side, ny=side, nz=side, S=S, n_moves=n)
+        spec["cap_blocks"] = int(np.ceil(1.12 * side ** 3 / spec["T"]))
+        spec["target_blocks"] = int(round(0.393 * spec["cap_blocks"]))
+        probs.append(W.chain_problem(spec))
+    return probs
+
+
+def models_for(probs):
+    out = []
+    for p in probs:
+        m = mm().Model.from_problem(p)
+        m.schedule_set(p.x0)
+        out.append(m)
+    return out
+
+
+def moves_of(p):
+    return torch.as_tensor(p.moves.reshape(-1, 2), device="cuda")
+
+
+def check_chain(m, mv, o, k):
+    """The batch's outputs for one chain equal a separate evaluation + top-k."""
+    n = mv.shape[0]
+    if n == 0:
+        assert int(o["count"].cpu()[0]) == 0
+        return
+    s, f, _ = m.eval_moves(mv, want_mean=False)
+    idx, top, cnt = m.topk(s, f, k)
+    torch.cuda.synchronize()
+    assert np.array_equal(o["feas"].cpu().numpy(), f.cpu().numpy())
+    assert np.array_equal(o["score"].cpu().numpy().view(np.uint32), s.cpu().numpy().view(np.uint32))
+    c = int(cnt.cpu()[0])
+    assert int(o["count"].cpu()[0]) == c
+    assert np.array_equal(o["idx"].cpu().numpy()[:c], idx.cpu().numpy()[:c])
+    assert np.array_equal(o["top"].cpu().numpy()[:c], top.cpu().numpy()[:c])
+
+
+@pytest.fixture(scope="module")
+def small():
+    probs = small_chains()
+    return probs, models_for(probs)
+
+
+def test_batch_matches_separate_calls_every_tile(small):
+    probs, models = small
+    mvs = [moves_of(p) for p in probs]
+    b = mm().Batch(list(zip(models, mvs)), k=32)
+    for tile, ctas in ((64, 0), (512, 0), (2048, 1), (1 << 20, 0)):
+        b.set_tile(tile, ctas)
+        for o in b.out:
+            o["score"].fill_(float("nan"))
+            o["count"].fill_(-1)
+        b.run()
+        torch.cuda.synchronize()
+        for m, mv, o in zip(models, mvs, b.out):
+            check_chain(m, mv, o, 32)
+    b.close()
+
+
+def test_batch_against_oracle(small):
+    probs, models = small
+    mvs = [moves_of(p) for p in probs]
+    b = mm().Batch(list(zip(models, mvs)), k=8)
+    b.run()
+    torch.cuda.synchronize()
+    for c in (1, 5):  # S = 32 (compiled shape) and S = 13 (run-time shape)
+        p = probs[c]
+        inc = O.OracleModel(p).eval_incremental(p.x0, p.moves)
+        assert np.array_equal(b.out[c]["feas"].cpu().numpy(), inc["flag"])
+        assert_close_floor(b.out[c]["score"].cpu().numpy(), inc["score"], inc["floor"], what=f"chain {c}")
+    b.close()
+
+
+def test_batch_graph_replay_with_new_moves(small):
+    probs, models = small
+    mvs = [moves_of(p) for p in probs]
+    st = torch.cuda.Stream()
+    b = mm().Batch(list(zip(models, mvs)), k=16, stream=st)
+    b.run()
+    st.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=st):
+        b.run()
+    rng = np.random.default_rng(3)
+    for rep in range(2):
+        for p, mv in zip(probs, mvs):  # new moves written into the same buffers
+            if mv.shape[0]:
+                new = W.random_moves(p.x0, p.T, mv.shape[0], 0.5, rng)
+                mv.copy_(torch.as_tensor(new))
+        torch.cuda.synchronize()
+        g.replay()
+        torch.cuda.synchronize()
+        for m, mv, o in zip(models, mvs, b.out):
+            check_chain(m, mv, o, 16)
+    b.close()
+
+
+def test_batch_autotune_keeps_results(small):
+    probs, models = small
+    mvs = [moves_of(p) for p in probs]
+    b = mm().Batch(list(zip(models, mvs)), k=4)
+    tile, ctas, ms = b.autotune(reps=2)
+    assert tile in (512, 1024, 2048, 4096, 8192, 16384) and ctas >= 1 and ms > 0
+    assert b.tile()[:2] == (tile, ctas)
+    b.run()
+    torch.cuda.synchronize()
+    for m, mv, o in zip(models, mvs, b.out):
+        check_chain(m, mv, o, 4)
+    b.close()
+
+
+def test_batch_apply_matches_search_step():
+    probs = small_chains(seed0=900)
+    twins = models_for(probs)
+    models = models_for(probs)
+    mvs = [moves_of(p) for p in probs]
+    b = mm().Batch(list(zip(models, mvs)), k=32, apply=True)
+    for step in range(3):
+        b.run()
+        torch.cuda.synchronize()
+        for c, (m, t, mv, o) in enumerate(zip(models, twins, mvs, b.out)):
+            if mv.shape[0] == 0:
+                assert int(o["count"].cpu()[0]) == 0
+                continue
+            s, f, idx, top, cnt = t.search_step(mv, k=32, apply=True)
+            torch.cuda.synchronize()
+            assert np.array_equal(o["score"].cpu().numpy().view(np.uint32), s.cpu().numpy().view(np.uint32))
+            ca = int(cnt.cpu()[0])
+            assert int(o["count"].cpu()[0]) == ca
+            assert np.array_equal(o["idx"].cpu().numpy()[:ca], idx.cpu().numpy()[:ca])
+            assert np.array_equal(m.schedule_get(), t.schedule_get()), (step, c)
+            assert m.last_apply() == t.last_apply()
+    b.close()
+
+
+def test_batch_errors(small):
+    probs, models = small
+    mvs = [moves_of(p) for p in probs]
+    with pytest.raises(mm().MMError):
+        mm().Batch([(models[0], mvs[0]), (models[0], mvs[0])], k=4)  # shared model
+    with pytest.raises(mm().MMError):
+        mm().Batch([(models[0], mvs[0])], k=33)
+    b = mm().Batch([(models[0], mvs[0])], k=4, apply=True)
+    with pytest.raises(mm().MMError):
+        b.autotune()  # a batch that applies is not autotuned
+    b.close()
+    with pytest.raises(mm().MMError):
+        b2 = mm().Batch([(models[0], mvs[0])], k=4)
+        b2.set_tile(100, 0)  # not a multiple of 64
+
+
+def test_batch_64_chains_full_workload():
+    """The 64-chain workload (cubes of side 15..40, S in {16, 32, 64, 100},
+    1,024..65,536 moves per chain) in one launch equals 64 separate calls."""
+    specs = W.batched_chain_specs(64)
+    probs = [W.chain_problem(s) for s in specs]
+    models = models_for(probs)
+    mvs = [moves_of(p) for p in probs]
+    b = mm().Batch(list(zip(models, mvs)), k=32)
+    b.autotune(reps=2)
+    b.run()
+    torch.cuda.synchronize()
+    for m, mv, o in zip(models, mvs, b.out):
+        check_chain(m, mv, o, 32)
+    b.close()

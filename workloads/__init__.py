@@ -17,6 +17,7 @@ from .grf import lognormal_grades, gaussian_field
 from .configs import (
     Problem,
     make_problem,
+    chain_problem,
     greedy_schedule,
     random_moves,
     CONFIGS,

@@ -230,6 +230,14 @@ def batched_chain_specs(n_chains: int = 64, base_seed: int = 100) -> list:
     return specs
 
 
+def chain_problem(spec: dict) -> Problem:
+    """The Problem of one chain spec (see batched_chain_specs); spec keys may be
+    overridden by the caller for smaller test cases."""
+    kw = {k: spec[k] for k in ("name", "nx", "ny", "nz", "S", "T", "cap_blocks", "target_blocks", "n_moves",
+                               "shift_frac", "seed", "mean", "cv", "rng_a", "nugget", "sill")}
+    return make_problem(**kw)
+
+
 def relaxed_x(B: int, T: int, seed: int) -> np.ndarray:
     """Fractional schedule x[b][t] in [0,1], rows drawn from Dirichlet(1) (float32)."""
     rng = np.random.default_rng(np.random.SeedSequence(seed))
