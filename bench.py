@@ -232,6 +232,68 @@ def reference_arm(args):
 # ------------------------------------------------------------------ GPU arm
 
 
+def batched_form(stream, flush, reps: int = 30):
+    """The 64-chain workload (cube sides 15..40, S in {16, 32, 64, 100}, T = 20,
+    1,024..65,536 moves per chain, seeds 100..163): one persistent batched launch
+    (autotuned tile, replayed from a CUDA graph) against the same 64 chains as
+    sequential plain calls (mm_eval_moves + mm_topk per chain, also replayed
+    from one CUDA graph).  L2 flushed before every run; times are CUDA events."""
+    import torch
+
+    import paper_2511_18296_b300 as mm
+    import workloads as W
+
+    probs = [W.chain_problem(s) for s in W.batched_chain_specs(64)]
+    models = []
+    for p in probs:
+        m = mm.Model.from_problem(p, stream=stream)
+        m.schedule_set(p.x0)
+        models.append(m)
+    mvs = [torch.as_tensor(p.moves, device=flush.device) for p in probs]
+    evals = int(sum(p.moves.shape[0] * p.S for p in probs))
+    b = mm.Batch(list(zip(models, mvs)), k=TOPK, stream=stream)
+    tile, ctas, _ = b.autotune(reps=3)
+
+    def graph_of(fn):
+        with torch.cuda.stream(stream):
+            fn()
+        stream.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            fn()
+        return g
+
+    def seq():
+        for m, mv, o in zip(models, mvs, b.out):
+            m.eval_moves(mv, score=o["score"], feas=o["feas"], want_mean=False)
+            m.topk(o["score"], o["feas"], TOPK, idx=o["idx"], top=o["top"], count=o["count"])
+
+    def time_graph(g):
+        ts = []
+        with torch.cuda.stream(stream):
+            for r in range(reps + 3):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                g.replay()
+                e1.record(stream)
+                e1.synchronize()
+                if r >= 3:
+                    ts.append(e0.elapsed_time(e1))
+        return float(np.mean(ts))
+
+    t_b = time_graph(graph_of(b.run))
+    t_s = time_graph(graph_of(seq))
+    b.close()
+    return {"workload": "64 chains: cubes of side 15..40, S in {16, 32, 64, 100}, T=20, 1,024..65,536 moves each",
+            "evals_per_run": evals, "chains": 64, "launches_per_run": 1,
+            "ms_per_run": t_b, "value": evals / (t_b * 1e-3), "unit": UNIT,
+            "tile": {"moves_per_item": tile, "ctas_per_sm": ctas, "chosen_by": "mm_batch_autotune"},
+            "sequential_plain": {"desc": "64 x (mm_eval_moves + mm_topk), one CUDA graph", "launches_per_run": 128,
+                                 "ms_per_run": t_s, "value": evals / (t_s * 1e-3)},
+            "speedup_vs_sequential": t_s / t_b}
+
+
 def gpu_arm(args):
     import torch
     import torch.distributed as dist
@@ -428,6 +490,8 @@ def gpu_arm(args):
         "clocks": clocks,
         "check": {"last_apply": applied, "npv_mean": npv_mean},
     }
+    if rank == 0 and not args.no_batched:
+        line["batched_form"] = batched_form(stream, flush)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(p, budget_s=args.cpu_budget)
     if world > 1:
@@ -445,6 +509,7 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 64-chain batched comparison")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     args = ap.parse_args(argv)
     if args.warmup < 3:
