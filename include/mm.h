@@ -312,6 +312,38 @@ mm_status mm_get_values(mm_model *m, float *value_host);
 mm_status mm_get_tonnage(mm_model *m, int64_t *mined_host, int64_t *ore_t_host);
 mm_status mm_get_metal(mm_model *m, double *metal_host);
 
+/* ---- Relaxed objective and its adjoint (differentiable form) ----
+ *
+ * Eq. 14 with the extraction decision relaxed to x[b][t] in [0, 1] (row sums
+ * are not forced) and the mill penalty smoothed, under the risk term
+ * J = mean_s NPV_s - lambda std_s NPV_s (population std):
+ *   O[t][s] = sum_b x[b][t] m_b ore[b][s],  V[t][s] = sum_b x[b][t] v[b][s],
+ *   NPV_s   = sum_t d_t (V[t][s] - P_t(O[t][s])),
+ *   P_t(O)  = a m_ref sp((Q_t - O) / m_ref) + e m_ref sp((O - Q_t) / m_ref),
+ *   sp(z)   = log(1 + exp(beta z)) / beta
+ * with d_t, Q_t, a, e, lambda and the economics of the model.  ore and v are
+ * recomputed from the grades: g_dev[B][S] (FP32, device) when given, else the
+ * model's own FP64 grades; the ore decision is (g * price) * recovery >
+ * proc_cost in FP64 on those values, v is FP32.  ore is a step in g: it has
+ * no gradient.
+ *
+ * mm_relaxed_forward: x_dev[B][T] FP32 -> *J_dev, npv_dev[S] and ore_t_dev[T][S]
+ * (FP64, device).  ore_t_dev is the per-period checkpoint O[t][s] that the
+ * adjoint reads.  Products in FP32, chunk sums of 128 blocks in FP32, the rest
+ * in FP64 (deterministic).
+ * mm_relaxed_backward: given the forward's npv_dev and ore_t_dev and the
+ * upstream gradient *gJ_dev (FP64, device), writes gx_dev[B][T] = dJ/dx and,
+ * if gg_dev is not NULL, gg_dev[B][S] = dJ/dg (FP32, device).  Where every
+ * NPV_s is equal the std term contributes no gradient.
+ * Both are asynchronous on the model's stream; the first call (or a larger
+ * model) allocates model-owned scratch.  beta, m_ref > 0 (MM_ERR_INVALID_ARG
+ * otherwise). */
+mm_status mm_relaxed_forward(mm_model *m, const float *x_dev, const float *g_dev, double beta, double m_ref,
+                             double *J_dev, double *npv_dev, double *ore_t_dev);
+mm_status mm_relaxed_backward(mm_model *m, const float *x_dev, const float *g_dev, double beta, double m_ref,
+                              const double *npv_dev, const double *ore_t_dev, const double *gJ_dev,
+                              float *gx_dev, float *gg_dev);
+
 /* Message of the last failing call on this thread ("" if none). */
 const char *mm_last_error(void);
 

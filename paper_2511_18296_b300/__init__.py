@@ -82,6 +82,8 @@ SIGNATURES = [
     ("mm_topk_noalloc", C.c_int, [P, P, I64, I32, P, P, P, P]),
     ("mm_search_step", C.c_int, [P, P, I64, I32, I32, P, P, P, P, P]),
     ("mm_set_step_event", C.c_int, [P, P]),
+    ("mm_relaxed_forward", C.c_int, [P, P, P, D, D, P, P, P]),
+    ("mm_relaxed_backward", C.c_int, [P, P, P, D, D, P, P, P, P, P]),
     ("mm_batch_create", C.c_int, [P, I32, I32, I32, P, P]),
     ("mm_batch_destroy", None, [P]),
     ("mm_batch_run", C.c_int, [P]),
@@ -290,6 +292,28 @@ class Model:
         self._step_event = event  # keep the caller's event alive while it is in use
         _check(lib().mm_set_step_event(self.h, h))
 
+    # -- relaxed objective ------------------------------------------------
+    def relaxed_forward(self, x, g=None, beta: float = 10.0, m_ref: float = 10_000.0):
+        """J (float64 [1]), NPV_s (float64 [S]) and the checkpoint O[t][s]
+        (float64 [T][S]) of the relaxed objective for x float32 [B][T] (CUDA);
+        g float32 [B][S] (CUDA) or None for the model's own grades."""
+        import torch
+        dev = x.device
+        J = torch.empty(1, dtype=torch.float64, device=dev)
+        npv = torch.empty(self.S, dtype=torch.float64, device=dev)
+        ot = torch.empty((self.T, self.S), dtype=torch.float64, device=dev)
+        _check(lib().mm_relaxed_forward(self.h, _ptr(x), _ptr(g), beta, m_ref, _ptr(J), _ptr(npv), _ptr(ot)))
+        return J, npv, ot
+
+    def relaxed_backward(self, x, g, npv, ot, gJ, beta: float = 10.0, m_ref: float = 10_000.0, want_g: bool = True):
+        """dJ/dx float32 [B][T] and dJ/dg float32 [B][S] (None unless want_g)."""
+        import torch
+        gx = torch.empty_like(x)
+        gg = torch.empty((self.B, self.S), dtype=torch.float32, device=x.device) if want_g else None
+        _check(lib().mm_relaxed_backward(self.h, _ptr(x), _ptr(g), beta, m_ref, _ptr(npv), _ptr(ot), _ptr(gJ),
+                                         _ptr(gx), _ptr(gg)))
+        return gx, gg
+
     # -- apply ----------------------------------------------------------
     def apply_move(self, move) -> Tuple[float, float]:
         """Apply (b1, arg); returns the NPV (mean, std).  Raises MMError with
@@ -395,3 +419,42 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def _relaxed_function():
+    import torch
+
+    class RelaxedObjective(torch.autograd.Function):
+        """J = mean_s NPV_s - lambda std_s NPV_s of the relaxed schedule x
+        (float32 [B][T]) and grades g (float32 [B][S]) on a model; backward runs
+        the library's adjoint kernels (dJ/dx, dJ/dg).  The forward keeps the
+        per-period checkpoint O[t][s] for the backward."""
+
+        @staticmethod
+        def forward(ctx, x, g, model, beta, m_ref):
+            x = x.contiguous()
+            g = g.contiguous()
+            J, npv, ot = model.relaxed_forward(x, g, beta, m_ref)
+            ctx.save_for_backward(x, g, npv, ot)
+            ctx.model, ctx.beta, ctx.m_ref = model, beta, m_ref
+            return J[0]
+
+        @staticmethod
+        def backward(ctx, gJ):
+            x, g, npv, ot = ctx.saved_tensors
+            gJ = gJ.reshape(1).to(torch.float64).contiguous()
+            gx, gg = ctx.model.relaxed_backward(x, g, npv, ot, gJ, ctx.beta, ctx.m_ref, want_g=ctx.needs_input_grad[1])
+            return gx, gg, None, None, None
+
+    return RelaxedObjective
+
+
+_RELAXED = None
+
+
+def relaxed_objective(model, x, g, beta: float = 10.0, m_ref: float = 10_000.0):
+    """Differentiable J(x, g) through torch.autograd (float64 scalar tensor)."""
+    global _RELAXED
+    if _RELAXED is None:
+        _RELAXED = _relaxed_function()
+    return _RELAXED.apply(x, g, model, beta, m_ref)

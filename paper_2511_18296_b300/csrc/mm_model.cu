@@ -284,6 +284,7 @@ void mm_model_destroy(mm_model *m) {
     cudaFree(m->ddt); cudaFree(m->disc); cudaFree(m->cap); cudaFree(m->target); cudaFree(m->status);
     cudaFree(m->apply_res);
     cudaFree(m->step_cta);
+    cudaFree(m->relax_scratch);
     if (m->apply_res_host) cudaFreeHost(m->apply_res_host);
     if (m->status_host) cudaFreeHost(m->status_host);
     topk_scratch_free(m->topk);

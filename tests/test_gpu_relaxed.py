@@ -1,0 +1,141 @@
+"""Relaxed objective and adjoint kernels against the float64 oracle.
+
+Forward (J, NPV_s, the checkpoint O[t][s]) and gradients (dJ/dx, dJ/dg) of the
+CUDA path against float64 torch autograd of oracle.relaxed, element by
+element; at the 50,000-block size also against central differences (step
+1e-3) of the float64 formula on 128 x and 128 g coordinates.  Tolerance: 1e-5
+relative to max(|reference|, F), F the magnitude of the terms that cancel in
+that coordinate (computed by the oracle; the scenario weight
+w_s = 1/S - lambda (NPV_s - mean) / (S std) is one of them).
+"""
+
+import numpy as np
+import pytest
+from scipy.special import expit
+
+import oracle.relaxed as R
+import workloads as W
+from helpers import tiny_problem
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+
+
+def mm():
+    import paper_2511_18296_b300 as m
+    return m
+
+
+def reference(p, x32, g32):
+    """Oracle parts and gradients on the exact float32 inputs (upcast), and the
+    floors: w_s = 1/S - lambda (NPV_s - mean) / (S std) can cancel, so every
+    term carries |w|_F = 1/S + lambda |NPV_s - mean| / (S std) instead of |w_s|;
+    F_x[b][t] = d_t (sum_s |w|_F |v| + m_b sum_s |w|_F |P_t'| ore) and
+    F_g[b][s] = |w|_F ore m_b price recovery sum_t d_t x[b][t]."""
+    mass, tgt = p.mass.astype(np.float64), p.target.astype(np.float64)
+    x64 = x32.astype(np.float64)
+    r = R.relaxed_grads(x64, g32.astype(np.float64), mass, tgt, p)
+    npv = r["npv"]
+    S = npv.shape[0]
+    sd = npv.std()
+    wf = np.full(S, 1.0 / S) + (p.lam * np.abs(npv - npv.mean()) / (S * sd) if sd > 0 else 0.0)
+    Q = tgt[:, None]
+    sig = lambda z: expit(R.BETA * z)
+    dpen = p.shortfall_pen * sig((Q - r["O"]) / R.M_REF) + p.excess_pen * sig((r["O"] - Q) / R.M_REF)
+    ore = r["ore"].astype(np.float64)
+    a1 = np.abs(r["v"]) @ wf
+    a2 = mass[:, None] * (ore @ (wf[None, :] * dpen).T)
+    r["floor_x"] = r["d"][None, :] * (a1[:, None] + a2)
+    r["floor_g"] = wf[None, :] * ore * mass[:, None] * p.price * p.recovery * (x64 @ r["d"])[:, None]
+    return r
+
+
+def check_close(got, ref, floor, what):
+    err = np.abs(got.astype(np.float64) - ref)
+    bound = TOL * np.maximum(np.abs(ref), floor)
+    bad = err > bound
+    assert not bad.any(), f"{what}: {bad.sum()} of {bad.size} off; worst {err[bad].max()} at bound {bound[bad].min()}"
+
+
+def run(m, x, g):
+    xt = torch.as_tensor(x, device="cuda")
+    gt = torch.as_tensor(g, device="cuda") if g is not None else None
+    J, npv, ot = m.relaxed_forward(xt, gt)
+    gJ = torch.ones(1, dtype=torch.float64, device="cuda")
+    gx, gg = m.relaxed_backward(xt, gt, npv, ot, gJ)
+    torch.cuda.synchronize()
+    return float(J.cpu()[0]), npv.cpu().numpy(), ot.cpu().numpy(), gx.cpu().numpy(), gg.cpu().numpy()
+
+
+@pytest.mark.parametrize("S,T", [(9, 5), (1, 3), (37, 17), (100, 20)])
+def test_relaxed_small_vs_oracle(S, T):
+    p = tiny_problem(6, 5, 4, S=S, T=T, seed=S + T, target_blocks=7)
+    x = W.relaxed_x(p.B, p.T, 2)
+    g = p.grade.astype(np.float32)
+    m = mm().Model.from_problem(p)
+    J, npv, ot, gx, gg = run(m, x, g)
+    r = reference(p, x, g)
+    assert J == pytest.approx(r["J"], rel=TOL)
+    np.testing.assert_allclose(ot, r["O"], rtol=1e-6, atol=1e-3)
+    np.testing.assert_allclose(npv, r["npv"], rtol=TOL)
+    check_close(gx, r["gx"], r["floor_x"], "dJ/dx")
+    check_close(gg, r["gg"], r["floor_g"], "dJ/dg")
+
+
+def test_relaxed_model_grades_path():
+    """g = NULL: the model's own FP64 grades."""
+    p = tiny_problem(5, 5, 3, S=12, T=6, seed=8, target_blocks=6)
+    x = W.relaxed_x(p.B, p.T, 4)
+    m = mm().Model.from_problem(p)
+    J, npv, ot, gx, gg = run(m, x, None)
+    r = reference(p, x, p.grade)
+    assert J == pytest.approx(r["J"], rel=TOL)
+    check_close(gx, r["gx"], r["floor_x"], "dJ/dx (model grades)")
+    check_close(gg, r["gg"], r["floor_g"], "dJ/dg (model grades)")
+
+
+def test_autograd_function_matches_kernels():
+    p = tiny_problem(5, 4, 4, S=16, T=8, seed=3, target_blocks=5)
+    m = mm().Model.from_problem(p)
+    x = torch.tensor(W.relaxed_x(p.B, p.T, 2), device="cuda", requires_grad=True)
+    g = torch.tensor(p.grade.astype(np.float32), device="cuda", requires_grad=True)
+    J = mm().relaxed_objective(m, x, g)
+    (2.0 * J).backward()
+    _, _, _, gx, gg = run(m, x.detach().cpu().numpy(), g.detach().cpu().numpy())
+    np.testing.assert_allclose(x.grad.cpu().numpy(), 2.0 * gx, rtol=1e-6, atol=1e-6 * np.abs(gx).max())
+    np.testing.assert_allclose(g.grad.cpu().numpy(), 2.0 * gg, rtol=1e-6, atol=1e-6 * np.abs(gg).max())
+
+
+def test_relaxed_50k_vs_oracle_and_differences():
+    """The 50,000-block model (T = 20, S = 100), x from Dirichlet(1) rows, seed 2."""
+    p = W.config("relaxed_50k", n_moves=0)
+    x = W.relaxed_x(p.B, p.T, 2)
+    g = p.grade.astype(np.float32)
+    m = mm().Model.from_problem(p)
+    J, npv, ot, gx, gg = run(m, x, g)
+    r = reference(p, x, g)
+    assert J == pytest.approx(r["J"], rel=TOL)
+    np.testing.assert_allclose(npv, r["npv"], rtol=TOL)
+    check_close(gx, r["gx"], r["floor_x"], "dJ/dx 50k")
+    check_close(gg, r["gg"], r["floor_g"], "dJ/dg 50k")
+    # central differences of the float64 formula, 128 x + 128 g coordinates
+    rng = np.random.default_rng(2)
+    mass, tgt = p.mass.astype(np.float64), p.target.astype(np.float64)
+    x64, g64 = x.astype(np.float64), g.astype(np.float64)
+    for _ in range(128):
+        b, t = int(rng.integers(p.B)), int(rng.integers(p.T))
+        fd = R.central_difference_x(x64, g64, mass, tgt, p, b, t)
+        assert abs(gx[b, t] - fd) <= 1e-4 * max(abs(fd), r["floor_x"][b, t]), (b, t, gx[b, t], fd)
+    far = np.abs(g64 * p.price * p.recovery - p.proc_cost) > 2e-3 * p.price * p.recovery
+    cand = np.argwhere(far)
+    for j in rng.choice(len(cand), 128, replace=False):
+        b, s = (int(v) for v in cand[j])
+        fd = R.central_difference_g(x64, g64, mass, tgt, p, b, s)
+        assert abs(gg[b, s] - fd) <= 1e-4 * max(abs(fd), r["floor_g"][b, s]), (b, s, gg[b, s], fd)

@@ -120,3 +120,22 @@ def test_autograd_matches_central_differences():
         i, s = (int(v) for v in cand[j])
         fd = R.central_difference(fg, gt, (i, s))
         assert fd == pytest.approx(r["gg"][i, s], rel=1e-6, abs=1e-6 * np.abs(r["gg"]).max())
+
+
+def test_incremental_differences_equal_full_reevaluation():
+    """The linear-update central differences used at full size equal central
+    differences by full re-evaluation of the formula."""
+    q = tiny_problem(4, 4, 3, S=8, T=4, seed=31, target_blocks=5)
+    x = W.relaxed_x(q.B, q.T, 3).astype(np.float64)
+    mass, tgt = q.mass.astype(np.float64), q.target.astype(np.float64)
+    xt, gt = torch.tensor(x), torch.tensor(q.grade)
+    rng = np.random.default_rng(1)
+    for _ in range(16):
+        b, t = int(rng.integers(q.B)), int(rng.integers(q.T))
+        full = R.central_difference(lambda xx: R.relaxed_objective(xx, gt, mass, tgt, q), xt, (b, t))
+        assert R.central_difference_x(x, q.grade, mass, tgt, q, b, t) == pytest.approx(full, rel=1e-9, abs=1e-6)
+    margin = np.argwhere(np.abs(q.grade * q.price * q.recovery - q.proc_cost) > 2e-3 * q.price * q.recovery)
+    for j in rng.choice(len(margin), 16, replace=False):
+        b, s_ = (int(v) for v in margin[j])
+        full = R.central_difference(lambda gg: R.relaxed_objective(xt, gg, mass, tgt, q), gt, (b, s_))
+        assert R.central_difference_g(x, q.grade, mass, tgt, q, b, s_) == pytest.approx(full, rel=1e-9, abs=1e-6)
