@@ -344,6 +344,19 @@ mm_status mm_relaxed_backward(mm_model *m, const float *x_dev, const float *g_de
                               const double *npv_dev, const double *ore_t_dev, const double *gJ_dev,
                               float *gx_dev, float *gg_dev);
 
+/* ---- Precision study: FP32 shadow accumulators (no counterpart in the paper) ----
+ * The model keeps its running per-period, per-scenario metal and NPV
+ * contributions and NPV_s in FP64 because their drift accumulates over many
+ * accepted moves.  mm_set_fp32_shadow(m, 1) adds the same running totals kept
+ * in FP32 beside them (initialised from the current FP64 state, re-initialised
+ * by every mm_schedule_set, updated by every apply with the same formulas in
+ * FP32), so that the drift of the two can be compared against a full FP64
+ * recomputation; 0 frees them.  Allocates; synchronising when freeing.
+ * mm_get_fp32_shadow_npv writes the FP32 NPV_s as doubles to npv_host[S]
+ * (synchronising; MM_ERR_STATE when the shadow is off). */
+mm_status mm_set_fp32_shadow(mm_model *m, int32_t enable);
+mm_status mm_get_fp32_shadow_npv(mm_model *m, double *npv_host);
+
 /* Message of the last failing call on this thread ("" if none). */
 const char *mm_last_error(void);
 

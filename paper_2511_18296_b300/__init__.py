@@ -82,6 +82,8 @@ SIGNATURES = [
     ("mm_topk_noalloc", C.c_int, [P, P, I64, I32, P, P, P, P]),
     ("mm_search_step", C.c_int, [P, P, I64, I32, I32, P, P, P, P, P]),
     ("mm_set_step_event", C.c_int, [P, P]),
+    ("mm_set_fp32_shadow", C.c_int, [P, I32]),
+    ("mm_get_fp32_shadow_npv", C.c_int, [P, P]),
     ("mm_relaxed_forward", C.c_int, [P, P, P, D, D, P, P, P]),
     ("mm_relaxed_backward", C.c_int, [P, P, P, D, D, P, P, P, P, P]),
     ("mm_batch_create", C.c_int, [P, I32, I32, I32, P, P]),
@@ -291,6 +293,15 @@ class Model:
                 raise ValueError("the event has no CUDA handle yet (record it once first)")
         self._step_event = event  # keep the caller's event alive while it is in use
         _check(lib().mm_set_step_event(self.h, h))
+
+    # -- precision study -------------------------------------------------
+    def set_fp32_shadow(self, enable: bool = True):
+        _check(lib().mm_set_fp32_shadow(self.h, 1 if enable else 0))
+
+    def fp32_shadow_npv(self) -> np.ndarray:
+        v = np.zeros(self.S, np.float64)
+        _check(lib().mm_get_fp32_shadow_npv(self.h, v.ctypes.data))
+        return v
 
     # -- relaxed objective ------------------------------------------------
     def relaxed_forward(self, x, g=None, beta: float = 10.0, m_ref: float = 10_000.0):

@@ -54,6 +54,15 @@ __device__ __forceinline__ double contrib_val(int64_t o, double metal, int64_t m
     return __dmul_rn(disc, __dsub_rn(cash, pen_of(o - target, a, e)));
 }
 
+// contrib_val in FP32 throughout (the FP32 shadow accumulators).
+__device__ __forceinline__ float contrib_val_f32(int64_t o, float metal, int64_t mined, int64_t target, double disc,
+                                                double pr, double pc, double mc, double a, double e) {
+    const float of = (float)o, dev = (float)(o - target);
+    const float cash = (float)pr * metal - (float)pc * of - (float)mc * (float)mined;
+    const float pen = dev < 0.0f ? (float)a * -dev : (float)e * dev;
+    return (float)disc * (cash - pen);
+}
+
 // Discounted net cash of period t in scenario s:
 //   d_t (price*rec*metal - pc*oreT - mc*minedT - pen_t(oreT)).
 __device__ __forceinline__ double contrib_of(int t, int s, int32_t S, const double *disc, const double *metal,
@@ -82,6 +91,9 @@ struct ApplyArgs {
     double *contrib;
     float *tab;
     float *ctab;  // nullptr when the period-pair table is not kept
+    // FP32 shadow accumulators (precision study; nullptr when off): the same
+    // per-period metal / contribution and NPV_s running totals kept in FP32
+    float *metal32, *contrib32, *npv32;
     const double *disc;
     const uint64_t *cap;
     const uint64_t *target;
@@ -243,6 +255,26 @@ static __device__ __noinline__ void apply_block(const ApplyArgs &A, int2 mv, int
             }
             my_npv = __dadd_rn(my_npv, dnpv);
             A.npv[s] = my_npv;
+            if (A.npv32) {
+                // the same update with FP32 running totals
+                float d32 = 0.0f;
+                const float g1f = (float)g1, g2f = (float)g2;
+                if (r1) {
+                    const float nM = A.metal32[i1] - g1f + g2f;
+                    const float c = contrib_val_f32(O1 + om2 - om1, nM, mined1, tgt1, disc1, A.pr, A.pc, A.mc, A.a, A.e);
+                    d32 += c - A.contrib32[i1];
+                    A.metal32[i1] = nM;
+                    A.contrib32[i1] = c;
+                }
+                if (r2) {
+                    const float nM = A.metal32[i2] - g2f + g1f;
+                    const float c = contrib_val_f32(O2 + om1 - om2, nM, mined2, tgt2, disc2, A.pr, A.pc, A.mc, A.a, A.e);
+                    d32 += c - A.contrib32[i2];
+                    A.metal32[i2] = nM;
+                    A.contrib32[i2] = c;
+                }
+                A.npv32[s] += d32;
+            }
         }
         if (A.ctab) {
             // period-pair table: rows and columns of the changed periods

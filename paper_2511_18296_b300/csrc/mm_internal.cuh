@@ -104,6 +104,7 @@ struct mm_model {
     uint64_t *step_cta = nullptr;    // fused search step: [step_max_ctas][32] published keys
     int step_max_ctas = 0;
     void *step_event = nullptr;      // cudaEvent_t recorded between the step's two launches (timing hook)
+    float *shadow32 = nullptr;       // FP32 shadow accumulators: metal [T][S], contrib [T][S], npv [S]
     float *relax_scratch = nullptr;  // relaxed objective: chunk partials / adjoint coefficients
     size_t relax_scratch_floats = 0;
 };

@@ -193,6 +193,37 @@ __global__ void k_npv(int32_t S, int32_t T, const double *__restrict__ disc, con
     npv[s] = acc;
 }
 
+// FP32 shadow accumulators from the current FP64 state: metal rounded to FP32,
+// the period contributions recomputed in FP32 from it and the exact integer
+// tonnages, NPV_s their FP32 sum in period order.
+__global__ void k_shadow_init(int32_t S, int32_t T, const double *__restrict__ disc, const double *__restrict__ metal,
+                              const int64_t *__restrict__ oreT, const int64_t *__restrict__ minedT,
+                              const uint64_t *__restrict__ target, double pr, double pc, double mc, double a, double e,
+                              float *__restrict__ shadow) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S) return;
+    float *metal32 = shadow, *contrib32 = shadow + (size_t)T * S, *npv32 = contrib32 + (size_t)T * S;
+    float acc = 0.0f;
+    for (int t = 0; t < T; t++) {
+        const size_t i = (size_t)t * S + s;
+        const float mf = (float)metal[i];
+        const float c = contrib_val_f32(oreT[i], mf, minedT[t], (int64_t)target[t], disc[t], pr, pc, mc, a, e);
+        metal32[i] = mf;
+        contrib32[i] = c;
+        acc += c;
+    }
+    npv32[s] = acc;
+}
+
+static mm_status shadow_init(mm_model *m) {
+    if (!m->shadow32) return MM_OK;
+    k_shadow_init<<<(m->S + 127) / 128, 128, 0, m->stream>>>(m->S, m->T, m->disc, m->metal, m->oreT, m->minedT,
+                                                             m->target, m->price * m->recovery, m->proc_cost,
+                                                             m->mining_cost, m->shortfall_pen, m->excess_pen,
+                                                             m->shadow32);
+    return check_launch("k_shadow_init");
+}
+
 // Apply kernel: the move comes either by value (from_dev = 0) or as
 // moves[idx[0]] when *count > 0 (from_dev = 1; an index outside the batch is a
 // bad move).
@@ -241,6 +272,9 @@ ApplyArgs apply_args(mm_model *m) {
     A.a = m->shortfall_pen; A.e = m->excess_pen;
     A.res = m->apply_res;
     A.status = m->status;
+    A.metal32 = m->shadow32;
+    A.contrib32 = m->shadow32 ? m->shadow32 + (size_t)m->T * m->S : nullptr;
+    A.npv32 = m->shadow32 ? m->shadow32 + 2 * (size_t)m->T * m->S : nullptr;
     return A;
 }
 
@@ -285,6 +319,7 @@ void mm_model_destroy(mm_model *m) {
     cudaFree(m->apply_res);
     cudaFree(m->step_cta);
     cudaFree(m->relax_scratch);
+    cudaFree(m->shadow32);
     if (m->apply_res_host) cudaFreeHost(m->apply_res_host);
     if (m->status_host) cudaFreeHost(m->status_host);
     topk_scratch_free(m->topk);
@@ -517,6 +552,7 @@ mm_status mm_schedule_set(mm_model *m, const uint8_t *period, int *base_feasible
                                            m->price * m->recovery, m->proc_cost, m->mining_cost, m->shortfall_pen,
                                            m->excess_pen, m->contrib, m->npv);
     if ((st = check_launch("k_npv")) != MM_OK) return done(st);
+    if ((st = shadow_init(m)) != MM_OK) return done(st);
     // base feasibility: arcs (device) + capacity (host, from minedT)
     uint32_t *d_bad = m->status_host ? nullptr : nullptr;
     TRY(cudaMemsetAsync(m->apply_res, 0, sizeof(ApplyResult), s), "clear apply result");
@@ -575,6 +611,33 @@ mm_status mm_apply_best(mm_model *m, const mm_move *moves, int64_t n, const int3
     ApplyArgs A = apply_args(m);
     k_apply<<<1, apply_threads(m), 0, m->stream>>>(A, make_int2(0, 0), (const int2 *)moves, n, idx, count, 1);
     return check_launch("k_apply");
+}
+
+mm_status mm_set_fp32_shadow(mm_model *m, int32_t enable) {
+    if (!m) return set_error(MM_ERR_INVALID_ARG, "NULL model");
+    if (!enable) {
+        MM_CUDA_TRY(cudaStreamSynchronize(m->stream), "synchronize");
+        cudaFree(m->shadow32);
+        m->shadow32 = nullptr;
+        return MM_OK;
+    }
+    if (!m->shadow32)
+        MM_CUDA_TRY(cudaMalloc(&m->shadow32, sizeof(float) * (2 * (size_t)m->T * m->S + m->S)),
+                    "allocate FP32 shadow accumulators");
+    return m->has_schedule ? shadow_init(m) : MM_OK;
+}
+
+mm_status mm_get_fp32_shadow_npv(mm_model *m, double *npv_host) {
+    if (!m || !npv_host) return set_error(MM_ERR_INVALID_ARG, "NULL argument");
+    if (!m->shadow32) return set_error(MM_ERR_STATE, "FP32 shadow accumulators are off");
+    if (!m->has_schedule) return set_error(MM_ERR_STATE, "no schedule installed");
+    std::vector<float> v(m->S);
+    MM_CUDA_TRY(cudaMemcpyAsync(v.data(), m->shadow32 + 2 * (size_t)m->T * m->S, sizeof(float) * m->S,
+                                cudaMemcpyDeviceToHost, m->stream),
+                "read FP32 shadow NPV");
+    MM_CUDA_TRY(cudaStreamSynchronize(m->stream), "synchronize");
+    for (int s = 0; s < m->S; s++) npv_host[s] = (double)v[s];
+    return read_sticky(m);
 }
 
 mm_status mm_last_apply(mm_model *m, int32_t *applied, double *mean, double *sd) {
