@@ -353,8 +353,8 @@ def gpu_arm(args):
             fn()
         return g
 
-    # the library records ev_mid between the step's evaluation and finisher
-    # launches (an external event node inside the graph)
+    # the library records ev_mid between the step's evaluation launch (with the
+    # top-k selection) and its apply launch (an external event node in the graph)
     ev_mid = torch.cuda.Event(enable_timing=True)
     ev_mid.record(stream)
     m.set_step_event(ev_mid)
@@ -379,7 +379,7 @@ def gpu_arm(args):
 
     def timed_step(K):
         """Per-step device times (ms) of the fused step: [step, evaluation
-        launch, finisher launch]; L2 flushed before every step.  ev_mid is
+        launch (with the top-k), apply launch]; L2 flushed before every step.  ev_mid is
         re-recorded by every replay, so each step is read before the next."""
         ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(K)]
         out = []
@@ -472,7 +472,7 @@ def gpu_arm(args):
                      "frac": achieved_gbs / peaks["hbm_gbs"], "traffic": profiled_traffic(),
                      "kernel": EVAL_KERNEL + " (evaluation launch of the fused step, with per-CTA top-32 lists)",
                      "kernel_ms": eval_avg_ms,
-                     "finisher_ms": finish_avg_ms,
+                     "apply_ms": finish_avg_ms,
                      "step_frac": alg / (step_avg_ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
                      "algorithmic_bytes_per_launch": alg, "peak_source": f"{which} (MEASURED_PEAKS.json hbm_gbs)"},
         "plain_form": {"desc": "mm_eval_moves, then mm_topk + mm_apply_best: one launch per call, same workload",
@@ -486,7 +486,7 @@ def gpu_arm(args):
                 "h2d_bytes_per_step": int(p.moves.nbytes), "d2h_bytes_per_step": TOPK * 8 + 4 + 24 + 4,
                 "ms_per_step": e2e_avg * 1e3,
                 "path": "pinned host moves -> mm_search_step (apply on device) -> top-k and NPV to host"},
-        "gpu_launches": 2 * K,  # per step: the evaluation launch and the finisher
+        "gpu_launches": 2 * K,  # per step: the evaluation launch (with the top-k) and the apply
         "clocks": clocks,
         "check": {"last_apply": applied, "npv_mean": npv_mean},
     }

@@ -162,11 +162,14 @@ mm_status mm_eval_moves_ex(mm_model *m, const mm_move *moves_dev, int64_t n, flo
  * Section 6 Phase 5, with an exact, deterministic selection).  Reads
  * score_dev[n], feasible_dev[n]; writes idx_dev[k] (move indices, best first),
  * topscore_dev[k] and *count_dev = min(k, number of feasible moves with a
- * non-NaN score).  -0.0 and +0.0 compare equal.  1 <= k <= 1024.
- * Device memory; asynchronous.  k <= 32: per-CTA warp lists of the 32 best
- * keys merged by one CTA (no allocation).  k > 32: histogram cut plus radix
- * select in model-owned scratch, grown on demand (the first call with a larger
- * n allocates).  Both give the same, exact result. */
+ * non-NaN score); topscore_dev[j] = score_dev[idx_dev[j]], except that a
+ * -0.0 score may come back as +0.0 (-0.0 and +0.0 compare equal in the
+ * selection).  1 <= k <= 1024.
+ * Device memory; asynchronous.  k <= 32: one launch; per-CTA warp lists of the
+ * 32 best keys, merged in two levels by the CTAs that finish last (model-owned
+ * lists, no allocation).  k > 32: histogram cut plus radix select in
+ * model-owned scratch, grown on demand (the first call with a larger n
+ * allocates).  Both give the same, exact result. */
 mm_status mm_topk(mm_model *m, const float *score_dev, const uint8_t *feasible_dev, int64_t n,
                   int32_t k, int32_t *idx_dev, float *topscore_dev, int32_t *count_dev);
 
@@ -176,9 +179,13 @@ mm_status mm_topk(mm_model *m, const float *score_dev, const uint8_t *feasible_d
  * feasible ones exactly as mm_topk (idx_dev[k], topscore_dev[k], *count_dev;
  * 1 <= k <= 32), and, if apply != 0, applies the best one on the device exactly
  * as mm_apply_best (outcome via mm_last_apply).  The evaluation launch keeps
- * each warp's 32 best keys in registers (warp shuffles) and publishes one list
- * per CTA; a one-CTA finisher merges the lists and applies.  Needs equal block
- * masses (else MM_ERR_INVALID_ARG; use the separate calls).  Asynchronous. */
+ * each warp's 32 best keys in registers (warp shuffles); each CTA publishes
+ * one list, the last CTA of each group of CTAs merges its group's lists and
+ * the last group merges the group lists and writes the top k (tickets, no
+ * waiting), all inside the same launch; a one-CTA launch then applies.  Needs
+ * equal block masses (else MM_ERR_INVALID_ARG; use the separate calls).
+ * Calls on one model must not overlap on the GPU (they share the model's
+ * list storage).  Asynchronous. */
 mm_status mm_search_step(mm_model *m, const mm_move *moves_dev, int64_t n, int32_t k, int32_t apply,
                          float *score_dev, uint8_t *feasible_dev, int32_t *idx_dev, float *topscore_dev,
                          int32_t *count_dev);
@@ -186,7 +193,8 @@ mm_status mm_search_step(mm_model *m, const mm_move *moves_dev, int64_t n, int32
 /* Timing hook; the paper has no counterpart.  When cuda_event (a cudaEvent_t
  * created with timing enabled, owned by the caller) is not NULL, every later
  * mm_search_step records it on the model's stream between its evaluation launch
- * and its finisher launch, so that the two can be timed apart; while the stream
+ * (which includes the top-k selection) and its apply launch, so that the two
+ * can be timed apart; while the stream
  * is being captured into a CUDA graph the record becomes an external event node.
  * NULL turns the hook off.  A failed record is MM_ERR_CUDA. */
 mm_status mm_set_step_event(mm_model *m, void *cuda_event);

@@ -39,11 +39,16 @@ __device__ __forceinline__ void table_entry(int t, int s, int32_t S, int32_t S_p
     tab[(int64_t)(T + 1) * S_pad + (int64_t)t * S_pad + s] = pi;
 }
 
-// Pout/Pin entry of period t, scenario s from its excess x = oreT - Q_t (t < T, s < S).
-__device__ __forceinline__ void table_store(int t, int s, int32_t S_pad, int32_t T, int64_t x, double d, int64_t m,
-                                            double a, double e, float *tab) {
-    tab[(int64_t)t * S_pad + s] = __double2float_rn(__dmul_rn(d, pen_diff(x, x - m, a, e)));
-    tab[(int64_t)(T + 1) * S_pad + (int64_t)t * S_pad + s] = __double2float_rn(__dmul_rn(d, pen_diff(x, x + m, a, e)));
+// The four x-independent table entries of period t (see table_store_c):
+// Pout at x = m (any x >= m), Pout at x = 0 (any x <= 0), Pin at x = 0 (any
+// x >= 0), Pin at x = -m (any x <= -m); zero for t = T.
+__device__ __forceinline__ float4 table_consts(int t, int32_t T, const double *disc, int64_t m, double a, double e) {
+    if (t >= T) return make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    const double d = disc[t];
+    return make_float4(__double2float_rn(__dmul_rn(d, pen_diff(m, 0, a, e))),
+                       __double2float_rn(__dmul_rn(d, pen_diff(0, -m, a, e))),
+                       __double2float_rn(__dmul_rn(d, pen_diff(0, m, a, e))),
+                       __double2float_rn(__dmul_rn(d, pen_diff(-m, 0, a, e))));
 }
 
 // Discounted net cash of a period from its accumulators (pure form):
@@ -90,6 +95,7 @@ struct ApplyArgs {
     double *npv;
     double *contrib;
     float *tab;
+    const float4 *tabc;  // [T+1] Pout / Pin constants far from the target (uniform mass)
     float *ctab;  // nullptr when the period-pair table is not kept
     // FP32 shadow accumulators (precision study; nullptr when off): the same
     // per-period metal / contribution and NPV_s running totals kept in FP32
@@ -98,55 +104,112 @@ struct ApplyArgs {
     const uint64_t *cap;
     const uint64_t *target;
     double pr, pc, mc, a, e;
+    double invS;  // 1 / S
     ApplyResult *res;
     uint32_t *status;
 };
 
-// Apply one move on a single CTA: exact re-check, period update, integer
-// tonnages, FP64 metal, lo/hi of the neighbourhood, tables and NPV
-// contributions of the affected periods (NPV_s += new - old), then the FP64
-// mean/std of NPV over scenarios (computed whether or not the move applied).
-// The move comes either by value (from_dev = 0) or as moves[idx[0]] when
-// *count > 0 (from_dev = 1).
-// Sum over the block of one FP64 value per thread, where only threads s < n
-// hold values: only the warps holding values reduce (FP64 is scarce on this
-// part), and thread 0 combines their partials.  Result valid in thread 0.
-static __device__ __forceinline__ double block_sum_f64(double x, int n, double *red) {
-    const int nwv = (n + 31) >> 5;  // warps holding values
-    const int warp = threadIdx.x >> 5;
-    if (warp < nwv) {
-        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-        if ((threadIdx.x & 31) == 0) red[warp] = x;
-    }
-    __syncthreads();
-    double t = 0.0;
-    if (threadIdx.x == 0)
-        for (int w = 0; w < nwv; w++) t += red[w];
-    __syncthreads();
-    return t;
+// Sum over one warp of one FP64 value per lane (xor tree: every lane gets it).
+static __device__ __forceinline__ double warp_sum_f64(double x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x = __dadd_rn(x, __shfl_xor_sync(0xffffffffu, x, o));
+    return x;
 }
 
-// The whole CTA applies one move (blockDim.x >= S; any block size from 64):
+// j-th block (0..21) whose lo/hi bounds a move of b1 (and b2) can change on the
+// 1-5 grid: j = 11q + r, q = 0 for b1, 1 for b2; r = 0 the block itself,
+// r = 1..10 the neighbour (dx, dy) of pattern entry (r - 1) / 2 one level up
+// (r odd) or down (r even).  -1 when it does not exist.
+static __device__ __forceinline__ int32_t apply_neighbour(const Topo &tp, int32_t b1, int32_t b2, int j) {
+    const int32_t b = j < 11 ? b1 : b2;
+    const int r = j < 11 ? j : j - 11;
+    if (b < 0) return -1;
+    if (r == 0) return b;
+    const int32_t nxy = tp.nx * tp.ny;
+    const int32_t x = b % tp.nx, y = (b / tp.nx) % tp.ny, z = b / nxy;
+    const int k = (r - 1) >> 1;
+    const int32_t px = x + (k == 1 ? -1 : (k == 2 ? 1 : 0)), py = y + (k == 3 ? -1 : (k == 4 ? 1 : 0));
+    const int32_t pz = (r & 1) ? z - 1 : z + 1;
+    if (px < 0 || px >= tp.nx || py < 0 || py >= tp.ny || pz < 0 || pz >= tp.nz) return -1;
+    return px + tp.nx * (py + tp.ny * pz);
+}
+
+// Pout / Pin entries of period t, scenario s, for uniform block mass m from the
+// excess x = oreT - Q_t.  Away from the target the entries do not depend on x:
+// tc = (Pout for x >= m, Pout for x <= 0, Pin for x >= 0, Pin for x <= -m) holds
+// the same FP64 expression evaluated at a representative x (same bits as
+// table_entry); in between the expression is evaluated here.
+static __device__ __forceinline__ void table_store_c(int t, int s, int32_t S_pad, int32_t T, int64_t x, float4 tc,
+                                                     double d, int64_t m, double a, double e, float *tab) {
+    const float po = x >= m ? tc.x : (x <= 0 ? tc.y : __double2float_rn(__dmul_rn(d, pen_diff(x, x - m, a, e))));
+    const float pi = x >= 0 ? tc.z : (x <= -m ? tc.w : __double2float_rn(__dmul_rn(d, pen_diff(x, x + m, a, e))));
+    tab[(int64_t)t * S_pad + s] = po;
+    tab[(int64_t)(T + 1) * S_pad + (int64_t)t * S_pad + s] = pi;
+}
+
+// Period-pair rows and columns of periods ra and rb (see apply_block), by
+// worker w of nw (a warp each); tab and ctab do not overlap.
+static __device__ __forceinline__ void ctab_rebuild(const float *__restrict__ tb, float *__restrict__ ct, uint32_t T1,
+                                                    uint32_t S, size_t sp, uint32_t ra, uint32_t rb, int w, int nw,
+                                                    int lane) {
+    const uint32_t nsl = (S + 31) / 32;  // scenario slots of 32
+    const uint32_t items = T1 * nsl;
+    const size_t pin = (size_t)T1 * sp;
+    for (uint32_t i0 = (uint32_t)w; i0 < items; i0 += 4u * (uint32_t)nw) {
+        float pob[4], pib[4], poa[4], pia[4], por[4], pir[4];
+        uint32_t bb[4], ss[4];
+        bool ok[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const uint32_t it = i0 + (uint32_t)u * (uint32_t)nw;
+            bb[u] = it / nsl;
+            ss[u] = (it - bb[u] * nsl) * 32u + (uint32_t)lane;
+            ok[u] = it < items && ss[u] < S;
+            if (ok[u]) {
+                pob[u] = tb[bb[u] * sp + ss[u]];
+                pib[u] = tb[pin + bb[u] * sp + ss[u]];
+                poa[u] = tb[ra * sp + ss[u]];
+                pia[u] = tb[pin + ra * sp + ss[u]];
+                por[u] = tb[rb * sp + ss[u]];
+                pir[u] = tb[pin + rb * sp + ss[u]];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            if (!ok[u]) continue;
+            const uint32_t b = bb[u];
+            const size_t s2 = ss[u];
+            ct[((size_t)ra * T1 + b) * sp + s2] = poa[u] + pib[u];
+            ct[((size_t)b * T1 + ra) * sp + s2] = pob[u] + pia[u];
+            ct[((size_t)rb * T1 + b) * sp + s2] = por[u] + pib[u];
+            ct[((size_t)b * T1 + rb) * sp + s2] = pob[u] + pir[u];
+        }
+    }
+}
+
+// Apply one move on a single CTA (blockDim.x >= max(S, 64), a multiple of 32):
 //   1. one round trip of independent loads: the moved blocks' schedule words
 //      and masses, every period's tonnage and capacity, and per scenario
 //      (thread s) the moved blocks' ore bits and FP64 grades;
-//   2. thread 0 re-checks the move exactly and updates periods and tonnage;
-//   3. per scenario: the two affected periods' ore tonnage, metal, NPV
-//      contribution and table entries (NPV_s += new - old), and the lo/hi
-//      bounds of the moved blocks' neighbourhood;
-//   4. FP64 mean and population std of NPV over scenarios, computed whether
-//      or not the move applied.
+//   2. thread 0 re-checks the move exactly and updates the mined tonnage;
+//   3. the last warp rewrites the packed period/lo/hi words of the moved
+//      blocks and their grid neighbours (the moved blocks' new periods come
+//      from the move, so the lanes need no ordering among themselves), while
+//      thread s updates scenario s: the two affected periods' ore tonnage,
+//      metal, NPV contribution and table entries (NPV_s += new - old);
+//   4. warp 0 forms the FP64 mean and population std of NPV over scenarios
+//      (two passes; computed whether or not the move applied) while the other
+//      warps rebuild the period-pair rows of the changed periods.
 // have = 0: nothing to apply (statistics only).
 static __device__ __noinline__ void apply_block(const ApplyArgs &A, int2 mv, int have) {
     __shared__ MoveView sv;
     __shared__ int s_go;
-    __shared__ int32_t s_nb[32];
-    __shared__ int s_nnb;
     __shared__ int64_t s_mined[kMaxT + 1];
     __shared__ uint64_t s_cap[kMaxT + 1];
     __shared__ uint32_t s_w[2], s_m[2];
-    __shared__ double red[33];
-    const int s = threadIdx.x;
+    __shared__ double s_npv[kMaxS];
+    const int s = threadIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarp = blockDim.x >> 5;
     const bool hs = s < A.S;
     const int32_t b1 = mv.x, b2 = mv.y;
     const bool ok1 = have && b1 >= 0 && b1 < A.tp.B;
@@ -162,6 +225,7 @@ static __device__ __noinline__ void apply_block(const ApplyArgs &A, int2 mv, int
     const uint32_t o2 = (hs && ok2) ? ore_bit(A.val, A.R, A.ore_off, b2, s) : 0u;
     const double gr1 = (hs && ok1) ? A.grade[(int64_t)b1 * A.S + s] : 0.0;
     const double gr2 = (hs && ok2) ? A.grade[(int64_t)b2 * A.S + s] : 0.0;
+    double my_npv = hs ? A.npv[s] : 0.0;
     __syncthreads();
     // 2. exact re-check and the scalar updates
     if (threadIdx.x == 0) {
@@ -185,39 +249,39 @@ static __device__ __noinline__ void apply_block(const ApplyArgs &A, int2 mv, int
             const int64_t dm1 = v.m1, dm2 = v.swap ? (int64_t)v.m2 : 0;
             if (v.t1 < (uint32_t)A.T) A.minedT[v.t1] = (s_mined[v.t1] += -dm1 + dm2);
             if (v.t2 < (uint32_t)A.T) A.minedT[v.t2] = (s_mined[v.t2] += dm1 - dm2);
-            A.blk[v.b1] = (s_w[0] & ~0xffu) | v.t2;  // lo/hi are recomputed below
-            if (v.swap) A.blk[v.b2] = (s_w[1] & ~0xffu) | v.t1;
-            // neighbourhood whose lo/hi may change: moved blocks and their neighbours
-            int n = 0;
-            const int32_t mb[2] = {v.b1, v.swap ? v.b2 : -1};
-            for (int q = 0; q < 2; q++) {
-                const int32_t b = mb[q];
-                if (b < 0) continue;
-                s_nb[n++] = b;
-                if (A.tp.nx > 0) {
-                    const int32_t nxy = A.tp.nx * A.tp.ny;
-                    const int32_t x = b % A.tp.nx, y = (b / A.tp.nx) % A.tp.ny, z = b / nxy;
-                    const int dx[5] = {0, -1, 1, 0, 0};
-                    const int dy[5] = {0, 0, 0, -1, 1};
-                    for (int k = 0; k < 5; k++) {
-                        const int32_t px = x + dx[k], py = y + dy[k];
-                        if (px < 0 || px >= A.tp.nx || py < 0 || py >= A.tp.ny) continue;
-                        if (z > 0) s_nb[n++] = px + A.tp.nx * (py + A.tp.ny * (z - 1));
-                        if (z + 1 < A.tp.nz) s_nb[n++] = px + A.tp.nx * (py + A.tp.ny * (z + 1));
-                    }
-                }
-            }
-            s_nnb = n;
         }
     }
     __syncthreads();
-    // 3. per-scenario updates of the two affected periods
-    double my_npv = hs ? A.npv[s] : 0.0;
+    // 3. schedule words of the neighbourhood, per-scenario updates
     if (s_go) {
         const MoveView v = sv;
-        if (A.tp.nx > 0 && threadIdx.x < (unsigned)s_nnb) {
-            const int32_t b = s_nb[threadIdx.x];
-            A.blk[b] = block_bounds(A.tp, b, [&](int32_t j) { return blk_period(A.blk[j]); });
+        const int32_t mb2 = v.swap ? v.b2 : -1;
+        // period of block j after the move: the moved blocks' from the move, the
+        // others' from their words (of which only the lo/hi bits change here)
+        auto period_after = [&](int32_t j) -> uint32_t {
+            if (j == v.b1) return v.t2;
+            if (j == mb2) return v.t1;
+            return blk_period(A.blk[j]);
+        };
+        if (A.tp.nx > 0) {
+            if (warp == nwarp - 1 && lane < 22) {
+                const int32_t b = apply_neighbour(A.tp, v.b1, mb2, lane);
+                if (b >= 0) A.blk[b] = block_bounds(A.tp, b, period_after);
+            }
+        } else {
+            // CSR: the moved blocks and every direct predecessor and successor
+            for (int q = 0; q < 2; q++) {
+                const int32_t b = q == 0 ? v.b1 : mb2;
+                if (b < 0) continue;
+                const int32_t np = A.tp.pred_ptr[b + 1] - A.tp.pred_ptr[b];
+                const int32_t ns = A.tp.succ_ptr[b + 1] - A.tp.succ_ptr[b];
+                for (int k = threadIdx.x; k <= np + ns; k += blockDim.x) {
+                    const int32_t j = k == np + ns ? b
+                                                   : (k < np ? A.tp.pred_idx[A.tp.pred_ptr[b] + k]
+                                                             : A.tp.succ_idx[A.tp.succ_ptr[b] + k - np]);
+                    A.blk[j] = block_bounds(A.tp, j, period_after);
+                }
+            }
         }
         if (hs) {
             const bool r1 = v.t1 < (uint32_t)A.T, r2 = v.t2 < (uint32_t)A.T;
@@ -227,6 +291,9 @@ static __device__ __noinline__ void apply_block(const ApplyArgs &A, int2 mv, int
             const double C1 = r1 ? A.contrib[i1] : 0.0, C2 = r2 ? A.contrib[i2] : 0.0;
             const int64_t tgt1 = r1 ? (int64_t)A.target[v.t1] : 0, tgt2 = r2 ? (int64_t)A.target[v.t2] : 0;
             const double disc1 = r1 ? A.disc[v.t1] : 0.0, disc2 = r2 ? A.disc[v.t2] : 0.0;
+            const float4 zero4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            const float4 tc1 = (r1 && A.uniform) ? A.tabc[v.t1] : zero4;
+            const float4 tc2 = (r2 && A.uniform) ? A.tabc[v.t2] : zero4;
             const int64_t mined1 = r1 ? s_mined[v.t1] : 0, mined2 = r2 ? s_mined[v.t2] : 0;
             const int64_t om1 = o1 ? (int64_t)v.m1 : 0, om2 = (v.swap && o2) ? (int64_t)v.m2 : 0;
             const double g1 = o1 ? __dmul_rn((double)v.m1, gr1) : 0.0;
@@ -241,7 +308,7 @@ static __device__ __noinline__ void apply_block(const ApplyArgs &A, int2 mv, int
                 A.oreT[i1] = nO;
                 A.metal[i1] = nM;
                 A.contrib[i1] = c;
-                if (A.uniform) table_store(v.t1, s, A.S_pad, A.T, nO - tgt1, disc1, mu_, A.a, A.e, A.tab);
+                if (A.uniform) table_store_c(v.t1, s, A.S_pad, A.T, nO - tgt1, tc1, disc1, mu_, A.a, A.e, A.tab);
             }
             if (r2) {
                 const int64_t nO = O2 + om1 - om2;
@@ -251,7 +318,7 @@ static __device__ __noinline__ void apply_block(const ApplyArgs &A, int2 mv, int
                 A.oreT[i2] = nO;
                 A.metal[i2] = nM;
                 A.contrib[i2] = c;
-                if (A.uniform) table_store(v.t2, s, A.S_pad, A.T, nO - tgt2, disc2, mu_, A.a, A.e, A.tab);
+                if (A.uniform) table_store_c(v.t2, s, A.S_pad, A.T, nO - tgt2, tc2, disc2, mu_, A.a, A.e, A.tab);
             }
             my_npv = __dadd_rn(my_npv, dnpv);
             A.npv[s] = my_npv;
@@ -276,57 +343,34 @@ static __device__ __noinline__ void apply_block(const ApplyArgs &A, int2 mv, int
                 A.npv32[s] += d32;
             }
         }
-        if (A.ctab) {
-            // period-pair table: rows and columns of the changed periods
-            __syncthreads();  // the new Pout / Pin entries of t1 and t2 are written
-            const uint32_t T = (uint32_t)A.T, T1 = T + 1;
-            const bool c1 = v.t1 < T, c2 = v.t2 < T && v.t2 != v.t1;
-            if (c1 || c2) {
-                const uint32_t ra = c1 ? v.t1 : v.t2, rb = c2 ? v.t2 : ra;
-                const size_t sp = (size_t)A.S_pad, pin = (size_t)T1 * sp;
-                const float *tb = A.tab;
-                for (int j = threadIdx.x; j < (int)T1 * A.S; j += blockDim.x) {
-                    const uint32_t b = (uint32_t)(j / A.S), s2 = (uint32_t)(j - (int)b * A.S);
-                    const float pob = tb[b * sp + s2], pib = tb[pin + b * sp + s2];
-                    const float poa = tb[ra * sp + s2], pia = tb[pin + ra * sp + s2];
-                    const float por = tb[rb * sp + s2], pir = tb[pin + rb * sp + s2];
-                    A.ctab[((size_t)ra * T1 + b) * sp + s2] = poa + pib;
-                    A.ctab[((size_t)b * T1 + ra) * sp + s2] = pob + pia;
-                    A.ctab[((size_t)rb * T1 + b) * sp + s2] = por + pib;
-                    A.ctab[((size_t)b * T1 + rb) * sp + s2] = pob + pir;
-                }
-            }
-        }
-        if (A.tp.nx == 0) {
-            // CSR: the moved blocks first, then every predecessor and successor
-            if (threadIdx.x < 2) {
-                const int32_t b = threadIdx.x == 0 ? v.b1 : (v.swap ? v.b2 : -1);
-                if (b >= 0) A.blk[b] = block_bounds(A.tp, b, [&](int32_t j) { return blk_period(A.blk[j]); });
-            }
-            __syncthreads();
-            for (int q = 0; q < 2; q++) {
-                const int32_t b = q == 0 ? v.b1 : (v.swap ? v.b2 : -1);
-                if (b < 0) continue;
-                const int32_t np = A.tp.pred_ptr[b + 1] - A.tp.pred_ptr[b];
-                const int32_t ns = A.tp.succ_ptr[b + 1] - A.tp.succ_ptr[b];
-                for (int k = threadIdx.x; k < np + ns; k += blockDim.x) {
-                    const int32_t j = k < np ? A.tp.pred_idx[A.tp.pred_ptr[b] + k] : A.tp.succ_idx[A.tp.succ_ptr[b] + k - np];
-                    A.blk[j] = block_bounds(A.tp, j, [&](int32_t i) { return blk_period(A.blk[i]); });
-                }
-                __syncthreads();
-            }
-        }
     }
-    // 4. statistics (two passes, values in registers; thread 0 divides)
-    const double sum = block_sum_f64(my_npv, A.S, red);
-    if (threadIdx.x == 0) red[32] = sum / A.S;
-    __syncthreads();
-    const double mean = red[32];
-    const double dv = hs ? my_npv - mean : 0.0;
-    const double ss = block_sum_f64(dv * dv, A.S, red);
-    if (threadIdx.x == 0) {
-        A.res->mean = mean;
-        A.res->std = sqrt(ss / A.S);
+    if (hs) s_npv[s] = my_npv;
+    __syncthreads();  // NPV_s staged; the new Pout / Pin entries of t1 and t2 are written
+    // 4. statistics (warp 0) beside the period-pair rows (the other warps)
+    if (warp == 0) {
+        double sum = 0.0;
+        for (int i = lane; i < A.S; i += 32) sum = __dadd_rn(sum, s_npv[i]);
+        const double mean = __dmul_rn(warp_sum_f64(sum), A.invS);
+        double ss = 0.0;
+        for (int i = lane; i < A.S; i += 32) {
+            const double dv = __dsub_rn(s_npv[i], mean);
+            ss = __fma_rn(dv, dv, ss);
+        }
+        ss = warp_sum_f64(ss);
+        if (lane == 0) {
+            A.res->mean = mean;
+            A.res->std = sqrt(__dmul_rn(ss, A.invS));
+        }
+    } else if (s_go && A.ctab) {
+        // ctab[a][b][s] = Pout[a][s] + Pin[b][s] for the rows a and columns b of
+        // the changed periods.  Work items (b, scenario slot) go round the warps
+        // 1..nwarp-1; each lane issues the loads of four items before their
+        // stores, so a round costs one memory round trip.
+        const MoveView v = sv;
+        const uint32_t T = (uint32_t)A.T, T1 = T + 1;
+        const bool c1 = v.t1 < T, c2 = v.t2 < T && v.t2 != v.t1;
+        if (c1 || c2) ctab_rebuild(A.tab, A.ctab, T1, (uint32_t)A.S, (size_t)A.S_pad, c1 ? v.t1 : v.t2,
+                                   c2 ? v.t2 : (c1 ? v.t1 : v.t2), warp - 1, nwarp - 1, lane);
     }
 }
 

@@ -159,7 +159,7 @@ __global__ void __launch_bounds__(kEvalThreads, MM_EVAL_MINB) k_batch_eval(Batch
             __threadfence();
             const uint64_t t = block_merge_lists<NW>(B.lists + (size_t)list0 * 32, n_items, s_wl);
             if (warp == 0) {
-                const int best = warp_write_topk(t, C->k, sA.n, sA.status, sA.score, C->idx_out, C->top_out,
+                const int best = warp_write_topk(t, C->k, sA.n, sA.status, C->idx_out, C->top_out,
                                                  C->count_out);
                 if (lane == 0) s_best = best;
             }

@@ -138,6 +138,18 @@ int default_team(int S) {
 
 // Evaluator arguments for a batch of n moves on model m (the step fields
 // cleared).
+StepLists step_lists(mm_model *m, int grid) {
+    StepLists L;
+    L.cta = m->step_cta;
+    L.grp = m->step_grp;
+    L.tick = m->step_tick;
+    L.final_slot = m->step_max_ctas;
+    int g = 1;
+    while (g * g < grid) g++;  // about sqrt(grid) CTAs per group and groups
+    L.grp_size = g;
+    return L;
+}
+
 EvalArgs eval_args(mm_model *m, const mm_move *moves, int64_t n, float *score, uint8_t *feas, float *mean,
                    float *delta) {
     EvalArgs A;
@@ -157,8 +169,11 @@ EvalArgs eval_args(mm_model *m, const mm_move *moves, int64_t n, float *score, u
     A.lambda = (float)m->lambda;
     A.a = m->shortfall_pen; A.e = m->excess_pen;
     A.qpl = 0;
-    A.k = 0; A.do_apply = 0; A.idx_out = nullptr; A.top_out = nullptr; A.count_out = nullptr;
-    A.step_cta = m->step_cta;
+    A.tail = StepTail{};
+    A.tail.L = step_lists(m, 1);
+    A.tail.n = n;
+    A.tail.status = m->status;
+    A.tail.moves = A.moves;
     return A;
 }
 
@@ -166,11 +181,12 @@ mm_status eval_launch(mm_model *m, const mm_move *moves, int64_t n, float *score
                       float *delta, int32_t options, int team, int ctas_per_sm, int stages, const StepOut *step) {
     EvalArgs A = eval_args(m, moves, n, score, feas, mean, delta);
     if (step) {
-        A.k = step->k;
-        A.do_apply = step->apply;
-        A.idx_out = step->idx;
-        A.top_out = step->top;
-        A.count_out = step->count;
+        A.tail.k = step->k;
+        A.tail.idx_out = step->idx;
+        A.tail.top_out = step->top;
+        A.tail.count_out = step->count;
+        A.tail.do_apply = step->apply;
+        if (step->apply) A.tail.ap = apply_args(m);
         stages = 0;  // the fused step runs on direct loads
     }
     const bool kahan = (options & MM_EVAL_KAHAN) != 0;
@@ -256,6 +272,7 @@ mm_status eval_launch(mm_model *m, const mm_move *moves, int64_t n, float *score
     if (blocks > grid_cap) blocks = grid_cap;
     if (blocks < 1) blocks = 1;
     if (step) const_cast<StepOut *>(step)->grid = (int)blocks;
+    A.tail.L = step_lists(m, (int)blocks);
     fn<<<(unsigned)blocks, kEvalThreads, smem, m->stream>>>(A);
     return check_launch("k_eval_tiled");
 }

@@ -31,6 +31,32 @@ namespace mm {
 constexpr int kEvalThreads = 256;  // threads per CTA
 constexpr int kChunk = 64;         // moves a warp decodes at once (two per lane)
 
+// Where a batch's top-k lists meet: the per-CTA lists, the merged lists of
+// groups of CTAs and the tickets that pick the merging CTAs.
+struct StepLists {
+    uint64_t *cta;        // [grid][32] each CTA's 32 best keys
+    uint64_t *grp;        // [groups][32] each group's 32 best keys
+    uint32_t *tick;       // [groups] group tickets; tick[final_slot] the final ticket
+    int32_t final_slot;
+    int32_t grp_size;     // CTAs per group (the last group may be smaller)
+};
+
+// What the end of a top-k launch needs (step_reduce): the lists, the
+// outputs, and for an in-launch apply of the best move the batch and the
+// model's apply arguments.
+struct StepTail {
+    StepLists L;
+    int32_t k;             // top-k size, 1..32
+    int64_t n;             // moves in the batch
+    uint32_t *status;      // sticky status bits
+    int32_t *idx_out;      // [k]
+    float *top_out;        // [k]
+    int32_t *count_out;    // [1]
+    int32_t do_apply;      // the final CTA applies the best move (S <= CTA threads)
+    const int2 *moves;     // the batch (do_apply)
+    ApplyArgs ap;          // (do_apply)
+};
+
 struct EvalArgs {
     const int2 *moves;
     int64_t n;
@@ -58,13 +84,7 @@ struct EvalArgs {
     int32_t prefetch;      // direct-load path: batches whose rows are prefetched into L1 ahead
     float lambda;
     double a, e;
-    // fused search step (TOPK kernels only)
-    int32_t k;             // top-k size, 1..32
-    int32_t do_apply;      // apply the best feasible move at the end
-    int32_t *idx_out;      // [k]
-    float *top_out;        // [k]
-    int32_t *count_out;    // [1]
-    uint64_t *step_cta;    // [grid][32] per-CTA top-32 keys
+    StepTail tail;         // fused search step (TOPK kernels only)
 };
 
 // ---------------------------------------------------------------- warp top-k
@@ -508,12 +528,12 @@ __device__ __forceinline__ uint64_t block_merge_lists(const uint64_t *lists, int
 }
 
 // Called by one full warp with the merged list t: writes the top k (move
-// indices, their scores read back from score[], the count) and returns the
+// indices, their scores decoded from the keys, the count) and returns the
 // best move's index in every lane, -1 when nothing is feasible.  A key always
 // decodes to a move of the batch; the range check (< n) makes sure a corrupted
 // list can never turn into an out-of-range access (it raises the bad-move bit).
-__device__ __forceinline__ int warp_write_topk(uint64_t t, int k, int64_t n, uint32_t *status, const float *score,
-                                               int32_t *idx_out, float *top_out, int32_t *count_out) {
+__device__ __forceinline__ int warp_write_topk(uint64_t t, int k, int64_t n, uint32_t *status, int32_t *idx_out,
+                                               float *top_out, int32_t *count_out) {
     const int lane = threadIdx.x & 31;
     const uint32_t valid = __ballot_sync(0xffffffffu, t != 0ull);
     int cnt = min(__popc(valid), k);
@@ -527,11 +547,111 @@ __device__ __forceinline__ int warp_write_topk(uint64_t t, int k, int64_t n, uin
     const uint32_t id0 = __shfl_sync(0xffffffffu, id, 0);
     if (lane < cnt) {
         idx_out[lane] = (int32_t)id;
-        top_out[lane] = __ldcg(score + id);
+        // the key's upper half is the score's order-preserving image: invert
+        // it (a -0.0 score, folded into +0.0 by the key, comes back as +0.0)
+        const uint32_t ord = (uint32_t)(t >> 32);
+        top_out[lane] = __uint_as_float((ord & 0x80000000u) ? (ord & 0x7fffffffu) : ~ord);
     }
     if (lane == 0) *count_out = cnt;
     return cnt > 0 ? (int)id0 : -1;
 }
+
+// Ticket counter increment with acquire-release semantics at GPU scope: it
+// publishes what the calling CTA wrote before its barrier (release is
+// cumulative over the barrier) and makes visible what the CTAs that drew the
+// earlier numbers published.
+__device__ __forceinline__ uint32_t ticket_next(uint32_t *p) {
+    uint32_t old;
+    asm volatile("atom.add.acq_rel.gpu.u32 %0, [%1], 1;" : "=r"(old) : "l"(p) : "memory");
+    return old;
+}
+
+// Non-binding prefetch into L2 of [p, p + bytes), 128-byte lines; thread i of
+// nt takes lines i, i + nt, ...
+__device__ __forceinline__ void prefetch_l2_range(const void *p, size_t bytes, int i, int nt) {
+    const char *c = static_cast<const char *>(p);
+    for (size_t o = (size_t)i * 128; o < bytes; o += (size_t)nt * 128)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(c + o));
+}
+
+// End of a batch's top-k selection, called by every thread of every CTA with
+// the warp's list wtk.  The CTA merges its warps' lists (a tree) and publishes
+// its 32 best keys; the last CTA of each group of grp_size CTAs to finish (a
+// ticket counter per group; nobody waits) merges the group's lists into one;
+// the last group to finish merges the group lists, writes the top k and, when
+// asked, applies the best move.  Each ticket is reset by the CTA that draws its
+// last number, so every counter is zero again for the next launch.  Two levels
+// of about sqrt(grid) lists each keep the merging short, and all but the last
+// group merge while others still evaluate.  Before an in-launch apply, the
+// group-merging CTAs pull the apply's per-period state and the grade rows of
+// their group's best move into L2.
+// Not inlined: the evaluator's main loop keeps its own register allocation.
+static __device__ __noinline__ void step_reduce(const StepTail &T, uint64_t wtk) {
+    constexpr int NW = kEvalThreads / 32;
+    __shared__ uint64_t s_wl[NW][32];
+    __shared__ int s_last, s_best;
+    const StepLists &L = T.L;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    s_wl[warp][lane] = wtk;
+    __syncthreads();
+#pragma unroll
+    for (int stride = NW / 2; stride > 0; stride >>= 1) {
+        if (warp < stride) {
+            wtk = warp_topk_merge(wtk, s_wl[warp + stride][lane]);
+            s_wl[warp][lane] = wtk;
+        }
+        __syncthreads();
+    }
+    if (warp == 0) L.cta[(size_t)blockIdx.x * 32 + lane] = wtk;
+    __syncthreads();
+    const int g = (int)blockIdx.x / L.grp_size, g0 = g * L.grp_size;
+    const int gn = min(L.grp_size, (int)gridDim.x - g0);
+    const int ng = ((int)gridDim.x + L.grp_size - 1) / L.grp_size;
+    if (tid == 0) s_last = ticket_next(L.tick + g) == (uint32_t)(gn - 1);
+    __syncthreads();
+    if (!s_last) return;
+    uint64_t t = block_merge_lists<NW>(L.cta + (size_t)g0 * 32, gn, s_wl);
+    if (warp == 0) L.grp[(size_t)g * 32 + lane] = t;
+    if (tid == 0) L.tick[g] = 0;
+    if (T.do_apply) {
+        const ApplyArgs &P = T.ap;
+        const size_t ts = (size_t)P.T * P.S, t1s = (size_t)(P.T + 1) * P.S;
+        const int i = g * kEvalThreads + tid, nt = ng * kEvalThreads;
+        prefetch_l2_range(P.oreT, t1s * sizeof(int64_t), i, nt);
+        prefetch_l2_range(P.metal, ts * sizeof(double), i, nt);
+        prefetch_l2_range(P.contrib, ts * sizeof(double), i, nt);
+        prefetch_l2_range(P.npv, (size_t)P.S * sizeof(double), i, nt);
+        prefetch_l2_range(P.tab, (size_t)2 * (P.T + 1) * P.S_pad * sizeof(float), i, nt);
+        if (warp == 0) {
+            const uint64_t best = __shfl_sync(0xffffffffu, t, 0);
+            const uint32_t id = ~(uint32_t)(best & 0xffffffffull);
+            if (best != 0ull && (int64_t)id < T.n) {
+                const int2 mv = __ldg(T.moves + id);
+                const size_t row = (size_t)P.S * sizeof(double);
+                if (mv.x >= 0 && mv.x < P.tp.B) prefetch_l2_range(P.grade + (size_t)mv.x * P.S, row, lane, 32);
+                if (mv.y >= 0 && mv.y < P.tp.B) prefetch_l2_range(P.grade + (size_t)mv.y * P.S, row, lane, 32);
+            }
+        }
+    }
+    __syncthreads();
+    if (tid == 0) s_last = ticket_next(L.tick + L.final_slot) == (uint32_t)(ng - 1);
+    __syncthreads();
+    if (!s_last) return;
+    t = block_merge_lists<NW>(L.grp, ng, s_wl);
+    if (warp == 0) {
+        const int best = warp_write_topk(t, T.k, T.n, T.status, T.idx_out, T.top_out, T.count_out);
+        if (lane == 0) s_best = best;
+    }
+    if (tid == 0) L.tick[L.final_slot] = 0;
+    if (!T.do_apply) return;
+    __syncthreads();
+    const int b = s_best;
+    const int2 mv = b >= 0 ? __ldg(T.moves + b) : make_int2(0, -1);
+    apply_block(T.ap, mv, b >= 0 ? 1 : 0);
+}
+
+// List storage and tickets of model m for a launch of `grid` CTAs (mm_eval.cu).
+StepLists step_lists(mm_model *m, int grid);
 
 // Evaluator arguments for a batch of n moves on model m (mm_eval.cu).
 EvalArgs eval_args(mm_model *m, const mm_move *moves, int64_t n, float *score, uint8_t *feas, float *mean,
@@ -731,7 +851,7 @@ __global__ void __launch_bounds__(kEvalThreads, MM_EVAL_MINB) k_eval_tiled(EvalA
     const int64_t r0 = gw * A.n / nwarps, r1 = (gw + 1) * A.n / nwarps;
     uint64_t wtk = 0;  // this warp's best 32 candidate keys (TOPK)
     eval_warp_range<TEAM, QMAX, KAHAN, DELTA, KF, TAIL, TOPK>(A, sh, s_lut, tab, s_dd, s_mined, s_cap, r0, r1, wtk);
-    if constexpr (TOPK) step_publish(A.step_cta + (size_t)blockIdx.x * 32, wtk);
+    if constexpr (TOPK) step_reduce(A.tail, wtk);
 }
 
 // ----------------------------------------------------------------------------

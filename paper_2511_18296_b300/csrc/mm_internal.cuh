@@ -91,6 +91,7 @@ struct mm_model {
     double *npv = nullptr;       // [S]
     double *contrib = nullptr;   // [T][S]    d_t (cash - penalty) per period
     float *tab = nullptr;        // [2][T+1][S_pad]  Pout, Pin
+    float *tabc = nullptr;       // [T+1][4] Pout / Pin of a period when the deviation is far from the target
     float *ctab = nullptr;       // [T+1][T+1][S_pad] Pout[a] + Pin[b] (FP32 sum); T <= kCtabMaxT only
     float *ddt = nullptr;        // [(T+1)*(T+1)]    d_{t'} - d_t  (index t*(T+1)+t')
     double *disc = nullptr;      // [T+1]
@@ -102,6 +103,8 @@ struct mm_model {
     uint32_t *status_host = nullptr;            // pinned
     mm::TopkScratch topk;
     uint64_t *step_cta = nullptr;    // fused search step: [step_max_ctas][32] published keys
+    uint64_t *step_grp = nullptr;    // [step_max_ctas][32] merged lists of groups of CTAs
+    uint32_t *step_tick = nullptr;   // [step_max_ctas + 1] group tickets, then the final ticket (zero between launches)
     int step_max_ctas = 0;
     void *step_event = nullptr;      // cudaEvent_t recorded between the step's two launches (timing hook)
     float *shadow32 = nullptr;       // FP32 shadow accumulators: metal [T][S], contrib [T][S], npv [S]

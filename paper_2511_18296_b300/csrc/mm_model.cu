@@ -162,9 +162,10 @@ __global__ void k_accum(const int32_t *__restrict__ order, const int32_t *__rest
 
 __global__ void k_tables(int32_t S, int32_t S_pad, int32_t T, const int64_t *__restrict__ oreT,
                          const uint64_t *__restrict__ target, const double *__restrict__ disc, int64_t m, double a,
-                         double e, float *__restrict__ tab) {
+                         double e, float *__restrict__ tab, float4 *__restrict__ tabc) {
     int t = blockIdx.x;
     for (int s = threadIdx.x; s < S_pad; s += blockDim.x) table_entry(t, s, S, S_pad, T, oreT, target, disc, m, a, e, tab);
+    if (threadIdx.x == 0) tabc[t] = table_consts(t, T, disc, m, a, e);
 }
 
 // ctab[a][b][s] = Pout[a][s] + Pin[b][s], the FP32 sum the evaluator would form.
@@ -251,7 +252,8 @@ __global__ void k_apply(ApplyArgs A, int2 mv_val, const int2 *moves, int64_t n_m
 mm_status rebuild_tables(mm_model *m) {
     if (!m->uniform_mass) return MM_OK;
     k_tables<<<m->T + 1, 128, 0, m->stream>>>(m->S, m->S_pad, m->T, m->oreT, m->target, m->disc, (int64_t)m->m_uniform,
-                                              m->shortfall_pen, m->excess_pen, m->tab);
+                                              m->shortfall_pen, m->excess_pen, m->tab,
+                                              reinterpret_cast<float4 *>(m->tabc));
     mm_status st = check_launch("k_tables");
     if (st != MM_OK || !m->ctab) return st;
     k_ctab<<<(m->T + 1) * (m->T + 1), 128, 0, m->stream>>>(m->S_pad, m->T, m->tab, m->ctab);
@@ -266,10 +268,12 @@ ApplyArgs apply_args(mm_model *m) {
     A.mass = m->mass; A.val = m->val; A.grade = m->grade; A.blk = m->blk;
     A.minedT = m->minedT; A.oreT = m->oreT; A.metal = m->metal; A.npv = m->npv; A.contrib = m->contrib;
     A.tab = m->tab;
+    A.tabc = reinterpret_cast<const float4 *>(m->tabc);
     A.ctab = m->ctab;
     A.disc = m->disc; A.cap = m->cap; A.target = m->target;
     A.pr = m->price * m->recovery; A.pc = m->proc_cost; A.mc = m->mining_cost;
     A.a = m->shortfall_pen; A.e = m->excess_pen;
+    A.invS = 1.0 / (double)m->S;
     A.res = m->apply_res;
     A.status = m->status;
     A.metal32 = m->shadow32;
@@ -318,6 +322,9 @@ void mm_model_destroy(mm_model *m) {
     cudaFree(m->ddt); cudaFree(m->disc); cudaFree(m->cap); cudaFree(m->target); cudaFree(m->status);
     cudaFree(m->apply_res);
     cudaFree(m->step_cta);
+    cudaFree(m->step_grp);
+    cudaFree(m->step_tick);
+    cudaFree(m->tabc);
     cudaFree(m->relax_scratch);
     cudaFree(m->shadow32);
     if (m->apply_res_host) cudaFreeHost(m->apply_res_host);
@@ -431,6 +438,9 @@ mm_status mm_model_create(const mm_model_desc *d, mm_model **out) {
     ALLOC(apply_res, 1);
     m->step_max_ctas = m->num_sms * 8;  // 256-thread CTAs: at most 8 resident per SM
     ALLOC(step_cta, (size_t)m->step_max_ctas * 32);
+    ALLOC(step_grp, (size_t)m->step_max_ctas * 32);
+    ALLOC(step_tick, (size_t)m->step_max_ctas + 1);
+    ALLOC(tabc, (int64_t)4 * (T + 1));
     if (!grid) {
         ALLOC(pred_ptr, B + 1);
         ALLOC(pred_idx, d->pred_ptr[B] > 0 ? d->pred_ptr[B] : 1);
@@ -474,6 +484,7 @@ mm_status mm_model_create(const mm_model_desc *d, mm_model **out) {
     TRY(cudaMemsetAsync(m->oreT, 0, sizeof(int64_t) * (size_t)(T + 1) * S, s), "clear oreT");
     TRY(cudaMemsetAsync(m->minedT, 0, sizeof(int64_t) * (T + 1), s), "clear minedT");
     TRY(cudaMemsetAsync(m->apply_res, 0, sizeof(ApplyResult), s), "clear apply result");
+    TRY(cudaMemsetAsync(m->step_tick, 0, sizeof(uint32_t) * ((size_t)m->step_max_ctas + 1), s), "clear step tickets");
     if (!grid) {
         TRY(cudaMemcpyAsync(m->pred_ptr, d->pred_ptr, sizeof(int32_t) * (B + 1), cudaMemcpyHostToDevice, s), "copy CSR");
         if (d->pred_ptr[B] > 0)

@@ -1,12 +1,12 @@
 // The fused search step: instantiations of the evaluator's top-k variant
-// (plain FP32 sums, no per-scenario output), the one-CTA finisher that selects
-// the batch's top k and applies the best move, and the entry point.
+// (plain FP32 sums, no per-scenario output; the batch's top k is selected and
+// the best move applied by the CTAs that finish last, see step_reduce), the
+// list-based top-k for k <= 32, and the entry point.
 #include "mm_eval_tiled.cuh"
 
 namespace mm {
 
 using EvalFn = void (*)(EvalArgs);
-ApplyArgs apply_args(mm_model *m);
 
 template <int TEAM, int KF, bool TAIL>
 static EvalFn step_fast3() {
@@ -60,58 +60,11 @@ EvalFn pick_step(int team, bool fast, int kf, bool tail, int qmax, bool tsm) {
     return nullptr;
 }
 
-// Arguments of the one-CTA finisher of a fused search step.
-struct StepFinishArgs {
-    const uint64_t *keys;  // [nkeys] published CTA lists (0 = empty)
-    int32_t nkeys;
-    int64_t n;             // moves in the batch (decoded indices must be < n)
-    uint32_t *status;      // sticky status bits
-    int32_t k;
-    int32_t do_apply;
-    const float *score;
-    const int2 *moves;
-    int32_t *idx_out;
-    float *top_out;
-    int32_t *count_out;
-};
-
-// The finisher of a fused step: selects the k largest keys among the
-// published CTA lists (block_merge_lists over 32 warps), warp 0 writes the top
-// k, and the CTA applies the best move when asked.
-__global__ void __launch_bounds__(1024) k_step_finish(StepFinishArgs F, ApplyArgs AP) {
-    __shared__ uint64_t s_wl[32][32];
-    __shared__ int s_best;
-    const int tid = threadIdx.x, warp = tid >> 5;
-    if (F.do_apply) {
-        // the apply's per-period state was evicted by the evaluation's row
-        // traffic: pull it back into L2 while the lists are merged
-        const size_t ts = (size_t)AP.T * AP.S;
-        const size_t tab_bytes = (size_t)2 * (AP.T + 1) * AP.S_pad * sizeof(float);
-        const char *regions[5] = {(const char *)AP.oreT, (const char *)AP.metal, (const char *)AP.contrib,
-                                  (const char *)AP.tab, (const char *)AP.npv};
-        const size_t bytes[5] = {ts * 8, ts * 8, ts * 8, tab_bytes, (size_t)AP.S * 8};
-        for (int r = 0; r < 5; r++)
-            for (size_t o = (size_t)tid * 128; o < bytes[r]; o += (size_t)blockDim.x * 128)
-                asm volatile("prefetch.global.L2 [%0];" ::"l"(regions[r] + o));
-    }
-    const uint64_t t = block_merge_lists<32>(F.keys, F.nkeys / 32, s_wl);
-    if (warp == 0) {
-        const int best = warp_write_topk(t, F.k, F.n, F.status, F.score, F.idx_out, F.top_out, F.count_out);
-        if ((tid & 31) == 0) s_best = best;
-    }
-    __syncthreads();
-    if (F.do_apply) {
-        const int b = s_best;
-        const int2 mv = b >= 0 ? __ldg(F.moves + b) : make_int2(0, -1);
-        apply_block(AP, mv, b >= 0 ? 1 : 0);
-    }
-}
-
 // Standalone top-k for k <= 32: the same per-CTA lists as the fused step,
 // built from stored scores and flags (four 32-key rounds in flight per warp).
 __global__ void __launch_bounds__(kEvalThreads) k_topk_lists(const float *__restrict__ score,
                                                              const uint8_t *__restrict__ feas, int64_t n,
-                                                             uint64_t *__restrict__ lists) {
+                                                             StepTail tail) {
     constexpr int NW = kEvalThreads / 32;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t nwarps = (int64_t)gridDim.x * NW, gw = (int64_t)blockIdx.x * NW + warp;
@@ -132,7 +85,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_topk_lists(const float *__rest
             wtk = warp_topk_insert(wtk, (ok[u] && !isnan(f[u])) ? score_key(f[u], i) : 0ull);
         }
     }
-    step_publish(lists + (size_t)blockIdx.x * 32, wtk);
+    step_reduce(tail, wtk);
 }
 
 mm_status topk_small_launch(mm_model *m, const float *score, const uint8_t *feas, int64_t n, int32_t k, int32_t *idx,
@@ -141,23 +94,18 @@ mm_status topk_small_launch(mm_model *m, const float *score, const uint8_t *feas
     if (blocks > (int64_t)m->num_sms * 2) blocks = (int64_t)m->num_sms * 2;
     if (blocks > m->step_max_ctas) blocks = m->step_max_ctas;
     if (blocks < 1) blocks = 1;
-    k_topk_lists<<<(unsigned)blocks, kEvalThreads, 0, m->stream>>>(score, feas, n, m->step_cta);
-    mm_status st = check_launch("k_topk_lists");
-    if (st != MM_OK) return st;
-    StepFinishArgs F;
-    F.keys = m->step_cta;
-    F.nkeys = (int32_t)blocks * 32;
-    F.n = n;
-    F.status = m->status;
-    F.k = k;
-    F.do_apply = 0;
-    F.score = score;
-    F.moves = nullptr;
-    F.idx_out = idx;
-    F.top_out = top;
-    F.count_out = count;
-    k_step_finish<<<1, 1024, 0, m->stream>>>(F, apply_args(m));
-    return check_launch("k_step_finish");
+    StepTail tail{};
+    tail.L = step_lists(m, (int)blocks);
+    tail.k = k;
+    tail.n = n;
+    tail.status = m->status;
+    tail.idx_out = idx;
+    tail.top_out = top;
+    tail.count_out = count;
+    tail.do_apply = 0;
+    tail.moves = nullptr;
+    k_topk_lists<<<(unsigned)blocks, kEvalThreads, 0, m->stream>>>(score, feas, n, tail);
+    return check_launch("k_topk_lists");
 }
 
 }  // namespace mm
@@ -185,7 +133,10 @@ extern "C" mm_status mm_search_step(mm_model *m, const mm_move *moves, int64_t n
         MM_CUDA_TRY(cudaMemsetAsync(count, 0, sizeof(int32_t), m->stream), "clear count");
         return apply ? mm_apply_best(m, moves, 0, idx, count) : MM_OK;
     }
-    StepOut so{k, apply ? 1 : 0, idx, top, count, 0};
+    // the final CTA of the evaluation launch applies the best move itself
+    // when a CTA has a thread per scenario; otherwise a one-CTA launch follows
+    const bool in_launch = apply && m->S <= kEvalThreads;
+    StepOut so{k, in_launch ? 1 : 0, idx, top, count, 0};
     st = eval_launch(m, moves, n, score, feas, nullptr, nullptr, MM_EVAL_PLAIN, m->team, m->ctas_per_sm, 0, &so);
     if (st != MM_OK) return st;
     if (m->step_event) {
@@ -196,20 +147,7 @@ extern "C" mm_status mm_search_step(mm_model *m, const mm_move *moves, int64_t n
                                                         : cudaEventRecord(ev, m->stream),
                     "record the step event");
     }
-    StepFinishArgs F;
-    F.keys = m->step_cta;
-    F.nkeys = so.grid * 32;
-    F.n = n;
-    F.status = m->status;
-    F.k = k;
-    F.do_apply = apply ? 1 : 0;
-    F.score = score;
-    F.moves = reinterpret_cast<const int2 *>(moves);
-    F.idx_out = idx;
-    F.top_out = top;
-    F.count_out = count;
-    k_step_finish<<<1, 1024, 0, m->stream>>>(F, apply_args(m));
-    return check_launch("k_step_finish");
+    return (apply && !in_launch) ? mm_apply_best(m, moves, n, idx, count) : MM_OK;
 }
 
 extern "C" mm_status mm_set_step_event(mm_model *m, void *cuda_event) {

@@ -111,7 +111,7 @@ def test_step_nothing_feasible_and_errors():
 
 def test_step_event_splits_the_two_launches():
     """The timing hook records the caller's event between the evaluation and
-    the finisher, eagerly and as an external node of a captured graph; the
+    the apply launch, eagerly and as an external node of a captured graph; the
     step's results do not change."""
     p = W.config("plain_4k")
     a, b = _pair(p)
