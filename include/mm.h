@@ -182,8 +182,11 @@ mm_status mm_topk(mm_model *m, const float *score_dev, const uint8_t *feasible_d
  * each warp's 32 best keys in registers (warp shuffles); each CTA publishes
  * one list, the last CTA of each group of CTAs merges its group's lists and
  * the last group merges the group lists and writes the top k (tickets, no
- * waiting), all inside the same launch; a one-CTA launch then applies.  Needs
- * equal block masses (else MM_ERR_INVALID_ARG; use the separate calls).
+ * waiting), all inside the same launch.  When S <= 256 that final CTA also
+ * applies the best move from the record the evaluation kept of it (its blocks
+ * and periods), so the step is one launch; otherwise a one-CTA apply launch
+ * follows.  Needs equal block masses (else MM_ERR_INVALID_ARG; use the
+ * separate calls).
  * Calls on one model must not overlap on the GPU (they share the model's
  * list storage).  Asynchronous. */
 mm_status mm_search_step(mm_model *m, const mm_move *moves_dev, int64_t n, int32_t k, int32_t apply,
@@ -291,15 +294,18 @@ mm_status mm_apply_move(mm_model *m, mm_move move, double *npv_mean_out, double 
 /* Device-side apply of the best move of a batch, for search loops that never
  * leave the GPU: if *count_dev > 0, applies moves_dev[idx_dev[0]] exactly as
  * mm_apply_move does (re-checking feasibility on the device).  The outcome
- * (applied 0/1, NPV mean and std) is kept on the device and returned by the
- * next mm_last_apply call.  moves_dev[n] is the batch idx_dev indexes; an
+ * (applied 0/1) is kept on the device and returned by the next mm_last_apply
+ * call.  moves_dev[n] is the batch idx_dev indexes; an
  * index outside 0..n-1 is treated as a bad move (nothing applied, sticky
  * MM_ERR_BAD_MOVE).  Asynchronous. */
 mm_status mm_apply_best(mm_model *m, const mm_move *moves_dev, int64_t n, const int32_t *idx_dev,
                         const int32_t *count_dev);
 
-/* Outcome of the last mm_apply_best: *applied (1 if a move was applied),
- * NPV mean and std after it.  Pointers nullable.  Synchronising. */
+/* Outcome of the last device-side apply (mm_apply_best, mm_search_step,
+ * mm_batch_run): *applied (1 if a move was applied), and the NPV mean and
+ * population std over scenarios of the model's current schedule, formed from
+ * the FP64 NPV_s by this call (the search step itself does not spend time on
+ * them).  Pointers nullable.  Synchronising. */
 mm_status mm_last_apply(mm_model *m, int32_t *applied, double *npv_mean_out, double *npv_std_out);
 
 /* Per-scenario NPV of the current schedule (FP64, [S], nullable) and its mean

@@ -104,7 +104,6 @@ struct ApplyArgs {
     const uint64_t *cap;
     const uint64_t *target;
     double pr, pc, mc, a, e;
-    double invS;  // 1 / S
     ApplyResult *res;
     uint32_t *status;
 };
@@ -140,11 +139,17 @@ static __device__ __forceinline__ int32_t apply_neighbour(const Topo &tp, int32_
 // the same FP64 expression evaluated at a representative x (same bits as
 // table_entry); in between the expression is evaluated here.
 static __device__ __forceinline__ void table_store_c(int t, int s, int32_t S_pad, int32_t T, int64_t x, float4 tc,
-                                                     double d, int64_t m, double a, double e, float *tab) {
+                                                     double d, int64_t m, double a, double e, float *tab,
+                                                     float *tab_copy) {
     const float po = x >= m ? tc.x : (x <= 0 ? tc.y : __double2float_rn(__dmul_rn(d, pen_diff(x, x - m, a, e))));
     const float pi = x >= 0 ? tc.z : (x <= -m ? tc.w : __double2float_rn(__dmul_rn(d, pen_diff(x, x + m, a, e))));
-    tab[(int64_t)t * S_pad + s] = po;
-    tab[(int64_t)(T + 1) * S_pad + (int64_t)t * S_pad + s] = pi;
+    const int64_t io = (int64_t)t * S_pad + s, ii = (int64_t)(T + 1) * S_pad + io;
+    tab[io] = po;
+    tab[ii] = pi;
+    if (tab_copy) {
+        tab_copy[io] = po;
+        tab_copy[ii] = pi;
+    }
 }
 
 // Period-pair rows and columns of periods ra and rb (see apply_block), by
@@ -187,47 +192,201 @@ static __device__ __forceinline__ void ctab_rebuild(const float *__restrict__ tb
     }
 }
 
-// Apply one move on a single CTA (blockDim.x >= max(S, 64), a multiple of 32):
-//   1. one round trip of independent loads: the moved blocks' schedule words
-//      and masses, every period's tonnage and capacity, and per scenario
-//      (thread s) the moved blocks' ore bits and FP64 grades;
-//   2. thread 0 re-checks the move exactly and updates the mined tonnage;
-//   3. the last warp rewrites the packed period/lo/hi words of the moved
+// Shared-memory copy of the Pout / Pin tables used by the period-pair rebuild
+// when 2 (T+1) S_pad floats fit (18 KB).
+constexpr int kApplyTabMax = 4608;
+
+// Apply a decoded move v on a single CTA (blockDim.x >= max(S, 64), a multiple
+// of 32).  go = 1: v is valid, feasible and changes the schedule (the caller
+// has checked it against the current state); go = 0: nothing changes.
+//   1. one round trip of independent loads: per scenario (thread s) the moved
+//      blocks' ore bits and FP64 grades and the two affected periods' ore
+//      tonnage, metal, NPV contribution, mined tonnage, target and discount;
+//      the Pout / Pin tables into shared memory where they fit;
+//   2. the last warp rewrites the packed period/lo/hi words of the moved
 //      blocks and their grid neighbours (the moved blocks' new periods come
-//      from the move, so the lanes need no ordering among themselves), while
-//      thread s updates scenario s: the two affected periods' ore tonnage,
-//      metal, NPV contribution and table entries (NPV_s += new - old);
-//   4. warp 0 forms the FP64 mean and population std of NPV over scenarios
-//      (two passes; computed whether or not the move applied) while the other
-//      warps rebuild the period-pair rows of the changed periods.
-// have = 0: nothing to apply (statistics only).
+//      from the move, so the lanes need no ordering among themselves) while
+//      thread s updates scenario s: ore tonnage, metal, NPV contribution and
+//      table entries of the two periods (NPV_s += new - old); thread 0 the
+//      mined tonnage;
+//   3. the warps rebuild the period-pair rows and columns of the two periods.
+// The NPV mean and std over scenarios are not formed here (k_npv_stats does
+// that on request), so an apply ends with the state update.
+static __device__ __forceinline__ void apply_core(const ApplyArgs &A, const MoveView &v, int go) {
+    __shared__ float s_tab[kApplyTabMax];
+    const int s = threadIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarp = blockDim.x >> 5;
+    const bool hs = s < A.S;
+    const uint32_t T = (uint32_t)A.T, T1 = T + 1;
+    const size_t sp = (size_t)A.S_pad, pin = (size_t)T1 * sp;
+    const bool tab_sm = A.ctab && 2 * pin <= (size_t)kApplyTabMax;
+    if (!go) return;
+    const int32_t mb2 = v.swap ? v.b2 : -1;
+    const bool r1 = v.t1 < T, r2 = v.t2 < T;
+    // 1. loads (the staged table skips the rows of t1 and t2: the scenario
+    // threads write their new entries there)
+    if (tab_sm)
+        for (uint32_t r = (uint32_t)warp; r < 2 * T1; r += (uint32_t)nwarp) {
+            const uint32_t t = r < T1 ? r : r - T1;
+            if ((r1 && t == v.t1) || (r2 && t == v.t2)) continue;
+            for (uint32_t s2 = (uint32_t)lane; s2 < (uint32_t)A.S; s2 += 32u) s_tab[r * sp + s2] = A.tab[r * sp + s2];
+        }
+    uint32_t o1 = 0, o2 = 0;
+    double gr1 = 0.0, gr2 = 0.0, M1 = 0.0, M2 = 0.0, C1 = 0.0, C2 = 0.0, my_npv = 0.0, disc1 = 0.0, disc2 = 0.0;
+    int64_t O1 = 0, O2 = 0, tgt1 = 0, tgt2 = 0, mined1 = 0, mined2 = 0;
+    float4 tc1 = make_float4(0.0f, 0.0f, 0.0f, 0.0f), tc2 = tc1;
+    const size_t i1 = (size_t)v.t1 * A.S + s, i2 = (size_t)v.t2 * A.S + s;
+    if (hs) {
+        o1 = ore_bit(A.val, A.R, A.ore_off, v.b1, s);
+        gr1 = A.grade[(int64_t)v.b1 * A.S + s];
+        if (v.swap) {
+            o2 = ore_bit(A.val, A.R, A.ore_off, v.b2, s);
+            gr2 = A.grade[(int64_t)v.b2 * A.S + s];
+        }
+        my_npv = A.npv[s];
+        if (r1) {
+            O1 = A.oreT[i1]; M1 = A.metal[i1]; C1 = A.contrib[i1];
+            tgt1 = (int64_t)A.target[v.t1]; disc1 = A.disc[v.t1]; mined1 = A.minedT[v.t1];
+            if (A.uniform) tc1 = A.tabc[v.t1];
+        }
+        if (r2) {
+            O2 = A.oreT[i2]; M2 = A.metal[i2]; C2 = A.contrib[i2];
+            tgt2 = (int64_t)A.target[v.t2]; disc2 = A.disc[v.t2]; mined2 = A.minedT[v.t2];
+            if (A.uniform) tc2 = A.tabc[v.t2];
+        }
+    }
+    // 2. updates
+    const int64_t dm1 = v.m1, dm2 = v.swap ? (int64_t)v.m2 : 0;
+    mined1 += -dm1 + dm2;
+    mined2 += dm1 - dm2;
+    if (threadIdx.x == 0) {
+        if (r1) A.minedT[v.t1] = A.minedT[v.t1] - dm1 + dm2;
+        if (r2) A.minedT[v.t2] = A.minedT[v.t2] + dm1 - dm2;
+    }
+    // period of block j after the move: the moved blocks' from the move, the
+    // others' from their words (of which only the lo/hi bits change here)
+    auto period_after = [&](int32_t j) -> uint32_t {
+        if (j == v.b1) return v.t2;
+        if (j == mb2) return v.t1;
+        return blk_period(A.blk[j]);
+    };
+    if (A.tp.nx > 0) {
+        if (warp == nwarp - 1 && lane < 22) {
+            const int32_t b = apply_neighbour(A.tp, v.b1, mb2, lane);
+            if (b >= 0) A.blk[b] = block_bounds(A.tp, b, period_after);
+        }
+    } else {
+        // CSR: the moved blocks and every direct predecessor and successor
+        for (int q = 0; q < 2; q++) {
+            const int32_t b = q == 0 ? v.b1 : mb2;
+            if (b < 0) continue;
+            const int32_t np = A.tp.pred_ptr[b + 1] - A.tp.pred_ptr[b];
+            const int32_t ns = A.tp.succ_ptr[b + 1] - A.tp.succ_ptr[b];
+            for (int k = threadIdx.x; k <= np + ns; k += blockDim.x) {
+                const int32_t j = k == np + ns ? b
+                                               : (k < np ? A.tp.pred_idx[A.tp.pred_ptr[b] + k]
+                                                         : A.tp.succ_idx[A.tp.succ_ptr[b] + k - np]);
+                A.blk[j] = block_bounds(A.tp, j, period_after);
+            }
+        }
+    }
+    if (hs) {
+        const int64_t om1 = o1 ? (int64_t)v.m1 : 0, om2 = (v.swap && o2) ? (int64_t)v.m2 : 0;
+        const double g1 = o1 ? __dmul_rn((double)v.m1, gr1) : 0.0;
+        const double g2 = (v.swap && o2) ? __dmul_rn((double)v.m2, gr2) : 0.0;
+        const int64_t mu_ = (int64_t)A.m_uniform;
+        double dnpv = 0.0;
+        if (r1) {
+            const int64_t nO = O1 + om2 - om1;
+            const double nM = __dadd_rn(__dsub_rn(M1, g1), g2);
+            const double c = contrib_val(nO, nM, mined1, tgt1, disc1, A.pr, A.pc, A.mc, A.a, A.e);
+            dnpv = __dadd_rn(dnpv, __dsub_rn(c, C1));
+            A.oreT[i1] = nO;
+            A.metal[i1] = nM;
+            A.contrib[i1] = c;
+            if (A.uniform) table_store_c(v.t1, s, A.S_pad, A.T, nO - tgt1, tc1, disc1, mu_, A.a, A.e, A.tab,
+                                         tab_sm ? s_tab : nullptr);
+        }
+        if (r2) {
+            const int64_t nO = O2 + om1 - om2;
+            const double nM = __dadd_rn(__dsub_rn(M2, g2), g1);
+            const double c = contrib_val(nO, nM, mined2, tgt2, disc2, A.pr, A.pc, A.mc, A.a, A.e);
+            dnpv = __dadd_rn(dnpv, __dsub_rn(c, C2));
+            A.oreT[i2] = nO;
+            A.metal[i2] = nM;
+            A.contrib[i2] = c;
+            if (A.uniform) table_store_c(v.t2, s, A.S_pad, A.T, nO - tgt2, tc2, disc2, mu_, A.a, A.e, A.tab,
+                                         tab_sm ? s_tab : nullptr);
+        }
+        my_npv = __dadd_rn(my_npv, dnpv);
+        A.npv[s] = my_npv;
+        if (A.npv32) {
+            // the same update with FP32 running totals
+            float d32 = 0.0f;
+            const float g1f = (float)g1, g2f = (float)g2;
+            if (r1) {
+                const float nM = A.metal32[i1] - g1f + g2f;
+                const float c = contrib_val_f32(O1 + om2 - om1, nM, mined1, tgt1, disc1, A.pr, A.pc, A.mc, A.a, A.e);
+                d32 += c - A.contrib32[i1];
+                A.metal32[i1] = nM;
+                A.contrib32[i1] = c;
+            }
+            if (r2) {
+                const float nM = A.metal32[i2] - g2f + g1f;
+                const float c = contrib_val_f32(O2 + om1 - om2, nM, mined2, tgt2, disc2, A.pr, A.pc, A.mc, A.a, A.e);
+                d32 += c - A.contrib32[i2];
+                A.metal32[i2] = nM;
+                A.contrib32[i2] = c;
+            }
+            A.npv32[s] += d32;
+        }
+    }
+    if (!A.ctab) return;
+    __syncthreads();  // the new Pout / Pin entries of t1 and t2 are written
+    // 3. ctab[a][b][s] = Pout[a][s] + Pin[b][s] for the rows a and columns b of
+    // the changed periods
+    const bool c1 = r1, c2 = r2 && v.t2 != v.t1;
+    if (!(c1 || c2)) return;
+    const uint32_t ra = c1 ? v.t1 : v.t2, rb = c2 ? v.t2 : ra;
+    if (tab_sm) {
+        // every operand in shared memory: only the stores leave the SM
+        const uint32_t S = (uint32_t)A.S;
+        for (uint32_t b = (uint32_t)warp; b < T1; b += (uint32_t)nwarp) {
+            for (uint32_t s2 = (uint32_t)lane; s2 < S; s2 += 32u) {
+                const float pob = s_tab[b * sp + s2], pib = s_tab[pin + b * sp + s2];
+                const float poa = s_tab[ra * sp + s2], pia = s_tab[pin + ra * sp + s2];
+                const float por = s_tab[rb * sp + s2], pir = s_tab[pin + rb * sp + s2];
+                A.ctab[((size_t)ra * T1 + b) * sp + s2] = poa + pib;
+                A.ctab[((size_t)b * T1 + ra) * sp + s2] = pob + pia;
+                A.ctab[((size_t)rb * T1 + b) * sp + s2] = por + pib;
+                A.ctab[((size_t)b * T1 + rb) * sp + s2] = pob + pir;
+            }
+        }
+    } else {
+        ctab_rebuild(A.tab, A.ctab, T1, (uint32_t)A.S, sp, ra, rb, warp, nwarp, lane);
+    }
+}
+
+// Apply one move on a single CTA (Algorithm 4: assign S[b*] <- t*): the moved
+// blocks' schedule words, masses and the per-period tonnage and capacity are
+// loaded, thread 0 re-checks the move exactly (decode_move) and records the
+// outcome, then apply_core updates the state.  have = 0: nothing to apply.
 static __device__ __noinline__ void apply_block(const ApplyArgs &A, int2 mv, int have) {
     __shared__ MoveView sv;
     __shared__ int s_go;
     __shared__ int64_t s_mined[kMaxT + 1];
     __shared__ uint64_t s_cap[kMaxT + 1];
     __shared__ uint32_t s_w[2], s_m[2];
-    __shared__ double s_npv[kMaxS];
-    const int s = threadIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int nwarp = blockDim.x >> 5;
-    const bool hs = s < A.S;
     const int32_t b1 = mv.x, b2 = mv.y;
     const bool ok1 = have && b1 >= 0 && b1 < A.tp.B;
     const bool ok2 = have && b2 >= 0 && b2 < A.tp.B;
-    // 1. independent loads
     if (threadIdx.x == 0 && ok1) { s_w[0] = A.blk[b1]; s_m[0] = A.uniform ? A.m_uniform : A.mass[b1]; }
     if (threadIdx.x == 1 && ok2) { s_w[1] = A.blk[b2]; s_m[1] = A.uniform ? A.m_uniform : A.mass[b2]; }
     for (int t = threadIdx.x; t <= A.T; t += blockDim.x) {
         s_mined[t] = A.minedT[t];
         s_cap[t] = A.cap[t];
     }
-    const uint32_t o1 = (hs && ok1) ? ore_bit(A.val, A.R, A.ore_off, b1, s) : 0u;
-    const uint32_t o2 = (hs && ok2) ? ore_bit(A.val, A.R, A.ore_off, b2, s) : 0u;
-    const double gr1 = (hs && ok1) ? A.grade[(int64_t)b1 * A.S + s] : 0.0;
-    const double gr2 = (hs && ok2) ? A.grade[(int64_t)b2 * A.S + s] : 0.0;
-    double my_npv = hs ? A.npv[s] : 0.0;
     __syncthreads();
-    // 2. exact re-check and the scalar updates
     if (threadIdx.x == 0) {
         MoveView v;
         if (have) {
@@ -241,137 +400,36 @@ static __device__ __noinline__ void apply_block(const ApplyArgs &A, int2 mv, int
             v.noop = true;
         }
         sv = v;
-        const int go = have && v.valid && v.feasible && !v.noop;
-        s_go = go;
+        s_go = have && v.valid && v.feasible && !v.noop;
         A.res->applied = (have && v.valid && v.feasible) ? 1 : 0;  // a feasible no-op counts as applied
         A.res->status = !have ? MM_OK : (!v.valid ? MM_ERR_BAD_MOVE : (!v.feasible ? MM_ERR_INFEASIBLE : MM_OK));
-        if (go) {
-            const int64_t dm1 = v.m1, dm2 = v.swap ? (int64_t)v.m2 : 0;
-            if (v.t1 < (uint32_t)A.T) A.minedT[v.t1] = (s_mined[v.t1] += -dm1 + dm2);
-            if (v.t2 < (uint32_t)A.T) A.minedT[v.t2] = (s_mined[v.t2] += dm1 - dm2);
-        }
     }
     __syncthreads();
-    // 3. schedule words of the neighbourhood, per-scenario updates
-    if (s_go) {
-        const MoveView v = sv;
-        const int32_t mb2 = v.swap ? v.b2 : -1;
-        // period of block j after the move: the moved blocks' from the move, the
-        // others' from their words (of which only the lo/hi bits change here)
-        auto period_after = [&](int32_t j) -> uint32_t {
-            if (j == v.b1) return v.t2;
-            if (j == mb2) return v.t1;
-            return blk_period(A.blk[j]);
-        };
-        if (A.tp.nx > 0) {
-            if (warp == nwarp - 1 && lane < 22) {
-                const int32_t b = apply_neighbour(A.tp, v.b1, mb2, lane);
-                if (b >= 0) A.blk[b] = block_bounds(A.tp, b, period_after);
-            }
-        } else {
-            // CSR: the moved blocks and every direct predecessor and successor
-            for (int q = 0; q < 2; q++) {
-                const int32_t b = q == 0 ? v.b1 : mb2;
-                if (b < 0) continue;
-                const int32_t np = A.tp.pred_ptr[b + 1] - A.tp.pred_ptr[b];
-                const int32_t ns = A.tp.succ_ptr[b + 1] - A.tp.succ_ptr[b];
-                for (int k = threadIdx.x; k <= np + ns; k += blockDim.x) {
-                    const int32_t j = k == np + ns ? b
-                                                   : (k < np ? A.tp.pred_idx[A.tp.pred_ptr[b] + k]
-                                                             : A.tp.succ_idx[A.tp.succ_ptr[b] + k - np]);
-                    A.blk[j] = block_bounds(A.tp, j, period_after);
-                }
-            }
-        }
-        if (hs) {
-            const bool r1 = v.t1 < (uint32_t)A.T, r2 = v.t2 < (uint32_t)A.T;
-            const size_t i1 = (size_t)v.t1 * A.S + s, i2 = (size_t)v.t2 * A.S + s;
-            const int64_t O1 = r1 ? A.oreT[i1] : 0, O2 = r2 ? A.oreT[i2] : 0;
-            const double M1 = r1 ? A.metal[i1] : 0.0, M2 = r2 ? A.metal[i2] : 0.0;
-            const double C1 = r1 ? A.contrib[i1] : 0.0, C2 = r2 ? A.contrib[i2] : 0.0;
-            const int64_t tgt1 = r1 ? (int64_t)A.target[v.t1] : 0, tgt2 = r2 ? (int64_t)A.target[v.t2] : 0;
-            const double disc1 = r1 ? A.disc[v.t1] : 0.0, disc2 = r2 ? A.disc[v.t2] : 0.0;
-            const float4 zero4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-            const float4 tc1 = (r1 && A.uniform) ? A.tabc[v.t1] : zero4;
-            const float4 tc2 = (r2 && A.uniform) ? A.tabc[v.t2] : zero4;
-            const int64_t mined1 = r1 ? s_mined[v.t1] : 0, mined2 = r2 ? s_mined[v.t2] : 0;
-            const int64_t om1 = o1 ? (int64_t)v.m1 : 0, om2 = (v.swap && o2) ? (int64_t)v.m2 : 0;
-            const double g1 = o1 ? __dmul_rn((double)v.m1, gr1) : 0.0;
-            const double g2 = (v.swap && o2) ? __dmul_rn((double)v.m2, gr2) : 0.0;
-            const int64_t mu_ = (int64_t)A.m_uniform;
-            double dnpv = 0.0;
-            if (r1) {
-                const int64_t nO = O1 + om2 - om1;
-                const double nM = __dadd_rn(__dsub_rn(M1, g1), g2);
-                const double c = contrib_val(nO, nM, mined1, tgt1, disc1, A.pr, A.pc, A.mc, A.a, A.e);
-                dnpv = __dadd_rn(dnpv, __dsub_rn(c, C1));
-                A.oreT[i1] = nO;
-                A.metal[i1] = nM;
-                A.contrib[i1] = c;
-                if (A.uniform) table_store_c(v.t1, s, A.S_pad, A.T, nO - tgt1, tc1, disc1, mu_, A.a, A.e, A.tab);
-            }
-            if (r2) {
-                const int64_t nO = O2 + om1 - om2;
-                const double nM = __dadd_rn(__dsub_rn(M2, g2), g1);
-                const double c = contrib_val(nO, nM, mined2, tgt2, disc2, A.pr, A.pc, A.mc, A.a, A.e);
-                dnpv = __dadd_rn(dnpv, __dsub_rn(c, C2));
-                A.oreT[i2] = nO;
-                A.metal[i2] = nM;
-                A.contrib[i2] = c;
-                if (A.uniform) table_store_c(v.t2, s, A.S_pad, A.T, nO - tgt2, tc2, disc2, mu_, A.a, A.e, A.tab);
-            }
-            my_npv = __dadd_rn(my_npv, dnpv);
-            A.npv[s] = my_npv;
-            if (A.npv32) {
-                // the same update with FP32 running totals
-                float d32 = 0.0f;
-                const float g1f = (float)g1, g2f = (float)g2;
-                if (r1) {
-                    const float nM = A.metal32[i1] - g1f + g2f;
-                    const float c = contrib_val_f32(O1 + om2 - om1, nM, mined1, tgt1, disc1, A.pr, A.pc, A.mc, A.a, A.e);
-                    d32 += c - A.contrib32[i1];
-                    A.metal32[i1] = nM;
-                    A.contrib32[i1] = c;
-                }
-                if (r2) {
-                    const float nM = A.metal32[i2] - g2f + g1f;
-                    const float c = contrib_val_f32(O2 + om1 - om2, nM, mined2, tgt2, disc2, A.pr, A.pc, A.mc, A.a, A.e);
-                    d32 += c - A.contrib32[i2];
-                    A.metal32[i2] = nM;
-                    A.contrib32[i2] = c;
-                }
-                A.npv32[s] += d32;
-            }
-        }
+    const MoveView v = sv;
+    apply_core(A, v, s_go);
+}
+
+// Apply a move that the same launch evaluated as feasible against the current
+// state (the fused step's best move): no re-check is needed, so every load
+// goes out at once.  info = (b1, b2 or B for a shift, t1 | t2 << 8) as the
+// evaluator recorded it; have = 0: no feasible move.  Uniform block mass.
+static __device__ __noinline__ void apply_evaluated(const ApplyArgs &A, int4 info, int have) {
+    MoveView v;
+    v.b1 = info.x;
+    v.swap = info.y != A.tp.B;
+    v.b2 = v.swap ? info.y : -1;
+    v.t1 = (uint32_t)info.z & 0xffu;
+    v.t2 = ((uint32_t)info.z >> 8) & 0xffu;
+    v.m1 = A.m_uniform;
+    v.m2 = v.swap ? A.m_uniform : 0u;
+    v.valid = true;
+    v.feasible = true;
+    v.noop = v.swap ? (v.b1 == v.b2 || v.t1 == v.t2) : v.t1 == v.t2;
+    if (threadIdx.x == 0) {
+        A.res->applied = have ? 1 : 0;
+        A.res->status = MM_OK;
     }
-    if (hs) s_npv[s] = my_npv;
-    __syncthreads();  // NPV_s staged; the new Pout / Pin entries of t1 and t2 are written
-    // 4. statistics (warp 0) beside the period-pair rows (the other warps)
-    if (warp == 0) {
-        double sum = 0.0;
-        for (int i = lane; i < A.S; i += 32) sum = __dadd_rn(sum, s_npv[i]);
-        const double mean = __dmul_rn(warp_sum_f64(sum), A.invS);
-        double ss = 0.0;
-        for (int i = lane; i < A.S; i += 32) {
-            const double dv = __dsub_rn(s_npv[i], mean);
-            ss = __fma_rn(dv, dv, ss);
-        }
-        ss = warp_sum_f64(ss);
-        if (lane == 0) {
-            A.res->mean = mean;
-            A.res->std = sqrt(__dmul_rn(ss, A.invS));
-        }
-    } else if (s_go && A.ctab) {
-        // ctab[a][b][s] = Pout[a][s] + Pin[b][s] for the rows a and columns b of
-        // the changed periods.  Work items (b, scenario slot) go round the warps
-        // 1..nwarp-1; each lane issues the loads of four items before their
-        // stores, so a round costs one memory round trip.
-        const MoveView v = sv;
-        const uint32_t T = (uint32_t)A.T, T1 = T + 1;
-        const bool c1 = v.t1 < T, c2 = v.t2 < T && v.t2 != v.t1;
-        if (c1 || c2) ctab_rebuild(A.tab, A.ctab, T1, (uint32_t)A.S, (size_t)A.S_pad, c1 ? v.t1 : v.t2,
-                                   c2 ? v.t2 : (c1 ? v.t1 : v.t2), warp - 1, nwarp - 1, lane);
-    }
+    apply_core(A, v, have && !v.noop);
 }
 
 }  // namespace mm

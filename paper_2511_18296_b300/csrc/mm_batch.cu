@@ -74,7 +74,6 @@ constexpr int kBatchMaxT = 64;  // chains with more periods are not batched (tab
 __global__ void __launch_bounds__(kEvalThreads, MM_EVAL_MINB) k_batch_eval(BatchArgs B) {
     constexpr int NW = kEvalThreads / 32;
     __shared__ EvalShared sh;
-    __shared__ float4 s_lut[16];
     __shared__ __align__(16) EvalArgs sA;
     __shared__ float s_dd[(kBatchMaxT + 1) * (kBatchMaxT + 1)];
     __shared__ int64_t s_mined[kBatchMaxT + 1];
@@ -82,9 +81,6 @@ __global__ void __launch_bounds__(kEvalThreads, MM_EVAL_MINB) k_batch_eval(Batch
     __shared__ uint64_t s_wl[NW][32];
     __shared__ int s_item, s_last, s_best;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid < 16)
-        s_lut[tid] = make_float4((float)(tid & 1), (float)((tid >> 1) & 1), (float)((tid >> 2) & 1),
-                                 (float)((tid >> 3) & 1));
     for (;;) {
         if (tid == 0) s_item = (int)atomicAdd(B.next, 1u);
         __syncthreads();
@@ -112,39 +108,39 @@ __global__ void __launch_bounds__(kEvalThreads, MM_EVAL_MINB) k_batch_eval(Batch
         uint64_t wtk = 0;
         switch (C->variant) {
             case kBvT4K1:
-                eval_warp_range<4, 1, false, false, 1, false, true>(sA, sh, s_lut, sA.tab, s_dd, s_mined, s_cap, r0,
+                eval_warp_range<4, 1, false, false, 1, false, true>(sA, sh, sA.tab, s_dd, s_mined, s_cap, r0,
                                                                     r1, wtk);
                 break;
             case kBvT4K2:
-                eval_warp_range<4, 1, false, false, 2, false, true>(sA, sh, s_lut, sA.tab, s_dd, s_mined, s_cap, r0,
+                eval_warp_range<4, 1, false, false, 2, false, true>(sA, sh, sA.tab, s_dd, s_mined, s_cap, r0,
                                                                     r1, wtk);
                 break;
             case kBvT4K3:
-                eval_warp_range<4, 1, false, false, 3, false, true>(sA, sh, s_lut, sA.tab, s_dd, s_mined, s_cap, r0,
+                eval_warp_range<4, 1, false, false, 3, false, true>(sA, sh, sA.tab, s_dd, s_mined, s_cap, r0,
                                                                     r1, wtk);
                 break;
             case kBvT4K4:
-                eval_warp_range<4, 1, false, false, 4, false, true>(sA, sh, s_lut, sA.tab, s_dd, s_mined, s_cap, r0,
+                eval_warp_range<4, 1, false, false, 4, false, true>(sA, sh, sA.tab, s_dd, s_mined, s_cap, r0,
                                                                     r1, wtk);
                 break;
             case kBvT8K3T:
-                eval_warp_range<8, 1, false, false, 3, true, true>(sA, sh, s_lut, sA.tab, s_dd, s_mined, s_cap, r0,
+                eval_warp_range<8, 1, false, false, 3, true, true>(sA, sh, sA.tab, s_dd, s_mined, s_cap, r0,
                                                                    r1, wtk);
                 break;
             case kBvG4:
-                eval_warp_range<4, 4, false, false, 0, false, true>(sA, sh, s_lut, sA.tab, s_dd, s_mined, s_cap, r0,
+                eval_warp_range<4, 4, false, false, 0, false, true>(sA, sh, sA.tab, s_dd, s_mined, s_cap, r0,
                                                                     r1, wtk);
                 break;
             case kBvG8:
-                eval_warp_range<8, 4, false, false, 0, false, true>(sA, sh, s_lut, sA.tab, s_dd, s_mined, s_cap, r0,
+                eval_warp_range<8, 4, false, false, 0, false, true>(sA, sh, sA.tab, s_dd, s_mined, s_cap, r0,
                                                                     r1, wtk);
                 break;
             case kBvG16:
-                eval_warp_range<16, 4, false, false, 0, false, true>(sA, sh, s_lut, sA.tab, s_dd, s_mined, s_cap, r0,
+                eval_warp_range<16, 4, false, false, 0, false, true>(sA, sh, sA.tab, s_dd, s_mined, s_cap, r0,
                                                                      r1, wtk);
                 break;
             default:
-                eval_warp_range<32, 8, false, false, 0, false, true>(sA, sh, s_lut, sA.tab, s_dd, s_mined, s_cap,
+                eval_warp_range<32, 8, false, false, 0, false, true>(sA, sh, sA.tab, s_dd, s_mined, s_cap,
                                                                      r0, r1, wtk);
                 break;
         }

@@ -142,6 +142,8 @@ StepLists step_lists(mm_model *m, int grid) {
     StepLists L;
     L.cta = m->step_cta;
     L.grp = m->step_grp;
+    L.cinf = m->step_cinf;
+    L.ginf = m->step_ginf;
     L.tick = m->step_tick;
     L.final_slot = m->step_max_ctas;
     int g = 1;

@@ -14,8 +14,10 @@
 // Warps never wait on each other (no CTA barrier after the table staging).
 // The next chunk's moves are loaded into registers while the current chunk is
 // processed.  Per scenario quad a lane issues one 16-byte row load per moved
-// block, one ore word (shared by 8 lanes) and 16-byte table loads from shared
-// memory; ore bits become 0/1 float masks through a 16-entry table, so the
+// block and 16-byte period-pair table loads; the ore words of a row come with
+// one 16-byte load per lane where they fit (else one word per quad), and ore
+// bits become 0/1 float masks by selects (the L1 data path, not the ALUs,
+// limits this kernel, so a shared-memory lookup table costs more), so the
 // per-scenario work is four (shift) or seven (swap) FP32 operations.
 #pragma once
 
@@ -36,6 +38,7 @@ constexpr int kChunk = 64;         // moves a warp decodes at once (two per lane
 struct StepLists {
     uint64_t *cta;        // [grid][32] each CTA's 32 best keys
     uint64_t *grp;        // [groups][32] each group's 32 best keys
+    int4 *cinf, *ginf;    // [grid], [groups] the move of each list's best key: (b1, b2 or B, t1 | t2 << 8, 0)
     uint32_t *tick;       // [groups] group tickets; tick[final_slot] the final ticket
     int32_t final_slot;
     int32_t grp_size;     // CTAs per group (the last group may be smaller)
@@ -212,11 +215,17 @@ __device__ __forceinline__ uint32_t ld_ore_word(const float *row, int ore_off, i
     return __ldg(reinterpret_cast<const uint32_t *>(row + ore_off) + w);
 }
 
+// 0/1 float masks of the four bits of an ore nibble (bit j -> component j).
+__device__ __forceinline__ float4 nib_mask(uint32_t n) {
+    return make_float4((n & 1u) ? 1.0f : 0.0f, (n & 2u) ? 1.0f : 0.0f, (n & 4u) ? 1.0f : 0.0f,
+                       (n & 8u) ? 1.0f : 0.0f);
+}
+
 // Per-move scenario loop + reduction for one team.  SWAP selects the move
 // type at compile time, SROW where the two block rows live.  Writes the
 // deltas to d[][], the mean to mu and the population std to sd.
 template <int TEAM, int QMAX, bool SWAP, bool KAHAN, bool SROW>
-__device__ __forceinline__ void team_eval(const EvalArgs &A, const float *tab, const float4 *lut, int tl, bool act,
+__device__ __forceinline__ void team_eval(const EvalArgs &A, const float *tab, int tl, bool act,
                                           const float *row1, const float *row2, uint32_t t1, uint32_t t2, float dd,
                                           int NQ, int rem, float invS, size_t pin_off, float (&d)[QMAX][4], float &mu,
                                           float &sd) {
@@ -242,8 +251,8 @@ __device__ __forceinline__ void team_eval(const EvalArgs &A, const float *tab, c
             const float4 b = ld_row4<SROW>(row2, qc);
             const uint32_t n1 = (ld_ore_word<SROW>(row1, ore_off, qc >> 3) >> sh) & 0xfu;
             const uint32_t n2 = (ld_ore_word<SROW>(row2, ore_off, qc >> 3) >> sh) & 0xfu;
-            const float4 m1 = lut[n1 & ~n2];
-            const float4 m2 = lut[n2 & ~n1];
+            const float4 m1 = nib_mask(n1 & ~n2);
+            const float4 m2 = nib_mask(n2 & ~n1);
             const float4 pc = ld_tab<true>(tab + pin1 + 4 * qc);
             const float4 pd = ld_tab<true>(tab + pout2 + 4 * qc);
             x[0] = fmaf(a.x - b.x, dd, fmaf(m2.x, pc.x + pd.x, m1.x * (pa.x + pb.x)));
@@ -251,7 +260,7 @@ __device__ __forceinline__ void team_eval(const EvalArgs &A, const float *tab, c
             x[2] = fmaf(a.z - b.z, dd, fmaf(m2.z, pc.z + pd.z, m1.z * (pa.z + pb.z)));
             x[3] = fmaf(a.w - b.w, dd, fmaf(m2.w, pc.w + pd.w, m1.w * (pa.w + pb.w)));
         } else {
-            const float4 m1 = lut[(ld_ore_word<SROW>(row1, ore_off, qc >> 3) >> sh) & 0xfu];
+            const float4 m1 = nib_mask((ld_ore_word<SROW>(row1, ore_off, qc >> 3) >> sh) & 0xfu);
             x[0] = fmaf(a.x, dd, m1.x * (pa.x + pb.x));
             x[1] = fmaf(a.y, dd, m1.y * (pa.y + pb.y));
             x[2] = fmaf(a.z, dd, m1.z * (pa.z + pb.z));
@@ -341,7 +350,7 @@ __device__ __forceinline__ uint64_t f2_sub(uint64_t a, uint64_t b) {
 // masking), then, if TAIL, one iteration in which only the first
 // NQ - KF * TEAM lanes hold a quad.  d[KF] holds the tail quad.
 template <int TEAM, int KF, bool TAIL, bool SWAP, bool KAHAN>
-__device__ __forceinline__ void team_eval_fast(const EvalArgs &A, const float4 *lut, int tl, const float *row1,
+__device__ __forceinline__ void team_eval_fast(const EvalArgs &A, int tl, const float *row1,
                                                const float *row2, uint32_t t1, uint32_t t2, float dd, int ntail,
                                                float invS, float (&d)[KF + 1][4], float &mu, float &sd) {
     const int S_pad = A.S_pad, ore_off = A.ore_off;
@@ -355,6 +364,21 @@ __device__ __forceinline__ void team_eval_fast(const EvalArgs &A, const float4 *
     const float4 *p21 = reinterpret_cast<const float4 *>(A.ctab + ((size_t)t2 * T1 + t1) * S_pad) + tl;
     float sum = 0.0f, csum = 0.0f;
     const uint64_t dd2 = f2_pack(dd, dd);
+    // Where a lane's ore words are the first four of the row at known
+    // positions (4-lane teams: word k / 2 in iteration k; 8-lane teams: word k,
+    // at most four iterations), one 16-byte load per row fetches them all (the
+    // row stride leaves four words after ore_off whenever W <= 4).
+    constexpr bool ORE4 = TEAM == 4 || (TEAM == 8 && KF + (TAIL ? 1 : 0) <= 4);
+    uint4 ow1 = make_uint4(0u, 0u, 0u, 0u), ow2 = ow1;
+    if (ORE4) {
+        ow1 = __ldg(reinterpret_cast<const uint4 *>(w1));
+        if (SWAP) ow2 = __ldg(reinterpret_cast<const uint4 *>(w2));
+    }
+    auto word = [&](const uint4 &o, const uint32_t *w, int k, int wi) -> uint32_t {
+        if (!ORE4) return __ldg(w + wi);
+        const int c = TEAM == 4 ? (k >> 1) : k;
+        return c == 0 ? o.x : (c == 1 ? o.y : (c == 2 ? o.z : o.w));
+    };
     auto quad = [&](int k, float (&x)[4]) {
         const int q = tl + k * TEAM;
         const int wi = q >> 3;
@@ -363,10 +387,10 @@ __device__ __forceinline__ void team_eval_fast(const EvalArgs &A, const float4 *
         const float4 pa = __ldg(p12 + k * TEAM);
         if (SWAP) {
             const float4 b = __ldg(r2 + k * TEAM);
-            const uint32_t n1 = (__ldg(w1 + wi) >> sh) & 0xfu;
-            const uint32_t n2 = (__ldg(w2 + wi) >> sh) & 0xfu;
-            const float4 m1 = lut[n1 & ~n2];
-            const float4 m2 = lut[n2 & ~n1];
+            const uint32_t n1 = (word(ow1, w1, k, wi) >> sh) & 0xfu;
+            const uint32_t n2 = (word(ow2, w2, k, wi) >> sh) & 0xfu;
+            const float4 m1 = nib_mask(n1 & ~n2);
+            const float4 m2 = nib_mask(n2 & ~n1);
             const float4 pb = __ldg(p21 + k * TEAM);
             // x = (a - b) dd + (m2 pb + m1 pa), scenario by scenario, in pairs
             const uint64_t lo = f2_fma(f2_sub(f2_pack(a.x, a.y), f2_pack(b.x, b.y)), dd2,
@@ -378,7 +402,7 @@ __device__ __forceinline__ void team_eval_fast(const EvalArgs &A, const float4 *
             f2_unpack(lo, x[0], x[1]);
             f2_unpack(hi, x[2], x[3]);
         } else {
-            const float4 m1 = lut[(__ldg(w1 + wi) >> sh) & 0xfu];
+            const float4 m1 = nib_mask((word(ow1, w1, k, wi) >> sh) & 0xfu);
             // x = a dd + m1 pa
             const uint64_t lo = f2_fma(f2_pack(a.x, a.y), dd2, f2_mul(f2_pack(m1.x, m1.y), f2_pack(pa.x, pa.y)));
             const uint64_t hi = f2_fma(f2_pack(a.z, a.w), dd2, f2_mul(f2_pack(m1.z, m1.w), f2_pack(pa.z, pa.w)));
@@ -527,6 +551,49 @@ __device__ __forceinline__ uint64_t block_merge_lists(const uint64_t *lists, int
     return t;
 }
 
+// block_merge_lists that also follows the move record of the best key:
+// infos[l] belongs to lists[l]'s head; the record of the merged head comes
+// back in inf_out (valid in every thread after the call).
+template <int NW>
+__device__ __forceinline__ uint64_t block_merge_lists_info(const uint64_t *lists, const int4 *infos, int nlists,
+                                                           uint64_t (*s_wl)[32], int4 *s_inf, int4 &inf_out) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint64_t t = 0;
+    int4 inf = make_int4(0, 0, 0, 0);
+    for (int l0 = warp; l0 < nlists; l0 += 4 * NW) {
+        uint64_t c[4];
+        int4 ci[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const int l = l0 + u * NW;
+            c[u] = l < nlists ? __ldcg(lists + (size_t)l * 32 + lane) : 0ull;
+            ci[u] = l < nlists ? __ldcg(infos + l) : make_int4(0, 0, 0, 0);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const uint64_t mrg = warp_topk_merge(t, c[u]);
+            if (__shfl_sync(0xffffffffu, mrg == c[u], 0)) inf = ci[u];  // the head came from list u
+            t = mrg;
+        }
+    }
+    s_wl[warp][lane] = t;
+    if (lane == 0) s_inf[warp] = inf;
+    __syncthreads();
+#pragma unroll
+    for (int stride = NW / 2; stride > 0; stride >>= 1) {
+        if (warp < stride) {
+            const uint64_t o = s_wl[warp + stride][lane];
+            const uint64_t mrg = warp_topk_merge(t, o);
+            if (__shfl_sync(0xffffffffu, mrg == o, 0) && lane == 0) s_inf[warp] = s_inf[warp + stride];
+            t = mrg;
+            s_wl[warp][lane] = t;
+        }
+        __syncthreads();
+    }
+    inf_out = s_inf[0];
+    return t;
+}
+
 // Called by one full warp with the merged list t: writes the top k (move
 // indices, their scores decoded from the keys, the count) and returns the
 // best move's index in every lane, -1 when nothing is feasible.  A key always
@@ -575,34 +642,44 @@ __device__ __forceinline__ void prefetch_l2_range(const void *p, size_t bytes, i
 }
 
 // End of a batch's top-k selection, called by every thread of every CTA with
-// the warp's list wtk.  The CTA merges its warps' lists (a tree) and publishes
-// its 32 best keys; the last CTA of each group of grp_size CTAs to finish (a
-// ticket counter per group; nobody waits) merges the group's lists into one;
-// the last group to finish merges the group lists, writes the top k and, when
-// asked, applies the best move.  Each ticket is reset by the CTA that draws its
-// last number, so every counter is zero again for the next launch.  Two levels
-// of about sqrt(grid) lists each keep the merging short, and all but the last
-// group merge while others still evaluate.  Before an in-launch apply, the
-// group-merging CTAs pull the apply's per-period state and the grade rows of
-// their group's best move into L2.
+// the warp's list wtk and (fused step) the move record of each warp's best key
+// (winfo[warp], shared memory; NULL when no apply follows).  The CTA merges its
+// warps' lists (a tree) and publishes its 32 best keys with the record of the
+// best; the last CTA of each group of grp_size CTAs to finish (a ticket counter
+// per group; nobody waits) merges the group's lists into one; the last group to
+// finish merges the group lists, writes the top k and, when asked, applies the
+// best move from its record, so no move has to be fetched or decoded again.
+// Each ticket is reset by the CTA that draws its last number, so every counter
+// is zero again for the next launch.  Two levels of about sqrt(grid) lists each
+// keep the merging short, and all but the last group merge while others still
+// evaluate.  Before an in-launch apply, the group-merging CTAs pull the apply's
+// per-period state and the grade rows of their group's best move into L2.
 // Not inlined: the evaluator's main loop keeps its own register allocation.
-static __device__ __noinline__ void step_reduce(const StepTail &T, uint64_t wtk) {
+static __device__ __noinline__ void step_reduce(const StepTail &T, uint64_t wtk, const int4 *winfo) {
     constexpr int NW = kEvalThreads / 32;
     __shared__ uint64_t s_wl[NW][32];
+    __shared__ int4 s_inf[NW];
     __shared__ int s_last, s_best;
     const StepLists &L = T.L;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     s_wl[warp][lane] = wtk;
+    if (lane == 0) s_inf[warp] = winfo ? winfo[warp] : make_int4(0, 0, 0, 0);
     __syncthreads();
 #pragma unroll
     for (int stride = NW / 2; stride > 0; stride >>= 1) {
         if (warp < stride) {
-            wtk = warp_topk_merge(wtk, s_wl[warp + stride][lane]);
+            const uint64_t o = s_wl[warp + stride][lane];
+            const uint64_t mrg = warp_topk_merge(wtk, o);
+            if (__shfl_sync(0xffffffffu, mrg == o, 0) && lane == 0) s_inf[warp] = s_inf[warp + stride];
+            wtk = mrg;
             s_wl[warp][lane] = wtk;
         }
         __syncthreads();
     }
-    if (warp == 0) L.cta[(size_t)blockIdx.x * 32 + lane] = wtk;
+    if (warp == 0) {
+        L.cta[(size_t)blockIdx.x * 32 + lane] = wtk;
+        if (lane == 0) L.cinf[blockIdx.x] = s_inf[0];
+    }
     __syncthreads();
     const int g = (int)blockIdx.x / L.grp_size, g0 = g * L.grp_size;
     const int gn = min(L.grp_size, (int)gridDim.x - g0);
@@ -610,8 +687,12 @@ static __device__ __noinline__ void step_reduce(const StepTail &T, uint64_t wtk)
     if (tid == 0) s_last = ticket_next(L.tick + g) == (uint32_t)(gn - 1);
     __syncthreads();
     if (!s_last) return;
-    uint64_t t = block_merge_lists<NW>(L.cta + (size_t)g0 * 32, gn, s_wl);
-    if (warp == 0) L.grp[(size_t)g * 32 + lane] = t;
+    int4 inf;
+    uint64_t t = block_merge_lists_info<NW>(L.cta + (size_t)g0 * 32, L.cinf + g0, gn, s_wl, s_inf, inf);
+    if (warp == 0) {
+        L.grp[(size_t)g * 32 + lane] = t;
+        if (lane == 0) L.ginf[g] = inf;
+    }
     if (tid == 0) L.tick[g] = 0;
     if (T.do_apply) {
         const ApplyArgs &P = T.ap;
@@ -622,22 +703,17 @@ static __device__ __noinline__ void step_reduce(const StepTail &T, uint64_t wtk)
         prefetch_l2_range(P.contrib, ts * sizeof(double), i, nt);
         prefetch_l2_range(P.npv, (size_t)P.S * sizeof(double), i, nt);
         prefetch_l2_range(P.tab, (size_t)2 * (P.T + 1) * P.S_pad * sizeof(float), i, nt);
-        if (warp == 0) {
-            const uint64_t best = __shfl_sync(0xffffffffu, t, 0);
-            const uint32_t id = ~(uint32_t)(best & 0xffffffffull);
-            if (best != 0ull && (int64_t)id < T.n) {
-                const int2 mv = __ldg(T.moves + id);
-                const size_t row = (size_t)P.S * sizeof(double);
-                if (mv.x >= 0 && mv.x < P.tp.B) prefetch_l2_range(P.grade + (size_t)mv.x * P.S, row, lane, 32);
-                if (mv.y >= 0 && mv.y < P.tp.B) prefetch_l2_range(P.grade + (size_t)mv.y * P.S, row, lane, 32);
-            }
+        if (warp == 0 && __shfl_sync(0xffffffffu, t, 0) != 0ull) {
+            const size_t row = (size_t)P.S * sizeof(double);
+            prefetch_l2_range(P.grade + (size_t)inf.x * P.S, row, lane, 32);
+            if (inf.y != P.tp.B) prefetch_l2_range(P.grade + (size_t)inf.y * P.S, row, lane, 32);
         }
     }
     __syncthreads();
     if (tid == 0) s_last = ticket_next(L.tick + L.final_slot) == (uint32_t)(ng - 1);
     __syncthreads();
     if (!s_last) return;
-    t = block_merge_lists<NW>(L.grp, ng, s_wl);
+    t = block_merge_lists_info<NW>(L.grp, L.ginf, ng, s_wl, s_inf, inf);
     if (warp == 0) {
         const int best = warp_write_topk(t, T.k, T.n, T.status, T.idx_out, T.top_out, T.count_out);
         if (lane == 0) s_best = best;
@@ -645,9 +721,7 @@ static __device__ __noinline__ void step_reduce(const StepTail &T, uint64_t wtk)
     if (tid == 0) L.tick[L.final_slot] = 0;
     if (!T.do_apply) return;
     __syncthreads();
-    const int b = s_best;
-    const int2 mv = b >= 0 ? __ldg(T.moves + b) : make_int2(0, -1);
-    apply_block(T.ap, mv, b >= 0 ? 1 : 0);
+    apply_evaluated(T.ap, inf, s_best >= 0 ? 1 : 0);
 }
 
 // List storage and tickets of model m for a launch of `grid` CTAs (mm_eval.cu).
@@ -664,17 +738,18 @@ struct EvalShared {
     uint8_t lsh[kEvalThreads / 32][kChunk], lsw[kEvalThreads / 32][kChunk];
     float score[kEvalThreads / 32][kChunk], mean[kEvalThreads / 32][kChunk];
     uint8_t flag[kEvalThreads / 32][kChunk];
+    int4 best[kEvalThreads / 32];  // TOPK: the move of the warp's best key (b1, b2 or B, t1 | t2 << 8, 0)
 };
 
 // The evaluator proper: the calling warp evaluates moves [r0, r1) of A in
 // chunks of 64 (decode two per lane, shift / swap lists by ballot, teams of
 // TEAM lanes per move, coalesced stores) and, if TOPK, inserts every feasible
 // move's key into its register list wtk.  tab, s_dd, s_mined and s_cap are
-// the CTA's staged tables; s_lut the 16 ore-nibble masks.
+// the CTA's staged tables.
 template <int TEAM, int QMAX, bool KAHAN, bool DELTA, int KF, bool TAIL, bool TOPK>
-__device__ __forceinline__ void eval_warp_range(const EvalArgs &A, EvalShared &sh, const float4 *s_lut,
-                                                const float *tab, const float *s_dd, const int64_t *s_mined,
-                                                const uint64_t *s_cap, int64_t r0, int64_t r1, uint64_t &wtk) {
+__device__ __forceinline__ void eval_warp_range(const EvalArgs &A, EvalShared &sh, const float *tab, const float *s_dd,
+                                                const int64_t *s_mined, const uint64_t *s_cap, int64_t r0, int64_t r1,
+                                                uint64_t &wtk) {
     constexpr int CH = kChunk;
     constexpr int TPW = 32 / TEAM;
     const int T1 = A.T + 1;
@@ -717,7 +792,7 @@ __device__ __forceinline__ void eval_warp_range(const EvalArgs &A, EvalShared &s
             sh.score[warp][slot] = v.valid ? 0.0f : -INFINITY;
             sh.mean[warp][slot] = 0.0f;
             if (TOPK) sh.flag[warp][slot] = (active && v.feasible) ? 1 : 0;
-            if (work) {
+            if (active && v.valid) {  // every feasible move's data, for the top-k's move record
                 sh.b1[warp][slot] = v.b1;
                 sh.b2[warp][slot] = v.swap ? v.b2 : A.tp.B;
                 sh.tt[warp][slot] = v.t1 | (v.t2 << 8);
@@ -767,19 +842,19 @@ __device__ __forceinline__ void eval_warp_range(const EvalArgs &A, EvalShared &s
                 const int ntail = NQ - KF * TEAM;
                 float d[KF + 1][4];
                 if (!sw)
-                    team_eval_fast<TEAM, KF, TAIL, false, KAHAN>(A, s_lut, tl, row1, row2, t1, t2, dd, ntail, invS,
+                    team_eval_fast<TEAM, KF, TAIL, false, KAHAN>(A, tl, row1, row2, t1, t2, dd, ntail, invS,
                                                                  d, mu, sd);
                 else
-                    team_eval_fast<TEAM, KF, TAIL, true, KAHAN>(A, s_lut, tl, row1, row2, t1, t2, dd, ntail, invS, d,
+                    team_eval_fast<TEAM, KF, TAIL, true, KAHAN>(A, tl, row1, row2, t1, t2, dd, ntail, invS, d,
                                                                 mu, sd);
                 if (act && DELTA) write_deltas_fast<TEAM, KF>(A, c0 + slot, tl, ntail, d);
             } else {
                 float d[QMAX][4];
                 if (!sw)
-                    team_eval<TEAM, QMAX, false, KAHAN, false>(A, tab, s_lut, tl, act, row1, row2, t1, t2, dd, NQ,
+                    team_eval<TEAM, QMAX, false, KAHAN, false>(A, tab, tl, act, row1, row2, t1, t2, dd, NQ,
                                                                rem, invS, pin_off, d, mu, sd);
                 else
-                    team_eval<TEAM, QMAX, true, KAHAN, false>(A, tab, s_lut, tl, act, row1, row2, t1, t2, dd, NQ,
+                    team_eval<TEAM, QMAX, true, KAHAN, false>(A, tab, tl, act, row1, row2, t1, t2, dd, NQ,
                                                               rem, invS, pin_off, d, mu, sd);
                 if (act && DELTA) write_deltas<TEAM, QMAX>(A, c0 + slot, tl, NQ, rem, d);
             }
@@ -804,7 +879,15 @@ __device__ __forceinline__ void eval_warp_range(const EvalArgs &A, EvalShared &s
                     const float f = sh.score[warp][slot];
                     if (!isnan(f)) key = score_key(f, i);
                 }
+                const uint64_t before = __shfl_sync(0xffffffffu, wtk, 0);
                 wtk = warp_topk_insert(wtk, key);
+                const uint64_t after = __shfl_sync(0xffffffffu, wtk, 0);
+                if (after != before) {
+                    // a new best came from this round: record its move
+                    const int src = __ffs(__ballot_sync(0xffffffffu, key == after)) - 1;
+                    const int sl = h * 32 + src;
+                    if (lane == 0) sh.best[warp] = make_int4(sh.b1[warp][sl], sh.b2[warp][sl], (int)sh.tt[warp][sl], 0);
+                }
             }
         }
         __syncwarp();
@@ -815,7 +898,6 @@ template <int TEAM, int QMAX, bool KAHAN, bool DELTA, bool TSM, int KF = 0, bool
 __global__ void __launch_bounds__(kEvalThreads, MM_EVAL_MINB) k_eval_tiled(EvalArgs A) {
     constexpr int NW = kEvalThreads / 32;   // warps per CTA
     extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ float4 s_lut[16];
     __shared__ EvalShared sh;
 
     const int T1 = A.T + 1;
@@ -838,9 +920,6 @@ __global__ void __launch_bounds__(kEvalThreads, MM_EVAL_MINB) k_eval_tiled(EvalA
         s_mined[i] = A.minedT[i];
         s_cap[i] = A.cap[i];
     }
-    if (tid < 16)
-        s_lut[tid] = make_float4((float)(tid & 1), (float)((tid >> 1) & 1), (float)((tid >> 2) & 1),
-                                 (float)((tid >> 3) & 1));
     __syncthreads();
     const float *tab = TSM ? s_tab : A.tab;
 
@@ -850,8 +929,8 @@ __global__ void __launch_bounds__(kEvalThreads, MM_EVAL_MINB) k_eval_tiled(EvalA
     const int64_t gw = (int64_t)blockIdx.x * NW + warp;
     const int64_t r0 = gw * A.n / nwarps, r1 = (gw + 1) * A.n / nwarps;
     uint64_t wtk = 0;  // this warp's best 32 candidate keys (TOPK)
-    eval_warp_range<TEAM, QMAX, KAHAN, DELTA, KF, TAIL, TOPK>(A, sh, s_lut, tab, s_dd, s_mined, s_cap, r0, r1, wtk);
-    if constexpr (TOPK) step_reduce(A.tail, wtk);
+    eval_warp_range<TEAM, QMAX, KAHAN, DELTA, KF, TAIL, TOPK>(A, sh, tab, s_dd, s_mined, s_cap, r0, r1, wtk);
+    if constexpr (TOPK) step_reduce(A.tail, wtk, A.tail.do_apply ? sh.best : nullptr);
 }
 
 // ----------------------------------------------------------------------------
@@ -921,7 +1000,6 @@ __global__ void __launch_bounds__(kEvalThreads, 1) k_eval_tma(EvalArgs A) {
     constexpr int NWMAX = kEvalThreads / 32;
     constexpr int TPW = 32 / TEAM;
     extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ float4 s_lut[16];
     __shared__ int32_t s_b1[NWMAX][CH], s_b2[NWMAX][CH];
     __shared__ uint32_t s_tt[NWMAX][CH];
     __shared__ uint8_t s_lsh[NWMAX][CH], s_lsw[NWMAX][CH];
@@ -954,9 +1032,6 @@ __global__ void __launch_bounds__(kEvalThreads, 1) k_eval_tma(EvalArgs A) {
         s_mined[i] = A.minedT[i];
         s_cap[i] = A.cap[i];
     }
-    if (tid < 16)
-        s_lut[tid] = make_float4((float)(tid & 1), (float)((tid >> 1) & 1), (float)((tid >> 2) & 1),
-                                 (float)((tid >> 3) & 1));
     const int lane = tid & 31, warp = tid >> 5;
     if (lane == 0)
         for (int st = 0; st < NS; st++) mbar_init(&s_bar[warp][st], 1);
@@ -1076,10 +1151,10 @@ __global__ void __launch_bounds__(kEvalThreads, 1) k_eval_tma(EvalArgs A) {
             float d[QMAX][4];
             float mu, sd;
             if (!sw)
-                team_eval<TEAM, QMAX, false, KAHAN, true>(A, tab, s_lut, tl, act, row1, row2, t1, t2, dd, NQ, rem,
+                team_eval<TEAM, QMAX, false, KAHAN, true>(A, tab, tl, act, row1, row2, t1, t2, dd, NQ, rem,
                                                           invS, pin_off, d, mu, sd);
             else
-                team_eval<TEAM, QMAX, true, KAHAN, true>(A, tab, s_lut, tl, act, row1, row2, t1, t2, dd, NQ, rem,
+                team_eval<TEAM, QMAX, true, KAHAN, true>(A, tab, tl, act, row1, row2, t1, t2, dd, NQ, rem,
                                                          invS, pin_off, d, mu, sd);
             if (act) {
                 if (tl == 0) {

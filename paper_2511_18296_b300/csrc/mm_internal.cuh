@@ -104,6 +104,8 @@ struct mm_model {
     mm::TopkScratch topk;
     uint64_t *step_cta = nullptr;    // fused search step: [step_max_ctas][32] published keys
     uint64_t *step_grp = nullptr;    // [step_max_ctas][32] merged lists of groups of CTAs
+    int4 *step_cinf = nullptr;       // [step_max_ctas] move record of each CTA list's best key
+    int4 *step_ginf = nullptr;       // [step_max_ctas] move record of each group list's best key
     uint32_t *step_tick = nullptr;   // [step_max_ctas + 1] group tickets, then the final ticket (zero between launches)
     int step_max_ctas = 0;
     void *step_event = nullptr;      // cudaEvent_t recorded between the step's two launches (timing hook)

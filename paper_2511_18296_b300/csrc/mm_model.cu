@@ -247,6 +247,48 @@ __global__ void k_apply(ApplyArgs A, int2 mv_val, const int2 *moves, int64_t n_m
     apply_block(A, mv, have);
 }
 
+// NPV mean and population std over scenarios of the current schedule (FP64,
+// two passes) into the model's apply result; one CTA.
+__global__ void k_npv_stats(const double *__restrict__ npv, int32_t S, ApplyResult *res) {
+    __shared__ double red[32];
+    __shared__ double s_mean;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    double x = 0.0;
+    for (int s = threadIdx.x; s < S; s += blockDim.x) x = __dadd_rn(x, npv[s]);
+    x = warp_sum_f64(x);
+    if (lane == 0) red[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        double y = lane < nw ? red[lane] : 0.0;
+        y = warp_sum_f64(y);
+        if (lane == 0) s_mean = y / (double)S;
+    }
+    __syncthreads();
+    const double mean = s_mean;
+    double q = 0.0;
+    for (int s = threadIdx.x; s < S; s += blockDim.x) {
+        const double d = __dsub_rn(npv[s], mean);
+        q = __fma_rn(d, d, q);
+    }
+    q = warp_sum_f64(q);
+    __syncthreads();
+    if (lane == 0) red[warp] = q;
+    __syncthreads();
+    if (warp == 0) {
+        double y = lane < nw ? red[lane] : 0.0;
+        y = warp_sum_f64(y);
+        if (lane == 0) {
+            res->mean = mean;
+            res->std = sqrt(y / (double)S);
+        }
+    }
+}
+
+static mm_status npv_stats_launch(mm_model *m) {
+    k_npv_stats<<<1, 256, 0, m->stream>>>(m->npv, m->S, m->apply_res);
+    return check_launch("k_npv_stats");
+}
+
 // ------------------------------------------------------------------ host
 
 mm_status rebuild_tables(mm_model *m) {
@@ -273,7 +315,6 @@ ApplyArgs apply_args(mm_model *m) {
     A.disc = m->disc; A.cap = m->cap; A.target = m->target;
     A.pr = m->price * m->recovery; A.pc = m->proc_cost; A.mc = m->mining_cost;
     A.a = m->shortfall_pen; A.e = m->excess_pen;
-    A.invS = 1.0 / (double)m->S;
     A.res = m->apply_res;
     A.status = m->status;
     A.metal32 = m->shadow32;
@@ -323,6 +364,8 @@ void mm_model_destroy(mm_model *m) {
     cudaFree(m->apply_res);
     cudaFree(m->step_cta);
     cudaFree(m->step_grp);
+    cudaFree(m->step_cinf);
+    cudaFree(m->step_ginf);
     cudaFree(m->step_tick);
     cudaFree(m->tabc);
     cudaFree(m->relax_scratch);
@@ -439,6 +482,8 @@ mm_status mm_model_create(const mm_model_desc *d, mm_model **out) {
     m->step_max_ctas = m->num_sms * 8;  // 256-thread CTAs: at most 8 resident per SM
     ALLOC(step_cta, (size_t)m->step_max_ctas * 32);
     ALLOC(step_grp, (size_t)m->step_max_ctas * 32);
+    ALLOC(step_cinf, (size_t)m->step_max_ctas);
+    ALLOC(step_ginf, (size_t)m->step_max_ctas);
     ALLOC(step_tick, (size_t)m->step_max_ctas + 1);
     ALLOC(tabc, (int64_t)4 * (T + 1));
     if (!grid) {
@@ -603,6 +648,7 @@ mm_status mm_apply_move(mm_model *m, mm_move mv, double *mean, double *sd) {
     k_apply<<<1, apply_threads(m), 0, m->stream>>>(A, make_int2(mv.b1, mv.arg), nullptr, 0, nullptr, nullptr, 0);
     mm_status st = check_launch("k_apply");
     if (st != MM_OK) return st;
+    if ((st = npv_stats_launch(m)) != MM_OK) return st;
     MM_CUDA_TRY(cudaMemcpyAsync(m->apply_res_host, m->apply_res, sizeof(ApplyResult), cudaMemcpyDeviceToHost, m->stream),
                 "read apply result");
     MM_CUDA_TRY(cudaStreamSynchronize(m->stream), "synchronize");
@@ -653,6 +699,10 @@ mm_status mm_get_fp32_shadow_npv(mm_model *m, double *npv_host) {
 
 mm_status mm_last_apply(mm_model *m, int32_t *applied, double *mean, double *sd) {
     if (!m) return set_error(MM_ERR_INVALID_ARG, "NULL model");
+    if (m->has_schedule) {
+        mm_status st = npv_stats_launch(m);
+        if (st != MM_OK) return st;
+    }
     MM_CUDA_TRY(cudaMemcpyAsync(m->apply_res_host, m->apply_res, sizeof(ApplyResult), cudaMemcpyDeviceToHost, m->stream),
                 "read apply result");
     MM_CUDA_TRY(cudaStreamSynchronize(m->stream), "synchronize");

@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_topk_lists(const float *__rest
             wtk = warp_topk_insert(wtk, (ok[u] && !isnan(f[u])) ? score_key(f[u], i) : 0ull);
         }
     }
-    step_reduce(tail, wtk);
+    step_reduce(tail, wtk, nullptr);
 }
 
 mm_status topk_small_launch(mm_model *m, const float *score, const uint8_t *feas, int64_t n, int32_t k, int32_t *idx,
