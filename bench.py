@@ -347,54 +347,46 @@ def gpu_arm(args):
             plain_rest()
     stream.synchronize()
 
-    def capture(fn):
+    R = 20  # steps per CUDA graph
+
+    def graph_of(fns):
+        """A CUDA graph of R steps, each an L2 flush followed by the launches
+        of fns (as a search loop runs them: back to back)."""
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g, stream=stream):
-            fn()
+            for _ in range(R):
+                flush.zero_()
+                for fn in fns:
+                    fn()
         return g
 
-    # the library records ev_mid between the step's evaluation launch (with the
-    # top-k selection) and its apply launch (an external event node in the graph)
-    ev_mid = torch.cuda.Event(enable_timing=True)
-    ev_mid.record(stream)
-    m.set_step_event(ev_mid)
-    g_step = capture(fused)
-    m.set_step_event(None)
-    g_eval, g_rest = capture(plain_eval), capture(plain_rest)
-    g_kahan = capture(lambda: m.eval_moves(moves_d, score=score, feas=feas, want_mean=False, kahan=True))
-
-    def timed(graphs, K):
-        """Per-step device times (ms) of the given graphs replayed in order,
-        L2 flushed before every step; returns [step][graph]."""
-        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(graphs) + 1)] for _ in range(K)]
+    def replay_ms(g):
+        """Device time (ms) of one replay, CUDA events on the launching stream."""
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         with torch.cuda.stream(stream):
-            for k in range(K):
-                flush.zero_()
-                ev[k][0].record(stream)
-                for j, g in enumerate(graphs):
-                    g.replay()
-                    ev[k][j + 1].record(stream)
-        torch.cuda.synchronize()
-        return [[ev[k][j].elapsed_time(ev[k][j + 1]) for j in range(len(graphs))] for k in range(K)]
+            e0.record(stream)
+            g.replay()
+            e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1)
 
-    def timed_step(K):
-        """Per-step device times (ms) of the fused step: [step, evaluation
-        launch (with the top-k), apply launch]; L2 flushed before every step.  ev_mid is
-        re-recorded by every replay, so each step is read before the next."""
-        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(K)]
+    g_flush = graph_of([])
+
+    def steps_ms(g, K):
+        """Per-step device times (ms) of K steps: replays of g (R steps each)
+        alternate with replays of the flush-only graph, and each replay's
+        flushes are subtracted, so the L2 flush between steps stays outside
+        the step times while the steps run exactly as in a loop (events
+        recorded between the launches would add their own gaps)."""
         out = []
-        with torch.cuda.stream(stream):
-            for k in range(K):
-                flush.zero_()
-                ev[k][0].record(stream)
-                g_step.replay()
-                ev[k][1].record(stream)
-                ev[k][1].synchronize()
-                out.append((ev[k][0].elapsed_time(ev[k][1]), ev[k][0].elapsed_time(ev_mid),
-                            ev_mid.elapsed_time(ev[k][1])))
-        return out
+        while len(out) < K:
+            t, f = replay_ms(g), replay_ms(g_flush)
+            out.extend([(t - f) / R] * R)
+        return out[:K]
 
-    timed_step(3)
+    g_step = graph_of([fused])
+    replay_ms(g_step)
+    replay_ms(g_flush)
     m.schedule_set(p.x0)  # every timed run starts from the same schedule
     K = args.steps
     with ClockSampler(local) as clk:
@@ -402,23 +394,25 @@ def gpu_arm(args):
             dist.barrier()
         torch.cuda.synchronize()
         t_start = time.time()
-        step_t = timed_step(K)
+        step_t = steps_ms(g_step, K)
         if world > 1:
             dist.barrier()
+        torch.cuda.synchronize()
         t_end = time.time()
-    total_ms = float(sum(t[0] for t in step_t))
+    total_ms = float(sum(step_t))
     step_avg_ms = total_ms / K
-    eval_avg_ms = float(np.mean([t[1] for t in step_t]))
-    finish_avg_ms = float(np.mean([t[2] for t in step_t]))
     applied, npv_mean, _ = m.last_apply()
     # the plain form (one launch per call) and the compensated-sum evaluator, same workload
-    m.schedule_set(p.x0)
     Kp = max(20, min(K, 500))
-    plain_t = timed([g_eval, g_rest], Kp)
-    plain_eval_ms = float(np.mean([t[0] for t in plain_t]))
-    plain_step_ms = float(np.mean([t[0] + t[1] for t in plain_t]))
+    g_eval, g_plain = graph_of([plain_eval]), graph_of([plain_eval, plain_rest])
+    g_kahan = graph_of([lambda: m.eval_moves(moves_d, score=score, feas=feas, want_mean=False, kahan=True)])
     m.schedule_set(p.x0)
-    kahan_eval_ms = float(np.mean([t[0] for t in timed([g_kahan], Kp)]))
+    plain_eval_ms = float(np.mean(steps_ms(g_eval, Kp)))
+    m.schedule_set(p.x0)
+    plain_step_ms = float(np.mean(steps_ms(g_plain, Kp)))
+    m.schedule_set(p.x0)
+    kahan_eval_ms = float(np.mean(steps_ms(g_kahan, Kp)))
+    m.schedule_set(p.x0)
 
     # end to end through the public API with host buffers
     K2 = max(20, min(200, K))
@@ -445,12 +439,11 @@ def gpu_arm(args):
     e2e_avg = sum(e2e_s) / len(e2e_s)
 
     # max over ranks
-    local_vals = torch.tensor([total_ms, step_avg_ms, e2e_avg, plain_step_ms, plain_eval_ms, eval_avg_ms,
-                               finish_avg_ms], dtype=torch.float64, device=dev)
+    local_vals = torch.tensor([total_ms, step_avg_ms, e2e_avg, plain_step_ms, plain_eval_ms],
+                              dtype=torch.float64, device=dev)
     if world > 1:
         dist.all_reduce(local_vals, op=dist.ReduceOp.MAX)
-    (total_ms, step_avg_ms, e2e_avg, plain_step_ms, plain_eval_ms, eval_avg_ms,
-     finish_avg_ms) = [float(v) for v in local_vals.cpu()]
+    total_ms, step_avg_ms, e2e_avg, plain_step_ms, plain_eval_ms = [float(v) for v in local_vals.cpu()]
 
     evals_per_step = n * S
     value = world * evals_per_step * K / (total_ms * 1e-3)
@@ -468,12 +461,13 @@ def gpu_arm(args):
                             + ", replayed from a CUDA graph"),
                    "topk": TOPK,
                    "l2": "flushed before every step (256 MB write outside the step events)",
+                   "timing": (f"CUDA events around replays of a CUDA graph of {R} (flush, step) pairs, minus replays "
+                              f"of the {R} flushes alone"),
                    "per_rank_moves": n, "parallelism": f"independent batches x{world}"},
         "roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved_gbs / peaks["hbm_gbs"], "traffic": profiled_traffic(),
                      "kernel": EVAL_KERNEL + " (mm_eval_moves: one evaluation launch per batch, timed in the plain form)",
                      "kernel_ms": plain_eval_ms,
-                     "step_launch_ms": eval_avg_ms + finish_avg_ms,
                      "step_frac": alg / (step_avg_ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
                      "algorithmic_bytes_per_launch": alg, "peak_source": f"{which} (MEASURED_PEAKS.json hbm_gbs)"},
         "plain_form": {"desc": "mm_eval_moves, then mm_topk + mm_apply_best: one launch per call, same workload",

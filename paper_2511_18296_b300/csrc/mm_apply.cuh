@@ -140,16 +140,13 @@ static __device__ __forceinline__ int32_t apply_neighbour(const Topo &tp, int32_
 // table_entry); in between the expression is evaluated here.
 static __device__ __forceinline__ void table_store_c(int t, int s, int32_t S_pad, int32_t T, int64_t x, float4 tc,
                                                      double d, int64_t m, double a, double e, float *tab,
-                                                     float *tab_copy) {
+                                                     float2 &out) {
     const float po = x >= m ? tc.x : (x <= 0 ? tc.y : __double2float_rn(__dmul_rn(d, pen_diff(x, x - m, a, e))));
     const float pi = x >= 0 ? tc.z : (x <= -m ? tc.w : __double2float_rn(__dmul_rn(d, pen_diff(x, x + m, a, e))));
-    const int64_t io = (int64_t)t * S_pad + s, ii = (int64_t)(T + 1) * S_pad + io;
+    const int64_t io = (int64_t)t * S_pad + s;
     tab[io] = po;
-    tab[ii] = pi;
-    if (tab_copy) {
-        tab_copy[io] = po;
-        tab_copy[ii] = pi;
-    }
+    tab[(int64_t)(T + 1) * S_pad + io] = pi;
+    out = make_float2(po, pi);
 }
 
 // Period-pair rows and columns of periods ra and rb (see apply_block), by
@@ -213,7 +210,7 @@ constexpr int kApplyTabMax = 4608;
 // The NPV mean and std over scenarios are not formed here (k_npv_stats does
 // that on request), so an apply ends with the state update.
 static __device__ __forceinline__ void apply_core(const ApplyArgs &A, const MoveView &v, int go) {
-    __shared__ float s_tab[kApplyTabMax];
+    __shared__ __align__(16) float s_tab[kApplyTabMax];
     const int s = threadIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nwarp = blockDim.x >> 5;
     const bool hs = s < A.S;
@@ -223,14 +220,18 @@ static __device__ __forceinline__ void apply_core(const ApplyArgs &A, const Move
     if (!go) return;
     const int32_t mb2 = v.swap ? v.b2 : -1;
     const bool r1 = v.t1 < T, r2 = v.t2 < T;
-    // 1. loads (the staged table skips the rows of t1 and t2: the scenario
-    // threads write their new entries there)
-    if (tab_sm)
-        for (uint32_t r = (uint32_t)warp; r < 2 * T1; r += (uint32_t)nwarp) {
-            const uint32_t t = r < T1 ? r : r - T1;
-            if ((r1 && t == v.t1) || (r2 && t == v.t2)) continue;
-            for (uint32_t s2 = (uint32_t)lane; s2 < (uint32_t)A.S; s2 += 32u) s_tab[r * sp + s2] = A.tab[r * sp + s2];
-        }
+    const bool c1 = r1, c2 = r2 && v.t2 != v.t1;  // periods whose period-pair rows change
+    const bool stage = tab_sm && (c1 || c2);     // copies issued here are always waited for below
+    // 1. loads: the Pout / Pin tables go to shared memory by asynchronous
+    // 16-byte copies, all in flight at once (waited for before the rebuild)
+    if (stage) {
+        const uint32_t n16 = (uint32_t)(2 * pin / 4);
+        for (uint32_t i = threadIdx.x; i < n16; i += blockDim.x)
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(s_tab + 4 * i)),
+                         "l"(A.tab + 4 * (size_t)i)
+                         : "memory");
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    }
     uint32_t o1 = 0, o2 = 0;
     double gr1 = 0.0, gr2 = 0.0, M1 = 0.0, M2 = 0.0, C1 = 0.0, C2 = 0.0, my_npv = 0.0, disc1 = 0.0, disc2 = 0.0;
     int64_t O1 = 0, O2 = 0, tgt1 = 0, tgt2 = 0, mined1 = 0, mined2 = 0;
@@ -273,7 +274,32 @@ static __device__ __forceinline__ void apply_core(const ApplyArgs &A, const Move
     if (A.tp.nx > 0) {
         if (warp == nwarp - 1 && lane < 22) {
             const int32_t b = apply_neighbour(A.tp, v.b1, mb2, lane);
-            if (b >= 0) A.blk[b] = block_bounds(A.tp, b, period_after);
+            if (b >= 0) {
+                // the ten grid neighbours' words are loaded together, then the
+                // moved blocks' periods are substituted
+                const int32_t nxy = A.tp.nx * A.tp.ny;
+                const int32_t x = b % A.tp.nx, y = (b / A.tp.nx) % A.tp.ny, z = b / nxy;
+                int32_t nb[10];
+                uint32_t w[10];
+#pragma unroll
+                for (int k = 0; k < 5; k++) {
+                    const int32_t px = x + (k == 1 ? -1 : (k == 2 ? 1 : 0)), py = y + (k == 3 ? -1 : (k == 4 ? 1 : 0));
+                    const bool in = px >= 0 && px < A.tp.nx && py >= 0 && py < A.tp.ny;
+                    nb[2 * k] = (in && z > 0) ? px + A.tp.nx * (py + A.tp.ny * (z - 1)) : -1;
+                    nb[2 * k + 1] = (in && z + 1 < A.tp.nz) ? px + A.tp.nx * (py + A.tp.ny * (z + 1)) : -1;
+                }
+#pragma unroll
+                for (int k = 0; k < 10; k++) w[k] = nb[k] >= 0 ? A.blk[nb[k]] : 0u;
+                uint32_t lo = 0, hi = T;
+#pragma unroll
+                for (int k = 0; k < 10; k++) {
+                    if (nb[k] < 0) continue;
+                    const uint32_t t = nb[k] == v.b1 ? v.t2 : (nb[k] == mb2 ? v.t1 : blk_period(w[k]));
+                    if (k & 1) hi = t < hi ? t : hi;
+                    else lo = t > lo ? t : lo;
+                }
+                A.blk[b] = blk_pack(b == v.b1 ? v.t2 : (b == mb2 ? v.t1 : blk_period(A.blk[b])), lo, hi);
+            }
         }
     } else {
         // CSR: the moved blocks and every direct predecessor and successor
@@ -290,6 +316,7 @@ static __device__ __forceinline__ void apply_core(const ApplyArgs &A, const Move
             }
         }
     }
+    float2 np1 = make_float2(0.0f, 0.0f), np2 = np1;  // new (Pout, Pin) of t1 and t2
     if (hs) {
         const int64_t om1 = o1 ? (int64_t)v.m1 : 0, om2 = (v.swap && o2) ? (int64_t)v.m2 : 0;
         const double g1 = o1 ? __dmul_rn((double)v.m1, gr1) : 0.0;
@@ -304,8 +331,7 @@ static __device__ __forceinline__ void apply_core(const ApplyArgs &A, const Move
             A.oreT[i1] = nO;
             A.metal[i1] = nM;
             A.contrib[i1] = c;
-            if (A.uniform) table_store_c(v.t1, s, A.S_pad, A.T, nO - tgt1, tc1, disc1, mu_, A.a, A.e, A.tab,
-                                         tab_sm ? s_tab : nullptr);
+            if (A.uniform) table_store_c(v.t1, s, A.S_pad, A.T, nO - tgt1, tc1, disc1, mu_, A.a, A.e, A.tab, np1);
         }
         if (r2) {
             const int64_t nO = O2 + om1 - om2;
@@ -315,8 +341,7 @@ static __device__ __forceinline__ void apply_core(const ApplyArgs &A, const Move
             A.oreT[i2] = nO;
             A.metal[i2] = nM;
             A.contrib[i2] = c;
-            if (A.uniform) table_store_c(v.t2, s, A.S_pad, A.T, nO - tgt2, tc2, disc2, mu_, A.a, A.e, A.tab,
-                                         tab_sm ? s_tab : nullptr);
+            if (A.uniform) table_store_c(v.t2, s, A.S_pad, A.T, nO - tgt2, tc2, disc2, mu_, A.a, A.e, A.tab, np2);
         }
         my_npv = __dadd_rn(my_npv, dnpv);
         A.npv[s] = my_npv;
@@ -341,29 +366,36 @@ static __device__ __forceinline__ void apply_core(const ApplyArgs &A, const Move
             A.npv32[s] += d32;
         }
     }
-    if (!A.ctab) return;
-    __syncthreads();  // the new Pout / Pin entries of t1 and t2 are written
-    // 3. ctab[a][b][s] = Pout[a][s] + Pin[b][s] for the rows a and columns b of
-    // the changed periods
-    const bool c1 = r1, c2 = r2 && v.t2 != v.t1;
-    if (!(c1 || c2)) return;
+    if (!A.ctab || !(c1 || c2)) return;
     const uint32_t ra = c1 ? v.t1 : v.t2, rb = c2 ? v.t2 : ra;
-    if (tab_sm) {
-        // every operand in shared memory: only the stores leave the SM
-        const uint32_t S = (uint32_t)A.S;
-        for (uint32_t b = (uint32_t)warp; b < T1; b += (uint32_t)nwarp) {
-            for (uint32_t s2 = (uint32_t)lane; s2 < S; s2 += 32u) {
-                const float pob = s_tab[b * sp + s2], pib = s_tab[pin + b * sp + s2];
-                const float poa = s_tab[ra * sp + s2], pia = s_tab[pin + ra * sp + s2];
-                const float por = s_tab[rb * sp + s2], pir = s_tab[pin + rb * sp + s2];
-                A.ctab[((size_t)ra * T1 + b) * sp + s2] = poa + pib;
-                A.ctab[((size_t)b * T1 + ra) * sp + s2] = pob + pia;
-                A.ctab[((size_t)rb * T1 + b) * sp + s2] = por + pib;
-                A.ctab[((size_t)b * T1 + rb) * sp + s2] = pob + pir;
-            }
-        }
-    } else {
+    if (!tab_sm) {
+        __syncthreads();  // the new Pout / Pin entries of t1 and t2 are in global memory
         ctab_rebuild(A.tab, A.ctab, T1, (uint32_t)A.S, sp, ra, rb, warp, nwarp, lane);
+        return;
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncthreads();  // every staged row has landed
+    if (hs && A.uniform) {
+        if (r1) { s_tab[v.t1 * sp + s] = np1.x; s_tab[pin + v.t1 * sp + s] = np1.y; }
+        if (r2) { s_tab[v.t2 * sp + s] = np2.x; s_tab[pin + v.t2 * sp + s] = np2.y; }
+    }
+    __syncthreads();
+    // 3. ctab[a][b][s] = Pout[a][s] + Pin[b][s] for the rows a and columns b of
+    // the changed periods, four scenarios per item, every operand in shared
+    // memory: only the 16-byte stores leave the SM
+    const uint32_t qp = (uint32_t)(sp / 4), items = T1 * qp;
+    const float4 *st4 = reinterpret_cast<const float4 *>(s_tab);
+    float4 *ct4 = reinterpret_cast<float4 *>(A.ctab);
+    const size_t pin4 = (size_t)T1 * qp;
+    for (uint32_t it = threadIdx.x; it < items; it += blockDim.x) {
+        const uint32_t b = it / qp, q = it - b * qp;
+        const float4 pob = st4[b * qp + q], pib = st4[pin4 + b * qp + q];
+        const float4 poa = st4[ra * qp + q], pia = st4[pin4 + ra * qp + q];
+        const float4 por = st4[rb * qp + q], pir = st4[pin4 + rb * qp + q];
+        ct4[((size_t)ra * T1 + b) * qp + q] = make_float4(poa.x + pib.x, poa.y + pib.y, poa.z + pib.z, poa.w + pib.w);
+        ct4[((size_t)b * T1 + ra) * qp + q] = make_float4(pob.x + pia.x, pob.y + pia.y, pob.z + pia.z, pob.w + pia.w);
+        ct4[((size_t)rb * T1 + b) * qp + q] = make_float4(por.x + pib.x, por.y + pib.y, por.z + pib.z, por.w + pib.w);
+        ct4[((size_t)b * T1 + rb) * qp + q] = make_float4(pob.x + pir.x, pob.y + pir.y, pob.z + pir.z, pob.w + pir.w);
     }
 }
 

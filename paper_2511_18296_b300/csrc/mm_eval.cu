@@ -168,6 +168,7 @@ EvalArgs eval_args(mm_model *m, const mm_move *moves, int64_t n, float *score, u
     A.m_uniform = m->m_uniform;
     A.nstage = 0;
     A.prefetch = m->prefetch < 0 ? kDefaultPrefetch : m->prefetch;
+
     A.lambda = (float)m->lambda;
     A.a = m->shortfall_pen; A.e = m->excess_pen;
     A.qpl = 0;

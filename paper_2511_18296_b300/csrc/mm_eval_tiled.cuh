@@ -154,11 +154,13 @@ __device__ __forceinline__ uint64_t warp_topk_insert(uint64_t t, uint64_t c) {
     return t;
 }
 
-// Merge another best-first list into t, skipped when it cannot contribute.
+// Merge another best-first list into t, skipped when it cannot contribute
+// (and taken as it is when t is empty).
 __device__ __forceinline__ uint64_t warp_topk_merge(uint64_t t, uint64_t c_sorted) {
     const uint64_t thr = __shfl_sync(0xffffffffu, t, 31);
     const uint64_t best = __shfl_sync(0xffffffffu, c_sorted, 0);
     if (best <= thr) return t;
+    if (__shfl_sync(0xffffffffu, t, 0) == 0ull) return c_sorted;
     return warp_merge_sorted(t, c_sorted);
 }
 

@@ -228,7 +228,7 @@ static mm_status shadow_init(mm_model *m) {
 // Apply kernel: the move comes either by value (from_dev = 0) or as
 // moves[idx[0]] when *count > 0 (from_dev = 1; an index outside the batch is a
 // bad move).
-__global__ void k_apply(ApplyArgs A, int2 mv_val, const int2 *moves, int64_t n_moves, const int32_t *idx,
+__global__ void __launch_bounds__(1024) k_apply(ApplyArgs A, int2 mv_val, const int2 *moves, int64_t n_moves, const int32_t *idx,
                         const int32_t *count, int from_dev) {
     int2 mv = mv_val;
     int have = 1;
