@@ -413,14 +413,37 @@ def gpu_arm(args):
     m.schedule_set(p.x0)
     kahan_eval_ms = float(np.mean(steps_ms(g_kahan, Kp)))
     m.schedule_set(p.x0)
+    # violation magnitudes of the batch (epsilon-relaxed fitness), same moves
+    cap_ex = torch.empty(n, dtype=torch.int64, device=dev)
+    prec_ex = torch.empty(n, dtype=torch.int32, device=dev)
+    viol = lambda: m.eval_violation(moves_d, cap_ex, prec_ex)  # noqa: E731
+    with torch.cuda.stream(stream):
+        viol()
+    viol_ms = float(np.mean(steps_ms(graph_of([viol]), Kp)))
+    # differentiated form: relaxed objective forward and adjoint on the same model
+    xr = torch.as_tensor(W.relaxed_x(p.B, p.T, 2), device=dev)
+    gr = torch.as_tensor(p.grade.astype(np.float32), device=dev)
+    gJ = torch.ones(1, dtype=torch.float64, device=dev)
+    fwd = lambda: m.relaxed_forward(xr, gr)  # noqa: E731
+
+    def fwd_bwd():
+        _, npv_r, ot_r = m.relaxed_forward(xr, gr)
+        m.relaxed_backward(xr, gr, npv_r, ot_r, gJ)
+
+    with torch.cuda.stream(stream):
+        fwd_bwd()
+    stream.synchronize()
+    rel_fwd_ms = float(np.mean(steps_ms(graph_of([fwd]), Kp)))
+    rel_both_ms = float(np.mean(steps_ms(graph_of([fwd_bwd]), Kp)))
 
     # end to end through the public API with host buffers
     K2 = max(20, min(200, K))
     moves_h = torch.from_numpy(p.moves).pin_memory()
     torch.cuda.set_stream(stream)
-    idx_h = torch.empty(TOPK, dtype=torch.int32).pin_memory()
-    top_h = torch.empty(TOPK, dtype=torch.float32).pin_memory()
-    cnt_h = torch.empty(1, dtype=torch.int32).pin_memory()
+    # the step's outputs in one device buffer (idx, top, count), read back with one copy
+    out_d = torch.empty(2 * TOPK + 1, dtype=torch.int32, device=dev)
+    idx_e, top_e, cnt_e = out_d[:TOPK], out_d[TOPK:2 * TOPK].view(torch.float32), out_d[2 * TOPK:]
+    out_h = torch.empty(2 * TOPK + 1, dtype=torch.int32).pin_memory()
     m.schedule_set(p.x0)
     e2e_s = []
     for k in range(K2 + 3):
@@ -428,10 +451,8 @@ def gpu_arm(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         moves_d.copy_(moves_h, non_blocking=True)
-        m.search_step(moves_d, k=TOPK, apply=True, score=score, feas=feas, idx=idx, top=top, count=cnt)
-        idx_h.copy_(idx, non_blocking=True)
-        top_h.copy_(top, non_blocking=True)
-        cnt_h.copy_(cnt, non_blocking=True)
+        m.search_step(moves_d, k=TOPK, apply=True, score=score, feas=feas, idx=idx_e, top=top_e, count=cnt_e)
+        out_h.copy_(out_d, non_blocking=True)
         _, e2e_mean, _ = m.last_apply()  # synchronises; NPV after the applied move
         t1 = time.perf_counter()
         if k >= 3:
@@ -477,8 +498,18 @@ def gpu_arm(args):
         "precision_form": {"desc": "mm_eval_moves_ex with compensated scenario sums (MM_EVAL_KAHAN)",
                            "eval_kernel_ms": kahan_eval_ms,
                            "eval_roofline_frac": alg / (kahan_eval_ms * 1e-3) / 1e9 / peaks["hbm_gbs"]},
+        "violation_form": {"desc": "mm_eval_violation: capacity and precedence excess of every move (exact integers)",
+                           "ms_per_batch": viol_ms, "moves_per_s": n / (viol_ms * 1e-3)},
+        "differentiated_form": {
+            "desc": "relaxed objective on the same model, x[b,t] ~ Dirichlet(1) (seed 2): forward, and forward + "
+                    "adjoint (dJ/dx, dJ/dg)",
+            "forward_ms": rel_fwd_ms, "forward_backward_ms": rel_both_ms,
+            "algorithmic_bytes": {"forward": 4 * p.B * (p.T + p.S), "forward_backward": 4 * p.B * 3 * (p.T + p.S)},
+            "forward_gbs": 4 * p.B * (p.T + p.S) / (rel_fwd_ms * 1e-3) / 1e9,
+            "forward_backward_gbs": 4 * p.B * 3 * (p.T + p.S) / (rel_both_ms * 1e-3) / 1e9,
+            "vs_plain_eval": {"plain_eval_ms": plain_eval_ms}},
         "e2e": {"value": evals_per_step * world / e2e_avg, "unit": UNIT,
-                "h2d_bytes_per_step": int(p.moves.nbytes), "d2h_bytes_per_step": TOPK * 8 + 4 + 24 + 4,
+                "h2d_bytes_per_step": int(p.moves.nbytes), "d2h_bytes_per_step": int(out_h.numel()) * 4 + 24 + 4,
                 "ms_per_step": e2e_avg * 1e3,
                 "path": "pinned host moves -> mm_search_step (apply on device) -> top-k and NPV to host"},
         "gpu_launches": (1 if S <= 256 else 2) * K,  # per step: the evaluation launch (top-k and apply inside when S <= 256)

@@ -132,6 +132,23 @@ mm_status mm_schedule_get(mm_model *m, uint8_t *period_host);
 mm_status mm_eval_moves(mm_model *m, const mm_move *moves_dev, int64_t n, float *score_dev,
                         uint8_t *feasible_dev, float *mean_dev);
 
+/* Violation magnitudes of n moves against the current schedule, for the
+ * epsilon-relaxed fitness of the paper's search (Algorithm 2: fitness =
+ * NPV - penalty max(0, violation - epsilon); Section 6, Phase 2).  The paper
+ * does not define violation(S) further; this library reports, exactly:
+ *   cap_excess[i]  = sum over the distinct periods t < T that a moved block
+ *                    leaves or enters of max(0, mined'_t - M_t), tonnes (Eq. 16);
+ *   prec_excess[i] = sum over the moved blocks b of max(0, L_b - x'_b) +
+ *                    max(0, x'_b - H_b), periods, with L_b / H_b the latest
+ *                    predecessor / earliest successor period in x' (0 / T when
+ *                    there are none) (Eq. 15).
+ * Both are 0 exactly when mm_eval_moves gives the move flag 1.  A bad move gets
+ * -1 in both and raises the sticky MM_ERR_BAD_MOVE.  moves_dev[n], outputs
+ * cap_excess_dev[n] (int64) and prec_excess_dev[n] (int32): device memory.
+ * Asynchronous. */
+mm_status mm_eval_violation(mm_model *m, const mm_move *moves_dev, int64_t n, int64_t *cap_excess_dev,
+                            int32_t *prec_excess_dev);
+
 /* Tile shape of the move evaluator (chosen by the autotuner or by hand):
  * team = lanes that evaluate one move (4, 8, 16 or 32; 0 = built-in choice),
  * ctas_per_sm = resident CTAs per SM of the persistent grid (0 = occupancy

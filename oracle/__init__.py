@@ -50,6 +50,7 @@ def _load():
     lib.or_topk.argtypes = [P, P, C.c_int64, C.c_int32, P, P]
     lib.or_apply.restype = C.c_int
     lib.or_apply.argtypes = [P, P, C.c_int32, C.c_int32]
+    lib.or_violation.argtypes = [P, P, P, C.c_int64, P, P]
     _lib = lib
     return lib
 
@@ -168,6 +169,17 @@ class OracleModel:
                                      _p(o["score"]), _p(o["flag"]), _p(o["floor"]),
                                      _p(fs) if fs is not None else None)
         return o
+
+    def violation(self, x, moves):
+        """(capacity excess int64 [n] tonnes, precedence excess int32 [n]
+        periods) of each move by brute force; -1 for bad moves."""
+        xx = np.ascontiguousarray(x, np.uint8)
+        mv = np.ascontiguousarray(moves, np.int32).reshape(-1, 2)
+        n = mv.shape[0]
+        ce = np.zeros(max(n, 1), np.int64)
+        pe = np.zeros(max(n, 1), np.int32)
+        self.lib.or_violation(self._mp, _p(xx), _p(mv), n, _p(ce), _p(pe))
+        return ce[:n], pe[:n]
 
     def apply(self, x, move) -> int:
         """Apply (b1, arg) to x in place: 0 applied, 1 infeasible, 2 bad move."""

@@ -450,3 +450,76 @@ int or_apply(const or_model *M, uint8_t *x, int32_t b1, int32_t arg) {
     free(xp);
     return ok ? 0 : 1;
 }
+
+/* ------------------------------------------------------------ violation */
+
+/* Violation magnitudes of each move, for the epsilon-relaxed fitness of
+ * Algorithm 2 (fitness = NPV - penalty * max(0, violation - epsilon)).  The
+ * paper leaves violation(S) undefined; the reading used here, both parts
+ * exact integers that are zero exactly when the move's flag is 1:
+ *   capacity excess: over the distinct periods t < T that a moved block
+ *     leaves or enters, the sum of max(0, mined'_t - M_t) (tonnes, Eq. 16);
+ *   precedence excess: over the moved blocks b, max(0, L_b - x'_b) +
+ *     max(0, x'_b - H_b) (periods, Eq. 15), where L_b is the latest period of
+ *     a direct predecessor of b and H_b the earliest period of a direct
+ *     successor of b in x' (0 and T when there are none).
+ * Brute force: x' is formed and every arc and every block is scanned.  A bad
+ * move gets -1 in both outputs. */
+void or_violation(const or_model *M, const uint8_t *x, const int32_t *moves, int64_t n, int64_t *cap_ex,
+                  int32_t *prec_ex) {
+#pragma omp parallel
+    {
+        uint8_t *xp = (uint8_t *)malloc(M->B);
+#pragma omp for schedule(dynamic, 16)
+        for (int64_t i = 0; i < n; i++) {
+            int32_t blk[2];
+            int newp[2], nm = 0;
+            if (!decode(M, x, moves[2 * i], moves[2 * i + 1], blk, newp, &nm)) {
+                cap_ex[i] = -1;
+                prec_ex[i] = -1;
+                continue;
+            }
+            if (nm == 2 && blk[0] == blk[1]) nm = 1; /* a block swapped with itself */
+            memcpy(xp, x, M->B);
+            for (int k = 0; k < nm; k++) xp[blk[k]] = (uint8_t)newp[k];
+            /* capacity over the distinct periods left or entered */
+            int per[4], np = 0;
+            for (int k = 0; k < nm; k++) {
+                int cand[2] = {x[blk[k]], xp[blk[k]]};
+                for (int q = 0; q < 2; q++) {
+                    int seen = 0;
+                    for (int r = 0; r < np; r++)
+                        if (per[r] == cand[q]) seen = 1;
+                    if (!seen) per[np++] = cand[q];
+                }
+            }
+            int64_t ce = 0;
+            for (int r = 0; r < np; r++) {
+                int t = per[r];
+                if (t >= M->T) continue;
+                int64_t mined = 0;
+                for (int32_t b = 0; b < M->B; b++)
+                    if (xp[b] == t) mined += M->mass[b];
+                if ((uint64_t)mined > M->cap[t]) ce += mined - (int64_t)M->cap[t];
+            }
+            /* precedence: bounds of every moved block in x' from all arcs */
+            int32_t pe = 0;
+            for (int k = 0; k < nm; k++) {
+                int32_t b = blk[k];
+                int L = 0, H = M->T;
+                for (int32_t c = 0; c < M->B; c++)
+                    for (int32_t e = M->pred_ptr[c]; e < M->pred_ptr[c + 1]; e++) {
+                        int32_t p = M->pred_idx[e];
+                        if (c == b && xp[p] > L) L = xp[p];
+                        if (p == b && xp[c] < H) H = xp[c];
+                    }
+                int t = xp[b];
+                pe += (L > t ? L - t : 0) + (t > H ? t - H : 0);
+            }
+            cap_ex[i] = ce;
+            prec_ex[i] = pe;
+        }
+        free(xp);
+    }
+}
+

@@ -77,6 +77,7 @@ SIGNATURES = [
     ("mm_schedule_get", C.c_int, [P, P]),
     ("mm_eval_moves", C.c_int, [P, P, I64, P, P, P]),
     ("mm_eval_moves_ex", C.c_int, [P, P, I64, P, P, P, P, I32]),
+    ("mm_eval_violation", C.c_int, [P, P, I64, P, P]),
     ("mm_set_tile", C.c_int, [P, I32, I32, I32, I32]),
     ("mm_topk", C.c_int, [P, P, P, I64, I32, P, P, P]),
     ("mm_topk_noalloc", C.c_int, [P, P, I64, I32, P, P, P, P]),
@@ -241,6 +242,19 @@ class Model:
             _check(L.mm_eval_moves_ex(self.h, _ptr(moves), n, _ptr(score), _ptr(feas), _ptr(mean), _ptr(delta),
                                       opts))
         return score, feas, mean
+
+    def eval_violation(self, moves, cap_excess=None, prec_excess=None):
+        """mm_eval_violation: (capacity excess int64 [n] in tonnes, precedence
+        excess int32 [n] in periods) of each move; both 0 iff its flag is 1."""
+        import torch
+        assert moves.is_cuda and moves.dtype == torch.int32 and moves.is_contiguous()
+        n = moves.shape[0]
+        if cap_excess is None:
+            cap_excess = torch.empty(n, dtype=torch.int64, device=moves.device)
+        if prec_excess is None:
+            prec_excess = torch.empty(n, dtype=torch.int32, device=moves.device)
+        _check(lib().mm_eval_violation(self.h, _ptr(moves), n, _ptr(cap_excess), _ptr(prec_excess)))
+        return cap_excess, prec_excess
 
     def eval_deltas(self, moves, kahan: bool = False, generic: bool = False):
         """Per-scenario deltas [n, S] as well (parity/debug path)."""

@@ -121,6 +121,7 @@ mm_status set_error(mm_status st, const char *fmt, ...);
 mm_status cuda_status(cudaError_t e, const char *what);
 mm_status check_launch(const char *what);
 mm_status read_sticky(mm_model *m);  // synchronises, clears and maps the sticky bits
+mm_status sticky_status(mm_model *m, uint32_t st);  // maps and clears sticky bits already read back
 
 // Kernels and launchers shared between translation units.
 mm_status rebuild_tables(mm_model *m);                     // Pout/Pin from oreT

@@ -53,7 +53,11 @@ mm_status read_sticky(mm_model *m) {
     MM_CUDA_TRY(cudaMemcpyAsync(m->status_host, m->status, sizeof(uint32_t), cudaMemcpyDeviceToHost, m->stream),
                 "read status");
     MM_CUDA_TRY(cudaStreamSynchronize(m->stream), "synchronize");
-    uint32_t st = *m->status_host;
+    return sticky_status(m, *m->status_host);
+}
+
+// Map the sticky bits st (already read back) to a status and clear them.
+mm_status sticky_status(mm_model *m, uint32_t st) {
     if (st) {
         MM_CUDA_TRY(cudaMemsetAsync(m->status, 0, sizeof(uint32_t), m->stream), "clear status");
         if (st & kStTimeout) return set_error(MM_ERR_TIMEOUT, "a bounded device wait ran out");
@@ -68,6 +72,8 @@ static Topo topo_of(const mm_model *m) {
     tp.pred_ptr = m->pred_ptr; tp.pred_idx = m->pred_idx; tp.succ_ptr = m->succ_ptr; tp.succ_idx = m->succ_idx;
     return tp;
 }
+
+Topo topo_of_model(const mm_model *m) { return topo_of(m); }
 
 // ---------------------------------------------------------------- kernels
 
@@ -703,13 +709,16 @@ mm_status mm_last_apply(mm_model *m, int32_t *applied, double *mean, double *sd)
         mm_status st = npv_stats_launch(m);
         if (st != MM_OK) return st;
     }
+    // the result and the sticky status come back with one synchronisation
     MM_CUDA_TRY(cudaMemcpyAsync(m->apply_res_host, m->apply_res, sizeof(ApplyResult), cudaMemcpyDeviceToHost, m->stream),
                 "read apply result");
+    MM_CUDA_TRY(cudaMemcpyAsync(m->status_host, m->status, sizeof(uint32_t), cudaMemcpyDeviceToHost, m->stream),
+                "read status");
     MM_CUDA_TRY(cudaStreamSynchronize(m->stream), "synchronize");
     if (applied) *applied = m->apply_res_host->applied;
     if (mean) *mean = m->apply_res_host->mean;
     if (sd) *sd = m->apply_res_host->std;
-    return read_sticky(m);
+    return sticky_status(m, *m->status_host);
 }
 
 mm_status mm_npv(mm_model *m, double *npv_host, double *mean, double *sd) {
