@@ -256,10 +256,12 @@ static __device__ __forceinline__ void apply_core(const ApplyArgs &A, const Move
             if (A.uniform) tc2 = A.tabc[v.t2];
         }
     }
-    // 2. updates
+    // 2. updates.  Every thread has read the mined tonnage of t1 and t2 above;
+    // thread 0 overwrites it only after the barrier (go is uniform over the CTA)
     const int64_t dm1 = v.m1, dm2 = v.swap ? (int64_t)v.m2 : 0;
     mined1 += -dm1 + dm2;
     mined2 += dm1 - dm2;
+    __syncthreads();
     if (threadIdx.x == 0) {
         if (r1) A.minedT[v.t1] = A.minedT[v.t1] - dm1 + dm2;
         if (r2) A.minedT[v.t2] = A.minedT[v.t2] + dm1 - dm2;

@@ -150,3 +150,25 @@ def test_step_event_splits_the_two_launches():
         rb = b.search_step(mv, k=32, apply=True)
     _compare(out, rb, 32)
     assert np.array_equal(a.schedule_get(), b.schedule_get())
+
+
+@pytest.mark.parametrize("name,steps", [("plain_4k", 60), ("plain_50k", 30)])
+def test_step_state_matches_rebuild(name, steps):
+    """After every fused step, the running FP64 state (per-period tonnage,
+    metal, NPV_s) equals a from-scratch rebuild of the same schedule on a
+    fresh model: exactly for the integer tonnages, to FP64 rounding for the
+    metal and NPV.  Many steps, so an ordering race inside the in-launch apply
+    (one thread updating a value others still read) cannot hide."""
+    p = W.config(name)
+    a, fresh = _pair(p)
+    mv = torch.as_tensor(p.moves, device="cuda")
+    for _ in range(steps):
+        a.search_step(mv, k=8, apply=True)
+        assert a.last_apply()[0] == 1
+        fresh.schedule_set(a.schedule_get())
+        ma, oa = a.tonnage()
+        mf, of = fresh.tonnage()
+        assert np.array_equal(ma, mf) and np.array_equal(oa, of)
+        np.testing.assert_allclose(a.metal(), fresh.metal(), rtol=1e-12, atol=1e-6)
+        npv_a, npv_f = a.npv()[0], fresh.npv()[0]
+        np.testing.assert_allclose(npv_a, npv_f, rtol=1e-12, atol=1e-3)
