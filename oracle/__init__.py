@@ -65,6 +65,7 @@ class _OrModel(C.Structure):
         ("mining_cost", C.c_double), ("proc_cost", C.c_double),
         ("shortfall_pen", C.c_double), ("excess_pen", C.c_double),
         ("discount_rate", C.c_double), ("lam", C.c_double),
+        ("sigma", C.c_void_p),
     ]
 
 
@@ -90,9 +91,11 @@ def stencil_preds(nx: int, ny: int, nz: int):
 class OracleModel:
     """FP64 oracle over one problem instance (a ``workloads.Problem`` or any
     object with the same attributes).  ``preds`` overrides the 1-5 stencil with
-    an explicit CSR (ptr, idx) of direct predecessors."""
+    an explicit CSR (ptr, idx) of direct predecessors.  ``sigma`` (float64
+    [T][S], optional) holds the uncertainty weights sigma(s,t) of Eq. 12, which
+    scale the processing margin of ore blocks."""
 
-    def __init__(self, prob, preds=None):
+    def __init__(self, prob, preds=None, sigma=None):
         self.lib = _load()
         self.B, self.S, self.T = prob.B, prob.S, prob.T
         if preds is None:
@@ -106,7 +109,11 @@ class OracleModel:
         self.m = _OrModel(self.B, self.S, self.T, _p(self.pred_ptr), _p(self.pred_idx), _p(self.mass),
                           _p(self.grade), _p(self.cap), _p(self.target), prob.price, prob.recovery,
                           prob.mining_cost, prob.proc_cost, prob.shortfall_pen, prob.excess_pen,
-                          prob.discount_rate, prob.lam)
+                          prob.discount_rate, prob.lam, None)
+        self.sigma = None
+        if sigma is not None:
+            self.sigma = np.ascontiguousarray(sigma, np.float64).reshape(self.T, self.S)
+            self.m.sigma = _p(self.sigma)
         self.ore, self.value = self.classify()
 
     @property

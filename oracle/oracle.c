@@ -45,6 +45,7 @@ typedef struct {
     const uint64_t *target;  /* [T] tonnes, mill ore target Q_t */
     double price, recovery, mining_cost, proc_cost;
     double shortfall_pen, excess_pen, discount_rate, lambda;
+    const double *sigma;     /* [T*S] uncertainty weights sigma(s,t), period-major; NULL = none */
 } or_model;
 
 /* ------------------------------------------------------------------ setup */
@@ -112,6 +113,21 @@ static double penalty(const or_model *M, int t, int64_t ore_t) {
     return M->shortfall_pen * short_t + M->excess_pen * excess_t;
 }
 
+/* Cash flow of block b in scenario s when mined in period t (0 when t = T,
+ * unmined).  Without weights it is value[b,s].  With the uncertainty weights
+ * of Section 5.6 (Eq. 12: ENPV_{b,s,t} = sigma(s,t) (Revenue - ProcessingCost))
+ * the processing margin m((g*p)*rec - pc) of an ore block is scaled by
+ * sigma(s,t); the mining cost m*mc (the scenario-independent c_bt of Eq. 14)
+ * and the mill penalties are not. */
+static double block_cash(const or_model *M, const uint8_t *ore, const double *value, int32_t b, int s, int t) {
+    if (t >= M->T) return 0.0;
+    int64_t i = (int64_t)b * M->S + s;
+    if (!M->sigma) return value[i];
+    double m = (double)M->mass[b];
+    double margin = ore[i] ? m * ((M->grade[i] * M->price) * M->recovery - M->proc_cost) : 0.0;
+    return M->sigma[(int64_t)t * M->S + s] * margin - m * M->mining_cost;
+}
+
 /* minedT[t] and oreT[t*S+s] for t < T (integer tonnes, exact). */
 void or_tonnage(const or_model *M, const uint8_t *ore, const uint8_t *x, int64_t *minedT, int64_t *oreT) {
     int S = M->S, T = M->T;
@@ -126,7 +142,8 @@ void or_tonnage(const or_model *M, const uint8_t *ore, const uint8_t *x, int64_t
     }
 }
 
-/* NPV_s(x) = sum_t d_t * ( sum_{b: x_b = t} value[b,s] - pen_t(oreT[t,s]) ). */
+/* NPV_s(x) = sum_t d_t * ( sum_{b: x_b = t} cash(b,s,t) - pen_t(oreT[t,s]) ),
+ * cash = value[b,s] or its weighted form (block_cash). */
 void or_npv(const or_model *M, const uint8_t *ore, const double *value, const uint8_t *x, double *npv) {
     int S = M->S, T = M->T;
     double *cash = (double *)calloc((size_t)T * S, sizeof(double));
@@ -135,7 +152,7 @@ void or_npv(const or_model *M, const uint8_t *ore, const double *value, const ui
         int t = x[b];
         if (t >= T) continue;
         for (int s = 0; s < S; s++) {
-            cash[(int64_t)t * S + s] += value[(int64_t)b * S + s];
+            cash[(int64_t)t * S + s] += block_cash(M, ore, value, b, s, t);
             if (ore[(int64_t)b * S + s]) oreT[(int64_t)t * S + s] += M->mass[b];
         }
     }
@@ -279,6 +296,7 @@ void or_eval_bruteforce(const or_model *M, const uint8_t *ore, const double *val
 /* Second, independent evaluator: O(S) per move from the per-period integer
  * tonnages.  For each moved block c going from period f to period u:
  *   value change   v[c,s] * (d_u - d_f)
+ *                  (weighted: cash(c,s,u) d_u - cash(c,s,f) d_f, see block_cash)
  *   ore change     -m_c*ore[c,s] in period f, +m_c*ore[c,s] in period u
  * then for each affected period p < T:
  *   NPV change  -d_p * ( pen_p(O[p,s] + dO[p,s]) - pen_p(O[p,s]) ).
@@ -360,9 +378,16 @@ void or_eval_incremental(const or_model *M, const uint8_t *ore, const double *va
             for (int s = 0; s < S; s++) {
                 double dv = 0.0, fs = 0.0;
                 for (int k = 0; k < nm; k++) {
-                    double term = value[(int64_t)blk[k] * S + s] * (d[newp[k]] - d[oldp[k]]);
-                    dv += term;
-                    fs += fabs(term);
+                    if (M->sigma) {
+                        double gain = block_cash(M, ore, value, blk[k], s, newp[k]) * d[newp[k]];
+                        double loss = block_cash(M, ore, value, blk[k], s, oldp[k]) * d[oldp[k]];
+                        dv += gain - loss;
+                        fs += fabs(gain) + fabs(loss);
+                    } else {
+                        double term = value[(int64_t)blk[k] * S + s] * (d[newp[k]] - d[oldp[k]]);
+                        dv += term;
+                        fs += fabs(term);
+                    }
                 }
                 for (int r = 0; r < np; r++) {
                     int t = per[r];

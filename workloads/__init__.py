@@ -24,6 +24,7 @@ from .configs import (
     config,
     batched_chain_specs,
     relaxed_x,
+    uncertainty_weights,
 )
 
 __all__ = [
@@ -37,4 +38,5 @@ __all__ = [
     "config",
     "batched_chain_specs",
     "relaxed_x",
+    "uncertainty_weights",
 ]

@@ -243,3 +243,20 @@ def relaxed_x(B: int, T: int, seed: int) -> np.ndarray:
     rng = np.random.default_rng(np.random.SeedSequence(seed))
     x = rng.dirichlet(np.ones(T), size=B)
     return np.ascontiguousarray(x, dtype=np.float32)
+
+
+def uncertainty_weights(T: int, S: int, seed: int = 4) -> np.ndarray:
+    """Synthetic uncertainty weights sigma(s,t) of Eq. 12, float64 [T][S].
+
+    Built as the product of Eq. 2: a spatial factor per scenario from Eq. 10,
+    1 - I_s + sigma_local_s with Moran's I_s ~ U(0.2, 0.6) and local variance
+    sigma_local_s ~ U(0.05, 0.3); a temporal confidence decay exp(-0.05 t);
+    and a geological factor per (s, t) ~ U(0.9, 1.1) standing in for the
+    feature-weighted term of Eq. 11 (so the weights are not a rank-one
+    product).  Values lie in about [0.15, 1.2]."""
+    rng = np.random.default_rng(np.random.SeedSequence(seed))
+    moran = rng.uniform(0.2, 0.6, size=S)
+    local = rng.uniform(0.05, 0.3, size=S)
+    geo = rng.uniform(0.9, 1.1, size=(T, S))
+    temporal = np.exp(-0.05 * np.arange(T, dtype=np.float64))
+    return np.ascontiguousarray(temporal[:, None] * (1.0 - moran + local)[None, :] * geo, np.float64)
