@@ -435,6 +435,22 @@ def gpu_arm(args):
     stream.synchronize()
     rel_fwd_ms = float(np.mean(steps_ms(graph_of([fwd]), Kp)))
     rel_both_ms = float(np.mean(steps_ms(graph_of([fwd_bwd]), Kp)))
+    # weighted form: the same model and batch with uncertainty weights sigma(s,t)
+    mw = mm.Model.from_problem(p, sigma=W.uncertainty_weights(p.T, p.S))
+    mw.schedule_set(p.x0)
+    mw.set_stream(stream)
+    w_eval = lambda: mw.eval_moves(moves_d, score=score, feas=feas, want_mean=False)  # noqa: E731
+    w_step = lambda: mw.search_step(moves_d, k=TOPK, apply=True, score=score, feas=feas, idx=idx, top=top,  # noqa: E731
+                                    count=cnt)
+    with torch.cuda.stream(stream):
+        w_eval()
+        w_step()
+    stream.synchronize()
+    mw.schedule_set(p.x0)
+    w_eval_ms = float(np.mean(steps_ms(graph_of([w_eval]), Kp)))
+    mw.schedule_set(p.x0)
+    w_step_ms = float(np.mean(steps_ms(graph_of([w_step]), Kp)))
+    mw.close()
 
     # end to end through the public API with host buffers: every step copies
     # its batch of moves from pinned host memory and reads its outputs back.
@@ -524,6 +540,13 @@ def gpu_arm(args):
         "precision_form": {"desc": "mm_eval_moves_ex with compensated scenario sums (MM_EVAL_KAHAN)",
                            "eval_kernel_ms": kahan_eval_ms,
                            "eval_roofline_frac": alg / (kahan_eval_ms * 1e-3) / 1e9 / peaks["hbm_gbs"]},
+        "weighted_form": {"desc": "uncertainty weights sigma(s,t) of Eq. 12 (synthetic, seed 4) on the same model and "
+                                  "batch: evaluation launch, and the step as separate evaluation, top-k and apply "
+                                  "launches",
+                          "eval_kernel_ms": w_eval_ms,
+                          "eval_roofline_frac": alg / (w_eval_ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
+                          "step_ms": w_step_ms,
+                          "value": n * p.S / (w_step_ms * 1e-3), "unit": UNIT},
         "violation_form": {"desc": "mm_eval_violation: capacity and precedence excess of every move (exact integers)",
                            "ms_per_batch": viol_ms, "moves_per_s": n / (viol_ms * 1e-3)},
         "differentiated_form": {

@@ -88,6 +88,13 @@ typedef struct {
     double shortfall_pen, excess_pen; /* $/t below / above Q_t */
     double discount_rate;           /* r, per period */
     double lambda;                  /* risk weight of score = mean - lambda*std */
+    /* Optional uncertainty weights sigma(s,t) of Section 5.6 (Eq. 12:
+     * ENPV_{b,s,t} = sigma(s,t) (Revenue - ProcessingCost)): [T][S] host,
+     * period-major, finite, >= 0, or NULL for none.  They scale the processing
+     * margin m((g*price)*recovery - pc) of a block that is ore in scenario s
+     * and mined in period t; the mining cost m*mc and the mill penalties are
+     * not weighted.  See mm_model_create for what changes with them. */
+    const double *sigma;
     void *cuda_stream;              /* cudaStream_t for all work (NULL = default stream) */
 } mm_model_desc;
 
@@ -96,8 +103,15 @@ typedef struct {
  * (g*price)*recovery > proc_cost (strict), and builds the FP32 per-block
  * value rows v[b][s] = ore ? m((g*price)*recovery - pc) - m*mc : -m*mc and the
  * ore bitmask.  The model has no schedule yet.  Synchronising.
- * Errors: MM_ERR_INVALID_ARG (NULL, sizes, non-finite or negative grade, zero
- * mass, bad CSR), MM_ERR_OVERFLOW, MM_ERR_OOM, MM_ERR_CUDA. */
+ * With uncertainty weights (desc->sigma) the rows hold the ore margin
+ * ore ? m((g*price)*recovery - pc) : 0, every NPV is
+ *   NPV_s = sum_t d_t (sigma(s,t) margin_t,s - mc mined_t - pen_t(ore_t,s)),
+ * the evaluator reads a [T+1][T+1][S_pad] FP32 table of the weighted discount
+ * differences sigma(s,b) d_b - sigma(s,a) d_a, mm_search_step runs as the
+ * separate evaluation, top-k and apply launches, and the relaxed objective and
+ * the batched evaluator refuse the model (MM_ERR_INVALID_ARG).
+ * Errors: MM_ERR_INVALID_ARG (NULL, sizes, non-finite or negative grade or
+ * weight, zero mass, bad CSR), MM_ERR_OVERFLOW, MM_ERR_OOM, MM_ERR_CUDA. */
 mm_status mm_model_create(const mm_model_desc *desc, mm_model **out);
 
 /* Free all device state of the model.  NULL is ignored. */

@@ -51,6 +51,7 @@ class MMModelDesc(C.Structure):
         ("mining_cost", C.c_double), ("proc_cost", C.c_double),
         ("shortfall_pen", C.c_double), ("excess_pen", C.c_double),
         ("discount_rate", C.c_double), ("lam", C.c_double),
+        ("sigma", C.c_void_p),
         ("cuda_stream", C.c_void_p),
     ]
 
@@ -156,10 +157,14 @@ class Model:
     def __init__(self, B: int, S: int, T: int, mass, grade, cap, target, price: float, recovery: float,
                  mining_cost: float, proc_cost: float, shortfall_pen: float, excess_pen: float,
                  discount_rate: float, lam: float, grid: Optional[Tuple[int, int, int]] = None,
-                 preds: Optional[Tuple[np.ndarray, np.ndarray]] = None, stream=None):
+                 preds: Optional[Tuple[np.ndarray, np.ndarray]] = None, stream=None, sigma=None):
+        """sigma: optional float64 [T][S] uncertainty weights sigma(s,t) of Eq. 12
+        on the ore processing margin (see mm_model_desc.sigma)."""
         L = lib()
         self._keep = dict(mass=_np(mass, np.uint32), grade=_np(grade, np.float64).reshape(B, S),
                           cap=_np(cap, np.uint64), target=_np(target, np.uint64))
+        if sigma is not None:
+            self._keep["sigma"] = _np(sigma, np.float64).reshape(T, S)
         nx = ny = nz = 0
         pp = pi = None
         if grid is not None:
@@ -173,22 +178,24 @@ class Model:
                                 pi.ctypes.data if pi is not None else None,
                                 k["mass"].ctypes.data, k["grade"].ctypes.data, k["cap"].ctypes.data,
                                 k["target"].ctypes.data, price, recovery, mining_cost, proc_cost, shortfall_pen,
-                                excess_pen, discount_rate, lam, _stream_handle(stream))
+                                excess_pen, discount_rate, lam,
+                                k["sigma"].ctypes.data if sigma is not None else None, _stream_handle(stream))
         h = C.c_void_p()
         _check(L.mm_model_create(C.byref(self.desc), C.byref(h)))
         self.h = h
         self.B, self.S, self.T = B, S, T
+        self.weighted = sigma is not None
         self._keep = None  # the library copied everything it needs
         sp = C.c_int32()
         _check(L.mm_model_info(self.h, None, None, None, C.byref(sp)))
         self.S_pad = sp.value
 
     @classmethod
-    def from_problem(cls, p, preds=None, stream=None) -> "Model":
+    def from_problem(cls, p, preds=None, stream=None, sigma=None) -> "Model":
         """From a workloads.Problem (1-5 grid unless a predecessor CSR is given)."""
         return cls(p.B, p.S, p.T, p.mass, p.grade, p.cap, p.target, p.price, p.recovery, p.mining_cost,
                    p.proc_cost, p.shortfall_pen, p.excess_pen, p.discount_rate, p.lam,
-                   grid=None if preds is not None else (p.nx, p.ny, p.nz), preds=preds, stream=stream)
+                   grid=None if preds is not None else (p.nx, p.ny, p.nz), preds=preds, stream=stream, sigma=sigma)
 
     def close(self):
         if getattr(self, "h", None):

@@ -52,32 +52,33 @@ __device__ __forceinline__ float4 table_consts(int t, int32_t T, const double *d
 }
 
 // Discounted net cash of a period from its accumulators (pure form):
-//   d_t (price*rec*metal - pc*ore_t - mc*mined_t - pen_t(ore_t)).
+//   d_t (sig (price*rec*metal - pc*ore_t) - mc*mined_t - pen_t(ore_t)),
+// sig = the uncertainty weight sigma(s,t) of Eq. 12 on the processing margin
+// (1 without weights; 1 * x == x, so the unweighted result is unchanged).
 __device__ __forceinline__ double contrib_val(int64_t o, double metal, int64_t mined, int64_t target, double disc,
-                                              double pr, double pc, double mc, double a, double e) {
-    double cash = __dsub_rn(__dsub_rn(__dmul_rn(pr, metal), __dmul_rn(pc, (double)o)), __dmul_rn(mc, (double)mined));
+                                              double pr, double pc, double mc, double a, double e, double sig) {
+    double margin = __dsub_rn(__dmul_rn(pr, metal), __dmul_rn(pc, (double)o));
+    double cash = __dsub_rn(__dmul_rn(sig, margin), __dmul_rn(mc, (double)mined));
     return __dmul_rn(disc, __dsub_rn(cash, pen_of(o - target, a, e)));
 }
 
 // contrib_val in FP32 throughout (the FP32 shadow accumulators).
 __device__ __forceinline__ float contrib_val_f32(int64_t o, float metal, int64_t mined, int64_t target, double disc,
-                                                double pr, double pc, double mc, double a, double e) {
+                                                double pr, double pc, double mc, double a, double e, double sig) {
     const float of = (float)o, dev = (float)(o - target);
-    const float cash = (float)pr * metal - (float)pc * of - (float)mc * (float)mined;
+    const float cash = (float)sig * ((float)pr * metal - (float)pc * of) - (float)mc * (float)mined;
     const float pen = dev < 0.0f ? (float)a * -dev : (float)e * dev;
     return (float)disc * (cash - pen);
 }
 
-// Discounted net cash of period t in scenario s:
-//   d_t (price*rec*metal - pc*oreT - mc*minedT - pen_t(oreT)).
+// Discounted net cash of period t in scenario s (contrib_val with the state
+// arrays; sig = nullptr: no uncertainty weights).
 __device__ __forceinline__ double contrib_of(int t, int s, int32_t S, const double *disc, const double *metal,
                                              const int64_t *oreT, const int64_t *minedT, const uint64_t *target,
-                                             double pr, double pc, double mc, double a, double e) {
-    int64_t o = oreT[(int64_t)t * S + s];
-    double cash = __dsub_rn(__dsub_rn(__dmul_rn(pr, metal[(int64_t)t * S + s]), __dmul_rn(pc, (double)o)),
-                            __dmul_rn(mc, (double)minedT[t]));
-    double p = pen_of(o - (int64_t)target[t], a, e);
-    return __dmul_rn(disc[t], __dsub_rn(cash, p));
+                                             double pr, double pc, double mc, double a, double e, const double *sig) {
+    const int64_t i = (int64_t)t * S + s;
+    return contrib_val(oreT[i], metal[i], minedT[t], (int64_t)target[t], disc[t], pr, pc, mc, a, e,
+                       sig ? sig[i] : 1.0);
 }
 
 struct ApplyArgs {
@@ -101,6 +102,7 @@ struct ApplyArgs {
     // per-period metal / contribution and NPV_s running totals kept in FP32
     float *metal32, *contrib32, *npv32;
     const double *disc;
+    const double *sig;   // [T][S] uncertainty weights sigma(s,t) (Eq. 12); nullptr = none
     const uint64_t *cap;
     const uint64_t *target;
     double pr, pc, mc, a, e;
@@ -234,6 +236,7 @@ static __device__ __forceinline__ void apply_core(const ApplyArgs &A, const Move
     }
     uint32_t o1 = 0, o2 = 0;
     double gr1 = 0.0, gr2 = 0.0, M1 = 0.0, M2 = 0.0, C1 = 0.0, C2 = 0.0, my_npv = 0.0, disc1 = 0.0, disc2 = 0.0;
+    double sg1 = 1.0, sg2 = 1.0;
     int64_t O1 = 0, O2 = 0, tgt1 = 0, tgt2 = 0, mined1 = 0, mined2 = 0;
     float4 tc1 = make_float4(0.0f, 0.0f, 0.0f, 0.0f), tc2 = tc1;
     const size_t i1 = (size_t)v.t1 * A.S + s, i2 = (size_t)v.t2 * A.S + s;
@@ -248,11 +251,13 @@ static __device__ __forceinline__ void apply_core(const ApplyArgs &A, const Move
         if (r1) {
             O1 = A.oreT[i1]; M1 = A.metal[i1]; C1 = A.contrib[i1];
             tgt1 = (int64_t)A.target[v.t1]; disc1 = A.disc[v.t1]; mined1 = A.minedT[v.t1];
+            if (A.sig) sg1 = A.sig[i1];
             if (A.uniform) tc1 = A.tabc[v.t1];
         }
         if (r2) {
             O2 = A.oreT[i2]; M2 = A.metal[i2]; C2 = A.contrib[i2];
             tgt2 = (int64_t)A.target[v.t2]; disc2 = A.disc[v.t2]; mined2 = A.minedT[v.t2];
+            if (A.sig) sg2 = A.sig[i2];
             if (A.uniform) tc2 = A.tabc[v.t2];
         }
     }
@@ -328,7 +333,7 @@ static __device__ __forceinline__ void apply_core(const ApplyArgs &A, const Move
         if (r1) {
             const int64_t nO = O1 + om2 - om1;
             const double nM = __dadd_rn(__dsub_rn(M1, g1), g2);
-            const double c = contrib_val(nO, nM, mined1, tgt1, disc1, A.pr, A.pc, A.mc, A.a, A.e);
+            const double c = contrib_val(nO, nM, mined1, tgt1, disc1, A.pr, A.pc, A.mc, A.a, A.e, sg1);
             dnpv = __dadd_rn(dnpv, __dsub_rn(c, C1));
             A.oreT[i1] = nO;
             A.metal[i1] = nM;
@@ -338,7 +343,7 @@ static __device__ __forceinline__ void apply_core(const ApplyArgs &A, const Move
         if (r2) {
             const int64_t nO = O2 + om1 - om2;
             const double nM = __dadd_rn(__dsub_rn(M2, g2), g1);
-            const double c = contrib_val(nO, nM, mined2, tgt2, disc2, A.pr, A.pc, A.mc, A.a, A.e);
+            const double c = contrib_val(nO, nM, mined2, tgt2, disc2, A.pr, A.pc, A.mc, A.a, A.e, sg2);
             dnpv = __dadd_rn(dnpv, __dsub_rn(c, C2));
             A.oreT[i2] = nO;
             A.metal[i2] = nM;
@@ -353,14 +358,14 @@ static __device__ __forceinline__ void apply_core(const ApplyArgs &A, const Move
             const float g1f = (float)g1, g2f = (float)g2;
             if (r1) {
                 const float nM = A.metal32[i1] - g1f + g2f;
-                const float c = contrib_val_f32(O1 + om2 - om1, nM, mined1, tgt1, disc1, A.pr, A.pc, A.mc, A.a, A.e);
+                const float c = contrib_val_f32(O1 + om2 - om1, nM, mined1, tgt1, disc1, A.pr, A.pc, A.mc, A.a, A.e, sg1);
                 d32 += c - A.contrib32[i1];
                 A.metal32[i1] = nM;
                 A.contrib32[i1] = c;
             }
             if (r2) {
                 const float nM = A.metal32[i2] - g2f + g1f;
-                const float c = contrib_val_f32(O2 + om1 - om2, nM, mined2, tgt2, disc2, A.pr, A.pc, A.mc, A.a, A.e);
+                const float c = contrib_val_f32(O2 + om1 - om2, nM, mined2, tgt2, disc2, A.pr, A.pc, A.mc, A.a, A.e, sg2);
                 d32 += c - A.contrib32[i2];
                 A.metal32[i2] = nM;
                 A.contrib32[i2] = c;

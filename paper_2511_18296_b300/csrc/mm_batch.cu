@@ -274,6 +274,7 @@ mm_status mm_batch_create(const mm_chain *chains, int32_t n_chains, int32_t k, i
         if (!m) return set_error(MM_ERR_INVALID_ARG, "chain %d: NULL model", c);
         if (!m->has_schedule) return set_error(MM_ERR_STATE, "chain %d: no schedule installed", c);
         if (!m->uniform_mass) return set_error(MM_ERR_INVALID_ARG, "chain %d: batched evaluation needs equal block masses", c);
+        if (m->sig) return set_error(MM_ERR_INVALID_ARG, "chain %d: batched evaluation does not take uncertainty weights", c);
         if (m->T > kBatchMaxT) return set_error(MM_ERR_INVALID_ARG, "chain %d: T = %d > %d", c, m->T, kBatchMaxT);
         if (ch.n_moves < 0 || ch.n_moves > 0x7fffffffLL)
             return set_error(MM_ERR_INVALID_ARG, "chain %d: move count out of range", c);

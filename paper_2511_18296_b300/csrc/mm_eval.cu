@@ -33,13 +33,18 @@ EvalFn pick_tiled_plain(int team, int qmax, bool delta, bool tsm, bool tma);
 EvalFn pick_tiled_kahan(int team, int qmax, bool delta, bool tsm, bool tma);
 EvalFn pick_fast_plain(int team, int kf, bool tail, bool delta);
 EvalFn pick_fast_kahan(int team, int kf, bool tail, bool delta);
+EvalFn pick_fast_sigma(int team, int kf, bool tail, bool delta);
 EvalFn pick_step(int team, bool fast, int kf, bool tail, int qmax, bool tsm);
 ApplyArgs apply_args(mm_model *m);
 
-// General evaluator (unequal block masses): one warp per move, one lane per
-// scenario, penalty change from the exact integer ore tonnages:
+// General evaluator (unequal block masses, and every weighted model the fast
+// form does not take): one warp per move, one lane per scenario, penalty
+// change from the exact integer ore tonnages:
 //   dO = m2*o2 - m1*o1 enters period t1 and leaves period t2;
 //   delta_s = (v1 - v2)(d_t2 - d_t1) + d_t1 (pen(x1) - pen(x1 + dO)) + d_t2 (pen(x2) - pen(x2 - dO)).
+// With uncertainty weights (Eq. 12) v is the ore margin, d_t2 - d_t1 becomes
+// the scenario's weighted difference dwt[t1][t2][s], and the mining cost adds
+// -mc (m1 - m2)(d_t2 - d_t1), formed in FP64 per move.
 __device__ __forceinline__ double pen_diff_g(int64_t x0, int64_t x1, double a, double e) {
     int64_t s0 = x0 < 0 ? -x0 : 0, s1 = x1 < 0 ? -x1 : 0;
     int64_t e0 = x0 > 0 ? x0 : 0, e1 = x1 > 0 ? x1 : 0;
@@ -61,6 +66,11 @@ __global__ void __launch_bounds__(256) k_eval_general(EvalArgs A) {
         float sum = 0.0f;
         float dl[kMaxS / 32];
         const float dd = work ? __ldg(A.ddt + v.t1 * T1 + v.t2) : 0.0f;
+        const bool sig = A.dwt != nullptr;
+        const float *dwrow = sig ? A.dwt + ((size_t)v.t1 * T1 + v.t2) * A.S_pad : nullptr;
+        float cmv = 0.0f;
+        if (sig && work)
+            cmv = (float)(-A.mc * ((double)v.m1 - (v.swap ? (double)v.m2 : 0.0)) * (A.disc[v.t2] - A.disc[v.t1]));
 #pragma unroll 4
         for (int k = 0; k < kMaxS / 32; k++) {
             const int s = lane + 32 * k;
@@ -88,7 +98,7 @@ __global__ void __launch_bounds__(256) k_eval_general(EvalArgs A) {
                         p += A.disc[v.t2] * pen_diff_g(x2, x2 - dO, A.a, A.e);
                     }
                 }
-                x = fmaf(v1 - v2, dd, (float)p);
+                x = sig ? fmaf(v1 - v2, __ldg(dwrow + s), (float)p + cmv) : fmaf(v1 - v2, dd, (float)p);
             }
             dl[k] = x;
             sum += x;
@@ -160,7 +170,7 @@ EvalArgs eval_args(mm_model *m, const mm_move *moves, int64_t n, float *score, u
     A.score = score; A.feas = feas; A.mean = mean; A.delta = delta;
     A.val = m->val; A.blk = m->blk; A.mass = m->mass;
     A.tab = m->tab; A.ctab = m->ctab; A.ddt = m->ddt; A.minedT = m->minedT; A.cap = m->cap;
-    A.oreT = m->oreT; A.target = m->target; A.disc = m->disc;
+    A.oreT = m->oreT; A.target = m->target; A.disc = m->disc; A.dwt = m->dwt;
     A.status = m->status;
     A.tp.B = m->B; A.tp.T = m->T; A.tp.nx = m->nx; A.tp.ny = m->ny; A.tp.nz = m->nz;
     A.tp.pred_ptr = m->pred_ptr; A.tp.pred_idx = m->pred_idx; A.tp.succ_ptr = m->succ_ptr; A.tp.succ_idx = m->succ_idx;
@@ -170,7 +180,8 @@ EvalArgs eval_args(mm_model *m, const mm_move *moves, int64_t n, float *score, u
     A.prefetch = m->prefetch < 0 ? kDefaultPrefetch : m->prefetch;
 
     A.lambda = (float)m->lambda;
-    A.a = m->shortfall_pen; A.e = m->excess_pen;
+    A.a = m->shortfall_pen; A.e = m->excess_pen; A.mc = m->mining_cost;
+    A.mcm = (float)(m->mining_cost * (double)m->m_uniform);
     A.qpl = 0;
     A.tail = StepTail{};
     A.tail.L = step_lists(m, 1);
@@ -178,6 +189,25 @@ EvalArgs eval_args(mm_model *m, const mm_move *moves, int64_t n, float *score, u
     A.tail.status = m->status;
     A.tail.moves = A.moves;
     return A;
+}
+
+// Resident CTAs per SM of an evaluator, cached so that calls captured into a
+// CUDA graph make no occupancy query.
+static mm_status eval_occupancy(EvalFn fn, size_t smem, int *per_sm) {
+    static std::mutex mu;
+    static std::map<std::pair<const void *, size_t>, int> cache;
+    std::lock_guard<std::mutex> lock(mu);
+    auto key = std::make_pair((const void *)fn, smem);
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+        *per_sm = it->second;
+        return MM_OK;
+    }
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, fn, kEvalThreads, smem);
+    if (e != cudaSuccess) return cuda_status(e, "occupancy query");
+    if (*per_sm < 1) *per_sm = 1;
+    cache[key] = *per_sm;
+    return MM_OK;
 }
 
 mm_status eval_launch(mm_model *m, const mm_move *moves, int64_t n, float *score, uint8_t *feas, float *mean,
@@ -194,7 +224,31 @@ mm_status eval_launch(mm_model *m, const mm_move *moves, int64_t n, float *score
     }
     const bool kahan = (options & MM_EVAL_KAHAN) != 0;
     const bool want_delta = delta != nullptr;
-    if (!m->uniform_mass) {
+    if (m->sig && step) return set_error(MM_ERR_INVALID_ARG, "the fused step does not take uncertainty weights");
+    if (m->sig && m->uniform_mass && !kahan && !(options & MM_EVAL_GENERIC) && m->ctab && m->S % 4 == 0) {
+        // weighted fast form (direct loads)
+        if (team <= 0) team = default_team(m->S);
+        const int nq = (m->S + 3) / 4, kf = nq / team;
+        EvalFn fn = (kf >= 1 && kf <= 4) ? pick_fast_sigma(team, kf, nq % team != 0, want_delta) : nullptr;
+        if (fn) {
+            const int T1 = m->T + 1;
+            const size_t smem = (((size_t)T1 * T1 * sizeof(float) + 15) & ~(size_t)15) + 2 * (size_t)T1 * sizeof(int64_t);
+            int per_sm = ctas_per_sm;
+            if (per_sm <= 0) {
+                const mm_status os = eval_occupancy(fn, smem, &per_sm);
+                if (os != MM_OK) return os;
+            }
+            A.qpl = (nq + team - 1) / team;
+            const int64_t chunks = (n + kChunk - 1) / kChunk;
+            int64_t blocks = (chunks + kEvalThreads / 32 - 1) / (kEvalThreads / 32);
+            const int64_t grid_cap = (int64_t)m->num_sms * per_sm;
+            if (blocks > grid_cap) blocks = grid_cap;
+            if (blocks < 1) blocks = 1;
+            fn<<<(unsigned)blocks, kEvalThreads, smem, m->stream>>>(A);
+            return check_launch("k_eval_tiled");
+        }
+    }
+    if (!m->uniform_mass || m->sig) {
         EvalFn fn = want_delta ? k_eval_general<true> : k_eval_general<false>;
         int64_t blocks = (n + 7) / 8;
         int64_t cap_blocks = (int64_t)m->num_sms * 8;
@@ -253,20 +307,8 @@ mm_status eval_launch(mm_model *m, const mm_move *moves, int64_t n, float *score
     }
     int per_sm = ctas_per_sm;
     if (per_sm <= 0) {
-        // cached, so that calls captured into a CUDA graph make no occupancy query
-        static std::mutex mu;
-        static std::map<std::pair<const void *, size_t>, int> cache;
-        std::lock_guard<std::mutex> lock(mu);
-        auto key = std::make_pair((const void *)fn, smem);
-        auto it = cache.find(key);
-        if (it != cache.end()) {
-            per_sm = it->second;
-        } else {
-            cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kEvalThreads, smem);
-            if (e != cudaSuccess) return cuda_status(e, "occupancy query");
-            if (per_sm < 1) per_sm = 1;
-            cache[key] = per_sm;
-        }
+        const mm_status os = eval_occupancy(fn, smem, &per_sm);
+        if (os != MM_OK) return os;
     }
     const int64_t chunks = (n + kChunk - 1) / kChunk;
     int64_t blocks = (chunks + kEvalThreads / 32 - 1) / (kEvalThreads / 32);

@@ -78,6 +78,7 @@ struct EvalArgs {
     const int64_t *oreT;
     const uint64_t *target;
     const double *disc;
+    const float *dwt;      // [T+1][T+1][S_pad] sigma(s,b) d_b - sigma(s,a) d_a with uncertainty weights, else nullptr
     uint32_t *status;
     Topo tp;
     int32_t S, S_pad, W, T, R, ore_off;
@@ -86,7 +87,8 @@ struct EvalArgs {
     int32_t nstage;        // bulk-copy pipeline depth per warp (TMA path)
     int32_t prefetch;      // direct-load path: batches whose rows are prefetched into L1 ahead
     float lambda;
-    double a, e;
+    float mcm;             // mining cost of one block, mc * m (uniform mass; weighted form)
+    double a, e, mc;
     StepTail tail;         // fused search step (TOPK kernels only)
 };
 
@@ -351,10 +353,15 @@ __device__ __forceinline__ uint64_t f2_sub(uint64_t a, uint64_t b) {
 // a real quad, offsets are compile-time immediates from per-lane bases, no
 // masking), then, if TAIL, one iteration in which only the first
 // NQ - KF * TEAM lanes hold a quad.  d[KF] holds the tail quad.
-template <int TEAM, int KF, bool TAIL, bool SWAP, bool KAHAN>
+// SIG (uncertainty weights, Eq. 12): the rows hold ore margins, the value
+// term takes the weighted discount difference of the scenario from the
+// period-pair row dwt[t1][t2] instead of the scalar dd, and a shift adds the
+// mining-cost change cm (a swap of equal masses has none).
+template <int TEAM, int KF, bool TAIL, bool SWAP, bool KAHAN, bool SIG = false>
 __device__ __forceinline__ void team_eval_fast(const EvalArgs &A, int tl, const float *row1,
-                                               const float *row2, uint32_t t1, uint32_t t2, float dd, int ntail,
-                                               float invS, float (&d)[KF + 1][4], float &mu, float &sd) {
+                                               const float *row2, uint32_t t1, uint32_t t2, float dd, float cm,
+                                               int ntail, float invS, float (&d)[KF + 1][4], float &mu,
+                                               float &sd) {
     const int S_pad = A.S_pad, ore_off = A.ore_off;
     const uint32_t T1 = (uint32_t)A.T + 1u;
     const float4 *r1 = reinterpret_cast<const float4 *>(row1) + tl;
@@ -364,8 +371,9 @@ __device__ __forceinline__ void team_eval_fast(const EvalArgs &A, int tl, const 
     // period-pair rows: p12 = Pout[t1] + Pin[t2] (ore leaving t1 for t2), p21 the reverse
     const float4 *p12 = reinterpret_cast<const float4 *>(A.ctab + ((size_t)t1 * T1 + t2) * S_pad) + tl;
     const float4 *p21 = reinterpret_cast<const float4 *>(A.ctab + ((size_t)t2 * T1 + t1) * S_pad) + tl;
+    const float4 *dw12 = SIG ? reinterpret_cast<const float4 *>(A.dwt + ((size_t)t1 * T1 + t2) * S_pad) + tl : nullptr;
     float sum = 0.0f, csum = 0.0f;
-    const uint64_t dd2 = f2_pack(dd, dd);
+    const uint64_t dd2 = f2_pack(dd, dd), cm2 = f2_pack(cm, cm);
     // Where a lane's ore words are the first four of the row at known
     // positions (4-lane teams: word k / 2 in iteration k; 8-lane teams: word k,
     // at most four iterations), one 16-byte load per row fetches them all (the
@@ -387,6 +395,9 @@ __device__ __forceinline__ void team_eval_fast(const EvalArgs &A, int tl, const 
         const uint32_t sh = (uint32_t)(q & 7) * 4u;
         const float4 a = __ldg(r1 + k * TEAM);
         const float4 pa = __ldg(p12 + k * TEAM);
+        float4 w = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (SIG) w = __ldg(dw12 + k * TEAM);
+        const uint64_t dlo = SIG ? f2_pack(w.x, w.y) : dd2, dhi = SIG ? f2_pack(w.z, w.w) : dd2;
         if (SWAP) {
             const float4 b = __ldg(r2 + k * TEAM);
             const uint32_t n1 = (word(ow1, w1, k, wi) >> sh) & 0xfu;
@@ -395,19 +406,23 @@ __device__ __forceinline__ void team_eval_fast(const EvalArgs &A, int tl, const 
             const float4 m2 = nib_mask(n2 & ~n1);
             const float4 pb = __ldg(p21 + k * TEAM);
             // x = (a - b) dd + (m2 pb + m1 pa), scenario by scenario, in pairs
-            const uint64_t lo = f2_fma(f2_sub(f2_pack(a.x, a.y), f2_pack(b.x, b.y)), dd2,
+            const uint64_t lo = f2_fma(f2_sub(f2_pack(a.x, a.y), f2_pack(b.x, b.y)), dlo,
                                        f2_fma(f2_pack(m2.x, m2.y), f2_pack(pb.x, pb.y),
                                               f2_mul(f2_pack(m1.x, m1.y), f2_pack(pa.x, pa.y))));
-            const uint64_t hi = f2_fma(f2_sub(f2_pack(a.z, a.w), f2_pack(b.z, b.w)), dd2,
+            const uint64_t hi = f2_fma(f2_sub(f2_pack(a.z, a.w), f2_pack(b.z, b.w)), dhi,
                                        f2_fma(f2_pack(m2.z, m2.w), f2_pack(pb.z, pb.w),
                                               f2_mul(f2_pack(m1.z, m1.w), f2_pack(pa.z, pa.w))));
             f2_unpack(lo, x[0], x[1]);
             f2_unpack(hi, x[2], x[3]);
         } else {
             const float4 m1 = nib_mask((word(ow1, w1, k, wi) >> sh) & 0xfu);
-            // x = a dd + m1 pa
-            const uint64_t lo = f2_fma(f2_pack(a.x, a.y), dd2, f2_mul(f2_pack(m1.x, m1.y), f2_pack(pa.x, pa.y)));
-            const uint64_t hi = f2_fma(f2_pack(a.z, a.w), dd2, f2_mul(f2_pack(m1.z, m1.w), f2_pack(pa.z, pa.w)));
+            // x = a dd + m1 pa  (SIG: a dw + (m1 pa + cm))
+            const uint64_t plo = SIG ? f2_fma(f2_pack(m1.x, m1.y), f2_pack(pa.x, pa.y), cm2)
+                                     : f2_mul(f2_pack(m1.x, m1.y), f2_pack(pa.x, pa.y));
+            const uint64_t phi = SIG ? f2_fma(f2_pack(m1.z, m1.w), f2_pack(pa.z, pa.w), cm2)
+                                     : f2_mul(f2_pack(m1.z, m1.w), f2_pack(pa.z, pa.w));
+            const uint64_t lo = f2_fma(f2_pack(a.x, a.y), dlo, plo);
+            const uint64_t hi = f2_fma(f2_pack(a.z, a.w), dhi, phi);
             f2_unpack(lo, x[0], x[1]);
             f2_unpack(hi, x[2], x[3]);
         }
@@ -748,7 +763,7 @@ struct EvalShared {
 // TEAM lanes per move, coalesced stores) and, if TOPK, inserts every feasible
 // move's key into its register list wtk.  tab, s_dd, s_mined and s_cap are
 // the CTA's staged tables.
-template <int TEAM, int QMAX, bool KAHAN, bool DELTA, int KF, bool TAIL, bool TOPK>
+template <int TEAM, int QMAX, bool KAHAN, bool DELTA, int KF, bool TAIL, bool TOPK, bool SIG = false>
 __device__ __forceinline__ void eval_warp_range(const EvalArgs &A, EvalShared &sh, const float *tab, const float *s_dd,
                                                 const int64_t *s_mined, const uint64_t *s_cap, int64_t r0, int64_t r1,
                                                 uint64_t &wtk) {
@@ -844,13 +859,15 @@ __device__ __forceinline__ void eval_warp_range(const EvalArgs &A, EvalShared &s
                 const int ntail = NQ - KF * TEAM;
                 float d[KF + 1][4];
                 if (!sw)
-                    team_eval_fast<TEAM, KF, TAIL, false, KAHAN>(A, tl, row1, row2, t1, t2, dd, ntail, invS,
-                                                                 d, mu, sd);
+                    team_eval_fast<TEAM, KF, TAIL, false, KAHAN, SIG>(A, tl, row1, row2, t1, t2, dd,
+                                                                      SIG ? -A.mcm * dd : 0.0f, ntail, invS, d, mu,
+                                                                      sd);
                 else
-                    team_eval_fast<TEAM, KF, TAIL, true, KAHAN>(A, tl, row1, row2, t1, t2, dd, ntail, invS, d,
-                                                                mu, sd);
+                    team_eval_fast<TEAM, KF, TAIL, true, KAHAN, SIG>(A, tl, row1, row2, t1, t2, dd, 0.0f, ntail,
+                                                                     invS, d, mu, sd);
                 if (act && DELTA) write_deltas_fast<TEAM, KF>(A, c0 + slot, tl, ntail, d);
             } else {
+                static_assert(!SIG, "the weighted form is the fast form only");
                 float d[QMAX][4];
                 if (!sw)
                     team_eval<TEAM, QMAX, false, KAHAN, false>(A, tab, tl, act, row1, row2, t1, t2, dd, NQ,
@@ -896,7 +913,8 @@ __device__ __forceinline__ void eval_warp_range(const EvalArgs &A, EvalShared &s
     }
 }
 
-template <int TEAM, int QMAX, bool KAHAN, bool DELTA, bool TSM, int KF = 0, bool TAIL = false, bool TOPK = false>
+template <int TEAM, int QMAX, bool KAHAN, bool DELTA, bool TSM, int KF = 0, bool TAIL = false, bool TOPK = false,
+          bool SIG = false>
 __global__ void __launch_bounds__(kEvalThreads, MM_EVAL_MINB) k_eval_tiled(EvalArgs A) {
     constexpr int NW = kEvalThreads / 32;   // warps per CTA
     extern __shared__ __align__(128) unsigned char smem[];
@@ -931,7 +949,7 @@ __global__ void __launch_bounds__(kEvalThreads, MM_EVAL_MINB) k_eval_tiled(EvalA
     const int64_t gw = (int64_t)blockIdx.x * NW + warp;
     const int64_t r0 = gw * A.n / nwarps, r1 = (gw + 1) * A.n / nwarps;
     uint64_t wtk = 0;  // this warp's best 32 candidate keys (TOPK)
-    eval_warp_range<TEAM, QMAX, KAHAN, DELTA, KF, TAIL, TOPK>(A, sh, tab, s_dd, s_mined, s_cap, r0, r1, wtk);
+    eval_warp_range<TEAM, QMAX, KAHAN, DELTA, KF, TAIL, TOPK, SIG>(A, sh, tab, s_dd, s_mined, s_cap, r0, r1, wtk);
     if constexpr (TOPK) step_reduce(A.tail, wtk, A.tail.do_apply ? sh.best : nullptr);
 }
 

@@ -79,7 +79,8 @@ struct mm_model {
     // device state
     uint32_t *mass = nullptr;    // [B]
     double *grade = nullptr;     // [B][S]
-    float *val = nullptr;        // [B+1][R] rows: S FP32 values, 0 up to ore_off, W ore words, 0 (row B all 0)
+    float *val = nullptr;        // [B+1][R] rows: S FP32 values, 0 up to ore_off, W ore words, 0 (row B all 0);
+                                 // with weights sigma the values are the ore processing margins (0 for waste)
     uint32_t *blk = nullptr;     // [B] packed period / lo / hi
     int32_t *pred_ptr = nullptr, *pred_idx = nullptr;  // CSR (device) when nx == 0
     int32_t *succ_ptr = nullptr, *succ_idx = nullptr;
@@ -95,6 +96,8 @@ struct mm_model {
     float *ctab = nullptr;       // [T+1][T+1][S_pad] Pout[a] + Pin[b] (FP32 sum); T <= kCtabMaxT only
     float *ddt = nullptr;        // [(T+1)*(T+1)]    d_{t'} - d_t  (index t*(T+1)+t')
     double *disc = nullptr;      // [T+1]
+    double *sig = nullptr;       // [T][S] uncertainty weights sigma(s,t) of Eq. 12 (nullptr: none)
+    float *dwt = nullptr;        // [T+1][T+1][S_pad] sigma(s,b) d_b - sigma(s,a) d_a (FP64, rounded once), with weights
     uint64_t *cap = nullptr;     // [T+1]  cap[T] = max
     uint64_t *target = nullptr;  // [T+1]
     uint32_t *status = nullptr;  // sticky bits

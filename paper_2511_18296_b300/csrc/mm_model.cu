@@ -80,9 +80,12 @@ Topo topo_of_model(const mm_model *m) { return topo_of(m); }
 // Ore/waste and FP32 value rows.  One thread per (block, ore word): 32
 // scenarios.  FP64 with explicit round-to-nearest operations in the order
 // ((g*price)*recovery) > proc_cost; value = m*(rev - pc) - m*mc or -(m*mc).
+// margin_only (uncertainty weights present): the row holds the processing
+// margin m*(rev - pc) of an ore scenario and 0 for waste, the part that
+// sigma(s,t) scales (Eq. 12); the mining cost is added per move.
 __global__ void k_classify(const double *__restrict__ grade, const uint32_t *__restrict__ mass, int32_t B, int32_t S,
                            int32_t R, int32_t ore_off, int32_t W, double price, double recovery, double pc,
-                           double mc, float *__restrict__ val) {
+                           double mc, int margin_only, float *__restrict__ val) {
     int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (gid >= (int64_t)B * W) return;
     int32_t b = (int32_t)(gid / W), w = (int32_t)(gid % W);
@@ -95,7 +98,9 @@ __global__ void k_classify(const double *__restrict__ grade, const uint32_t *__r
         double g = grade[(int64_t)b * S + s];
         double rev = __dmul_rn(__dmul_rn(g, price), recovery);
         bool o = rev > pc;
-        double vv = o ? __dsub_rn(__dmul_rn(m, __dsub_rn(rev, pc)), __dmul_rn(m, mc)) : -__dmul_rn(m, mc);
+        double vv;
+        if (margin_only) vv = o ? __dmul_rn(m, __dsub_rn(rev, pc)) : 0.0;
+        else vv = o ? __dsub_rn(__dmul_rn(m, __dsub_rn(rev, pc)), __dmul_rn(m, mc)) : -__dmul_rn(m, mc);
         row[s] = __double2float_rn(vv);
         bits |= (o ? 1u : 0u) << j;
     }
@@ -188,12 +193,12 @@ __global__ void k_ctab(int32_t S_pad, int32_t T, const float *__restrict__ tab, 
 __global__ void k_npv(int32_t S, int32_t T, const double *__restrict__ disc, const double *__restrict__ metal,
                       const int64_t *__restrict__ oreT, const int64_t *__restrict__ minedT,
                       const uint64_t *__restrict__ target, double pr, double pc, double mc, double a, double e,
-                      double *__restrict__ contrib, double *__restrict__ npv) {
+                      const double *__restrict__ sig, double *__restrict__ contrib, double *__restrict__ npv) {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= S) return;
     double acc = 0.0;
     for (int t = 0; t < T; t++) {
-        double c = contrib_of(t, s, S, disc, metal, oreT, minedT, target, pr, pc, mc, a, e);
+        double c = contrib_of(t, s, S, disc, metal, oreT, minedT, target, pr, pc, mc, a, e, sig);
         contrib[(int64_t)t * S + s] = c;
         acc = __dadd_rn(acc, c);
     }
@@ -206,7 +211,7 @@ __global__ void k_npv(int32_t S, int32_t T, const double *__restrict__ disc, con
 __global__ void k_shadow_init(int32_t S, int32_t T, const double *__restrict__ disc, const double *__restrict__ metal,
                               const int64_t *__restrict__ oreT, const int64_t *__restrict__ minedT,
                               const uint64_t *__restrict__ target, double pr, double pc, double mc, double a, double e,
-                              float *__restrict__ shadow) {
+                              const double *__restrict__ sig, float *__restrict__ shadow) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= S) return;
     float *metal32 = shadow, *contrib32 = shadow + (size_t)T * S, *npv32 = contrib32 + (size_t)T * S;
@@ -214,7 +219,8 @@ __global__ void k_shadow_init(int32_t S, int32_t T, const double *__restrict__ d
     for (int t = 0; t < T; t++) {
         const size_t i = (size_t)t * S + s;
         const float mf = (float)metal[i];
-        const float c = contrib_val_f32(oreT[i], mf, minedT[t], (int64_t)target[t], disc[t], pr, pc, mc, a, e);
+        const float c = contrib_val_f32(oreT[i], mf, minedT[t], (int64_t)target[t], disc[t], pr, pc, mc, a, e,
+                                        sig ? sig[i] : 1.0);
         metal32[i] = mf;
         contrib32[i] = c;
         acc += c;
@@ -227,7 +233,7 @@ static mm_status shadow_init(mm_model *m) {
     k_shadow_init<<<(m->S + 127) / 128, 128, 0, m->stream>>>(m->S, m->T, m->disc, m->metal, m->oreT, m->minedT,
                                                              m->target, m->price * m->recovery, m->proc_cost,
                                                              m->mining_cost, m->shortfall_pen, m->excess_pen,
-                                                             m->shadow32);
+                                                             m->sig, m->shadow32);
     return check_launch("k_shadow_init");
 }
 
@@ -318,7 +324,7 @@ ApplyArgs apply_args(mm_model *m) {
     A.tab = m->tab;
     A.tabc = reinterpret_cast<const float4 *>(m->tabc);
     A.ctab = m->ctab;
-    A.disc = m->disc; A.cap = m->cap; A.target = m->target;
+    A.disc = m->disc; A.sig = m->sig; A.cap = m->cap; A.target = m->target;
     A.pr = m->price * m->recovery; A.pc = m->proc_cost; A.mc = m->mining_cost;
     A.a = m->shortfall_pen; A.e = m->excess_pen;
     A.res = m->apply_res;
@@ -366,6 +372,7 @@ void mm_model_destroy(mm_model *m) {
     cudaFree(m->minedT); cudaFree(m->oreT); cudaFree(m->metal); cudaFree(m->npv); cudaFree(m->contrib);
     cudaFree(m->tab);
     cudaFree(m->ctab);
+    cudaFree(m->sig); cudaFree(m->dwt);
     cudaFree(m->ddt); cudaFree(m->disc); cudaFree(m->cap); cudaFree(m->target); cudaFree(m->status);
     cudaFree(m->apply_res);
     cudaFree(m->step_cta);
@@ -416,6 +423,10 @@ mm_status mm_model_create(const mm_model_desc *d, mm_model **out) {
     for (int64_t i = 0; i < (int64_t)B * S; i++)
         if (!std::isfinite(d->grade[i]) || d->grade[i] < 0.0)
             return set_error(MM_ERR_INVALID_ARG, "grade[%lld] is negative or not finite", (long long)i);
+    if (d->sigma)
+        for (int64_t i = 0; i < (int64_t)T * S; i++)
+            if (!std::isfinite(d->sigma[i]) || d->sigma[i] < 0.0)
+                return set_error(MM_ERR_INVALID_ARG, "sigma[%lld] is negative or not finite", (long long)i);
     std::vector<int32_t> sptr, sidx;
     if (!grid) {
         if (d->pred_ptr[0] != 0) return set_error(MM_ERR_INVALID_ARG, "pred_ptr[0] must be 0");
@@ -480,6 +491,10 @@ mm_status mm_model_create(const mm_model_desc *d, mm_model **out) {
     ALLOC(tab, (int64_t)2 * (T + 1) * m->S_pad);
     if (T <= kCtabMaxT && m->uniform_mass) ALLOC(ctab, (int64_t)(T + 1) * (T + 1) * m->S_pad);
     ALLOC(ddt, (int64_t)(T + 1) * (T + 1));
+    if (d->sigma) {
+        ALLOC(sig, (int64_t)T * S);
+        ALLOC(dwt, (int64_t)(T + 1) * (T + 1) * m->S_pad);
+    }
     ALLOC(disc, T + 1);
     ALLOC(cap, T + 1);
     ALLOC(target, T + 1);
@@ -530,6 +545,22 @@ mm_status mm_model_create(const mm_model_desc *d, mm_model **out) {
     TRY(cudaMemcpyAsync(m->target, tgtx.data(), sizeof(uint64_t) * (T + 1), cudaMemcpyHostToDevice, s), "copy target");
     TRY(cudaMemcpyAsync(m->disc, m->h_disc.data(), sizeof(double) * (T + 1), cudaMemcpyHostToDevice, s), "copy disc");
     TRY(cudaMemcpyAsync(m->ddt, ddt.data(), sizeof(float) * ddt.size(), cudaMemcpyHostToDevice, s), "copy ddt");
+    std::vector<float> dwt;
+    if (d->sigma) {
+        // weighted discount W[t][s] = sigma(s,t) d_t (W[T] = 0, unmined) and
+        // its period-pair differences, each formed in FP64 and rounded once
+        const int T1 = T + 1, Sp = m->S_pad;
+        std::vector<double> w((size_t)T1 * S, 0.0);
+        for (int t = 0; t < T; t++)
+            for (int sc = 0; sc < S; sc++) w[(size_t)t * S + sc] = d->sigma[(size_t)t * S + sc] * m->h_disc[t];
+        dwt.assign((size_t)T1 * T1 * Sp, 0.0f);
+        for (int a = 0; a <= T; a++)
+            for (int b = 0; b <= T; b++)
+                for (int sc = 0; sc < S; sc++)
+                    dwt[((size_t)a * T1 + b) * Sp + sc] = (float)(w[(size_t)b * S + sc] - w[(size_t)a * S + sc]);
+        TRY(cudaMemcpyAsync(m->sig, d->sigma, sizeof(double) * (size_t)T * S, cudaMemcpyHostToDevice, s), "copy sigma");
+        TRY(cudaMemcpyAsync(m->dwt, dwt.data(), sizeof(float) * dwt.size(), cudaMemcpyHostToDevice, s), "copy dwt");
+    }
     TRY(cudaMemsetAsync(m->status, 0, sizeof(uint32_t), s), "clear status");
     TRY(cudaMemsetAsync(m->val, 0, sizeof(float) * (size_t)(B + 1) * m->R, s), "clear rows");
     TRY(cudaMemsetAsync(m->oreT, 0, sizeof(int64_t) * (size_t)(T + 1) * S, s), "clear oreT");
@@ -548,7 +579,7 @@ mm_status mm_model_create(const mm_model_desc *d, mm_model **out) {
     int64_t nthreads = (int64_t)B * m->W;
     k_classify<<<(unsigned)((nthreads + 255) / 256), 256, 0, s>>>(m->grade, m->mass, B, S, m->R, m->ore_off, m->W,
                                                                   m->price, m->recovery, m->proc_cost, m->mining_cost,
-                                                                  m->val);
+                                                                  m->sig ? 1 : 0, m->val);
     mm_status ls = check_launch("k_classify");
     if (ls != MM_OK) return fail(ls);
     TRY(cudaStreamSynchronize(s), "synchronize after create");
@@ -612,7 +643,7 @@ mm_status mm_schedule_set(mm_model *m, const uint8_t *period, int *base_feasible
     if ((st = rebuild_tables(m)) != MM_OK) return done(st);
     k_npv<<<(S + 127) / 128, 128, 0, s>>>(S, T, m->disc, m->metal, m->oreT, m->minedT, m->target,
                                            m->price * m->recovery, m->proc_cost, m->mining_cost, m->shortfall_pen,
-                                           m->excess_pen, m->contrib, m->npv);
+                                           m->excess_pen, m->sig, m->contrib, m->npv);
     if ((st = check_launch("k_npv")) != MM_OK) return done(st);
     if ((st = shadow_init(m)) != MM_OK) return done(st);
     // base feasibility: arcs (device) + capacity (host, from minedT)

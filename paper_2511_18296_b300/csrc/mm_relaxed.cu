@@ -490,6 +490,7 @@ static RelaxEcon relax_econ(const mm_model *m, double beta, double m_ref) {
 
 static mm_status relax_check(mm_model *m, const float *x, double beta, double m_ref) {
     if (!m) return set_error(MM_ERR_INVALID_ARG, "NULL model");
+    if (m->sig) return set_error(MM_ERR_INVALID_ARG, "the relaxed objective does not take uncertainty weights");
     if (!x) return set_error(MM_ERR_INVALID_ARG, "NULL x");
     if (!(beta > 0.0) || !(m_ref > 0.0) || !std::isfinite(beta) || !std::isfinite(m_ref))
         return set_error(MM_ERR_INVALID_ARG, "beta and m_ref must be positive and finite");

@@ -121,6 +121,19 @@ static mm_status step_check(mm_model *m, const mm_move *moves, int64_t n, float 
     return MM_OK;
 }
 
+// The timing hook: the caller's event between a step's evaluation and apply
+// (an external node while the stream is being captured).
+static mm_status record_step_event(mm_model *m) {
+    if (!m->step_event) return MM_OK;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    MM_CUDA_TRY(cudaStreamIsCapturing(m->stream, &cs), "query stream capture");
+    cudaEvent_t ev = static_cast<cudaEvent_t>(m->step_event);
+    MM_CUDA_TRY(cs == cudaStreamCaptureStatusActive ? cudaEventRecordWithFlags(ev, m->stream, cudaEventRecordExternal)
+                                                    : cudaEventRecord(ev, m->stream),
+                "record the step event");
+    return MM_OK;
+}
+
 extern "C" mm_status mm_search_step(mm_model *m, const mm_move *moves, int64_t n, int32_t k, int32_t apply,
                                     float *score, uint8_t *feas, int32_t *idx, float *top, int32_t *count) {
     mm_status st = step_check(m, moves, n, score, feas);
@@ -133,20 +146,22 @@ extern "C" mm_status mm_search_step(mm_model *m, const mm_move *moves, int64_t n
         MM_CUDA_TRY(cudaMemsetAsync(count, 0, sizeof(int32_t), m->stream), "clear count");
         return apply ? mm_apply_best(m, moves, 0, idx, count) : MM_OK;
     }
+    if (m->sig) {
+        // uncertainty weights: the separate evaluation, top-k and apply launches
+        st = eval_launch(m, moves, n, score, feas, nullptr, nullptr, MM_EVAL_PLAIN, m->team, m->ctas_per_sm, 0,
+                         nullptr);
+        if (st == MM_OK) st = mm_topk(m, score, feas, n, k, idx, top, count);
+        if (st == MM_OK) st = record_step_event(m);
+        return (st == MM_OK && apply) ? mm_apply_best(m, moves, n, idx, count) : st;
+    }
     // the final CTA of the evaluation launch applies the best move itself
     // when a CTA has a thread per scenario; otherwise a one-CTA launch follows
     const bool in_launch = apply && m->S <= kEvalThreads;
     StepOut so{k, in_launch ? 1 : 0, idx, top, count, 0};
     st = eval_launch(m, moves, n, score, feas, nullptr, nullptr, MM_EVAL_PLAIN, m->team, m->ctas_per_sm, 0, &so);
     if (st != MM_OK) return st;
-    if (m->step_event) {
-        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-        MM_CUDA_TRY(cudaStreamIsCapturing(m->stream, &cs), "query stream capture");
-        cudaEvent_t ev = static_cast<cudaEvent_t>(m->step_event);
-        MM_CUDA_TRY(cs == cudaStreamCaptureStatusActive ? cudaEventRecordWithFlags(ev, m->stream, cudaEventRecordExternal)
-                                                        : cudaEventRecord(ev, m->stream),
-                    "record the step event");
-    }
+    st = record_step_event(m);
+    if (st != MM_OK) return st;
     return (apply && !in_launch) ? mm_apply_best(m, moves, n, idx, count) : MM_OK;
 }
 

@@ -55,3 +55,25 @@ def test_error_path_without_model():
     # NULL model pointer: argument checks run on the host and return an error code
     assert L.mm_eval_moves(None, None, 0, None, None, None) == 1
     assert L.mm_last_error().decode() != ""
+
+
+@pytest.mark.parametrize("struct,cls", [("mm_model_desc", "MMModelDesc"), ("mm_move", "MMMove")])
+def test_binding_struct_layout_matches_header(struct, cls, tmp_path):
+    """The ctypes structures have the header's field offsets and size (a C
+    program built against include/mm.h prints them)."""
+    import subprocess
+    import paper_2511_18296_b300 as mm
+    C = getattr(mm, cls)
+    names = [f[0] for f in C._fields_]
+    cnames = {"lam": "lambda"}
+    prog = ["#include <stddef.h>", "#include <stdio.h>", '#include "mm.h"', "int main(void) {",
+            f'  printf("%zu\\n", sizeof({struct}));']
+    prog += [f'  printf("%zu\\n", offsetof({struct}, {cnames.get(n, n)}));' for n in names]
+    prog += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(prog) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = [int(v) for v in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
+    assert out[0] == ctypes.sizeof(C)
+    assert out[1:] == [getattr(C, n).offset for n in names]
