@@ -113,7 +113,8 @@ struct mm_model {
     int step_max_ctas = 0;
     void *step_event = nullptr;      // cudaEvent_t recorded between the step's two launches (timing hook)
     float *shadow32 = nullptr;       // FP32 shadow accumulators: metal [T][S], contrib [T][S], npv [S]
-    float *relax_scratch = nullptr;  // relaxed objective: chunk partials / adjoint coefficients
+    float *relax_scratch = nullptr;  // relaxed objective: range partials and terms / adjoint coefficients
+    uint32_t *relax_tick = nullptr;  // relaxed forward: ticket of its finishing launch (zero between launches)
     size_t relax_scratch_floats = 0;
 };
 

@@ -382,6 +382,7 @@ void mm_model_destroy(mm_model *m) {
     cudaFree(m->step_tick);
     cudaFree(m->tabc);
     cudaFree(m->relax_scratch);
+    cudaFree(m->relax_tick);
     cudaFree(m->shadow32);
     if (m->apply_res_host) cudaFreeHost(m->apply_res_host);
     if (m->status_host) cudaFreeHost(m->status_host);
@@ -507,6 +508,7 @@ mm_status mm_model_create(const mm_model_desc *d, mm_model **out) {
     ALLOC(step_ginf, (size_t)m->step_max_ctas);
     ALLOC(step_tick, (size_t)m->step_max_ctas + 1);
     ALLOC(tabc, (int64_t)4 * (T + 1));
+    ALLOC(relax_tick, 1);
     if (!grid) {
         ALLOC(pred_ptr, B + 1);
         ALLOC(pred_idx, d->pred_ptr[B] > 0 ? d->pred_ptr[B] : 1);
@@ -567,6 +569,7 @@ mm_status mm_model_create(const mm_model_desc *d, mm_model **out) {
     TRY(cudaMemsetAsync(m->minedT, 0, sizeof(int64_t) * (T + 1), s), "clear minedT");
     TRY(cudaMemsetAsync(m->apply_res, 0, sizeof(ApplyResult), s), "clear apply result");
     TRY(cudaMemsetAsync(m->step_tick, 0, sizeof(uint32_t) * ((size_t)m->step_max_ctas + 1), s), "clear step tickets");
+    TRY(cudaMemsetAsync(m->relax_tick, 0, sizeof(uint32_t), s), "clear relaxed ticket");
     if (!grid) {
         TRY(cudaMemcpyAsync(m->pred_ptr, d->pred_ptr, sizeof(int32_t) * (B + 1), cudaMemcpyHostToDevice, s), "copy CSR");
         if (d->pred_ptr[B] > 0)

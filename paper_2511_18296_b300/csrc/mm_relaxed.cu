@@ -35,13 +35,13 @@
 
 namespace mm {
 
-constexpr int kRelaxChunk = 128;  // blocks per forward CTA
-constexpr int kRelaxTile = 24;    // periods per forward CTA (at most; wider tiles spill)
+constexpr int kRelaxTile = 24;    // periods per forward CTA (at most)
 
 struct RelaxEcon {
     double p, r, pc;   // price, recovery, processing cost (FP64 ore decision)
     float pf, rf, pcf, mcf;
     double a, e, lambda, beta, m_ref;
+    double inv_beta, inv_mref, inv_S;  // reciprocals formed on the host (FP64 division is slow on this part)
     float g_thr;       // ore iff g >= g_thr, when use_thr
     int32_t use_thr;
 };
@@ -56,38 +56,6 @@ template <typename G>
 __device__ __forceinline__ bool relax_ore(G g, const RelaxEcon &E) {
     if (E.use_thr) return (float)g >= E.g_thr;
     return ((double)g * E.p) * E.r > E.pc;
-}
-
-// Raw inputs of (b, s) for relax_eval: the grade (caller grades) or the value
-// and ore word from the model's rows (model grades); fetched ahead of use.
-struct RelaxRaw {
-    float a;
-    uint32_t w;
-};
-template <typename G>
-__device__ __forceinline__ RelaxRaw relax_fetch(const G *g, const RelaxRows &Rw, int32_t b, int32_t S, int s);
-template <>
-__device__ __forceinline__ RelaxRaw relax_fetch<float>(const float *g, const RelaxRows &, int32_t b, int32_t S, int s) {
-    return RelaxRaw{__ldg(g + (size_t)b * S + s), 0u};
-}
-template <>
-__device__ __forceinline__ RelaxRaw relax_fetch<double>(const double *, const RelaxRows &Rw, int32_t b, int32_t,
-                                                        int s) {
-    const float *row = Rw.val + (size_t)b * Rw.R;
-    return RelaxRaw{__ldg(row + s), __ldg(reinterpret_cast<const uint32_t *>(row + Rw.ore_off) + (s >> 5))};
-}
-template <typename G>
-__device__ __forceinline__ void relax_eval(RelaxRaw r, int s, float m, const RelaxEcon &E, bool &ore, float &val);
-template <>
-__device__ __forceinline__ void relax_eval<float>(RelaxRaw r, int, float m, const RelaxEcon &E, bool &ore, float &val) {
-    ore = relax_ore(r.a, E);
-    const float mc = m * E.mcf;
-    val = ore ? m * ((r.a * E.pf) * E.rf - E.pcf) - mc : -mc;
-}
-template <>
-__device__ __forceinline__ void relax_eval<double>(RelaxRaw r, int s, float, const RelaxEcon &, bool &ore, float &val) {
-    val = r.a;
-    ore = (r.w >> (s & 31)) & 1u;
 }
 
 // ore and v of (b, s): from the model's rows (model grades) or the grade.
@@ -110,183 +78,253 @@ __device__ __forceinline__ void relax_ore_value<double>(const double *, const Re
     ore = (__ldg(reinterpret_cast<const uint32_t *>(row + Rw.ore_off) + (s >> 5)) >> (s & 31)) & 1u;
 }
 
-// Partial sums of O and V over one chunk of blocks for one tile of TT periods
-// starting at t_base (TT a multiple of 4: the staged x rows are read four
-// periods at a time).  Thread (s, k): scenario blockIdx.z * SW + s,
-// blocks k, k + KS, ... of the chunk; the KS partial sums of a scenario are
-// then added in k order through shared memory (deterministic), so KS times
-// more warps keep loads in flight than one thread per scenario would.
-constexpr int kRelaxSplit = 4;
+// Forward contraction, staged: CTA (r, z) owns the contiguous range r of the
+// blocks and scenario tile z (up to kFwdSW scenarios) for one tile of TT
+// periods starting at t0 (TT a multiple of 4: the staged x rows are read four
+// periods at a time).  Tiles of kFwdBT blocks -- the grade slices (caller
+// grades) or value slices and ore words (model rows), the x rows and the
+// masses -- are copied into shared memory by cp.async, up to kFwdStages - 1
+// tiles ahead of the one being summed, so every grade is read from memory
+// once and many copies are in flight.  The CTA's kFwdGroups thread groups
+// split each tile's blocks (group k takes blocks k, k + kFwdGroups, ...);
+// thread s of a group sums x[b][t] m_b ore[b][s] and x[b][t] v[b][s] in FP32
+// registers, the groups' sums are added in group order through shared memory
+// and the CTA writes one partial of O and V; the partials are added in FP64 in
+// range order afterwards (deterministic).
+constexpr int kFwdBT = 24;      // blocks per staged tile (three stages stay under 48 KB of static shared memory)
+constexpr int kFwdStages = 3;   // staged tiles (two in flight while one is summed)
+constexpr int kFwdSW = 128;     // scenarios per CTA (at most)
+constexpr int kFwdGroups = 2;   // thread groups splitting a tile's blocks
+#ifndef MM_RELAX_CTAS_PER_SM
+#define MM_RELAX_CTAS_PER_SM 2      // forward CTAs per SM (each writes one partial)
+#endif
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+
+// Two FP32 values in one 64-bit register pair and the paired FMA of the
+// sm_100 family (each lane rounded exactly like the scalar fmaf).
+__device__ __forceinline__ uint64_t rx_pack(float lo, float hi) {
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void rx_unpack(uint64_t v, float &lo, float &hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ uint64_t rx_fma2(uint64_t a, uint64_t b, uint64_t c) {
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
 template <typename G, int TT>
-__global__ void __launch_bounds__(512) k_relax_partial(const float *__restrict__ x, const G *__restrict__ g,
-                                                        RelaxRows Rw, const uint32_t *__restrict__ mass, int32_t B,
-                                                        int32_t S, int32_t T, int32_t t_base, RelaxEcon E,
-                                                        float *__restrict__ part_o, float *__restrict__ part_v) {
-    constexpr int KS = kRelaxSplit;
-    __shared__ __align__(16) float s_x[kRelaxChunk][TT];
-    __shared__ float s_m[kRelaxChunk];
-    extern __shared__ float s_red[];  // [KS - 1][TT][SW]
-    const int SW = blockDim.x / KS;   // scenarios per CTA
-    const int chunk = blockIdx.x, t0 = t_base;
-    const int b0 = chunk * kRelaxChunk;
-    const int nb = min(kRelaxChunk, B - b0), nt = min(TT, T - t0);
-    for (int i = threadIdx.x; i < kRelaxChunk * TT; i += blockDim.x) {
-        const int bb = i / TT, j = i % TT;
-        s_x[bb][j] = (bb < nb && j < nt) ? x[(size_t)(b0 + bb) * T + t0 + j] : 0.0f;
-    }
-    for (int i = threadIdx.x; i < kRelaxChunk; i += blockDim.x) s_m[i] = i < nb ? (float)mass[b0 + i] : 0.0f;
+__global__ void __launch_bounds__(kFwdSW * kFwdGroups) k_relax_fwd(const float *__restrict__ x, const G *__restrict__ g,
+                                                      RelaxRows Rw, const uint32_t *__restrict__ mass, int32_t B,
+                                                      int32_t S, int32_t T, int32_t t0, RelaxEcon E, int32_t vec,
+                                                      float *__restrict__ part_o, float *__restrict__ part_v) {
+    constexpr bool ROWS = sizeof(G) == sizeof(double);          // model rows: values, then ore words
+    constexpr int RW = kFwdSW + (ROWS ? 4 : 0);                  // staged floats per block
+    __shared__ __align__(16) float s_g[kFwdStages][kFwdBT][RW];
+    __shared__ __align__(16) float s_x[kFwdStages][kFwdBT][TT];
+    __shared__ uint32_t s_m[kFwdStages][kFwdBT];
+    const int r = blockIdx.x, nr = gridDim.x;
+    const int b_lo = (int)((int64_t)r * B / nr), b_hi = (int)((int64_t)(r + 1) * B / nr);
+    const int s0 = blockIdx.z * kFwdSW, sw = min(kFwdSW, S - s0);
+    const int nt = min(TT, T - t0);
+    const int ntiles = (b_hi - b_lo + kFwdBT - 1) / kFwdBT;
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const int gw = nth / kFwdGroups;                 // threads per group (a multiple of 32)
+    const int grp = tid / gw, lt = tid - grp * gw;   // group, scenario lane
+    auto issue = [&](int k) {
+        const int st = k % kFwdStages, bb0 = b_lo + k * kFwdBT, nb = min(kFwdBT, b_hi - bb0);
+        if (ROWS) {
+            // value slice [s0, s0 + sw) rounded up to 16 bytes (the row's zero padding
+            // runs to a multiple of 4 floats) and the slice's ore words (one 16-byte copy)
+            const int nv4 = (sw + 3) / 4, per = nv4 + 1;
+            for (int i = tid; i < nb * per; i += nth) {
+                const int j = i / per, q = i - j * per;
+                const float *row = Rw.val + (size_t)(bb0 + j) * Rw.R;
+                if (q < nv4) cp_async16(&s_g[st][j][4 * q], row + s0 + 4 * q);
+                else cp_async16(&s_g[st][j][kFwdSW], row + Rw.ore_off + s0 / 32);
+            }
+        } else if (vec) {
+            const int nv4 = sw / 4;  // S % 4 == 0
+            for (int i = tid; i < nb * nv4; i += nth) {
+                const int j = i / nv4, q = i - j * nv4;
+                cp_async16(&s_g[st][j][4 * q], reinterpret_cast<const float *>(g) + (size_t)(bb0 + j) * S + s0 + 4 * q);
+            }
+        } else {
+            for (int i = tid; i < nb * sw; i += nth) {
+                const int j = i / sw, q = i - j * sw;
+                cp_async4(&s_g[st][j][q], reinterpret_cast<const float *>(g) + (size_t)(bb0 + j) * S + s0 + q);
+            }
+        }
+        for (int i = tid; i < nb * nt; i += nth) {
+            const int j = i / nt, q = i - j * nt;
+            cp_async4(&s_x[st][j][q], x + (size_t)(bb0 + j) * T + t0 + q);
+        }
+        for (int j = tid; j < nb; j += nth) cp_async4(&s_m[st][j], mass + bb0 + j);
+    };
+    // periods t0 + nt .. t0 + TT - 1 of the x tiles stay zero
+    if (nt < TT)
+        for (int i = tid; i < kFwdStages * kFwdBT * TT; i += nth) (&s_x[0][0][0])[i] = 0.0f;
     __syncthreads();
-    const int sl = threadIdx.x % SW, k = threadIdx.x / SW;
-    const int s = blockIdx.z * SW + sl;
-    const bool live = s < S;
+    // always kFwdStages - 1 groups (empty ones past the last tile), so that the
+    // wait below counts the same groups for every range length
+    for (int k = 0; k < kFwdStages - 1; k++) {
+        if (k < ntiles) issue(k);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    }
+    const bool live = lt < sw;
+    const int s = s0 + lt;
+    uint64_t o2[TT / 2], v2[TT / 2];  // period pairs (2q, 2q + 1)
+#pragma unroll
+    for (int j = 0; j < TT / 2; j++) o2[j] = v2[j] = 0ull;
+    for (int k = 0; k < ntiles; k++) {
+        if (k + kFwdStages - 1 < ntiles) issue(k + kFwdStages - 1);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        asm volatile("cp.async.wait_group %0;" ::"n"(kFwdStages - 1) : "memory");  // tile k has landed
+        __syncthreads();
+        const int st = k % kFwdStages, nb = min(kFwdBT, b_hi - (b_lo + k * kFwdBT));
+        if (live) {
+            // the next block's grade (or value and ore word) and mass are read
+            // from shared memory before the current block's products
+            int j = grp;
+            float g_n = 0.0f;
+            uint32_t w_n = 0u, m_n = 0u;
+            if (j < nb) {
+                g_n = s_g[st][j][lt];
+                if (ROWS) w_n = __float_as_uint(s_g[st][j][kFwdSW + (lt >> 5)]);
+                m_n = s_m[st][j];
+            }
+            for (; j < nb; j += kFwdGroups) {
+                const float gv = g_n, m = (float)m_n;
+                const uint32_t ow = w_n;
+                const int jn = j + kFwdGroups;
+                if (jn < nb) {
+                    g_n = s_g[st][jn][lt];
+                    if (ROWS) w_n = __float_as_uint(s_g[st][jn][kFwdSW + (lt >> 5)]);
+                    m_n = s_m[st][jn];
+                }
+                float val;
+                bool ore;
+                if (ROWS) {
+                    val = gv;
+                    ore = (ow >> (lt & 31)) & 1u;
+                } else {
+                    ore = relax_ore(gv, E);
+                    const float mc = m * E.mcf;
+                    val = ore ? m * ((gv * E.pf) * E.rf - E.pcf) - mc : -mc;
+                }
+                const float mo = ore ? m : 0.0f;
+                const uint64_t mo2 = rx_pack(mo, mo), val2 = rx_pack(val, val);
+                const float4 *xr = reinterpret_cast<const float4 *>(s_x[st][j]);
+#pragma unroll
+                for (int q = 0; q < TT / 4; q++) {
+                    const float4 x4 = xr[q];
+                    const uint64_t xa = rx_pack(x4.x, x4.y), xb = rx_pack(x4.z, x4.w);
+                    o2[2 * q] = rx_fma2(xa, mo2, o2[2 * q]);
+                    o2[2 * q + 1] = rx_fma2(xb, mo2, o2[2 * q + 1]);
+                    v2[2 * q] = rx_fma2(xa, val2, v2[2 * q]);
+                    v2[2 * q + 1] = rx_fma2(xb, val2, v2[2 * q + 1]);
+                }
+            }
+        }
+        __syncthreads();  // stage k % kFwdStages is refilled next
+    }
     float o[TT], v[TT];
 #pragma unroll
-    for (int j = 0; j < TT; j++) o[j] = v[j] = 0.0f;
-    if (live) {
-        // two blocks' inputs in flight ahead of use
-        RelaxRaw r0 = k < nb ? relax_fetch<G>(g, Rw, b0 + k, S, s) : RelaxRaw{0.0f, 0u};
-        RelaxRaw r1 = k + KS < nb ? relax_fetch<G>(g, Rw, b0 + k + KS, S, s) : RelaxRaw{0.0f, 0u};
-        for (int bb = k; bb < nb; bb += KS) {
-            const RelaxRaw rc = r0;
-            r0 = r1;
-            if (bb + 2 * KS < nb) r1 = relax_fetch<G>(g, Rw, b0 + bb + 2 * KS, S, s);
-            bool ore;
-            float val;
-            relax_eval<G>(rc, s, s_m[bb], E, ore, val);
-            const float mo = ore ? s_m[bb] : 0.0f;
-            const float4 *xr = reinterpret_cast<const float4 *>(s_x[bb]);
+    for (int j = 0; j < TT / 2; j++) {
+        rx_unpack(o2[j], o[2 * j], o[2 * j + 1]);
+        rx_unpack(v2[j], v[2 * j], v[2 * j + 1]);
+    }
+    // groups 1.. hand their sums to group 0 through the (now idle) grade
+    // stages, which group 0 adds in group order
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncthreads();
+    float *red = &s_g[0][0][0];  // [kFwdGroups - 1][2][TT][kFwdSW]
+    static_assert((kFwdGroups - 1) * 2 * TT * kFwdSW <= kFwdStages * kFwdBT * RW, "combine space");
+    if (grp > 0) {
 #pragma unroll
-            for (int q = 0; q < TT / 4; q++) {
-                const float4 x4 = xr[q];
-                o[4 * q] = fmaf(x4.x, mo, o[4 * q]);
-                o[4 * q + 1] = fmaf(x4.y, mo, o[4 * q + 1]);
-                o[4 * q + 2] = fmaf(x4.z, mo, o[4 * q + 2]);
-                o[4 * q + 3] = fmaf(x4.w, mo, o[4 * q + 3]);
-                v[4 * q] = fmaf(x4.x, val, v[4 * q]);
-                v[4 * q + 1] = fmaf(x4.y, val, v[4 * q + 1]);
-                v[4 * q + 2] = fmaf(x4.z, val, v[4 * q + 2]);
-                v[4 * q + 3] = fmaf(x4.w, val, v[4 * q + 3]);
+        for (int j = 0; j < TT; j++) {
+            red[(((size_t)(grp - 1) * 2) * TT + j) * kFwdSW + lt] = o[j];
+            red[(((size_t)(grp - 1) * 2 + 1) * TT + j) * kFwdSW + lt] = v[j];
+        }
+    }
+    __syncthreads();
+    if (grp == 0 && live) {
+#pragma unroll
+        for (int j = 0; j < TT; j++) {
+            float a = o[j], c = v[j];
+#pragma unroll
+            for (int k = 1; k < kFwdGroups; k++) {
+                a += red[(((size_t)(k - 1) * 2) * TT + j) * kFwdSW + lt];
+                c += red[(((size_t)(k - 1) * 2 + 1) * TT + j) * kFwdSW + lt];
+            }
+            if (j < nt) {
+                part_o[((size_t)r * T + t0 + j) * S + s] = a;
+                part_v[((size_t)r * T + t0 + j) * S + s] = c;
             }
         }
     }
-    // o: partials of k >= 1 to shared memory, k = 0 adds them in k order; then
-    // v.  Written out twice with static indices so o and v stay in registers.
-    if (k > 0) {
-#pragma unroll
-        for (int j = 0; j < TT; j++) s_red[((size_t)(k - 1) * TT + j) * SW + sl] = o[j];
-    }
-    __syncthreads();
-    if (k == 0 && live) {
-#pragma unroll
-        for (int j = 0; j < TT; j++) {
-            float a = o[j];
-#pragma unroll
-            for (int kk = 1; kk < KS; kk++) a += s_red[((size_t)(kk - 1) * TT + j) * SW + sl];
-            if (j < nt) part_o[((size_t)chunk * T + t0 + j) * S + s] = a;
-        }
-    }
-    __syncthreads();
-    if (k > 0) {
-#pragma unroll
-        for (int j = 0; j < TT; j++) s_red[((size_t)(k - 1) * TT + j) * SW + sl] = v[j];
-    }
-    __syncthreads();
-    if (k == 0 && live) {
-#pragma unroll
-        for (int j = 0; j < TT; j++) {
-            float a = v[j];
-#pragma unroll
-            for (int kk = 1; kk < KS; kk++) a += s_red[((size_t)(kk - 1) * TT + j) * SW + sl];
-            if (j < nt) part_v[((size_t)chunk * T + t0 + j) * S + s] = a;
-        }
-    }
-}
-
-template <typename G, int TT>
-static void relax_partial_tile(dim3 grid, int threads, size_t smem, cudaStream_t st, const float *x, const G *g,
-                               RelaxRows Rw, const uint32_t *mass, int32_t B, int32_t S, int32_t T, int32_t tb,
-                               RelaxEcon E, float *part_o, float *part_v) {
-    // static + dynamic shared memory passes 48 KB for the wide tiles
-    static const cudaError_t attr = cudaFuncSetAttribute(
-        k_relax_partial<G, TT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-        (int)((kRelaxSplit - 1) * TT * (512 / kRelaxSplit) * sizeof(float)));
-    (void)attr;
-    k_relax_partial<G, TT><<<grid, threads, smem, st>>>(x, g, Rw, mass, B, S, T, tb, E, part_o, part_v);
 }
 
 template <typename G>
-static mm_status relax_partial_launch(const float *x, const G *g, RelaxRows Rw, const uint32_t *mass, int32_t B,
-                                      int32_t S, int32_t T, RelaxEcon E, float *part_o, float *part_v, int nchunks,
-                                      int threads, cudaStream_t st) {
-    // tiles of up to kRelaxTile periods, each as wide as needed rounded up to 4,
-    // so a batch with T <= kRelaxTile reads the grades once
-    const int sw = threads / kRelaxSplit;
-    const int zs = (S + sw - 1) / sw;
+static mm_status relax_fwd_launch(const float *x, const G *g, RelaxRows Rw, const uint32_t *mass, int32_t B, int32_t S,
+                                  int32_t T, RelaxEcon E, float *part_o, float *part_v, int nr, cudaStream_t st) {
+    const int zs = (S + kFwdSW - 1) / kFwdSW;
+    const int threads = std::min(((S + 31) / 32) * 32, kFwdSW) * kFwdGroups;
+    const int vec = (S % 4 == 0 && ((uintptr_t)g & 15u) == 0) ? 1 : 0;
     for (int tb = 0; tb < T; tb += kRelaxTile) {
-        const int w = std::min(kRelaxTile, T - tb), tt = (w + 3) / 4 * 4;
-        const dim3 grid(nchunks, 1, zs);
-        const size_t smem = (size_t)(kRelaxSplit - 1) * tt * sw * sizeof(float);
+        const int tt = (std::min(kRelaxTile, T - tb) + 3) / 4 * 4;
+        const dim3 grid(nr, 1, zs);
         switch (tt) {
-            case 4: relax_partial_tile<G, 4>(grid, threads, smem, st, x, g, Rw, mass, B, S, T, tb, E, part_o, part_v); break;
-            case 8: relax_partial_tile<G, 8>(grid, threads, smem, st, x, g, Rw, mass, B, S, T, tb, E, part_o, part_v); break;
-            case 12: relax_partial_tile<G, 12>(grid, threads, smem, st, x, g, Rw, mass, B, S, T, tb, E, part_o, part_v); break;
-            case 16: relax_partial_tile<G, 16>(grid, threads, smem, st, x, g, Rw, mass, B, S, T, tb, E, part_o, part_v); break;
-            case 20: relax_partial_tile<G, 20>(grid, threads, smem, st, x, g, Rw, mass, B, S, T, tb, E, part_o, part_v); break;
-            default: relax_partial_tile<G, 24>(grid, threads, smem, st, x, g, Rw, mass, B, S, T, tb, E, part_o, part_v); break;
+            case 4: k_relax_fwd<G, 4><<<grid, threads, 0, st>>>(x, g, Rw, mass, B, S, T, tb, E, vec, part_o, part_v); break;
+            case 8: k_relax_fwd<G, 8><<<grid, threads, 0, st>>>(x, g, Rw, mass, B, S, T, tb, E, vec, part_o, part_v); break;
+            case 12: k_relax_fwd<G, 12><<<grid, threads, 0, st>>>(x, g, Rw, mass, B, S, T, tb, E, vec, part_o, part_v); break;
+            case 16: k_relax_fwd<G, 16><<<grid, threads, 0, st>>>(x, g, Rw, mass, B, S, T, tb, E, vec, part_o, part_v); break;
+            case 20: k_relax_fwd<G, 20><<<grid, threads, 0, st>>>(x, g, Rw, mass, B, S, T, tb, E, vec, part_o, part_v); break;
+            default: k_relax_fwd<G, 24><<<grid, threads, 0, st>>>(x, g, Rw, mass, B, S, T, tb, E, vec, part_o, part_v); break;
         }
-        mm_status r = check_launch("k_relax_partial");
+        mm_status r = check_launch("k_relax_fwd");
         if (r != MM_OK) return r;
     }
     return MM_OK;
 }
 
-// O and V from the chunk partials in FP64, one warp per (t, s): lane l adds
-// chunks l, l + 32, ... in order, then a fixed xor tree (deterministic).
-__global__ void __launch_bounds__(256) k_relax_reduce(const float *__restrict__ part_o,
-                                                      const float *__restrict__ part_v, int32_t nchunks, int32_t TS,
-                                                      double *__restrict__ o_out, double *__restrict__ v_out) {
-    const int lane = threadIdx.x & 31;
-    const int i = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
-    if (i >= TS) return;
-    double so = 0.0, sv = 0.0;
-    for (int c = lane; c < nchunks; c += 32) {
-        so += (double)__ldg(part_o + (size_t)c * TS + i);
-        sv += (double)__ldg(part_v + (size_t)c * TS + i);
-    }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        so += __shfl_xor_sync(0xffffffffu, so, off);
-        sv += __shfl_xor_sync(0xffffffffu, sv, off);
-    }
-    if (lane == 0) {
-        o_out[i] = so;
-        v_out[i] = sv;
-    }
-}
-
 // softplus and its derivative of beta z, the argument formed in FP64 and the
 // transcendental part in FP32 (relative error ~1e-7 of a term far below the
 // NPV and gradient tolerances).
-__device__ __forceinline__ double relax_softplus(double z, double beta) {
-    const double bz = beta * z;
+__device__ __forceinline__ double relax_softplus(double z, const RelaxEcon &E) {
+    const double bz = E.beta * z;
     const float abz = (float)fabs(bz);
-    return (fmax(bz, 0.0) + (double)log1pf(expf(-abz))) / beta;
+    return (fmax(bz, 0.0) + (double)log1pf(expf(-abz))) * E.inv_beta;
 }
 __device__ __forceinline__ double relax_sigmoid(double z, double beta) {
     return (double)(1.0f / (1.0f + expf((float)(-beta * z))));
 }
 
-// FP64 sum over the threads of one CTA (valid in every thread).
+// FP64 sum over the threads of one CTA (valid in every thread): xor trees
+// inside each warp and then over the warp sums (a fixed order, ten dependent
+// additions rather than one per warp).
 __device__ double relax_block_sum(double x, double *red) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
     if (lane == 0) red[warp] = x;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int w = 0; w < nw; w++) t += red[w];
-        red[32] = t;
+    if (warp == 0) {
+        double t = lane < nw ? red[lane] : 0.0;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+        if (lane == 0) red[32] = t;
     }
     __syncthreads();
     const double r = red[32];
@@ -294,35 +332,113 @@ __device__ double relax_block_sum(double x, double *red) {
     return r;
 }
 
-// Discounted net value of every (t, s): d_t (V[t][s] - P_t(O[t][s])), one
-// thread each over many CTAs (FP64 is scarce per SM on this part).
-__global__ void __launch_bounds__(256) k_relax_terms(const double *__restrict__ o, const double *__restrict__ v,
-                                                     const double *__restrict__ disc,
-                                                     const uint64_t *__restrict__ target, int32_t S, int32_t TS,
-                                                     RelaxEcon E, double *__restrict__ term) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= TS) return;
-    const int t = i / S;
-    const double O = o[i], Q = (double)target[t], inv = 1.0 / E.m_ref;
-    const double pen = E.a * E.m_ref * relax_softplus((Q - O) * inv, E.beta) +
-                       E.e * E.m_ref * relax_softplus((O - Q) * inv, E.beta);
-    term[i] = disc[t] * (v[i] - pen);
+// Neumaier-compensated FP32 accumulation (s, c) += x, and the merge of two
+// compensated sums.
+__device__ __forceinline__ void relax_neumaier(float &s, float &c, float x) {
+    const float t = s + x;
+    c += fabsf(s) >= fabsf(x) ? (s - t) + x : (x - t) + s;
+    s = t;
+}
+__device__ __forceinline__ void relax_merge(float &s, float &c, float s2, float c2) {
+    relax_neumaier(s, c, s2);
+    c += c2;
 }
 
-// NPV_s = sum_t term[t][s] (period order) and J (one CTA, one thread per scenario).
-__global__ void __launch_bounds__(1024) k_relax_npv(const double *__restrict__ term, int32_t S, int32_t T,
-                                                    RelaxEcon E, double *__restrict__ npv, double *__restrict__ J) {
+// End of the forward pass, one launch:
+//   1. O[t][s] and V[t][s] from the range partials: a CTA of 32 warps per 32
+//      consecutive (t, s) (coalesced), warp w adding ranges w, w + 32, ... by
+//      compensated FP32 sums, the 32 warp sums merged by a fixed pairwise
+//      tree (deterministic; the error is about one FP32 rounding of the
+//      total, with no FP64 work on the long sums);
+//   2. the FP64 checkpoint O[t][s] and term[t][s] = d_t (V - P_t(O));
+//   3. the last CTA to finish (acquire-release ticket) forms
+//      NPV_s = sum_t term[t][s] in period order, the mean and population std
+//      over scenarios and J, and resets the ticket.
+__global__ void __launch_bounds__(1024) k_relax_finish(const float *__restrict__ part_o,
+                                                       const float *__restrict__ part_v, int32_t nr, int32_t S,
+                                                       int32_t T, const double *__restrict__ disc,
+                                                       const uint64_t *__restrict__ target, RelaxEcon E,
+                                                       double *__restrict__ o_out, double *term, uint32_t *tick,
+                                                       double *__restrict__ npv, double *__restrict__ J) {
+    __shared__ float s_sum[2][32][32], s_cmp[2][32][32];  // [O / V][warp][lane]
     __shared__ double red[33];
+    __shared__ int s_last;
+    const int TS = T * S;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int i = blockIdx.x * 32 + lane;
+    float so = 0.0f, co = 0.0f, sv = 0.0f, cv = 0.0f;
+    if (i < TS) {
+        // eight ranges' partials loaded before any is added
+        for (int c0 = warp; c0 < nr; c0 += 8 * 32) {
+            float a[8], b[8];
+#pragma unroll
+            for (int u = 0; u < 8; u++) {
+                const int c = c0 + 32 * u;
+                a[u] = c < nr ? __ldg(part_o + (size_t)c * TS + i) : 0.0f;
+                b[u] = c < nr ? __ldg(part_v + (size_t)c * TS + i) : 0.0f;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; u++) {
+                relax_neumaier(so, co, a[u]);
+                relax_neumaier(sv, cv, b[u]);
+            }
+        }
+    }
+    s_sum[0][warp][lane] = so; s_cmp[0][warp][lane] = co;
+    s_sum[1][warp][lane] = sv; s_cmp[1][warp][lane] = cv;
+    __syncthreads();
+#pragma unroll
+    for (int h = 16; h > 0; h >>= 1) {
+        if (warp < h) {
+#pragma unroll
+            for (int q = 0; q < 2; q++) {
+                float a = s_sum[q][warp][lane], b = s_cmp[q][warp][lane];
+                relax_merge(a, b, s_sum[q][warp + h][lane], s_cmp[q][warp + h][lane]);
+                s_sum[q][warp][lane] = a;
+                s_cmp[q][warp][lane] = b;
+            }
+        }
+        __syncthreads();
+    }
+    if (warp == 0 && i < TS) {
+        const double O = (double)s_sum[0][0][lane] + (double)s_cmp[0][0][lane];
+        const double V = (double)s_sum[1][0][lane] + (double)s_cmp[1][0][lane];
+        o_out[i] = O;
+        const int t = i / S;
+        const double Q = (double)target[t];
+        const double pen = E.a * E.m_ref * relax_softplus((Q - O) * E.inv_mref, E) +
+                           E.e * E.m_ref * relax_softplus((O - Q) * E.inv_mref, E);
+        term[i] = disc[t] * (V - pen);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t old;
+        asm volatile("atom.add.acq_rel.gpu.u32 %0, [%1], 1;" : "=r"(old) : "l"(tick) : "memory");
+        s_last = old == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
     const int s = threadIdx.x;
     double acc = 0.0;
     if (s < S) {
-        for (int t = 0; t < T; t++) acc += term[(size_t)t * S + s];
+        // eight periods' terms loaded before any is added (period order kept)
+        for (int t0 = 0; t0 < T; t0 += 8) {
+            double q[8];
+#pragma unroll
+            for (int u = 0; u < 8; u++) q[u] = t0 + u < T ? __ldcg(term + (size_t)(t0 + u) * S + s) : 0.0;
+#pragma unroll
+            for (int u = 0; u < 8; u++)
+                if (t0 + u < T) acc += q[u];
+        }
         npv[s] = acc;
     }
-    const double mean = relax_block_sum(s < S ? acc : 0.0, red) / S;
+    const double mean = relax_block_sum(s < S ? acc : 0.0, red) * E.inv_S;
     const double dv = s < S ? acc - mean : 0.0;
-    const double var = relax_block_sum(dv * dv, red) / S;
-    if (s == 0) J[0] = mean - E.lambda * sqrt(var);
+    const double var = relax_block_sum(dv * dv, red) * E.inv_S;
+    if (s == 0) {
+        J[0] = mean - E.lambda * sqrt(var);
+        *tick = 0u;
+    }
 }
 
 // Adjoint coefficients: w_s = gJ (1/S - lambda (NPV_s - mean) / (S std))
@@ -335,22 +451,22 @@ __global__ void __launch_bounds__(256) k_relax_coef(const double *__restrict__ n
     __shared__ double red[33];
     double part = 0.0;
     for (int s = threadIdx.x; s < S; s += blockDim.x) part += npv[s];
-    const double mean = relax_block_sum(part, red) / S;
+    const double mean = relax_block_sum(part, red) * E.inv_S;
     double pv = 0.0;
     for (int s = threadIdx.x; s < S; s += blockDim.x) {
         const double d = npv[s] - mean;
         pv += d * d;
     }
-    const double sd = sqrt(relax_block_sum(pv, red) / S);
+    const double sd = sqrt(relax_block_sum(pv, red) * E.inv_S);
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= T * S) return;
     const int t = i / S, s = i - t * S;
     const double g = gJ[0];
-    double w = g / S;
-    if (sd > 0.0) w -= g * E.lambda * (npv[s] - mean) / (S * sd);
+    double w = g * E.inv_S;
+    if (sd > 0.0) w -= g * E.lambda * (npv[s] - mean) * E.inv_S / sd;
     if (t == 0) w_out[s] = (float)w;
-    const double O = o[i], Q = (double)target[t], inv = 1.0 / E.m_ref;
-    const double dp = -E.a * relax_sigmoid((Q - O) * inv, E.beta) + E.e * relax_sigmoid((O - Q) * inv, E.beta);
+    const double O = o[i], Q = (double)target[t];
+    const double dp = -E.a * relax_sigmoid((Q - O) * E.inv_mref, E.beta) + E.e * relax_sigmoid((O - Q) * E.inv_mref, E.beta);
     c_out[(size_t)t * Sp + s] = (float)(w * dp);
 }
 
@@ -462,6 +578,7 @@ static RelaxEcon relax_econ(const mm_model *m, double beta, double m_ref) {
     E.p = m->price; E.r = m->recovery; E.pc = m->proc_cost;
     E.pf = (float)m->price; E.rf = (float)m->recovery; E.pcf = (float)m->proc_cost; E.mcf = (float)m->mining_cost;
     E.a = m->shortfall_pen; E.e = m->excess_pen; E.lambda = m->lambda; E.beta = beta; E.m_ref = m_ref;
+    E.inv_beta = 1.0 / beta; E.inv_mref = 1.0 / m_ref; E.inv_S = 1.0 / m->S;
     // (g p) r > pc is non-decreasing in g >= 0 when p, r > 0, and false for
     // g < 0 when pc >= 0: the smallest non-negative float with the test true
     // (binary search over the ordered bit patterns of 0 .. +inf) is g_t
@@ -509,32 +626,24 @@ mm_status mm_relaxed_forward(mm_model *m, const float *x_dev, const float *g_dev
     if (st != MM_OK) return st;
     if (!J_dev || !npv_dev || !ore_t_dev) return set_error(MM_ERR_INVALID_ARG, "NULL output");
     const int B = m->B, S = m->S, T = m->T;
-    const int nchunks = (B + kRelaxChunk - 1) / kRelaxChunk;
+    // block ranges: MM_RELAX_CTAS_PER_SM CTAs per SM over the scenario tiles,
+    // at least one staged tile each
+    const int zs = (S + kFwdSW - 1) / kFwdSW;
+    const int nr = std::max(1, std::min((B + kFwdBT - 1) / kFwdBT, std::max(1, MM_RELAX_CTAS_PER_SM * m->num_sms / zs)));
     const size_t TS = (size_t)T * S;
-    // scratch: chunk partials of O and V (FP32), then V and the terms in FP64
-    st = relax_scratch(m, 2 * (size_t)nchunks * TS + 4 * TS);
+    // scratch: range partials of O and V (FP32), then the terms in FP64
+    st = relax_scratch(m, 2 * (size_t)nr * TS + 2 * TS);
     if (st != MM_OK) return st;
-    float *part_o = m->relax_scratch, *part_v = part_o + (size_t)nchunks * TS;
-    double *v_sum = reinterpret_cast<double *>(part_v + (size_t)nchunks * TS);
+    float *part_o = m->relax_scratch, *part_v = part_o + (size_t)nr * TS;
+    double *term = reinterpret_cast<double *>(part_v + (size_t)nr * TS);
     const RelaxEcon E = relax_econ(m, beta, m_ref);
-    const int threads = kRelaxSplit * std::min(((S + 31) / 32) * 32, 128);  // scenarios per CTA x split
     const RelaxRows Rw{m->val, m->R, m->ore_off};
-    st = g_dev ? relax_partial_launch<float>(x_dev, g_dev, Rw, m->mass, B, S, T, E, part_o, part_v, nchunks, threads,
-                                             m->stream)
-               : relax_partial_launch<double>(x_dev, m->grade, Rw, m->mass, B, S, T, E, part_o, part_v, nchunks,
-                                              threads, m->stream);
+    st = g_dev ? relax_fwd_launch<float>(x_dev, g_dev, Rw, m->mass, B, S, T, E, part_o, part_v, nr, m->stream)
+               : relax_fwd_launch<double>(x_dev, m->grade, Rw, m->mass, B, S, T, E, part_o, part_v, nr, m->stream);
     if (st != MM_OK) return st;
-    k_relax_reduce<<<(unsigned)((TS * 32 + 255) / 256), 256, 0, m->stream>>>(part_o, part_v, nchunks, (int)TS,
-                                                                            ore_t_dev, v_sum);
-    st = check_launch("k_relax_reduce");
-    if (st != MM_OK) return st;
-    double *term = v_sum + TS;
-    k_relax_terms<<<(unsigned)((TS + 255) / 256), 256, 0, m->stream>>>(ore_t_dev, v_sum, m->disc, m->target, S, (int)TS,
-                                                                      E, term);
-    st = check_launch("k_relax_terms");
-    if (st != MM_OK) return st;
-    k_relax_npv<<<1, ((S + 31) / 32) * 32, 0, m->stream>>>(term, S, T, E, npv_dev, J_dev);  // a thread per scenario
-    return check_launch("k_relax_npv");
+    k_relax_finish<<<(unsigned)((TS + 31) / 32), 1024, 0, m->stream>>>(part_o, part_v, nr, S, T, m->disc, m->target, E,
+                                                                       ore_t_dev, term, m->relax_tick, npv_dev, J_dev);
+    return check_launch("k_relax_finish");
 }
 
 mm_status mm_relaxed_backward(mm_model *m, const float *x_dev, const float *g_dev, double beta, double m_ref,
@@ -549,8 +658,10 @@ mm_status mm_relaxed_backward(mm_model *m, const float *x_dev, const float *g_de
     if (st != MM_OK) return st;
     float *w = m->relax_scratch, *c = w + S;
     const RelaxEcon E = relax_econ(m, beta, m_ref);
-    k_relax_coef<<<(unsigned)(((size_t)T * S + 255) / 256), 256, 0, m->stream>>>(npv_dev, ore_t_dev, m->target,
-                                                                                  gJ_dev, S, T, Sp, E, w, c);
+    // small CTAs: each forms the scenario mean and std itself, in FP64, so more
+    // SMs share that work
+    k_relax_coef<<<(unsigned)(((size_t)T * S + 63) / 64), 64, 0, m->stream>>>(npv_dev, ore_t_dev, m->target, gJ_dev, S,
+                                                                               T, Sp, E, w, c);
     st = check_launch("k_relax_coef");
     if (st != MM_OK) return st;
     const int W = (S + 31) / 32;
