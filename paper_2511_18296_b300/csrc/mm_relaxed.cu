@@ -332,6 +332,39 @@ __device__ double relax_block_sum(double x, double *red) {
     return r;
 }
 
+// (sum of x, sum of x^2) over the threads of one CTA in FP64, the two chains
+// side by side (valid in every thread); the same fixed trees as
+// relax_block_sum.
+__device__ double2 relax_block_sum2(double x, double y, double *red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        x += __shfl_xor_sync(0xffffffffu, x, off);
+        y += __shfl_xor_sync(0xffffffffu, y, off);
+    }
+    if (lane == 0) {
+        red[warp] = x;
+        red[32 + warp] = y;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        double a = lane < nw ? red[lane] : 0.0, b = lane < nw ? red[32 + lane] : 0.0;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            a += __shfl_xor_sync(0xffffffffu, a, off);
+            b += __shfl_xor_sync(0xffffffffu, b, off);
+        }
+        if (lane == 0) {
+            red[64] = a;
+            red[65] = b;
+        }
+    }
+    __syncthreads();
+    const double2 r = make_double2(red[64], red[65]);
+    __syncthreads();
+    return r;
+}
+
 // Neumaier-compensated FP32 accumulation (s, c) += x, and the merge of two
 // compensated sums.
 __device__ __forceinline__ void relax_neumaier(float &s, float &c, float x) {
@@ -361,7 +394,7 @@ __global__ void __launch_bounds__(1024) k_relax_finish(const float *__restrict__
                                                        double *__restrict__ o_out, double *term, uint32_t *tick,
                                                        double *__restrict__ npv, double *__restrict__ J) {
     __shared__ float s_sum[2][32][32], s_cmp[2][32][32];  // [O / V][warp][lane]
-    __shared__ double red[33];
+    __shared__ double red[66];
     __shared__ int s_last;
     const int TS = T * S;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -421,20 +454,20 @@ __global__ void __launch_bounds__(1024) k_relax_finish(const float *__restrict__
     const int s = threadIdx.x;
     double acc = 0.0;
     if (s < S) {
-        // eight periods' terms loaded before any is added (period order kept)
+        // periods in batches of eight, loaded together and added by a fixed
+        // pairwise tree, the batch sums in period order (short FP64 chains)
         for (int t0 = 0; t0 < T; t0 += 8) {
             double q[8];
 #pragma unroll
             for (int u = 0; u < 8; u++) q[u] = t0 + u < T ? __ldcg(term + (size_t)(t0 + u) * S + s) : 0.0;
-#pragma unroll
-            for (int u = 0; u < 8; u++)
-                if (t0 + u < T) acc += q[u];
+            acc += ((q[0] + q[1]) + (q[2] + q[3])) + ((q[4] + q[5]) + (q[6] + q[7]));
         }
         npv[s] = acc;
     }
-    const double mean = relax_block_sum(s < S ? acc : 0.0, red) * E.inv_S;
-    const double dv = s < S ? acc - mean : 0.0;
-    const double var = relax_block_sum(dv * dv, red) * E.inv_S;
+    // mean and population variance in one pass of (sum, sum of squares)
+    const double2 sums = relax_block_sum2(s < S ? acc : 0.0, s < S ? acc * acc : 0.0, red);
+    const double mean = sums.x * E.inv_S;
+    const double var = fmax(sums.y * E.inv_S - mean * mean, 0.0);
     if (s == 0) {
         J[0] = mean - E.lambda * sqrt(var);
         *tick = 0u;
@@ -472,6 +505,166 @@ __global__ void __launch_bounds__(256) k_relax_coef(const double *__restrict__ n
 
 // dJ/dx and dJ/dg, one warp per block.  Shared memory: w[S], c[T][Sp] (Sp odd:
 // lane t reads row t without bank conflicts), d[T], the warp's ore bits.
+// Tiled adjoint (the fast path): a tile of kAdjBT blocks at a time, one per
+// lane.  The tile's grades (or values and ore words), x rows and masses go to
+// shared memory by asynchronous 4-byte copies, all in flight at once (reads
+// coalesced along each row); warp w takes scenarios w, w + 8, ... and
+// keeps, per block (lane), u = sum_s w_s v[b][s] and A[t] = sum_s c[t][s]
+// ore[b][s] for the period tile t0 .. t0 + TT - 1 in registers (period pairs,
+// paired FMAs; c is held transposed, [s][TT]); the eight warps' partial sums
+// are added in warp order; then
+//   dJ/dx[b][t] = d_t (u_b - m_b A[t]),
+//   dJ/dg[b][s] = w_s ore[b][s] m_b price recovery sum_t d_t x[b][t]  (t0 == 0),
+// both written coalesced.  Persistent: CTA i takes tiles i, i + grid, ...
+constexpr int kAdjBT = 32;
+constexpr int kAdjWarps = 8;
+
+struct AdjLayout {
+    int Sg, Wo, TT4;  // odd grade row stride, odd ore-word row stride, padded period tile
+    size_t c, w, d, D, acc, g, ow, x, m, floats;
+};
+__host__ __device__ inline AdjLayout adj_layout(int S, int T, int TT, bool rows) {
+    AdjLayout L;
+    L.Sg = S | 1;
+    L.Wo = rows ? (((S + 31) / 32) | 1) : 0;
+    L.TT4 = TT;
+    L.c = 0;                                        // [S][TT]
+    L.w = L.c + (size_t)S * TT;                     // [S]
+    L.d = L.w + S;                                  // [T]
+    L.D = L.d + T;                                  // [kAdjBT]
+    L.acc = L.D + kAdjBT;                           // [kAdjWarps][TT + 1][kAdjBT]
+    L.g = L.acc + (size_t)kAdjWarps * (TT + 1) * kAdjBT;  // [kAdjBT][Sg]
+    L.ow = L.g + (size_t)kAdjBT * L.Sg;             // [kAdjBT][Wo] (u32)
+    L.x = L.ow + (size_t)kAdjBT * L.Wo;             // [kAdjBT * T]
+    L.m = L.x + (size_t)kAdjBT * T;                 // [kAdjBT] (u32 masses)
+    L.floats = L.m + kAdjBT;
+    return L;
+}
+
+template <typename G, int TT>
+__global__ void __launch_bounds__(32 * kAdjWarps) k_relax_adj_tiled(const float *__restrict__ x,
+                                                                     const G *__restrict__ g, RelaxRows Rw,
+                                                                     const uint32_t *__restrict__ mass,
+                                                                     const float *__restrict__ w,
+                                                                     const float *__restrict__ c,
+                                                                     const double *__restrict__ disc, int32_t B,
+                                                                     int32_t S, int32_t T, int32_t Sp, int32_t t0,
+                                                                     RelaxEcon E, float *__restrict__ gx,
+                                                                     float *__restrict__ gg) {
+    constexpr bool ROWS = sizeof(G) == sizeof(double);
+    extern __shared__ __align__(16) float sm[];
+    const AdjLayout L = adj_layout(S, T, TT, ROWS);
+    float *s_c = sm + L.c, *s_w = sm + L.w, *s_d = sm + L.d, *s_D = sm + L.D;
+    float *s_acc = sm + L.acc;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nth = blockDim.x;
+    const int nt = min(TT, T - t0);
+    // per CTA: c transposed to [s][TT] (zero past the period tile), w, d
+    for (int q = nt + warp; q < TT; q += kAdjWarps)
+        for (int sc = lane; sc < S; sc += 32) s_c[(size_t)sc * TT + q] = 0.0f;
+    for (int q = warp; q < nt; q += kAdjWarps)
+        for (int sc = lane; sc < S; sc += 32) cp_async4(&s_c[(size_t)sc * TT + q], c + (size_t)(t0 + q) * Sp + sc);
+    for (int i = tid; i < S; i += nth) cp_async4(&s_w[i], w + i);
+    for (int i = tid; i < T; i += nth) s_d[i] = (float)disc[i];
+    const float prf = E.pf * E.rf;
+    const int ntile = (B + kAdjBT - 1) / kAdjBT;
+    float *s_g = sm + L.g, *s_x = sm + L.x;
+    uint32_t *s_ow = reinterpret_cast<uint32_t *>(sm + L.ow), *s_m = reinterpret_cast<uint32_t *>(sm + L.m);
+    for (int tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
+        const int b0 = tile * kAdjBT, nb = min(kAdjBT, B - b0);
+        // stage the tile: a warp per block row, lanes along the row, every
+        // copy in flight at once (the first tile's join those of c and w)
+        for (int j = warp; j < nb; j += kAdjWarps) {
+            if (ROWS) {
+                const float *row = Rw.val + (size_t)(b0 + j) * Rw.R;
+                for (int sc = lane; sc < S; sc += 32) cp_async4(&s_g[j * L.Sg + sc], row + sc);
+                for (int k = lane; k < (S + 31) / 32; k += 32) cp_async4(&s_ow[j * L.Wo + k], row + Rw.ore_off + k);
+            } else {
+                const float *row = reinterpret_cast<const float *>(g) + (size_t)(b0 + j) * S;
+                for (int sc = lane; sc < S; sc += 32) cp_async4(&s_g[j * L.Sg + sc], row + sc);
+            }
+        }
+        for (int i = tid; i < nb * T; i += nth) cp_async4(&s_x[i], x + (size_t)b0 * T + i);
+        for (int j = tid; j < nb; j += nth) cp_async4(&s_m[j], mass + b0 + j);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        __syncthreads();
+        const bool have = lane < nb;
+        const float m = have ? (float)s_m[lane] : 0.0f;
+        if (warp == 0 && have) {
+            float D = 0.0f;
+            for (int t = 0; t < T; t++) D = fmaf(s_d[t], s_x[lane * T + t], D);
+            s_D[lane] = D;
+        }
+        // per-warp sums over scenarios warp, warp + 8, ... for block `lane`
+        uint64_t a2[TT / 2];
+#pragma unroll
+        for (int q = 0; q < TT / 2; q++) a2[q] = 0ull;
+        float u = 0.0f;
+        if (have) {
+            const float *grow = s_g + lane * L.Sg;
+            for (int sc = warp; sc < S; sc += kAdjWarps) {
+                const float gv = grow[sc];
+                bool ore;
+                float val;
+                if (ROWS) {
+                    val = gv;
+                    ore = (s_ow[lane * L.Wo + (sc >> 5)] >> (sc & 31)) & 1u;
+                } else {
+                    ore = relax_ore(gv, E);
+                    const float mc = m * E.mcf;
+                    val = ore ? m * ((gv * E.pf) * E.rf - E.pcf) - mc : -mc;
+                }
+                u = fmaf(s_w[sc], val, u);
+                const float of = ore ? 1.0f : 0.0f;
+                const uint64_t of2 = rx_pack(of, of);
+                const float4 *cr = reinterpret_cast<const float4 *>(s_c + (size_t)sc * TT);
+#pragma unroll
+                for (int q = 0; q < TT / 4; q++) {
+                    const float4 c4 = cr[q];
+                    a2[2 * q] = rx_fma2(rx_pack(c4.x, c4.y), of2, a2[2 * q]);
+                    a2[2 * q + 1] = rx_fma2(rx_pack(c4.z, c4.w), of2, a2[2 * q + 1]);
+                }
+            }
+        }
+        // partial sums to shared memory: [warp][TT + 1][lane] (row TT = u)
+        float *my = s_acc + (size_t)warp * (TT + 1) * kAdjBT;
+#pragma unroll
+        for (int q = 0; q < TT / 2; q++) {
+            float lo, hi;
+            rx_unpack(a2[q], lo, hi);
+            my[(2 * q) * kAdjBT + lane] = lo;
+            my[(2 * q + 1) * kAdjBT + lane] = hi;
+        }
+        my[TT * kAdjBT + lane] = u;
+        __syncthreads();
+        // warp-order sums into warp 0's slot
+        for (int i = tid; i < (TT + 1) * kAdjBT; i += nth) {
+            float a = s_acc[i];
+#pragma unroll
+            for (int k = 1; k < kAdjWarps; k++) a += s_acc[(size_t)k * (TT + 1) * kAdjBT + i];
+            s_acc[i] = a;
+        }
+        __syncthreads();
+        // dJ/dx of the period tile and dJ/dg (once, with the first period
+        // tile): a warp per block row, lanes along the row
+        for (int j = warp; j < nb; j += kAdjWarps) {
+            const float mj = (float)s_m[j];
+            for (int q = lane; q < nt; q += 32)
+                gx[(size_t)(b0 + j) * T + t0 + q] = s_d[t0 + q] * (s_acc[TT * kAdjBT + j] - mj * s_acc[q * kAdjBT + j]);
+            if (gg && t0 == 0) {
+                const float f = mj * prf * s_D[j];
+                for (int sc = lane; sc < S; sc += 32) {
+                    bool ore;
+                    if (ROWS) ore = (s_ow[j * L.Wo + (sc >> 5)] >> (sc & 31)) & 1u;
+                    else ore = relax_ore(s_g[j * L.Sg + sc], E);
+                    gg[(size_t)(b0 + j) * S + sc] = ore ? s_w[sc] * f : 0.0f;
+                }
+            }
+        }
+        __syncthreads();  // the tile's shared data and sums are read no more before they are refilled
+    }
+}
+
 template <typename G>
 __global__ void __launch_bounds__(256) k_relax_adjoint(const float *__restrict__ x, const G *__restrict__ g,
                                                        RelaxRows Rw, const uint32_t *__restrict__ mass,
@@ -664,6 +857,38 @@ mm_status mm_relaxed_backward(mm_model *m, const float *x_dev, const float *g_de
                                                                                T, Sp, E, w, c);
     st = check_launch("k_relax_coef");
     if (st != MM_OK) return st;
+    const RelaxRows Rw{m->val, m->R, m->ore_off};
+    {
+        // the tiled path, period tiles of up to kRelaxTile, when its shared memory fits
+        const bool rows = g_dev == nullptr;
+        size_t need = 0;
+        for (int tb = 0; tb < T; tb += kRelaxTile) {
+            const int tt = (std::min(kRelaxTile, T - tb) + 3) / 4 * 4;
+            need = std::max(need, adj_layout(S, T, tt, rows).floats * sizeof(float));
+        }
+        if (need + 1024 <= (size_t)m->max_smem_optin) {
+            const int tiles = (B + kAdjBT - 1) / kAdjBT;
+            for (int tb = 0; tb < T; tb += kRelaxTile) {
+                const int tt = (std::min(kRelaxTile, T - tb) + 3) / 4 * 4;
+                const size_t sm = adj_layout(S, T, tt, rows).floats * sizeof(float);
+                const void *fn = nullptr;
+                switch (tt) {
+#define MM_ADJ_CASE(V) case V: fn = rows ? (const void *)k_relax_adj_tiled<double, V> : (const void *)k_relax_adj_tiled<float, V>; break;
+                    MM_ADJ_CASE(4) MM_ADJ_CASE(8) MM_ADJ_CASE(12) MM_ADJ_CASE(16) MM_ADJ_CASE(20) default: MM_ADJ_CASE(24)
+#undef MM_ADJ_CASE
+                }
+                MM_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm), "adjoint smem");
+                int per_sm = 1;
+                MM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 32 * kAdjWarps, sm), "occupancy");
+                const int grid = std::max(1, std::min(tiles, std::max(1, per_sm) * m->num_sms));
+                void *args[] = {(void *)&x_dev, rows ? (void *)&m->grade : (void *)&g_dev, (void *)&Rw, (void *)&m->mass,
+                                (void *)&w, (void *)&c, (void *)&m->disc, (void *)&B, (void *)&S, (void *)&T, (void *)&Sp,
+                                (void *)&tb, (void *)&E, (void *)&gx_dev, (void *)&gg_dev};
+                MM_CUDA_TRY(cudaLaunchKernel(fn, dim3(grid), dim3(32 * kAdjWarps), args, sm, m->stream), "adjoint launch");
+            }
+            return check_launch("k_relax_adj_tiled");
+        }
+    }
     const int W = (S + 31) / 32;
     const size_t smem = ((size_t)S + (size_t)T * Sp + 2 * (size_t)T) * sizeof(float) + (size_t)8 * W * sizeof(uint32_t);
     const void *fn = g_dev ? (const void *)k_relax_adjoint<float> : (const void *)k_relax_adjoint<double>;
@@ -672,7 +897,6 @@ mm_status mm_relaxed_backward(mm_model *m, const float *x_dev, const float *g_de
         MM_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), "adjoint smem");
     }
     const int blocks = std::min((B + 7) / 8, m->num_sms * 8);
-    const RelaxRows Rw{m->val, m->R, m->ore_off};
     if (g_dev)
         k_relax_adjoint<float><<<blocks, 256, smem, m->stream>>>(x_dev, g_dev, Rw, m->mass, w, c, m->disc, B, S, T, Sp,
                                                                  E, gx_dev, gg_dev);
