@@ -461,13 +461,20 @@ def gpu_arm(args):
     # the compute stream, before the step), so it is timed too.  The NPV
     # statistics are read once, after the last step.
     K2 = max(20, min(200, K))
-    moves_h = torch.from_numpy(p.moves).pin_memory()
+    # the batch travels in the compact 4-byte form (mm_unpack_moves expands it on
+    # the device) when the model allows it, else as 8-byte moves
+    packed = p.B + p.T + 1 <= 65536
+    if packed:
+        moves_h = torch.from_numpy(mm.pack_moves(p.moves, p.B, p.T).view(np.int32)).pin_memory()
+    else:
+        moves_h = torch.from_numpy(p.moves).pin_memory()
     torch.cuda.set_stream(stream)
     # the step's outputs in one device buffer (idx, top, count), read back with one copy
     out_d = torch.empty(2 * TOPK + 1, dtype=torch.int32, device=dev)
     idx_e, top_e, cnt_e = out_d[:TOPK], out_d[TOPK:2 * TOPK].view(torch.float32), out_d[2 * TOPK:]
     out_h = torch.empty(2 * TOPK + 1, dtype=torch.int32).pin_memory()
-    bufs = [moves_d, torch.empty_like(moves_d)]
+    bufs = [torch.empty_like(moves_h, device=dev) for _ in range(2)]
+    mv_e = torch.empty_like(moves_d)  # the unpacked batch of the current step
     copy_stream = torch.cuda.Stream(device=dev)
     copied = [torch.cuda.Event() for _ in range(2)]
     freed = [torch.cuda.Event() for _ in range(2)]
@@ -487,8 +494,13 @@ def gpu_arm(args):
             b = k % 2
             flush.zero_()
             stream.wait_event(copied[b])
-            m.search_step(bufs[b], k=TOPK, apply=True, score=score, feas=feas, idx=idx_e, top=top_e, count=cnt_e)
-            freed[b].record(stream)
+            if packed:
+                m.unpack_moves(bufs[b], out=mv_e)
+                freed[b].record(stream)
+                m.search_step(mv_e, k=TOPK, apply=True, score=score, feas=feas, idx=idx_e, top=top_e, count=cnt_e)
+            else:
+                m.search_step(bufs[b], k=TOPK, apply=True, score=score, feas=feas, idx=idx_e, top=top_e, count=cnt_e)
+                freed[b].record(stream)
             out_h.copy_(out_d, non_blocking=True)
             if k + 1 < steps:
                 issue_copy(k + 1)
@@ -561,11 +573,14 @@ def gpu_arm(args):
             "forward_backward_gbs": 4 * p.B * 3 * (p.T + p.S) / (rel_both_ms * 1e-3) / 1e9,
             "vs_plain_eval": {"plain_eval_ms": plain_eval_ms}},
         "e2e": {"value": evals_per_step * world / e2e_avg, "unit": UNIT,
-                "h2d_bytes_per_step": int(p.moves.nbytes), "d2h_bytes_per_step": int(out_h.numel()) * 4,
+                "h2d_bytes_per_step": int(moves_h.numel()) * moves_h.element_size(),
+                "d2h_bytes_per_step": int(out_h.numel()) * 4,
                 "ms_per_step": e2e_avg * 1e3,
-                "path": ("pinned host moves -> mm_search_step (apply on device) -> top-k and count to pinned host memory "
-                         "every step; double-buffered (batch k+1 copied on a second stream while step k runs), the host "
-                         "not waiting on each step; L2 flush inside each step; NPV statistics read after the last step")},
+                "path": (("pinned host moves in the compact 4-byte form -> mm_unpack_moves -> " if packed else
+                          "pinned host moves -> ")
+                         + "mm_search_step (apply on device) -> top-k and count to pinned host memory every step; "
+                         "double-buffered (batch k+1 copied on a second stream while step k runs), the host not waiting on "
+                         "each step; L2 flush inside each step; NPV statistics read after the last step")},
         "gpu_launches": (1 if S <= 256 else 2) * K,  # per step: the evaluation launch (top-k and apply inside when S <= 256)
         "clocks": clocks,
         "check": {"last_apply": applied, "npv_mean": npv_mean, "e2e_npv_mean": e2e_mean},

@@ -146,6 +146,18 @@ mm_status mm_schedule_get(mm_model *m, uint8_t *period_host);
 mm_status mm_eval_moves(mm_model *m, const mm_move *moves_dev, int64_t n, float *score_dev,
                         uint8_t *feasible_dev, float *mean_dev);
 
+/* Compact 4-byte moves, for moving candidate batches from host memory at half
+ * the bytes (the paper has no counterpart; its moves are generated where they
+ * are evaluated).  Packed move p = (b1 << 16) | code with b1 < 2^16 and
+ *   code < B          : swap b1 with block `code`   -> mm_move {b1, code};
+ *   code = 65535 - t  : shift b1 to period t, 0 <= t <= T (T = leave unmined)
+ *                                                   -> mm_move {b1, -t - 1};
+ * usable when B + T + 1 <= 65536 (MM_ERR_INVALID_ARG otherwise).  Codes between
+ * B and 65535 - T, and b1 >= B, decode to a bad move {-1, -1}, which the
+ * evaluator flags as such.  packed_dev[n] (4-byte aligned) and moves_dev[n]
+ * (8-byte aligned): device memory; n = 0 is allowed.  Asynchronous. */
+mm_status mm_unpack_moves(mm_model *m, const uint32_t *packed_dev, int64_t n, mm_move *moves_dev);
+
 /* Violation magnitudes of n moves against the current schedule, for the
  * epsilon-relaxed fitness of the paper's search (Algorithm 2: fitness =
  * NPV - penalty max(0, violation - epsilon); Section 6, Phase 2).  The paper

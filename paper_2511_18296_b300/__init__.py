@@ -79,6 +79,7 @@ SIGNATURES = [
     ("mm_eval_moves", C.c_int, [P, P, I64, P, P, P]),
     ("mm_eval_moves_ex", C.c_int, [P, P, I64, P, P, P, P, I32]),
     ("mm_eval_violation", C.c_int, [P, P, I64, P, P]),
+    ("mm_unpack_moves", C.c_int, [P, P, I64, P]),
     ("mm_set_tile", C.c_int, [P, I32, I32, I32, I32]),
     ("mm_topk", C.c_int, [P, P, P, I64, I32, P, P, P]),
     ("mm_topk_noalloc", C.c_int, [P, P, I64, I32, P, P, P, P]),
@@ -149,6 +150,20 @@ def topk_noalloc(score, feas, k: int, idx, top, count, stream=None):
     _check(lib().mm_topk_noalloc(_ptr(score), _ptr(feas), int(score.shape[0]), int(k), _ptr(idx), _ptr(top),
                                  _ptr(count), _stream_handle(stream)))
     return idx, top, count
+
+
+def pack_moves(moves, B: int, T: int) -> np.ndarray:
+    """Host-side compact form of a move batch for mm_unpack_moves: uint32
+    (b1 << 16) | code, code = the swap partner, or 65535 - t for a shift to
+    period t.  Needs B + T + 1 <= 65536 and valid moves (checked here)."""
+    mv = np.asarray(moves, dtype=np.int64).reshape(-1, 2)
+    if B + T + 1 > 65536:
+        raise ValueError(f"packed moves need B + T + 1 <= 65536 (B = {B}, T = {T})")
+    b1, arg = mv[:, 0], mv[:, 1]
+    if ((b1 < 0) | (b1 >= B)).any() or ((arg >= B) | (arg < -(T + 1))).any():
+        raise ValueError("a move is out of range for this model")
+    code = np.where(arg >= 0, arg, 65535 - (-arg - 1))
+    return np.ascontiguousarray(((b1 << 16) | code).astype(np.uint32))
 
 
 class Model:
@@ -249,6 +264,16 @@ class Model:
             _check(L.mm_eval_moves_ex(self.h, _ptr(moves), n, _ptr(score), _ptr(feas), _ptr(mean), _ptr(delta),
                                       opts))
         return score, feas, mean
+
+    def unpack_moves(self, packed, out=None):
+        """mm_unpack_moves: uint32 packed moves (device) -> int32 [n, 2] moves (device)."""
+        import torch
+        assert packed.is_cuda and packed.dtype in (torch.int32, torch.uint32) and packed.is_contiguous()
+        n = packed.shape[0]
+        if out is None:
+            out = torch.empty((n, 2), dtype=torch.int32, device=packed.device)
+        _check(lib().mm_unpack_moves(self.h, _ptr(packed), n, _ptr(out)))
+        return out
 
     def eval_violation(self, moves, cap_excess=None, prec_excess=None):
         """mm_eval_violation: (capacity excess int64 [n] in tonnes, precedence
