@@ -184,6 +184,32 @@ def cpu_baseline(p, budget_s: float = 12.0):
             "bruteforce_value": bf_rate}
 
 
+def accuracy_report(p, sel, gpu, k: int = 32):
+    """Error of the GPU scores against the FP64 oracle's on a sample of the
+    batch: the largest |gpu - ref| / max(|ref|, F) (F = the oracle's scale of
+    the summed terms), whether the flags agree bit for bit, and whether the
+    sample's top-k indices agree (ties within the bound allowed to swap)."""
+    import oracle as O
+    import workloads as W
+    out = {"sample": f"{len(sel)} moves of the batch (seed 5) at the initial schedule", "bound": 1e-5}
+    for form, sig in (("plain", None), ("compensated", None), ("weighted", W.uncertainty_weights(p.T, p.S))):
+        om = O.OracleModel(p, sigma=sig)
+        ref = om.eval_incremental(p.x0, p.moves[sel])
+        score, flag = gpu[form]
+        r, f = ref["score"], ref["floor"]
+        ok = np.isfinite(r)
+        err = np.abs(score[ok].astype(np.float64) - r[ok]) / np.maximum(np.abs(r[ok]), np.maximum(f[ok], 1e-300))
+        gi, _ = O.topk(score.astype(np.float64), flag, k)
+        ri, rtop = O.topk(r, ref["flag"], k)
+        same = np.array_equal(gi, ri)
+        if not same and len(gi) == len(ri):
+            # a swap is allowed only inside a certified near-tie of the oracle's scores
+            same = bool(np.all(np.abs(r[gi] - r[ri]) <= 1e-5 * np.maximum(np.abs(r[ri]), f[ri])))
+        out[form] = {"max_rel_err": float(err.max()) if err.size else 0.0,
+                     "flags_equal": bool(np.array_equal(flag, ref["flag"])), "topk_agrees": bool(same)}
+    return out
+
+
 def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -450,6 +476,19 @@ def gpu_arm(args):
     w_eval_ms = float(np.mean(steps_ms(graph_of([w_eval]), Kp)))
     mw.schedule_set(p.x0)
     w_step_ms = float(np.mean(steps_ms(graph_of([w_step]), Kp)))
+    # scores of a seeded sample of the batch at the initial schedule, for the
+    # accuracy report against the FP64 oracle (made in the CPU leg)
+    acc_sel = np.sort(np.random.default_rng(5).choice(n, min(n, 4096), replace=False))
+    mv_acc = torch.as_tensor(p.moves[acc_sel], device=dev)
+    acc_gpu = {}
+    with torch.cuda.stream(stream):
+        mw.schedule_set(p.x0)
+        acc_gpu["weighted"] = mw.eval_moves(mv_acc, want_mean=False)
+        m.schedule_set(p.x0)
+        acc_gpu["plain"] = m.eval_moves(mv_acc, want_mean=False)
+        acc_gpu["compensated"] = m.eval_moves(mv_acc, want_mean=False, kahan=True)
+    stream.synchronize()
+    acc_gpu = {k: (v[0].cpu().numpy(), v[1].cpu().numpy()) for k, v in acc_gpu.items()}
     mw.close()
 
     # end to end through the public API with host buffers: every step copies
@@ -589,6 +628,7 @@ def gpu_arm(args):
         line["batched_form"] = batched_form(stream, flush)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(p, budget_s=args.cpu_budget)
+        line["accuracy"] = accuracy_report(p, acc_sel, acc_gpu)
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
