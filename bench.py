@@ -210,6 +210,18 @@ def accuracy_report(p, sel, gpu, k: int = 32):
     return out
 
 
+def drift_report(p, x_final, npv64, npv32, n_apply: int):
+    """NPV_s of the device's running FP64 totals and of their FP32 shadow after
+    n_apply applies, against the oracle's full FP64 recomputation of the same
+    schedule: the largest relative difference over scenarios."""
+    import oracle as O
+    ref = O.OracleModel(p).npv(x_final)
+    scale = np.maximum(np.abs(ref), 1.0)
+    return {"applies": n_apply, "workload": "the bench batch, search steps with apply from the initial schedule",
+            "fp64_running_max_rel": float(np.max(np.abs(npv64 - ref) / scale)),
+            "fp32_shadow_max_rel": float(np.max(np.abs(npv32 - ref) / scale))}
+
+
 def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -554,6 +566,19 @@ def gpu_arm(args):
     e2e_mean = e2e_run(K2)
     e2e_avg = (time.perf_counter() - t0) / K2
 
+    # precision: the FP64 running totals beside an FP32 shadow of them over
+    # 1,000 device applies (untimed); the CPU leg compares both with the
+    # oracle's full FP64 recomputation of the final schedule
+    N_APPLY = 1000
+    m.set_fp32_shadow(True)
+    m.schedule_set(p.x0)
+    with torch.cuda.stream(stream):
+        for _ in range(N_APPLY):
+            m.search_step(moves_d, k=TOPK, apply=True, score=score, feas=feas, idx=idx, top=top, count=cnt)
+    stream.synchronize()
+    drift_gpu = (m.schedule_get(), m.npv()[0], m.fp32_shadow_npv())
+    m.set_fp32_shadow(False)
+
 
     # max over ranks
     local_vals = torch.tensor([total_ms, step_avg_ms, e2e_avg, plain_step_ms, plain_eval_ms],
@@ -591,7 +616,9 @@ def gpu_arm(args):
                        "value": evals_per_step * world / (plain_step_ms * 1e-3), "unit": UNIT,
                        "ms_per_step": plain_step_ms, "eval_kernel_ms": plain_eval_ms,
                        "eval_roofline_frac": achieved_gbs / peaks["hbm_gbs"], "eval_achieved_gbs": achieved_gbs},
-        "precision_form": {"desc": "mm_eval_moves_ex with compensated scenario sums (MM_EVAL_KAHAN)",
+        "precision_form": {"desc": "mm_eval_moves_ex with compensated scenario sums (MM_EVAL_KAHAN); drift: NPV from "
+                                   "the FP64 running totals and from an FP32 shadow after 1,000 applies, against the "
+                                   "oracle's recomputation",
                            "eval_kernel_ms": kahan_eval_ms,
                            "eval_roofline_frac": alg / (kahan_eval_ms * 1e-3) / 1e9 / peaks["hbm_gbs"]},
         "weighted_form": {"desc": "uncertainty weights sigma(s,t) of Eq. 12 (synthetic, seed 4) on the same model and "
@@ -629,6 +656,7 @@ def gpu_arm(args):
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(p, budget_s=args.cpu_budget)
         line["accuracy"] = accuracy_report(p, acc_sel, acc_gpu)
+        line["precision_form"]["drift"] = drift_report(p, *drift_gpu, n_apply=N_APPLY)
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
