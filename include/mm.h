@@ -386,8 +386,9 @@ mm_status mm_get_metal(mm_model *m, double *metal_host);
  *
  * mm_relaxed_forward: x_dev[B][T] FP32 -> *J_dev, npv_dev[S] and ore_t_dev[T][S]
  * (FP64, device).  ore_t_dev is the per-period checkpoint O[t][s] that the
- * adjoint reads.  Products in FP32, chunk sums of 128 blocks in FP32, the rest
- * in FP64 (deterministic).
+ * adjoint reads.  Products and each CTA's sums over its range of blocks in
+ * FP32, the ranges' sums added by compensated FP32 in a fixed order, the
+ * penalty, NPV_s and J in FP64 (deterministic).
  * mm_relaxed_backward: given the forward's npv_dev and ore_t_dev and the
  * upstream gradient *gJ_dev (FP64, device), writes gx_dev[B][T] = dJ/dx and,
  * if gg_dev is not NULL, gg_dev[B][S] = dJ/dg (FP32, device).  Where every
@@ -400,6 +401,19 @@ mm_status mm_relaxed_forward(mm_model *m, const float *x_dev, const float *g_dev
 mm_status mm_relaxed_backward(mm_model *m, const float *x_dev, const float *g_dev, double beta, double m_ref,
                               const double *npv_dev, const double *ore_t_dev, const double *gJ_dev,
                               float *gx_dev, float *gg_dev);
+
+/* The relaxed gradient as a first-order prior over candidate moves: at the
+ * model's current schedule read as the one-hot x (x[b][t] = 1 at b's period,
+ * none when unmined), moving block b from t1 to t2 changes x by -1 at (b, t1)
+ * and +1 at (b, t2), so for the gradient gx_dev[B][T] = dJ/dx at that x
+ *   shift b1: t1 -> t2 : prior = gx[b1][t2] - gx[b1][t1],
+ *   swap b1 (t1) with b2 (t2): prior = (gx[b1][t2] - gx[b1][t1])
+ *                                    + (gx[b2][t1] - gx[b2][t2]),
+ * with gx[b][T] read as 0 (unmined).  prior_dev[n] (FP32, device); a bad move
+ * gets -infinity and raises the sticky MM_ERR_BAD_MOVE.  A ranking aid only:
+ * feasibility and the exact delta stay with mm_eval_moves.  Asynchronous. */
+mm_status mm_relaxed_move_prior(mm_model *m, const float *gx_dev, const mm_move *moves_dev, int64_t n,
+                                float *prior_dev);
 
 /* ---- Precision study: FP32 shadow accumulators (no counterpart in the paper) ----
  * The model keeps its running per-period, per-scenario metal and NPV

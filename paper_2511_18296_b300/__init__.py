@@ -80,6 +80,7 @@ SIGNATURES = [
     ("mm_eval_moves_ex", C.c_int, [P, P, I64, P, P, P, P, I32]),
     ("mm_eval_violation", C.c_int, [P, P, I64, P, P]),
     ("mm_unpack_moves", C.c_int, [P, P, I64, P]),
+    ("mm_relaxed_move_prior", C.c_int, [P, P, P, I64, P]),
     ("mm_set_tile", C.c_int, [P, I32, I32, I32, I32]),
     ("mm_topk", C.c_int, [P, P, P, I64, I32, P, P, P]),
     ("mm_topk_noalloc", C.c_int, [P, P, I64, I32, P, P, P, P]),
@@ -350,6 +351,16 @@ class Model:
         return v
 
     # -- relaxed objective ------------------------------------------------
+    def relaxed_move_prior(self, gx, moves, prior=None):
+        """mm_relaxed_move_prior: first-order change of the relaxed J for each
+        move at the current schedule, from gx = dJ/dx [B, T] (device)."""
+        import torch
+        n = moves.shape[0]
+        if prior is None:
+            prior = torch.empty(n, dtype=torch.float32, device=moves.device)
+        _check(lib().mm_relaxed_move_prior(self.h, _ptr(gx), _ptr(moves), n, _ptr(prior)))
+        return prior
+
     def relaxed_forward(self, x, g=None, beta: float = 10.0, m_ref: float = 10_000.0):
         """J (float64 [1]), NPV_s (float64 [S]) and the checkpoint O[t][s]
         (float64 [T][S]) of the relaxed objective for x float32 [B][T] (CUDA);

@@ -807,11 +807,53 @@ static mm_status relax_check(mm_model *m, const float *x, double beta, double m_
     return MM_OK;
 }
 
+// First-order prior of candidate moves from dJ/dx at the one-hot schedule:
+// one thread per move, the periods from the packed schedule words.
+__global__ void __launch_bounds__(256) k_relax_prior(const float *__restrict__ gx, const int2 *__restrict__ moves,
+                                                     int64_t n, int32_t B, int32_t T,
+                                                     const uint32_t *__restrict__ blk, uint32_t *status,
+                                                     float *__restrict__ prior) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const int2 mv = __ldg(moves + i);
+        const bool swap = mv.y >= 0;
+        const int64_t tn = -(int64_t)mv.y - 1;
+        const bool valid = mv.x >= 0 && mv.x < B && (swap ? mv.y < B : (tn >= 0 && tn <= (int64_t)T));
+        if (!valid) {
+            prior[i] = -INFINITY;
+            atomicOr(status, kStBadMove);
+            continue;
+        }
+        auto g = [&](int32_t b, uint32_t t) { return t < (uint32_t)T ? __ldg(gx + (size_t)b * T + t) : 0.0f; };
+        const uint32_t t1 = blk_period(__ldg(blk + mv.x));
+        if (swap) {
+            const uint32_t t2 = blk_period(__ldg(blk + mv.y));
+            prior[i] = (g(mv.x, t2) - g(mv.x, t1)) + (g(mv.y, t1) - g(mv.y, t2));
+        } else {
+            prior[i] = g(mv.x, (uint32_t)tn) - g(mv.x, t1);
+        }
+    }
+}
+
 }  // namespace mm
 
 using namespace mm;
 
 extern "C" {
+
+mm_status mm_relaxed_move_prior(mm_model *m, const float *gx_dev, const mm_move *moves, int64_t n, float *prior) {
+    if (!m) return set_error(MM_ERR_INVALID_ARG, "NULL model");
+    if (!m->has_schedule) return set_error(MM_ERR_STATE, "no schedule installed");
+    if (n < 0) return set_error(MM_ERR_INVALID_ARG, "negative move count");
+    if (n == 0) return MM_OK;
+    if (!gx_dev || !moves || !prior) return set_error(MM_ERR_INVALID_ARG, "NULL gradient, move or output pointer");
+    if (((uintptr_t)moves & 7u) != 0) return set_error(MM_ERR_INVALID_ARG, "moves must be 8-byte aligned");
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > (int64_t)m->num_sms * 8) blocks = (int64_t)m->num_sms * 8;
+    k_relax_prior<<<(unsigned)blocks, 256, 0, m->stream>>>(gx_dev, reinterpret_cast<const int2 *>(moves), n, m->B,
+                                                            m->T, m->blk, m->status, prior);
+    return check_launch("k_relax_prior");
+}
 
 mm_status mm_relaxed_forward(mm_model *m, const float *x_dev, const float *g_dev, double beta, double m_ref,
                              double *J_dev, double *npv_dev, double *ore_t_dev) {
