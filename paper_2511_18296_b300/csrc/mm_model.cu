@@ -17,6 +17,7 @@
 //                               in period t, scenario s (uniform block mass)
 #include <cmath>
 #include <cstdarg>
+#include <cstdlib>
 #include <cstring>
 #include <limits>
 #include <numeric>
@@ -351,6 +352,14 @@ template <typename T>
 static mm_status dalloc(T **p, size_t count, const char *what) {
     size_t bytes = count * sizeof(T);
     if (bytes == 0) bytes = sizeof(T);
+    // host-side fault injection for tests: with MM_ALLOC_CAP_BYTES set, an
+    // allocation larger than it fails as out of memory before any CUDA call
+    if (const char *cap = std::getenv("MM_ALLOC_CAP_BYTES")) {
+        if (*cap && bytes > (size_t)std::strtoull(cap, nullptr, 10)) {
+            *p = nullptr;
+            return set_error(MM_ERR_OOM, "%s: %zu bytes exceed MM_ALLOC_CAP_BYTES", what, bytes);
+        }
+    }
     cudaError_t e = cudaMalloc((void **)p, bytes);
     if (e != cudaSuccess) {
         *p = nullptr;

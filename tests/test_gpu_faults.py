@@ -1,0 +1,103 @@
+"""Failure handling without any GPU fault: invalid arguments are refused on
+the host with MM_ERR_INVALID_ARG / MM_ERR_STATE; a corrupted move list is
+flagged (flag 0, score -inf, sticky MM_ERR_BAD_MOVE on the next synchronising
+call) and leaves the model usable; an allocation cap (host-side injection,
+MM_ALLOC_CAP_BYTES) turns model creation into MM_ERR_OOM with nothing left
+allocated.  Nothing here traps, faults or hangs the GPU."""
+
+import ctypes as C
+import os
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+INVALID_ARG, OOM, BAD_MOVE, STATE = 1, 3, 6, 8
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+
+
+def _mm():
+    import paper_2511_18296_b300 as mm
+    return mm
+
+
+def test_invalid_arguments_refused_on_the_host():
+    mm = _mm()
+    L = mm.lib()
+    p = W.config("plain_4k")
+    m = mm.Model.from_problem(p)
+    n = p.moves.shape[0]
+    mv = torch.as_tensor(p.moves, device="cuda")
+    score = torch.empty(n, device="cuda")
+    feas = torch.empty(n, dtype=torch.uint8, device="cuda")
+    # no schedule installed yet
+    assert L.mm_eval_moves(m.h, mv.data_ptr(), n, score.data_ptr(), feas.data_ptr(), None) == STATE
+    m.schedule_set(p.x0)
+    assert L.mm_eval_moves(None, mv.data_ptr(), n, score.data_ptr(), feas.data_ptr(), None) == INVALID_ARG
+    assert L.mm_eval_moves(m.h, mv.data_ptr(), -1, score.data_ptr(), feas.data_ptr(), None) == INVALID_ARG
+    assert L.mm_eval_moves(m.h, mv.data_ptr() + 4, n - 1, score.data_ptr(), feas.data_ptr(), None) == INVALID_ARG
+    assert L.mm_eval_moves(m.h, None, n, score.data_ptr(), feas.data_ptr(), None) == INVALID_ARG
+    idx = torch.empty(32, dtype=torch.int32, device="cuda")
+    top = torch.empty(32, device="cuda")
+    cnt = torch.empty(1, dtype=torch.int32, device="cuda")
+    for k in (0, 1025):
+        assert L.mm_topk(m.h, score.data_ptr(), feas.data_ptr(), n, k, idx.data_ptr(), top.data_ptr(),
+                         cnt.data_ptr()) == INVALID_ARG
+    bad = p.x0.copy()
+    bad[0] = p.T + 1
+    assert L.mm_schedule_set(m.h, bad.ctypes.data, None) == INVALID_ARG
+    assert L.mm_last_error().decode()  # a message explains each refusal
+    # the model still works
+    s1, f1, _ = m.eval_moves(mv, want_mean=False)
+    torch.cuda.synchronize()
+    assert f1.cpu().numpy().sum() > 0
+
+
+def test_corrupted_move_list_is_flagged_and_the_model_stays_usable():
+    mm = _mm()
+    p = W.config("plain_4k")
+    m = mm.Model.from_problem(p)
+    m.schedule_set(p.x0)
+    rng = np.random.default_rng(13)
+    junk = rng.integers(-2**31, 2**31 - 1, size=(5000, 2), dtype=np.int64).astype(np.int32)
+    junk[:10] = p.moves[:10]  # a few genuine moves among the garbage
+    s, f, _ = m.eval_moves(torch.as_tensor(junk, device="cuda"), want_mean=False)
+    torch.cuda.synchronize()
+    s, f = s.cpu().numpy(), f.cpu().numpy()
+    valid = (junk[:, 0] >= 0) & (junk[:, 0] < p.B) & (((junk[:, 1] >= 0) & (junk[:, 1] < p.B)) |
+                                                     ((junk[:, 1] < 0) & (junk[:, 1] >= -(p.T + 1))))
+    assert np.all(f[~valid] == 0) and np.all(np.isneginf(s[~valid]))
+    with pytest.raises(mm.MMError) as e:
+        m.npv()
+    assert e.value.status == BAD_MOVE
+    # cleared by the read: the same model evaluates the genuine batch as a fresh one does
+    fresh = mm.Model.from_problem(p)
+    fresh.schedule_set(p.x0)
+    mv = torch.as_tensor(p.moves, device="cuda")
+    a = m.eval_moves(mv, want_mean=False)[0].cpu().numpy()
+    b = fresh.eval_moves(mv, want_mean=False)[0].cpu().numpy()
+    assert np.array_equal(a.view(np.uint32), b.view(np.uint32))
+    m.npv()  # no sticky status left
+
+
+def test_allocation_cap_gives_out_of_memory():
+    mm = _mm()
+    p = W.config("plain_4k")
+    os.environ["MM_ALLOC_CAP_BYTES"] = "100000"  # the 4k model's FP64 grade array alone is 4,000 x 16 x 8 = 512,000 bytes
+    try:
+        with pytest.raises(mm.MMError) as e:
+            mm.Model.from_problem(p)
+        assert e.value.status == OOM
+    finally:
+        del os.environ["MM_ALLOC_CAP_BYTES"]
+    m = mm.Model.from_problem(p)  # without the cap the same model is created and works
+    m.schedule_set(p.x0)
+    m.npv()
