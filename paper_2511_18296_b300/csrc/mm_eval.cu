@@ -299,10 +299,17 @@ mm_status eval_launch(mm_model *m, const mm_move *moves, int64_t n, float *score
                        : pick_tiled_plain(team, qmax, want_delta, tsm, use_tma);
     }
     if (!fn) return set_error(MM_ERR_INVALID_ARG, "no evaluator for team %d with %d quads per lane", team, qpl);
-    // the 48 KB default covers static + dynamic shared memory (~12 KB static here)
-    if (smem + 16 * 1024 > 48 * 1024 && m->smem_attr[(const void *)fn] < smem) {
-        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return cuda_status(e, "set evaluator shared memory");
+    // the 48 KB default covers static + dynamic shared memory; a kernel whose
+    // static part (up to ~32 KB with the in-launch apply) and dynamic part
+    // exceed it opts in (once per kernel and size)
+    if (m->smem_attr[(const void *)fn] < smem) {
+        cudaFuncAttributes fa;
+        cudaError_t e = cudaFuncGetAttributes(&fa, fn);
+        if (e != cudaSuccess) return cuda_status(e, "evaluator attributes");
+        if (fa.sharedSizeBytes + smem > 48 * 1024) {
+            e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return cuda_status(e, "set evaluator shared memory");
+        }
         m->smem_attr[(const void *)fn] = smem;
     }
     int per_sm = ctas_per_sm;

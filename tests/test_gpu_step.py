@@ -172,3 +172,15 @@ def test_step_state_matches_rebuild(name, steps):
         np.testing.assert_allclose(a.metal(), fresh.metal(), rtol=1e-12, atol=1e-6)
         npv_a, npv_f = a.npv()[0], fresh.npv()[0]
         np.testing.assert_allclose(npv_a, npv_f, rtol=1e-12, atol=1e-3)
+
+
+def test_step_run_time_shaped_loop_large_tables():
+    """S = 101 (not a multiple of 4), T = 30: the run-time-shaped step kernel
+    with its penalty tables staged in shared memory (25.8 KB) on top of the
+    in-launch apply's static buffers, past the 48 KB default."""
+    p = tiny_problem(8, 8, 4, S=101, T=30, seed=6, cap_blocks=12, target_blocks=5)
+    a, b = _pair(p)
+    mv = torch.as_tensor(all_moves(p.B, p.T)[::7].copy(), device="cuda")
+    for _ in range(3):
+        _compare(a.search_step(mv, k=8, apply=True), _separate(b, mv, 8, True), 8)
+    assert np.array_equal(a.schedule_get(), b.schedule_get())
