@@ -204,6 +204,7 @@ __global__ void __launch_bounds__(kFwdSW * kFwdGroups) k_relax_fwd(const float *
                 if (ROWS) w_n = __float_as_uint(s_g[st][j][kFwdSW + (lt >> 5)]);
                 m_n = s_m[st][j];
             }
+#pragma unroll 4
             for (; j < nb; j += kFwdGroups) {
                 const float gv = g_n, m = (float)m_n;
                 const uint32_t ow = w_n;
