@@ -622,8 +622,8 @@ def gpu_arm(args):
                            "eval_kernel_ms": kahan_eval_ms,
                            "eval_roofline_frac": alg / (kahan_eval_ms * 1e-3) / 1e9 / peaks["hbm_gbs"]},
         "weighted_form": {"desc": "uncertainty weights sigma(s,t) of Eq. 12 (synthetic, seed 4) on the same model and "
-                                  "batch: evaluation launch, and the step as separate evaluation, top-k and apply "
-                                  "launches",
+                                  "batch: evaluation launch, and the fused step (evaluate + top-32 + apply, one "
+                                  "launch)",
                           "eval_kernel_ms": w_eval_ms,
                           "eval_roofline_frac": alg / (w_eval_ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
                           "step_ms": w_step_ms,

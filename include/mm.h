@@ -107,9 +107,10 @@ typedef struct {
  * ore ? m((g*price)*recovery - pc) : 0, every NPV is
  *   NPV_s = sum_t d_t (sigma(s,t) margin_t,s - mc mined_t - pen_t(ore_t,s)),
  * the evaluator reads a [T+1][T+1][S_pad] FP32 table of the weighted discount
- * differences sigma(s,b) d_b - sigma(s,a) d_a, mm_search_step runs as the
- * separate evaluation, top-k and apply launches, and the relaxed objective and
- * the batched evaluator refuse the model (MM_ERR_INVALID_ARG).
+ * differences sigma(s,b) d_b - sigma(s,a) d_a, mm_search_step is one launch
+ * when the weighted fast form applies (equal masses, S % 4 == 0) and runs as the
+ * separate evaluation, top-k and apply launches otherwise, and the relaxed
+ * objective and the batched evaluator refuse the model (MM_ERR_INVALID_ARG).
  * Errors: MM_ERR_INVALID_ARG (NULL, sizes, non-finite or negative grade or
  * weight, zero mass, bad CSR), MM_ERR_OVERFLOW, MM_ERR_OOM, MM_ERR_CUDA. */
 mm_status mm_model_create(const mm_model_desc *desc, mm_model **out);

@@ -34,6 +34,17 @@ EvalFn pick_tiled_kahan(int team, int qmax, bool delta, bool tsm, bool tma);
 EvalFn pick_fast_plain(int team, int kf, bool tail, bool delta);
 EvalFn pick_fast_kahan(int team, int kf, bool tail, bool delta);
 EvalFn pick_fast_sigma(int team, int kf, bool tail, bool delta);
+EvalFn pick_step_sigma(int team, int kf, bool tail);
+
+// The weighted fast form applies: equal masses, the period-pair table kept,
+// S % 4 == 0 and 1..4 full quad iterations per lane at the model's team.
+bool sigma_fast_ok(const mm_model *m, int options) {
+    if (!m->sig || !m->uniform_mass || !m->ctab || m->S % 4 != 0) return false;
+    if (options & (MM_EVAL_KAHAN | MM_EVAL_GENERIC)) return false;
+    const int team = m->team > 0 ? m->team : default_team(m->S);
+    const int kf = ((m->S + 3) / 4) / team;
+    return kf >= 1 && kf <= 4;
+}
 EvalFn pick_step(int team, bool fast, int kf, bool tail, int qmax, bool tsm);
 ApplyArgs apply_args(mm_model *m);
 
@@ -224,15 +235,26 @@ mm_status eval_launch(mm_model *m, const mm_move *moves, int64_t n, float *score
     }
     const bool kahan = (options & MM_EVAL_KAHAN) != 0;
     const bool want_delta = delta != nullptr;
-    if (m->sig && step) return set_error(MM_ERR_INVALID_ARG, "the fused step does not take uncertainty weights");
-    if (m->sig && m->uniform_mass && !kahan && !(options & MM_EVAL_GENERIC) && m->ctab && m->S % 4 == 0) {
-        // weighted fast form (direct loads)
+    if (m->sig && step && !sigma_fast_ok(m, options))
+        return set_error(MM_ERR_INVALID_ARG, "the fused step takes uncertainty weights in the fast form only");
+    if (sigma_fast_ok(m, options) && (team <= 0 || team == (m->team > 0 ? m->team : default_team(m->S)))) {
+        // weighted fast form (direct loads), evaluation or the fused step
         if (team <= 0) team = default_team(m->S);
         const int nq = (m->S + 3) / 4, kf = nq / team;
-        EvalFn fn = (kf >= 1 && kf <= 4) ? pick_fast_sigma(team, kf, nq % team != 0, want_delta) : nullptr;
+        EvalFn fn = step ? pick_step_sigma(team, kf, nq % team != 0) : pick_fast_sigma(team, kf, nq % team != 0, want_delta);
         if (fn) {
             const int T1 = m->T + 1;
             const size_t smem = (((size_t)T1 * T1 * sizeof(float) + 15) & ~(size_t)15) + 2 * (size_t)T1 * sizeof(int64_t);
+            if (m->smem_attr[(const void *)fn] < smem) {
+                cudaFuncAttributes fa;
+                cudaError_t e = cudaFuncGetAttributes(&fa, fn);
+                if (e != cudaSuccess) return cuda_status(e, "evaluator attributes");
+                if (fa.sharedSizeBytes + smem > 48 * 1024) {
+                    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                    if (e != cudaSuccess) return cuda_status(e, "set evaluator shared memory");
+                }
+                m->smem_attr[(const void *)fn] = smem;
+            }
             int per_sm = ctas_per_sm;
             if (per_sm <= 0) {
                 const mm_status os = eval_occupancy(fn, smem, &per_sm);
@@ -241,13 +263,17 @@ mm_status eval_launch(mm_model *m, const mm_move *moves, int64_t n, float *score
             A.qpl = (nq + team - 1) / team;
             const int64_t chunks = (n + kChunk - 1) / kChunk;
             int64_t blocks = (chunks + kEvalThreads / 32 - 1) / (kEvalThreads / 32);
-            const int64_t grid_cap = (int64_t)m->num_sms * per_sm;
+            int64_t grid_cap = (int64_t)m->num_sms * per_sm;
+            if (step && grid_cap > m->step_max_ctas) grid_cap = m->step_max_ctas;
             if (blocks > grid_cap) blocks = grid_cap;
             if (blocks < 1) blocks = 1;
+            if (step) const_cast<StepOut *>(step)->grid = (int)blocks;
+            A.tail.L = step_lists(m, (int)blocks);
             fn<<<(unsigned)blocks, kEvalThreads, smem, m->stream>>>(A);
             return check_launch("k_eval_tiled");
         }
     }
+    if (m->sig && step) return set_error(MM_ERR_INVALID_ARG, "no weighted step kernel for this tile");
     if (!m->uniform_mass || m->sig) {
         EvalFn fn = want_delta ? k_eval_general<true> : k_eval_general<false>;
         int64_t blocks = (n + 7) / 8;

@@ -24,6 +24,32 @@ static EvalFn fast2(int kf, bool tail, bool delta) {
     return nullptr;
 }
 
+// The fused search step's weighted form (top-k and in-launch apply).
+template <int TEAM>
+static EvalFn step2(int kf, bool tail) {
+    switch (kf) {
+        case 1: return tail ? k_eval_tiled<TEAM, 1, false, false, false, 1, true, true, true>
+                            : k_eval_tiled<TEAM, 1, false, false, false, 1, false, true, true>;
+        case 2: return tail ? k_eval_tiled<TEAM, 1, false, false, false, 2, true, true, true>
+                            : k_eval_tiled<TEAM, 1, false, false, false, 2, false, true, true>;
+        case 3: return tail ? k_eval_tiled<TEAM, 1, false, false, false, 3, true, true, true>
+                            : k_eval_tiled<TEAM, 1, false, false, false, 3, false, true, true>;
+        case 4: return tail ? k_eval_tiled<TEAM, 1, false, false, false, 4, true, true, true>
+                            : k_eval_tiled<TEAM, 1, false, false, false, 4, false, true, true>;
+    }
+    return nullptr;
+}
+
+EvalFn pick_step_sigma(int team, int kf, bool tail) {
+    switch (team) {
+        case 4: return step2<4>(kf, tail);
+        case 8: return step2<8>(kf, tail);
+        case 16: return step2<16>(kf, tail);
+        case 32: return step2<32>(kf, tail);
+    }
+    return nullptr;
+}
+
 EvalFn pick_fast_sigma(int team, int kf, bool tail, bool delta) {
     switch (team) {
         case 4: return fast2<4>(kf, tail, delta);

@@ -140,6 +140,7 @@ struct StepOut {
 mm_status eval_launch(mm_model *m, const mm_move *moves, int64_t n, float *score, uint8_t *feas, float *mean,
                       float *delta, int32_t options, int team, int ctas_per_sm, int stages, const StepOut *step);
 int default_team(int S);
+bool sigma_fast_ok(const mm_model *m, int options);  // the weighted fast form (and fused step) applies
 // Top-k for k <= 32 through per-CTA warp lists and the step finisher.
 mm_status topk_small_launch(mm_model *m, const float *score, const uint8_t *feas, int64_t n, int32_t k, int32_t *idx,
                             float *top, int32_t *count);

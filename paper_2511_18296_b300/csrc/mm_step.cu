@@ -146,8 +146,9 @@ extern "C" mm_status mm_search_step(mm_model *m, const mm_move *moves, int64_t n
         MM_CUDA_TRY(cudaMemsetAsync(count, 0, sizeof(int32_t), m->stream), "clear count");
         return apply ? mm_apply_best(m, moves, 0, idx, count) : MM_OK;
     }
-    if (m->sig) {
-        // uncertainty weights: the separate evaluation, top-k and apply launches
+    if (m->sig && !sigma_fast_ok(m, MM_EVAL_PLAIN)) {
+        // uncertainty weights outside the weighted fast form: the separate
+        // evaluation, top-k and apply launches
         st = eval_launch(m, moves, n, score, feas, nullptr, nullptr, MM_EVAL_PLAIN, m->team, m->ctas_per_sm, 0,
                          nullptr);
         if (st == MM_OK) st = mm_topk(m, score, feas, n, k, idx, top, count);

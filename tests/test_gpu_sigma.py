@@ -5,9 +5,10 @@ weighted discount differences; the fast evaluator (S % 4 == 0, equal masses)
 and the general one (any S, unequal masses, the compensated or generic
 option) must both match the oracle's weighted deltas within the usual FP32
 bound, the flags bit for bit; applies must keep the FP64 NPV equal to the
-oracle's weighted NPV of the new schedule; the search step (separate launches
-for a weighted model) must match the separate calls.  With all weights 1 the
-NPV equals the unweighted model's bit for bit.
+oracle's weighted NPV of the new schedule; the search step (one fused launch
+in the weighted fast form) must match the separate calls bit for bit and keep
+its running state equal to a rebuild.  With all weights 1 the NPV equals the
+unweighted model's bit for bit.
 """
 
 import numpy as np
@@ -169,3 +170,26 @@ def test_bad_weights_rejected():
     for bad in (np.full((3, 4), np.nan), np.full((3, 4), -1.0)):
         with pytest.raises(mm.MMError):
             mm.Model.from_problem(p, sigma=bad)
+
+
+@pytest.mark.parametrize("name,steps", [("plain_4k", 40), ("plain_50k", 15)])
+def test_fused_weighted_step_state_matches_rebuild(name, steps):
+    """The fused step in its weighted form (S % 4 == 0, equal masses): after
+    every step the running FP64 state equals a fresh weighted model rebuilt
+    from the same schedule (the in-launch apply uses the weighted margin)."""
+    import paper_2511_18296_b300 as mm
+    p = W.config(name)
+    sigma = W.uncertainty_weights(p.T, p.S, seed=3)
+    a = mm.Model.from_problem(p, sigma=sigma)
+    fresh = mm.Model.from_problem(p, sigma=sigma)
+    a.schedule_set(p.x0)
+    mv = torch.as_tensor(p.moves, device="cuda")
+    for _ in range(steps):
+        a.search_step(mv, k=8, apply=True)
+        assert a.last_apply()[0] == 1
+        fresh.schedule_set(a.schedule_get())
+        ma, oa = a.tonnage()
+        mf, of = fresh.tonnage()
+        assert np.array_equal(ma, mf) and np.array_equal(oa, of)
+        np.testing.assert_allclose(a.metal(), fresh.metal(), rtol=1e-12, atol=1e-6)
+        np.testing.assert_allclose(a.npv()[0], fresh.npv()[0], rtol=1e-12, atol=1e-3)
