@@ -210,14 +210,15 @@ def accuracy_report(p, sel, gpu, k: int = 32):
     return out
 
 
-def drift_report(p, x_final, npv64, npv32, n_apply: int):
+def drift_report(p, x_final, npv64, npv32, n_apply: int,
+                 workload: str = "the bench batch, search steps with apply from the initial schedule"):
     """NPV_s of the device's running FP64 totals and of their FP32 shadow after
     n_apply applies, against the oracle's full FP64 recomputation of the same
     schedule: the largest relative difference over scenarios."""
     import oracle as O
     ref = O.OracleModel(p).npv(x_final)
     scale = np.maximum(np.abs(ref), 1.0)
-    return {"applies": n_apply, "workload": "the bench batch, search steps with apply from the initial schedule",
+    return {"applies": n_apply, "workload": workload,
             "fp64_running_max_rel": float(np.max(np.abs(npv64 - ref) / scale)),
             "fp32_shadow_max_rel": float(np.max(np.abs(npv32 - ref) / scale))}
 
@@ -330,6 +331,87 @@ def batched_form(stream, flush, reps: int = 30):
             "sequential_plain": {"desc": "64 x (mm_eval_moves + mm_topk), one CUDA graph", "launches_per_run": 128,
                                  "ms_per_run": t_s, "value": evals / (t_s * 1e-3)},
             "speedup_vs_sequential": t_s / t_b}
+
+
+def stress_form(stream, flush, reps: int = 10, n_accept: int = 1000):
+    """The 100x100x40 = 400,000-block workload, S = 500, T = 30, 1,048,576
+    moves (70 % shifts; seed 3).  Its 806 MB of value rows exceed L2, so here
+    the evaluation streams them from DRAM.  Timed (CUDA events around CUDA-graph
+    replays, L2 flushed before each): the plain and compensated evaluation
+    launches and the search step (evaluate + top-32, then the apply launch).
+    Untimed: n_accept accepted moves (compensated sums, best feasible move of
+    the batch, applied on the device) beside an FP32 shadow of the running
+    totals; returns the report and (problem, final schedule, FP64 NPV_s, FP32
+    shadow NPV_s) for the oracle's comparison in the CPU leg."""
+    import torch
+
+    import paper_2511_18296_b300 as mm
+    import workloads as W
+
+    dev = flush.device
+    p = W.config("stress_400k")
+    m = mm.Model.from_problem(p, stream=stream)
+    m.schedule_set(p.x0)
+    mv = torch.as_tensor(p.moves, device=dev)
+    n = p.moves.shape[0]
+    score = torch.empty(n, dtype=torch.float32, device=dev)
+    feas = torch.empty(n, dtype=torch.uint8, device=dev)
+    idx = torch.empty(TOPK, dtype=torch.int32, device=dev)
+    top = torch.empty(TOPK, dtype=torch.float32, device=dev)
+    cnt = torch.empty(1, dtype=torch.int32, device=dev)
+
+    def time_fn(fn):
+        with torch.cuda.stream(stream):
+            fn()
+        stream.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            fn()
+        ts = []
+        with torch.cuda.stream(stream):
+            for r in range(reps + 3):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                g.replay()
+                e1.record(stream)
+                e1.synchronize()
+                if r >= 3:
+                    ts.append(e0.elapsed_time(e1))
+        return float(np.mean(ts))
+
+    plain_ms = time_fn(lambda: m.eval_moves(mv, score=score, feas=feas, want_mean=False))
+    kahan_ms = time_fn(lambda: m.eval_moves(mv, score=score, feas=feas, want_mean=False, kahan=True))
+    step_ms = time_fn(lambda: m.search_step(mv, k=TOPK, apply=True, score=score, feas=feas, idx=idx, top=top,
+                                            count=cnt))
+    # drift: FP64 running totals beside their FP32 shadow over n_accept applies
+    m.set_fp32_shadow(True)
+    m.schedule_set(p.x0)
+    accepted = steps = 0
+    with torch.cuda.stream(stream):
+        while accepted < n_accept and steps < n_accept + n_accept // 5:
+            m.eval_moves(mv, score=score, feas=feas, want_mean=False, kahan=True)
+            m.topk(score, feas, 1, idx=idx[:1], top=top[:1], count=cnt)
+            m.apply_best(mv, idx[:1], cnt)
+            accepted += m.last_apply()[0]
+            steps += 1
+    x = m.schedule_get()
+    drift_in = (p, x, m.npv()[0], m.fp32_shadow_npv(), accepted)
+    m.close()
+    alg = algorithmic_bytes(p.moves, p.S)
+    peaks, which = measured_peaks()
+    evals = n * p.S
+    return {"workload": "100x100x40 = 400,000 blocks, S=500, T=30, 1,048,576 moves (70% shifts, 30% swaps)",
+            "desc": "value rows (806 MB) larger than L2: the evaluation reads them from DRAM",
+            "algorithmic_bytes_per_launch": alg,
+            "eval_kernel_ms": plain_ms, "eval_roofline_frac": alg / (plain_ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
+            "eval_value": evals / (plain_ms * 1e-3),
+            "compensated_eval_kernel_ms": kahan_ms,
+            "compensated_eval_roofline_frac": alg / (kahan_ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
+            "step_ms": step_ms, "step_desc": "mm_search_step: evaluate + top-32 (one launch), then the apply launch",
+            "value": evals / (step_ms * 1e-3), "unit": UNIT,
+            "peak_source": f"{which} (MEASURED_PEAKS.json hbm_gbs)",
+            "accepted_moves": accepted, "steps": steps}, drift_in
 
 
 def gpu_arm(args):
@@ -653,10 +735,19 @@ def gpu_arm(args):
     }
     if rank == 0 and not args.no_batched:
         line["batched_form"] = batched_form(stream, flush)
+    stress_in = None
+    if rank == 0 and not args.no_stress:
+        line["stress_form"], stress_in = stress_form(stream, flush)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(p, budget_s=args.cpu_budget)
         line["accuracy"] = accuracy_report(p, acc_sel, acc_gpu)
         line["precision_form"]["drift"] = drift_report(p, *drift_gpu, n_apply=N_APPLY)
+        if stress_in is not None:
+            ps, xs, n64, n32, acc = stress_in
+            line["stress_form"]["drift"] = drift_report(
+                ps, xs, n64, n32, n_apply=acc,
+                workload="the 400,000-block model: accepted moves (compensated sums, best feasible move of the "
+                         "batch) applied on the device from the initial schedule")
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
@@ -673,6 +764,8 @@ def main(argv=None):
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-chain batched comparison")
+    ap.add_argument("--no-stress", action="store_true",
+                    help="skip the 400,000-block, 500-scenario DRAM-bound form (about a minute to generate)")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     args = ap.parse_args(argv)
     if args.warmup < 3:

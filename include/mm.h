@@ -182,7 +182,8 @@ mm_status mm_eval_violation(mm_model *m, const mm_move *moves_dev, int64_t n, in
  * maximum), stages = how block rows reach the lanes: 0 = direct global loads,
  * 1..4 = bulk copies into shared memory with that many batches in flight per
  * warp, -1 = built-in choice; prefetch = with direct loads, how many batches
- * ahead the rows are prefetched into L1 (0..8, -1 = built-in choice).  team must
+ * ahead the rows are prefetched into L1 (0..8, -1 = built-in choice: 0 while the
+ * value rows fit in L2, 1 when they are larger and come from DRAM).  team must
  * leave at most 8 scenario quads per lane (ceil(ceil(S/4)/team) <= 8), else
  * MM_ERR_INVALID_ARG. */
 mm_status mm_set_tile(mm_model *m, int32_t team, int32_t ctas_per_sm, int32_t stages, int32_t prefetch);

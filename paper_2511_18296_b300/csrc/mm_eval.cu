@@ -188,7 +188,7 @@ EvalArgs eval_args(mm_model *m, const mm_move *moves, int64_t n, float *score, u
     A.S = m->S; A.S_pad = m->S_pad; A.W = m->W; A.T = m->T; A.R = m->R; A.ore_off = m->ore_off;
     A.m_uniform = m->m_uniform;
     A.nstage = 0;
-    A.prefetch = m->prefetch < 0 ? kDefaultPrefetch : m->prefetch;
+    A.prefetch = m->prefetch >= 0 ? m->prefetch : ((size_t)m->B * m->R * sizeof(float) > m->l2_bytes ? kPrefetchDram : 0);
 
     A.lambda = (float)m->lambda;
     A.a = m->shortfall_pen; A.e = m->excess_pen; A.mc = m->mining_cost;

@@ -65,6 +65,7 @@ struct mm_model {
     cudaStream_t stream = nullptr;
     int has_schedule = 0;
     int num_sms = 148;
+    size_t l2_bytes = 126u << 20;  // L2 size (cudaDevAttrL2CacheSize)
     int max_smem_optin = 227 * 1024;  // per-CTA shared-memory limit (opt-in)
     int team = 0;          // evaluator tile: lanes per move (0 = default)
     int ctas_per_sm = 0;   // evaluator grid: CTAs per SM (0 = occupancy maximum)

@@ -476,6 +476,10 @@ mm_status mm_model_create(const mm_model_desc *d, mm_model **out) {
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&m->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    {
+        int l2 = 0;
+        if (cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) == cudaSuccess && l2 > 0) m->l2_bytes = (size_t)l2;
+    }
     cudaDeviceGetAttribute(&m->max_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
 
     m->h_disc.resize(T + 1);
