@@ -589,10 +589,11 @@ def gpu_arm(args):
     # its batch of moves from pinned host memory and reads its result (the
     # top-k and count) back to pinned host memory.  Double-buffered, as a
     # search loop runs it: batch k+1 is copied on a copy stream while step k
-    # computes, and the host does not wait on each step (stream order and
-    # events keep the buffers safe); the L2 flush stays inside every step (on
-    # the compute stream, before the step), so it is timed too.  The NPV
-    # statistics are read once, after the last step.
+    # computes, step k's result is read back on the copy stream too (so the
+    # compute stream never waits on a transfer), and the host does not wait on
+    # each step (stream order and events keep the buffers safe); the L2 flush
+    # stays inside every step (on the compute stream, before the step), so it
+    # is timed too.  The NPV statistics are read once, after the last step.
     K2 = max(20, min(200, K))
     # the batch travels in the compact 4-byte form (mm_unpack_moves expands it on
     # the device) when the model allows it, else as 8-byte moves
@@ -602,16 +603,17 @@ def gpu_arm(args):
     else:
         moves_h = torch.from_numpy(p.moves).pin_memory()
     torch.cuda.set_stream(stream)
-    # the step's outputs in one device buffer (idx, top, count), read back with one copy
-    out_d = torch.empty(2 * TOPK + 1, dtype=torch.int32, device=dev)
-    idx_e, top_e, cnt_e = out_d[:TOPK], out_d[TOPK:2 * TOPK].view(torch.float32), out_d[2 * TOPK:]
-    out_h = torch.empty(2 * TOPK + 1, dtype=torch.int32).pin_memory()
+    # each step's outputs in one device buffer (idx, top, count), read back with one copy
+    outs_d = [torch.empty(2 * TOPK + 1, dtype=torch.int32, device=dev) for _ in range(2)]
+    outs_h = [torch.empty(2 * TOPK + 1, dtype=torch.int32).pin_memory() for _ in range(2)]
     bufs = [torch.empty_like(moves_h, device=dev) for _ in range(2)]
     mv_e = torch.empty_like(moves_d)  # the unpacked batch of the current step
     copy_stream = torch.cuda.Stream(device=dev)
-    copied = [torch.cuda.Event() for _ in range(2)]
-    freed = [torch.cuda.Event() for _ in range(2)]
-    for e in freed:
+    copied = [torch.cuda.Event() for _ in range(2)]  # batch k is on the device
+    freed = [torch.cuda.Event() for _ in range(2)]   # step k no longer reads its batch buffer
+    done = [torch.cuda.Event() for _ in range(2)]    # step k's outputs are written
+    read = [torch.cuda.Event() for _ in range(2)]    # step k's outputs are in host memory
+    for e in freed + read:
         e.record(stream)
 
     def issue_copy(k):
@@ -625,19 +627,27 @@ def gpu_arm(args):
         issue_copy(0)
         for k in range(steps):
             b = k % 2
+            o = outs_d[b]
             flush.zero_()
             stream.wait_event(copied[b])
+            stream.wait_event(read[b])  # step k-2's outputs have been read back
             if packed:
                 m.unpack_moves(bufs[b], out=mv_e)
                 freed[b].record(stream)
-                m.search_step(mv_e, k=TOPK, apply=True, score=score, feas=feas, idx=idx_e, top=top_e, count=cnt_e)
+                m.search_step(mv_e, k=TOPK, apply=True, score=score, feas=feas, idx=o[:TOPK],
+                              top=o[TOPK:2 * TOPK].view(torch.float32), count=o[2 * TOPK:])
             else:
-                m.search_step(bufs[b], k=TOPK, apply=True, score=score, feas=feas, idx=idx_e, top=top_e, count=cnt_e)
+                m.search_step(bufs[b], k=TOPK, apply=True, score=score, feas=feas, idx=o[:TOPK],
+                              top=o[TOPK:2 * TOPK].view(torch.float32), count=o[2 * TOPK:])
                 freed[b].record(stream)
-            out_h.copy_(out_d, non_blocking=True)
+            done[b].record(stream)
             if k + 1 < steps:
                 issue_copy(k + 1)
-        stream.synchronize()
+            with torch.cuda.stream(copy_stream):
+                copy_stream.wait_event(done[b])
+                outs_h[b].copy_(o, non_blocking=True)
+                read[b].record(copy_stream)
+        torch.cuda.synchronize()
         return m.last_apply()[1]  # NPV mean after the last step's move
 
     m.schedule_set(p.x0)
@@ -722,13 +732,14 @@ def gpu_arm(args):
             "vs_plain_eval": {"plain_eval_ms": plain_eval_ms}},
         "e2e": {"value": evals_per_step * world / e2e_avg, "unit": UNIT,
                 "h2d_bytes_per_step": int(moves_h.numel()) * moves_h.element_size(),
-                "d2h_bytes_per_step": int(out_h.numel()) * 4,
+                "d2h_bytes_per_step": int(outs_h[0].numel()) * 4,
                 "ms_per_step": e2e_avg * 1e3,
                 "path": (("pinned host moves in the compact 4-byte form -> mm_unpack_moves -> " if packed else
                           "pinned host moves -> ")
                          + "mm_search_step (apply on device) -> top-k and count to pinned host memory every step; "
-                         "double-buffered (batch k+1 copied on a second stream while step k runs), the host not waiting on "
-                         "each step; L2 flush inside each step; NPV statistics read after the last step")},
+                         "double-buffered (batch k+1 copied and step k-1's result read back on a second stream while "
+                         "step k runs), the host not waiting on each step; L2 flush inside each step; NPV statistics "
+                         "read after the last step")},
         "gpu_launches": (1 if S <= 256 else 2) * K,  # per step: the evaluation launch (top-k and apply inside when S <= 256)
         "clocks": clocks,
         "check": {"last_apply": applied, "npv_mean": npv_mean, "e2e_npv_mean": e2e_mean},
