@@ -128,7 +128,8 @@ template <typename G, int TT>
 __global__ void __launch_bounds__(kFwdSW * kFwdGroups) k_relax_fwd(const float *__restrict__ x, const G *__restrict__ g,
                                                       RelaxRows Rw, const uint32_t *__restrict__ mass, int32_t B,
                                                       int32_t S, int32_t T, int32_t t0, RelaxEcon E, int32_t vec,
-                                                      float *__restrict__ part_o, float *__restrict__ part_v) {
+                                                      int32_t xvec, float *__restrict__ part_o,
+                                                      float *__restrict__ part_v) {
     constexpr bool ROWS = sizeof(G) == sizeof(double);          // model rows: values, then ore words
     constexpr int RW = kFwdSW + (ROWS ? 4 : 0);                  // staged floats per block
     __shared__ __align__(16) float s_g[kFwdStages][kFwdBT][RW];
@@ -140,35 +141,49 @@ __global__ void __launch_bounds__(kFwdSW * kFwdGroups) k_relax_fwd(const float *
     const int nt = min(TT, T - t0);
     const int ntiles = (b_hi - b_lo + kFwdBT - 1) / kFwdBT;
     const int tid = threadIdx.x, nth = blockDim.x;
-    const int gw = nth / kFwdGroups;                 // threads per group (a multiple of 32)
+    const int lane = tid & 31, warp = tid >> 5, nwarps = nth >> 5;
+    // the groups are packed: group k is threads [k gw, (k + 1) gw), gw the
+    // widest scenario tile, so that few lanes idle when S is not a multiple of
+    // 32 (threads from kFwdGroups gw on only copy)
+    const int gw = min(S, kFwdSW);
     const int grp = tid / gw, lt = tid - grp * gw;   // group, scenario lane
     auto issue = [&](int k) {
         const int st = k % kFwdStages, bb0 = b_lo + k * kFwdBT, nb = min(kFwdBT, b_hi - bb0);
+        // one warp per block row, one lane per 16 (or 4) bytes: no divisions
         if (ROWS) {
             // value slice [s0, s0 + sw) rounded up to 16 bytes (the row's zero padding
             // runs to a multiple of 4 floats) and the slice's ore words (one 16-byte copy)
             const int nv4 = (sw + 3) / 4, per = nv4 + 1;
-            for (int i = tid; i < nb * per; i += nth) {
-                const int j = i / per, q = i - j * per;
+            for (int j = warp; j < nb; j += nwarps) {
                 const float *row = Rw.val + (size_t)(bb0 + j) * Rw.R;
-                if (q < nv4) cp_async16(&s_g[st][j][4 * q], row + s0 + 4 * q);
-                else cp_async16(&s_g[st][j][kFwdSW], row + Rw.ore_off + s0 / 32);
+                for (int q = lane; q < per; q += 32) {
+                    if (q < nv4) cp_async16(&s_g[st][j][4 * q], row + s0 + 4 * q);
+                    else cp_async16(&s_g[st][j][kFwdSW], row + Rw.ore_off + s0 / 32);
+                }
             }
         } else if (vec) {
             const int nv4 = sw / 4;  // S % 4 == 0
-            for (int i = tid; i < nb * nv4; i += nth) {
-                const int j = i / nv4, q = i - j * nv4;
-                cp_async16(&s_g[st][j][4 * q], reinterpret_cast<const float *>(g) + (size_t)(bb0 + j) * S + s0 + 4 * q);
+            for (int j = warp; j < nb; j += nwarps) {
+                const float *row = reinterpret_cast<const float *>(g) + (size_t)(bb0 + j) * S + s0;
+                for (int q = lane; q < nv4; q += 32) cp_async16(&s_g[st][j][4 * q], row + 4 * q);
             }
         } else {
-            for (int i = tid; i < nb * sw; i += nth) {
-                const int j = i / sw, q = i - j * sw;
-                cp_async4(&s_g[st][j][q], reinterpret_cast<const float *>(g) + (size_t)(bb0 + j) * S + s0 + q);
+            for (int j = warp; j < nb; j += nwarps) {
+                const float *row = reinterpret_cast<const float *>(g) + (size_t)(bb0 + j) * S + s0;
+                for (int q = lane; q < sw; q += 32) cp_async4(&s_g[st][j][q], row + q);
             }
         }
-        for (int i = tid; i < nb * nt; i += nth) {
-            const int j = i / nt, q = i - j * nt;
-            cp_async4(&s_x[st][j][q], x + (size_t)(bb0 + j) * T + t0 + q);
+        if (xvec) {
+            // T % 4 == 0 (so t0, nt and every row start are multiples of 4 floats):
+            // the tile's x rows in 16-byte pieces, nt / 4 per block
+            const int n4 = nt >> 2;
+            for (int i = tid; i < nb * n4; i += nth) {
+                const int j = i / n4, q = i - j * n4;
+                cp_async16(&s_x[st][j][4 * q], x + (size_t)(bb0 + j) * T + t0 + 4 * q);
+            }
+        } else {
+            for (int j = warp; j < nb; j += nwarps)
+                for (int q = lane; q < nt; q += 32) cp_async4(&s_x[st][j][q], x + (size_t)(bb0 + j) * T + t0 + q);
         }
         for (int j = tid; j < nb; j += nth) cp_async4(&s_m[st][j], mass + bb0 + j);
     };
@@ -182,7 +197,7 @@ __global__ void __launch_bounds__(kFwdSW * kFwdGroups) k_relax_fwd(const float *
         if (k < ntiles) issue(k);
         asm volatile("cp.async.commit_group;" ::: "memory");
     }
-    const bool live = lt < sw;
+    const bool live = grp < kFwdGroups && lt < sw;
     const int s = s0 + lt;
     uint64_t o2[TT / 2], v2[TT / 2];  // period pairs (2q, 2q + 1)
 #pragma unroll
@@ -252,7 +267,7 @@ __global__ void __launch_bounds__(kFwdSW * kFwdGroups) k_relax_fwd(const float *
     __syncthreads();
     float *red = &s_g[0][0][0];  // [kFwdGroups - 1][2][TT][kFwdSW]
     static_assert((kFwdGroups - 1) * 2 * TT * kFwdSW <= kFwdStages * kFwdBT * RW, "combine space");
-    if (grp > 0) {
+    if (grp > 0 && live) {
 #pragma unroll
         for (int j = 0; j < TT; j++) {
             red[(((size_t)(grp - 1) * 2) * TT + j) * kFwdSW + lt] = o[j];
@@ -281,18 +296,20 @@ template <typename G>
 static mm_status relax_fwd_launch(const float *x, const G *g, RelaxRows Rw, const uint32_t *mass, int32_t B, int32_t S,
                                   int32_t T, RelaxEcon E, float *part_o, float *part_v, int nr, cudaStream_t st) {
     const int zs = (S + kFwdSW - 1) / kFwdSW;
-    const int threads = std::min(((S + 31) / 32) * 32, kFwdSW) * kFwdGroups;
+    const int threads = (kFwdGroups * std::min(S, kFwdSW) + 31) / 32 * 32;
     const int vec = (S % 4 == 0 && ((uintptr_t)g & 15u) == 0) ? 1 : 0;
+    const int xvec = (T % 4 == 0 && ((uintptr_t)x & 15u) == 0) ? 1 : 0;  // period tiles start at multiples of 4
+    static_assert(kRelaxTile % 4 == 0, "period tiles must start at multiples of 4 floats");
     for (int tb = 0; tb < T; tb += kRelaxTile) {
         const int tt = (std::min(kRelaxTile, T - tb) + 3) / 4 * 4;
         const dim3 grid(nr, 1, zs);
         switch (tt) {
-            case 4: k_relax_fwd<G, 4><<<grid, threads, 0, st>>>(x, g, Rw, mass, B, S, T, tb, E, vec, part_o, part_v); break;
-            case 8: k_relax_fwd<G, 8><<<grid, threads, 0, st>>>(x, g, Rw, mass, B, S, T, tb, E, vec, part_o, part_v); break;
-            case 12: k_relax_fwd<G, 12><<<grid, threads, 0, st>>>(x, g, Rw, mass, B, S, T, tb, E, vec, part_o, part_v); break;
-            case 16: k_relax_fwd<G, 16><<<grid, threads, 0, st>>>(x, g, Rw, mass, B, S, T, tb, E, vec, part_o, part_v); break;
-            case 20: k_relax_fwd<G, 20><<<grid, threads, 0, st>>>(x, g, Rw, mass, B, S, T, tb, E, vec, part_o, part_v); break;
-            default: k_relax_fwd<G, 24><<<grid, threads, 0, st>>>(x, g, Rw, mass, B, S, T, tb, E, vec, part_o, part_v); break;
+            case 4: k_relax_fwd<G, 4><<<grid, threads, 0, st>>>(x, g, Rw, mass, B, S, T, tb, E, vec, xvec, part_o, part_v); break;
+            case 8: k_relax_fwd<G, 8><<<grid, threads, 0, st>>>(x, g, Rw, mass, B, S, T, tb, E, vec, xvec, part_o, part_v); break;
+            case 12: k_relax_fwd<G, 12><<<grid, threads, 0, st>>>(x, g, Rw, mass, B, S, T, tb, E, vec, xvec, part_o, part_v); break;
+            case 16: k_relax_fwd<G, 16><<<grid, threads, 0, st>>>(x, g, Rw, mass, B, S, T, tb, E, vec, xvec, part_o, part_v); break;
+            case 20: k_relax_fwd<G, 20><<<grid, threads, 0, st>>>(x, g, Rw, mass, B, S, T, tb, E, vec, xvec, part_o, part_v); break;
+            default: k_relax_fwd<G, 24><<<grid, threads, 0, st>>>(x, g, Rw, mass, B, S, T, tb, E, vec, xvec, part_o, part_v); break;
         }
         mm_status r = check_launch("k_relax_fwd");
         if (r != MM_OK) return r;
