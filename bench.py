@@ -595,9 +595,10 @@ def gpu_arm(args):
     # stays inside every step (on the compute stream, before the step), so it
     # is timed too.  The NPV statistics are read once, after the last step.
     K2 = max(20, min(200, K))
-    # the batch travels in the compact 4-byte form (mm_unpack_moves expands it on
-    # the device) when the model allows it, else as 8-byte moves
-    packed = p.B + p.T + 1 <= 65536
+    # the batch travels in the compact 4-byte form (mm_search_step_packed
+    # decodes it inside the step's launch) when the model allows it, else as
+    # 8-byte moves
+    packed = p.B + p.T + 1 <= 65536 and p.S <= 256
     if packed:
         moves_h = torch.from_numpy(mm.pack_moves(p.moves, p.B, p.T).view(np.int32)).pin_memory()
     else:
@@ -607,7 +608,6 @@ def gpu_arm(args):
     outs_d = [torch.empty(2 * TOPK + 1, dtype=torch.int32, device=dev) for _ in range(2)]
     outs_h = [torch.empty(2 * TOPK + 1, dtype=torch.int32).pin_memory() for _ in range(2)]
     bufs = [torch.empty_like(moves_h, device=dev) for _ in range(2)]
-    mv_e = torch.empty_like(moves_d)  # the unpacked batch of the current step
     copy_stream = torch.cuda.Stream(device=dev)
     copied = [torch.cuda.Event() for _ in range(2)]  # batch k is on the device
     freed = [torch.cuda.Event() for _ in range(2)]   # step k no longer reads its batch buffer
@@ -631,15 +631,10 @@ def gpu_arm(args):
             flush.zero_()
             stream.wait_event(copied[b])
             stream.wait_event(read[b])  # step k-2's outputs have been read back
-            if packed:
-                m.unpack_moves(bufs[b], out=mv_e)
-                freed[b].record(stream)
-                m.search_step(mv_e, k=TOPK, apply=True, score=score, feas=feas, idx=o[:TOPK],
-                              top=o[TOPK:2 * TOPK].view(torch.float32), count=o[2 * TOPK:])
-            else:
-                m.search_step(bufs[b], k=TOPK, apply=True, score=score, feas=feas, idx=o[:TOPK],
-                              top=o[TOPK:2 * TOPK].view(torch.float32), count=o[2 * TOPK:])
-                freed[b].record(stream)
+            step_fn = m.search_step_packed if packed else m.search_step
+            step_fn(bufs[b], k=TOPK, apply=True, score=score, feas=feas, idx=o[:TOPK],
+                    top=o[TOPK:2 * TOPK].view(torch.float32), count=o[2 * TOPK:])
+            freed[b].record(stream)
             done[b].record(stream)
             if k + 1 < steps:
                 issue_copy(k + 1)
@@ -734,9 +729,10 @@ def gpu_arm(args):
                 "h2d_bytes_per_step": int(moves_h.numel()) * moves_h.element_size(),
                 "d2h_bytes_per_step": int(outs_h[0].numel()) * 4,
                 "ms_per_step": e2e_avg * 1e3,
-                "path": (("pinned host moves in the compact 4-byte form -> mm_unpack_moves -> " if packed else
-                          "pinned host moves -> ")
-                         + "mm_search_step (apply on device) -> top-k and count to pinned host memory every step; "
+                "path": (("pinned host moves in the compact 4-byte form -> mm_search_step_packed (decoded inside "
+                          "the step's launch; apply on device)" if packed else
+                          "pinned host moves -> mm_search_step (apply on device)")
+                         + " -> top-k and count to pinned host memory every step; "
                          "double-buffered (batch k+1 copied and step k-1's result read back on a second stream while "
                          "step k runs), the host not waiting on each step; L2 flush inside each step; NPV statistics "
                          "read after the last step")},

@@ -238,6 +238,21 @@ mm_status mm_search_step(mm_model *m, const mm_move *moves_dev, int64_t n, int32
                          float *score_dev, uint8_t *feasible_dev, int32_t *idx_dev, float *topscore_dev,
                          int32_t *count_dev);
 
+/* mm_search_step on a batch in the compact 4-byte form of mm_unpack_moves,
+ * decoded inside the evaluation launch (no unpack launch, half the bytes of
+ * moves read): packed_dev[n] (device memory, 4-byte aligned; NULL allowed
+ * when n = 0).  Every output, the applied move and the sticky status are
+ * exactly those of mm_unpack_moves followed by mm_search_step on the same
+ * batch; codes that name no move are bad moves (feasible = 0, score = -inf,
+ * sticky MM_ERR_BAD_MOVE).  Only where the whole step is one launch: needs
+ * B + T + 1 <= 65536, equal block masses, S <= 256 when apply != 0, and, with
+ * uncertainty weights, the weighted fast form (S % 4 == 0); otherwise
+ * MM_ERR_INVALID_ARG (use mm_unpack_moves and mm_search_step).
+ * Asynchronous. */
+mm_status mm_search_step_packed(mm_model *m, const uint32_t *packed_dev, int64_t n, int32_t k, int32_t apply,
+                                float *score_dev, uint8_t *feasible_dev, int32_t *idx_dev, float *topscore_dev,
+                                int32_t *count_dev);
+
 /* Timing hook; the paper has no counterpart.  When cuda_event (a cudaEvent_t
  * created with timing enabled, owned by the caller) is not NULL, every later
  * mm_search_step records it on the model's stream between its evaluation launch
@@ -340,7 +355,7 @@ mm_status mm_apply_move(mm_model *m, mm_move move, double *npv_mean_out, double 
  * leave the GPU: if *count_dev > 0, applies moves_dev[idx_dev[0]] exactly as
  * mm_apply_move does (re-checking feasibility on the device).  The outcome
  * (applied 0/1) is kept on the device and returned by the next mm_last_apply
- * call.  moves_dev[n] is the batch idx_dev indexes; an
+ * call.  moves_dev[n] is the batch idx_dev indexes (NULL allowed when n = 0); an
  * index outside 0..n-1 is treated as a bad move (nothing applied, sticky
  * MM_ERR_BAD_MOVE).  Asynchronous. */
 mm_status mm_apply_best(mm_model *m, const mm_move *moves_dev, int64_t n, const int32_t *idx_dev,

@@ -85,6 +85,7 @@ SIGNATURES = [
     ("mm_topk", C.c_int, [P, P, P, I64, I32, P, P, P]),
     ("mm_topk_noalloc", C.c_int, [P, P, I64, I32, P, P, P, P]),
     ("mm_search_step", C.c_int, [P, P, I64, I32, I32, P, P, P, P, P]),
+    ("mm_search_step_packed", C.c_int, [P, P, I64, I32, I32, P, P, P, P, P]),
     ("mm_set_step_event", C.c_int, [P, P]),
     ("mm_set_fp32_shadow", C.c_int, [P, I32]),
     ("mm_get_fp32_shadow_npv", C.c_int, [P, P]),
@@ -327,6 +328,28 @@ class Model:
             count = torch.empty(1, dtype=torch.int32, device=dev)
         _check(lib().mm_search_step(self.h, _ptr(moves), n, k, 1 if apply else 0, _ptr(score), _ptr(feas), _ptr(idx),
                                     _ptr(top), _ptr(count)))
+        return score, feas, idx, top, count
+
+    def search_step_packed(self, packed, k: int = 32, apply: bool = True, score=None, feas=None, idx=None, top=None,
+                           count=None):
+        """mm_search_step_packed: search_step on a batch in the compact 4-byte
+        form (pack_moves), decoded inside the evaluation launch."""
+        import torch
+        assert packed.is_cuda and packed.dtype in (torch.int32, torch.uint32) and packed.is_contiguous()
+        n = packed.shape[0]
+        dev = packed.device
+        if score is None:
+            score = torch.empty(n, dtype=torch.float32, device=dev)
+        if feas is None:
+            feas = torch.empty(n, dtype=torch.uint8, device=dev)
+        if idx is None:
+            idx = torch.empty(k, dtype=torch.int32, device=dev)
+        if top is None:
+            top = torch.empty(k, dtype=torch.float32, device=dev)
+        if count is None:
+            count = torch.empty(1, dtype=torch.int32, device=dev)
+        _check(lib().mm_search_step_packed(self.h, _ptr(packed), n, k, 1 if apply else 0, _ptr(score), _ptr(feas),
+                                           _ptr(idx), _ptr(top), _ptr(count)))
         return score, feas, idx, top, count
 
     def set_step_event(self, event=None):

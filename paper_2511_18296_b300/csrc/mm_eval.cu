@@ -177,6 +177,7 @@ EvalArgs eval_args(mm_model *m, const mm_move *moves, int64_t n, float *score, u
                    float *delta) {
     EvalArgs A;
     A.moves = reinterpret_cast<const int2 *>(moves);
+    A.pmoves = nullptr;
     A.n = n;
     A.score = score; A.feas = feas; A.mean = mean; A.delta = delta;
     A.val = m->val; A.blk = m->blk; A.mass = m->mass;
@@ -222,8 +223,10 @@ static mm_status eval_occupancy(EvalFn fn, size_t smem, int *per_sm) {
 }
 
 mm_status eval_launch(mm_model *m, const mm_move *moves, int64_t n, float *score, uint8_t *feas, float *mean,
-                      float *delta, int32_t options, int team, int ctas_per_sm, int stages, const StepOut *step) {
+                      float *delta, int32_t options, int team, int ctas_per_sm, int stages, const StepOut *step,
+                      const uint32_t *pmoves) {
     EvalArgs A = eval_args(m, moves, n, score, feas, mean, delta);
+    A.pmoves = pmoves;
     if (step) {
         A.tail.k = step->k;
         A.tail.idx_out = step->idx;
@@ -275,6 +278,7 @@ mm_status eval_launch(mm_model *m, const mm_move *moves, int64_t n, float *score
     }
     if (m->sig && step) return set_error(MM_ERR_INVALID_ARG, "no weighted step kernel for this tile");
     if (!m->uniform_mass || m->sig) {
+        if (pmoves) return set_error(MM_ERR_INVALID_ARG, "compact moves need the tiled evaluator");
         EvalFn fn = want_delta ? k_eval_general<true> : k_eval_general<false>;
         int64_t blocks = (n + 7) / 8;
         int64_t cap_blocks = (int64_t)m->num_sms * 8;

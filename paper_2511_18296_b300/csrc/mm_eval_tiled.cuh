@@ -62,6 +62,7 @@ struct StepTail {
 
 struct EvalArgs {
     const int2 *moves;
+    const uint32_t *pmoves;  // the batch in the compact 4-byte form instead (fused step), else nullptr
     int64_t n;
     float *score;
     uint8_t *feas;
@@ -744,6 +745,11 @@ static __device__ __noinline__ void step_reduce(const StepTail &T, uint64_t wtk,
 // List storage and tickets of model m for a launch of `grid` CTAs (mm_eval.cu).
 StepLists step_lists(mm_model *m, int grid);
 
+// Move i of the batch, from the 8-byte or the compact 4-byte form.
+__device__ __forceinline__ int2 load_move(const EvalArgs &A, int64_t i) {
+    return A.pmoves ? unpack_move(__ldg(A.pmoves + i), A.tp.B, A.tp.T) : __ldg(A.moves + i);
+}
+
 // Evaluator arguments for a batch of n moves on model m (mm_eval.cu).
 EvalArgs eval_args(mm_model *m, const mm_move *moves, int64_t n, float *score, uint8_t *feas, float *mean,
                    float *delta);
@@ -782,7 +788,7 @@ __device__ __forceinline__ void eval_warp_range(const EvalArgs &A, EvalShared &s
 #pragma unroll
     for (int h = 0; h < 2; h++) {
         const int64_t i = r0 + h * 32 + lane;
-        mv[h] = i < r1 ? __ldg(A.moves + i) : make_int2(0, -1);
+        mv[h] = i < r1 ? load_move(A, i) : make_int2(0, -1);
     }
     for (int64_t c0 = r0; c0 < r1; c0 += CH) {
         // ---- decode: two moves per lane ----
@@ -796,7 +802,7 @@ __device__ __forceinline__ void eval_warp_range(const EvalArgs &A, EvalShared &s
                 mv[h], A.tp, [&](int32_t b) { return __ldg(A.blk + b); }, [&](int32_t) { return A.m_uniform; },
                 [&](uint32_t t) { return s_mined[t]; }, [&](uint32_t t) { return s_cap[t]; });
             const int64_t ni = i + CH;  // prefetch the next chunk's move
-            mv[h] = ni < r1 ? __ldg(A.moves + ni) : make_int2(0, -1);
+            mv[h] = ni < r1 ? load_move(A, ni) : make_int2(0, -1);
             const bool work = active && v.valid && !v.noop;
             if (active) {
                 A.feas[i] = v.feasible ? 1 : 0;
@@ -1083,7 +1089,7 @@ __global__ void __launch_bounds__(kEvalThreads, 1) k_eval_tma(EvalArgs A) {
 #pragma unroll
     for (int h = 0; h < 2; h++) {
         const int64_t i = r0 + h * 32 + lane;
-        mv[h] = i < r1 ? __ldg(A.moves + i) : make_int2(0, -1);
+        mv[h] = i < r1 ? load_move(A, i) : make_int2(0, -1);
     }
     for (int64_t c0 = r0; c0 < r1; c0 += CH) {
         // ---- decode: two moves per lane ----
@@ -1097,7 +1103,7 @@ __global__ void __launch_bounds__(kEvalThreads, 1) k_eval_tma(EvalArgs A) {
                 mv[h], A.tp, [&](int32_t b) { return __ldg(A.blk + b); }, [&](int32_t) { return A.m_uniform; },
                 [&](uint32_t t) { return s_mined[t]; }, [&](uint32_t t) { return s_cap[t]; });
             const int64_t ni = i + CH;
-            mv[h] = ni < r1 ? __ldg(A.moves + ni) : make_int2(0, -1);
+            mv[h] = ni < r1 ? load_move(A, ni) : make_int2(0, -1);
             const bool work = active && v.valid && !v.noop;
             if (active) {
                 A.feas[i] = v.feasible ? 1 : 0;

@@ -139,7 +139,8 @@ struct StepOut {
     int grid;  // set by eval_launch: CTAs that publish a list
 };
 mm_status eval_launch(mm_model *m, const mm_move *moves, int64_t n, float *score, uint8_t *feas, float *mean,
-                      float *delta, int32_t options, int team, int ctas_per_sm, int stages, const StepOut *step);
+                      float *delta, int32_t options, int team, int ctas_per_sm, int stages, const StepOut *step,
+                      const uint32_t *pmoves = nullptr);  // pmoves: the batch in the compact 4-byte form
 int default_team(int S);
 bool sigma_fast_ok(const mm_model *m, int options);  // the weighted fast form (and fused step) applies
 // Top-k for k <= 32 through per-CTA warp lists and the step finisher.

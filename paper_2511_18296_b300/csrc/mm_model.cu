@@ -715,7 +715,7 @@ mm_status mm_apply_move(mm_model *m, mm_move mv, double *mean, double *sd) {
 }
 
 mm_status mm_apply_best(mm_model *m, const mm_move *moves, int64_t n, const int32_t *idx, const int32_t *count) {
-    if (!m || !moves || !idx || !count) return set_error(MM_ERR_INVALID_ARG, "mm_apply_best: NULL argument");
+    if (!m || (!moves && n > 0) || !idx || !count) return set_error(MM_ERR_INVALID_ARG, "mm_apply_best: NULL argument");
     if (n < 0) return set_error(MM_ERR_INVALID_ARG, "negative move count");
     if (!m->has_schedule) return set_error(MM_ERR_STATE, "no schedule installed");
     ApplyArgs A = apply_args(m);

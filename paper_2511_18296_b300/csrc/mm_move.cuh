@@ -29,6 +29,18 @@ struct Topo {
     const int32_t *pred_ptr, *pred_idx, *succ_ptr, *succ_idx;  // CSR when nx == 0
 };
 
+// Compact 4-byte move p = (b1 << 16) | code (needs B + T + 1 <= 65536):
+// code < B swaps b1 with block `code`, code = 65535 - t shifts b1 to period t
+// (0..T); any other code, or b1 >= B, is the bad move {-1, -1}.
+__device__ __forceinline__ int2 unpack_move(uint32_t p, int32_t B, int32_t T) {
+    const int32_t b1 = (int32_t)(p >> 16), code = (int32_t)(p & 0xffffu);
+    if (b1 < B) {
+        if (code < B) return make_int2(b1, code);
+        if (code >= 65535 - T) return make_int2(b1, -(65535 - code) - 1);
+    }
+    return make_int2(-1, -1);
+}
+
 // Is a a direct predecessor of b?  (1-5 pattern or CSR)
 __device__ __forceinline__ bool is_pred(const Topo &tp, int32_t a, int32_t b) {
     if (tp.nx > 0) {

@@ -2,6 +2,7 @@
 // p = (b1 << 16) | code, code < B a swap partner, code = 65535 - t a shift to
 // period t (0..T); anything else decodes to the bad move {-1, -1}.
 #include "mm_internal.cuh"
+#include "mm_move.cuh"
 
 namespace mm {
 
@@ -9,14 +10,7 @@ __global__ void __launch_bounds__(256) k_unpack_moves(const uint32_t *__restrict
                                                       int32_t T, int2 *__restrict__ moves) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const uint32_t p = __ldg(packed + i);
-        const int32_t b1 = (int32_t)(p >> 16), code = (int32_t)(p & 0xffffu);
-        int2 mv = make_int2(-1, -1);
-        if (b1 < B) {
-            if (code < B) mv = make_int2(b1, code);
-            else if (code >= 65535 - T) mv = make_int2(b1, -(65535 - code) - 1);
-        }
-        moves[i] = mv;
+        moves[i] = unpack_move(__ldg(packed + i), B, T);
     }
 }
 

@@ -134,19 +134,31 @@ static mm_status record_step_event(mm_model *m) {
     return MM_OK;
 }
 
-extern "C" mm_status mm_search_step(mm_model *m, const mm_move *moves, int64_t n, int32_t k, int32_t apply,
-                                    float *score, uint8_t *feas, int32_t *idx, float *top, int32_t *count) {
-    mm_status st = step_check(m, moves, n, score, feas);
-    if (st != MM_OK) return st;
-    if (k < 1 || k > 32) return set_error(MM_ERR_INVALID_ARG, "mm_search_step: k = %d outside 1..32", k);
+// The step on a batch in either form (moves, or pmoves when packed; the
+// compact form only where the whole step is one launch).
+static mm_status search_step(mm_model *m, const mm_move *moves, const uint32_t *pmoves, bool packed, int64_t n,
+                             int32_t k, int32_t apply, float *score, uint8_t *feas, int32_t *idx, float *top,
+                             int32_t *count) {
+    const char *name = packed ? "mm_search_step_packed" : "mm_search_step";
+    if (k < 1 || k > 32) return set_error(MM_ERR_INVALID_ARG, "%s: k = %d outside 1..32", name, k);
     if (!idx || !top || !count) return set_error(MM_ERR_INVALID_ARG, "NULL top-k output");
     if (!m->uniform_mass)
-        return set_error(MM_ERR_INVALID_ARG, "mm_search_step needs equal block masses (use the separate calls)");
+        return set_error(MM_ERR_INVALID_ARG, "%s needs equal block masses (use the separate calls)", name);
+    const bool weighted_split = m->sig && !sigma_fast_ok(m, MM_EVAL_PLAIN);
+    // the final CTA of the evaluation launch applies the best move itself
+    // when a CTA has a thread per scenario; otherwise a one-CTA launch follows
+    const bool in_launch = apply && m->S <= kEvalThreads;
+    if (packed && (weighted_split || (apply && !in_launch)))
+        return set_error(MM_ERR_INVALID_ARG,
+                         "mm_search_step_packed: this model's step is not one launch (S = %d%s); use "
+                         "mm_unpack_moves and mm_search_step",
+                         m->S, weighted_split ? ", weights outside the fast form" : "");
     if (n == 0) {
         MM_CUDA_TRY(cudaMemsetAsync(count, 0, sizeof(int32_t), m->stream), "clear count");
         return apply ? mm_apply_best(m, moves, 0, idx, count) : MM_OK;
     }
-    if (m->sig && !sigma_fast_ok(m, MM_EVAL_PLAIN)) {
+    mm_status st;
+    if (weighted_split) {
         // uncertainty weights outside the weighted fast form: the separate
         // evaluation, top-k and apply launches
         st = eval_launch(m, moves, n, score, feas, nullptr, nullptr, MM_EVAL_PLAIN, m->team, m->ctas_per_sm, 0,
@@ -155,15 +167,32 @@ extern "C" mm_status mm_search_step(mm_model *m, const mm_move *moves, int64_t n
         if (st == MM_OK) st = record_step_event(m);
         return (st == MM_OK && apply) ? mm_apply_best(m, moves, n, idx, count) : st;
     }
-    // the final CTA of the evaluation launch applies the best move itself
-    // when a CTA has a thread per scenario; otherwise a one-CTA launch follows
-    const bool in_launch = apply && m->S <= kEvalThreads;
     StepOut so{k, in_launch ? 1 : 0, idx, top, count, 0};
-    st = eval_launch(m, moves, n, score, feas, nullptr, nullptr, MM_EVAL_PLAIN, m->team, m->ctas_per_sm, 0, &so);
+    st = eval_launch(m, moves, n, score, feas, nullptr, nullptr, MM_EVAL_PLAIN, m->team, m->ctas_per_sm, 0, &so,
+                     pmoves);
     if (st != MM_OK) return st;
     st = record_step_event(m);
     if (st != MM_OK) return st;
     return (apply && !in_launch) ? mm_apply_best(m, moves, n, idx, count) : MM_OK;
+}
+
+extern "C" mm_status mm_search_step(mm_model *m, const mm_move *moves, int64_t n, int32_t k, int32_t apply,
+                                    float *score, uint8_t *feas, int32_t *idx, float *top, int32_t *count) {
+    mm_status st = step_check(m, moves, n, score, feas);
+    if (st != MM_OK) return st;
+    return search_step(m, moves, nullptr, false, n, k, apply, score, feas, idx, top, count);
+}
+
+extern "C" mm_status mm_search_step_packed(mm_model *m, const uint32_t *packed, int64_t n, int32_t k, int32_t apply,
+                                           float *score, uint8_t *feas, int32_t *idx, float *top, int32_t *count) {
+    if (!m) return set_error(MM_ERR_INVALID_ARG, "NULL model");
+    if (!m->has_schedule) return set_error(MM_ERR_STATE, "no schedule installed");
+    if (n < 0 || n > 0x7fffffffLL) return set_error(MM_ERR_INVALID_ARG, "move count out of range");
+    if ((int64_t)m->B + m->T + 1 > 65536)
+        return set_error(MM_ERR_INVALID_ARG, "packed moves need B + T + 1 <= 65536 (B = %d, T = %d)", m->B, m->T);
+    if (n > 0 && (!packed || !score || !feas)) return set_error(MM_ERR_INVALID_ARG, "NULL output or move pointer");
+    if (((uintptr_t)packed & 3u) != 0) return set_error(MM_ERR_INVALID_ARG, "packed moves must be 4-byte aligned");
+    return search_step(m, nullptr, packed, true, n, k, apply, score, feas, idx, top, count);
 }
 
 extern "C" mm_status mm_set_step_event(mm_model *m, void *cuda_event) {
