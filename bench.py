@@ -39,6 +39,7 @@ WORKLOAD = "plain_50k"
 METRIC = "move-scenario evals/sec at 50k blocks, S=100; % of HBM roofline vs plain form"
 UNIT = "move-scenario evals/s"
 TOPK = 32
+FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12  # CUDA-core FP32 FMA peak at the maximum SM clock
 FLUSH_BYTES = 256 << 20
 EVAL_KERNEL = "k_eval_tiled"  # the move evaluator (mm_eval_moves launches it alone)
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k_eval_tiled_plain_50k.md")
@@ -324,9 +325,14 @@ def batched_form(stream, flush, reps: int = 30):
     t_b = time_graph(graph_of(b.run))
     t_s = time_graph(graph_of(seq))
     b.close()
+    alg = float(sum(algorithmic_bytes(p.moves, p.S) for p in probs))
+    peaks, which = measured_peaks()
     return {"workload": "64 chains: cubes of side 15..40, S in {16, 32, 64, 100}, T=20, 1,024..65,536 moves each",
             "evals_per_run": evals, "chains": 64, "launches_per_run": 1,
             "ms_per_run": t_b, "value": evals / (t_b * 1e-3), "unit": UNIT,
+            "algorithmic_bytes_per_run": alg,
+            "roofline_frac": alg / (t_b * 1e-3) / 1e9 / peaks["hbm_gbs"],
+            "peak_source": f"{which} (MEASURED_PEAKS.json hbm_gbs)",
             "tile": {"moves_per_item": tile, "ctas_per_sm": ctas, "chosen_by": "mm_batch_autotune"},
             "sequential_plain": {"desc": "64 x (mm_eval_moves + mm_topk), one CUDA graph", "launches_per_run": 128,
                                  "ms_per_run": t_s, "value": evals / (t_s * 1e-3)},
@@ -724,6 +730,19 @@ def gpu_arm(args):
             "algorithmic_bytes": {"forward": 4 * p.B * (p.T + p.S), "forward_backward": 4 * p.B * 3 * (p.T + p.S)},
             "forward_gbs": 4 * p.B * (p.T + p.S) / (rel_fwd_ms * 1e-3) / 1e9,
             "forward_backward_gbs": 4 * p.B * 3 * (p.T + p.S) / (rel_both_ms * 1e-3) / 1e9,
+            # the contractions are FP32 FMA work: 2 B T S FMAs forward (O and V),
+            # B T S + 2 B S in the adjoint (sum_s c[t,s] ore, sum_s w v, dJ/dg)
+            "alu_roofline": {
+                "bound": "alu", "unit": "TFLOP/s", "peak": FP32_PEAK_TFLOPS,
+                "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2 FLOP per FMA x 2.032 GHz",
+                "forward_flop": 4.0 * p.B * p.T * p.S,
+                "forward_backward_flop": 4.0 * p.B * p.T * p.S + 2.0 * p.B * (p.T * p.S + 2 * p.S),
+                "forward_achieved": 4.0 * p.B * p.T * p.S / (rel_fwd_ms * 1e-3) / 1e12,
+                "forward_frac": 4.0 * p.B * p.T * p.S / (rel_fwd_ms * 1e-3) / 1e12 / FP32_PEAK_TFLOPS,
+                "forward_backward_achieved": (4.0 * p.B * p.T * p.S + 2.0 * p.B * (p.T * p.S + 2 * p.S))
+                / (rel_both_ms * 1e-3) / 1e12,
+                "forward_backward_frac": (4.0 * p.B * p.T * p.S + 2.0 * p.B * (p.T * p.S + 2 * p.S))
+                / (rel_both_ms * 1e-3) / 1e12 / FP32_PEAK_TFLOPS},
             "vs_plain_eval": {"plain_eval_ms": plain_eval_ms}},
         "e2e": {"value": evals_per_step * world / e2e_avg, "unit": UNIT,
                 "h2d_bytes_per_step": int(moves_h.numel()) * moves_h.element_size(),
