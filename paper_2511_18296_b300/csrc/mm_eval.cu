@@ -189,6 +189,7 @@ EvalArgs eval_args(mm_model *m, const mm_move *moves, int64_t n, float *score, u
     A.S = m->S; A.S_pad = m->S_pad; A.W = m->W; A.T = m->T; A.R = m->R; A.ore_off = m->ore_off;
     A.m_uniform = m->m_uniform;
     A.nstage = 0;
+    A.dd_smem = (size_t)(m->T + 1) * (m->T + 1) * sizeof(float) <= kDdSmemMax ? 1 : 0;
     A.prefetch = m->prefetch >= 0 ? m->prefetch : ((size_t)m->B * m->R * sizeof(float) > m->l2_bytes ? kPrefetchDram : 0);
 
     A.lambda = (float)m->lambda;
@@ -247,7 +248,8 @@ mm_status eval_launch(mm_model *m, const mm_move *moves, int64_t n, float *score
         EvalFn fn = step ? pick_step_sigma(team, kf, nq % team != 0) : pick_fast_sigma(team, kf, nq % team != 0, want_delta);
         if (fn) {
             const int T1 = m->T + 1;
-            const size_t smem = (((size_t)T1 * T1 * sizeof(float) + 15) & ~(size_t)15) + 2 * (size_t)T1 * sizeof(int64_t);
+            const size_t smem = (((A.dd_smem ? (size_t)T1 * T1 * sizeof(float) : 0) + 15) & ~(size_t)15) +
+                                2 * (size_t)T1 * sizeof(int64_t);
             if (m->smem_attr[(const void *)fn] < smem) {
                 cudaFuncAttributes fa;
                 cudaError_t e = cudaFuncGetAttributes(&fa, fn);
@@ -295,7 +297,8 @@ mm_status eval_launch(mm_model *m, const mm_move *moves, int64_t n, float *score
     A.qpl = qpl;
     const int T1 = m->T + 1;
     const size_t tab_bytes = (size_t)2 * T1 * m->S_pad * sizeof(float);
-    const size_t small = (((size_t)T1 * T1 * sizeof(float) + 15) & ~(size_t)15) + 2 * (size_t)T1 * sizeof(int64_t);
+    const size_t small = (((A.dd_smem ? (size_t)T1 * T1 * sizeof(float) : 0) + 15) & ~(size_t)15) +
+                         2 * (size_t)T1 * sizeof(int64_t);
     if (stages < 0) stages = kDefaultStages;
     if (stages > kMaxStages) stages = kMaxStages;
     const bool tma = stages > 0;

@@ -87,6 +87,7 @@ struct EvalArgs {
     int32_t qpl;           // quads per lane actually used (<= QMAX)
     int32_t nstage;        // bulk-copy pipeline depth per warp (TMA path)
     int32_t prefetch;      // direct-load path: batches whose rows are prefetched into L1 ahead
+    int32_t dd_smem;       // the (T+1)^2 discount differences are staged in shared memory (else read from ddt)
     float lambda;
     float mcm;             // mining cost of one block, mc * m (uniform mass; weighted form)
     double a, e, mc;
@@ -929,8 +930,8 @@ __global__ void __launch_bounds__(kEvalThreads, MM_EVAL_MINB) k_eval_tiled(EvalA
     const int T1 = A.T + 1;
     const size_t tab_floats = (size_t)2 * T1 * A.S_pad;
     float *s_tab = reinterpret_cast<float *>(smem);                            // [2][T+1][S_pad] if TSM
-    float *s_dd = s_tab + (TSM ? tab_floats : 0);                              // [(T+1)^2]
-    size_t off = ((TSM ? tab_floats : 0) + (size_t)T1 * T1) * sizeof(float);
+    float *s_dd = s_tab + (TSM ? tab_floats : 0);                              // [(T+1)^2] if dd_smem
+    size_t off = ((TSM ? tab_floats : 0) + (A.dd_smem ? (size_t)T1 * T1 : 0)) * sizeof(float);
     off = (off + 15) & ~(size_t)15;
     int64_t *s_mined = reinterpret_cast<int64_t *>(smem + off);                // [T+1]
     uint64_t *s_cap = reinterpret_cast<uint64_t *>(s_mined + T1);              // [T+1]
@@ -941,7 +942,8 @@ __global__ void __launch_bounds__(kEvalThreads, MM_EVAL_MINB) k_eval_tiled(EvalA
         float4 *dst = reinterpret_cast<float4 *>(s_tab);
         for (int i = tid; i < (int)(tab_floats / 4); i += kEvalThreads) dst[i] = __ldg(src + i);
     }
-    for (int i = tid; i < T1 * T1; i += kEvalThreads) s_dd[i] = __ldg(A.ddt + i);
+    if (A.dd_smem)
+        for (int i = tid; i < T1 * T1; i += kEvalThreads) s_dd[i] = __ldg(A.ddt + i);
     for (int i = tid; i < T1; i += kEvalThreads) {
         s_mined[i] = A.minedT[i];
         s_cap[i] = A.cap[i];
@@ -955,7 +957,8 @@ __global__ void __launch_bounds__(kEvalThreads, MM_EVAL_MINB) k_eval_tiled(EvalA
     const int64_t gw = (int64_t)blockIdx.x * NW + warp;
     const int64_t r0 = gw * A.n / nwarps, r1 = (gw + 1) * A.n / nwarps;
     uint64_t wtk = 0;  // this warp's best 32 candidate keys (TOPK)
-    eval_warp_range<TEAM, QMAX, KAHAN, DELTA, KF, TAIL, TOPK, SIG>(A, sh, tab, s_dd, s_mined, s_cap, r0, r1, wtk);
+    eval_warp_range<TEAM, QMAX, KAHAN, DELTA, KF, TAIL, TOPK, SIG>(A, sh, tab, A.dd_smem ? s_dd : A.ddt, s_mined,
+                                                                   s_cap, r0, r1, wtk);
     if constexpr (TOPK) step_reduce(A.tail, wtk, A.tail.do_apply ? sh.best : nullptr);
 }
 
@@ -1018,6 +1021,11 @@ __device__ __forceinline__ bool stage_wait(uint64_t *bar, uint32_t parity) {
 
 constexpr int kMaxStages = 4;
 constexpr int kDefaultStages = 0;    // direct loads measured faster than bulk copies of 416-byte rows
+// The (T+1)^2 table of discount differences is staged in shared memory while
+// it takes at most this many bytes (T <= 89); above, the kernels read it from
+// global memory through L1 (at T = 254 it would take 254 KB).
+constexpr size_t kDdSmemMax = 32 * 1024;
+
 // Built-in L1 prefetch distance (batches ahead): none while the value rows fit
 // in L2 (there the prefetches only add L1 traffic), one batch once they exceed
 // it and the gathers come from DRAM (measured: 50k blocks x 100 scenarios is
@@ -1043,8 +1051,8 @@ __global__ void __launch_bounds__(kEvalThreads, 1) k_eval_tma(EvalArgs A) {
     const int R = A.R;
     const size_t tab_floats = (size_t)2 * T1 * A.S_pad;
     float *s_tab = reinterpret_cast<float *>(smem);                            // [2][T+1][S_pad] if TSM
-    float *s_dd = s_tab + (TSM ? tab_floats : 0);                              // [(T+1)^2]
-    size_t off = ((TSM ? tab_floats : 0) + (size_t)T1 * T1) * sizeof(float);
+    float *s_dd = s_tab + (TSM ? tab_floats : 0);                              // [(T+1)^2] if dd_smem
+    size_t off = ((TSM ? tab_floats : 0) + (A.dd_smem ? (size_t)T1 * T1 : 0)) * sizeof(float);
     off = (off + 15) & ~(size_t)15;
     int64_t *s_mined = reinterpret_cast<int64_t *>(smem + off);                // [T+1]
     uint64_t *s_cap = reinterpret_cast<uint64_t *>(s_mined + T1);              // [T+1]
@@ -1058,7 +1066,9 @@ __global__ void __launch_bounds__(kEvalThreads, 1) k_eval_tma(EvalArgs A) {
         float4 *dst = reinterpret_cast<float4 *>(s_tab);
         for (int i = tid; i < (int)(tab_floats / 4); i += blockDim.x) dst[i] = __ldg(src + i);
     }
-    for (int i = tid; i < T1 * T1; i += blockDim.x) s_dd[i] = __ldg(A.ddt + i);
+    if (A.dd_smem)
+        for (int i = tid; i < T1 * T1; i += blockDim.x) s_dd[i] = __ldg(A.ddt + i);
+    const float *dd_tab = A.dd_smem ? s_dd : A.ddt;
     for (int i = tid; i < T1; i += blockDim.x) {
         s_mined[i] = A.minedT[i];
         s_cap[i] = A.cap[i];
@@ -1176,7 +1186,7 @@ __global__ void __launch_bounds__(kEvalThreads, 1) k_eval_tma(EvalArgs A) {
             const int slot = act ? list[e] : 0;
             const uint32_t tt = act ? s_tt[warp][slot] : 0;
             const uint32_t t1 = tt & 0xffu, t2 = tt >> 8;
-            const float dd = s_dd[t1 * T1 + t2];
+            const float dd = dd_tab[t1 * T1 + t2];
             const float *row1 = stage0 + ((size_t)st * TPW + tw) * 2 * R;
             const float *row2 = row1 + R;
             float d[QMAX][4];
