@@ -74,11 +74,13 @@ def run(m, x, g):
     return float(J.cpu()[0]), npv.cpu().numpy(), ot.cpu().numpy(), gx.cpu().numpy(), gg.cpu().numpy()
 
 
-@pytest.mark.parametrize("S,T", [(9, 5), (1, 3), (37, 17), (100, 20), (200, 30), (1024, 30)])
+@pytest.mark.parametrize("S,T", [(9, 5), (1, 3), (37, 17), (100, 20), (200, 30), (1024, 30), (100, 97), (8, 254)])
 def test_relaxed_small_vs_oracle(S, T):
     """(200, 30): two period tiles and two scenario tiles in the forward, the
     tiled adjoint over two period tiles; (1024, 30): eight scenario tiles, and
-    the adjoint whose tile would not fit in shared memory (one warp per block)."""
+    the adjoint whose tile would not fit in shared memory (one warp per block);
+    (100, 97): T not a multiple of 4, a one-period last tile; (8, 254): the
+    period limit, eleven period tiles."""
     p = tiny_problem(6, 5, 4, S=S, T=T, seed=S + T, target_blocks=7)
     x = W.relaxed_x(p.B, p.T, 2)
     g = p.grade.astype(np.float32)
@@ -92,7 +94,7 @@ def test_relaxed_small_vs_oracle(S, T):
     check_close(gg, r["gg"], r["floor_g"], "dJ/dg")
 
 
-@pytest.mark.parametrize("S,T", [(12, 6), (200, 30), (1024, 30)])
+@pytest.mark.parametrize("S,T", [(12, 6), (200, 30), (1024, 30), (12, 254)])
 def test_relaxed_model_grades_path(S, T):
     """g = NULL: the model's own FP64 grades (value rows and ore words staged
     per scenario tile)."""
