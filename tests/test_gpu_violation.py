@@ -70,3 +70,13 @@ def test_50k_sample():
     m = _check(p, p.moves, sample=sample)
     with pytest.raises(Exception):
         m.eval_violation(torch.zeros((0, 2), dtype=torch.int64, device="cuda"))
+
+
+def test_period_limit_every_move():
+    """T = 254 (the limit), blocks spread over the periods, one block of
+    capacity per period so that many shifts overfill their target period."""
+    B, T = 27, 254
+    x0 = np.minimum(np.arange(B) * (T // B), T - 1).astype(np.uint8)
+    p = tiny_problem(S=4, T=T, cap_blocks=1, seed=11, x0=x0)
+    mv = np.concatenate([all_moves(p.B, p.T), [[0, -(p.T + 2)]]]).astype(np.int32)
+    _check(p, mv)
