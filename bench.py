@@ -39,6 +39,7 @@ WORKLOAD = "plain_50k"
 METRIC = "move-scenario evals/sec at 50k blocks, S=100; % of HBM roofline vs plain form"
 UNIT = "move-scenario evals/s"
 TOPK = 32
+HBM_NOMINAL_GBS = 7700.0  # B300 HBM3e nominal bandwidth, for context beside the measured copy peak
 FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12  # CUDA-core FP32 FMA peak at the maximum SM clock
 FLUSH_BYTES = 256 << 20
 EVAL_KERNEL = "k_eval_tiled"  # the move evaluator (mm_eval_moves launches it alone)
@@ -704,7 +705,8 @@ def gpu_arm(args):
                      "kernel": EVAL_KERNEL + " (mm_eval_moves: one evaluation launch per batch, timed in the plain form)",
                      "kernel_ms": plain_eval_ms,
                      "step_frac": alg / (step_avg_ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
-                     "algorithmic_bytes_per_launch": alg, "peak_source": f"{which} (MEASURED_PEAKS.json hbm_gbs)"},
+                     "algorithmic_bytes_per_launch": alg, "peak_source": f"{which} (MEASURED_PEAKS.json hbm_gbs)",
+                     "nominal_peak": HBM_NOMINAL_GBS, "frac_of_nominal": achieved_gbs / HBM_NOMINAL_GBS},
         "plain_form": {"desc": "mm_eval_moves, then mm_topk + mm_apply_best: one launch per call, same workload",
                        "value": evals_per_step * world / (plain_step_ms * 1e-3), "unit": UNIT,
                        "ms_per_step": plain_step_ms, "eval_kernel_ms": plain_eval_ms,
