@@ -191,7 +191,8 @@ mm_status mm_set_tile(mm_model *m, int32_t team, int32_t ctas_per_sm, int32_t st
 /* Evaluation options for mm_eval_moves_ex. */
 enum {
     MM_EVAL_PLAIN = 0,     /* FP32 scenario sums, tree reduction */
-    MM_EVAL_KAHAN = 1,     /* compensated (TwoSum) scenario sums for mean and variance */
+    MM_EVAL_KAHAN = 1,     /* compensated scenario sums for mean and variance (Neumaier's update
+                              per scenario, error-free TwoSum merges across the lanes of a team) */
     MM_EVAL_GENERIC = 2    /* use the evaluator whose scenario loop is shaped at run time even
                               where a compile-time-shaped one exists (same results; for
                               cross-checking the two) */
