@@ -219,7 +219,7 @@ mm_status mm_eval_moves_ex(mm_model *m, const mm_move *moves_dev, int64_t n, flo
 mm_status mm_topk(mm_model *m, const float *score_dev, const uint8_t *feasible_dev, int64_t n,
                   int32_t k, int32_t *idx_dev, float *topscore_dev, int32_t *count_dev);
 
-/* One local-search step in two launches (Algorithm 4's evaluate-then-assign
+/* One local-search step, one launch for S <= 256 (Algorithm 4's evaluate-then-assign
  * loop body with Algorithm 5's candidate evaluation): evaluates the n moves
  * exactly as mm_eval_moves (score_dev[n], feasible_dev[n]), selects the k best
  * feasible ones exactly as mm_topk (idx_dev[k], topscore_dev[k], *count_dev;
