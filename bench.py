@@ -42,6 +42,7 @@ TOPK = 32
 HBM_NOMINAL_GBS = 7700.0  # B300 HBM3e nominal bandwidth, for context beside the measured copy peak
 FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12  # CUDA-core FP32 FMA peak at the maximum SM clock
 FLUSH_BYTES = 256 << 20
+K_FORM = 50  # timed steps of every secondary form (median and best of 50)
 EVAL_KERNEL = "k_eval_tiled"  # the move evaluator (mm_eval_moves launches it alone)
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k_eval_tiled_plain_50k.md")
 EVAL_SOURCES = ["paper_2511_18296_b300/csrc/mm_eval.cu", "paper_2511_18296_b300/csrc/mm_eval_tiled.cuh",
@@ -152,6 +153,62 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": reasons, "samples": len(inside),
                 "power_w_max": max((float(r[4]) for r in inside if r[4].replace(".", "").isdigit()), default=None)}
+
+
+class StepTimer:
+    """Device time of single steps, each bracketed by two CUDA events recorded
+    inside a CUDA graph (external event nodes), an L2 flush before every step
+    outside the events.  A graph holds up to R steps; it is replayed until K
+    steps are timed, reading its events after each replay (a replay re-records
+    them).  The host enqueues nothing between the events, so host overhead never
+    shows up inside a step."""
+
+    def __init__(self, stream, flush, R: int = 50):
+        self.stream, self.flush, self.R = stream, flush, R
+
+    def graph(self, fns, R=None):
+        import torch
+        R = R or self.R
+        evs = [(torch.cuda.Event(enable_timing=True, external=True),
+                torch.cuda.Event(enable_timing=True, external=True)) for _ in range(R)]
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=self.stream):
+            for e0, e1 in evs:
+                self.flush.zero_()
+                e0.record(self.stream)
+                for fn in fns:
+                    fn()
+                e1.record(self.stream)
+        return g, evs
+
+    def run(self, ge, K: int):
+        """Per-step device times (ms) of K steps."""
+        g, evs = ge
+        out = []
+        while len(out) < K:
+            g.replay()
+            evs[-1][1].synchronize()
+            out.extend(e0.elapsed_time(e1) for e0, e1 in evs)
+        return out[:K]
+
+    def warm(self, ge, seconds: float = 0.0, reps: int = 3):
+        """Untimed replays: at least reps, and for at least `seconds` (brings the
+        clocks up under load before a timed region)."""
+        g, evs = ge
+        t0 = time.perf_counter()
+        r = 0
+        while r < reps or time.perf_counter() - t0 < seconds:
+            g.replay()
+            r += 1
+        evs[-1][1].synchronize()
+
+
+def stats(ts):
+    """Median, best, interquartile range and mean of per-step times (ms)."""
+    a = np.asarray(ts, float)
+    return {"n": int(a.size), "median_ms": float(np.median(a)), "min_ms": float(a.min()),
+            "p25_ms": float(np.percentile(a, 25)), "p75_ms": float(np.percentile(a, 75)),
+            "mean_ms": float(a.mean())}
 
 
 # ----------------------------------------------------------------- CPU oracle
@@ -273,7 +330,7 @@ def reference_arm(args):
 # ------------------------------------------------------------------ GPU arm
 
 
-def batched_form(stream, flush, reps: int = 30):
+def batched_form(stream, flush, reps: int = K_FORM):
     """The 64-chain workload (cube sides 15..40, S in {16, 32, 64, 100}, T = 20,
     1,024..65,536 moves per chain, seeds 100..163): one persistent batched launch
     (autotuned tile, replayed from a CUDA graph) against the same 64 chains as
@@ -295,52 +352,40 @@ def batched_form(stream, flush, reps: int = 30):
     b = mm.Batch(list(zip(models, mvs)), k=TOPK, stream=stream)
     tile, ctas, _ = b.autotune(reps=3)
 
-    def graph_of(fn):
-        with torch.cuda.stream(stream):
-            fn()
-        stream.synchronize()
-        g = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(g, stream=stream):
-            fn()
-        return g
+    timer = StepTimer(stream, flush, R=reps)
 
     def seq():
         for m, mv, o in zip(models, mvs, b.out):
             m.eval_moves(mv, score=o["score"], feas=o["feas"], want_mean=False)
             m.topk(o["score"], o["feas"], TOPK, idx=o["idx"], top=o["top"], count=o["count"])
 
-    def time_graph(g):
-        ts = []
+    def run_ms(fn):
         with torch.cuda.stream(stream):
-            for r in range(reps + 3):
-                flush.zero_()
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                g.replay()
-                e1.record(stream)
-                e1.synchronize()
-                if r >= 3:
-                    ts.append(e0.elapsed_time(e1))
-        return float(np.mean(ts))
+            fn()
+        stream.synchronize()
+        ge = timer.graph([fn])
+        timer.warm(ge)
+        return timer.run(ge, reps)
 
-    t_b = time_graph(graph_of(b.run))
-    t_s = time_graph(graph_of(seq))
+    bt = run_ms(b.run)
+    st = run_ms(seq)
+    t_b, t_s = float(np.mean(bt)), float(np.mean(st))
     b.close()
     alg = float(sum(algorithmic_bytes(p.moves, p.S) for p in probs))
     peaks, which = measured_peaks()
     return {"workload": "64 chains: cubes of side 15..40, S in {16, 32, 64, 100}, T=20, 1,024..65,536 moves each",
             "evals_per_run": evals, "chains": 64, "launches_per_run": 1,
-            "ms_per_run": t_b, "value": evals / (t_b * 1e-3), "unit": UNIT,
+            "ms_per_run": t_b, "time": stats(bt), "value": evals / (t_b * 1e-3), "unit": UNIT,
             "algorithmic_bytes_per_run": alg,
             "roofline_frac": alg / (t_b * 1e-3) / 1e9 / peaks["hbm_gbs"],
             "peak_source": f"{which} (MEASURED_PEAKS.json hbm_gbs)",
             "tile": {"moves_per_item": tile, "ctas_per_sm": ctas, "chosen_by": "mm_batch_autotune"},
             "sequential_plain": {"desc": "64 x (mm_eval_moves + mm_topk), one CUDA graph", "launches_per_run": 128,
-                                 "ms_per_run": t_s, "value": evals / (t_s * 1e-3)},
+                                 "ms_per_run": t_s, "time": stats(st), "value": evals / (t_s * 1e-3)},
             "speedup_vs_sequential": t_s / t_b}
 
 
-def stress_form(stream, flush, reps: int = 10, n_accept: int = 1000):
+def stress_form(stream, flush, reps: int = 20, n_accept: int = 1000):
     """The 100x100x40 = 400,000-block workload, S = 500, T = 30, 1,048,576
     moves (70 % shifts; seed 3).  Its 806 MB of value rows exceed L2, so here
     the evaluation streams them from DRAM.  Timed (CUDA events around CUDA-graph
@@ -367,30 +412,23 @@ def stress_form(stream, flush, reps: int = 10, n_accept: int = 1000):
     top = torch.empty(TOPK, dtype=torch.float32, device=dev)
     cnt = torch.empty(1, dtype=torch.int32, device=dev)
 
-    def time_fn(fn):
+    timer = StepTimer(stream, flush, R=reps)
+    times = {}
+
+    def time_fn(fn, name):
         with torch.cuda.stream(stream):
             fn()
         stream.synchronize()
-        g = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(g, stream=stream):
-            fn()
-        ts = []
-        with torch.cuda.stream(stream):
-            for r in range(reps + 3):
-                flush.zero_()
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                g.replay()
-                e1.record(stream)
-                e1.synchronize()
-                if r >= 3:
-                    ts.append(e0.elapsed_time(e1))
-        return float(np.mean(ts))
+        ge = timer.graph([fn])
+        timer.warm(ge)
+        m.schedule_set(p.x0)
+        times[name] = timer.run(ge, reps)
+        return float(np.mean(times[name]))
 
-    plain_ms = time_fn(lambda: m.eval_moves(mv, score=score, feas=feas, want_mean=False))
-    kahan_ms = time_fn(lambda: m.eval_moves(mv, score=score, feas=feas, want_mean=False, kahan=True))
+    plain_ms = time_fn(lambda: m.eval_moves(mv, score=score, feas=feas, want_mean=False), "eval")
+    kahan_ms = time_fn(lambda: m.eval_moves(mv, score=score, feas=feas, want_mean=False, kahan=True), "kahan")
     step_ms = time_fn(lambda: m.search_step(mv, k=TOPK, apply=True, score=score, feas=feas, idx=idx, top=top,
-                                            count=cnt))
+                                            count=cnt), "step")
     # drift: FP64 running totals beside their FP32 shadow over n_accept applies
     m.set_fp32_shadow(True)
     m.schedule_set(p.x0)
@@ -411,11 +449,11 @@ def stress_form(stream, flush, reps: int = 10, n_accept: int = 1000):
     return {"workload": "100x100x40 = 400,000 blocks, S=500, T=30, 1,048,576 moves (70% shifts, 30% swaps)",
             "desc": "value rows (806 MB) larger than L2: the evaluation reads them from DRAM",
             "algorithmic_bytes_per_launch": alg,
-            "eval_kernel_ms": plain_ms, "eval_roofline_frac": alg / (plain_ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
+            "eval_kernel_ms": plain_ms, "eval_time": stats(times["eval"]), "eval_roofline_frac": alg / (plain_ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
             "eval_value": evals / (plain_ms * 1e-3),
-            "compensated_eval_kernel_ms": kahan_ms,
+            "compensated_eval_kernel_ms": kahan_ms, "compensated_eval_time": stats(times["kahan"]),
             "compensated_eval_roofline_frac": alg / (kahan_ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
-            "step_ms": step_ms, "step_desc": "mm_search_step: evaluate + top-32 (one launch), then the apply launch",
+            "step_ms": step_ms, "step_time": stats(times["step"]), "step_desc": "mm_search_step: evaluate + top-32 + apply the best move, one launch",
             "value": evals / (step_ms * 1e-3), "unit": UNIT,
             "peak_source": f"{which} (MEASURED_PEAKS.json hbm_gbs)",
             "accepted_moves": accepted, "steps": steps}, drift_in
@@ -474,71 +512,43 @@ def gpu_arm(args):
             plain_rest()
     stream.synchronize()
 
-    R = 20  # steps per CUDA graph
+    timer = StepTimer(stream, flush, R=K_FORM)
 
-    def graph_of(fns):
-        """A CUDA graph of R steps, each an L2 flush followed by the launches
-        of fns (as a search loop runs them: back to back)."""
-        g = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(g, stream=stream):
-            for _ in range(R):
-                flush.zero_()
-                for fn in fns:
-                    fn()
-        return g
+    def form_ms(fns, K=None, reset=True):
+        """Per-step device times of a form: K steps (K_FORM by default) from
+        the initial schedule, after three untimed ones."""
+        ge = timer.graph(fns)
+        timer.warm(ge)
+        if reset:
+            m.schedule_set(p.x0)
+        return timer.run(ge, K or K_FORM)
 
-    def replay_ms(g):
-        """Device time (ms) of one replay, CUDA events on the launching stream."""
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        with torch.cuda.stream(stream):
-            e0.record(stream)
-            g.replay()
-            e1.record(stream)
-        e1.synchronize()
-        return e0.elapsed_time(e1)
-
-    g_flush = graph_of([])
-
-    def steps_ms(g, K):
-        """Per-step device times (ms) of K steps: replays of g (R steps each)
-        alternate with replays of the flush-only graph, and each replay's
-        flushes are subtracted, so the L2 flush between steps stays outside
-        the step times while the steps run exactly as in a loop (events
-        recorded between the launches would add their own gaps)."""
-        out = []
-        while len(out) < K:
-            t, f = replay_ms(g), replay_ms(g_flush)
-            out.extend([(t - f) / R] * R)
-        return out[:K]
-
-    g_step = graph_of([fused])
-    replay_ms(g_step)
-    replay_ms(g_flush)
-    m.schedule_set(p.x0)  # every timed run starts from the same schedule
     K = args.steps
+    g_step = timer.graph([fused], R=K if K <= 50 else 50)
     with ClockSampler(local) as clk:
+        t_load = time.time()
+        timer.warm(g_step, seconds=0.3)  # the clocks under load before the timed region
+        m.schedule_set(p.x0)  # every timed run starts from the same schedule
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
         t_start = time.time()
-        step_t = steps_ms(g_step, K)
+        step_t = timer.run(g_step, K)
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
         t_end = time.time()
     total_ms = float(sum(step_t))
     step_avg_ms = total_ms / K
+    step_stats = stats(step_t)
     applied, npv_mean, _ = m.last_apply()
     # the plain form (one launch per call) and the compensated-sum evaluator, same workload
-    Kp = max(20, min(K, 500))
-    g_eval, g_plain = graph_of([plain_eval]), graph_of([plain_eval, plain_rest])
-    g_kahan = graph_of([lambda: m.eval_moves(moves_d, score=score, feas=feas, want_mean=False, kahan=True)])
-    m.schedule_set(p.x0)
-    plain_eval_ms = float(np.mean(steps_ms(g_eval, Kp)))
-    m.schedule_set(p.x0)
-    plain_step_ms = float(np.mean(steps_ms(g_plain, Kp)))
-    m.schedule_set(p.x0)
-    kahan_eval_ms = float(np.mean(steps_ms(g_kahan, Kp)))
+    eval_t = form_ms([plain_eval])
+    plain_eval_ms = float(np.mean(eval_t))
+    plain_t = form_ms([plain_eval, plain_rest])
+    plain_step_ms = float(np.mean(plain_t))
+    kahan_t = form_ms([lambda: m.eval_moves(moves_d, score=score, feas=feas, want_mean=False, kahan=True)])
+    kahan_eval_ms = float(np.mean(kahan_t))
     m.schedule_set(p.x0)
     # violation magnitudes of the batch (epsilon-relaxed fitness), same moves
     cap_ex = torch.empty(n, dtype=torch.int64, device=dev)
@@ -546,7 +556,8 @@ def gpu_arm(args):
     viol = lambda: m.eval_violation(moves_d, cap_ex, prec_ex)  # noqa: E731
     with torch.cuda.stream(stream):
         viol()
-    viol_ms = float(np.mean(steps_ms(graph_of([viol]), Kp)))
+    viol_t = form_ms([viol], reset=False)
+    viol_ms = float(np.mean(viol_t))
     # differentiated form: relaxed objective forward and adjoint on the same model
     xr = torch.as_tensor(W.relaxed_x(p.B, p.T, 2), device=dev)
     gr = torch.as_tensor(p.grade.astype(np.float32), device=dev)
@@ -560,8 +571,10 @@ def gpu_arm(args):
     with torch.cuda.stream(stream):
         fwd_bwd()
     stream.synchronize()
-    rel_fwd_ms = float(np.mean(steps_ms(graph_of([fwd]), Kp)))
-    rel_both_ms = float(np.mean(steps_ms(graph_of([fwd_bwd]), Kp)))
+    fwd_t = form_ms([fwd], reset=False)
+    rel_fwd_ms = float(np.mean(fwd_t))
+    both_t = form_ms([fwd_bwd], reset=False)
+    rel_both_ms = float(np.mean(both_t))
     # weighted form: the same model and batch with uncertainty weights sigma(s,t)
     mw = mm.Model.from_problem(p, sigma=W.uncertainty_weights(p.T, p.S))
     mw.schedule_set(p.x0)
@@ -573,10 +586,16 @@ def gpu_arm(args):
         w_eval()
         w_step()
     stream.synchronize()
+    ge = timer.graph([w_eval])
+    timer.warm(ge)
     mw.schedule_set(p.x0)
-    w_eval_ms = float(np.mean(steps_ms(graph_of([w_eval]), Kp)))
+    w_eval_t = timer.run(ge, K_FORM)
+    w_eval_ms = float(np.mean(w_eval_t))
+    ge = timer.graph([w_step])
+    timer.warm(ge)
     mw.schedule_set(p.x0)
-    w_step_ms = float(np.mean(steps_ms(graph_of([w_step]), Kp)))
+    w_step_t = timer.run(ge, K_FORM)
+    w_step_ms = float(np.mean(w_step_t))
     # scores of a seeded sample of the batch at the initial schedule, for the
     # accuracy report against the FP64 oracle (made in the CPU leg)
     acc_sel = np.sort(np.random.default_rng(5).choice(n, min(n, 4096), replace=False))
@@ -605,7 +624,7 @@ def gpu_arm(args):
     # the batch travels in the compact 4-byte form (mm_search_step_packed
     # decodes it inside the step's launch) when the model allows it, else as
     # 8-byte moves
-    packed = p.B + p.T + 1 <= 65536 and p.S <= 256
+    packed = p.B + p.T + 1 <= 65536 and p.S <= 768
     if packed:
         moves_h = torch.from_numpy(mm.pack_moves(p.moves, p.B, p.T).view(np.int32)).pin_memory()
     else:
@@ -686,19 +705,25 @@ def gpu_arm(args):
     alg = algorithmic_bytes(p.moves, S)
     peaks, which = measured_peaks()
     achieved_gbs = alg / (plain_eval_ms * 1e-3) / 1e9
-    clocks = clk.summary(t_start, t_end)
+    clocks = clk.summary(t_load, t_end)
+    clocks["window"] = "0.3 s of untimed steps under load, then the timed steps"
+    if clocks.get("sm_mhz"):
+        # time x clock separates clock effects from box effects: SM cycles per step
+        clocks["step_median_kcycles"] = step_stats["median_ms"] * clocks["sm_mhz"]
+        clocks["eval_median_kcycles"] = float(np.median(eval_t)) * clocks["sm_mhz"]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
         "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic (seeded lognormal Gaussian-random-field grades; no public dataset)",
         "config": {"workload": "50x50x20 = 50,000 blocks, S=100, T=20, 262,144 moves (50% shifts, 50% swaps)",
                    "step": ("mm_search_step: evaluate + top-32 + apply the best move, "
-                            + ("one launch" if S <= 256 else "an evaluation launch and an apply launch")
+                            + ("one launch" if S <= 768 else "an evaluation launch and an apply launch")
                             + ", replayed from a CUDA graph"),
                    "topk": TOPK,
                    "l2": "flushed before every step (256 MB write outside the step events)",
-                   "timing": (f"CUDA events around replays of a CUDA graph of {R} (flush, step) pairs, minus replays "
-                              f"of the {R} flushes alone"),
+                   "timing": ("every step bracketed by CUDA events recorded inside a CUDA graph of (flush, step) "
+                              "pairs (external event nodes; the flush outside the events); 0.3 s of untimed steps "
+                              "under load first; forms: median, best and quartiles of 50 steps"),
                    "per_rank_moves": n, "parallelism": f"independent batches x{world}"},
         "roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved_gbs / peaks["hbm_gbs"], "traffic": profiled_traffic(),
@@ -707,28 +732,31 @@ def gpu_arm(args):
                      "step_frac": alg / (step_avg_ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
                      "algorithmic_bytes_per_launch": alg, "peak_source": f"{which} (MEASURED_PEAKS.json hbm_gbs)",
                      "nominal_peak": HBM_NOMINAL_GBS, "frac_of_nominal": achieved_gbs / HBM_NOMINAL_GBS},
+        "step_time": step_stats,
         "plain_form": {"desc": "mm_eval_moves, then mm_topk + mm_apply_best: one launch per call, same workload",
+                       "step_time": stats(plain_t), "eval_time": stats(eval_t),
                        "value": evals_per_step * world / (plain_step_ms * 1e-3), "unit": UNIT,
                        "ms_per_step": plain_step_ms, "eval_kernel_ms": plain_eval_ms,
                        "eval_roofline_frac": achieved_gbs / peaks["hbm_gbs"], "eval_achieved_gbs": achieved_gbs},
         "precision_form": {"desc": "mm_eval_moves_ex with compensated scenario sums (MM_EVAL_KAHAN); drift: NPV from "
                                    "the FP64 running totals and from an FP32 shadow after 1,000 applies, against the "
                                    "oracle's recomputation",
-                           "eval_kernel_ms": kahan_eval_ms,
+                           "eval_kernel_ms": kahan_eval_ms, "eval_time": stats(kahan_t),
                            "eval_roofline_frac": alg / (kahan_eval_ms * 1e-3) / 1e9 / peaks["hbm_gbs"]},
         "weighted_form": {"desc": "uncertainty weights sigma(s,t) of Eq. 12 (synthetic, seed 4) on the same model and "
                                   "batch: evaluation launch, and the fused step (evaluate + top-32 + apply, one "
                                   "launch)",
-                          "eval_kernel_ms": w_eval_ms,
+                          "eval_kernel_ms": w_eval_ms, "eval_time": stats(w_eval_t), "step_time": stats(w_step_t),
                           "eval_roofline_frac": alg / (w_eval_ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
                           "step_ms": w_step_ms,
                           "value": n * p.S / (w_step_ms * 1e-3), "unit": UNIT},
         "violation_form": {"desc": "mm_eval_violation: capacity and precedence excess of every move (exact integers)",
-                           "ms_per_batch": viol_ms, "moves_per_s": n / (viol_ms * 1e-3)},
+                           "ms_per_batch": viol_ms, "moves_per_s": n / (viol_ms * 1e-3), "time": stats(viol_t)},
         "differentiated_form": {
             "desc": "relaxed objective on the same model, x[b,t] ~ Dirichlet(1) (seed 2): forward, and forward + "
                     "adjoint (dJ/dx, dJ/dg)",
             "forward_ms": rel_fwd_ms, "forward_backward_ms": rel_both_ms,
+            "forward_time": stats(fwd_t), "forward_backward_time": stats(both_t),
             "algorithmic_bytes": {"forward": 4 * p.B * (p.T + p.S), "forward_backward": 4 * p.B * 3 * (p.T + p.S)},
             "forward_gbs": 4 * p.B * (p.T + p.S) / (rel_fwd_ms * 1e-3) / 1e9,
             "forward_backward_gbs": 4 * p.B * 3 * (p.T + p.S) / (rel_both_ms * 1e-3) / 1e9,
@@ -757,7 +785,7 @@ def gpu_arm(args):
                          "double-buffered (batch k+1 copied and step k-1's result read back on a second stream while "
                          "step k runs), the host not waiting on each step; L2 flush inside each step; NPV statistics "
                          "read after the last step")},
-        "gpu_launches": (1 if S <= 256 else 2) * K,  # per step: the evaluation launch (top-k and apply inside when S <= 256)
+        "gpu_launches": (1 if S <= 768 else 2) * K,  # per step: the evaluation launch (top-k and apply inside when S <= 768)
         "clocks": clocks,
         "check": {"last_apply": applied, "npv_mean": npv_mean, "e2e_npv_mean": e2e_mean},
     }

@@ -191,8 +191,12 @@ mm_status mm_set_tile(mm_model *m, int32_t team, int32_t ctas_per_sm, int32_t st
 /* Evaluation options for mm_eval_moves_ex. */
 enum {
     MM_EVAL_PLAIN = 0,     /* FP32 scenario sums, tree reduction */
-    MM_EVAL_KAHAN = 1,     /* compensated scenario sums for mean and variance (Neumaier's update
-                              per scenario, error-free TwoSum merges across the lanes of a team) */
+    MM_EVAL_KAHAN = 1,     /* compensated scenario sums: the mean's sum by Kahan's update per
+                              scenario (error-free TwoSum merges across the lanes of a team), the
+                              variance by the corrected two-pass formula (the sum of squared
+                              deviations minus (sum of deviations)^2 / S, which removes the error
+                              of the rounded mean; the squares need no compensation: they are
+                              non-negative, nothing cancels) */
     MM_EVAL_GENERIC = 2    /* use the evaluator whose scenario loop is shaped at run time even
                               where a compile-time-shaped one exists (same results; for
                               cross-checking the two) */
@@ -219,20 +223,28 @@ mm_status mm_eval_moves_ex(mm_model *m, const mm_move *moves_dev, int64_t n, flo
 mm_status mm_topk(mm_model *m, const float *score_dev, const uint8_t *feasible_dev, int64_t n,
                   int32_t k, int32_t *idx_dev, float *topscore_dev, int32_t *count_dev);
 
-/* One local-search step, one launch for S <= 256 (Algorithm 4's evaluate-then-assign
+/* One local-search step, one launch for S <= 768 (Algorithm 4's evaluate-then-assign
  * loop body with Algorithm 5's candidate evaluation): evaluates the n moves
  * exactly as mm_eval_moves (score_dev[n], feasible_dev[n]), selects the k best
  * feasible ones exactly as mm_topk (idx_dev[k], topscore_dev[k], *count_dev;
  * 1 <= k <= 32), and, if apply != 0, applies the best one on the device exactly
- * as mm_apply_best (outcome via mm_last_apply).  The evaluation launch keeps
- * each warp's 32 best keys in registers (warp shuffles); each CTA publishes
- * one list, the last CTA of each group of CTAs merges its group's lists and
- * the last group merges the group lists and writes the top k (tickets, no
- * waiting), all inside the same launch.  When S <= 256 that final CTA also
- * applies the best move from the record the evaluation kept of it (its blocks
- * and periods), so the step is one launch; otherwise a one-CTA apply launch
- * follows.  Needs equal block masses (else MM_ERR_INVALID_ARG; use the
- * separate calls).
+ * as mm_apply_best (outcome via mm_last_apply).  The launch runs one CTA of
+ * 768 threads per SM (mm_set_tile's ctas_per_sm does not apply to it); each
+ * warp keeps its 32 best keys in registers (warp shuffles), each CTA merges
+ * its warps' lists and publishes one list, and the CTA that finishes last
+ * (a ticket, no waiting) ranks the lists' heads, merges the lists that can
+ * hold one of the 32 best keys and writes the top k.  When S <= 768 that
+ * final CTA also applies the best move from the record the evaluation kept of
+ * it (its blocks and periods): the tonnage, schedule words and penalty tables
+ * (everything the next evaluation reads) in this launch, the move's FP64
+ * totals (metal, net cash per period, NPV_s) by the next step's CTAs on this
+ * model (a share of the scenarios each, while they still evaluate) or, before
+ * that, by the library ahead of any call that reads or changes those totals
+ * (mm_npv, mm_last_apply, mm_get_metal, mm_apply_move, mm_apply_best,
+ * mm_get_fp32_shadow_npv, mm_set_fp32_shadow, mm_batch_run with apply);
+ * mm_schedule_set discards it.  Every total is the same bits as with
+ * mm_apply_best.  Above 768 scenarios a one-CTA apply launch follows.  Needs
+ * equal block masses (else MM_ERR_INVALID_ARG; use the separate calls).
  * Calls on one model must not overlap on the GPU (they share the model's
  * list storage).  Asynchronous. */
 mm_status mm_search_step(mm_model *m, const mm_move *moves_dev, int64_t n, int32_t k, int32_t apply,
@@ -246,7 +258,7 @@ mm_status mm_search_step(mm_model *m, const mm_move *moves_dev, int64_t n, int32
  * exactly those of mm_unpack_moves followed by mm_search_step on the same
  * batch; codes that name no move are bad moves (feasible = 0, score = -inf,
  * sticky MM_ERR_BAD_MOVE).  Only where the whole step is one launch: needs
- * B + T + 1 <= 65536, equal block masses, S <= 256 when apply != 0, and, with
+ * B + T + 1 <= 65536, equal block masses, S <= 768 when apply != 0, and, with
  * uncertainty weights, the weighted fast form (S % 4 == 0); otherwise
  * MM_ERR_INVALID_ARG (use mm_unpack_moves and mm_search_step).
  * Asynchronous. */

@@ -191,49 +191,100 @@ static __device__ __forceinline__ void ctab_rebuild(const float *__restrict__ tb
     }
 }
 
-// Shared-memory copy of the Pout / Pin tables used by the period-pair rebuild
-// when 2 (T+1) S_pad floats fit (18 KB).
-constexpr int kApplyTabMax = 4608;
+// Shared scratch of an apply: the new Pout / Pin entries of the two changed
+// periods, 4 S_pad floats (S_pad <= 1024).
+constexpr int kApplyTabMax = 4096;
 
-// Apply a decoded move v on a single CTA (blockDim.x >= max(S, 64), a multiple
-// of 32).  go = 1: v is valid, feasible and changes the schedule (the caller
-// has checked it against the current state); go = 0: nothing changes.
+// The FP64 side of scenario s's update for a move of b1 from t1 to t2 (and,
+// for a swap, of b2 from t2 to t1): metal and discounted net cash of the two
+// periods, and NPV_s; the FP32 shadow totals alongside when they are kept.
+// nO1 / nO2 and mined1 / mined2 are the periods' ore and mined tonnage after
+// the move; o1 / o2, gr1 / gr2 are the moved blocks' ore bits and grades in s;
+// M, C and npv are the accumulators before the move.
+static __device__ __forceinline__ void money_scenario(const ApplyArgs &A, int s, const MoveView &v, bool r1, bool r2,
+                                                      uint32_t o1, uint32_t o2, double gr1, double gr2, int64_t nO1,
+                                                      int64_t nO2, int64_t mined1, int64_t mined2, int64_t tgt1,
+                                                      int64_t tgt2, double disc1, double disc2, double sg1, double sg2,
+                                                      double M1, double M2, double C1, double C2, double my_npv) {
+    const size_t i1 = (size_t)v.t1 * A.S + s, i2 = (size_t)v.t2 * A.S + s;
+    const double g1 = o1 ? __dmul_rn((double)v.m1, gr1) : 0.0;
+    const double g2 = (v.swap && o2) ? __dmul_rn((double)v.m2, gr2) : 0.0;
+    double dnpv = 0.0;
+    if (r1) {
+        const double nM = __dadd_rn(__dsub_rn(M1, g1), g2);
+        const double c = contrib_val(nO1, nM, mined1, tgt1, disc1, A.pr, A.pc, A.mc, A.a, A.e, sg1);
+        dnpv = __dadd_rn(dnpv, __dsub_rn(c, C1));
+        A.metal[i1] = nM;
+        A.contrib[i1] = c;
+    }
+    if (r2) {
+        const double nM = __dadd_rn(__dsub_rn(M2, g2), g1);
+        const double c = contrib_val(nO2, nM, mined2, tgt2, disc2, A.pr, A.pc, A.mc, A.a, A.e, sg2);
+        dnpv = __dadd_rn(dnpv, __dsub_rn(c, C2));
+        A.metal[i2] = nM;
+        A.contrib[i2] = c;
+    }
+    A.npv[s] = __dadd_rn(my_npv, dnpv);
+    if (A.npv32) {
+        // the same update with FP32 running totals
+        float d32 = 0.0f;
+        const float g1f = (float)g1, g2f = (float)g2;
+        if (r1) {
+            const float nM = A.metal32[i1] - g1f + g2f;
+            const float c = contrib_val_f32(nO1, nM, mined1, tgt1, disc1, A.pr, A.pc, A.mc, A.a, A.e, sg1);
+            d32 += c - A.contrib32[i1];
+            A.metal32[i1] = nM;
+            A.contrib32[i1] = c;
+        }
+        if (r2) {
+            const float nM = A.metal32[i2] - g2f + g1f;
+            const float c = contrib_val_f32(nO2, nM, mined2, tgt2, disc2, A.pr, A.pc, A.mc, A.a, A.e, sg2);
+            d32 += c - A.contrib32[i2];
+            A.metal32[i2] = nM;
+            A.contrib32[i2] = c;
+        }
+        A.npv32[s] += d32;
+    }
+}
+
+// Apply a decoded move v on a single CTA (blockDim.x >= max(S_pad, 64), a
+// multiple of 32).  go = 1: v is valid, feasible and changes the schedule
+// (the caller has checked it against the current state); go = 0: nothing
+// changes.  MONEY = false does the structural part only (what the next
+// evaluation reads: tonnage, schedule words, penalty tables); apply_money then
+// does the FP64 part later, with the same arithmetic.  s_new: shared scratch
+// of kApplyTabMax floats, 16-byte aligned.
 //   1. one round trip of independent loads: per scenario (thread s) the moved
-//      blocks' ore bits and FP64 grades and the two affected periods' ore
-//      tonnage, metal, NPV contribution, mined tonnage, target and discount;
-//      the Pout / Pin tables into shared memory where they fit;
+//      blocks' ore bits and the two affected periods' ore tonnage, mined
+//      tonnage, target, discount (and for MONEY the grades, metal, NPV
+//      contribution and NPV_s); the last warp the schedule words around the
+//      moved blocks; every thread the Pout / Pin quads of the period-pair
+//      items it rebuilds (when they are at most two per thread);
 //   2. the last warp rewrites the packed period/lo/hi words of the moved
 //      blocks and their grid neighbours (the moved blocks' new periods come
 //      from the move, so the lanes need no ordering among themselves) while
-//      thread s updates scenario s: ore tonnage, metal, NPV contribution and
-//      table entries of the two periods (NPV_s += new - old); thread 0 the
-//      mined tonnage;
-//   3. the warps rebuild the period-pair rows and columns of the two periods.
+//      thread s updates scenario s: ore tonnage and table entries of the two
+//      periods, also kept in s_new (and for MONEY metal, contribution and
+//      NPV_s += new - old); thread 0 the mined tonnage;
+//   3. the threads rewrite the period-pair rows and columns of the two
+//      periods, ctab[a][b] = Pout[a] + Pin[b], four scenarios per item.
 // The NPV mean and std over scenarios are not formed here (k_npv_stats does
 // that on request), so an apply ends with the state update.
-static __device__ __forceinline__ void apply_core(const ApplyArgs &A, const MoveView &v, int go) {
-    __shared__ __align__(16) float s_tab[kApplyTabMax];
+template <bool MONEY>
+static __device__ __forceinline__ void apply_core(const ApplyArgs &A, const MoveView &v, int go, float *s_new) {
     const int s = threadIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int nwarp = blockDim.x >> 5;
+    const int nt = blockDim.x, nwarp = nt >> 5;
     const bool hs = s < A.S;
     const uint32_t T = (uint32_t)A.T, T1 = T + 1;
     const size_t sp = (size_t)A.S_pad, pin = (size_t)T1 * sp;
-    const bool tab_sm = A.ctab && 2 * pin <= (size_t)kApplyTabMax;
     if (!go) return;
     const int32_t mb2 = v.swap ? v.b2 : -1;
     const bool r1 = v.t1 < T, r2 = v.t2 < T;
     const bool c1 = r1, c2 = r2 && v.t2 != v.t1;  // periods whose period-pair rows change
-    const bool stage = tab_sm && (c1 || c2);     // copies issued here are always waited for below
-    // 1. loads: the Pout / Pin tables go to shared memory by asynchronous
-    // 16-byte copies, all in flight at once (waited for before the rebuild)
-    if (stage) {
-        const uint32_t n16 = (uint32_t)(2 * pin / 4);
-        for (uint32_t i = threadIdx.x; i < n16; i += blockDim.x)
-            asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(s_tab + 4 * i)),
-                         "l"(A.tab + 4 * (size_t)i)
-                         : "memory");
-        asm volatile("cp.async.commit_group;" ::: "memory");
-    }
+    const bool rebuild = A.ctab && A.uniform && (c1 || c2);
+    const uint32_t qp = (uint32_t)(sp / 4), items = T1 * qp;
+    const bool pre = rebuild && items <= 2u * (uint32_t)nt;  // the items' quads are loaded up front
+    // 1. loads
     uint32_t o1 = 0, o2 = 0;
     double gr1 = 0.0, gr2 = 0.0, M1 = 0.0, M2 = 0.0, C1 = 0.0, C2 = 0.0, my_npv = 0.0, disc1 = 0.0, disc2 = 0.0;
     double sg1 = 1.0, sg2 = 1.0;
@@ -242,23 +293,63 @@ static __device__ __forceinline__ void apply_core(const ApplyArgs &A, const Move
     const size_t i1 = (size_t)v.t1 * A.S + s, i2 = (size_t)v.t2 * A.S + s;
     if (hs) {
         o1 = ore_bit(A.val, A.R, A.ore_off, v.b1, s);
-        gr1 = A.grade[(int64_t)v.b1 * A.S + s];
-        if (v.swap) {
-            o2 = ore_bit(A.val, A.R, A.ore_off, v.b2, s);
-            gr2 = A.grade[(int64_t)v.b2 * A.S + s];
+        if (v.swap) o2 = ore_bit(A.val, A.R, A.ore_off, v.b2, s);
+        if (MONEY) {
+            gr1 = A.grade[(int64_t)v.b1 * A.S + s];
+            if (v.swap) gr2 = A.grade[(int64_t)v.b2 * A.S + s];
+            my_npv = A.npv[s];
         }
-        my_npv = A.npv[s];
         if (r1) {
-            O1 = A.oreT[i1]; M1 = A.metal[i1]; C1 = A.contrib[i1];
+            O1 = A.oreT[i1];
             tgt1 = (int64_t)A.target[v.t1]; disc1 = A.disc[v.t1]; mined1 = A.minedT[v.t1];
-            if (A.sig) sg1 = A.sig[i1];
             if (A.uniform) tc1 = A.tabc[v.t1];
+            if (MONEY) {
+                M1 = A.metal[i1]; C1 = A.contrib[i1];
+                if (A.sig) sg1 = A.sig[i1];
+            }
         }
         if (r2) {
-            O2 = A.oreT[i2]; M2 = A.metal[i2]; C2 = A.contrib[i2];
+            O2 = A.oreT[i2];
             tgt2 = (int64_t)A.target[v.t2]; disc2 = A.disc[v.t2]; mined2 = A.minedT[v.t2];
-            if (A.sig) sg2 = A.sig[i2];
             if (A.uniform) tc2 = A.tabc[v.t2];
+            if (MONEY) {
+                M2 = A.metal[i2]; C2 = A.contrib[i2];
+                if (A.sig) sg2 = A.sig[i2];
+            }
+        }
+    }
+    // the schedule words around the moved blocks (grid pattern): block j of
+    // the last warp's lane and its ten grid neighbours, loaded together
+    int32_t bj = -1;
+    int32_t nb[10];
+    uint32_t w[10], wj = 0u;
+    if (A.tp.nx > 0 && warp == nwarp - 1 && lane < 22) {
+        bj = apply_neighbour(A.tp, v.b1, mb2, lane);
+        if (bj >= 0) {
+            const int32_t nxy = A.tp.nx * A.tp.ny;
+            const int32_t x = bj % A.tp.nx, y = (bj / A.tp.nx) % A.tp.ny, z = bj / nxy;
+#pragma unroll
+            for (int k = 0; k < 5; k++) {
+                const int32_t px = x + (k == 1 ? -1 : (k == 2 ? 1 : 0)), py = y + (k == 3 ? -1 : (k == 4 ? 1 : 0));
+                const bool in = px >= 0 && px < A.tp.nx && py >= 0 && py < A.tp.ny;
+                nb[2 * k] = (in && z > 0) ? px + A.tp.nx * (py + A.tp.ny * (z - 1)) : -1;
+                nb[2 * k + 1] = (in && z + 1 < A.tp.nz) ? px + A.tp.nx * (py + A.tp.ny * (z + 1)) : -1;
+            }
+#pragma unroll
+            for (int k = 0; k < 10; k++) w[k] = nb[k] >= 0 ? A.blk[nb[k]] : 0u;
+            wj = A.blk[bj];
+        }
+    }
+    // Pout / Pin quads of the thread's period-pair items (b, q): it = s, s + nt
+    const float4 *tb4 = reinterpret_cast<const float4 *>(A.tab);
+    float4 pob[2], pib[2];
+#pragma unroll
+    for (int u = 0; u < 2; u++) {
+        const uint32_t it = (uint32_t)s + (uint32_t)u * (uint32_t)nt;
+        pob[u] = pib[u] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (pre && it < items) {
+            pob[u] = tb4[it];              // item it = b * qp + q: Pout[b] quad q
+            pib[u] = tb4[pin / 4 + it];    // Pin[b] quad q
         }
     }
     // 2. updates.  Every thread has read the mined tonnage of t1 and t2 above;
@@ -267,9 +358,9 @@ static __device__ __forceinline__ void apply_core(const ApplyArgs &A, const Move
     mined1 += -dm1 + dm2;
     mined2 += dm1 - dm2;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        if (r1) A.minedT[v.t1] = A.minedT[v.t1] - dm1 + dm2;
-        if (r2) A.minedT[v.t2] = A.minedT[v.t2] + dm1 - dm2;
+    if (threadIdx.x == 0) {  // thread 0 always holds a scenario (S >= 1), so it loaded both
+        if (r1) A.minedT[v.t1] = mined1;
+        if (r2) A.minedT[v.t2] = mined2;
     }
     // period of block j after the move: the moved blocks' from the move, the
     // others' from their words (of which only the lo/hi bits change here)
@@ -279,34 +370,16 @@ static __device__ __forceinline__ void apply_core(const ApplyArgs &A, const Move
         return blk_period(A.blk[j]);
     };
     if (A.tp.nx > 0) {
-        if (warp == nwarp - 1 && lane < 22) {
-            const int32_t b = apply_neighbour(A.tp, v.b1, mb2, lane);
-            if (b >= 0) {
-                // the ten grid neighbours' words are loaded together, then the
-                // moved blocks' periods are substituted
-                const int32_t nxy = A.tp.nx * A.tp.ny;
-                const int32_t x = b % A.tp.nx, y = (b / A.tp.nx) % A.tp.ny, z = b / nxy;
-                int32_t nb[10];
-                uint32_t w[10];
+        if (bj >= 0) {
+            uint32_t lo = 0, hi = T;
 #pragma unroll
-                for (int k = 0; k < 5; k++) {
-                    const int32_t px = x + (k == 1 ? -1 : (k == 2 ? 1 : 0)), py = y + (k == 3 ? -1 : (k == 4 ? 1 : 0));
-                    const bool in = px >= 0 && px < A.tp.nx && py >= 0 && py < A.tp.ny;
-                    nb[2 * k] = (in && z > 0) ? px + A.tp.nx * (py + A.tp.ny * (z - 1)) : -1;
-                    nb[2 * k + 1] = (in && z + 1 < A.tp.nz) ? px + A.tp.nx * (py + A.tp.ny * (z + 1)) : -1;
-                }
-#pragma unroll
-                for (int k = 0; k < 10; k++) w[k] = nb[k] >= 0 ? A.blk[nb[k]] : 0u;
-                uint32_t lo = 0, hi = T;
-#pragma unroll
-                for (int k = 0; k < 10; k++) {
-                    if (nb[k] < 0) continue;
-                    const uint32_t t = nb[k] == v.b1 ? v.t2 : (nb[k] == mb2 ? v.t1 : blk_period(w[k]));
-                    if (k & 1) hi = t < hi ? t : hi;
-                    else lo = t > lo ? t : lo;
-                }
-                A.blk[b] = blk_pack(b == v.b1 ? v.t2 : (b == mb2 ? v.t1 : blk_period(A.blk[b])), lo, hi);
+            for (int k = 0; k < 10; k++) {
+                if (nb[k] < 0) continue;
+                const uint32_t t = nb[k] == v.b1 ? v.t2 : (nb[k] == mb2 ? v.t1 : blk_period(w[k]));
+                if (k & 1) hi = t < hi ? t : hi;
+                else lo = t > lo ? t : lo;
             }
+            A.blk[bj] = blk_pack(bj == v.b1 ? v.t2 : (bj == mb2 ? v.t1 : blk_period(wj)), lo, hi);
         }
     } else {
         // CSR: the moved blocks and every direct predecessor and successor
@@ -323,86 +396,96 @@ static __device__ __forceinline__ void apply_core(const ApplyArgs &A, const Move
             }
         }
     }
-    float2 np1 = make_float2(0.0f, 0.0f), np2 = np1;  // new (Pout, Pin) of t1 and t2
+    float2 np1 = make_float2(0.0f, 0.0f), np2 = np1;  // new (Pout, Pin) of t1 and t2 (0 past S)
     if (hs) {
         const int64_t om1 = o1 ? (int64_t)v.m1 : 0, om2 = (v.swap && o2) ? (int64_t)v.m2 : 0;
-        const double g1 = o1 ? __dmul_rn((double)v.m1, gr1) : 0.0;
-        const double g2 = (v.swap && o2) ? __dmul_rn((double)v.m2, gr2) : 0.0;
+        const int64_t nO1 = O1 + om2 - om1, nO2 = O2 + om1 - om2;
         const int64_t mu_ = (int64_t)A.m_uniform;
-        double dnpv = 0.0;
         if (r1) {
-            const int64_t nO = O1 + om2 - om1;
-            const double nM = __dadd_rn(__dsub_rn(M1, g1), g2);
-            const double c = contrib_val(nO, nM, mined1, tgt1, disc1, A.pr, A.pc, A.mc, A.a, A.e, sg1);
-            dnpv = __dadd_rn(dnpv, __dsub_rn(c, C1));
-            A.oreT[i1] = nO;
-            A.metal[i1] = nM;
-            A.contrib[i1] = c;
-            if (A.uniform) table_store_c(v.t1, s, A.S_pad, A.T, nO - tgt1, tc1, disc1, mu_, A.a, A.e, A.tab, np1);
+            A.oreT[i1] = nO1;
+            if (A.uniform) table_store_c(v.t1, s, A.S_pad, A.T, nO1 - tgt1, tc1, disc1, mu_, A.a, A.e, A.tab, np1);
         }
         if (r2) {
-            const int64_t nO = O2 + om1 - om2;
-            const double nM = __dadd_rn(__dsub_rn(M2, g2), g1);
-            const double c = contrib_val(nO, nM, mined2, tgt2, disc2, A.pr, A.pc, A.mc, A.a, A.e, sg2);
-            dnpv = __dadd_rn(dnpv, __dsub_rn(c, C2));
-            A.oreT[i2] = nO;
-            A.metal[i2] = nM;
-            A.contrib[i2] = c;
-            if (A.uniform) table_store_c(v.t2, s, A.S_pad, A.T, nO - tgt2, tc2, disc2, mu_, A.a, A.e, A.tab, np2);
+            A.oreT[i2] = nO2;
+            if (A.uniform) table_store_c(v.t2, s, A.S_pad, A.T, nO2 - tgt2, tc2, disc2, mu_, A.a, A.e, A.tab, np2);
         }
-        my_npv = __dadd_rn(my_npv, dnpv);
-        A.npv[s] = my_npv;
-        if (A.npv32) {
-            // the same update with FP32 running totals
-            float d32 = 0.0f;
-            const float g1f = (float)g1, g2f = (float)g2;
-            if (r1) {
-                const float nM = A.metal32[i1] - g1f + g2f;
-                const float c = contrib_val_f32(O1 + om2 - om1, nM, mined1, tgt1, disc1, A.pr, A.pc, A.mc, A.a, A.e, sg1);
-                d32 += c - A.contrib32[i1];
-                A.metal32[i1] = nM;
-                A.contrib32[i1] = c;
-            }
-            if (r2) {
-                const float nM = A.metal32[i2] - g2f + g1f;
-                const float c = contrib_val_f32(O2 + om1 - om2, nM, mined2, tgt2, disc2, A.pr, A.pc, A.mc, A.a, A.e, sg2);
-                d32 += c - A.contrib32[i2];
-                A.metal32[i2] = nM;
-                A.contrib32[i2] = c;
-            }
-            A.npv32[s] += d32;
-        }
+        if (MONEY)
+            money_scenario(A, s, v, r1, r2, o1, o2, gr1, gr2, nO1, nO2, mined1, mined2, tgt1, tgt2, disc1, disc2,
+                           sg1, sg2, M1, M2, C1, C2, my_npv);
     }
-    if (!A.ctab || !(c1 || c2)) return;
+    if (!rebuild) return;
     const uint32_t ra = c1 ? v.t1 : v.t2, rb = c2 ? v.t2 : ra;
-    if (!tab_sm) {
+    if (!pre) {
         __syncthreads();  // the new Pout / Pin entries of t1 and t2 are in global memory
         ctab_rebuild(A.tab, A.ctab, T1, (uint32_t)A.S, sp, ra, rb, warp, nwarp, lane);
         return;
     }
-    asm volatile("cp.async.wait_all;" ::: "memory");
-    __syncthreads();  // every staged row has landed
-    if (hs && A.uniform) {
-        if (r1) { s_tab[v.t1 * sp + s] = np1.x; s_tab[pin + v.t1 * sp + s] = np1.y; }
-        if (r2) { s_tab[v.t2 * sp + s] = np2.x; s_tab[pin + v.t2 * sp + s] = np2.y; }
+    if ((size_t)s < sp) {  // s_new rows: Pout[t1], Pin[t1], Pout[t2], Pin[t2] after the move
+        s_new[s] = np1.x;
+        s_new[sp + s] = np1.y;
+        s_new[2 * sp + s] = np2.x;
+        s_new[3 * sp + s] = np2.y;
     }
     __syncthreads();
     // 3. ctab[a][b][s] = Pout[a][s] + Pin[b][s] for the rows a and columns b of
-    // the changed periods, four scenarios per item, every operand in shared
-    // memory: only the 16-byte stores leave the SM
-    const uint32_t qp = (uint32_t)(sp / 4), items = T1 * qp;
-    const float4 *st4 = reinterpret_cast<const float4 *>(s_tab);
+    // the changed periods, four scenarios per item; the new entries of t1 and
+    // t2 come from s_new, every other operand was loaded in step 1
+    const float4 *sn4 = reinterpret_cast<const float4 *>(s_new);
+    auto po_new = [&](uint32_t t, uint32_t q) { return sn4[(t == v.t1 ? 0 : 2 * qp) + q]; };
+    auto pi_new = [&](uint32_t t, uint32_t q) { return sn4[(t == v.t1 ? qp : 3 * qp) + q]; };
     float4 *ct4 = reinterpret_cast<float4 *>(A.ctab);
-    const size_t pin4 = (size_t)T1 * qp;
-    for (uint32_t it = threadIdx.x; it < items; it += blockDim.x) {
+#pragma unroll
+    for (int u = 0; u < 2; u++) {
+        const uint32_t it = (uint32_t)s + (uint32_t)u * (uint32_t)nt;
+        if (it >= items) continue;
         const uint32_t b = it / qp, q = it - b * qp;
-        const float4 pob = st4[b * qp + q], pib = st4[pin4 + b * qp + q];
-        const float4 poa = st4[ra * qp + q], pia = st4[pin4 + ra * qp + q];
-        const float4 por = st4[rb * qp + q], pir = st4[pin4 + rb * qp + q];
-        ct4[((size_t)ra * T1 + b) * qp + q] = make_float4(poa.x + pib.x, poa.y + pib.y, poa.z + pib.z, poa.w + pib.w);
-        ct4[((size_t)b * T1 + ra) * qp + q] = make_float4(pob.x + pia.x, pob.y + pia.y, pob.z + pia.z, pob.w + pia.w);
-        ct4[((size_t)rb * T1 + b) * qp + q] = make_float4(por.x + pib.x, por.y + pib.y, por.z + pib.z, por.w + pib.w);
-        ct4[((size_t)b * T1 + rb) * qp + q] = make_float4(pob.x + pir.x, pob.y + pir.y, pob.z + pir.z, pob.w + pir.w);
+        const bool bnew = (c1 && b == v.t1) || (c2 && b == v.t2);
+        const float4 pob_ = bnew ? po_new(b, q) : pob[u], pib_ = bnew ? pi_new(b, q) : pib[u];
+        const float4 poa = po_new(ra, q), pia = pi_new(ra, q);
+        const float4 por = po_new(rb, q), pir = pi_new(rb, q);
+        ct4[((size_t)ra * T1 + b) * qp + q] = make_float4(poa.x + pib_.x, poa.y + pib_.y, poa.z + pib_.z, poa.w + pib_.w);
+        ct4[((size_t)b * T1 + ra) * qp + q] = make_float4(pob_.x + pia.x, pob_.y + pia.y, pob_.z + pia.z, pob_.w + pia.w);
+        ct4[((size_t)rb * T1 + b) * qp + q] = make_float4(por.x + pib_.x, por.y + pib_.y, por.z + pib_.z, por.w + pib_.w);
+        ct4[((size_t)b * T1 + rb) * qp + q] = make_float4(pob_.x + pir.x, pob_.y + pir.y, pob_.z + pir.z, pob_.w + pir.w);
+    }
+}
+
+// The FP64 part of an apply whose structural part (apply_core<false>) is done:
+// info = (b1, b2 or B for a shift, t1 | t2 << 8, valid) of the move, uniform
+// block mass.  The tonnage read here is the tonnage after the move, so the
+// result is the same bits as a full apply.  The calling thread updates
+// scenarios s_begin, s_begin + s_step, ... (scenarios are independent).
+static __device__ __forceinline__ void apply_money(const ApplyArgs &A, int4 info, int s_begin, int s_step) {
+    MoveView v;
+    v.b1 = info.x;
+    v.swap = info.y != A.tp.B;
+    v.b2 = v.swap ? info.y : -1;
+    v.t1 = (uint32_t)info.z & 0xffu;
+    v.t2 = ((uint32_t)info.z >> 8) & 0xffu;
+    v.m1 = A.m_uniform;
+    v.m2 = v.swap ? A.m_uniform : 0u;
+    const uint32_t T = (uint32_t)A.T;
+    const bool r1 = v.t1 < T, r2 = v.t2 < T;
+    for (int s = s_begin; s < A.S; s += s_step) {
+        const size_t i1 = (size_t)v.t1 * A.S + s, i2 = (size_t)v.t2 * A.S + s;
+        const uint32_t o1 = ore_bit(A.val, A.R, A.ore_off, v.b1, s);
+        const uint32_t o2 = v.swap ? ore_bit(A.val, A.R, A.ore_off, v.b2, s) : 0u;
+        const double gr1 = A.grade[(int64_t)v.b1 * A.S + s];
+        const double gr2 = v.swap ? A.grade[(int64_t)v.b2 * A.S + s] : 0.0;
+        int64_t nO1 = 0, nO2 = 0, mined1 = 0, mined2 = 0, tgt1 = 0, tgt2 = 0;
+        double disc1 = 0.0, disc2 = 0.0, sg1 = 1.0, sg2 = 1.0, M1 = 0.0, M2 = 0.0, C1 = 0.0, C2 = 0.0;
+        if (r1) {
+            nO1 = A.oreT[i1]; mined1 = A.minedT[v.t1]; tgt1 = (int64_t)A.target[v.t1]; disc1 = A.disc[v.t1];
+            M1 = A.metal[i1]; C1 = A.contrib[i1];
+            if (A.sig) sg1 = A.sig[i1];
+        }
+        if (r2) {
+            nO2 = A.oreT[i2]; mined2 = A.minedT[v.t2]; tgt2 = (int64_t)A.target[v.t2]; disc2 = A.disc[v.t2];
+            M2 = A.metal[i2]; C2 = A.contrib[i2];
+            if (A.sig) sg2 = A.sig[i2];
+        }
+        money_scenario(A, s, v, r1, r2, o1, o2, gr1, gr2, nO1, nO2, mined1, mined2, tgt1, tgt2, disc1, disc2, sg1,
+                       sg2, M1, M2, C1, C2, A.npv[s]);
     }
 }
 
@@ -410,7 +493,7 @@ static __device__ __forceinline__ void apply_core(const ApplyArgs &A, const Move
 // blocks' schedule words, masses and the per-period tonnage and capacity are
 // loaded, thread 0 re-checks the move exactly (decode_move) and records the
 // outcome, then apply_core updates the state.  have = 0: nothing to apply.
-static __device__ __noinline__ void apply_block(const ApplyArgs &A, int2 mv, int have) {
+static __device__ __noinline__ void apply_block(const ApplyArgs &A, int2 mv, int have, float *s_tab) {
     __shared__ MoveView sv;
     __shared__ int s_go;
     __shared__ int64_t s_mined[kMaxT + 1];
@@ -445,14 +528,17 @@ static __device__ __noinline__ void apply_block(const ApplyArgs &A, int2 mv, int
     }
     __syncthreads();
     const MoveView v = sv;
-    apply_core(A, v, s_go);
+    apply_core<true>(A, v, s_go, s_tab);
 }
 
 // Apply a move that the same launch evaluated as feasible against the current
 // state (the fused step's best move): no re-check is needed, so every load
 // goes out at once.  info = (b1, b2 or B for a shift, t1 | t2 << 8) as the
 // evaluator recorded it; have = 0: no feasible move.  Uniform block mass.
-static __device__ __noinline__ void apply_evaluated(const ApplyArgs &A, int4 info, int have) {
+// MONEY = false: the structural part only (see apply_core).  Returns whether
+// the state changed (a feasible move that is not a no-op).
+template <bool MONEY>
+static __device__ __noinline__ int apply_evaluated(const ApplyArgs &A, int4 info, int have, float *s_tab) {
     MoveView v;
     v.b1 = info.x;
     v.swap = info.y != A.tp.B;
@@ -468,7 +554,8 @@ static __device__ __noinline__ void apply_evaluated(const ApplyArgs &A, int4 inf
         A.res->applied = have ? 1 : 0;
         A.res->status = MM_OK;
     }
-    apply_core(A, v, have && !v.noop);
+    apply_core<MONEY>(A, v, have && !v.noop, s_tab);
+    return have && !v.noop;
 }
 
 }  // namespace mm

@@ -79,6 +79,7 @@ __global__ void __launch_bounds__(kEvalThreads, MM_EVAL_MINB) k_batch_eval(Batch
     __shared__ int64_t s_mined[kBatchMaxT + 1];
     __shared__ uint64_t s_cap[kBatchMaxT + 1];
     __shared__ uint64_t s_wl[NW][32];
+    __shared__ __align__(16) float s_apply_tab[kApplyTabMax];
     __shared__ int s_item, s_last, s_best;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (;;) {
@@ -163,7 +164,7 @@ __global__ void __launch_bounds__(kEvalThreads, MM_EVAL_MINB) k_batch_eval(Batch
             if (C->do_apply) {
                 const int b = s_best;
                 const int2 mv = b >= 0 ? __ldg(sA.moves + b) : make_int2(0, -1);
-                apply_block(C->AP, mv, b >= 0 ? 1 : 0);
+                apply_block(C->AP, mv, b >= 0 ? 1 : 0, s_apply_tab);
             }
         }
         __syncthreads();  // shared state is reused by the next item
@@ -184,6 +185,7 @@ struct mm_batch {
     int moves_per_item = 2048;        // tile shape: moves per queue item
     int ctas_per_sm = 0;              // 0 = max_per_sm
     std::vector<ChainDev> chains;     // host copy (list0 / n_items follow the tile shape)
+    std::vector<mm_model *> models;   // each chain's model
     std::vector<int64_t> n_moves;
     std::vector<int> S;
     ChainDev *d_chains = nullptr;
@@ -295,6 +297,7 @@ mm_status mm_batch_create(const mm_chain *chains, int32_t n_chains, int32_t k, i
     b->stream = static_cast<cudaStream_t>(cuda_stream);
     b->num_sms = chains[0].model->num_sms;
     b->chains.resize(n_chains);
+    b->models.resize(n_chains);
     b->n_moves.resize(n_chains);
     b->S.resize(n_chains);
     for (int c = 0; c < n_chains; c++) {
@@ -316,6 +319,7 @@ mm_status mm_batch_create(const mm_chain *chains, int32_t n_chains, int32_t k, i
         d.count_out = ch.count_dev;
         b->n_moves[c] = ch.n_moves;
         b->S[c] = m->S;
+        b->models[c] = m;
     }
     cudaError_t e = cudaMalloc(&b->d_chains, sizeof(ChainDev) * (size_t)n_chains);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_next, sizeof(uint32_t) * (size_t)(n_chains + 1));
@@ -363,6 +367,13 @@ mm_status mm_batch_run(mm_batch *b) {
     for (int c = 0; c < b->n_chains; c++)
         if (b->n_moves[c] == 0)
             MM_CUDA_TRY(cudaMemsetAsync(b->chains[c].count_out, 0, sizeof(int32_t), b->stream), "clear count");
+    // an apply in the batch updates the FP64 totals: any update a fused step
+    // left due on a chain's model is done first, on the batch's stream
+    if (b->do_apply)
+        for (mm_model *m : b->models) {
+            const mm_status st = settle_money(m, b->stream);
+            if (st != MM_OK) return st;
+        }
     if (b->n_items == 0) return MM_OK;
     const int per_sm = b->ctas_per_sm > 0 ? b->ctas_per_sm : b->max_per_sm;
     const int grid = std::min(b->n_items, b->num_sms * per_sm);

@@ -206,7 +206,7 @@ EvalArgs eval_args(mm_model *m, const mm_move *moves, int64_t n, float *score, u
 
 // Resident CTAs per SM of an evaluator, cached so that calls captured into a
 // CUDA graph make no occupancy query.
-static mm_status eval_occupancy(EvalFn fn, size_t smem, int *per_sm) {
+static mm_status eval_occupancy(EvalFn fn, int threads, size_t smem, int *per_sm) {
     static std::mutex mu;
     static std::map<std::pair<const void *, size_t>, int> cache;
     std::lock_guard<std::mutex> lock(mu);
@@ -216,7 +216,7 @@ static mm_status eval_occupancy(EvalFn fn, size_t smem, int *per_sm) {
         *per_sm = it->second;
         return MM_OK;
     }
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, fn, kEvalThreads, smem);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, fn, threads, smem);
     if (e != cudaSuccess) return cuda_status(e, "occupancy query");
     if (*per_sm < 1) *per_sm = 1;
     cache[key] = *per_sm;
@@ -228,13 +228,17 @@ mm_status eval_launch(mm_model *m, const mm_move *moves, int64_t n, float *score
                       const uint32_t *pmoves) {
     EvalArgs A = eval_args(m, moves, n, score, feas, mean, delta);
     A.pmoves = pmoves;
+    // the fused step runs one CTA of kStepThreads per SM (its top-k lists meet
+    // in one level); evaluation-only launches several CTAs of kEvalThreads
+    const int nt = step ? kStepThreads : kEvalThreads;
     if (step) {
         A.tail.k = step->k;
         A.tail.idx_out = step->idx;
         A.tail.top_out = step->top;
         A.tail.count_out = step->count;
         A.tail.do_apply = step->apply;
-        if (step->apply) A.tail.ap = apply_args(m);
+        A.tail.ap = apply_args(m);  // the first CTA to finish also settles the previous step's FP64 update
+        A.tail.pending = m->pending;
         stages = 0;  // the fused step runs on direct loads
     }
     const bool kahan = (options & MM_EVAL_KAHAN) != 0;
@@ -260,21 +264,21 @@ mm_status eval_launch(mm_model *m, const mm_move *moves, int64_t n, float *score
                 }
                 m->smem_attr[(const void *)fn] = smem;
             }
-            int per_sm = ctas_per_sm;
+            int per_sm = step ? 0 : ctas_per_sm;
             if (per_sm <= 0) {
-                const mm_status os = eval_occupancy(fn, smem, &per_sm);
+                const mm_status os = eval_occupancy(fn, nt, smem, &per_sm);
                 if (os != MM_OK) return os;
             }
             A.qpl = (nq + team - 1) / team;
             const int64_t chunks = (n + kChunk - 1) / kChunk;
-            int64_t blocks = (chunks + kEvalThreads / 32 - 1) / (kEvalThreads / 32);
+            int64_t blocks = (chunks + nt / 32 - 1) / (nt / 32);
             int64_t grid_cap = (int64_t)m->num_sms * per_sm;
             if (step && grid_cap > m->step_max_ctas) grid_cap = m->step_max_ctas;
             if (blocks > grid_cap) blocks = grid_cap;
             if (blocks < 1) blocks = 1;
             if (step) const_cast<StepOut *>(step)->grid = (int)blocks;
             A.tail.L = step_lists(m, (int)blocks);
-            fn<<<(unsigned)blocks, kEvalThreads, smem, m->stream>>>(A);
+            fn<<<(unsigned)blocks, nt, smem, m->stream>>>(A);
             return check_launch("k_eval_tiled");
         }
     }
@@ -345,20 +349,20 @@ mm_status eval_launch(mm_model *m, const mm_move *moves, int64_t n, float *score
         }
         m->smem_attr[(const void *)fn] = smem;
     }
-    int per_sm = ctas_per_sm;
+    int per_sm = step ? 0 : ctas_per_sm;
     if (per_sm <= 0) {
-        const mm_status os = eval_occupancy(fn, smem, &per_sm);
+        const mm_status os = eval_occupancy(fn, nt, smem, &per_sm);
         if (os != MM_OK) return os;
     }
     const int64_t chunks = (n + kChunk - 1) / kChunk;
-    int64_t blocks = (chunks + kEvalThreads / 32 - 1) / (kEvalThreads / 32);
+    int64_t blocks = (chunks + nt / 32 - 1) / (nt / 32);
     int64_t grid_cap = (int64_t)m->num_sms * per_sm;
     if (step && grid_cap > m->step_max_ctas) grid_cap = m->step_max_ctas;
     if (blocks > grid_cap) blocks = grid_cap;
     if (blocks < 1) blocks = 1;
     if (step) const_cast<StepOut *>(step)->grid = (int)blocks;
     A.tail.L = step_lists(m, (int)blocks);
-    fn<<<(unsigned)blocks, kEvalThreads, smem, m->stream>>>(A);
+    fn<<<(unsigned)blocks, nt, smem, m->stream>>>(A);
     return check_launch("k_eval_tiled");
 }
 

@@ -24,18 +24,19 @@ static EvalFn fast2(int kf, bool tail, bool delta) {
     return nullptr;
 }
 
-// The fused search step's weighted form (top-k and in-launch apply).
+// The fused search step's weighted form (top-k and in-launch apply), one
+// CTA of kStepThreads per SM.
 template <int TEAM>
 static EvalFn step2(int kf, bool tail) {
     switch (kf) {
-        case 1: return tail ? k_eval_tiled<TEAM, 1, false, false, false, 1, true, true, true>
-                            : k_eval_tiled<TEAM, 1, false, false, false, 1, false, true, true>;
-        case 2: return tail ? k_eval_tiled<TEAM, 1, false, false, false, 2, true, true, true>
-                            : k_eval_tiled<TEAM, 1, false, false, false, 2, false, true, true>;
-        case 3: return tail ? k_eval_tiled<TEAM, 1, false, false, false, 3, true, true, true>
-                            : k_eval_tiled<TEAM, 1, false, false, false, 3, false, true, true>;
-        case 4: return tail ? k_eval_tiled<TEAM, 1, false, false, false, 4, true, true, true>
-                            : k_eval_tiled<TEAM, 1, false, false, false, 4, false, true, true>;
+        case 1: return tail ? k_eval_tiled<TEAM, 1, false, false, false, 1, true, true, true, kStepThreads>
+                            : k_eval_tiled<TEAM, 1, false, false, false, 1, false, true, true, kStepThreads>;
+        case 2: return tail ? k_eval_tiled<TEAM, 1, false, false, false, 2, true, true, true, kStepThreads>
+                            : k_eval_tiled<TEAM, 1, false, false, false, 2, false, true, true, kStepThreads>;
+        case 3: return tail ? k_eval_tiled<TEAM, 1, false, false, false, 3, true, true, true, kStepThreads>
+                            : k_eval_tiled<TEAM, 1, false, false, false, 3, false, true, true, kStepThreads>;
+        case 4: return tail ? k_eval_tiled<TEAM, 1, false, false, false, 4, true, true, true, kStepThreads>
+                            : k_eval_tiled<TEAM, 1, false, false, false, 4, false, true, true, kStepThreads>;
     }
     return nullptr;
 }

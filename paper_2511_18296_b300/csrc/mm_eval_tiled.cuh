@@ -21,6 +21,8 @@
 // per-scenario work is four (shift) or seven (swap) FP32 operations.
 #pragma once
 
+#include <type_traits>
+
 #include "mm_apply.cuh"
 #include "mm_sort.cuh"
 
@@ -31,6 +33,8 @@ namespace mm {
 #endif
 
 constexpr int kEvalThreads = 256;  // threads per CTA
+constexpr int kStepThreads = 768;  // threads per CTA of the fused search step: one CTA per SM, so the
+                                   // batch's top-k lists (one per CTA) meet in a single level
 constexpr int kChunk = 64;         // moves a warp decodes at once (two per lane)
 
 // Where a batch's top-k lists meet: the per-CTA lists, the merged lists of
@@ -57,7 +61,9 @@ struct StepTail {
     int32_t *count_out;    // [1]
     int32_t do_apply;      // the final CTA applies the best move (S <= CTA threads)
     const int2 *moves;     // the batch (do_apply)
-    ApplyArgs ap;          // (do_apply)
+    ApplyArgs ap;          // the model's apply arguments (fused step)
+    int4 *pending;         // fused step: the move whose FP64 update is still due, (b1, b2 or B,
+                           // t1 | t2 << 8, due); the next step's CTAs do it, a share of the scenarios each
 };
 
 struct EvalArgs {
@@ -169,10 +175,12 @@ __device__ __forceinline__ uint64_t warp_topk_merge(uint64_t t, uint64_t c_sorte
 }
 
 
-// Neumaier-compensated accumulation: (s, c) += x.
-__device__ __forceinline__ void comp_add(float &s, float &c, float x) {
-    float t = s + x;
-    c += (fabsf(s) >= fabsf(x)) ? ((s - t) + x) : ((x - t) + s);
+// Kahan-compensated accumulation: s += x, with c the running negative of
+// the low-order part lost so far (the sum is s - c).
+__device__ __forceinline__ void kahan_add(float &s, float &c, float x) {
+    const float y = x - c;
+    const float t = s + y;
+    c = (t - s) - y;
     s = t;
 }
 
@@ -277,18 +285,19 @@ __device__ __forceinline__ void team_eval(const EvalArgs &A, const float *tab, i
         for (int j = 0; j < 4; j++) d[k][j] = live ? x[j] : 0.0f;
         if (KAHAN) {
 #pragma unroll
-            for (int j = 0; j < 4; j++) comp_add(sum, csum, d[k][j]);
+            for (int j = 0; j < 4; j++) kahan_add(sum, csum, d[k][j]);
         } else {
             sum += (d[k][0] + d[k][2]) + (d[k][1] + d[k][3]);  // the fast form's order
         }
     }
     if (KAHAN) {
+        csum = -csum;  // (sum, csum): the sum is sum + csum
         team_sum_comp<TEAM>(sum, csum);
         mu = (sum + csum) * invS;
     } else {
         mu = team_sum<TEAM>(sum) * invS;
     }
-    float var = 0.0f, cvar = 0.0f;
+    float var = 0.0f, dsum = 0.0f;
 #pragma unroll
     for (int k = 0; k < QMAX; k++) {
         const int q = tl + k * TEAM;
@@ -303,16 +312,17 @@ __device__ __forceinline__ void team_eval(const EvalArgs &A, const float *tab, i
             }
 #pragma unroll
             for (int j = 0; j < 4; j++) {
-                if (KAHAN) comp_add(var, cvar, dv[j] * dv[j]);
-                else var = fmaf(dv[j], dv[j], var);
+                var = fmaf(dv[j], dv[j], var);
+                if (KAHAN) dsum += dv[j];
             }
         }
     }
+    var = team_sum<TEAM>(var);
     if (KAHAN) {
-        team_sum_comp<TEAM>(var, cvar);
-        var = var + cvar;
-    } else {
-        var = team_sum<TEAM>(var);
+        // corrected two-pass variance: the sum of the deviations from the
+        // rounded mean removes that rounding's bias from the sum of squares
+        const float ds = team_sum<TEAM>(dsum);
+        var = fmaxf(var - ds * ds * invS, 0.0f);
     }
     sd = sqrtf(var * invS);
 }
@@ -429,10 +439,18 @@ __device__ __forceinline__ void team_eval_fast(const EvalArgs &A, int tl, const 
             f2_unpack(hi, x[2], x[3]);
         }
     };
+    // compensated form: two Kahan accumulators in one register pair (the
+    // even and the odd scenario of each pair), paired instructions
+    uint64_t ks = 0ull, kc = 0ull;  // two +0.0f each
     auto acc = [&](const float (&x)[4]) {
         if (KAHAN) {
 #pragma unroll
-            for (int j = 0; j < 4; j++) comp_add(sum, csum, x[j]);
+            for (int h = 0; h < 2; h++) {
+                const uint64_t y = f2_sub(f2_pack(x[2 * h], x[2 * h + 1]), kc);
+                const uint64_t t = f2_add(ks, y);
+                kc = f2_sub(f2_sub(t, ks), y);
+                ks = t;
+            }
         } else {
             // (x0 + x2) + (x1 + x3), the first level as one paired add
             float u, v;
@@ -452,12 +470,22 @@ __device__ __forceinline__ void team_eval_fast(const EvalArgs &A, int tl, const 
         acc(d[KF]);
     }
     if (KAHAN) {
+        // (s, -c) of each accumulator is a value and its error term: the two
+        // and then the team's are merged by error-free TwoSum
+        float s1, c0, c1;
+        f2_unpack(ks, sum, s1);
+        f2_unpack(kc, c0, c1);
+        csum = -c0;
+        comp_merge(sum, csum, s1, -c1);
         team_sum_comp<TEAM>(sum, csum);
         mu = (sum + csum) * invS;
     } else {
         mu = team_sum<TEAM>(sum) * invS;
     }
-    float var = 0.0f, cvar = 0.0f;
+    // second pass: squared deviations (non-negative terms: nothing cancels);
+    // the compensated form also sums the deviations themselves for the
+    // corrected two-pass variance
+    float var = 0.0f, dsum = 0.0f;
     const uint64_t mu2 = f2_pack(mu, mu);
     auto vacc = [&](const float (&x)[4]) {
         float dv[4];
@@ -465,18 +493,19 @@ __device__ __forceinline__ void team_eval_fast(const EvalArgs &A, int tl, const 
         f2_unpack(f2_sub(f2_pack(x[2], x[3]), mu2), dv[2], dv[3]);
 #pragma unroll
         for (int j = 0; j < 4; j++) {
-            if (KAHAN) comp_add(var, cvar, dv[j] * dv[j]);
-            else var = fmaf(dv[j], dv[j], var);
+            var = fmaf(dv[j], dv[j], var);
+            if (KAHAN) dsum += dv[j];
         }
     };
 #pragma unroll
     for (int k = 0; k < KF; k++) vacc(d[k]);
     if (TAIL && tl < ntail) vacc(d[KF]);
+    var = team_sum<TEAM>(var);
     if (KAHAN) {
-        team_sum_comp<TEAM>(var, cvar);
-        var = var + cvar;
-    } else {
-        var = team_sum<TEAM>(var);
+        // corrected two-pass variance: the deviations' sum removes the bias
+        // that the rounded mean leaves in the sum of squares
+        const float ds = team_sum<TEAM>(dsum);
+        var = fmaxf(var - ds * ds * invS, 0.0f);
     }
     sd = sqrtf(var * invS);
 }
@@ -538,10 +567,33 @@ __device__ __forceinline__ void step_publish(uint64_t *out32, uint64_t wtk) {
     }
 }
 
+// Merge tree over the NW warps' lists (any NW >= 1): t is the calling warp's
+// list, also stored in s_wl[warp]; at each level the upper half of the
+// remaining lists is merged into the lower half.  With INFO the move record of
+// each list's head follows it in s_inf.  Every thread must call it; the result
+// is valid in warp 0 (and s_inf[0]).
+template <int NW, bool INFO>
+__device__ __forceinline__ uint64_t tree_merge(uint64_t t, uint64_t (*s_wl)[32], int4 *s_inf) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int width = NW; width > 1; width = (width + 1) / 2) {
+        const int half = (width + 1) / 2;
+        if (warp < width - half) {
+            const uint64_t o = s_wl[warp + half][lane];
+            const uint64_t mrg = warp_topk_merge(t, o);
+            if (INFO && __shfl_sync(0xffffffffu, mrg == o, 0) && lane == 0) s_inf[warp] = s_inf[warp + half];
+            t = mrg;
+            s_wl[warp][lane] = t;
+        }
+        __syncthreads();
+    }
+    return t;
+}
+
 // Selection of the 32 largest keys among nlists published lists (each sorted
-// best-first, 0 = empty; keys unique) by the whole CTA (NW warps, NW a power of
-// two): warp w merges lists w, w + NW, ... with pruned warp merges, four
-// lists' loads in flight at a time, then a tree over the warps.  Every thread
+// best-first, 0 = empty; keys unique) by the whole CTA (NW warps): warp w
+// merges lists w, w + NW, ... with pruned warp merges, four lists' loads in
+// flight at a time, then a tree over the warps.  Every thread
 // must call it; the result is valid in warp 0 (sorted, lane 0 best).
 template <int NW>
 __device__ __forceinline__ uint64_t block_merge_lists(const uint64_t *lists, int nlists, uint64_t (*s_wl)[32]) {
@@ -559,15 +611,7 @@ __device__ __forceinline__ uint64_t block_merge_lists(const uint64_t *lists, int
     }
     s_wl[warp][lane] = t;
     __syncthreads();
-#pragma unroll
-    for (int stride = NW / 2; stride > 0; stride >>= 1) {
-        if (warp < stride) {
-            t = warp_topk_merge(t, s_wl[warp + stride][lane]);
-            s_wl[warp][lane] = t;
-        }
-        __syncthreads();
-    }
-    return t;
+    return tree_merge<NW, false>(t, s_wl, nullptr);
 }
 
 // block_merge_lists that also follows the move record of the best key:
@@ -598,17 +642,7 @@ __device__ __forceinline__ uint64_t block_merge_lists_info(const uint64_t *lists
     s_wl[warp][lane] = t;
     if (lane == 0) s_inf[warp] = inf;
     __syncthreads();
-#pragma unroll
-    for (int stride = NW / 2; stride > 0; stride >>= 1) {
-        if (warp < stride) {
-            const uint64_t o = s_wl[warp + stride][lane];
-            const uint64_t mrg = warp_topk_merge(t, o);
-            if (__shfl_sync(0xffffffffu, mrg == o, 0) && lane == 0) s_inf[warp] = s_inf[warp + stride];
-            t = mrg;
-            s_wl[warp][lane] = t;
-        }
-        __syncthreads();
-    }
+    t = tree_merge<NW, true>(t, s_wl, s_inf);
     inf_out = s_inf[0];
     return t;
 }
@@ -660,45 +694,26 @@ __device__ __forceinline__ void prefetch_l2_range(const void *p, size_t bytes, i
         asm volatile("prefetch.global.L2 [%0];" ::"l"(c + o));
 }
 
-// End of a batch's top-k selection, called by every thread of every CTA with
-// the warp's list wtk and (fused step) the move record of each warp's best key
-// (winfo[warp], shared memory; NULL when no apply follows).  The CTA merges its
-// warps' lists (a tree) and publishes its 32 best keys with the record of the
-// best; the last CTA of each group of grp_size CTAs to finish (a ticket counter
-// per group; nobody waits) merges the group's lists into one; the last group to
-// finish merges the group lists, writes the top k and, when asked, applies the
-// best move from its record, so no move has to be fetched or decoded again.
-// Each ticket is reset by the CTA that draws its last number, so every counter
-// is zero again for the next launch.  Two levels of about sqrt(grid) lists each
-// keep the merging short, and all but the last group merge while others still
-// evaluate.  Before an in-launch apply, the group-merging CTAs pull the apply's
-// per-period state and the grade rows of their group's best move into L2.
-// Not inlined: the evaluator's main loop keeps its own register allocation.
-static __device__ __noinline__ void step_reduce(const StepTail &T, uint64_t wtk, const int4 *winfo) {
+// End of a standalone top-k selection (k_topk_lists), called by every thread
+// of every CTA with the warp's list wtk.  The CTA merges its warps' lists (a
+// tree) and publishes its 32 best keys; the last CTA of each group of
+// grp_size CTAs to finish (a ticket counter per group; nobody waits) merges
+// the group's lists into one; the last group to finish merges the group lists
+// and writes the top k.  Each ticket is reset by the CTA that draws its last
+// number, so every counter is zero again for the next launch.  Two levels of
+// about sqrt(grid) lists each keep the merging short, and all but the last
+// group merge while others still run.  Not inlined: the caller's main loop
+// keeps its own register allocation.
+static __device__ __noinline__ void step_reduce(const StepTail &T, uint64_t wtk) {
     constexpr int NW = kEvalThreads / 32;
     __shared__ uint64_t s_wl[NW][32];
-    __shared__ int4 s_inf[NW];
-    __shared__ int s_last, s_best;
+    __shared__ int s_last;
     const StepLists &L = T.L;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     s_wl[warp][lane] = wtk;
-    if (lane == 0) s_inf[warp] = winfo ? winfo[warp] : make_int4(0, 0, 0, 0);
     __syncthreads();
-#pragma unroll
-    for (int stride = NW / 2; stride > 0; stride >>= 1) {
-        if (warp < stride) {
-            const uint64_t o = s_wl[warp + stride][lane];
-            const uint64_t mrg = warp_topk_merge(wtk, o);
-            if (__shfl_sync(0xffffffffu, mrg == o, 0) && lane == 0) s_inf[warp] = s_inf[warp + stride];
-            wtk = mrg;
-            s_wl[warp][lane] = wtk;
-        }
-        __syncthreads();
-    }
-    if (warp == 0) {
-        L.cta[(size_t)blockIdx.x * 32 + lane] = wtk;
-        if (lane == 0) L.cinf[blockIdx.x] = s_inf[0];
-    }
+    wtk = tree_merge<NW, false>(wtk, s_wl, nullptr);
+    if (warp == 0) L.cta[(size_t)blockIdx.x * 32 + lane] = wtk;
     __syncthreads();
     const int g = (int)blockIdx.x / L.grp_size, g0 = g * L.grp_size;
     const int gn = min(L.grp_size, (int)gridDim.x - g0);
@@ -706,41 +721,155 @@ static __device__ __noinline__ void step_reduce(const StepTail &T, uint64_t wtk,
     if (tid == 0) s_last = ticket_next(L.tick + g) == (uint32_t)(gn - 1);
     __syncthreads();
     if (!s_last) return;
-    int4 inf;
-    uint64_t t = block_merge_lists_info<NW>(L.cta + (size_t)g0 * 32, L.cinf + g0, gn, s_wl, s_inf, inf);
-    if (warp == 0) {
-        L.grp[(size_t)g * 32 + lane] = t;
-        if (lane == 0) L.ginf[g] = inf;
-    }
+    uint64_t t = block_merge_lists<NW>(L.cta + (size_t)g0 * 32, gn, s_wl);
+    if (warp == 0) L.grp[(size_t)g * 32 + lane] = t;
     if (tid == 0) L.tick[g] = 0;
-    if (T.do_apply) {
-        const ApplyArgs &P = T.ap;
-        const size_t ts = (size_t)P.T * P.S, t1s = (size_t)(P.T + 1) * P.S;
-        const int i = g * kEvalThreads + tid, nt = ng * kEvalThreads;
-        prefetch_l2_range(P.oreT, t1s * sizeof(int64_t), i, nt);
-        prefetch_l2_range(P.metal, ts * sizeof(double), i, nt);
-        prefetch_l2_range(P.contrib, ts * sizeof(double), i, nt);
-        prefetch_l2_range(P.npv, (size_t)P.S * sizeof(double), i, nt);
-        prefetch_l2_range(P.tab, (size_t)2 * (P.T + 1) * P.S_pad * sizeof(float), i, nt);
-        if (warp == 0 && __shfl_sync(0xffffffffu, t, 0) != 0ull) {
-            const size_t row = (size_t)P.S * sizeof(double);
-            prefetch_l2_range(P.grade + (size_t)inf.x * P.S, row, lane, 32);
-            if (inf.y != P.tp.B) prefetch_l2_range(P.grade + (size_t)inf.y * P.S, row, lane, 32);
-        }
-    }
     __syncthreads();
     if (tid == 0) s_last = ticket_next(L.tick + L.final_slot) == (uint32_t)(ng - 1);
     __syncthreads();
     if (!s_last) return;
-    t = block_merge_lists_info<NW>(L.grp, L.ginf, ng, s_wl, s_inf, inf);
+    t = block_merge_lists<NW>(L.grp, ng, s_wl);
+    if (warp == 0) warp_write_topk(t, T.k, T.n, T.status, T.idx_out, T.top_out, T.count_out);
+    if (tid == 0) L.tick[L.final_slot] = 0;
+}
+
+// Per-warp lists and staging of the evaluator (static shared memory).
+template <int NW>
+struct EvalSharedT {
+    int32_t b1[NW][kChunk], b2[NW][kChunk];
+    uint32_t tt[NW][kChunk];
+    uint8_t lsh[NW][kChunk], lsw[NW][kChunk];
+    float score[NW][kChunk], mean[NW][kChunk];
+    uint8_t flag[NW][kChunk];
+    int4 best[NW];  // TOPK: the move of the warp's best key (b1, b2 or B, t1 | t2 << 8, 0)
+};
+using EvalShared = EvalSharedT<kEvalThreads / 32>;
+
+// Static shared memory of an evaluator CTA.  The fused step's final CTA reuses
+// the per-warp staging once every warp has finished evaluating, for the
+// batch's selection and the apply.
+template <int NW>
+struct EvalSmemPlain {
+    EvalSharedT<NW> ev;
+};
+template <int NW>
+union EvalSmemStep {
+    EvalSharedT<NW> ev;
+    float apply_tab[kApplyTabMax];
+};
+
+// End of the fused search step, called by every thread of every CTA (NW warps,
+// one CTA per SM) with the warp's list wtk and the move record of each warp's
+// best key (winfo[warp], shared memory).  su: the CTA's shared staging, free
+// for reuse once every warp has arrived here (the final CTA's selection and
+// apply use it).
+//   0. The first warp of the CTA to finish evaluating (s_fin, a shared counter
+//      zeroed at the CTA's start) does the CTA's share of the FP64 update the
+//      previous step left due (*pending): metal, net cash and NPV_s of
+//      scenarios blockIdx.x, blockIdx.x + gridDim.x, ..., while the CTA's
+//      other warps still evaluate.
+//   1. The CTA merges its warps' lists (a tree of warp merges, keeping the
+//      record of the best key), publishes the result and that record,
+//      prefetches its share of the state the final apply touches into L2, and
+//      draws the final ticket (acquire-release; nobody waits).
+//   2. The CTA that draws the last number ranks the lists' heads (only lists
+//      whose heads rank among the 32 best can hold one of the 32 best keys),
+//      merges those lists (a tree of warp merges), writes the top k, applies
+//      the structural part of the best move from its record (tonnage, schedule
+//      words, penalty tables: all the next evaluation reads) and leaves the
+//      move's FP64 part due in *pending (or clears *pending without an apply).
+// Counters are reset by the final CTA.  Not inlined: the evaluator's main loop
+// keeps its own register allocation.
+template <int NW>
+static __device__ __noinline__ void step_finish(const StepTail &T, uint64_t wtk, const int4 *winfo,
+                                                EvalSmemStep<NW> &su, uint32_t *s_fin) {
+    constexpr int NT = NW * 32;
+    __shared__ uint64_t s_wl[NW][32];
+    __shared__ int4 s_inf[NW];
+    __shared__ uint64_t s_heads[256];  // grids of up to 256 CTAs (one per SM)
+    __shared__ int s_slot[32];
+    __shared__ int4 s_best_inf;
+    __shared__ int s_last, s_best;
+    const StepLists &L = T.L;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    uint32_t order = 0u;
+    if (lane == 0) order = atomicAdd(s_fin, 1u);
+    if (__shfl_sync(0xffffffffu, order, 0) == 0u) {
+        const int4 pend = *T.pending;
+        if (pend.w) apply_money(T.ap, pend, (int)blockIdx.x + lane * (int)gridDim.x, 32 * (int)gridDim.x);
+    }
+    s_wl[warp][lane] = wtk;
+    if (lane == 0) s_inf[warp] = winfo[warp];
+    __syncthreads();
+    // 1. the CTA's 32 best keys: a tree of warp merges
+    wtk = tree_merge<NW, true>(wtk, s_wl, s_inf);
+    if (warp == 0) {
+        L.cta[(size_t)blockIdx.x * 32 + lane] = wtk;
+        if (lane == 0) L.cinf[blockIdx.x] = s_inf[0];  // unused when the list is empty
+    }
+    if (T.do_apply) {
+        const ApplyArgs &P = T.ap;
+        const int i = (int)blockIdx.x * NT + tid, nt = (int)gridDim.x * NT;
+        prefetch_l2_range(P.oreT, (size_t)(P.T + 1) * P.S * sizeof(int64_t), i, nt);
+        prefetch_l2_range(P.tab, (size_t)2 * (P.T + 1) * P.S_pad * sizeof(float), i, nt);
+        prefetch_l2_range(P.blk, (size_t)P.tp.B * sizeof(uint32_t), i, nt);
+    }
+    __syncthreads();
+    if (tid == 0) s_last = ticket_next(L.tick + L.final_slot) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    // 2. the batch's top k
+    const int G = (int)gridDim.x;
+    int4 inf;
+    uint64_t t;
+    if (G <= 256) {
+        // Only a list whose head is among the 32 best heads can hold one of
+        // the 32 best keys (those heads are 32 keys at least as large as any
+        // key of a list below them): rank the heads, then merge those lists.
+        uint64_t head = 0ull;
+        int4 my_inf = make_int4(0, 0, 0, 0);
+        if (tid < G) {
+            head = __ldcg(L.cta + (size_t)tid * 32);
+            my_inf = __ldcg(L.cinf + tid);
+            s_heads[tid] = head;
+        }
+        const int nonempty = __syncthreads_count(head != 0ull);
+        if (tid < G && head != 0ull) {
+            int r = 0;
+            for (int j = 0; j < G; j++) r += s_heads[j] > head ? 1 : 0;
+            if (r < 32) {
+                s_slot[r] = tid;
+                if (r == 0) s_best_inf = my_inf;  // the best key heads its CTA's list
+            }
+        }
+        __syncthreads();
+        // warp w < 16 merges the lists of ranks 2w and 2w + 1, then a tree
+        const int nc = min(nonempty, 32);
+        t = 0ull;
+        if (warp < 16) {
+            const uint64_t a = 2 * warp < nc ? __ldcg(L.cta + (size_t)s_slot[2 * warp] * 32 + lane) : 0ull;
+            const uint64_t b = 2 * warp + 1 < nc ? __ldcg(L.cta + (size_t)s_slot[2 * warp + 1] * 32 + lane) : 0ull;
+            t = warp_topk_merge(a, b);
+            s_wl[warp][lane] = t;
+        }
+        __syncthreads();
+        t = tree_merge<(NW < 16 ? NW : 16), false>(t, s_wl, nullptr);
+        inf = s_best_inf;
+    } else {
+        t = block_merge_lists_info<NW>(L.cta, L.cinf, G, s_wl, s_inf, inf);
+    }
     if (warp == 0) {
         const int best = warp_write_topk(t, T.k, T.n, T.status, T.idx_out, T.top_out, T.count_out);
         if (lane == 0) s_best = best;
     }
     if (tid == 0) L.tick[L.final_slot] = 0;
-    if (!T.do_apply) return;
+    if (!T.do_apply) {
+        if (tid == 0) T.pending->w = 0;  // every CTA has read it
+        return;
+    }
     __syncthreads();
-    apply_evaluated(T.ap, inf, s_best >= 0 ? 1 : 0);
+    const int changed = apply_evaluated<false>(T.ap, inf, s_best >= 0 ? 1 : 0, su.apply_tab);
+    if (tid == 0) *T.pending = make_int4(inf.x, inf.y, inf.z, changed);
 }
 
 // List storage and tickets of model m for a launch of `grid` CTAs (mm_eval.cu).
@@ -755,23 +884,15 @@ __device__ __forceinline__ int2 load_move(const EvalArgs &A, int64_t i) {
 EvalArgs eval_args(mm_model *m, const mm_move *moves, int64_t n, float *score, uint8_t *feas, float *mean,
                    float *delta);
 
-// Per-warp lists and staging of the evaluator (static shared memory).
-struct EvalShared {
-    int32_t b1[kEvalThreads / 32][kChunk], b2[kEvalThreads / 32][kChunk];
-    uint32_t tt[kEvalThreads / 32][kChunk];
-    uint8_t lsh[kEvalThreads / 32][kChunk], lsw[kEvalThreads / 32][kChunk];
-    float score[kEvalThreads / 32][kChunk], mean[kEvalThreads / 32][kChunk];
-    uint8_t flag[kEvalThreads / 32][kChunk];
-    int4 best[kEvalThreads / 32];  // TOPK: the move of the warp's best key (b1, b2 or B, t1 | t2 << 8, 0)
-};
 
 // The evaluator proper: the calling warp evaluates moves [r0, r1) of A in
 // chunks of 64 (decode two per lane, shift / swap lists by ballot, teams of
 // TEAM lanes per move, coalesced stores) and, if TOPK, inserts every feasible
 // move's key into its register list wtk.  tab, s_dd, s_mined and s_cap are
 // the CTA's staged tables.
-template <int TEAM, int QMAX, bool KAHAN, bool DELTA, int KF, bool TAIL, bool TOPK, bool SIG = false>
-__device__ __forceinline__ void eval_warp_range(const EvalArgs &A, EvalShared &sh, const float *tab, const float *s_dd,
+template <int TEAM, int QMAX, bool KAHAN, bool DELTA, int KF, bool TAIL, bool TOPK, bool SIG = false,
+          int NW = kEvalThreads / 32>
+__device__ __forceinline__ void eval_warp_range(const EvalArgs &A, EvalSharedT<NW> &sh, const float *tab, const float *s_dd,
                                                 const int64_t *s_mined, const uint64_t *s_cap, int64_t r0, int64_t r1,
                                                 uint64_t &wtk) {
     constexpr int CH = kChunk;
@@ -921,11 +1042,12 @@ __device__ __forceinline__ void eval_warp_range(const EvalArgs &A, EvalShared &s
 }
 
 template <int TEAM, int QMAX, bool KAHAN, bool DELTA, bool TSM, int KF = 0, bool TAIL = false, bool TOPK = false,
-          bool SIG = false>
-__global__ void __launch_bounds__(kEvalThreads, MM_EVAL_MINB) k_eval_tiled(EvalArgs A) {
-    constexpr int NW = kEvalThreads / 32;   // warps per CTA
+          bool SIG = false, int NT = kEvalThreads>
+__global__ void __launch_bounds__(NT, NT == kEvalThreads ? MM_EVAL_MINB : 1) k_eval_tiled(EvalArgs A) {
+    constexpr int NW = NT / 32;   // warps per CTA
     extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ EvalShared sh;
+    __shared__ __align__(16) std::conditional_t<TOPK, EvalSmemStep<NW>, EvalSmemPlain<NW>> su;
+    EvalSharedT<NW> &sh = su.ev;
 
     const int T1 = A.T + 1;
     const size_t tab_floats = (size_t)2 * T1 * A.S_pad;
@@ -937,14 +1059,16 @@ __global__ void __launch_bounds__(kEvalThreads, MM_EVAL_MINB) k_eval_tiled(EvalA
     uint64_t *s_cap = reinterpret_cast<uint64_t *>(s_mined + T1);              // [T+1]
 
     const int tid = threadIdx.x;
+    __shared__ uint32_t s_fin;  // TOPK: warps of this CTA that have finished evaluating
+    if (TOPK && tid == 0) s_fin = 0u;
     if (TSM) {
         const float4 *src = reinterpret_cast<const float4 *>(A.tab);
         float4 *dst = reinterpret_cast<float4 *>(s_tab);
-        for (int i = tid; i < (int)(tab_floats / 4); i += kEvalThreads) dst[i] = __ldg(src + i);
+        for (int i = tid; i < (int)(tab_floats / 4); i += NT) dst[i] = __ldg(src + i);
     }
     if (A.dd_smem)
-        for (int i = tid; i < T1 * T1; i += kEvalThreads) s_dd[i] = __ldg(A.ddt + i);
-    for (int i = tid; i < T1; i += kEvalThreads) {
+        for (int i = tid; i < T1 * T1; i += NT) s_dd[i] = __ldg(A.ddt + i);
+    for (int i = tid; i < T1; i += NT) {
         s_mined[i] = A.minedT[i];
         s_cap[i] = A.cap[i];
     }
@@ -957,9 +1081,9 @@ __global__ void __launch_bounds__(kEvalThreads, MM_EVAL_MINB) k_eval_tiled(EvalA
     const int64_t gw = (int64_t)blockIdx.x * NW + warp;
     const int64_t r0 = gw * A.n / nwarps, r1 = (gw + 1) * A.n / nwarps;
     uint64_t wtk = 0;  // this warp's best 32 candidate keys (TOPK)
-    eval_warp_range<TEAM, QMAX, KAHAN, DELTA, KF, TAIL, TOPK, SIG>(A, sh, tab, A.dd_smem ? s_dd : A.ddt, s_mined,
-                                                                   s_cap, r0, r1, wtk);
-    if constexpr (TOPK) step_reduce(A.tail, wtk, A.tail.do_apply ? sh.best : nullptr);
+    eval_warp_range<TEAM, QMAX, KAHAN, DELTA, KF, TAIL, TOPK, SIG, NW>(A, sh, tab, A.dd_smem ? s_dd : A.ddt,
+                                                                       s_mined, s_cap, r0, r1, wtk);
+    if constexpr (TOPK) step_finish<NW>(A.tail, wtk, sh.best, su, &s_fin);
 }
 
 // ----------------------------------------------------------------------------

@@ -111,6 +111,10 @@ struct mm_model {
     int4 *step_cinf = nullptr;       // [step_max_ctas] move record of each CTA list's best key
     int4 *step_ginf = nullptr;       // [step_max_ctas] move record of each group list's best key
     uint32_t *step_tick = nullptr;   // [step_max_ctas + 1] group tickets, then the final ticket (zero between launches)
+    int4 *pending = nullptr;         // the move whose FP64 update a fused step left due: (b1, b2 or B,
+                                     // t1 | t2 << 8, due); done by the next step's CTAs (a share of the
+                                     // scenarios each) or by settle_money
+    int money_due = 0;               // host: a fused step with apply was issued since the last settle
     int step_max_ctas = 0;
     void *step_event = nullptr;      // cudaEvent_t recorded between the step's two launches (timing hook)
     float *shadow32 = nullptr;       // FP32 shadow accumulators: metal [T][S], contrib [T][S], npv [S]
@@ -130,6 +134,9 @@ mm_status sticky_status(mm_model *m, uint32_t st);  // maps and clears sticky bi
 
 // Kernels and launchers shared between translation units.
 mm_status rebuild_tables(mm_model *m);                     // Pout/Pin from oreT
+// Launch the FP64 update a fused step left due (metal, net cash, NPV_s), if
+// any; every host path that reads or changes those totals calls it first.
+mm_status settle_money(mm_model *m, cudaStream_t stream = nullptr);  // nullptr: the model's stream
 // Outputs of the fused search step (top-k of the batch, optional apply).
 struct StepOut {
     int32_t k, apply;

@@ -243,6 +243,7 @@ static mm_status shadow_init(mm_model *m) {
 // bad move).
 __global__ void __launch_bounds__(1024) k_apply(ApplyArgs A, int2 mv_val, const int2 *moves, int64_t n_moves, const int32_t *idx,
                         const int32_t *count, int from_dev) {
+    __shared__ __align__(16) float s_tab[kApplyTabMax];
     int2 mv = mv_val;
     int have = 1;
     if (from_dev) {
@@ -257,7 +258,16 @@ __global__ void __launch_bounds__(1024) k_apply(ApplyArgs A, int2 mv_val, const 
             }
         }
     }
-    apply_block(A, mv, have);
+    apply_block(A, mv, have, s_tab);
+}
+
+// The FP64 part of the move a fused step applied structurally (*pending, if
+// still due): metal, net cash and NPV_s, then the record is cleared.
+__global__ void __launch_bounds__(1024) k_apply_pending(ApplyArgs A, int4 *pending) {
+    const int4 p = *pending;
+    if (p.w) apply_money(A, p, threadIdx.x, blockDim.x);
+    __syncthreads();
+    if (threadIdx.x == 0) pending->w = 0;
 }
 
 // NPV mean and population std over scenarios of the current schedule (FP64,
@@ -336,6 +346,16 @@ ApplyArgs apply_args(mm_model *m) {
     return A;
 }
 
+static int apply_threads(const mm_model *m);
+
+mm_status settle_money(mm_model *m, cudaStream_t stream) {
+    if (!m->money_due) return MM_OK;
+    k_apply_pending<<<1, apply_threads(m), 0, stream ? stream : m->stream>>>(apply_args(m), m->pending);
+    mm_status st = check_launch("k_apply_pending");
+    if (st == MM_OK) m->money_due = 0;
+    return st;
+}
+
 static int apply_threads(const mm_model *m) {
     int t = ((m->S + 31) / 32) * 32;
     if (t < 64) t = 64;
@@ -389,6 +409,7 @@ void mm_model_destroy(mm_model *m) {
     cudaFree(m->step_cinf);
     cudaFree(m->step_ginf);
     cudaFree(m->step_tick);
+    cudaFree(m->pending);
     cudaFree(m->tabc);
     cudaFree(m->relax_scratch);
     cudaFree(m->relax_tick);
@@ -520,6 +541,7 @@ mm_status mm_model_create(const mm_model_desc *d, mm_model **out) {
     ALLOC(step_cinf, (size_t)m->step_max_ctas);
     ALLOC(step_ginf, (size_t)m->step_max_ctas);
     ALLOC(step_tick, (size_t)m->step_max_ctas + 1);
+    ALLOC(pending, 1);
     ALLOC(tabc, (int64_t)4 * (T + 1));
     ALLOC(relax_tick, 1);
     if (!grid) {
@@ -582,6 +604,7 @@ mm_status mm_model_create(const mm_model_desc *d, mm_model **out) {
     TRY(cudaMemsetAsync(m->minedT, 0, sizeof(int64_t) * (T + 1), s), "clear minedT");
     TRY(cudaMemsetAsync(m->apply_res, 0, sizeof(ApplyResult), s), "clear apply result");
     TRY(cudaMemsetAsync(m->step_tick, 0, sizeof(uint32_t) * ((size_t)m->step_max_ctas + 1), s), "clear step tickets");
+    TRY(cudaMemsetAsync(m->pending, 0, sizeof(int4), s), "clear the pending apply");
     TRY(cudaMemsetAsync(m->relax_tick, 0, sizeof(uint32_t), s), "clear relaxed ticket");
     if (!grid) {
         TRY(cudaMemcpyAsync(m->pred_ptr, d->pred_ptr, sizeof(int32_t) * (B + 1), cudaMemcpyHostToDevice, s), "copy CSR");
@@ -644,6 +667,9 @@ mm_status mm_schedule_set(mm_model *m, const uint8_t *period, int *base_feasible
         cudaError_t e_ = (expr);                          \
         if (e_ != cudaSuccess) return done(cuda_status(e_, what)); \
     } while (0)
+    // every total is rebuilt from the new schedule: an FP64 update still due is void
+    TRY(cudaMemsetAsync(m->pending, 0, sizeof(int4), s), "clear the pending apply");
+    m->money_due = 0;
     TRY(cudaMemcpyAsync(d_period, period, B, cudaMemcpyHostToDevice, s), "copy schedule");
     TRY(cudaMemcpyAsync(m->order, order.data(), sizeof(int32_t) * B, cudaMemcpyHostToDevice, s), "copy order");
     TRY(cudaMemcpyAsync(m->porder, cnt.data(), sizeof(int32_t) * (T + 2), cudaMemcpyHostToDevice, s), "copy order");
@@ -697,6 +723,8 @@ mm_status mm_schedule_get(mm_model *m, uint8_t *period) {
 mm_status mm_apply_move(mm_model *m, mm_move mv, double *mean, double *sd) {
     if (!m) return set_error(MM_ERR_INVALID_ARG, "NULL model");
     if (!m->has_schedule) return set_error(MM_ERR_STATE, "no schedule installed");
+    mm_status ss = settle_money(m);
+    if (ss != MM_OK) return ss;
     ApplyArgs A = apply_args(m);
     k_apply<<<1, apply_threads(m), 0, m->stream>>>(A, make_int2(mv.b1, mv.arg), nullptr, 0, nullptr, nullptr, 0);
     mm_status st = check_launch("k_apply");
@@ -718,6 +746,8 @@ mm_status mm_apply_best(mm_model *m, const mm_move *moves, int64_t n, const int3
     if (!m || (!moves && n > 0) || !idx || !count) return set_error(MM_ERR_INVALID_ARG, "mm_apply_best: NULL argument");
     if (n < 0) return set_error(MM_ERR_INVALID_ARG, "negative move count");
     if (!m->has_schedule) return set_error(MM_ERR_STATE, "no schedule installed");
+    mm_status ss = settle_money(m);
+    if (ss != MM_OK) return ss;
     ApplyArgs A = apply_args(m);
     k_apply<<<1, apply_threads(m), 0, m->stream>>>(A, make_int2(0, 0), (const int2 *)moves, n, idx, count, 1);
     return check_launch("k_apply");
@@ -725,6 +755,8 @@ mm_status mm_apply_best(mm_model *m, const mm_move *moves, int64_t n, const int3
 
 mm_status mm_set_fp32_shadow(mm_model *m, int32_t enable) {
     if (!m) return set_error(MM_ERR_INVALID_ARG, "NULL model");
+    mm_status ss = settle_money(m);
+    if (ss != MM_OK) return ss;
     if (!enable) {
         MM_CUDA_TRY(cudaStreamSynchronize(m->stream), "synchronize");
         cudaFree(m->shadow32);
@@ -741,6 +773,8 @@ mm_status mm_get_fp32_shadow_npv(mm_model *m, double *npv_host) {
     if (!m || !npv_host) return set_error(MM_ERR_INVALID_ARG, "NULL argument");
     if (!m->shadow32) return set_error(MM_ERR_STATE, "FP32 shadow accumulators are off");
     if (!m->has_schedule) return set_error(MM_ERR_STATE, "no schedule installed");
+    mm_status ss = settle_money(m);
+    if (ss != MM_OK) return ss;
     std::vector<float> v(m->S);
     MM_CUDA_TRY(cudaMemcpyAsync(v.data(), m->shadow32 + 2 * (size_t)m->T * m->S, sizeof(float) * m->S,
                                 cudaMemcpyDeviceToHost, m->stream),
@@ -753,7 +787,8 @@ mm_status mm_get_fp32_shadow_npv(mm_model *m, double *npv_host) {
 mm_status mm_last_apply(mm_model *m, int32_t *applied, double *mean, double *sd) {
     if (!m) return set_error(MM_ERR_INVALID_ARG, "NULL model");
     if (m->has_schedule) {
-        mm_status st = npv_stats_launch(m);
+        mm_status st = settle_money(m);
+        if (st == MM_OK) st = npv_stats_launch(m);
         if (st != MM_OK) return st;
     }
     // the result and the sticky status come back with one synchronisation
@@ -771,6 +806,8 @@ mm_status mm_last_apply(mm_model *m, int32_t *applied, double *mean, double *sd)
 mm_status mm_npv(mm_model *m, double *npv_host, double *mean, double *sd) {
     if (!m) return set_error(MM_ERR_INVALID_ARG, "NULL model");
     if (!m->has_schedule) return set_error(MM_ERR_STATE, "no schedule installed");
+    mm_status ss = settle_money(m);
+    if (ss != MM_OK) return ss;
     std::vector<double> v(m->S);
     MM_CUDA_TRY(cudaMemcpyAsync(v.data(), m->npv, sizeof(double) * m->S, cudaMemcpyDeviceToHost, m->stream), "read npv");
     MM_CUDA_TRY(cudaStreamSynchronize(m->stream), "synchronize");
@@ -817,6 +854,8 @@ mm_status mm_get_tonnage(mm_model *m, int64_t *mined_host, int64_t *ore_t_host) 
 mm_status mm_get_metal(mm_model *m, double *metal_host) {
     if (!m || !metal_host) return set_error(MM_ERR_INVALID_ARG, "NULL argument");
     if (!m->has_schedule) return set_error(MM_ERR_STATE, "no schedule installed");
+    mm_status ss = settle_money(m);
+    if (ss != MM_OK) return ss;
     MM_CUDA_TRY(cudaMemcpyAsync(metal_host, m->metal, sizeof(double) * (size_t)m->T * m->S, cudaMemcpyDeviceToHost,
                                 m->stream), "read metal");
     MM_CUDA_TRY(cudaStreamSynchronize(m->stream), "synchronize");

@@ -1,7 +1,8 @@
 // The fused search step: instantiations of the evaluator's top-k variant
-// (plain FP32 sums, no per-scenario output; the batch's top k is selected and
-// the best move applied by the CTAs that finish last, see step_reduce), the
-// list-based top-k for k <= 32, and the entry point.
+// (plain FP32 sums, no per-scenario output, one CTA of kStepThreads per SM;
+// the batch's top k is selected and the best move applied by the CTA that
+// finishes last, see step_finish), the list-based top-k for k <= 32, and the
+// entry point.
 #include "mm_eval_tiled.cuh"
 
 namespace mm {
@@ -10,7 +11,7 @@ using EvalFn = void (*)(EvalArgs);
 
 template <int TEAM, int KF, bool TAIL>
 static EvalFn step_fast3() {
-    return k_eval_tiled<TEAM, 1, false, false, false, KF, TAIL, true>;
+    return k_eval_tiled<TEAM, 1, false, false, false, KF, TAIL, true, false, kStepThreads>;
 }
 
 template <int TEAM>
@@ -26,8 +27,8 @@ static EvalFn step_fast2(int kf, bool tail) {
 
 template <int TEAM, int QMAX>
 static EvalFn step_gen2(bool tsm) {
-    return tsm ? k_eval_tiled<TEAM, QMAX, false, false, true, 0, false, true>
-               : k_eval_tiled<TEAM, QMAX, false, false, false, 0, false, true>;
+    return tsm ? k_eval_tiled<TEAM, QMAX, false, false, true, 0, false, true, false, kStepThreads>
+               : k_eval_tiled<TEAM, QMAX, false, false, false, 0, false, true, false, kStepThreads>;
 }
 
 template <int TEAM>
@@ -85,7 +86,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_topk_lists(const float *__rest
             wtk = warp_topk_insert(wtk, (ok[u] && !isnan(f[u])) ? score_key(f[u], i) : 0ull);
         }
     }
-    step_reduce(tail, wtk, nullptr);
+    step_reduce(tail, wtk);
 }
 
 mm_status topk_small_launch(mm_model *m, const float *score, const uint8_t *feas, int64_t n, int32_t k, int32_t *idx,
@@ -147,7 +148,7 @@ static mm_status search_step(mm_model *m, const mm_move *moves, const uint32_t *
     const bool weighted_split = m->sig && !sigma_fast_ok(m, MM_EVAL_PLAIN);
     // the final CTA of the evaluation launch applies the best move itself
     // when a CTA has a thread per scenario; otherwise a one-CTA launch follows
-    const bool in_launch = apply && m->S <= kEvalThreads;
+    const bool in_launch = apply && m->S <= kStepThreads;
     if (packed && (weighted_split || (apply && !in_launch)))
         return set_error(MM_ERR_INVALID_ARG,
                          "mm_search_step_packed: this model's step is not one launch (S = %d%s); use "
@@ -171,6 +172,8 @@ static mm_status search_step(mm_model *m, const mm_move *moves, const uint32_t *
     st = eval_launch(m, moves, n, score, feas, nullptr, nullptr, MM_EVAL_PLAIN, m->team, m->ctas_per_sm, 0, &so,
                      pmoves);
     if (st != MM_OK) return st;
+    // the launch's final CTA leaves the applied move's FP64 update due
+    if (in_launch) m->money_due = 1;
     st = record_step_event(m);
     if (st != MM_OK) return st;
     return (apply && !in_launch) ? mm_apply_best(m, moves, n, idx, count) : MM_OK;

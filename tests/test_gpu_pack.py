@@ -128,8 +128,9 @@ def test_packed_step_bad_codes_and_no_apply():
 def test_packed_step_refused_where_not_one_launch():
     import paper_2511_18296_b300 as mm
     packed = torch.zeros(8, dtype=torch.int32, device="cuda")
-    # S > 256 with apply: the apply is a second launch
-    p = tiny_problem(S=260, T=3)
+    # S > 768 (more scenarios than the step's CTA has threads) with apply:
+    # the apply is a second launch
+    p = tiny_problem(S=800, T=3)
     m = mm.Model.from_problem(p)
     m.schedule_set(p.x0)
     with pytest.raises(mm.MMError) as e:

@@ -184,3 +184,99 @@ def test_step_run_time_shaped_loop_large_tables():
     for _ in range(3):
         _compare(a.search_step(mv, k=8, apply=True), _separate(b, mv, 8, True), 8)
     assert np.array_equal(a.schedule_get(), b.schedule_get())
+
+
+def test_step_fp64_update_settles_before_every_reader():
+    """The fused step's final CTA applies the structural part of the best move
+    (tonnage, schedule words, tables) and leaves its FP64 part (metal, net
+    cash, NPV_s) to the first CTA of the next step, or to the library before
+    any call that reads or changes those totals.  Interleave fused steps with
+    each such call on one model and the separate calls on a twin: every
+    result must be the same bits.  Batches of 100 moves run as one CTA (its
+    first and final CTA are the same)."""
+    import paper_2511_18296_b300 as mm
+    p = W.config("plain_4k")
+    a, b = _pair(p)
+    mv = torch.as_tensor(p.moves, device="cuda")
+    small = torch.as_tensor(p.moves[:100], device="cuda")
+
+    def both_step(batch, k=8):
+        _compare(a.search_step(batch, k=k, apply=True), _separate(b, batch, k, True), k)
+
+    def same_npv():
+        na, nb = a.npv(), b.npv()
+        assert np.array_equal(na[0], nb[0]) and na[1:] == nb[1:]
+
+    both_step(mv)
+    same_npv()                                   # mm_npv settles
+    both_step(mv)
+    both_step(small)                             # one CTA: first finisher and final CTA at once
+    assert a.last_apply() == b.last_apply()      # mm_last_apply settles
+    both_step(mv)
+    assert np.array_equal(a.metal(), b.metal())  # mm_get_metal settles
+    both_step(mv)
+    inc = O.OracleModel(p).eval_incremental(a.schedule_get(), p.moves)
+    j = int(np.flatnonzero(inc["flag"])[0])
+    assert a.apply_move(tuple(p.moves[j])) == b.apply_move(tuple(p.moves[j]))  # mm_apply_move settles first
+    same_npv()
+    for m in (a, b):
+        m.set_fp32_shadow(True)                  # the shadow starts from settled totals
+    both_step(mv)
+    both_step(mv)
+    assert np.array_equal(a.fp32_shadow_npv(), b.fp32_shadow_npv())
+    for m in (a, b):
+        m.set_fp32_shadow(False)
+    both_step(mv)
+    for m in (a, b):                             # a batch that applies settles its chains first
+        bt = mm.Batch([(m, small)], k=4, apply=True)
+        bt.run()
+        torch.cuda.synchronize()
+        bt.close()
+    same_npv()
+    both_step(mv)                                # a new schedule voids the update still due
+    for m in (a, b):
+        m.schedule_set(p.x0)
+    same_npv()
+    both_step(mv)
+    st = torch.cuda.Stream()                     # steps replayed from a captured graph
+    a.set_stream(st)
+    outs = [torch.empty(p.moves.shape[0], device="cuda"), torch.empty(p.moves.shape[0], dtype=torch.uint8,
+            device="cuda"), torch.empty(8, dtype=torch.int32, device="cuda"), torch.empty(8, device="cuda"),
+            torch.empty(1, dtype=torch.int32, device="cuda")]
+    step = lambda: a.search_step(mv, k=8, apply=True, score=outs[0], feas=outs[1], idx=outs[2], top=outs[3],  # noqa
+                                 count=outs[4])
+    with torch.cuda.stream(st):
+        step()
+    st.synchronize()
+    _separate(b, mv, 8, True)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=st):
+        step()
+        step()
+    for _ in range(3):
+        g.replay()
+        for _ in range(2):
+            rb = _separate(b, mv, 8, True)
+    st.synchronize()
+    _compare(outs, rb, 8)
+    assert np.array_equal(a.schedule_get(), b.schedule_get())
+    same_npv()
+
+
+@pytest.mark.parametrize("S", [260, 500, 768])
+def test_step_in_launch_apply_up_to_768_scenarios(S):
+    """Up to 768 scenarios (one thread each in the step's CTA) the best move is
+    applied inside the step's launch: same scores, flags, top-k, schedule and
+    NPV as the separate calls, and the FP64 state equals a rebuild."""
+    p = tiny_problem(6, 6, 3, S=S, T=6, seed=S, cap_blocks=8, target_blocks=3)
+    a, b = _pair(p)
+    mv = torch.as_tensor(all_moves(p.B, p.T)[::3].copy(), device="cuda")
+    for _ in range(4):
+        _compare(a.search_step(mv, k=8, apply=True), _separate(b, mv, 8, True), 8)
+        assert a.last_apply() == b.last_apply()
+    assert np.array_equal(a.schedule_get(), b.schedule_get())
+    assert np.array_equal(a.npv()[0], b.npv()[0])
+    import paper_2511_18296_b300 as mm
+    fresh = mm.Model.from_problem(p)
+    fresh.schedule_set(a.schedule_get())
+    np.testing.assert_allclose(a.npv()[0], fresh.npv()[0], rtol=1e-12, atol=1e-3)
