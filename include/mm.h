@@ -336,24 +336,29 @@ mm_status mm_batch_autotune(mm_batch *b, int32_t reps, int32_t *moves_per_item, 
                             float *best_ms);
 
 /* mm_topk for callers that must not allocate device memory, such as code
- * that runs while a CUDA stream is being captured into a graph (cudaMalloc may
- * not be called then), code that owns a fixed memory budget or pool and must
- * not grow it, or a loop that must never block the device the way cudaMalloc
- * and cudaFree can.  The paper has no counterpart: it is an interface
- * convenience of this library.  It needs no model: it selects, from
- * score_dev[n] / feasible_dev[n], the k feasible moves with the largest score
- * exactly as mm_topk does (same outputs, ties to the lower index) and enqueues
- * the work on cuda_stream (NULL = default stream).
- * Scratch: one fixed device array inside this library (about 8 MiB, held on
- * every GPU that loads the library until the process exits); n must be at
- * most 1,048,576 (else MM_ERR_INVALID_ARG) and 1 <= k <= 1024.  No call
- * allocates: each clears the parts of the array that must start at zero with
- * an asynchronous memset on cuda_stream.  The first call on a device looks up
- * the array's device address (cudaGetSymbolAddress) with that device current;
- * make that first call before capturing a stream into a graph.  All calls
- * share the one array, so two calls that may run at the same time on the GPU
- * (different streams, or the same device from two threads) race: serialise
- * them.  Asynchronous. */
+ * that owns a fixed memory budget or pool and must not grow it, or a loop that
+ * must never block the device the way cudaMalloc and cudaFree can.  The paper
+ * has no counterpart: it is an interface convenience of this library.  It
+ * needs no model: it selects, from score_dev[n] / feasible_dev[n], the k
+ * feasible moves with the largest score exactly as mm_topk does (same outputs,
+ * ties to the lower index) and enqueues the work on cuda_stream (NULL = default
+ * stream).
+ * Scratch: one fixed device array inside this library (about 8 MiB).  It is
+ * created on a device when the library's top-k module is loaded there: when
+ * the context is created under eager module loading, or at the first use of
+ * the module on that device under lazy loading (the CUDA default), which may
+ * be this entry point's first call; that load allocates, so make the first call
+ * on a device before any fixed memory budget applies.  From then on the array
+ * stays until the process exits; n must be at most 1,048,576 (else
+ * MM_ERR_INVALID_ARG) and 1 <= k <= 1024.  No later call allocates: each clears
+ * the parts of the array that must start at zero with an asynchronous memset
+ * on cuda_stream.  The first call on a device also looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current and keeps it; make
+ * that first call before any stream capture.  The kept address is not valid
+ * across cudaDeviceReset or a destroyed and re-created primary context in the
+ * same process.  All calls share the one array, so two calls that may run at
+ * the same time on the GPU (different streams, or the same device from two
+ * threads) race: serialise them.  Asynchronous. */
 mm_status mm_topk_noalloc(const float *score_dev, const uint8_t *feasible_dev, int64_t n, int32_t k,
                           int32_t *idx_dev, float *topscore_dev, int32_t *count_dev, void *cuda_stream);
 

@@ -148,8 +148,22 @@ def _stream_handle(stream) -> int:
 
 def topk_noalloc(score, feas, k: int, idx, top, count, stream=None):
     """mm_topk_noalloc: top-k without any device allocation (caller passes
-    every output buffer; the scratch is a fixed array inside the library)."""
-    _check(lib().mm_topk_noalloc(_ptr(score), _ptr(feas), int(score.shape[0]), int(k), _ptr(idx), _ptr(top),
+    every output buffer; the scratch is a fixed array inside the library).
+    score float32 [n], feas uint8 [>= n], idx int32 [>= k], top float32
+    [>= k], count int32 [>= 1]: contiguous CUDA tensors on one device
+    (ValueError otherwise, before any device work)."""
+    import torch
+    n = int(score.shape[0])
+    want = ((score, torch.float32, n, "score"), (feas, torch.uint8, n, "feas"), (idx, torch.int32, k, "idx"),
+            (top, torch.float32, k, "top"), (count, torch.int32, 1, "count"))
+    for t, dt, size, name in want:
+        if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != dt or not t.is_contiguous():
+            raise ValueError(f"topk_noalloc: {name} must be a contiguous CUDA tensor of {dt}")
+        if t.numel() < size:
+            raise ValueError(f"topk_noalloc: {name} holds {t.numel()} elements, needs {size}")
+        if t.device != score.device:
+            raise ValueError(f"topk_noalloc: {name} is on {t.device}, score on {score.device}")
+    _check(lib().mm_topk_noalloc(_ptr(score), _ptr(feas), n, int(k), _ptr(idx), _ptr(top),
                                  _ptr(count), _stream_handle(stream)))
     return idx, top, count
 

@@ -189,6 +189,8 @@ EvalArgs eval_args(mm_model *m, const mm_move *moves, int64_t n, float *score, u
     A.S = m->S; A.S_pad = m->S_pad; A.W = m->W; A.T = m->T; A.R = m->R; A.ore_off = m->ore_off;
     A.m_uniform = m->m_uniform;
     A.nstage = 0;
+    A.tx_extra = m->test_stall ? 16u : 0u;
+    A.wait_cycles = m->test_stall ? kTestWaitCycles : kWaitCycles;
     A.dd_smem = (size_t)(m->T + 1) * (m->T + 1) * sizeof(float) <= kDdSmemMax ? 1 : 0;
     A.prefetch = m->prefetch >= 0 ? m->prefetch : ((size_t)m->B * m->R * sizeof(float) > m->l2_bytes ? kPrefetchDram : 0);
 

@@ -92,6 +92,9 @@ struct EvalArgs {
     uint32_t m_uniform;
     int32_t qpl;           // quads per lane actually used (<= QMAX)
     int32_t nstage;        // bulk-copy pipeline depth per warp (TMA path)
+    uint32_t tx_extra;     // TMA path: bytes each stage expects beyond what it copies (0; the test-only stall
+                           // mode expects more, so the stage's bounded wait runs out)
+    long long wait_cycles; // TMA path: limit of a stage's wait (clock cycles)
     int32_t prefetch;      // direct-load path: batches whose rows are prefetched into L1 ahead
     int32_t dd_smem;       // the (T+1)^2 discount differences are staged in shared memory (else read from ddt)
     float lambda;
@@ -1131,14 +1134,16 @@ __device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz: far beyond any legitimate copy latency
+constexpr long long kTestWaitCycles = 2000000LL;  // ~1 ms: the test-only stall mode's limit
 
-// Bounded wait for a pipeline stage (uniform across the warp).
-__device__ __forceinline__ bool stage_wait(uint64_t *bar, uint32_t parity) {
+// Bounded wait for a pipeline stage (uniform across the warp): false when
+// `limit` clock cycles pass first.
+__device__ __forceinline__ bool stage_wait(uint64_t *bar, uint32_t parity, long long limit) {
     bool ok = mbar_try_wait(bar, parity);
     if (!ok) {
         const long long t0 = clock64();
         while (!(ok = mbar_try_wait(bar, parity)))
-            if (clock64() - t0 > kWaitCycles) break;
+            if (clock64() - t0 > limit) break;
     }
     return __all_sync(0xffffffffu, ok);
 }
@@ -1275,7 +1280,7 @@ __global__ void __launch_bounds__(kEvalThreads, 1) k_eval_tma(EvalArgs A) {
                 float *buf = stage0 + (size_t)st * TPW * 2 * R;
                 int ne = nl - e0 < TPW ? nl - e0 : TPW;
                 fence_proxy_async();
-                mbar_arrive_expect_tx(&s_bar[warp][st], (uint32_t)ne * row_bytes * (sw ? 2u : 1u));
+                mbar_arrive_expect_tx(&s_bar[warp][st], (uint32_t)ne * row_bytes * (sw ? 2u : 1u) + A.tx_extra);
                 for (int t = 0; t < ne; t++) {
                     const int slot = list[e0 + t];
                     bulk_copy_g2s(buf + (size_t)t * 2 * R, A.val + (size_t)s_b1[warp][slot] * R, row_bytes,
@@ -1292,12 +1297,12 @@ __global__ void __launch_bounds__(kEvalThreads, 1) k_eval_tma(EvalArgs A) {
 #pragma unroll 1
         for (int j = 0; j < nb; j++) {
             const int st = (int)((cnt0 + (uint32_t)j) % (uint32_t)NS);
-            if (!stage_wait(&s_bar[warp][st], (parity >> st) & 1u)) {
+            if (!stage_wait(&s_bar[warp][st], (parity >> st) & 1u, A.wait_cycles)) {
                 timed_out = true;
                 // drain this warp's copies in flight (bounded), then leave
                 for (int jj = j; jj < nb && jj < j + NS; jj++) {
                     const int st2 = (int)((cnt0 + (uint32_t)jj) % (uint32_t)NS);
-                    stage_wait(&s_bar[warp][st2], (parity >> st2) & 1u);
+                    stage_wait(&s_bar[warp][st2], (parity >> st2) & 1u, A.wait_cycles);
                 }
                 break;
             }

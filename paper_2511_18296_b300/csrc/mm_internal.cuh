@@ -115,6 +115,9 @@ struct mm_model {
                                      // t1 | t2 << 8, due); done by the next step's CTAs (a share of the
                                      // scenarios each) or by settle_money
     int money_due = 0;               // host: a fused step with apply was issued since the last settle
+    int test_stall = 0;              // test-only (MM_TEST_STALL_BULK_WAIT at create): every bulk-copy stage
+                                     // expects 16 bytes it never receives and waits about 1 ms, so the
+                                     // evaluator's timeout path runs without any fault
     int step_max_ctas = 0;
     void *step_event = nullptr;      // cudaEvent_t recorded between the step's two launches (timing hook)
     float *shadow32 = nullptr;       // FP32 shadow accumulators: metal [T][S], contrib [T][S], npv [S]

@@ -6,8 +6,11 @@ global.  Each rank evaluates its slice and selects its own top k; the only
 exchange is an all-gather of the ranks' k (index, score) keys, after which
 every rank selects the batch's top k from the gathered candidates with the
 library's top-k kernel and applies the same best move to its replica of the
-state, so all replicas stay identical.  (When every rank searches its own
-independent batch, nothing is exchanged at all.)
+state (Algorithm 4's assignment after Algorithm 5's evaluation), so all
+replicas stay identical, FP64 totals included: every replica runs the same
+deterministic apply on the same state.  Per step a rank sends k keys of 12
+bytes (8-byte index, 4-byte score) and an 8-byte count.  (When every rank
+searches its own independent batch, nothing is exchanged at all.)
 
 The merge is exact: ranks own increasing index ranges and each rank's
 candidates arrive sorted by (score desc, index asc), so the candidates'
@@ -104,3 +107,51 @@ def model_sharded_topk(model, moves_dev, k: int, group=None):
         return i, t, int(c.cpu()[0])
 
     return sharded_topk(local, merge, n, k, group)
+
+
+def sharded_step(local_select: Callable[[int, int], tuple], merge_select: Callable,
+                 apply_winner: Callable[[int], None], n: int, k: int, group=None):
+    """One search step over ranks: sharded_topk, then apply_winner(global
+    index of the batch's best move) on this rank's replica when some move is
+    feasible.  Every rank applies the same move.  Returns what sharded_topk
+    returns."""
+    gi, gs, c = sharded_topk(local_select, merge_select, n, k, group)
+    if c > 0:
+        apply_winner(int(gi[0]))
+    return gi, gs, c
+
+
+def model_sharded_step(model, moves_dev, k: int, group=None):
+    """sharded_step with the CUDA library, without a host round trip: the
+    fused step on the rank's slice with apply off (mm_search_step), an
+    all-gather of the k keys and the count (device tensors), the exact merge
+    (mm_topk over the candidates), then the device apply of the best move
+    (mm_apply_best on the whole batch with its global index).  Returns (global
+    move indices int64 [k], scores float32 [k], count int32 [1]), device
+    tensors equal on every rank; entries past the count are unspecified."""
+    import torch
+    import torch.distributed as dist
+
+    n = int(moves_dev.shape[0])
+    world, rank = dist.get_world_size(group), dist.get_rank(group)
+    lo, hi = shard_range(n, world, rank)
+    dev = moves_dev.device
+    _, _, idx, top, cnt = model.search_step(moves_dev[lo:hi], k=k, apply=False)
+    live = torch.arange(k, device=dev) < cnt.to(torch.int64)
+    gidx = torch.where(live, idx.to(torch.int64) + lo, torch.full_like(idx, -1, dtype=torch.int64))
+    gsc = torch.where(live, top, torch.zeros_like(top))
+    all_idx = [torch.empty_like(gidx) for _ in range(world)]
+    all_sc = [torch.empty_like(gsc) for _ in range(world)]
+    all_cnt = [torch.empty_like(cnt) for _ in range(world)]
+    dist.all_gather(all_idx, gidx, group=group)
+    dist.all_gather(all_sc, gsc, group=group)
+    dist.all_gather(all_cnt, cnt, group=group)
+    cidx, csc = torch.cat(all_idx), torch.cat(all_sc)
+    cnts = torch.cat(all_cnt).to(torch.int64)
+    cflag = (torch.arange(k, device=dev)[None, :] < cnts[:, None]).reshape(-1).to(torch.uint8)
+    pos, best, count = model.topk(csc.contiguous(), cflag.contiguous(), k)
+    # positions past the count are unspecified: clamp before the gather
+    gpos = pos.to(torch.int64).clamp(0, world * k - 1)
+    win = cidx[gpos]
+    model.apply_best(moves_dev, win[:1].to(torch.int32).contiguous(), count)
+    return win, best, count

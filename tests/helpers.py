@@ -79,3 +79,22 @@ def assert_close_floor(gpu, ref, floor, rel=REL_TOL, what=""):
         idx = np.unravel_index(k, r.shape)
         raise AssertionError(f"{what}: {int(bad.sum())} of {bad.size} outside tolerance; worst at {idx}: "
                              f"gpu={g[idx]!r} ref={r[idx]!r} floor={f[idx]!r}")
+
+
+def certified_swaps(gi, ri, ref_score, ref_floor, rel=REL_TOL):
+    """Positions where the GPU's top-k indices gi differ from the FP64
+    oracle's ri, each checked to be a certified near-tie: the oracle's own
+    scores of the two moves within rel * max(|score|, floor) of each other (so
+    FP32 rounding alone can order them either way).  Returns the count; raises
+    if a swap is not certified or the lengths differ."""
+    gi, ri = np.asarray(gi), np.asarray(ri)
+    if gi.size != ri.size:
+        raise AssertionError(f"top-k sizes differ: {gi.size} vs {ri.size}")
+    bad = np.nonzero(gi != ri)[0]
+    for j in bad:
+        a, b = ref_score[gi[j]], ref_score[ri[j]]
+        scale = max(abs(a), abs(b), ref_floor[gi[j]], ref_floor[ri[j]])
+        if not abs(a - b) <= rel * scale:
+            raise AssertionError(f"top-k position {j}: gpu move {gi[j]} vs oracle move {ri[j]}, oracle scores "
+                                 f"{a!r} and {b!r} are not within {rel} of {scale!r}")
+    return int(bad.size)

@@ -3,7 +3,10 @@ the host with MM_ERR_INVALID_ARG / MM_ERR_STATE; a corrupted move list is
 flagged (flag 0, score -inf, sticky MM_ERR_BAD_MOVE on the next synchronising
 call) and leaves the model usable; an allocation cap (host-side injection,
 MM_ALLOC_CAP_BYTES) turns model creation into MM_ERR_OOM with nothing left
-allocated.  Nothing here traps, faults or hangs the GPU."""
+allocated; a bounded device wait made to run out (test-only mode, set at
+model creation: the bulk-copy stages expect bytes that never come, every copy
+issued still lands) returns MM_ERR_TIMEOUT at the next synchronising call and
+leaves the model usable.  Nothing here traps, faults or hangs the GPU."""
 
 import ctypes as C
 import os
@@ -16,7 +19,7 @@ import workloads as W
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
-INVALID_ARG, OOM, BAD_MOVE, STATE = 1, 3, 6, 8
+INVALID_ARG, OOM, BAD_MOVE, TIMEOUT, STATE = 1, 3, 6, 7, 8
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -100,4 +103,35 @@ def test_allocation_cap_gives_out_of_memory():
         del os.environ["MM_ALLOC_CAP_BYTES"]
     m = mm.Model.from_problem(p)  # without the cap the same model is created and works
     m.schedule_set(p.x0)
+    m.npv()
+
+
+def test_bulk_copy_wait_runs_out_and_the_model_stays_usable(monkeypatch):
+    """With MM_TEST_STALL_BULK_WAIT set at model creation every stage of the
+    bulk-copy evaluator expects 16 bytes that no copy delivers, so its bounded
+    wait (about 1 ms in this mode) runs out; the warp then waits, bounded
+    again, for the copies it issued (they all land) and leaves.  The next
+    synchronising call reports MM_ERR_TIMEOUT once; the same model then
+    evaluates the batch with direct loads, matching the FP64 oracle."""
+    import oracle as O
+    from helpers import assert_close_floor
+    mm = _mm()
+    p = W.config("plain_4k", n_moves=1024)
+    monkeypatch.setenv("MM_TEST_STALL_BULK_WAIT", "1")
+    m = mm.Model.from_problem(p)
+    monkeypatch.delenv("MM_TEST_STALL_BULK_WAIT")
+    m.schedule_set(p.x0)
+    mv = torch.as_tensor(p.moves, device="cuda")
+    m.set_tile(stages=2)  # the bulk-copy evaluator
+    m.eval_moves(mv, want_mean=False)
+    with pytest.raises(mm.MMError) as e:
+        m.npv()
+    assert e.value.status == TIMEOUT
+    m.npv()  # reported once, then cleared
+    m.set_tile(stages=0)  # direct loads: no bulk copies, no waits
+    s, f, _ = m.eval_moves(mv, want_mean=False)
+    torch.cuda.synchronize()
+    ref = O.OracleModel(p).eval_incremental(p.x0, p.moves)
+    assert np.array_equal(f.cpu().numpy(), ref["flag"])
+    assert_close_floor(s.cpu().numpy(), ref["score"], ref["floor"], what="scores after the timeout")
     m.npv()

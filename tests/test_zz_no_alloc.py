@@ -1,11 +1,14 @@
 """The caller-free top-k (mm_topk_noalloc) against the model-owned one (mm_topk).
 
 mm_topk_noalloc exists for callers that cannot allocate device memory (code
-running under CUDA stream capture, fixed memory pools, loops that must not let
+held to a fixed memory budget or pool, loops that must not let
 cudaMalloc/cudaFree block the device); its scratch is a fixed array inside the
 library.  Both entry points are called through the C ABI on the same inputs, two
-calls in a row, and must agree exactly (indices bit for bit, scores equal).
-This file is collected last so that a failure here never hides another test.
+calls in a row, and must agree exactly (indices bit for bit, scores equal); the
+Python wrapper is checked on the largest batch the array takes with every
+score tied (all keys in one histogram bin: the array's whole key region in
+use) and on an empty batch.  This file is collected last so that a failure here
+never hides another test.
 """
 
 import ctypes
@@ -70,3 +73,34 @@ def test_noalloc_topk_rejects_oversized_batch():
     big = (1 << 20) + 1
     st = L.mm_topk_noalloc(None, None, big, 4, None, None, None, None)
     assert st == 1 and b"fixed scratch size" in L.mm_last_error()
+
+
+def test_noalloc_topk_full_size_all_tied_and_empty_through_the_wrapper():
+    mm, L = _abi()
+    p = W.config("plain_4k")
+    m = mm.Model.from_problem(p)
+    m.schedule_set(p.x0)
+    n, k = 1 << 20, 1024
+    score = torch.full((n,), 1.5, dtype=torch.float32, device="cuda")  # every key in one histogram bin
+    feas = torch.ones(n, dtype=torch.uint8, device="cuda")
+    for _ in range(2):
+        idx = torch.full((k,), -7, dtype=torch.int32, device="cuda")
+        top = torch.zeros(k, dtype=torch.float32, device="cuda")
+        cnt = torch.zeros(1, dtype=torch.int32, device="cuda")
+        mm.topk_noalloc(score, feas, k, idx, top, cnt)
+        ri, rt, rc = m.topk(score, feas, k)
+        torch.cuda.synchronize()
+        assert int(cnt.cpu()[0]) == int(rc.cpu()[0]) == k
+        assert np.array_equal(idx.cpu().numpy(), np.arange(k, dtype=np.int32))  # ties: the lower indices
+        assert np.array_equal(idx.cpu().numpy(), ri.cpu().numpy())
+        assert np.array_equal(top.cpu().numpy(), rt.cpu().numpy())
+    empty_s = torch.empty(0, dtype=torch.float32, device="cuda")
+    empty_f = torch.empty(0, dtype=torch.uint8, device="cuda")
+    cnt = torch.full((1,), -7, dtype=torch.int32, device="cuda")
+    mm.topk_noalloc(empty_s, empty_f, 4, torch.empty(4, dtype=torch.int32, device="cuda"),
+                    torch.empty(4, dtype=torch.float32, device="cuda"), cnt)
+    torch.cuda.synchronize()
+    assert int(cnt.cpu()[0]) == 0
+    with pytest.raises(ValueError):  # the wrapper refuses a flag array shorter than the scores
+        mm.topk_noalloc(score, feas[:10], 4, torch.empty(4, dtype=torch.int32, device="cuda"),
+                        torch.empty(4, dtype=torch.float32, device="cuda"), cnt)
