@@ -192,11 +192,13 @@ mm_status mm_set_tile(mm_model *m, int32_t team, int32_t ctas_per_sm, int32_t st
 enum {
     MM_EVAL_PLAIN = 0,     /* FP32 scenario sums, tree reduction */
     MM_EVAL_KAHAN = 1,     /* compensated scenario sums: the mean's sum by Kahan's update per
-                              scenario (error-free TwoSum merges across the lanes of a team), the
-                              variance by the corrected two-pass formula (the sum of squared
-                              deviations minus (sum of deviations)^2 / S, which removes the error
-                              of the rounded mean; the squares need no compensation: they are
-                              non-negative, nothing cancels) */
+                              scenario quad (the quad's four deltas summed first; error-free
+                              TwoSum merges across the lanes of a team), the variance by the
+                              corrected two-pass formula: the sum of squared deviations minus
+                              (sum of deviations)^2 / S, which removes the error of the rounded
+                              mean, with the deviations' sum formed as the compensated total
+                              minus S times the mean (the squares need no compensation: they
+                              are non-negative, nothing cancels) */
     MM_EVAL_GENERIC = 2    /* use the evaluator whose scenario loop is shaped at run time even
                               where a compile-time-shaped one exists (same results; for
                               cross-checking the two) */

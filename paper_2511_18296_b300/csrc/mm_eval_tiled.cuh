@@ -286,12 +286,9 @@ __device__ __forceinline__ void team_eval(const EvalArgs &A, const float *tab, i
         // padding scenarios (s >= S) have zero values and zero ore bits: d = 0 there
 #pragma unroll
         for (int j = 0; j < 4; j++) d[k][j] = live ? x[j] : 0.0f;
-        if (KAHAN) {
-#pragma unroll
-            for (int j = 0; j < 4; j++) kahan_add(sum, csum, d[k][j]);
-        } else {
-            sum += (d[k][0] + d[k][2]) + (d[k][1] + d[k][3]);  // the fast form's order
-        }
+        // the fast form's order; the compensated form adds the quad's sum with Kahan's update
+        if (KAHAN) kahan_add(sum, csum, (d[k][0] + d[k][2]) + (d[k][1] + d[k][3]));
+        else sum += (d[k][0] + d[k][2]) + (d[k][1] + d[k][3]);
     }
     if (KAHAN) {
         csum = -csum;  // (sum, csum): the sum is sum + csum
@@ -300,7 +297,7 @@ __device__ __forceinline__ void team_eval(const EvalArgs &A, const float *tab, i
     } else {
         mu = team_sum<TEAM>(sum) * invS;
     }
-    float var = 0.0f, dsum = 0.0f;
+    float var = 0.0f;
 #pragma unroll
     for (int k = 0; k < QMAX; k++) {
         const int q = tl + k * TEAM;
@@ -314,17 +311,14 @@ __device__ __forceinline__ void team_eval(const EvalArgs &A, const float *tab, i
                     if (j >= rem) dv[j] = 0.0f;
             }
 #pragma unroll
-            for (int j = 0; j < 4; j++) {
-                var = fmaf(dv[j], dv[j], var);
-                if (KAHAN) dsum += dv[j];
-            }
+            for (int j = 0; j < 4; j++) var = fmaf(dv[j], dv[j], var);
         }
     }
     var = team_sum<TEAM>(var);
     if (KAHAN) {
-        // corrected two-pass variance: the sum of the deviations from the
-        // rounded mean removes that rounding's bias from the sum of squares
-        const float ds = team_sum<TEAM>(dsum);
+        // corrected two-pass variance: minus (sum of deviations)^2 / S, with
+        // the deviations' sum formed as the compensated total minus S mu
+        const float ds = fmaf(-(float)A.S, mu, sum) + csum;
         var = fmaxf(var - ds * ds * invS, 0.0f);
     }
     sd = sqrtf(var * invS);
@@ -442,24 +436,13 @@ __device__ __forceinline__ void team_eval_fast(const EvalArgs &A, int tl, const 
             f2_unpack(hi, x[2], x[3]);
         }
     };
-    // compensated form: two Kahan accumulators in one register pair (the
-    // even and the odd scenario of each pair), paired instructions
-    uint64_t ks = 0ull, kc = 0ull;  // two +0.0f each
     auto acc = [&](const float (&x)[4]) {
-        if (KAHAN) {
-#pragma unroll
-            for (int h = 0; h < 2; h++) {
-                const uint64_t y = f2_sub(f2_pack(x[2 * h], x[2 * h + 1]), kc);
-                const uint64_t t = f2_add(ks, y);
-                kc = f2_sub(f2_sub(t, ks), y);
-                ks = t;
-            }
-        } else {
-            // (x0 + x2) + (x1 + x3), the first level as one paired add
-            float u, v;
-            f2_unpack(f2_add(f2_pack(x[0], x[1]), f2_pack(x[2], x[3])), u, v);
-            sum += u + v;
-        }
+        // (x0 + x2) + (x1 + x3), the first level as one paired add; the
+        // compensated form then adds the quad's sum with Kahan's update
+        float u, v;
+        f2_unpack(f2_add(f2_pack(x[0], x[1]), f2_pack(x[2], x[3])), u, v);
+        if (KAHAN) kahan_add(sum, csum, u + v);
+        else sum += u + v;
     };
 #pragma unroll
     for (int k = 0; k < KF; k++) {
@@ -473,41 +456,33 @@ __device__ __forceinline__ void team_eval_fast(const EvalArgs &A, int tl, const 
         acc(d[KF]);
     }
     if (KAHAN) {
-        // (s, -c) of each accumulator is a value and its error term: the two
-        // and then the team's are merged by error-free TwoSum
-        float s1, c0, c1;
-        f2_unpack(ks, sum, s1);
-        f2_unpack(kc, c0, c1);
-        csum = -c0;
-        comp_merge(sum, csum, s1, -c1);
+        // (sum, -csum) is a value and its error term: the team's are merged by
+        // error-free TwoSum
+        csum = -csum;
         team_sum_comp<TEAM>(sum, csum);
         mu = (sum + csum) * invS;
     } else {
         mu = team_sum<TEAM>(sum) * invS;
     }
-    // second pass: squared deviations (non-negative terms: nothing cancels);
-    // the compensated form also sums the deviations themselves for the
-    // corrected two-pass variance
-    float var = 0.0f, dsum = 0.0f;
+    // second pass: squared deviations (non-negative terms: nothing cancels)
+    float var = 0.0f;
     const uint64_t mu2 = f2_pack(mu, mu);
     auto vacc = [&](const float (&x)[4]) {
         float dv[4];
         f2_unpack(f2_sub(f2_pack(x[0], x[1]), mu2), dv[0], dv[1]);
         f2_unpack(f2_sub(f2_pack(x[2], x[3]), mu2), dv[2], dv[3]);
 #pragma unroll
-        for (int j = 0; j < 4; j++) {
-            var = fmaf(dv[j], dv[j], var);
-            if (KAHAN) dsum += dv[j];
-        }
+        for (int j = 0; j < 4; j++) var = fmaf(dv[j], dv[j], var);
     };
 #pragma unroll
     for (int k = 0; k < KF; k++) vacc(d[k]);
     if (TAIL && tl < ntail) vacc(d[KF]);
     var = team_sum<TEAM>(var);
     if (KAHAN) {
-        // corrected two-pass variance: the deviations' sum removes the bias
-        // that the rounded mean leaves in the sum of squares
-        const float ds = team_sum<TEAM>(dsum);
+        // corrected two-pass variance: minus (sum of deviations)^2 / S, the
+        // bias the rounded mean leaves in the sum of squares; the deviations'
+        // sum is the compensated total minus S mu (one rounding, by FMA)
+        const float ds = fmaf(-(float)A.S, mu, sum) + csum;
         var = fmaxf(var - ds * ds * invS, 0.0f);
     }
     sd = sqrtf(var * invS);

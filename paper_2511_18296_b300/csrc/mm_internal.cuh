@@ -87,6 +87,12 @@ struct mm_model {
     int32_t *succ_ptr = nullptr, *succ_idx = nullptr;
     int32_t *order = nullptr;    // [B] blocks sorted by period (schedule_set)
     int32_t *porder = nullptr;   // [T+2] offsets of each period in order
+    int4 *accum_chunk = nullptr;     // schedule_set: chunks of one period's blocks, (period, begin, end, 0) in order
+    int32_t *accum_cbase = nullptr;  // [T+1] first chunk of each period
+    int64_t *accum_ore = nullptr;    // [chunks][S] chunk partial ore tonnage
+    double *accum_met = nullptr;     // [chunks][S] chunk partial metal
+    int64_t *accum_mass = nullptr;   // [chunks] chunk mined tonnage
+    int32_t accum_chunk_len = 0, accum_max_chunks = 0;
     int64_t *minedT = nullptr;   // [T+1]
     int64_t *oreT = nullptr;     // [T+1][S]  (row T stays 0)
     double *metal = nullptr;     // [T][S]    grams in situ of ore

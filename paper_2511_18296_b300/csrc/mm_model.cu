@@ -15,6 +15,7 @@
 //   ctab  FP32 [T+1][T+1][S_pad] Pout[a] + Pin[b]: the penalty change of moving one
 //         block of ore from period a to period b (kept while T <= kCtabMaxT)
 //                               in period t, scenario s (uniform block mass)
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdlib>
@@ -123,52 +124,76 @@ __global__ void k_base_arcs(int32_t B, const uint32_t *__restrict__ blk, uint32_
     if (blk_lo(w) > blk_period(w)) atomicOr(bad, 1u);
 }
 
-// Per-period sums in a fixed order (blocks of period t sorted by id):
-// minedT[t], oreT[t][s], metal[t][s].  Grid (T, ceil(S/32)); block of 32 x 8:
-// lanes over scenarios, 8 slices over the period's blocks, combined in slice order.
-__global__ void k_accum(const int32_t *__restrict__ order, const int32_t *__restrict__ porder,
-                        const uint32_t *__restrict__ mass, const float *__restrict__ val, int32_t R, int32_t ore_off,
-                        const double *__restrict__ grade, int32_t S, int32_t T,
-                        int64_t *__restrict__ minedT, int64_t *__restrict__ oreT, double *__restrict__ metal) {
-    int t = blockIdx.x;
-    int s = blockIdx.y * 32 + threadIdx.x;
-    int slice = threadIdx.y;
-    int32_t beg = porder[t], end = porder[t + 1];
-    __shared__ int64_t s_ore[8][32];
-    __shared__ double s_met[8][32];
-    __shared__ int64_t s_mass[8][32];
-    int64_t o = 0, mt = 0;
-    double g = 0.0;
-    for (int32_t k = beg + slice; k < end; k += 8) {
-        int32_t b = order[k];
-        uint32_t mb = mass[b];
-        if (blockIdx.y == 0 && threadIdx.x == 0) mt += mb;  // one lane per slice counts mass
-        if (s < S && ore_bit(val, R, ore_off, b, s)) {
-            o += mb;
-            g = __dadd_rn(g, __dmul_rn((double)mb, grade[(int64_t)b * S + s]));
+// Per-period sums in a fixed order (blocks of period t sorted by id), in two
+// levels.  k_accum_part: one CTA per chunk of up to accum_chunk_len
+// consecutive blocks of one period (chunk table built on the host); thread s
+// sums scenario s over the chunk's blocks, eight blocks' loads in flight at a
+// time: ore tonnage (integer), metal m_b * g[b][s] of ore blocks (FP64, block
+// order) and, in thread 0, the mined tonnage.  k_accum_reduce: thread s of
+// period t adds the period's chunk partials in chunk order.  Deterministic:
+// the same schedule always gives the same bits.
+__global__ void __launch_bounds__(128) k_accum_part(const int4 *__restrict__ chunk, const int32_t *__restrict__ order,
+                                                    const uint32_t *__restrict__ mass, const float *__restrict__ val,
+                                                    int32_t R, int32_t ore_off, const double *__restrict__ grade,
+                                                    int32_t S, int64_t *__restrict__ p_ore, double *__restrict__ p_met,
+                                                    int64_t *__restrict__ p_mass) {
+    const int4 c = chunk[blockIdx.x];  // (period, begin, end, 0)
+    for (int s = threadIdx.x; s < S; s += blockDim.x) {
+        int64_t o = 0;
+        double g = 0.0;
+        for (int32_t k0 = c.y; k0 < c.z; k0 += 8) {
+            int32_t b[8];
+            uint32_t mb[8], ob[8];
+            double gb[8];
+#pragma unroll
+            for (int u = 0; u < 8; u++) b[u] = k0 + u < c.z ? __ldg(order + k0 + u) : -1;
+#pragma unroll
+            for (int u = 0; u < 8; u++) {
+                mb[u] = ob[u] = 0u;
+                gb[u] = 0.0;
+                if (b[u] >= 0) {
+                    mb[u] = __ldg(mass + b[u]);
+                    ob[u] = ore_bit(val, R, ore_off, b[u], s);
+                    gb[u] = __ldg(grade + (int64_t)b[u] * S + s);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 8; u++)
+                if (ob[u]) {
+                    o += mb[u];
+                    g = __dadd_rn(g, __dmul_rn((double)mb[u], gb[u]));
+                }
         }
+        p_ore[(int64_t)blockIdx.x * S + s] = o;
+        p_met[(int64_t)blockIdx.x * S + s] = g;
     }
-    s_ore[slice][threadIdx.x] = o;
-    s_met[slice][threadIdx.x] = g;
-    s_mass[slice][threadIdx.x] = mt;
-    __syncthreads();
-    if (slice == 0) {
-        int64_t oo = 0;
-        double gg = 0.0;
-        for (int k = 0; k < 8; k++) {
-            oo += s_ore[k][threadIdx.x];
-            gg = __dadd_rn(gg, s_met[k][threadIdx.x]);
+    if (threadIdx.x == 0) {
+        int64_t mt = 0;
+        for (int32_t k = c.y; k < c.z; k++) mt += __ldg(mass + __ldg(order + k));
+        p_mass[blockIdx.x] = mt;
+    }
+}
+
+__global__ void k_accum_reduce(const int32_t *__restrict__ cbase, const int64_t *__restrict__ p_ore,
+                               const double *__restrict__ p_met, const int64_t *__restrict__ p_mass, int32_t S,
+                               int64_t *__restrict__ minedT, int64_t *__restrict__ oreT, double *__restrict__ metal) {
+    const int t = blockIdx.x;
+    const int s = blockIdx.y * blockDim.x + threadIdx.x;
+    const int32_t c0 = cbase[t], c1 = cbase[t + 1];
+    if (s < S) {
+        int64_t o = 0;
+        double g = 0.0;
+        for (int32_t c = c0; c < c1; c++) {
+            o += p_ore[(int64_t)c * S + s];
+            g = __dadd_rn(g, p_met[(int64_t)c * S + s]);
         }
-        if (s < S) {
-            oreT[(int64_t)t * S + s] = oo;
-            metal[(int64_t)t * S + s] = gg;
-        }
-        if (blockIdx.y == 0 && threadIdx.x == 0) {
-            int64_t mm_ = 0;
-            for (int k = 0; k < 8; k++)
-                for (int l = 0; l < 32; l++) mm_ += s_mass[k][l];
-            minedT[t] = mm_;
-        }
+        oreT[(int64_t)t * S + s] = o;
+        metal[(int64_t)t * S + s] = g;
+    }
+    if (blockIdx.y == 0 && threadIdx.x == 0) {
+        int64_t mt = 0;
+        for (int32_t c = c0; c < c1; c++) mt += p_mass[c];
+        minedT[t] = mt;
     }
 }
 
@@ -398,6 +423,8 @@ void mm_model_destroy(mm_model *m) {
     cudaFree(m->mass); cudaFree(m->grade); cudaFree(m->val); cudaFree(m->blk);
     cudaFree(m->pred_ptr); cudaFree(m->pred_idx); cudaFree(m->succ_ptr); cudaFree(m->succ_idx);
     cudaFree(m->order); cudaFree(m->porder);
+    cudaFree(m->accum_chunk); cudaFree(m->accum_cbase); cudaFree(m->accum_ore); cudaFree(m->accum_met);
+    cudaFree(m->accum_mass);
     cudaFree(m->minedT); cudaFree(m->oreT); cudaFree(m->metal); cudaFree(m->npv); cudaFree(m->contrib);
     cudaFree(m->tab);
     cudaFree(m->ctab);
@@ -521,6 +548,14 @@ mm_status mm_model_create(const mm_model_desc *d, mm_model **out) {
     ALLOC(blk, B);
     ALLOC(order, B);
     ALLOC(porder, T + 2);
+    // schedule_set's chunked sums: about 1,600 chunks (at least 32 blocks each)
+    m->accum_chunk_len = std::max<int32_t>(32, (B + 1599) / 1600);
+    m->accum_max_chunks = (B + m->accum_chunk_len - 1) / m->accum_chunk_len + T;
+    ALLOC(accum_chunk, m->accum_max_chunks);
+    ALLOC(accum_cbase, T + 1);
+    ALLOC(accum_ore, (size_t)m->accum_max_chunks * S);
+    ALLOC(accum_met, (size_t)m->accum_max_chunks * S);
+    ALLOC(accum_mass, m->accum_max_chunks);
     ALLOC(minedT, T + 1);
     ALLOC(oreT, (int64_t)(T + 1) * S);
     ALLOC(metal, (int64_t)T * S);
@@ -656,6 +691,15 @@ mm_status mm_schedule_set(mm_model *m, const uint8_t *period, int *base_feasible
     for (int t = 0; t <= T; t++) cnt[t + 1] += cnt[t];
     std::vector<int32_t> order(B), fill(cnt.begin(), cnt.end() - 1);
     for (int32_t b = 0; b < B; b++) order[fill[period[b]]++] = b;
+    // chunks of each mined period's blocks (period T, unmined, is not summed)
+    std::vector<int4> chunks;
+    std::vector<int32_t> cbase(T + 1, 0);
+    const int32_t CL = m->accum_chunk_len;
+    for (int t = 0; t < T; t++) {
+        cbase[t] = (int32_t)chunks.size();
+        for (int32_t k = cnt[t]; k < cnt[t + 1]; k += CL) chunks.push_back(make_int4(t, k, std::min(k + CL, cnt[t + 1]), 0));
+    }
+    cbase[T] = (int32_t)chunks.size();
     cudaStream_t s = m->stream;
     uint8_t *d_period = nullptr;
     mm_status st = dalloc(&d_period, B, "allocate period staging");
@@ -681,10 +725,21 @@ mm_status mm_schedule_set(mm_model *m, const uint8_t *period, int *base_feasible
     if ((st = check_launch("k_blk_build")) != MM_OK) return done(st);
     TRY(cudaMemsetAsync(m->oreT, 0, sizeof(int64_t) * (size_t)(T + 1) * S, s), "clear oreT");
     TRY(cudaMemsetAsync(m->minedT, 0, sizeof(int64_t) * (T + 1), s), "clear minedT");
-    dim3 grid(T, (S + 31) / 32), block(32, 8);
-    k_accum<<<grid, block, 0, s>>>(m->order, m->porder, m->mass, m->val, m->R, m->ore_off, m->grade, S, T, m->minedT,
-                                   m->oreT, m->metal);
-    if ((st = check_launch("k_accum")) != MM_OK) return done(st);
+    if (!chunks.empty()) {
+        TRY(cudaMemcpyAsync(m->accum_chunk, chunks.data(), sizeof(int4) * chunks.size(), cudaMemcpyHostToDevice, s),
+            "copy chunk table");
+        TRY(cudaMemcpyAsync(m->accum_cbase, cbase.data(), sizeof(int32_t) * (T + 1), cudaMemcpyHostToDevice, s),
+            "copy chunk offsets");
+        k_accum_part<<<(unsigned)chunks.size(), 128, 0, s>>>(m->accum_chunk, m->order, m->mass, m->val, m->R,
+                                                             m->ore_off, m->grade, S, m->accum_ore, m->accum_met,
+                                                             m->accum_mass);
+        if ((st = check_launch("k_accum_part")) != MM_OK) return done(st);
+        k_accum_reduce<<<dim3(T, (S + 127) / 128), 128, 0, s>>>(m->accum_cbase, m->accum_ore, m->accum_met,
+                                                                m->accum_mass, S, m->minedT, m->oreT, m->metal);
+        if ((st = check_launch("k_accum_reduce")) != MM_OK) return done(st);
+    } else {
+        TRY(cudaMemsetAsync(m->metal, 0, sizeof(double) * (size_t)T * S, s), "clear metal");
+    }
     if ((st = rebuild_tables(m)) != MM_OK) return done(st);
     k_npv<<<(S + 127) / 128, 128, 0, s>>>(S, T, m->disc, m->metal, m->oreT, m->minedT, m->target,
                                            m->price * m->recovery, m->proc_cost, m->mining_cost, m->shortfall_pen,
