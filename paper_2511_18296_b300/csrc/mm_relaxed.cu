@@ -16,17 +16,21 @@
 // compare in FP32 and take identical decisions (FP64 runs at a small fraction
 // of the FP32 rate on this part); otherwise they evaluate the FP64 test.
 //
-// Forward: the two skinny contractions over blocks run on CUDA cores -- each
-// CTA takes a chunk of blocks and a tile of periods, one thread per scenario,
-// FP32 products summed over the chunk -- and the chunk partials are added in
-// FP64 in chunk order (deterministic), one warp per (t, s).  O[t][s] is kept as
-// the checkpoint the adjoint reads, so the backward pass never redoes the
-// contraction.  The smoothed penalty and its derivative evaluate the
-// exponential and logarithm in FP32 on an argument formed in FP64.
+// Forward: the two skinny contractions over blocks run on the tensor cores
+// (m16n8k8 TF32 with each FP32 operand split into hi + lo, FP32-accurate) --
+// each CTA takes a range of blocks and a tile of periods, the grades turned
+// into operands in registers -- and the range partials are added by
+// compensated FP32 in range order (deterministic), then the penalty, NPV_s and
+// J in FP64.  O[t][s] is kept as the checkpoint the adjoint reads, so the
+// backward pass never redoes the contraction.  The smoothed penalty and its
+// derivative evaluate the exponential and logarithm in FP32 on an argument
+// formed in FP64.
 // Adjoint: with w_s = dJ/dNPV_s and c[t][s] = w_s P_t'(O[t][s]),
 //   dJ/dx[b][t] = d_t (sum_s w_s v[b][s] - m_b sum_s c[t][s] ore[b][s]),
-//   dJ/dg[b][s] = w_s ore[b][s] m_b price recovery sum_t d_t x[b][t],
-// one warp per block.
+//   dJ/dg[b][s] = w_s ore[b][s] m_b price recovery sum_t d_t x[b][t];
+// the sum over scenarios against c is again a TF32 product on the tensor
+// cores (ore is exact in TF32).  FP64 runs at a small fraction of the FP32
+// rate on this part, so only sums and differences that need it are FP64.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -78,309 +82,331 @@ __device__ __forceinline__ void relax_ore_value<double>(const double *, const Re
     ore = (__ldg(reinterpret_cast<const uint32_t *>(row + Rw.ore_off) + (s >> 5)) >> (s & 31)) & 1u;
 }
 
-// Forward contraction, staged: CTA (r, z) owns the contiguous range r of the
-// blocks and scenario tile z (up to kFwdSW scenarios) for one tile of TT
-// periods starting at t0 (TT a multiple of 4: the staged x rows are read four
-// periods at a time).  Tiles of kFwdBT blocks -- the grade slices (caller
-// grades) or value slices and ore words (model rows), the x rows and the
-// masses -- are copied into shared memory by cp.async, up to kFwdStages - 1
-// tiles ahead of the one being summed, so every grade is read from memory
-// once and many copies are in flight.  The CTA's kFwdGroups thread groups
-// split each tile's blocks (group k takes blocks k, k + kFwdGroups, ...);
-// thread s of a group sums x[b][t] m_b ore[b][s] and x[b][t] v[b][s] in FP32
-// registers, the groups' sums are added in group order through shared memory
-// and the CTA writes one partial of O and V; the partials are added in FP64 in
-// range order afterwards (deterministic).
-constexpr int kFwdBT = 24;      // blocks per staged tile (three stages stay under 48 KB of static shared memory)
-constexpr int kFwdStages = 3;   // staged tiles (two in flight while one is summed)
 constexpr int kFwdSW = 128;     // scenarios per CTA (at most)
-constexpr int kFwdGroups = 2;   // thread groups splitting a tile's blocks
 #ifndef MM_RELAX_CTAS_PER_SM
 #define MM_RELAX_CTAS_PER_SM 2      // forward CTAs per SM (each writes one partial)
 #endif
 
-__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+// d += a b for one 16 x 8 x 8 TF32 tile with FP32 accumulation, warp-wide:
+// a holds A[gid][tig], A[gid + 8][tig], A[gid][tig + 4], A[gid + 8][tig + 4],
+// b holds B[tig][gid], B[tig + 4][gid], d holds D[gid][2 tig], D[gid][2 tig + 1],
+// D[gid + 8][2 tig], D[gid + 8][2 tig + 1] (gid = lane / 4, tig = lane % 4).
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+    asm("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+        "{%0, %1, %2, %3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// Forward contraction on the tensor cores.  CTA (r, z) owns the contiguous
+// range r of the blocks and scenario tile z (up to kFwdSW scenarios) for one
+// tile of TT periods starting at t0.  Tiles of kTcBT blocks -- the grade
+// slices (caller grades) or value slices and ore words (model rows), the x
+// rows and the masses -- are copied into shared memory by cp.async one tile
+// ahead of the one being summed, so every grade is read from memory once;
+// rows past the end of the range are zero-filled by the copy itself.  With
+// y[b][t] = x[b][t] m_b and, for caller grades,
+//   v'[b][s] = ore ? g c1 - (pc + mc) : -mc    (so v[b][s] = m_b v'[b][s]),
+// warp w of group q (of kTcGroups) owns scenarios 16 (w mod W) .. 16 (w mod
+// W) + 15 and every period of the tile, and takes the K steps (eight blocks)
+// q, q + kTcGroups, ... of each tile as m16n8k8 TF32 products
+//   O[s][t] += sum_b ore[b][s] y[b][t],      V[s][t] += sum_b v'[b][s] y[b][t]
+// (model rows: V[s][t] += sum_b v[b][s] x[b][t]).  Each FP32 operand is split
+// into TF32 hi + lo and hi*hi + hi*lo + lo*hi are accumulated in FP32; ore is
+// 0 or 1, exact in TF32, so O takes two products.  y (and x) are split once
+// per tile into shared memory in fragment order (one 16-byte load gives a
+// lane its hi and lo pieces of one product); the grades become operands in
+// registers, so the loop is shared loads, a compare, an FMA, the split and
+// the MMAs.  The groups' sums are added in group order ((0 + 1) + (2 + 3) for
+// four) through shared memory and group 0 writes the CTA's partial; the
+// partials are added in range order afterwards (deterministic).  TT is a multiple of 8.  Padded rows and columns of a tile
+// only reach rows and columns of the products that are never written out.
+constexpr int kTcBT = 64;  // blocks per staged tile (eight K steps)
+constexpr int kTcStages = 2;
+constexpr int kTcGroups = 2;  // warp groups splitting the K steps of a tile
+
+// Shared-memory layout of the forward (floats).  rw: staged row stride, = 8
+// (mod 32) so the A-fragment loads of a warp hit distinct banks; ow: column of
+// the ore words (model rows).
+struct FwdLayout {
+    int rw, ow;
+    size_t g, x, m, y, xs, floats;
+};
+__host__ __device__ inline FwdLayout fwd_layout(int sw, int TT, bool rows) {
+    const int W = (sw + 15) / 16;  // warps per group
+    FwdLayout L;
+    L.ow = (sw + 3) / 4 * 4;
+    int rw = L.ow + (rows ? 4 : 0);
+    rw += (40 - rw % 32) % 32;
+    L.rw = rw;
+    size_t off = 0;
+    L.g = off; off += (size_t)kTcStages * kTcBT * L.rw;
+    L.x = off; off += (size_t)kTcStages * kTcBT * TT;
+    L.m = off; off += (size_t)kTcStages * kTcBT;
+    L.y = off; off += (size_t)kTcBT * TT * 2;           // (hi, lo) of y in fragment order
+    L.xs = off; off += rows ? (size_t)kTcBT * TT * 2 : 0;  // (hi, lo) of x
+    // the groups' sums meet at the end in two buffers over the whole area
+    L.floats = off > (size_t)2 * W * 32 * TT ? off : (size_t)2 * W * 32 * TT;
+    return L;
+}
+
+// TF32 pieces of an FP32 value without a conversion instruction: hi = x on
+// the TF32 grid (ten explicit mantissa bits; half a TF32 unit added to the
+// magnitude, so ties go away from zero), lo = x - hi, exact in FP32.  The MMA
+// reads lo truncated to TF32, an error below 2^-21 |x| of either sign.
+__device__ __forceinline__ void tf32_split(float x, uint32_t &hi, uint32_t &lo) {
+    hi = (__float_as_uint(x) + 0x1000u) & 0xffffe000u;
+    lo = __float_as_uint(x - __uint_as_float(hi));
+}
+
+__device__ __forceinline__ void cp_async16z(void *dst, const void *src, bool full) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src), "r"(full ? 16 : 0)
                  : "memory");
 }
-__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+__device__ __forceinline__ void cp_async4z(void *dst, const void *src, bool full) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src), "r"(full ? 4 : 0)
                  : "memory");
 }
 
-// Two FP32 values in one 64-bit register pair and the paired FMA of the
-// sm_100 family (each lane rounded exactly like the scalar fmaf).
-__device__ __forceinline__ uint64_t rx_pack(float lo, float hi) {
-    uint64_t r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-    return r;
-}
-__device__ __forceinline__ void rx_unpack(uint64_t v, float &lo, float &hi) {
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
-}
-__device__ __forceinline__ uint64_t rx_fma2(uint64_t a, uint64_t b, uint64_t c) {
-    uint64_t d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-    return d;
-}
+// n / d for the small n of the copy loops: for d >= 2, m = floor((2^32 - 1) / d)
+// + 1 = (2^32 + e) / d with 0 <= e < d fits 32 bits, and the high word of n m
+// is n / d + n e / (d 2^32), exact whenever n d < 2^32; m = 0 marks d = 1.
+__host__ __device__ inline uint32_t fdiv_magic(uint32_t d) { return d > 1u ? 0xffffffffu / d + 1u : 0u; }
+__device__ __forceinline__ uint32_t fdiv(uint32_t n, uint32_t magic) { return magic ? __umulhi(n, magic) : n; }
 
-template <typename G, int TT>
-__global__ void __launch_bounds__(kFwdSW * kFwdGroups) k_relax_fwd(const float *__restrict__ x, const G *__restrict__ g,
-                                                      RelaxRows Rw, const uint32_t *__restrict__ mass, int32_t B,
-                                                      int32_t S, int32_t T, int32_t t0, RelaxEcon E, int32_t vec,
-                                                      int32_t xvec, float *__restrict__ part_o,
-                                                      float *__restrict__ part_v) {
-    constexpr bool ROWS = sizeof(G) == sizeof(double);          // model rows: values, then ore words
-    constexpr int RW = kFwdSW + (ROWS ? 4 : 0);                  // staged floats per block
-    __shared__ __align__(16) float s_g[kFwdStages][kFwdBT][RW];
-    __shared__ __align__(16) float s_x[kFwdStages][kFwdBT][TT];
-    __shared__ uint32_t s_m[kFwdStages][kFwdBT];
+template <typename G, int TT, bool THR>
+__global__ void __launch_bounds__(kFwdSW / 16 * 32 * kTcGroups, MM_RELAX_CTAS_PER_SM) k_relax_fwd_tc(const float *__restrict__ x, const G *__restrict__ g,
+                                                                 RelaxRows Rw, const uint32_t *__restrict__ mass,
+                                                                 int32_t B, int32_t S, int32_t T, int32_t t0,
+                                                                 RelaxEcon E, int32_t vec, int32_t xvec,
+                                                                 float *__restrict__ part_o, float *__restrict__ part_v) {
+    constexpr bool ROWS = sizeof(G) == sizeof(double);  // model rows: values, then ore words
+    static_assert(TT % 8 == 0 && kTcBT % 16 == 0, "MMA tiles");
+    // the finishing launch may start now: it waits for this grid's results
+    // (griddepcontrol.wait) before it reads any partial
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    extern __shared__ __align__(16) float sm_tc[];
     const int r = blockIdx.x, nr = gridDim.x;
     const int b_lo = (int)((int64_t)r * B / nr), b_hi = (int)((int64_t)(r + 1) * B / nr);
     const int s0 = blockIdx.z * kFwdSW, sw = min(kFwdSW, S - s0);
+    const FwdLayout L = fwd_layout(sw, TT, ROWS);
+    float *s_g = sm_tc + L.g, *s_x = sm_tc + L.x;
+    uint32_t *s_m = reinterpret_cast<uint32_t *>(sm_tc + L.m);
+    const uint4 *s_y = reinterpret_cast<const uint4 *>(sm_tc + L.y), *s_xs = reinterpret_cast<const uint4 *>(sm_tc + L.xs);
+    uint32_t *s_yw = reinterpret_cast<uint32_t *>(sm_tc + L.y), *s_xw = reinterpret_cast<uint32_t *>(sm_tc + L.xs);
     const int nt = min(TT, T - t0);
-    const int ntiles = (b_hi - b_lo + kFwdBT - 1) / kFwdBT;
+    const int ntiles = (b_hi - b_lo + kTcBT - 1) / kTcBT;
     const int tid = threadIdx.x, nth = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5, nwarps = nth >> 5;
-    // the groups are packed: group k is threads [k gw, (k + 1) gw), gw the
-    // widest scenario tile, so that few lanes idle when S is not a multiple of
-    // 32 (threads from kFwdGroups gw on only copy)
-    const int gw = min(S, kFwdSW);
-    const int grp = tid / gw, lt = tid - grp * gw;   // group, scenario lane
+    const int W = nwarps / kTcGroups;                 // warps per group: one per 16 scenarios
+    const int grp = warp / W, m0 = (warp - grp * W) * 16;
+    const int gid = lane >> 2, tig = lane & 3;
+    // copy chunks per staged row: grade / value chunks of four scenarios (or
+    // single scenarios), the ore-word chunk; x chunks of four periods (or one)
+    const int gcs = ROWS ? (sw + 3) / 4 + 1 : (vec ? sw / 4 : sw);
+    const int xcs = xvec ? nt / 4 : nt;
+    const uint32_t gmag = fdiv_magic(gcs), xmag = fdiv_magic(xcs);
     auto issue = [&](int k) {
-        const int st = k % kFwdStages, bb0 = b_lo + k * kFwdBT, nb = min(kFwdBT, b_hi - bb0);
-        // one warp per block row, one lane per 16 (or 4) bytes: no divisions
-        if (ROWS) {
-            // value slice [s0, s0 + sw) rounded up to 16 bytes (the row's zero padding
-            // runs to a multiple of 4 floats) and the slice's ore words (one 16-byte copy)
-            const int nv4 = (sw + 3) / 4, per = nv4 + 1;
-            for (int j = warp; j < nb; j += nwarps) {
-                const float *row = Rw.val + (size_t)(bb0 + j) * Rw.R;
-                for (int q = lane; q < per; q += 32) {
-                    if (q < nv4) cp_async16(&s_g[st][j][4 * q], row + s0 + 4 * q);
-                    else cp_async16(&s_g[st][j][kFwdSW], row + Rw.ore_off + s0 / 32);
-                }
-            }
-        } else if (vec) {
-            const int nv4 = sw / 4;  // S % 4 == 0
-            for (int j = warp; j < nb; j += nwarps) {
-                const float *row = reinterpret_cast<const float *>(g) + (size_t)(bb0 + j) * S + s0;
-                for (int q = lane; q < nv4; q += 32) cp_async16(&s_g[st][j][4 * q], row + 4 * q);
-            }
-        } else {
-            for (int j = warp; j < nb; j += nwarps) {
-                const float *row = reinterpret_cast<const float *>(g) + (size_t)(bb0 + j) * S + s0;
-                for (int q = lane; q < sw; q += 32) cp_async4(&s_g[st][j][q], row + q);
+        const int st = k % kTcStages, bb0 = b_lo + k * kTcBT, nb = min(kTcBT, b_hi - bb0);
+        float *sg = s_g + (size_t)st * kTcBT * L.rw;
+        for (int i = tid; i < kTcBT * gcs; i += nth) {
+            const int j = (int)fdiv((uint32_t)i, gmag), q = i - j * gcs;
+            const bool live = j < nb;
+            const size_t b = (size_t)(bb0 + (live ? j : 0));
+            if (ROWS) {
+                const float *row = Rw.val + b * Rw.R;
+                if (q < gcs - 1) cp_async16z(sg + j * L.rw + 4 * q, row + s0 + 4 * q, live);
+                else cp_async16z(sg + j * L.rw + L.ow, row + Rw.ore_off + s0 / 32, live);
+            } else if (vec) {
+                cp_async16z(sg + j * L.rw + 4 * q, reinterpret_cast<const float *>(g) + b * S + s0 + 4 * q, live);
+            } else {
+                cp_async4z(sg + j * L.rw + q, reinterpret_cast<const float *>(g) + b * S + s0 + q, live);
             }
         }
-        if (xvec) {
-            // T % 4 == 0 (so t0, nt and every row start are multiples of 4 floats):
-            // the tile's x rows in 16-byte pieces, nt / 4 per block
-            const int n4 = nt >> 2;
-            for (int i = tid; i < nb * n4; i += nth) {
-                const int j = i / n4, q = i - j * n4;
-                cp_async16(&s_x[st][j][4 * q], x + (size_t)(bb0 + j) * T + t0 + 4 * q);
-            }
-        } else {
-            for (int j = warp; j < nb; j += nwarps)
-                for (int q = lane; q < nt; q += 32) cp_async4(&s_x[st][j][q], x + (size_t)(bb0 + j) * T + t0 + q);
+        float *sx = s_x + (size_t)st * kTcBT * TT;
+        for (int i = tid; i < kTcBT * xcs; i += nth) {
+            const int j = (int)fdiv((uint32_t)i, xmag), q = i - j * xcs;
+            const bool live = j < nb;
+            const float *row = x + (size_t)(bb0 + (live ? j : 0)) * T + t0;
+            if (xvec) cp_async16z(sx + j * TT + 4 * q, row + 4 * q, live);
+            else cp_async4z(sx + j * TT + q, row + q, live);
         }
-        for (int j = tid; j < nb; j += nth) cp_async4(&s_m[st][j], mass + bb0 + j);
+        for (int j = tid; j < kTcBT; j += nth) cp_async4z(&s_m[st * kTcBT + j], mass + bb0 + (j < nb ? j : 0), j < nb);
     };
-    // periods t0 + nt .. t0 + TT - 1 of the x tiles stay zero
-    if (nt < TT)
-        for (int i = tid; i < kFwdStages * kFwdBT * TT; i += nth) (&s_x[0][0][0])[i] = 0.0f;
-    __syncthreads();
-    // always kFwdStages - 1 groups (empty ones past the last tile), so that the
-    // wait below counts the same groups for every range length
-    for (int k = 0; k < kFwdStages - 1; k++) {
-        if (k < ntiles) issue(k);
-        asm volatile("cp.async.commit_group;" ::: "memory");
-    }
-    const bool live = grp < kFwdGroups && lt < sw;
-    const int s = s0 + lt;
-    uint64_t o2[TT / 2], v2[TT / 2];  // period pairs (2q, 2q + 1)
+    issue(0);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    float dO[TT / 8][4], dV[TT / 8][4];
 #pragma unroll
-    for (int j = 0; j < TT / 2; j++) o2[j] = v2[j] = 0ull;
+    for (int n = 0; n < TT / 8; n++)
+#pragma unroll
+        for (int c = 0; c < 4; c++) dO[n][c] = dV[n][c] = 0.0f;
+    const float c1 = E.pf * E.rf, pcm = E.pcf + E.mcf, mcn = -E.mcf;
+    const uint32_t one = __float_as_uint(1.0f);
     for (int k = 0; k < ntiles; k++) {
-        if (k + kFwdStages - 1 < ntiles) issue(k + kFwdStages - 1);
+        if (k + 1 < ntiles) issue(k + 1);
         asm volatile("cp.async.commit_group;" ::: "memory");
-        asm volatile("cp.async.wait_group %0;" ::"n"(kFwdStages - 1) : "memory");  // tile k has landed
+        asm volatile("cp.async.wait_group 1;" ::: "memory");  // tile k has landed
         __syncthreads();
-        const int st = k % kFwdStages, nb = min(kFwdBT, b_hi - (b_lo + k * kFwdBT));
-        if (live) {
-            // the next block's grade (or value and ore word) and mass are read
-            // from shared memory before the current block's products
-            int j = grp;
-            float g_n = 0.0f;
-            uint32_t w_n = 0u, m_n = 0u;
-            if (j < nb) {
-                g_n = s_g[st][j][lt];
-                if (ROWS) w_n = __float_as_uint(s_g[st][j][kFwdSW + (lt >> 5)]);
-                m_n = s_m[st][j];
-            }
-#pragma unroll 4
-            for (; j < nb; j += kFwdGroups) {
-                const float gv = g_n, m = (float)m_n;
-                const uint32_t ow = w_n;
-                const int jn = j + kFwdGroups;
-                if (jn < nb) {
-                    g_n = s_g[st][jn][lt];
-                    if (ROWS) w_n = __float_as_uint(s_g[st][jn][kFwdSW + (lt >> 5)]);
-                    m_n = s_m[st][jn];
-                }
-                float val;
-                bool ore;
+        const int st = k % kTcStages, nb = min(kTcBT, b_hi - (b_lo + k * kTcBT));
+        const float *sg = s_g + (size_t)st * kTcBT * L.rw;
+        // the tile's y = x m (and, for model rows, x) split into TF32 pieces in
+        // fragment order: 16-byte word ((q TT + t) 4 + i) holds, for K step q
+        // and period t, hi and lo of blocks 8q + i and 8q + i + 4 (consecutive
+        // threads write consecutive words); zero-filled rows give y = 0
+        {
+            const float *sx = s_x + (size_t)st * kTcBT * TT;
+            const uint32_t *sm = s_m + st * kTcBT;
+            uint4 *y4 = reinterpret_cast<uint4 *>(s_yw), *x4 = reinterpret_cast<uint4 *>(s_xw);
+            for (int u = tid; u < (kTcBT / 8) * TT * 4; u += nth) {
+                const int i = u & 3, qt = u >> 2, q = qt / TT, t = qt - q * TT;
+                const int j0 = 8 * q + i, j1 = j0 + 4;
+                const float x0 = sx[j0 * TT + t], x1 = sx[j1 * TT + t];
+                uint4 o;
+                tf32_split(x0 * (float)sm[j0], o.x, o.z);
+                tf32_split(x1 * (float)sm[j1], o.y, o.w);
+                y4[u] = o;
                 if (ROWS) {
-                    val = gv;
-                    ore = (ow >> (lt & 31)) & 1u;
-                } else {
-                    ore = relax_ore(gv, E);
-                    const float mc = m * E.mcf;
-                    val = ore ? m * ((gv * E.pf) * E.rf - E.pcf) - mc : -mc;
-                }
-                const float mo = ore ? m : 0.0f;
-                const uint64_t mo2 = rx_pack(mo, mo), val2 = rx_pack(val, val);
-                const float4 *xr = reinterpret_cast<const float4 *>(s_x[st][j]);
-#pragma unroll
-                for (int q = 0; q < TT / 4; q++) {
-                    const float4 x4 = xr[q];
-                    const uint64_t xa = rx_pack(x4.x, x4.y), xb = rx_pack(x4.z, x4.w);
-                    o2[2 * q] = rx_fma2(xa, mo2, o2[2 * q]);
-                    o2[2 * q + 1] = rx_fma2(xb, mo2, o2[2 * q + 1]);
-                    v2[2 * q] = rx_fma2(xa, val2, v2[2 * q]);
-                    v2[2 * q + 1] = rx_fma2(xb, val2, v2[2 * q + 1]);
+                    tf32_split(x0, o.x, o.z);
+                    tf32_split(x1, o.y, o.w);
+                    x4[u] = o;
                 }
             }
         }
-        __syncthreads();  // stage k % kFwdStages is refilled next
-    }
-    float o[TT], v[TT];
+        __syncthreads();
+        if (m0 < sw) {
 #pragma unroll
-    for (int j = 0; j < TT / 2; j++) {
-        rx_unpack(o2[j], o[2 * j], o[2 * j + 1]);
-        rx_unpack(v2[j], v[2 * j], v[2 * j + 1]);
+            for (int hh = 0; hh < kTcBT / (8 * kTcGroups); hh++) {
+                const int q = kTcGroups * hh + grp, k8 = 8 * q;  // this group's K step
+                if (k8 >= nb) break;
+                // A: operands of (scenario m0 + gid (+8), block k8 + tig (+4))
+                uint32_t vh[4], vl[4], oa[4];
+#pragma unroll
+                for (int a = 0; a < 4; a++) {
+                    const int mm = m0 + gid + ((a & 1) ? 8 : 0);
+                    const float *rowp = sg + (k8 + tig + ((a & 2) ? 4 : 0)) * L.rw;
+                    const float gv = rowp[mm];
+                    bool ore;
+                    float val;
+                    if (ROWS) {
+                        val = gv;
+                        ore = (__float_as_uint(rowp[L.ow + (mm >> 5)]) >> (mm & 31)) & 1u;
+                    } else {
+                        ore = THR ? gv >= E.g_thr : relax_ore(gv, E);
+                        val = ore ? fmaf(gv, c1, -pcm) : mcn;
+                    }
+                    tf32_split(val, vh[a], vl[a]);
+                    oa[a] = ore ? one : 0u;
+                }
+                const uint4 *yb = s_y + (q * TT + gid) * 4 + tig;
+                const uint4 *xb = s_xs + (q * TT + gid) * 4 + tig;
+#pragma unroll
+                for (int n = 0; n < TT / 8; n++) {
+                    // B: y (x) of (block k8 + tig (+4), period 8n + gid)
+                    const uint4 yv = yb[32 * n];
+                    const uint32_t yh[2] = {yv.x, yv.y}, yl[2] = {yv.z, yv.w};
+                    if (ROWS) {
+                        const uint4 xv = xb[32 * n];
+                        const uint32_t xh[2] = {xv.x, xv.y}, xl[2] = {xv.z, xv.w};
+                        mma_tf32(dV[n], vh, xh);
+                        mma_tf32(dV[n], vh, xl);
+                        mma_tf32(dV[n], vl, xh);
+                    } else {
+                        mma_tf32(dV[n], vh, yh);
+                        mma_tf32(dV[n], vh, yl);
+                        mma_tf32(dV[n], vl, yh);
+                    }
+                    mma_tf32(dO[n], oa, yh);
+                    mma_tf32(dO[n], oa, yl);
+                }
+            }
+        }
+        __syncthreads();  // stage k % kTcStages and the split tiles are refilled next
     }
-    // groups 1.. hand their sums to group 0 through the (now idle) grade
-    // stages, which group 0 adds in group order
     asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();
-    float *red = &s_g[0][0][0];  // [kFwdGroups - 1][2][TT][kFwdSW]
-    static_assert((kFwdGroups - 1) * 2 * TT * kFwdSW <= kFwdStages * kFwdBT * RW, "combine space");
-    if (grp > 0 && live) {
+    // the groups' sums added as (0 + 1) + (2 + 3) through two buffers over
+    // the idle shared memory: [2][W][32][TT / 8][8]
+    const int wl = warp - grp * W;
+    float *red = sm_tc;
+    auto put = [&](int buf) {
+        float *my = red + (((size_t)buf * W + wl) * 32 + lane) * (TT / 8) * 8;
 #pragma unroll
-        for (int j = 0; j < TT; j++) {
-            red[(((size_t)(grp - 1) * 2) * TT + j) * kFwdSW + lt] = o[j];
-            red[(((size_t)(grp - 1) * 2 + 1) * TT + j) * kFwdSW + lt] = v[j];
-        }
+        for (int n = 0; n < TT / 8; n++)
+#pragma unroll
+            for (int c = 0; c < 4; c++) {
+                my[n * 8 + c] = dO[n][c];
+                my[n * 8 + 4 + c] = dV[n][c];
+            }
+    };
+    auto add = [&](int buf) {
+        const float *oth = red + (((size_t)buf * W + wl) * 32 + lane) * (TT / 8) * 8;
+#pragma unroll
+        for (int n = 0; n < TT / 8; n++)
+#pragma unroll
+            for (int c = 0; c < 4; c++) {
+                dO[n][c] += oth[n * 8 + c];
+                dV[n][c] += oth[n * 8 + 4 + c];
+            }
+    };
+    if (kTcGroups == 4) {
+        if (grp & 1) put(grp >> 1);
+        __syncthreads();
+        if (!(grp & 1)) add(grp >> 1);
+        __syncthreads();
+        if (grp == 2) put(0);
+    } else {
+        if (grp == 1) put(0);
     }
     __syncthreads();
-    if (grp == 0 && live) {
+    if (grp == 0 && m0 < sw) {
+        add(0);
+        // D[scenario m0 + gid (+8)][period 8n + 2 tig (+1)]; V carries the
+        // factor m_b inside y for caller grades
 #pragma unroll
-        for (int j = 0; j < TT; j++) {
-            float a = o[j], c = v[j];
+        for (int n = 0; n < TT / 8; n++)
 #pragma unroll
-            for (int k = 1; k < kFwdGroups; k++) {
-                a += red[(((size_t)(k - 1) * 2) * TT + j) * kFwdSW + lt];
-                c += red[(((size_t)(k - 1) * 2 + 1) * TT + j) * kFwdSW + lt];
+            for (int c = 0; c < 4; c++) {
+                const int mm = m0 + gid + (c >= 2 ? 8 : 0), j = 8 * n + 2 * tig + (c & 1);
+                if (mm < sw && j < nt) {
+                    part_o[((size_t)r * T + t0 + j) * S + s0 + mm] = dO[n][c];
+                    part_v[((size_t)r * T + t0 + j) * S + s0 + mm] = dV[n][c];
+                }
             }
-            if (j < nt) {
-                part_o[((size_t)r * T + t0 + j) * S + s] = a;
-                part_v[((size_t)r * T + t0 + j) * S + s] = c;
-            }
-        }
     }
+}
+
+template <typename G>
+using FwdFn = void (*)(const float *, const G *, RelaxRows, const uint32_t *, int32_t, int32_t, int32_t, int32_t,
+                       RelaxEcon, int32_t, int32_t, float *, float *);
+
+template <typename G>
+static FwdFn<G> fwd_fn(int tt, bool thr) {
+    if (thr) return tt == 8 ? k_relax_fwd_tc<G, 8, true> : (tt == 16 ? k_relax_fwd_tc<G, 16, true> : k_relax_fwd_tc<G, 24, true>);
+    return tt == 8 ? k_relax_fwd_tc<G, 8, false> : (tt == 16 ? k_relax_fwd_tc<G, 16, false> : k_relax_fwd_tc<G, 24, false>);
 }
 
 template <typename G>
 static mm_status relax_fwd_launch(const float *x, const G *g, RelaxRows Rw, const uint32_t *mass, int32_t B, int32_t S,
                                   int32_t T, RelaxEcon E, float *part_o, float *part_v, int nr, cudaStream_t st) {
     const int zs = (S + kFwdSW - 1) / kFwdSW;
-    const int threads = (kFwdGroups * std::min(S, kFwdSW) + 31) / 32 * 32;
+    const int threads = 32 * kTcGroups * ((std::min(S, kFwdSW) + 15) / 16);  // each group: a warp per 16 scenarios
     const int vec = (S % 4 == 0 && ((uintptr_t)g & 15u) == 0) ? 1 : 0;
     const int xvec = (T % 4 == 0 && ((uintptr_t)x & 15u) == 0) ? 1 : 0;  // period tiles start at multiples of 4
-    static_assert(kRelaxTile % 4 == 0, "period tiles must start at multiples of 4 floats");
+    static_assert(kRelaxTile % 8 == 0, "period tiles must start at multiples of 8 floats");
     for (int tb = 0; tb < T; tb += kRelaxTile) {
-        const int tt = (std::min(kRelaxTile, T - tb) + 3) / 4 * 4;
-        const dim3 grid(nr, 1, zs);
-        switch (tt) {
-            case 4: k_relax_fwd<G, 4><<<grid, threads, 0, st>>>(x, g, Rw, mass, B, S, T, tb, E, vec, xvec, part_o, part_v); break;
-            case 8: k_relax_fwd<G, 8><<<grid, threads, 0, st>>>(x, g, Rw, mass, B, S, T, tb, E, vec, xvec, part_o, part_v); break;
-            case 12: k_relax_fwd<G, 12><<<grid, threads, 0, st>>>(x, g, Rw, mass, B, S, T, tb, E, vec, xvec, part_o, part_v); break;
-            case 16: k_relax_fwd<G, 16><<<grid, threads, 0, st>>>(x, g, Rw, mass, B, S, T, tb, E, vec, xvec, part_o, part_v); break;
-            case 20: k_relax_fwd<G, 20><<<grid, threads, 0, st>>>(x, g, Rw, mass, B, S, T, tb, E, vec, xvec, part_o, part_v); break;
-            default: k_relax_fwd<G, 24><<<grid, threads, 0, st>>>(x, g, Rw, mass, B, S, T, tb, E, vec, xvec, part_o, part_v); break;
-        }
-        mm_status r = check_launch("k_relax_fwd");
+        const int tt = (std::min(kRelaxTile, T - tb) + 7) / 8 * 8;
+        const size_t smem = fwd_layout(std::min(S, kFwdSW), tt, sizeof(G) == sizeof(double)).floats * sizeof(float);
+        const FwdFn<G> fn = fwd_fn<G>(tt, E.use_thr != 0);
+        MM_CUDA_TRY(cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+                    "forward smem");
+        fn<<<dim3((unsigned)nr, 1, (unsigned)zs), threads, smem, st>>>(x, g, Rw, mass, B, S, T, tb, E, vec, xvec,
+                                                                       part_o, part_v);
+        mm_status r = check_launch("k_relax_fwd_tc");
         if (r != MM_OK) return r;
     }
     return MM_OK;
-}
-
-// softplus and its derivative of beta z, the argument formed in FP64 and the
-// transcendental part in FP32 (relative error ~1e-7 of a term far below the
-// NPV and gradient tolerances).
-__device__ __forceinline__ double relax_softplus(double z, const RelaxEcon &E) {
-    const double bz = E.beta * z;
-    const float abz = (float)fabs(bz);
-    return (fmax(bz, 0.0) + (double)log1pf(expf(-abz))) * E.inv_beta;
-}
-__device__ __forceinline__ double relax_sigmoid(double z, double beta) {
-    return (double)(1.0f / (1.0f + expf((float)(-beta * z))));
-}
-
-// FP64 sum over the threads of one CTA (valid in every thread): xor trees
-// inside each warp and then over the warp sums (a fixed order, ten dependent
-// additions rather than one per warp).
-__device__ double relax_block_sum(double x, double *red) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
-    if (lane == 0) red[warp] = x;
-    __syncthreads();
-    if (warp == 0) {
-        double t = lane < nw ? red[lane] : 0.0;
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
-        if (lane == 0) red[32] = t;
-    }
-    __syncthreads();
-    const double r = red[32];
-    __syncthreads();
-    return r;
-}
-
-// (sum of x, sum of x^2) over the threads of one CTA in FP64, the two chains
-// side by side (valid in every thread); the same fixed trees as
-// relax_block_sum.
-__device__ double2 relax_block_sum2(double x, double y, double *red) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        x += __shfl_xor_sync(0xffffffffu, x, off);
-        y += __shfl_xor_sync(0xffffffffu, y, off);
-    }
-    if (lane == 0) {
-        red[warp] = x;
-        red[32 + warp] = y;
-    }
-    __syncthreads();
-    if (warp == 0) {
-        double a = lane < nw ? red[lane] : 0.0, b = lane < nw ? red[32 + lane] : 0.0;
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            a += __shfl_xor_sync(0xffffffffu, a, off);
-            b += __shfl_xor_sync(0xffffffffu, b, off);
-        }
-        if (lane == 0) {
-            red[64] = a;
-            red[65] = b;
-        }
-    }
-    __syncthreads();
-    const double2 r = make_double2(red[64], red[65]);
-    __syncthreads();
-    return r;
 }
 
 // Neumaier-compensated FP32 accumulation (s, c) += x, and the merge of two
@@ -395,294 +421,452 @@ __device__ __forceinline__ void relax_merge(float &s, float &c, float s2, float 
     c += c2;
 }
 
-// End of the forward pass, one launch:
-//   1. O[t][s] and V[t][s] from the range partials: a CTA of 32 warps per 32
-//      consecutive (t, s) (coalesced), warp w adding ranges w, w + 32, ... by
-//      compensated FP32 sums, the 32 warp sums merged by a fixed pairwise
-//      tree (deterministic; the error is about one FP32 rounding of the
-//      total, with no FP64 work on the long sums);
-//   2. the FP64 checkpoint O[t][s] and term[t][s] = d_t (V - P_t(O));
-//   3. the last CTA to finish (acquire-release ticket) forms
-//      NPV_s = sum_t term[t][s] in period order, the mean and population std
-//      over scenarios and J, and resets the ticket.
-__global__ void __launch_bounds__(1024) k_relax_finish(const float *__restrict__ part_o,
-                                                       const float *__restrict__ part_v, int32_t nr, int32_t S,
-                                                       int32_t T, const double *__restrict__ disc,
-                                                       const uint64_t *__restrict__ target, RelaxEcon E,
-                                                       double *__restrict__ o_out, double *term, uint32_t *tick,
-                                                       double *__restrict__ npv, double *__restrict__ J) {
-    __shared__ float s_sum[2][32][32], s_cmp[2][32][32];  // [O / V][warp][lane]
-    __shared__ double red[66];
-    __shared__ int s_last;
-    const int TS = T * S;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int i = blockIdx.x * 32 + lane;
-    float so = 0.0f, co = 0.0f, sv = 0.0f, cv = 0.0f;
-    if (i < TS) {
-        // eight ranges' partials loaded before any is added
-        for (int c0 = warp; c0 < nr; c0 += 8 * 32) {
-            float a[8], b[8];
+// End of the forward pass, one launch over (32-scenario chunk, period):
+//   1. O[t][s] and V[t][s] for the CTA's 32 scenarios of period t from the
+//      range partials: warp w adds ranges w, w + kFinWarps, ... by compensated
+//      FP32 sums (each load reads 32 consecutive floats of one partial; all of
+//      a lane's loads are in flight together), and warp 0 merges the warp sums
+//      in warp order (deterministic; the error is about one FP32 rounding of
+//      the total, no FP64 on the long sums);
+//   2. the FP64 checkpoint O[t][s] and term[t][s] = d_t (V - P_t(O)), with
+//      (Q_t - O) / m_ref formed in FP64 and the two softplus branches in FP32;
+//   3. the last CTA (release-acquire ticket) forms every NPV_s = sum_t
+//      term[t][s] by fixed pairwise trees over the periods, the (sum, sum of
+//      squares) over scenarios by fixed trees, the mean, the population std
+//      and J, and resets the ticket.
+// Many small CTAs keep the FP64 work (a small fraction of the FP32 rate on
+// this part) spread over the SMs; after the ticket only one round of loads
+// and short FP64 chains remain.
+constexpr int kFinWarps = 16;
+constexpr int kFinBatch = 20;  // partial loads in flight per lane and array
+
+__device__ __forceinline__ float relax_softplus_f(float bz) { return fmaxf(bz, 0.0f) + log1pf(expf(-fabsf(bz))); }
+
+// sum of q[0 .. 31] by a fixed pairwise tree
+__device__ __forceinline__ double relax_tree32(const double (&q)[32]) {
+    double a[16];
 #pragma unroll
-            for (int u = 0; u < 8; u++) {
-                const int c = c0 + 32 * u;
-                a[u] = c < nr ? __ldg(part_o + (size_t)c * TS + i) : 0.0f;
-                b[u] = c < nr ? __ldg(part_v + (size_t)c * TS + i) : 0.0f;
+    for (int u = 0; u < 16; u++) a[u] = q[2 * u] + q[2 * u + 1];
+#pragma unroll
+    for (int w = 8; w > 0; w >>= 1)
+#pragma unroll
+        for (int u = 0; u < w; u++) a[u] = a[2 * u] + a[2 * u + 1];
+    return a[0];
+}
+
+__global__ void __launch_bounds__(32 * kFinWarps, 1) k_relax_finish(const float *__restrict__ part_o,
+                                                                const float *__restrict__ part_v, int32_t nr,
+                                                                int32_t S, int32_t T, const double *__restrict__ disc,
+                                                                const uint64_t *__restrict__ target, RelaxEcon E,
+                                                                double *__restrict__ o_out, double *term,
+                                                                uint32_t *tick, double *__restrict__ npv,
+                                                                double *__restrict__ J) {
+    __shared__ float s_sum[2][kFinWarps][32], s_cmp[2][kFinWarps][32];  // [O / V][warp][lane]
+    __shared__ double s_red[2][kFinWarps];
+    __shared__ int s_last;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int chunk = blockIdx.x, t = blockIdx.y;
+    const int s = 32 * chunk + lane;
+    const size_t TS = (size_t)T * S, col = (size_t)t * S + s;
+    // launched as a programmatic dependent of the forward contraction: wait
+    // until its grid has completed and its partials are visible
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    float so = 0.0f, co = 0.0f, sv = 0.0f, cv = 0.0f;
+    if (s < S) {
+        for (int c0 = warp; c0 < nr; c0 += kFinBatch * kFinWarps) {
+            float a[kFinBatch], b[kFinBatch];
+#pragma unroll
+            for (int u = 0; u < kFinBatch; u++) {
+                const int c = c0 + kFinWarps * u;
+                a[u] = c < nr ? __ldcg(part_o + (size_t)c * TS + col) : 0.0f;
+                b[u] = c < nr ? __ldcg(part_v + (size_t)c * TS + col) : 0.0f;
             }
 #pragma unroll
-            for (int u = 0; u < 8; u++) {
+            for (int u = 0; u < kFinBatch; u++) {
                 relax_neumaier(so, co, a[u]);
                 relax_neumaier(sv, cv, b[u]);
             }
         }
     }
-    s_sum[0][warp][lane] = so; s_cmp[0][warp][lane] = co;
-    s_sum[1][warp][lane] = sv; s_cmp[1][warp][lane] = cv;
+    s_sum[0][warp][lane] = so;
+    s_cmp[0][warp][lane] = co;
+    s_sum[1][warp][lane] = sv;
+    s_cmp[1][warp][lane] = cv;
     __syncthreads();
-#pragma unroll
-    for (int h = 16; h > 0; h >>= 1) {
-        if (warp < h) {
-#pragma unroll
-            for (int q = 0; q < 2; q++) {
-                float a = s_sum[q][warp][lane], b = s_cmp[q][warp][lane];
-                relax_merge(a, b, s_sum[q][warp + h][lane], s_cmp[q][warp + h][lane]);
-                s_sum[q][warp][lane] = a;
-                s_cmp[q][warp][lane] = b;
-            }
+    if (warp == 0) {
+        for (int w = 1; w < kFinWarps; w++) {
+            relax_merge(so, co, s_sum[0][w][lane], s_cmp[0][w][lane]);
+            relax_merge(sv, cv, s_sum[1][w][lane], s_cmp[1][w][lane]);
         }
-        __syncthreads();
-    }
-    if (warp == 0 && i < TS) {
-        const double O = (double)s_sum[0][0][lane] + (double)s_cmp[0][0][lane];
-        const double V = (double)s_sum[1][0][lane] + (double)s_cmp[1][0][lane];
-        o_out[i] = O;
-        const int t = i / S;
-        const double Q = (double)target[t];
-        const double pen = E.a * E.m_ref * relax_softplus((Q - O) * E.inv_mref, E) +
-                           E.e * E.m_ref * relax_softplus((O - Q) * E.inv_mref, E);
-        term[i] = disc[t] * (V - pen);
+        if (s < S) {
+            const double O = (double)so + (double)co, V = (double)sv + (double)cv;
+            o_out[col] = O;
+            const float bz = (float)E.beta * (float)(((double)target[t] - O) * E.inv_mref);
+            const float pen = (float)(E.a * E.m_ref * E.inv_beta) * relax_softplus_f(bz) +
+                              (float)(E.e * E.m_ref * E.inv_beta) * relax_softplus_f(-bz);
+            term[col] = disc[t] * (V - (double)pen);
+        }
+        __threadfence();
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        uint32_t old;
-        asm volatile("atom.add.acq_rel.gpu.u32 %0, [%1], 1;" : "=r"(old) : "l"(tick) : "memory");
-        s_last = old == gridDim.x - 1;
-    }
+    if (threadIdx.x == 0) s_last = atomicAdd(tick, 1u) == gridDim.x * gridDim.y - 1;
     __syncthreads();
     if (!s_last) return;
-    const int s = threadIdx.x;
-    double acc = 0.0;
-    if (s < S) {
-        // periods in batches of eight, loaded together and added by a fixed
-        // pairwise tree, the batch sums in period order (short FP64 chains)
-        for (int t0 = 0; t0 < T; t0 += 8) {
-            double q[8];
+    __threadfence();
+    // the last CTA: NPV_s for every scenario (32 periods at a time, all loads
+    // in flight, each batch by a fixed pairwise tree, the batch sums in period
+    // order), then (sum, sum of squares) by fixed trees over lanes and warps
+    double x1 = 0.0, x2 = 0.0;
+    for (int sc = threadIdx.x; sc < S; sc += blockDim.x) {
+        double acc = 0.0;
+        for (int t0 = 0; t0 < T; t0 += 32) {
+            double q[32];
 #pragma unroll
-            for (int u = 0; u < 8; u++) q[u] = t0 + u < T ? __ldcg(term + (size_t)(t0 + u) * S + s) : 0.0;
-            acc += ((q[0] + q[1]) + (q[2] + q[3])) + ((q[4] + q[5]) + (q[6] + q[7]));
+            for (int u = 0; u < 32; u++) q[u] = t0 + u < T ? __ldcg(term + (size_t)(t0 + u) * S + sc) : 0.0;
+            acc += relax_tree32(q);
         }
-        npv[s] = acc;
+        npv[sc] = acc;
+        x1 += acc;
+        x2 += acc * acc;
     }
-    // mean and population variance in one pass of (sum, sum of squares)
-    const double2 sums = relax_block_sum2(s < S ? acc : 0.0, s < S ? acc * acc : 0.0, red);
-    const double mean = sums.x * E.inv_S;
-    const double var = fmax(sums.y * E.inv_S - mean * mean, 0.0);
-    if (s == 0) {
-        J[0] = mean - E.lambda * sqrt(var);
-        *tick = 0u;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        x1 += __shfl_xor_sync(0xffffffffu, x1, off);
+        x2 += __shfl_xor_sync(0xffffffffu, x2, off);
+    }
+    if (lane == 0) {
+        s_red[0][warp] = x1;
+        s_red[1][warp] = x2;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        double y1 = lane < kFinWarps ? s_red[0][lane] : 0.0, y2 = lane < kFinWarps ? s_red[1][lane] : 0.0;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            y1 += __shfl_xor_sync(0xffffffffu, y1, off);
+            y2 += __shfl_xor_sync(0xffffffffu, y2, off);
+        }
+        if (lane == 0) {
+            const double mean = y1 * E.inv_S;
+            const double var = fmax(y2 * E.inv_S - mean * mean, 0.0);
+            // the std to FP32 accuracy (a relative 1e-7 of lambda std in J)
+            J[0] = mean - E.lambda * (double)sqrtf((float)var);
+            *tick = 0u;  // every CTA has taken its ticket
+        }
     }
 }
 
 // Adjoint coefficients: w_s = gJ (1/S - lambda (NPV_s - mean) / (S std))
 // (the std term dropped where std = 0) and c[t][s] = w_s P_t'(O[t][s]), one
-// thread per (t, s) over many CTAs; every CTA forms mean and std itself.
-__global__ void __launch_bounds__(256) k_relax_coef(const double *__restrict__ npv, const double *__restrict__ o,
+// thread per (t, s) over many CTAs; every CTA forms mean and std itself, in
+// one pass over NPV_s - NPV_0 (sum and sum of squares side by side), with the
+// thread's own inputs loaded before that pass, and 1 / std in FP32.  Only what needs it is FP64
+// (the scenario statistics, w_s and Q_t - O[t][s]); the sigmoids, a and e and
+// the product are FP32 (c is stored in FP32).  The adjoint that reads c and w
+// launches as this grid's programmatic dependent.
+__global__ void __launch_bounds__(128) k_relax_coef(const double *__restrict__ npv, const double *__restrict__ o,
                                                     const uint64_t *__restrict__ target, const double *__restrict__ gJ,
                                                     int32_t S, int32_t T, int32_t Sp, RelaxEcon E,
                                                     float *__restrict__ w_out, float *__restrict__ c_out) {
-    __shared__ double red[33];
-    double part = 0.0;
-    for (int s = threadIdx.x; s < S; s += blockDim.x) part += npv[s];
-    const double mean = relax_block_sum(part, red) * E.inv_S;
-    double pv = 0.0;
-    for (int s = threadIdx.x; s < S; s += blockDim.x) {
-        const double d = npv[s] - mean;
-        pv += d * d;
-    }
-    const double sd = sqrt(relax_block_sum(pv, red) * E.inv_S);
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    __shared__ double red[2][4];
+    __shared__ double s_k[3];
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= T * S) return;
-    const int t = i / S, s = i - t * S;
-    const double g = gJ[0];
-    double w = g * E.inv_S;
-    if (sd > 0.0) w -= g * E.lambda * (npv[s] - mean) * E.inv_S / sd;
+    const bool on = i < T * S;
+    const int t = on ? i / S : 0, s = on ? i - t * S : 0;
+    const double O = on ? o[i] : 0.0, Q = on ? (double)target[t] : 0.0, ns = npv[s], x0 = npv[0];
+    double a1 = 0.0, a2 = 0.0;
+    for (int k = threadIdx.x; k < S; k += blockDim.x) {
+        const double d = npv[k] - x0;
+        a1 += d;
+        a2 += d * d;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        a1 += __shfl_xor_sync(0xffffffffu, a1, off);
+        a2 += __shfl_xor_sync(0xffffffffu, a2, off);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        red[0][warp] = a1;
+        red[1][warp] = a2;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        // one division per CTA: w_s = k0 - k1 ((NPV_s - NPV_0) - dm)
+        const double A1 = (red[0][0] + red[0][1]) + (red[0][2] + red[0][3]);
+        const double A2 = (red[1][0] + red[1][1]) + (red[1][2] + red[1][3]);
+        // 1 / std to FP32 accuracy (w is stored in FP32)
+        const double dm = A1 * E.inv_S, var = fmax(A2 * E.inv_S - dm * dm, 0.0), g = gJ[0];
+        s_k[0] = g * E.inv_S;
+        s_k[1] = var > 0.0 ? g * E.lambda * E.inv_S * (double)rsqrtf((float)var) : 0.0;
+        s_k[2] = dm;
+    }
+    __syncthreads();
+    if (!on) return;
+    const double w = s_k[0] - s_k[1] * ((ns - x0) - s_k[2]);
     if (t == 0) w_out[s] = (float)w;
-    const double O = o[i], Q = (double)target[t];
-    const double dp = -E.a * relax_sigmoid((Q - O) * E.inv_mref, E.beta) + E.e * relax_sigmoid((O - Q) * E.inv_mref, E.beta);
-    c_out[(size_t)t * Sp + s] = (float)(w * dp);
+    const float bz = (float)E.beta * (float)((Q - O) * E.inv_mref);
+    const float dp = -(float)E.a / (1.0f + expf(-bz)) + (float)E.e / (1.0f + expf(bz));
+    c_out[(size_t)t * Sp + s] = (float)w * dp;
+}
+
+// Tiled adjoint on the tensor cores (the fast path).  With the period tile
+// t0 .. t0 + TT - 1 (TT a multiple of 8, at most 32),
+//   A[b][t] = sum_s ore[b][s] c[t][s]
+// is an m16n8k8 TF32 product: ore is 0 or 1 (exact in TF32) and c is split
+// into TF32 hi + lo (two products, FP32-accurate), so the tensor pipe does the
+// B x S x TT contraction and the CUDA cores only turn grades into ore flags.
+// Alongside, each lane sums its share of u_b = sum_s w_s v[b][s] (caller
+// grades: v = m_b v', v' = ore ? g c1 - (pc + mc) : -mc) in FP32, and
+//   dJ/dx[b][t] = d_t (u_b - m_b A[b][t]),
+//   dJ/dg[b][s] = w_s ore[b][s] m_b price recovery sum_t d_t x[b][t]  (t0 == 0).
+// CTA r owns a contiguous range of the blocks, in tiles of kAdjBT whose grade
+// rows (or value rows and ore words), x rows and masses are copied into
+// shared memory by cp.async one tile ahead (rows past the range zero-filled),
+// so each grade is read from memory once; warp w owns the tile's blocks
+// 16 w .. 16 w + 15 across every scenario (no cross-warp sums).  dJ/dg is
+// written row by row, four scenarios per lane, with streaming stores.  The
+// coefficients come from k_relax_coef: this grid issues its first copies and
+// only then waits for that launch (griddepcontrol.wait).
+constexpr int kAdjBT = 64;       // blocks per staged tile
+constexpr int kAdjWarps = kAdjBT / 16;
+constexpr int kAdjStages = 2;
+constexpr int kAdjMaxTT = 32;
+
+struct AdjLayout {
+    int K8, RS, XS;  // scenarios padded to 8; staged row stride (4 mod 8: conflict-free fragment
+                     // loads); staged x row stride (0: not staged)
+    size_t g, x, m, c, w, d, D, floats;
+};
+__host__ __device__ inline AdjLayout adj_layout(int S, int T, int TT, bool rows, bool stage_x) {
+    AdjLayout L;
+    L.K8 = (S + 7) / 8 * 8;
+    const int words = rows ? ((S + 31) / 32 + 3) / 4 * 4 : 0;  // ore words at column K8
+    int rs = L.K8 + words;
+    rs += (12 - rs % 8) % 8;
+    L.RS = rs;
+    L.XS = stage_x ? (T + 3) / 4 * 4 : 0;
+    size_t off = 0;
+    L.g = off; off += (size_t)kAdjStages * kAdjBT * L.RS;
+    L.x = off; off += (size_t)kAdjStages * kAdjBT * L.XS;
+    L.m = off; off += (size_t)kAdjStages * kAdjBT;
+    L.c = off; off += (size_t)2 * L.K8 * TT;  // (hi, lo) of c in fragment order
+    L.w = off; off += L.K8;
+    L.d = off; off += (size_t)(T + 3) / 4 * 4;
+    L.D = off; off += kAdjBT;
+    L.floats = off;
+    return L;
+}
+
+template <typename G, int TT, bool THR>
+__global__ void __launch_bounds__(32 * kAdjWarps, 2) k_relax_adj_tc(const float *__restrict__ x, const G *__restrict__ g,
+                                                               RelaxRows Rw, const uint32_t *__restrict__ mass,
+                                                               const float *__restrict__ w, const float *__restrict__ c,
+                                                               int32_t Sp, const double *__restrict__ disc, int32_t B,
+                                                               int32_t S, int32_t T, int32_t t0, RelaxEcon E,
+                                                               int32_t vec, int32_t xvec, int32_t gvec,
+                                                               float *__restrict__ gx, float *__restrict__ gg) {
+    constexpr bool ROWS = sizeof(G) == sizeof(double);
+    static_assert(TT % 8 == 0 && TT <= kAdjMaxTT, "period tile");
+    extern __shared__ __align__(16) float sm[];
+    const bool want_g = gg != nullptr && t0 == 0;
+    const bool xst = want_g && T <= kAdjMaxTT;  // x rows staged with the tile, else read from memory
+    const AdjLayout L = adj_layout(S, T, TT, ROWS, xst);
+    float *s_g = sm + L.g, *s_x = sm + L.x, *s_w = sm + L.w, *s_d = sm + L.d, *s_D = sm + L.D;
+    uint32_t *s_m = reinterpret_cast<uint32_t *>(sm + L.m);
+    uint4 *s_c = reinterpret_cast<uint4 *>(sm + L.c);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nth = blockDim.x;
+    const int gid = lane >> 2, tig = lane & 3;
+    const int r = blockIdx.x, nr = gridDim.x;
+    const int b_lo = (int)((int64_t)r * B / nr), b_hi = (int)((int64_t)(r + 1) * B / nr);
+    const int ntiles = (b_hi - b_lo + kAdjBT - 1) / kAdjBT;
+    const int nt = min(TT, T - t0);
+    // scenario columns S .. K8 - 1 of the staged rows are never copied (only
+    // K-padding of the products): zero them once
+    if (L.K8 > S)
+        for (int i = tid; i < kAdjStages * kAdjBT * (L.K8 - S); i += nth) {
+            const int row = i / (L.K8 - S);
+            s_g[(size_t)row * L.RS + S + (i - row * (L.K8 - S))] = 0.0f;
+        }
+    // copy chunks per staged row: grade / value chunks of four scenarios (or
+    // single scenarios) and ore-word chunks; x chunks of four periods (or one)
+    const int nv4 = (S + 3) / 4;
+    const int gcs = ROWS ? nv4 + ((S + 31) / 32 + 3) / 4 : (vec ? S / 4 : S);
+    const int xcs = xvec ? T / 4 : T;
+    const uint32_t gmag = fdiv_magic(gcs), xmag = fdiv_magic(xcs);
+    const uint32_t cmag = fdiv_magic(S / 4 > 0 ? S / 4 : 1), smag = fdiv_magic(S);
+    auto issue = [&](int k) {
+        const int st = k % kAdjStages, bb0 = b_lo + k * kAdjBT, nb = min(kAdjBT, b_hi - bb0);
+        float *sg = s_g + (size_t)st * kAdjBT * L.RS;
+        for (int i = tid; i < kAdjBT * gcs; i += nth) {
+            const int j = (int)fdiv((uint32_t)i, gmag), q = i - j * gcs;
+            const bool live = j < nb;
+            const size_t b = (size_t)(bb0 + (live ? j : 0));
+            float *dst = sg + j * L.RS;
+            if (ROWS) {
+                const float *row = Rw.val + b * Rw.R;
+                if (q < nv4) cp_async16z(dst + 4 * q, row + 4 * q, live);
+                else cp_async16z(dst + L.K8 + 4 * (q - nv4), row + Rw.ore_off + 4 * (q - nv4), live);
+            } else if (vec) {
+                cp_async16z(dst + 4 * q, reinterpret_cast<const float *>(g) + b * S + 4 * q, live);
+            } else {
+                cp_async4z(dst + q, reinterpret_cast<const float *>(g) + b * S + q, live);
+            }
+        }
+        if (xst)
+            for (int i = tid; i < kAdjBT * xcs; i += nth) {
+                const int j = (int)fdiv((uint32_t)i, xmag), q = i - j * xcs;
+                const bool live = j < nb;
+                const float *xr = x + (size_t)(bb0 + (live ? j : 0)) * T;
+                float *xd = s_x + ((size_t)st * kAdjBT + j) * L.XS;
+                if (xvec) cp_async16z(xd + 4 * q, xr + 4 * q, live);
+                else cp_async4z(xd + q, xr + q, live);
+            }
+        for (int j = tid; j < kAdjBT; j += nth)
+            cp_async4z(&s_m[st * kAdjBT + j], mass + bb0 + (j < nb ? j : 0), j < nb);
+    };
+    for (int k = 0; k < kAdjStages - 1; k++) {
+        if (k < ntiles) issue(k);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    }
+    // the coefficients are the preceding launch's results
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    for (int i = tid; i < L.K8; i += nth) s_w[i] = i < S ? w[i] : 0.0f;
+    for (int i = tid; i < T; i += nth) s_d[i] = (float)disc[i];
+    // c[t0 + n][s] split into TF32 pieces in fragment order: 16-byte word
+    // ((q TT + n) 4 + i) holds hi and lo of scenarios 8q + i and 8q + i + 4
+    for (int u = tid; u < (L.K8 / 8) * TT * 4; u += nth) {
+        const int i = u & 3, qn = u >> 2, q = qn / TT, n = qn - q * TT;
+        const int sa = 8 * q + i, sb = sa + 4;
+        const bool on = n < nt;
+        const float ca = on && sa < S ? c[(size_t)(t0 + n) * Sp + sa] : 0.0f;
+        const float cb = on && sb < S ? c[(size_t)(t0 + n) * Sp + sb] : 0.0f;
+        uint4 o;
+        tf32_split(ca, o.x, o.z);
+        tf32_split(cb, o.y, o.w);
+        s_c[u] = o;
+    }
+    const float c1 = E.pf * E.rf, pcm = E.pcf + E.mcf, mcn = -E.mcf;
+    const uint32_t one = __float_as_uint(1.0f);
+    for (int k = 0; k < ntiles; k++) {
+        if (k + kAdjStages - 1 < ntiles) issue(k + kAdjStages - 1);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        asm volatile("cp.async.wait_group %0;" ::"n"(kAdjStages - 1) : "memory");  // tile k has landed
+        __syncthreads();
+        const int st = k % kAdjStages, b0 = b_lo + k * kAdjBT, nb = min(kAdjBT, b_hi - b0);
+        const float *sg = s_g + (size_t)st * kAdjBT * L.RS;
+        const uint32_t *sm_m = s_m + st * kAdjBT;
+        if (want_g)
+            for (int j = tid; j < nb; j += nth) {  // m_b c1 D_b, D_b = sum_t d_t x[b][t]
+                float D = 0.0f;
+                if (xst) {
+                    const float *xr = s_x + ((size_t)st * kAdjBT + j) * L.XS;
+                    for (int t = 0; t < T; t++) D = fmaf(s_d[t], xr[t], D);
+                } else {
+                    const float *xr = x + (size_t)(b0 + j) * T;
+                    for (int t = 0; t < T; t++) D = fmaf(s_d[t], __ldg(xr + t), D);
+                }
+                s_D[j] = (float)sm_m[j] * c1 * D;
+            }
+        const int mb = 16 * warp;
+        if (mb < nb) {
+            float acc[TT / 8][4];
+#pragma unroll
+            for (int n = 0; n < TT / 8; n++)
+#pragma unroll
+                for (int q = 0; q < 4; q++) acc[n][q] = 0.0f;
+            float u0 = 0.0f, u1 = 0.0f;  // blocks mb + gid and mb + gid + 8
+            const float *r0 = sg + (size_t)(mb + gid) * L.RS, *r1 = r0 + 8 * L.RS;
+            for (int k8 = 0; k8 < L.K8; k8 += 8) {
+                const int sa = k8 + tig, sb = sa + 4;
+                // A[m][k]: m = gid (+8), k = tig (+4)
+                const float gv[4] = {r0[sa], r1[sa], r0[sb], r1[sb]};
+                const float wa = s_w[sa], wb = s_w[sb];
+                uint32_t a[4];
+                float v[4];
+#pragma unroll
+                for (int e = 0; e < 4; e++) {
+                    bool ore;
+                    if (ROWS) {
+                        const float *rw = (e & 1) ? r1 : r0;
+                        const int s = (e & 2) ? sb : sa;
+                        ore = (__float_as_uint(rw[L.K8 + (s >> 5)]) >> (s & 31)) & 1u;
+                        v[e] = gv[e];
+                    } else {
+                        ore = THR ? gv[e] >= E.g_thr : relax_ore(gv[e], E);
+                        v[e] = ore ? fmaf(gv[e], c1, -pcm) : mcn;
+                    }
+                    a[e] = ore ? one : 0u;
+                }
+                u0 = fmaf(wb, v[2], fmaf(wa, v[0], u0));
+                u1 = fmaf(wb, v[3], fmaf(wa, v[1], u1));
+                const uint4 *cb = s_c + ((k8 >> 3) * TT + gid) * 4 + tig;
+#pragma unroll
+                for (int n = 0; n < TT / 8; n++) {
+                    const uint4 p = cb[32 * n];  // B[k][n]: k = tig (+4), n = gid
+                    const uint32_t bh[2] = {p.x, p.y}, bl[2] = {p.z, p.w};
+                    mma_tf32(acc[n], a, bh);
+                    mma_tf32(acc[n], a, bl);
+                }
+            }
+            u0 += __shfl_xor_sync(0xffffffffu, u0, 1);
+            u0 += __shfl_xor_sync(0xffffffffu, u0, 2);
+            u1 += __shfl_xor_sync(0xffffffffu, u1, 1);
+            u1 += __shfl_xor_sync(0xffffffffu, u1, 2);
+            // D[m][n] at m = gid (+8 for q >= 2), n = 2 tig + (q & 1)
+#pragma unroll
+            for (int n = 0; n < TT / 8; n++)
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    const int j = mb + gid + (q >= 2 ? 8 : 0), t = 8 * n + 2 * tig + (q & 1);
+                    if (j < nb && t < nt) {
+                        const float mj = (float)sm_m[j], uj = q >= 2 ? u1 : u0;
+                        const float val = ROWS ? uj - mj * acc[n][q] : mj * (uj - acc[n][q]);
+                        gx[(size_t)(b0 + j) * T + t0 + t] = s_d[t0 + t] * val;
+                    }
+                }
+        }
+        if (want_g) {
+            __syncthreads();  // s_D
+            // the tile's rows of dJ/dg are one contiguous stretch: consecutive
+            // threads write consecutive 16-byte chunks (streaming stores)
+            float *out = gg + (size_t)b0 * S;
+            if (gvec) {
+                const int cpr = S / 4;
+                for (int i = tid; i < nb * cpr; i += nth) {
+                    const int j = (int)fdiv((uint32_t)i, cmag), q = i - j * cpr;
+                    const float f = s_D[j];
+                    const float *row = sg + (size_t)j * L.RS;
+                    const float4 g4 = *reinterpret_cast<const float4 *>(row + 4 * q);
+                    const float4 w4 = *reinterpret_cast<const float4 *>(s_w + 4 * q);
+                    const float gs[4] = {g4.x, g4.y, g4.z, g4.w}, ws[4] = {w4.x, w4.y, w4.z, w4.w};
+                    float o4[4];
+#pragma unroll
+                    for (int e = 0; e < 4; e++) {
+                        const int sc = 4 * q + e;
+                        const bool ore = ROWS ? ((__float_as_uint(row[L.K8 + (sc >> 5)]) >> (sc & 31)) & 1u)
+                                              : (THR ? gs[e] >= E.g_thr : relax_ore(gs[e], E));
+                        o4[e] = ore ? ws[e] * f : 0.0f;
+                    }
+                    __stcs(reinterpret_cast<float4 *>(out + (size_t)j * S + 4 * q), make_float4(o4[0], o4[1], o4[2], o4[3]));
+                }
+            } else {
+                for (int i = tid; i < nb * S; i += nth) {
+                    const int j = (int)fdiv((uint32_t)i, smag), sc = i - j * S;
+                    const float *row = sg + (size_t)j * L.RS;
+                    const bool ore = ROWS ? ((__float_as_uint(row[L.K8 + (sc >> 5)]) >> (sc & 31)) & 1u)
+                                          : (THR ? row[sc] >= E.g_thr : relax_ore(row[sc], E));
+                    __stcs(out + i, ore ? s_w[sc] * s_D[j] : 0.0f);
+                }
+            }
+        }
+        __syncthreads();  // the stage is refilled next
+    }
 }
 
 // dJ/dx and dJ/dg, one warp per block.  Shared memory: w[S], c[T][Sp] (Sp odd:
 // lane t reads row t without bank conflicts), d[T], the warp's ore bits.
-// Tiled adjoint (the fast path): a tile of kAdjBT blocks at a time, one per
-// lane.  The tile's grades (or values and ore words), x rows and masses go to
-// shared memory by asynchronous 4-byte copies, all in flight at once (reads
-// coalesced along each row); warp w takes scenarios w, w + 8, ... and
-// keeps, per block (lane), u = sum_s w_s v[b][s] and A[t] = sum_s c[t][s]
-// ore[b][s] for the period tile t0 .. t0 + TT - 1 in registers (period pairs,
-// paired FMAs; c is held transposed, [s][TT]); the eight warps' partial sums
-// are added in warp order; then
-//   dJ/dx[b][t] = d_t (u_b - m_b A[t]),
-//   dJ/dg[b][s] = w_s ore[b][s] m_b price recovery sum_t d_t x[b][t]  (t0 == 0),
-// both written coalesced.  Persistent: CTA i takes tiles i, i + grid, ...
-constexpr int kAdjBT = 32;
-constexpr int kAdjWarps = 8;
-
-struct AdjLayout {
-    int Sg, Wo, TT4;  // odd grade row stride, odd ore-word row stride, padded period tile
-    size_t c, w, d, D, acc, g, ow, x, m, floats;
-};
-__host__ __device__ inline AdjLayout adj_layout(int S, int T, int TT, bool rows) {
-    AdjLayout L;
-    L.Sg = S | 1;
-    L.Wo = rows ? (((S + 31) / 32) | 1) : 0;
-    L.TT4 = TT;
-    L.c = 0;                                        // [S][TT]
-    L.w = L.c + (size_t)S * TT;                     // [S]
-    L.d = L.w + S;                                  // [T]
-    L.D = L.d + T;                                  // [kAdjBT]
-    L.acc = L.D + kAdjBT;                           // [kAdjWarps][TT + 1][kAdjBT]
-    L.g = L.acc + (size_t)kAdjWarps * (TT + 1) * kAdjBT;  // [kAdjBT][Sg]
-    L.ow = L.g + (size_t)kAdjBT * L.Sg;             // [kAdjBT][Wo] (u32)
-    L.x = L.ow + (size_t)kAdjBT * L.Wo;             // [kAdjBT * T]
-    L.m = L.x + (size_t)kAdjBT * T;                 // [kAdjBT] (u32 masses)
-    L.floats = L.m + kAdjBT;
-    return L;
-}
-
-template <typename G, int TT>
-__global__ void __launch_bounds__(32 * kAdjWarps) k_relax_adj_tiled(const float *__restrict__ x,
-                                                                     const G *__restrict__ g, RelaxRows Rw,
-                                                                     const uint32_t *__restrict__ mass,
-                                                                     const float *__restrict__ w,
-                                                                     const float *__restrict__ c,
-                                                                     const double *__restrict__ disc, int32_t B,
-                                                                     int32_t S, int32_t T, int32_t Sp, int32_t t0,
-                                                                     RelaxEcon E, float *__restrict__ gx,
-                                                                     float *__restrict__ gg) {
-    constexpr bool ROWS = sizeof(G) == sizeof(double);
-    extern __shared__ __align__(16) float sm[];
-    const AdjLayout L = adj_layout(S, T, TT, ROWS);
-    float *s_c = sm + L.c, *s_w = sm + L.w, *s_d = sm + L.d, *s_D = sm + L.D;
-    float *s_acc = sm + L.acc;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nth = blockDim.x;
-    const int nt = min(TT, T - t0);
-    // per CTA: c transposed to [s][TT] (zero past the period tile), w, d
-    for (int q = nt + warp; q < TT; q += kAdjWarps)
-        for (int sc = lane; sc < S; sc += 32) s_c[(size_t)sc * TT + q] = 0.0f;
-    for (int q = warp; q < nt; q += kAdjWarps)
-        for (int sc = lane; sc < S; sc += 32) cp_async4(&s_c[(size_t)sc * TT + q], c + (size_t)(t0 + q) * Sp + sc);
-    for (int i = tid; i < S; i += nth) cp_async4(&s_w[i], w + i);
-    for (int i = tid; i < T; i += nth) s_d[i] = (float)disc[i];
-    const float prf = E.pf * E.rf;
-    const int ntile = (B + kAdjBT - 1) / kAdjBT;
-    float *s_g = sm + L.g, *s_x = sm + L.x;
-    uint32_t *s_ow = reinterpret_cast<uint32_t *>(sm + L.ow), *s_m = reinterpret_cast<uint32_t *>(sm + L.m);
-    for (int tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
-        const int b0 = tile * kAdjBT, nb = min(kAdjBT, B - b0);
-        // stage the tile: a warp per block row, lanes along the row, every
-        // copy in flight at once (the first tile's join those of c and w)
-        for (int j = warp; j < nb; j += kAdjWarps) {
-            if (ROWS) {
-                const float *row = Rw.val + (size_t)(b0 + j) * Rw.R;
-                for (int sc = lane; sc < S; sc += 32) cp_async4(&s_g[j * L.Sg + sc], row + sc);
-                for (int k = lane; k < (S + 31) / 32; k += 32) cp_async4(&s_ow[j * L.Wo + k], row + Rw.ore_off + k);
-            } else {
-                const float *row = reinterpret_cast<const float *>(g) + (size_t)(b0 + j) * S;
-                for (int sc = lane; sc < S; sc += 32) cp_async4(&s_g[j * L.Sg + sc], row + sc);
-            }
-        }
-        for (int i = tid; i < nb * T; i += nth) cp_async4(&s_x[i], x + (size_t)b0 * T + i);
-        for (int j = tid; j < nb; j += nth) cp_async4(&s_m[j], mass + b0 + j);
-        asm volatile("cp.async.commit_group;" ::: "memory");
-        asm volatile("cp.async.wait_all;" ::: "memory");
-        __syncthreads();
-        const bool have = lane < nb;
-        const float m = have ? (float)s_m[lane] : 0.0f;
-        if (warp == 0 && have) {
-            float D = 0.0f;
-            for (int t = 0; t < T; t++) D = fmaf(s_d[t], s_x[lane * T + t], D);
-            s_D[lane] = D;
-        }
-        // per-warp sums over scenarios warp, warp + 8, ... for block `lane`
-        uint64_t a2[TT / 2];
-#pragma unroll
-        for (int q = 0; q < TT / 2; q++) a2[q] = 0ull;
-        float u = 0.0f;
-        if (have) {
-            const float *grow = s_g + lane * L.Sg;
-            for (int sc = warp; sc < S; sc += kAdjWarps) {
-                const float gv = grow[sc];
-                bool ore;
-                float val;
-                if (ROWS) {
-                    val = gv;
-                    ore = (s_ow[lane * L.Wo + (sc >> 5)] >> (sc & 31)) & 1u;
-                } else {
-                    ore = relax_ore(gv, E);
-                    const float mc = m * E.mcf;
-                    val = ore ? m * ((gv * E.pf) * E.rf - E.pcf) - mc : -mc;
-                }
-                u = fmaf(s_w[sc], val, u);
-                const float of = ore ? 1.0f : 0.0f;
-                const uint64_t of2 = rx_pack(of, of);
-                const float4 *cr = reinterpret_cast<const float4 *>(s_c + (size_t)sc * TT);
-#pragma unroll
-                for (int q = 0; q < TT / 4; q++) {
-                    const float4 c4 = cr[q];
-                    a2[2 * q] = rx_fma2(rx_pack(c4.x, c4.y), of2, a2[2 * q]);
-                    a2[2 * q + 1] = rx_fma2(rx_pack(c4.z, c4.w), of2, a2[2 * q + 1]);
-                }
-            }
-        }
-        // partial sums to shared memory: [warp][TT + 1][lane] (row TT = u)
-        float *my = s_acc + (size_t)warp * (TT + 1) * kAdjBT;
-#pragma unroll
-        for (int q = 0; q < TT / 2; q++) {
-            float lo, hi;
-            rx_unpack(a2[q], lo, hi);
-            my[(2 * q) * kAdjBT + lane] = lo;
-            my[(2 * q + 1) * kAdjBT + lane] = hi;
-        }
-        my[TT * kAdjBT + lane] = u;
-        __syncthreads();
-        // warp-order sums into warp 0's slot
-        for (int i = tid; i < (TT + 1) * kAdjBT; i += nth) {
-            float a = s_acc[i];
-#pragma unroll
-            for (int k = 1; k < kAdjWarps; k++) a += s_acc[(size_t)k * (TT + 1) * kAdjBT + i];
-            s_acc[i] = a;
-        }
-        __syncthreads();
-        // dJ/dx of the period tile and dJ/dg (once, with the first period
-        // tile): a warp per block row, lanes along the row
-        for (int j = warp; j < nb; j += kAdjWarps) {
-            const float mj = (float)s_m[j];
-            for (int q = lane; q < nt; q += 32)
-                gx[(size_t)(b0 + j) * T + t0 + q] = s_d[t0 + q] * (s_acc[TT * kAdjBT + j] - mj * s_acc[q * kAdjBT + j]);
-            if (gg && t0 == 0) {
-                const float f = mj * prf * s_D[j];
-                for (int sc = lane; sc < S; sc += 32) {
-                    bool ore;
-                    if (ROWS) ore = (s_ow[j * L.Wo + (sc >> 5)] >> (sc & 31)) & 1u;
-                    else ore = relax_ore(s_g[j * L.Sg + sc], E);
-                    gg[(size_t)(b0 + j) * S + sc] = ore ? s_w[sc] * f : 0.0f;
-                }
-            }
-        }
-        __syncthreads();  // the tile's shared data and sums are read no more before they are refilled
-    }
-}
-
 template <typename G>
 __global__ void __launch_bounds__(256) k_relax_adjoint(const float *__restrict__ x, const G *__restrict__ g,
                                                        RelaxRows Rw, const uint32_t *__restrict__ mass,
@@ -879,23 +1063,38 @@ mm_status mm_relaxed_forward(mm_model *m, const float *x_dev, const float *g_dev
     if (st != MM_OK) return st;
     if (!J_dev || !npv_dev || !ore_t_dev) return set_error(MM_ERR_INVALID_ARG, "NULL output");
     const int B = m->B, S = m->S, T = m->T;
+    const RelaxEcon E = relax_econ(m, beta, m_ref);
+    const RelaxRows Rw{m->val, m->R, m->ore_off};
     // block ranges: MM_RELAX_CTAS_PER_SM CTAs per SM over the scenario tiles,
     // at least one staged tile each
     const int zs = (S + kFwdSW - 1) / kFwdSW;
-    const int nr = std::max(1, std::min((B + kFwdBT - 1) / kFwdBT, std::max(1, MM_RELAX_CTAS_PER_SM * m->num_sms / zs)));
+    const int nr = std::max(1, std::min((B + kTcBT - 1) / kTcBT, std::max(1, MM_RELAX_CTAS_PER_SM * m->num_sms / zs)));
     const size_t TS = (size_t)T * S;
-    // scratch: range partials of O and V (FP32), then the terms in FP64
+    // scratch: range partials of O and V (FP32), then the terms (FP64)
+    const int nchunk = (S + 31) / 32;
     st = relax_scratch(m, 2 * (size_t)nr * TS + 2 * TS);
     if (st != MM_OK) return st;
     float *part_o = m->relax_scratch, *part_v = part_o + (size_t)nr * TS;
     double *term = reinterpret_cast<double *>(part_v + (size_t)nr * TS);
-    const RelaxEcon E = relax_econ(m, beta, m_ref);
-    const RelaxRows Rw{m->val, m->R, m->ore_off};
     st = g_dev ? relax_fwd_launch<float>(x_dev, g_dev, Rw, m->mass, B, S, T, E, part_o, part_v, nr, m->stream)
                : relax_fwd_launch<double>(x_dev, m->grade, Rw, m->mass, B, S, T, E, part_o, part_v, nr, m->stream);
     if (st != MM_OK) return st;
-    k_relax_finish<<<(unsigned)((TS + 31) / 32), 1024, 0, m->stream>>>(part_o, part_v, nr, S, T, m->disc, m->target, E,
-                                                                       ore_t_dev, term, m->relax_tick, npv_dev, J_dev);
+    // the finish launches as a programmatic dependent of the forward grid, so
+    // its launch overlaps the forward's tail
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)nchunk, (unsigned)T);
+    cfg.blockDim = dim3(32 * kFinWarps);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = m->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    MM_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_relax_finish, (const float *)part_o, (const float *)part_v, (int32_t)nr,
+                                   (int32_t)S, (int32_t)T, (const double *)m->disc, (const uint64_t *)m->target, E,
+                                   ore_t_dev, term, m->relax_tick, npv_dev, J_dev),
+                "k_relax_finish launch");
     return check_launch("k_relax_finish");
 }
 
@@ -907,48 +1106,71 @@ mm_status mm_relaxed_backward(mm_model *m, const float *x_dev, const float *g_de
     if (!npv_dev || !ore_t_dev || !gJ_dev || !gx_dev) return set_error(MM_ERR_INVALID_ARG, "NULL argument");
     const int B = m->B, S = m->S, T = m->T;
     const int Sp = S | 1;  // odd row stride of c
+    const RelaxEcon E = relax_econ(m, beta, m_ref);
+    const RelaxRows Rw{m->val, m->R, m->ore_off};
     st = relax_scratch(m, (size_t)S + (size_t)T * Sp);
     if (st != MM_OK) return st;
     float *w = m->relax_scratch, *c = w + S;
-    const RelaxEcon E = relax_econ(m, beta, m_ref);
-    // small CTAs: each forms the scenario mean and std itself, in FP64, so more
-    // SMs share that work
-    k_relax_coef<<<(unsigned)(((size_t)T * S + 63) / 64), 64, 0, m->stream>>>(npv_dev, ore_t_dev, m->target, gJ_dev, S,
-                                                                               T, Sp, E, w, c);
+    // small CTAs: each forms the scenario mean and std itself, so more SMs
+    // share the FP64 work
+    k_relax_coef<<<(unsigned)(((size_t)T * S + 127) / 128), 128, 0, m->stream>>>(npv_dev, ore_t_dev, m->target,
+                                                                                  gJ_dev, S, T, Sp, E, w, c);
     st = check_launch("k_relax_coef");
     if (st != MM_OK) return st;
-    const RelaxRows Rw{m->val, m->R, m->ore_off};
-    {
-        // the tiled path, period tiles of up to kRelaxTile, when its shared memory fits
-        const bool rows = g_dev == nullptr;
-        size_t need = 0;
-        for (int tb = 0; tb < T; tb += kRelaxTile) {
-            const int tt = (std::min(kRelaxTile, T - tb) + 3) / 4 * 4;
-            need = std::max(need, adj_layout(S, T, tt, rows).floats * sizeof(float));
-        }
-        if (need + 1024 <= (size_t)m->max_smem_optin) {
-            const int tiles = (B + kAdjBT - 1) / kAdjBT;
-            for (int tb = 0; tb < T; tb += kRelaxTile) {
-                const int tt = (std::min(kRelaxTile, T - tb) + 3) / 4 * 4;
-                const size_t sm = adj_layout(S, T, tt, rows).floats * sizeof(float);
-                const void *fn = nullptr;
-                switch (tt) {
-#define MM_ADJ_CASE(V) case V: fn = rows ? (const void *)k_relax_adj_tiled<double, V> : (const void *)k_relax_adj_tiled<float, V>; break;
-                    MM_ADJ_CASE(4) MM_ADJ_CASE(8) MM_ADJ_CASE(12) MM_ADJ_CASE(16) MM_ADJ_CASE(20) default: MM_ADJ_CASE(24)
-#undef MM_ADJ_CASE
-                }
-                MM_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm), "adjoint smem");
-                int per_sm = 1;
-                MM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 32 * kAdjWarps, sm), "occupancy");
-                const int grid = std::max(1, std::min(tiles, std::max(1, per_sm) * m->num_sms));
-                void *args[] = {(void *)&x_dev, rows ? (void *)&m->grade : (void *)&g_dev, (void *)&Rw, (void *)&m->mass,
-                                (void *)&w, (void *)&c, (void *)&m->disc, (void *)&B, (void *)&S, (void *)&T, (void *)&Sp,
-                                (void *)&tb, (void *)&E, (void *)&gx_dev, (void *)&gg_dev};
-                MM_CUDA_TRY(cudaLaunchKernel(fn, dim3(grid), dim3(32 * kAdjWarps), args, sm, m->stream), "adjoint launch");
-            }
-            return check_launch("k_relax_adj_tiled");
-        }
+    const bool rows = g_dev == nullptr;
+    // the tensor-core adjoint, period tiles of up to kAdjMaxTT, when its shared memory fits
+    size_t need = 0;
+    for (int tb = 0; tb < T; tb += kAdjMaxTT) {
+        const int tt = (std::min(kAdjMaxTT, T - tb) + 7) / 8 * 8;
+        need = std::max(need, adj_layout(S, T, tt, rows, gg_dev && tb == 0 && T <= kAdjMaxTT).floats * sizeof(float));
     }
+    if (need + 1024 <= (size_t)m->max_smem_optin) {
+        const int vec = (!rows && S % 4 == 0 && ((uintptr_t)g_dev & 15u) == 0) ? 1 : 0;
+        const int xvec = (T % 4 == 0 && ((uintptr_t)x_dev & 15u) == 0) ? 1 : 0;
+        const int gvec = (gg_dev && S % 4 == 0 && ((uintptr_t)gg_dev & 15u) == 0) ? 1 : 0;
+        const float *gf = rows ? nullptr : g_dev;
+        for (int tb = 0; tb < T; tb += kAdjMaxTT) {
+            const int tt = (std::min(kAdjMaxTT, T - tb) + 7) / 8 * 8;
+            const size_t sm = adj_layout(S, T, tt, rows, gg_dev && tb == 0 && T <= kAdjMaxTT).floats * sizeof(float);
+            const void *fn = nullptr;
+            switch (tt) {
+#define MM_ADJ_FN(V)                                                                                               \
+    rows ? (E.use_thr ? (const void *)k_relax_adj_tc<double, V, true> : (const void *)k_relax_adj_tc<double, V, false>) \
+         : (E.use_thr ? (const void *)k_relax_adj_tc<float, V, true> : (const void *)k_relax_adj_tc<float, V, false>)
+                case 8: fn = MM_ADJ_FN(8); break;
+                case 16: fn = MM_ADJ_FN(16); break;
+                case 24: fn = MM_ADJ_FN(24); break;
+                default: fn = MM_ADJ_FN(32); break;
+#undef MM_ADJ_FN
+            }
+            MM_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm), "adjoint smem");
+            int per_sm = 1;
+            MM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 32 * kAdjWarps, sm), "occupancy");
+            const int grid = std::max(1, std::min((B + 15) / 16, std::max(1, per_sm) * m->num_sms));
+            // a programmatic dependent of the previous launch (the coefficients,
+            // or the previous period tile): its first copies overlap that launch's tail
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3((unsigned)grid);
+            cfg.blockDim = dim3(32 * kAdjWarps);
+            cfg.dynamicSmemBytes = sm;
+            cfg.stream = m->stream;
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+            attr[0].val.programmaticStreamSerializationAllowed = 1;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            const void *gp = rows ? (const void *)m->grade : (const void *)gf;
+            int32_t Sp32 = Sp, tb32 = tb;
+            void *args[] = {(void *)&x_dev, (void *)&gp, (void *)&Rw, (void *)&m->mass, (void *)&w, (void *)&c,
+                            (void *)&Sp32, (void *)&m->disc, (void *)&B, (void *)&S, (void *)&T, (void *)&tb32,
+                            (void *)&E, (void *)&vec, (void *)&xvec, (void *)&gvec, (void *)&gx_dev, (void *)&gg_dev};
+            MM_CUDA_TRY(cudaLaunchKernelExC(&cfg, fn, args), "adjoint launch");
+            st = check_launch("k_relax_adj_tc");
+            if (st != MM_OK) return st;
+        }
+        return MM_OK;
+    }
+    // the one-warp-per-block kernel for rows that do not fit the staged tiles
     const int W = (S + 31) / 32;
     const size_t smem = ((size_t)S + (size_t)T * Sp + 2 * (size_t)T) * sizeof(float) + (size_t)8 * W * sizeof(uint32_t);
     const void *fn = g_dev ? (const void *)k_relax_adjoint<float> : (const void *)k_relax_adjoint<double>;
