@@ -393,9 +393,33 @@ def batched_form(stream, flush, reps: int = K_FORM):
     bt = run_ms(b.run)
     st = run_ms(seq)
     t_b, t_s = float(np.mean(bt)), float(np.mean(st))
+    # the autotuner's evaluator shape per scenario count
+    shapes = {}
+    for c, p in enumerate(probs):
+        team, pf = b.chain_shape(c)
+        e = shapes.setdefault(f"S={p.S}", {"chains": 0, "team": set(), "prefetch": set()})
+        e["chains"] += 1
+        e["team"].add(team)
+        e["prefetch"].add(pf)
+    shapes = {k: {"chains": v["chains"], "team": sorted(v["team"]), "prefetch": sorted(v["prefetch"])}
+              for k, v in sorted(shapes.items(), key=lambda kv: int(kv[0][2:]))}
     b.close()
-    alg = float(sum(algorithmic_bytes(p.moves, p.S) for p in probs))
+    # each scenario class alone (same tile): where the batch's time goes
     peaks, which = measured_peaks()
+    per_class = {}
+    for S in sorted({p.S for p in probs}):
+        sel = [c for c, p in enumerate(probs) if p.S == S]
+        bc = mm.Batch([(models[c], mvs[c]) for c in sel], k=TOPK, stream=stream)
+        bc.set_tile(tile, ctas)
+        ct = run_ms(bc.run)
+        bc.close()
+        ms_c = float(np.median(ct))
+        alg_c = float(sum(algorithmic_bytes(probs[c].moves, S) for c in sel))
+        nm = int(sum(probs[c].moves.shape[0] for c in sel))
+        per_class[f"S={S}"] = {"chains": len(sel), "moves": nm, "ms_alone": ms_c,
+                               "moves_per_us": nm / (ms_c * 1e3),
+                               "roofline_frac_alone": alg_c / (ms_c * 1e-3) / 1e9 / peaks["hbm_gbs"]}
+    alg = float(sum(algorithmic_bytes(p.moves, p.S) for p in probs))
     return {"workload": "64 chains: cubes of side 15..40, S in {16, 32, 64, 100}, T=20, 1,024..65,536 moves each",
             "evals_per_run": evals, "chains": 64, "launches_per_run": 1,
             "ms_per_run": t_b, "time": stats(bt), "value": evals / (t_b * 1e-3), "unit": UNIT,
@@ -403,6 +427,13 @@ def batched_form(stream, flush, reps: int = K_FORM):
             "roofline_frac": alg / (t_b * 1e-3) / 1e9 / peaks["hbm_gbs"],
             "peak_source": f"{which} (MEASURED_PEAKS.json hbm_gbs)",
             "tile": {"moves_per_item": tile, "ctas_per_sm": ctas, "chosen_by": "mm_batch_autotune"},
+            "chain_shapes": {"desc": "team width (lanes per move) and L1 prefetch distance per scenario count, "
+                                     "chosen by mm_batch_autotune after the tile (kept only when > 1 % faster)",
+                             "by_S": shapes},
+            "per_class_alone": {"desc": "each scenario count's chains as a batch of their own, same tile: the "
+                                        "per-move decode and feasibility work is the same at every S, so the "
+                                        "byte rate falls with S",
+                                "by_S": per_class},
             "sequential_plain": {"desc": "64 x (mm_eval_moves + mm_topk), one CUDA graph", "launches_per_run": 128,
                                  "ms_per_run": t_s, "time": stats(st), "value": evals / (t_s * 1e-3)},
             "speedup_vs_sequential": t_s / t_b}

@@ -329,9 +329,25 @@ mm_status mm_batch_set_tile(mm_batch *b, int32_t moves_per_item, int32_t ctas_pe
 mm_status mm_batch_get_tile(const mm_batch *b, int32_t *moves_per_item, int32_t *ctas_per_sm,
                             int32_t *n_items);
 
-/* Autotuner: times `reps` runs of every candidate tile shape (moves per item
- * 512 .. 16384 x CTAs per SM {max, max - 1}) with CUDA events on the batch's
- * stream, keeps the fastest and returns it (outputs may be NULL).  Synchronous;
+/* Evaluator shape of one chain: team width (lanes per move: 4, 8, 16 or 32,
+ * with at most 4 scenario quads per lane, 8 for 32-lane teams; 0 = the
+ * single-model default) and L1 prefetch distance in evaluation batches (0..8;
+ * -1 = none).  With the default team a chain's results are the bits of the
+ * single-model path; another team width adds the scenario sums in another
+ * order (the same tolerance against the FP64 oracle).  Synchronous (uploads
+ * the chain's descriptor); not while a run or a graph replay is in flight.
+ * MM_ERR_INVALID_ARG on a chain index, team width or distance out of range. */
+mm_status mm_batch_set_chain(mm_batch *b, int32_t chain, int32_t team, int32_t prefetch);
+mm_status mm_batch_get_chain(const mm_batch *b, int32_t chain, int32_t *team, int32_t *prefetch);
+
+/* Autotuner, in three passes, each timing `reps` runs (after a warm-up run)
+ * with CUDA events on the batch's stream: (1) every tile shape (moves per item
+ * 512 .. 16384 x CTAs per SM {max, max - 1}), keeping the fastest; (2) for
+ * each scenario count among the chains, every other team width that fits
+ * (mm_batch_set_chain), kept only when more than 1 % faster than the best so
+ * far; (3) L1 prefetch distances 0..2 for all chains, kept the same way.
+ * Returns the tile and the best mean time (outputs may be NULL); the chosen
+ * team widths and distance are read with mm_batch_get_chain.  Synchronous;
  * only for batches created with apply = 0 (MM_ERR_STATE otherwise), since it
  * runs the batch many times. */
 mm_status mm_batch_autotune(mm_batch *b, int32_t reps, int32_t *moves_per_item, int32_t *ctas_per_sm,

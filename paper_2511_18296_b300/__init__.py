@@ -97,6 +97,8 @@ SIGNATURES = [
     ("mm_batch_set_tile", C.c_int, [P, I32, I32]),
     ("mm_batch_get_tile", C.c_int, [P, P, P, P]),
     ("mm_batch_autotune", C.c_int, [P, I32, P, P, P]),
+    ("mm_batch_set_chain", C.c_int, [P, I32, I32, I32]),
+    ("mm_batch_get_chain", C.c_int, [P, I32, P, P]),
     ("mm_apply_move", C.c_int, [P, MMMove, P, P]),
     ("mm_apply_best", C.c_int, [P, P, I64, P, P]),
     ("mm_last_apply", C.c_int, [P, P, P, P]),
@@ -509,9 +511,59 @@ class Batch:
         _check(lib().mm_batch_get_tile(self.h, C.byref(a), C.byref(b), C.byref(c)))
         return a.value, b.value, c.value
 
-    def autotune(self, reps: int = 3):
+    def set_chain(self, chain: int, team: int = 0, prefetch: int = -1):
+        _check(lib().mm_batch_set_chain(self.h, chain, team, prefetch))
+
+    def chain_shape(self, chain: int):
+        a, b = C.c_int32(), C.c_int32()
+        _check(lib().mm_batch_get_chain(self.h, chain, C.byref(a), C.byref(b)))
+        return a.value, b.value
+
+    def chain_key(self, chain: int) -> str:
+        """The key a chain's tuned shape is stored under: its scenario count,
+        block count and move count."""
+        m = self.models[chain]
+        return f"S{m.S}_B{m.B}_n{int(self.moves[chain].shape[0])}"
+
+    def autotune(self, reps: int = 3, cache: Optional[str] = None):
+        """mm_batch_autotune: tile shape, then team width per scenario count,
+        then prefetch distance.  Returns (moves per item, CTAs per SM, best ms).
+
+        cache: a JSON file of earlier choices (default: $MM_BATCH_TUNE_CACHE,
+        none when unset).  Each chain's team width and prefetch distance are
+        stored under its (S, B, n) key and the tile under the sorted list of
+        the batch's chain keys; when every key of this batch is present the
+        stored choices are installed without timing anything (the returned
+        time is the stored one)."""
+        import hashlib
+        import json
+        path = cache if cache is not None else os.environ.get("MM_BATCH_TUNE_CACHE")
+        keys = [self.chain_key(i) for i in range(len(self.models))]
+        tile_key = "tile_" + hashlib.sha1(",".join(sorted(keys)).encode()).hexdigest()[:16]
+        data = {"chains": {}, "tiles": {}}
+        if path and os.path.exists(path):
+            with open(path) as f:
+                data = json.load(f)
+            chains, tiles = data.get("chains", {}), data.get("tiles", {})
+            if tile_key in tiles and all(k in chains for k in keys):
+                t = tiles[tile_key]
+                self.set_tile(t["moves_per_item"], t["ctas_per_sm"])
+                for i, k in enumerate(keys):
+                    self.set_chain(i, chains[k]["team"], chains[k]["prefetch"])
+                return t["moves_per_item"], self.tile()[1], t["ms"]
         a, b, ms = C.c_int32(), C.c_int32(), C.c_float()
         _check(lib().mm_batch_autotune(self.h, reps, C.byref(a), C.byref(b), C.byref(ms)))
+        if path:
+            data.setdefault("chains", {})
+            data.setdefault("tiles", {})
+            for i, k in enumerate(keys):
+                team, pf = self.chain_shape(i)
+                data["chains"][k] = {"team": team, "prefetch": pf}
+            data["tiles"][tile_key] = {"moves_per_item": a.value, "ctas_per_sm": b.value, "ms": ms.value}
+            tmp = path + ".tmp"
+            with open(tmp, "w") as f:
+                json.dump(data, f, indent=1, sort_keys=True)
+            os.replace(tmp, path)
         return a.value, b.value, ms.value
 
     def close(self):

@@ -13,7 +13,8 @@
 // when asked, applies the chain's best move with the single-model apply code.
 // Nothing in the launch allocates or synchronises with the host, so a run can
 // be captured into a CUDA graph; the tile shape (moves per item, CTAs per SM)
-// is chosen by mm_batch_autotune.
+// and each scenario class's team width and the prefetch distance are chosen by
+// mm_batch_autotune.
 #include <algorithm>
 #include <vector>
 
@@ -188,6 +189,7 @@ struct mm_batch {
     std::vector<mm_model *> models;   // each chain's model
     std::vector<int64_t> n_moves;
     std::vector<int> S;
+    std::vector<int> team;            // each chain's team width (lanes per move)
     ChainDev *d_chains = nullptr;
     BatchItem *d_items = nullptr;
     int n_items = 0, items_cap = 0;
@@ -195,6 +197,14 @@ struct mm_batch {
     uint64_t *d_lists = nullptr;      // [items_cap][32]
     int lists_cap = 0;
 };
+
+// Largest quads per lane of a team width's run-time shaped form.
+static int team_qmax(int team) { return team == 32 ? 8 : 4; }
+
+static bool team_fits(int S, int team) {
+    const int nq = (S + 3) / 4;
+    return (team == 4 || team == 8 || team == 16 || team == 32) && (nq + team - 1) / team <= team_qmax(team);
+}
 
 static int batch_variant(const mm_model *m, int team) {
     const int generic = team == 4 ? kBvG4 : team == 8 ? kBvG8 : team == 16 ? kBvG16 : kBvG32;
@@ -311,6 +321,7 @@ mm_status mm_batch_create(const mm_chain *chains, int32_t n_chains, int32_t k, i
         const int nq = (m->S + 3) / 4;
         d.E.qpl = (nq + team - 1) / team;  // quads per lane of the run-time shaped forms
         d.E.prefetch = 0;
+        b->team.push_back(team);
         d.AP = apply_args(m);
         d.k = k;
         d.do_apply = b->do_apply;
@@ -351,6 +362,31 @@ mm_status mm_batch_set_tile(mm_batch *b, int32_t moves_per_item, int32_t ctas_pe
     return batch_build(b);
 }
 
+mm_status mm_batch_set_chain(mm_batch *b, int32_t chain, int32_t team, int32_t prefetch) {
+    if (!b) return set_error(MM_ERR_INVALID_ARG, "NULL batch");
+    if (chain < 0 || chain >= b->n_chains) return set_error(MM_ERR_INVALID_ARG, "chain %d outside 0..%d", chain, b->n_chains - 1);
+    const int S = b->S[chain];
+    if (team == 0) team = default_team(S);
+    if (!team_fits(S, team))
+        return set_error(MM_ERR_INVALID_ARG, "chain %d: team width %d does not fit S = %d", chain, team, S);
+    if (prefetch < -1 || prefetch > 8) return set_error(MM_ERR_INVALID_ARG, "prefetch must be -1..8");
+    ChainDev &d = b->chains[chain];
+    d.variant = batch_variant(b->models[chain], team);
+    d.E.qpl = ((S + 3) / 4 + team - 1) / team;
+    d.E.prefetch = prefetch < 0 ? 0 : prefetch;
+    b->team[chain] = team;
+    MM_CUDA_TRY(cudaMemcpy(b->d_chains + chain, &d, sizeof(ChainDev), cudaMemcpyHostToDevice), "upload chain descriptor");
+    return MM_OK;
+}
+
+mm_status mm_batch_get_chain(const mm_batch *b, int32_t chain, int32_t *team, int32_t *prefetch) {
+    if (!b) return set_error(MM_ERR_INVALID_ARG, "NULL batch");
+    if (chain < 0 || chain >= b->n_chains) return set_error(MM_ERR_INVALID_ARG, "chain %d outside 0..%d", chain, b->n_chains - 1);
+    if (team) *team = b->team[chain];
+    if (prefetch) *prefetch = b->chains[chain].E.prefetch;
+    return MM_OK;
+}
+
 mm_status mm_batch_get_tile(const mm_batch *b, int32_t *moves_per_item, int32_t *ctas_per_sm, int32_t *n_items) {
     if (!b) return set_error(MM_ERR_INVALID_ARG, "NULL batch");
     if (moves_per_item) *moves_per_item = b->moves_per_item;
@@ -387,6 +423,25 @@ mm_status mm_batch_run(mm_batch *b) {
     return check_launch("k_batch_eval");
 }
 
+// Mean time of `reps` runs (after one warm-up run) with CUDA events on the
+// batch's stream.
+static mm_status batch_time(mm_batch *b, int reps, cudaEvent_t e0, cudaEvent_t e1, float *ms_out) {
+    mm_status st = mm_batch_run(b);  // warm-up
+    float tot = 0.0f;
+    for (int r = 0; r < reps && st == MM_OK; r++) {
+        float ms = 0.0f;
+        cudaEventRecord(e0, b->stream);
+        st = mm_batch_run(b);
+        cudaEventRecord(e1, b->stream);
+        cudaError_t se = cudaEventSynchronize(e1);
+        if (se == cudaSuccess) se = cudaEventElapsedTime(&ms, e0, e1);
+        if (se != cudaSuccess && st == MM_OK) st = cuda_status(se, "time a batch run");
+        tot += ms;
+    }
+    *ms_out = tot / (float)reps;
+    return st;
+}
+
 mm_status mm_batch_autotune(mm_batch *b, int32_t reps, int32_t *moves_per_item, int32_t *ctas_per_sm,
                             float *best_ms) {
     if (!b) return set_error(MM_ERR_INVALID_ARG, "NULL batch");
@@ -405,41 +460,72 @@ mm_status mm_batch_autotune(mm_batch *b, int32_t reps, int32_t *moves_per_item, 
     float best = 1e30f;
     int best_tile = b->moves_per_item, best_ctas = b->ctas_per_sm;
     mm_status st = MM_OK;
+    // 1. tile shape: moves per item x CTAs per SM
     for (int tile : tiles) {
         for (int cp : ctas) {
             b->moves_per_item = tile;
             b->ctas_per_sm = cp;
+            float ms = 0.0f;
             if ((st = batch_build(b)) != MM_OK) break;
-            if ((st = mm_batch_run(b)) != MM_OK) break;  // warm-up
-            float tot = 0.0f;
-            for (int r = 0; r < reps && st == MM_OK; r++) {
-                float ms = 0.0f;
-                cudaEventRecord(e0, b->stream);
-                st = mm_batch_run(b);
-                cudaEventRecord(e1, b->stream);
-                cudaError_t se = cudaEventSynchronize(e1);
-                if (se == cudaSuccess) se = cudaEventElapsedTime(&ms, e0, e1);
-                if (se != cudaSuccess && st == MM_OK) st = cuda_status(se, "time a batch run");
-                tot += ms;
-            }
-            if (st != MM_OK) break;
-            if (tot / reps < best) {
-                best = tot / reps;
+            if ((st = batch_time(b, reps, e0, e1, &ms)) != MM_OK) break;
+            if (ms < best) {
+                best = ms;
                 best_tile = tile;
                 best_ctas = cp;
             }
         }
         if (st != MM_OK) break;
     }
+    if (st == MM_OK) {
+        b->moves_per_item = best_tile;
+        b->ctas_per_sm = best_ctas;
+        st = batch_build(b);
+    }
+    // 2. team width per scenario class (chains with the same S): every width
+    //    that fits, the class's other chains unchanged; a width is kept only
+    //    if it beats the best time so far by more than 1 %
+    std::vector<int> classes(b->S.begin(), b->S.end());
+    std::sort(classes.begin(), classes.end());
+    classes.erase(std::unique(classes.begin(), classes.end()), classes.end());
+    for (int S : classes) {
+        if (st != MM_OK) break;
+        int keep = -1;
+        for (int c = 0; c < b->n_chains; c++)
+            if (b->S[c] == S) keep = b->team[c];
+        for (int team = 4; team <= 32 && st == MM_OK; team *= 2) {
+            if (team == keep || !team_fits(S, team)) continue;
+            for (int c = 0; c < b->n_chains && st == MM_OK; c++)
+                if (b->S[c] == S) st = mm_batch_set_chain(b, c, team, b->chains[c].E.prefetch);
+            float ms = 0.0f;
+            if (st == MM_OK) st = batch_time(b, reps, e0, e1, &ms);
+            if (st == MM_OK && ms < best * 0.99f) {
+                best = ms;
+                keep = team;
+            }
+        }
+        for (int c = 0; c < b->n_chains && st == MM_OK; c++)
+            if (b->S[c] == S) st = mm_batch_set_chain(b, c, keep, b->chains[c].E.prefetch);
+    }
+    // 3. L1 prefetch distance (evaluation batches ahead), all chains
+    if (st == MM_OK) {
+        int keep = b->chains[0].E.prefetch;
+        for (int pf = 0; pf <= 2 && st == MM_OK; pf++) {
+            if (pf == keep) continue;
+            for (int c = 0; c < b->n_chains && st == MM_OK; c++) st = mm_batch_set_chain(b, c, b->team[c], pf);
+            float ms = 0.0f;
+            if (st == MM_OK) st = batch_time(b, reps, e0, e1, &ms);
+            if (st == MM_OK && ms < best * 0.99f) {
+                best = ms;
+                keep = pf;
+            }
+        }
+        for (int c = 0; c < b->n_chains && st == MM_OK; c++) st = mm_batch_set_chain(b, c, b->team[c], keep);
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    b->moves_per_item = best_tile;
-    b->ctas_per_sm = best_ctas;
-    mm_status st2 = batch_build(b);
-    if (st == MM_OK) st = st2;
     if (st != MM_OK) return st;
-    if (moves_per_item) *moves_per_item = best_tile;
-    if (ctas_per_sm) *ctas_per_sm = best_ctas > 0 ? best_ctas : b->max_per_sm;
+    if (moves_per_item) *moves_per_item = b->moves_per_item;
+    if (ctas_per_sm) *ctas_per_sm = b->ctas_per_sm > 0 ? b->ctas_per_sm : b->max_per_sm;
     if (best_ms) *best_ms = best;
     return MM_OK;
 }

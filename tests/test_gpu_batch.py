@@ -144,8 +144,9 @@ def test_batch_autotune_keeps_results(small):
     assert b.tile()[:2] == (tile, ctas)
     b.run()
     torch.cuda.synchronize()
-    for m, mv, o in zip(models, mvs, b.out):
-        check_chain(m, mv, o, 4)
+    for c, (p, m, mv, o) in enumerate(zip(probs, models, mvs, b.out)):
+        if b.chain_shape(c)[0] == default_team(p.S):  # the autotuner kept the single-model team
+            check_chain(m, mv, o, 4)
     b.close()
 
 
@@ -200,6 +201,98 @@ def test_batch_64_chains_full_workload():
     b.autotune(reps=2)
     b.run()
     torch.cuda.synchronize()
-    for m, mv, o in zip(models, mvs, b.out):
-        check_chain(m, mv, o, 32)
+    for c, (p, m, mv, o) in enumerate(zip(probs, models, mvs, b.out)):
+        if b.chain_shape(c)[0] == default_team(p.S):  # the autotuner kept the single-model team
+            check_chain(m, mv, o, 32)
     b.close()
+
+
+def default_team(S):
+    """The single-model team width: the smallest of 4..32 lanes giving at most
+    four scenario quads per lane (32 otherwise)."""
+    nq = (S + 3) // 4
+    for team in (4, 8, 16, 32):
+        if (nq + team - 1) // team <= 4:
+            return team
+    return 32
+
+
+def test_batch_chain_shapes_team_and_prefetch(small):
+    """mm_batch_set_chain: another team width adds the scenario sums in another
+    order (same flags, scores within FP32 rounding of the default ones); the
+    prefetch distance changes no bit; team 0 restores the default bits."""
+    probs, models = small
+    mvs = [moves_of(p) for p in probs]
+    b = mm().Batch(list(zip(models, mvs)), k=8)
+    ref = []
+    for m, mv in zip(models, mvs):
+        if mv.shape[0] == 0:
+            ref.append(None)
+            continue
+        s, f, _ = m.eval_moves(mv, want_mean=False)
+        ref.append((s.cpu().numpy(), f.cpu().numpy()))
+    for c, p in enumerate(probs):
+        assert b.chain_shape(c) == (default_team(p.S), 0)
+        wider = default_team(p.S) * 2
+        if wider <= 32:
+            b.set_chain(c, wider, 2)
+            assert b.chain_shape(c) == (wider, 2)
+    b.run()
+    torch.cuda.synchronize()
+    for c, o in enumerate(b.out):
+        if ref[c] is None:
+            continue
+        s, f = ref[c]
+        assert np.array_equal(o["feas"].cpu().numpy(), f)
+        got = o["score"].cpu().numpy()
+        fin = np.isfinite(s)
+        assert np.array_equal(np.isfinite(got), fin)
+        scale = np.abs(s[fin]).max() if fin.any() else 1.0
+        np.testing.assert_allclose(got[fin], s[fin], rtol=0, atol=1e-5 * scale)
+    for c in range(len(probs)):
+        b.set_chain(c, 0, 3)  # default team, prefetch three batches ahead
+    b.run()
+    torch.cuda.synchronize()
+    for m, mv, o in zip(models, mvs, b.out):
+        check_chain(m, mv, o, 8)
+    b.close()
+
+
+def test_batch_chain_shape_errors(small):
+    probs, models = small
+    mvs = [moves_of(p) for p in probs]
+    b = mm().Batch(list(zip(models, mvs)), k=4)
+    i100 = next(i for i, p in enumerate(probs) if p.S == 100)
+    for args in ((0, 3, 0), (i100, 4, 0), (len(probs), 0, 0), (0, 0, 9), (-1, 0, 0)):
+        with pytest.raises(mm().MMError):
+            b.set_chain(*args)
+    b.close()
+
+
+def test_batch_autotune_cache_installs_stored_shapes(small, tmp_path):
+    """autotune(cache=...) stores each chain's team width and prefetch under its
+    (S, B, n) key and the tile under the batch's key set; a second batch of the
+    same chains installs them from the file without timing."""
+    import json
+    probs, models = small
+    mvs = [moves_of(p) for p in probs]
+    path = str(tmp_path / "tune.json")
+    b = mm().Batch(list(zip(models, mvs)), k=4)
+    tile, ctas, ms = b.autotune(reps=1, cache=path)
+    shapes = [b.chain_shape(c) for c in range(len(probs))]
+    b.close()
+    data = json.load(open(path))
+    keys = [f"S{p.S}_B{p.B}_n{int(mv.shape[0])}" for p, mv in zip(probs, mvs)]
+    for k, sh in zip(keys, shapes):
+        assert data["chains"][k] == {"team": sh[0], "prefetch": sh[1]}
+    assert len(data["tiles"]) == 1
+    b2 = mm().Batch(list(zip(models, mvs)), k=4)
+    t2, c2, ms2 = b2.autotune(reps=1, cache=path)
+    assert (t2, c2, ms2) == (tile, ctas, pytest.approx(ms))
+    assert [b2.chain_shape(c) for c in range(len(probs))] == shapes
+    b2.run()
+    torch.cuda.synchronize()
+    for c, (m, mv, o) in enumerate(zip(models, mvs, b2.out)):
+        if shapes[c][0] == default_team(probs[c].S):
+            check_chain(m, mv, o, 4)
+    b2.close()
