@@ -445,7 +445,13 @@ mm_status mm_get_metal(mm_model *m, double *metal_host);
  * mm_relaxed_backward: given the forward's npv_dev and ore_t_dev and the
  * upstream gradient *gJ_dev (FP64, device), writes gx_dev[B][T] = dJ/dx and,
  * if gg_dev is not NULL, gg_dev[B][S] = dJ/dg (FP32, device).  Where every
- * NPV_s is equal the std term contributes no gradient.
+ * NPV_s is equal the std term contributes no gradient.  When npv_dev and
+ * ore_t_dev are the buffers the model's last mm_relaxed_forward wrote, with
+ * the same beta and m_ref, the adjoint reuses the coefficients that forward
+ * left in model-owned memory (P_t'(O) and the scenario weights per unit gJ,
+ * FP32) and launches no coefficient kernel; those buffers must then still hold
+ * what that forward wrote.  Any other buffers: the coefficients are formed
+ * from their contents first.
  * Both are asynchronous on the model's stream; the first call (or a larger
  * model) allocates model-owned scratch.  beta, m_ref > 0 (MM_ERR_INVALID_ARG
  * otherwise). */

@@ -130,6 +130,13 @@ struct mm_model {
     float *relax_scratch = nullptr;  // relaxed objective: range partials and terms / adjoint coefficients
     uint32_t *relax_tick = nullptr;  // relaxed forward: ticket of its finishing launch (zero between launches)
     size_t relax_scratch_floats = 0;
+    // relaxed forward -> adjoint: P_t'(O[t][s]) [T][S] and the scenario weights
+    // w_s / gJ [S] (FP32) the last forward prepared, for the outputs and
+    // smoothing it was called with
+    float *relax_coef = nullptr;
+    size_t relax_coef_floats = 0;
+    const double *rc_npv = nullptr, *rc_ore = nullptr;
+    double rc_beta = 0.0, rc_mref = 0.0;
 };
 
 namespace mm {

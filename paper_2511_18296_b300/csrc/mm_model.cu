@@ -439,6 +439,7 @@ void mm_model_destroy(mm_model *m) {
     cudaFree(m->pending);
     cudaFree(m->tabc);
     cudaFree(m->relax_scratch);
+    cudaFree(m->relax_coef);
     cudaFree(m->relax_tick);
     cudaFree(m->shadow32);
     if (m->apply_res_host) cudaFreeHost(m->apply_res_host);

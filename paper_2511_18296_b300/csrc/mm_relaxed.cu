@@ -434,6 +434,10 @@ __device__ __forceinline__ void relax_merge(float &s, float &c, float s2, float 
 //      term[t][s] by fixed pairwise trees over the periods, the (sum, sum of
 //      squares) over scenarios by fixed trees, the mean, the population std
 //      and J, and resets the ticket.
+// For the adjoint it also leaves P_t'(O[t][s]) (step 2) and the scenario
+// weights per unit upstream gradient, 1/S - lambda (NPV_s - mean) / (S std)
+// (step 3), both FP32, so a backward pass on these outputs needs no
+// coefficient launch.
 // Many small CTAs keep the FP64 work (a small fraction of the FP32 rate on
 // this part) spread over the SMs; after the ticket only one round of loads
 // and short FP64 chains remain.
@@ -460,14 +464,20 @@ __global__ void __launch_bounds__(32 * kFinWarps, 1) k_relax_finish(const float 
                                                                 const uint64_t *__restrict__ target, RelaxEcon E,
                                                                 double *__restrict__ o_out, double *term,
                                                                 uint32_t *tick, double *__restrict__ npv,
-                                                                double *__restrict__ J) {
+                                                                double *__restrict__ J, float *__restrict__ dp_out,
+                                                                float *__restrict__ wt_out) {
     __shared__ float s_sum[2][kFinWarps][32], s_cmp[2][kFinWarps][32];  // [O / V][warp][lane]
     __shared__ double s_red[2][kFinWarps];
+    __shared__ double s_mv[2];
     __shared__ int s_last;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int chunk = blockIdx.x, t = blockIdx.y;
     const int s = 32 * chunk + lane;
     const size_t TS = (size_t)T * S, col = (size_t)t * S + s;
+    // a backward launched next (as this grid's programmatic dependent) may
+    // start staging its grades now; it waits for this grid before it reads
+    // anything this grid writes
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     // launched as a programmatic dependent of the forward contraction: wait
     // until its grid has completed and its partials are visible
     asm volatile("griddepcontrol.wait;" ::: "memory");
@@ -505,6 +515,8 @@ __global__ void __launch_bounds__(32 * kFinWarps, 1) k_relax_finish(const float 
             const float pen = (float)(E.a * E.m_ref * E.inv_beta) * relax_softplus_f(bz) +
                               (float)(E.e * E.m_ref * E.inv_beta) * relax_softplus_f(-bz);
             term[col] = disc[t] * (V - (double)pen);
+            // P_t'(O) for the adjoint: -a sigma(beta (Q - O) / m_ref) + e sigma(beta (O - Q) / m_ref)
+            dp_out[col] = -(float)E.a / (1.0f + expf(-bz)) + (float)E.e / (1.0f + expf(bz));
         }
         __threadfence();
     }
@@ -551,9 +563,15 @@ __global__ void __launch_bounds__(32 * kFinWarps, 1) k_relax_finish(const float 
             const double var = fmax(y2 * E.inv_S - mean * mean, 0.0);
             // the std to FP32 accuracy (a relative 1e-7 of lambda std in J)
             J[0] = mean - E.lambda * (double)sqrtf((float)var);
+            s_mv[0] = mean;
+            s_mv[1] = var > 0.0 ? E.lambda * E.inv_S * (double)rsqrtf((float)var) : 0.0;
             *tick = 0u;  // every CTA has taken its ticket
         }
     }
+    __syncthreads();
+    // the adjoint's scenario weights per unit gJ: 1/S - lambda (NPV_s - mean) / (S std)
+    for (int sc = threadIdx.x; sc < S; sc += blockDim.x)
+        wt_out[sc] = (float)(E.inv_S - s_mv[1] * (npv[sc] - s_mv[0]));
 }
 
 // Adjoint coefficients: w_s = gJ (1/S - lambda (NPV_s - mean) / (S std))
@@ -624,20 +642,23 @@ __global__ void __launch_bounds__(128) k_relax_coef(const double *__restrict__ n
 // CTA r owns a contiguous range of the blocks, in tiles of kAdjBT whose grade
 // rows (or value rows and ore words), x rows and masses are copied into
 // shared memory by cp.async one tile ahead (rows past the range zero-filled),
-// so each grade is read from memory once; warp w owns the tile's blocks
-// 16 w .. 16 w + 15 across every scenario (no cross-warp sums).  dJ/dg is
-// written row by row, four scenarios per lane, with streaming stores.  The
-// coefficients come from k_relax_coef: this grid issues its first copies and
-// only then waits for that launch (griddepcontrol.wait).
+// so each grade is read from memory once; two warps share each 16-block M
+// tile, one taking the even and one the odd K steps (eight scenarios each),
+// and the odd one's sums are added to the even one's in that order through
+// shared memory.  dJ/dg is written as one contiguous stretch per tile, four
+// scenarios per lane, with streaming stores.  The coefficients come from
+// k_relax_coef: this grid issues its first copies and only then waits for
+// that launch (griddepcontrol.wait).
 constexpr int kAdjBT = 64;       // blocks per staged tile
-constexpr int kAdjWarps = kAdjBT / 16;
+constexpr int kAdjKSplit = 2;  // warps sharing a 16-block M tile (halves of the K steps)
+constexpr int kAdjWarps = kAdjBT / 16 * kAdjKSplit;
 constexpr int kAdjStages = 2;
 constexpr int kAdjMaxTT = 32;
 
 struct AdjLayout {
     int K8, RS, XS;  // scenarios padded to 8; staged row stride (4 mod 8: conflict-free fragment
                      // loads); staged x row stride (0: not staged)
-    size_t g, x, m, c, w, d, D, floats;
+    size_t g, x, m, c, w, d, D, x2, floats;
 };
 __host__ __device__ inline AdjLayout adj_layout(int S, int T, int TT, bool rows, bool stage_x) {
     AdjLayout L;
@@ -655,6 +676,7 @@ __host__ __device__ inline AdjLayout adj_layout(int S, int T, int TT, bool rows,
     L.w = off; off += L.K8;
     L.d = off; off += (size_t)(T + 3) / 4 * 4;
     L.D = off; off += kAdjBT;
+    L.x2 = off; off += (size_t)(kAdjBT / 16) * 32 * (TT / 2 + 2);  // the K halves' exchange
     L.floats = off;
     return L;
 }
@@ -663,7 +685,8 @@ template <typename G, int TT, bool THR>
 __global__ void __launch_bounds__(32 * kAdjWarps, 2) k_relax_adj_tc(const float *__restrict__ x, const G *__restrict__ g,
                                                                RelaxRows Rw, const uint32_t *__restrict__ mass,
                                                                const float *__restrict__ w, const float *__restrict__ c,
-                                                               int32_t Sp, const double *__restrict__ disc, int32_t B,
+                                                               int32_t Sp, const double *__restrict__ gJs,
+                                                               const double *__restrict__ disc, int32_t B,
                                                                int32_t S, int32_t T, int32_t t0, RelaxEcon E,
                                                                int32_t vec, int32_t xvec, int32_t gvec,
                                                                float *__restrict__ gx, float *__restrict__ gg) {
@@ -673,7 +696,7 @@ __global__ void __launch_bounds__(32 * kAdjWarps, 2) k_relax_adj_tc(const float 
     const bool want_g = gg != nullptr && t0 == 0;
     const bool xst = want_g && T <= kAdjMaxTT;  // x rows staged with the tile, else read from memory
     const AdjLayout L = adj_layout(S, T, TT, ROWS, xst);
-    float *s_g = sm + L.g, *s_x = sm + L.x, *s_w = sm + L.w, *s_d = sm + L.d, *s_D = sm + L.D;
+    float *s_g = sm + L.g, *s_x = sm + L.x, *s_w = sm + L.w, *s_d = sm + L.d, *s_D = sm + L.D, *s_x2 = sm + L.x2;
     uint32_t *s_m = reinterpret_cast<uint32_t *>(sm + L.m);
     uint4 *s_c = reinterpret_cast<uint4 *>(sm + L.c);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nth = blockDim.x;
@@ -730,9 +753,12 @@ __global__ void __launch_bounds__(32 * kAdjWarps, 2) k_relax_adj_tc(const float 
         if (k < ntiles) issue(k);
         asm volatile("cp.async.commit_group;" ::: "memory");
     }
-    // the coefficients are the preceding launch's results
+    // the coefficients are the preceding launch's results: w_s and c[t][s]
+    // from k_relax_coef, or (gJs set) the forward's weights per unit gJ and
+    // P_t'(O[t][s]), scaled here: w_s = gJ wt_s, c[t][s] = w_s P_t'
     asm volatile("griddepcontrol.wait;" ::: "memory");
-    for (int i = tid; i < L.K8; i += nth) s_w[i] = i < S ? w[i] : 0.0f;
+    const float gsc = gJs ? (float)gJs[0] : 1.0f;
+    for (int i = tid; i < L.K8; i += nth) s_w[i] = i < S ? gsc * w[i] : 0.0f;
     for (int i = tid; i < T; i += nth) s_d[i] = (float)disc[i];
     // c[t0 + n][s] split into TF32 pieces in fragment order: 16-byte word
     // ((q TT + n) 4 + i) holds hi and lo of scenarios 8q + i and 8q + i + 4
@@ -740,8 +766,12 @@ __global__ void __launch_bounds__(32 * kAdjWarps, 2) k_relax_adj_tc(const float 
         const int i = u & 3, qn = u >> 2, q = qn / TT, n = qn - q * TT;
         const int sa = 8 * q + i, sb = sa + 4;
         const bool on = n < nt;
-        const float ca = on && sa < S ? c[(size_t)(t0 + n) * Sp + sa] : 0.0f;
-        const float cb = on && sb < S ? c[(size_t)(t0 + n) * Sp + sb] : 0.0f;
+        float ca = on && sa < S ? c[(size_t)(t0 + n) * Sp + sa] : 0.0f;
+        float cb = on && sb < S ? c[(size_t)(t0 + n) * Sp + sb] : 0.0f;
+        if (gJs) {
+            ca *= sa < S ? gsc * w[sa] : 0.0f;
+            cb *= sb < S ? gsc * w[sb] : 0.0f;
+        }
         uint4 o;
         tf32_split(ca, o.x, o.z);
         tf32_split(cb, o.y, o.w);
@@ -769,16 +799,17 @@ __global__ void __launch_bounds__(32 * kAdjWarps, 2) k_relax_adj_tc(const float 
                 }
                 s_D[j] = (float)sm_m[j] * c1 * D;
             }
-        const int mb = 16 * warp;
+        // warp w: the M tile of blocks 16 (w mod 4) .. + 15, K steps of parity w / 4
+        const int mb = 16 * (warp % (kAdjBT / 16)), kh = warp / (kAdjBT / 16);
+        float acc[TT / 8][4];
+#pragma unroll
+        for (int n = 0; n < TT / 8; n++)
+#pragma unroll
+            for (int q = 0; q < 4; q++) acc[n][q] = 0.0f;
+        float u0 = 0.0f, u1 = 0.0f;  // blocks mb + gid and mb + gid + 8
         if (mb < nb) {
-            float acc[TT / 8][4];
-#pragma unroll
-            for (int n = 0; n < TT / 8; n++)
-#pragma unroll
-                for (int q = 0; q < 4; q++) acc[n][q] = 0.0f;
-            float u0 = 0.0f, u1 = 0.0f;  // blocks mb + gid and mb + gid + 8
             const float *r0 = sg + (size_t)(mb + gid) * L.RS, *r1 = r0 + 8 * L.RS;
-            for (int k8 = 0; k8 < L.K8; k8 += 8) {
+            for (int k8 = 8 * kh; k8 < L.K8; k8 += 8 * kAdjKSplit) {
                 const int sa = k8 + tig, sb = sa + 4;
                 // A[m][k]: m = gid (+8), k = tig (+4)
                 const float gv[4] = {r0[sa], r1[sa], r0[sb], r1[sb]};
@@ -810,6 +841,25 @@ __global__ void __launch_bounds__(32 * kAdjWarps, 2) k_relax_adj_tc(const float 
                     mma_tf32(acc[n], a, bl);
                 }
             }
+        }
+        // the odd-K warps hand their sums to the even-K warp of their M tile
+        float *xch = s_x2 + ((size_t)(warp % (kAdjBT / 16)) * 32 + lane) * (TT / 2 + 2);
+        if (kh == 1) {
+#pragma unroll
+            for (int n = 0; n < TT / 8; n++)
+#pragma unroll
+                for (int q = 0; q < 4; q++) xch[4 * n + q] = acc[n][q];
+            xch[TT / 2] = u0;
+            xch[TT / 2 + 1] = u1;
+        }
+        __syncthreads();
+        if (kh == 0 && mb < nb) {
+#pragma unroll
+            for (int n = 0; n < TT / 8; n++)
+#pragma unroll
+                for (int q = 0; q < 4; q++) acc[n][q] += xch[4 * n + q];
+            u0 += xch[TT / 2];
+            u1 += xch[TT / 2 + 1];
             u0 += __shfl_xor_sync(0xffffffffu, u0, 1);
             u0 += __shfl_xor_sync(0xffffffffu, u0, 2);
             u1 += __shfl_xor_sync(0xffffffffu, u1, 1);
@@ -1070,6 +1120,16 @@ mm_status mm_relaxed_forward(mm_model *m, const float *x_dev, const float *g_dev
     const int zs = (S + kFwdSW - 1) / kFwdSW;
     const int nr = std::max(1, std::min((B + kTcBT - 1) / kTcBT, std::max(1, MM_RELAX_CTAS_PER_SM * m->num_sms / zs)));
     const size_t TS = (size_t)T * S;
+    // the adjoint's coefficients: P_t'(O) [T][S], then w_s / gJ [S]
+    if (m->relax_coef_floats < TS + S) {
+        cudaFree(m->relax_coef);
+        m->relax_coef = nullptr;
+        m->relax_coef_floats = 0;
+        m->rc_npv = m->rc_ore = nullptr;
+        MM_CUDA_TRY(cudaMalloc(&m->relax_coef, (TS + S) * sizeof(float)), "allocate relaxed coefficients");
+        m->relax_coef_floats = TS + S;
+    }
+    m->rc_npv = m->rc_ore = nullptr;  // valid again once the finish is launched
     // scratch: range partials of O and V (FP32), then the terms (FP64)
     const int nchunk = (S + 31) / 32;
     st = relax_scratch(m, 2 * (size_t)nr * TS + 2 * TS);
@@ -1093,8 +1153,13 @@ mm_status mm_relaxed_forward(mm_model *m, const float *x_dev, const float *g_dev
     cfg.numAttrs = 1;
     MM_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_relax_finish, (const float *)part_o, (const float *)part_v, (int32_t)nr,
                                    (int32_t)S, (int32_t)T, (const double *)m->disc, (const uint64_t *)m->target, E,
-                                   ore_t_dev, term, m->relax_tick, npv_dev, J_dev),
+                                   ore_t_dev, term, m->relax_tick, npv_dev, J_dev, m->relax_coef,
+                                   m->relax_coef + TS),
                 "k_relax_finish launch");
+    m->rc_npv = npv_dev;
+    m->rc_ore = ore_t_dev;
+    m->rc_beta = beta;
+    m->rc_mref = m_ref;
     return check_launch("k_relax_finish");
 }
 
@@ -1108,15 +1173,6 @@ mm_status mm_relaxed_backward(mm_model *m, const float *x_dev, const float *g_de
     const int Sp = S | 1;  // odd row stride of c
     const RelaxEcon E = relax_econ(m, beta, m_ref);
     const RelaxRows Rw{m->val, m->R, m->ore_off};
-    st = relax_scratch(m, (size_t)S + (size_t)T * Sp);
-    if (st != MM_OK) return st;
-    float *w = m->relax_scratch, *c = w + S;
-    // small CTAs: each forms the scenario mean and std itself, so more SMs
-    // share the FP64 work
-    k_relax_coef<<<(unsigned)(((size_t)T * S + 127) / 128), 128, 0, m->stream>>>(npv_dev, ore_t_dev, m->target,
-                                                                                  gJ_dev, S, T, Sp, E, w, c);
-    st = check_launch("k_relax_coef");
-    if (st != MM_OK) return st;
     const bool rows = g_dev == nullptr;
     // the tensor-core adjoint, period tiles of up to kAdjMaxTT, when its shared memory fits
     size_t need = 0;
@@ -1124,7 +1180,31 @@ mm_status mm_relaxed_backward(mm_model *m, const float *x_dev, const float *g_de
         const int tt = (std::min(kAdjMaxTT, T - tb) + 7) / 8 * 8;
         need = std::max(need, adj_layout(S, T, tt, rows, gg_dev && tb == 0 && T <= kAdjMaxTT).floats * sizeof(float));
     }
-    if (need + 1024 <= (size_t)m->max_smem_optin) {
+    const bool tc = need + 1024 <= (size_t)m->max_smem_optin;
+    // the last forward's outputs with the same smoothing: its coefficients
+    // are reused (scaled by gJ in the adjoint), no coefficient launch
+    const bool cached = tc && m->relax_coef && npv_dev == m->rc_npv && ore_t_dev == m->rc_ore &&
+                        beta == m->rc_beta && m_ref == m->rc_mref;
+    const float *w = nullptr, *c = nullptr;
+    int cs = Sp;
+    if (cached) {
+        c = m->relax_coef;
+        w = m->relax_coef + (size_t)T * S;
+        cs = S;
+    } else {
+        st = relax_scratch(m, (size_t)S + (size_t)T * Sp);
+        if (st != MM_OK) return st;
+        float *ws = m->relax_scratch, *cw = ws + S;
+        // small CTAs: each forms the scenario mean and std itself, so more SMs
+        // share the FP64 work
+        k_relax_coef<<<(unsigned)(((size_t)T * S + 127) / 128), 128, 0, m->stream>>>(npv_dev, ore_t_dev, m->target,
+                                                                                      gJ_dev, S, T, Sp, E, ws, cw);
+        st = check_launch("k_relax_coef");
+        if (st != MM_OK) return st;
+        w = ws;
+        c = cw;
+    }
+    if (tc) {
         const int vec = (!rows && S % 4 == 0 && ((uintptr_t)g_dev & 15u) == 0) ? 1 : 0;
         const int xvec = (T % 4 == 0 && ((uintptr_t)x_dev & 15u) == 0) ? 1 : 0;
         const int gvec = (gg_dev && S % 4 == 0 && ((uintptr_t)gg_dev & 15u) == 0) ? 1 : 0;
@@ -1160,9 +1240,10 @@ mm_status mm_relaxed_backward(mm_model *m, const float *x_dev, const float *g_de
             cfg.attrs = attr;
             cfg.numAttrs = 1;
             const void *gp = rows ? (const void *)m->grade : (const void *)gf;
-            int32_t Sp32 = Sp, tb32 = tb;
+            int32_t Sp32 = cs, tb32 = tb;
+            const double *gJs = cached ? gJ_dev : nullptr;
             void *args[] = {(void *)&x_dev, (void *)&gp, (void *)&Rw, (void *)&m->mass, (void *)&w, (void *)&c,
-                            (void *)&Sp32, (void *)&m->disc, (void *)&B, (void *)&S, (void *)&T, (void *)&tb32,
+                            (void *)&Sp32, (void *)&gJs, (void *)&m->disc, (void *)&B, (void *)&S, (void *)&T, (void *)&tb32,
                             (void *)&E, (void *)&vec, (void *)&xvec, (void *)&gvec, (void *)&gx_dev, (void *)&gg_dev};
             MM_CUDA_TRY(cudaLaunchKernelExC(&cfg, fn, args), "adjoint launch");
             st = check_launch("k_relax_adj_tc");

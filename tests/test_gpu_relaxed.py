@@ -120,6 +120,36 @@ def test_autograd_function_matches_kernels():
     np.testing.assert_allclose(g.grad.cpu().numpy(), 2.0 * gg, rtol=1e-6, atol=1e-6 * np.abs(gg).max())
 
 
+@pytest.mark.parametrize("S,T", [(37, 17), (100, 20), (200, 30)])
+def test_adjoint_reused_coefficients_match_coefficient_launch(S, T):
+    """The backward on the last forward's own outputs reuses that forward's
+    coefficients (scaled by gJ); on copies of them it forms the coefficients
+    in a launch of its own.  Both agree with the oracle and with each other;
+    after another forward the first outputs are no longer reused (their
+    copies and the originals give the same gradient)."""
+    p = tiny_problem(6, 5, 4, S=S, T=T, seed=S + 2 * T, target_blocks=7)
+    x = torch.as_tensor(W.relaxed_x(p.B, p.T, 3), device="cuda")
+    g = torch.as_tensor(p.grade.astype(np.float32), device="cuda")
+    m = mm().Model.from_problem(p)
+    J, npv, ot = m.relaxed_forward(x, g)
+    gJ = torch.full((1,), -1.5, dtype=torch.float64, device="cuda")
+    gx1, gg1 = m.relaxed_backward(x, g, npv, ot, gJ)           # reused coefficients
+    gx2, gg2 = m.relaxed_backward(x, g, npv.clone(), ot.clone(), gJ)  # coefficient launch
+    torch.cuda.synchronize()
+    r = reference(p, x.cpu().numpy(), g.cpu().numpy())
+    for gx, gg in ((gx1, gg1), (gx2, gg2)):
+        check_close(gx.cpu().numpy(), r["gx"] * -1.5, np.abs(r["floor_x"]) * 1.5, "dJ/dx")
+        check_close(gg.cpu().numpy(), r["gg"] * -1.5, np.abs(r["floor_g"]) * 1.5, "dJ/dg")
+    a, b = gx1.cpu().numpy(), gx2.cpu().numpy()
+    np.testing.assert_allclose(a, b, rtol=1e-6, atol=1e-6 * np.abs(b).max())
+    # another forward (other x) into new buffers: the first outputs are stale keys now
+    x2 = torch.as_tensor(W.relaxed_x(p.B, p.T, 4), device="cuda")
+    m.relaxed_forward(x2, g)
+    gx3, _ = m.relaxed_backward(x, g, npv, ot, gJ)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(gx3.cpu().numpy(), b, rtol=1e-6, atol=1e-6 * np.abs(b).max())
+
+
 def test_relaxed_50k_vs_oracle_and_differences():
     """The 50,000-block model (T = 20, S = 100), x from Dirichlet(1) rows, seed 2."""
     p = W.config("relaxed_50k", n_moves=0)
