@@ -943,6 +943,65 @@ def gpu_arm(args):
     return 0
 
 
+def profile_run(form: str) -> int:
+    """A short fixed launch sequence of one form for an ncu capture (no timing,
+    no JSON line): four launches of the form's kernels on the 50k workload
+    (the 64-chain workload for `batched`), the L2 flushed before each, so
+    `-s 3 -c 1` on the form's kernel captures the fourth, cold like a bench
+    step.  eval: mm_eval_moves; step: mm_search_step with apply; relaxed: the
+    forward and the adjoint on its outputs; batched: mm_batch_run with 1,024
+    moves per item and the maximum CTAs per SM (the autotuner's choice there)."""
+    import torch
+
+    import paper_2511_18296_b300 as mm
+    import workloads as W
+
+    dev = torch.device("cuda")
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    if form == "batched":
+        probs = [W.chain_problem(s) for s in W.batched_chain_specs(64)]
+        models = []
+        for p in probs:
+            m = mm.Model.from_problem(p)
+            m.schedule_set(p.x0)
+            models.append(m)
+        mvs = [torch.as_tensor(p.moves, device=dev) for p in probs]
+        b = mm.Batch(list(zip(models, mvs)), k=TOPK)
+        b.set_tile(1024, 0)  # the tile the autotuner picks on this workload
+        run = b.run
+    else:
+        p = W.config(WORKLOAD)
+        m = mm.Model.from_problem(p)
+        m.schedule_set(p.x0)
+        mv = torch.as_tensor(p.moves, device=dev)
+        n = mv.shape[0]
+        score = torch.empty(n, dtype=torch.float32, device=dev)
+        feas = torch.empty(n, dtype=torch.uint8, device=dev)
+        if form == "eval":
+            def run():
+                m.eval_moves(mv, score=score, feas=feas, want_mean=False)
+        elif form == "step":
+            def run():
+                m.search_step(mv, k=TOPK, apply=True, score=score, feas=feas)
+        elif form == "relaxed":
+            xr = torch.as_tensor(W.relaxed_x(p.B, p.T, 2), device=dev)
+            gr = torch.as_tensor(p.grade.astype(np.float32), device=dev)
+            gJ = torch.ones(1, dtype=torch.float64, device=dev)
+
+            def run():
+                _, npv_r, ot_r = m.relaxed_forward(xr, gr)
+                m.relaxed_backward(xr, gr, npv_r, ot_r, gJ)
+        else:
+            raise SystemExit(f"--profile: unknown form {form!r}")
+    torch.cuda.synchronize()
+    for _ in range(4):
+        flush.zero_()
+        run()
+    torch.cuda.synchronize()
+    print(f"profile {form}: 4 runs done", flush=True)
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -957,7 +1016,11 @@ def main(argv=None):
     ap.add_argument("--shard", action="store_true",
                     help="under torchrun: one batch split over the ranks, the ranks' top k exchanged and the winner "
                          "applied on every replica (strong scaling); default: an independent batch per rank")
+    ap.add_argument("--profile", default=None, choices=["eval", "step", "relaxed", "batched"],
+                    help="run a short fixed launch sequence of one form for an ncu capture and exit (no timing)")
     args = ap.parse_args(argv)
+    if args.profile:
+        return profile_run(args.profile)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
