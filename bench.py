@@ -40,7 +40,6 @@ METRIC = "move-scenario evals/sec at 50k blocks, S=100; % of HBM roofline vs pla
 UNIT = "move-scenario evals/s"
 TOPK = 32
 HBM_NOMINAL_GBS = 7700.0  # B300 HBM3e nominal bandwidth, for context beside the measured copy peak
-FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12  # CUDA-core FP32 FMA peak at the maximum SM clock
 FLUSH_BYTES = 256 << 20
 K_FORM = 50  # timed steps of every secondary form (median and best of 50)
 EVAL_KERNEL = "k_eval_tiled"  # the move evaluator (mm_eval_moves launches it alone)
@@ -890,19 +889,25 @@ def gpu_arm(args):
             "algorithmic_bytes": {"forward": 4 * p.B * (p.T + p.S), "forward_backward": 4 * p.B * 3 * (p.T + p.S)},
             "forward_gbs": 4 * p.B * (p.T + p.S) / (rel_fwd_ms * 1e-3) / 1e9,
             "forward_backward_gbs": 4 * p.B * 3 * (p.T + p.S) / (rel_both_ms * 1e-3) / 1e9,
-            # the contractions are FP32 FMA work: 2 B T S FMAs forward (O and V),
-            # B T S + 2 B S in the adjoint (sum_s c[t,s] ore, sum_s w v, dJ/dg)
-            "alu_roofline": {
-                "bound": "alu", "unit": "TFLOP/s", "peak": FP32_PEAK_TFLOPS,
-                "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2 FLOP per FMA x 2.032 GHz",
+            "forward_hbm_frac": 4 * p.B * (p.T + p.S) / (rel_fwd_ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
+            "forward_backward_hbm_frac": 4 * p.B * 3 * (p.T + p.S) / (rel_both_ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
+            # the contractions run on the tensor cores as TF32 products with
+            # hi/lo splits (O two products, V three, the adjoint's sum over
+            # scenarios two): algorithmic FLOPs 2 B T S per product of the
+            # definition, against the TF32 peak (the measured bf16 burst x the
+            # nominal TF32 / bf16 ratio 1.1 / 2.25)
+            "tensor_roofline": {
+                "bound": "tensor", "unit": "TFLOP/s", "peak": peaks["bf16_tflops"] * 1.1 / 2.25,
+                "peak_source": f"{which}: MEASURED_PEAKS.json bf16_tflops x nominal TF32/bf16 ratio 1.1/2.25",
                 "forward_flop": 4.0 * p.B * p.T * p.S,
-                "forward_backward_flop": 4.0 * p.B * p.T * p.S + 2.0 * p.B * (p.T * p.S + 2 * p.S),
+                "forward_backward_flop": 6.0 * p.B * p.T * p.S,
+                "forward_mma_flop_with_splits": 10.0 * p.B * p.T * p.S,
                 "forward_achieved": 4.0 * p.B * p.T * p.S / (rel_fwd_ms * 1e-3) / 1e12,
-                "forward_frac": 4.0 * p.B * p.T * p.S / (rel_fwd_ms * 1e-3) / 1e12 / FP32_PEAK_TFLOPS,
-                "forward_backward_achieved": (4.0 * p.B * p.T * p.S + 2.0 * p.B * (p.T * p.S + 2 * p.S))
-                / (rel_both_ms * 1e-3) / 1e12,
-                "forward_backward_frac": (4.0 * p.B * p.T * p.S + 2.0 * p.B * (p.T * p.S + 2 * p.S))
-                / (rel_both_ms * 1e-3) / 1e12 / FP32_PEAK_TFLOPS},
+                "forward_frac": 4.0 * p.B * p.T * p.S / (rel_fwd_ms * 1e-3) / 1e12
+                / (peaks["bf16_tflops"] * 1.1 / 2.25),
+                "forward_backward_achieved": 6.0 * p.B * p.T * p.S / (rel_both_ms * 1e-3) / 1e12,
+                "forward_backward_frac": 6.0 * p.B * p.T * p.S / (rel_both_ms * 1e-3) / 1e12
+                / (peaks["bf16_tflops"] * 1.1 / 2.25)},
             "vs_plain_eval": {"plain_eval_ms": plain_eval_ms}},
         "e2e": {"value": evals_per_step * world / e2e_avg, "unit": UNIT,
                 "h2d_bytes_per_step": int(moves_h.numel()) * moves_h.element_size(),
