@@ -16,12 +16,12 @@
 // compare in FP32 and take identical decisions (FP64 runs at a small fraction
 // of the FP32 rate on this part); otherwise they evaluate the FP64 test.
 //
-// Forward: the two skinny contractions over blocks run on the tensor cores
-// (m16n8k8 TF32 with each FP32 operand split into hi + lo, FP32-accurate) --
-// each CTA takes a range of blocks and a tile of periods, the grades turned
-// into operands in registers -- and the range partials are added by
-// compensated FP32 in range order (deterministic), then the penalty, NPV_s and
-// J in FP64.  O[t][s] is kept as the checkpoint the adjoint reads, so the
+// Forward: the two skinny contractions over blocks run on the fifth-generation
+// tensor cores (tcgen05 kind::tf32 with each FP32 operand split into hi + lo,
+// FP32-accurate; accumulators and the grade-side operand in tensor memory) --
+// one warp-specialised CTA per SM takes a range of blocks and a tile of
+// periods -- and the range partials are added by compensated FP32 in range
+// order (deterministic), then the penalty, NPV_s and J in FP64.  O[t][s] is kept as the checkpoint the adjoint reads, so the
 // backward pass never redoes the contraction.  The smoothed penalty and its
 // derivative evaluate the exponential and logarithm in FP32 on an argument
 // formed in FP64.
@@ -29,17 +29,16 @@
 //   dJ/dx[b][t] = d_t (sum_s w_s v[b][s] - m_b sum_s c[t][s] ore[b][s]),
 //   dJ/dg[b][s] = w_s ore[b][s] m_b price recovery sum_t d_t x[b][t];
 // the sum over scenarios against c is again a TF32 product on the tensor
-// cores (ore is exact in TF32).  FP64 runs at a small fraction of the FP32
+// cores (m16n8k8 from registers; ore is exact in TF32).  FP64 runs at a small fraction of the FP32
 // rate on this part, so only sums and differences that need it are FP64.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
 
 #include "mm_internal.cuh"
+#include "mm_umma.cuh"
 
 namespace mm {
-
-constexpr int kRelaxTile = 24;    // periods per forward CTA (at most)
 
 struct RelaxEcon {
     double p, r, pc;   // price, recovery, processing cost (FP64 ore decision)
@@ -83,9 +82,6 @@ __device__ __forceinline__ void relax_ore_value<double>(const double *, const Re
 }
 
 constexpr int kFwdSW = 128;     // scenarios per CTA (at most)
-#ifndef MM_RELAX_CTAS_PER_SM
-#define MM_RELAX_CTAS_PER_SM 2      // forward CTAs per SM (each writes one partial)
-#endif
 
 // d += a b for one 16 x 8 x 8 TF32 tile with FP32 accumulation, warp-wide:
 // a holds A[gid][tig], A[gid + 8][tig], A[gid][tig + 4], A[gid + 8][tig + 4],
@@ -96,58 +92,6 @@ __device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], 
         "{%0, %1, %2, %3};"
         : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-
-// Forward contraction on the tensor cores.  CTA (r, z) owns the contiguous
-// range r of the blocks and scenario tile z (up to kFwdSW scenarios) for one
-// tile of TT periods starting at t0.  Tiles of kTcBT blocks -- the grade
-// slices (caller grades) or value slices and ore words (model rows), the x
-// rows and the masses -- are copied into shared memory by cp.async one tile
-// ahead of the one being summed, so every grade is read from memory once;
-// rows past the end of the range are zero-filled by the copy itself.  With
-// y[b][t] = x[b][t] m_b and, for caller grades,
-//   v'[b][s] = ore ? g c1 - (pc + mc) : -mc    (so v[b][s] = m_b v'[b][s]),
-// warp w of group q (of kTcGroups) owns scenarios 16 (w mod W) .. 16 (w mod
-// W) + 15 and every period of the tile, and takes the K steps (eight blocks)
-// q, q + kTcGroups, ... of each tile as m16n8k8 TF32 products
-//   O[s][t] += sum_b ore[b][s] y[b][t],      V[s][t] += sum_b v'[b][s] y[b][t]
-// (model rows: V[s][t] += sum_b v[b][s] x[b][t]).  Each FP32 operand is split
-// into TF32 hi + lo and hi*hi + hi*lo + lo*hi are accumulated in FP32; ore is
-// 0 or 1, exact in TF32, so O takes two products.  y (and x) are split once
-// per tile into shared memory in fragment order (one 16-byte load gives a
-// lane its hi and lo pieces of one product); the grades become operands in
-// registers, so the loop is shared loads, a compare, an FMA, the split and
-// the MMAs.  The groups' sums are added in group order ((0 + 1) + (2 + 3) for
-// four) through shared memory and group 0 writes the CTA's partial; the
-// partials are added in range order afterwards (deterministic).  TT is a multiple of 8.  Padded rows and columns of a tile
-// only reach rows and columns of the products that are never written out.
-constexpr int kTcBT = 64;  // blocks per staged tile (eight K steps)
-constexpr int kTcStages = 2;
-constexpr int kTcGroups = 2;  // warp groups splitting the K steps of a tile
-
-// Shared-memory layout of the forward (floats).  rw: staged row stride, = 8
-// (mod 32) so the A-fragment loads of a warp hit distinct banks; ow: column of
-// the ore words (model rows).
-struct FwdLayout {
-    int rw, ow;
-    size_t g, x, m, y, xs, floats;
-};
-__host__ __device__ inline FwdLayout fwd_layout(int sw, int TT, bool rows) {
-    const int W = (sw + 15) / 16;  // warps per group
-    FwdLayout L;
-    L.ow = (sw + 3) / 4 * 4;
-    int rw = L.ow + (rows ? 4 : 0);
-    rw += (40 - rw % 32) % 32;
-    L.rw = rw;
-    size_t off = 0;
-    L.g = off; off += (size_t)kTcStages * kTcBT * L.rw;
-    L.x = off; off += (size_t)kTcStages * kTcBT * TT;
-    L.m = off; off += (size_t)kTcStages * kTcBT;
-    L.y = off; off += (size_t)kTcBT * TT * 2;           // (hi, lo) of y in fragment order
-    L.xs = off; off += rows ? (size_t)kTcBT * TT * 2 : 0;  // (hi, lo) of x
-    // the groups' sums meet at the end in two buffers over the whole area
-    L.floats = off > (size_t)2 * W * 32 * TT ? off : (size_t)2 * W * 32 * TT;
-    return L;
 }
 
 // TF32 pieces of an FP32 value without a conversion instruction: hi = x on
@@ -176,234 +120,413 @@ __device__ __forceinline__ void cp_async4z(void *dst, const void *src, bool full
 __host__ __device__ inline uint32_t fdiv_magic(uint32_t d) { return d > 1u ? 0xffffffffu / d + 1u : 0u; }
 __device__ __forceinline__ uint32_t fdiv(uint32_t n, uint32_t magic) { return magic ? __umulhi(n, magic) : n; }
 
-template <typename G, int TT, bool THR>
-__global__ void __launch_bounds__(kFwdSW / 16 * 32 * kTcGroups, MM_RELAX_CTAS_PER_SM) k_relax_fwd_tc(const float *__restrict__ x, const G *__restrict__ g,
-                                                                 RelaxRows Rw, const uint32_t *__restrict__ mass,
-                                                                 int32_t B, int32_t S, int32_t T, int32_t t0,
-                                                                 RelaxEcon E, int32_t vec, int32_t xvec,
-                                                                 float *__restrict__ part_o, float *__restrict__ part_v) {
-    constexpr bool ROWS = sizeof(G) == sizeof(double);  // model rows: values, then ore words
-    static_assert(TT % 8 == 0 && kTcBT % 16 == 0, "MMA tiles");
-    // the finishing launch may start now: it waits for this grid's results
-    // (griddepcontrol.wait) before it reads any partial
+// Forward contraction on the fifth-generation tensor cores (tcgen05), warp
+// specialised.  One CTA per SM owns a contiguous range of whole 32-block
+// tiles and a scenario tile of up to 128 (the MMA's M; rows past the tile are
+// zero) for one tile of N periods from t0.  Its warps:
+//   * four copy warps stage tile k into one of kUmStages stages by cp.async,
+//     each thread arriving on the stage's "full" mbarrier when its copies
+//     have landed: 16-byte chunks of one contiguous stretch when the scenario
+//     tile is the whole row (likewise x when the period tile is all periods),
+//     else 16-byte chunks per row, else (rows not 16-byte aligned) elements;
+//     1-D bulk (TMA) copies measured at about 16 bytes per clock per SM here,
+//     well short of an SM's share of DRAM bandwidth, so they are not used;
+//   * sixteen A warps, thread (m, q) for scenario row m and quarter q of the
+//     tile's blocks: v' (model rows: v) split into TF32 hi + lo and the 0/1 ore flag,
+//     stored into one of two operand buffers in TENSOR memory (lane m, one
+//     column per block), where the MMA reads its A operand: the only operand
+//     the tensor core reads from shared memory is the small B;
+//   * two B warps, lane n for period n and half h of the blocks: y = x m
+//     (model rows: also x) split into hi + lo, written into shared memory in
+//     the tensor core's K-major layout (8-row x 16-byte core matrices);
+//   * an MMA warp: one lane issues the tile's products, three per K step of
+//     eight blocks with yh and yl side by side as one B of 2 N rows
+//     (vh [yh | yl], o [yh | yl], vl yh), into FP32 accumulators in tensor
+//     memory, and commits them to the operand buffer's "empty" mbarrier.
+//     Consecutive products into one accumulator wait for each other, so even
+//     and odd K steps go to two accumulator sets: six independent chains;
+//     V = (vh yh + vh yl + vl yh) and O = (o yh + o yl) are summed from them
+//     at the end.
+// Stages and buffers pass between the roles through mbarriers only (a stage
+// is refilled after both preparing roles read it, a buffer rewritten after
+// its products completed), so copies, operand preparation and products of
+// consecutive tiles overlap.  Blocks past the last block of the range enter
+// the products as zeros.  At the end the A warps read the accumulators (one
+// scenario row per lane) and write the CTA's partial; the partials are added
+// in range order afterwards (deterministic).  Every wait is bounded: on
+// expiry the sticky timeout bit is raised and the CTA stops; the copies in
+// flight are waited for and the tensor memory is always released.
+constexpr int kUmBT = 32;        // blocks per tile: four K steps of eight
+constexpr int kUmStages = 8;     // staged tiles
+constexpr int kUmBufs = 2;       // operand buffers
+constexpr int kUmM = 128;        // MMA M: scenarios per CTA
+// Tensor memory (all 512 columns; one CTA per SM): two accumulator sets
+// (even and odd K steps), each [Vh: vh [yh | yl], 2 N][O: o [yh | yl], 2 N]
+// [Vl: vl yh, N], then the A buffers [buffer][vh, vl, o][kUmBT columns].
+constexpr uint32_t kUmNCols = 512;
+constexpr uint32_t kUmACol = 320;
+constexpr int kUmAWarps = 16, kUmBWarps = 2;  // A: quarters of a tile's blocks per row, B: halves
+constexpr int kUmCopyWarps = 4;
+constexpr int kUmCopyWarp = kUmAWarps + kUmBWarps, kUmMmaWarp = kUmCopyWarp + kUmCopyWarps;
+constexpr int kUmThreads = 32 * (kUmMmaWarp + 1);  // 736
+constexpr long long kUmWait = 4000000000LL;        // clock cycles (about 2 s)
+
+// Copy modes of the forward's stages.
+struct UmCopy {
+    int32_t g_rows;   // grade / value rows in 16-byte chunks (16-byte aligned)
+    int32_t g_whole;  // ... the tile's rows as one contiguous stretch (scenario tile = whole row)
+    int32_t x_rows;   // x rows in 16-byte chunks
+    int32_t x_whole;  // ... the tile's x rows as one contiguous stretch (period tile = all periods)
+};
+
+struct UmLayout {
+    int rw, ow, xs;  // staged grade-row stride, ore-word column (model rows), staged x-row stride
+    size_t stg_g, stg_x, stg_m, opB, floats;
+};
+// sw: scenarios of the tile, zs: scenario tiles, R: model row length (floats).
+__host__ __device__ inline UmLayout um_layout(int sw, int zs, int N, int T, int R, bool rows) {
+    UmLayout L;
+    const int c4 = (sw + 3) / 4 * 4;
+    if (rows) {
+        L.rw = zs == 1 ? R : c4 + 4;
+        L.ow = zs == 1 ? -1 : c4;  // whole rows: the ore words at the model's own offset
+    } else {
+        L.rw = c4;
+        L.ow = c4;
+    }
+    L.xs = T <= N ? (T + 3) / 4 * 4 : N;
+    size_t off = 0;
+    L.stg_g = off; off += (size_t)kUmStages * kUmBT * L.rw;
+    L.stg_x = off; off += (size_t)kUmStages * kUmBT * L.xs;
+    L.stg_m = off; off += (size_t)kUmStages * kUmBT;
+    off = (off + 31) / 32 * 32;                                       // 128-byte aligned operands
+    L.opB = off; off += (size_t)kUmBufs * (rows ? 4 : 2) * N * kUmBT; // [buffer][yh, yl (, xh, xl)][N x kUmBT]
+    L.floats = off;
+    return L;
+}
+
+// Arrive once on an mbarrier when all of this thread's earlier cp.async
+// copies have completed (the expected count includes this arrival).
+__device__ __forceinline__ void cp_async_arrive(uint64_t *bar) {
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(umma_saddr(bar)) : "memory");
+}
+// 16-byte cp.async to a shared-memory address (both 16-byte aligned).
+__device__ __forceinline__ void cp_async16_sa(uint32_t dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(umma_saddr(bar)) : "memory");
+}
+template <typename G, int N, bool THR>
+__global__ void __launch_bounds__(kUmThreads, 1) k_relax_fwd_umma(const float *__restrict__ x, const G *__restrict__ g,
+                                                                   RelaxRows Rw, const uint32_t *__restrict__ mass,
+                                                                   int32_t B, int32_t S, int32_t T, int32_t t0,
+                                                                   RelaxEcon E, UmCopy C, float *__restrict__ part_o,
+                                                                   float *__restrict__ part_v, uint32_t *status) {
+    constexpr bool ROWS = sizeof(G) == sizeof(double);
+    constexpr int KC = kUmBT / 4;  // 16-byte chunks of an operand row
+    constexpr int KH = KC / 2;     // chunks per half tile
+    constexpr uint32_t IDESC1 = umma_idesc_tf32(kUmM, N), IDESC2 = umma_idesc_tf32(kUmM, 2 * N);
+    constexpr uint32_t SETC = 5 * N;  // columns of one accumulator set
+    static_assert(2 * SETC <= kUmACol && kUmACol + kUmBufs * 3 * kUmBT <= kUmNCols, "tensor-memory columns");
+    constexpr int NPREP = 32 * (kUmAWarps + kUmBWarps);  // threads that read a stage and write operands
+    static_assert(N == 16 || N == 32, "N: a multiple of 16 for M = 128");
+    static_assert(kUmAWarps == 16 && kUmBWarps == 2 && kUmBT == 32, "A: four quarters, B: two halves of a tile");
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-    extern __shared__ __align__(16) float sm_tc[];
+    extern __shared__ __align__(1024) float sm_um[];
+    __shared__ __align__(8) uint64_t s_full[kUmStages], s_empty[kUmStages], s_opfull[kUmBufs], s_opempty[kUmBufs];
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_err;
     const int r = blockIdx.x, nr = gridDim.x;
-    const int b_lo = (int)((int64_t)r * B / nr), b_hi = (int)((int64_t)(r + 1) * B / nr);
+    const int tiles = (B + kUmBT - 1) / kUmBT;
+    const int k_lo = (int)((int64_t)r * tiles / nr), k_hi = (int)((int64_t)(r + 1) * tiles / nr);
+    const int b_lo = k_lo * kUmBT, b_hi = min(B, k_hi * kUmBT), ntiles = k_hi - k_lo;
     const int s0 = blockIdx.z * kFwdSW, sw = min(kFwdSW, S - s0);
-    const FwdLayout L = fwd_layout(sw, TT, ROWS);
-    float *s_g = sm_tc + L.g, *s_x = sm_tc + L.x;
-    uint32_t *s_m = reinterpret_cast<uint32_t *>(sm_tc + L.m);
-    const uint4 *s_y = reinterpret_cast<const uint4 *>(sm_tc + L.y), *s_xs = reinterpret_cast<const uint4 *>(sm_tc + L.xs);
-    uint32_t *s_yw = reinterpret_cast<uint32_t *>(sm_tc + L.y), *s_xw = reinterpret_cast<uint32_t *>(sm_tc + L.xs);
-    const int nt = min(TT, T - t0);
-    const int ntiles = (b_hi - b_lo + kTcBT - 1) / kTcBT;
-    const int tid = threadIdx.x, nth = blockDim.x;
-    const int lane = tid & 31, warp = tid >> 5, nwarps = nth >> 5;
-    const int W = nwarps / kTcGroups;                 // warps per group: one per 16 scenarios
-    const int grp = warp / W, m0 = (warp - grp * W) * 16;
-    const int gid = lane >> 2, tig = lane & 3;
-    // copy chunks per staged row: grade / value chunks of four scenarios (or
-    // single scenarios), the ore-word chunk; x chunks of four periods (or one)
-    const int gcs = ROWS ? (sw + 3) / 4 + 1 : (vec ? sw / 4 : sw);
-    const int xcs = xvec ? nt / 4 : nt;
-    const uint32_t gmag = fdiv_magic(gcs), xmag = fdiv_magic(xcs);
-    auto issue = [&](int k) {
-        const int st = k % kTcStages, bb0 = b_lo + k * kTcBT, nb = min(kTcBT, b_hi - bb0);
-        float *sg = s_g + (size_t)st * kTcBT * L.rw;
-        for (int i = tid; i < kTcBT * gcs; i += nth) {
-            const int j = (int)fdiv((uint32_t)i, gmag), q = i - j * gcs;
-            const bool live = j < nb;
-            const size_t b = (size_t)(bb0 + (live ? j : 0));
-            if (ROWS) {
-                const float *row = Rw.val + b * Rw.R;
-                if (q < gcs - 1) cp_async16z(sg + j * L.rw + 4 * q, row + s0 + 4 * q, live);
-                else cp_async16z(sg + j * L.rw + L.ow, row + Rw.ore_off + s0 / 32, live);
-            } else if (vec) {
-                cp_async16z(sg + j * L.rw + 4 * q, reinterpret_cast<const float *>(g) + b * S + s0 + 4 * q, live);
+    const UmLayout L = um_layout(sw, (int)gridDim.z, N, T, Rw.R, ROWS);
+    const int ow = L.ow < 0 ? Rw.ore_off : L.ow;
+    float *stg_g = sm_um + L.stg_g, *stg_x = sm_um + L.stg_x;
+    uint32_t *stg_m = reinterpret_cast<uint32_t *>(sm_um + L.stg_m);
+    float *opB = sm_um + L.opB;
+    const int nt = min(N, T - t0);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) {
+        for (int i = 0; i < kUmStages; i++) {
+            umma_bar_init(&s_full[i], 32 * kUmCopyWarps);  // one cp.async arrival per copy thread
+            umma_bar_init(&s_empty[i], NPREP);
+        }
+        for (int i = 0; i < kUmBufs; i++) {
+            umma_bar_init(&s_opfull[i], NPREP);
+            umma_bar_init(&s_opempty[i], 1);
+        }
+        s_err = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) umma_alloc(&s_tmem, kUmNCols);
+    umma_fence_before();
+    __syncthreads();
+    umma_fence_after();
+    const uint32_t tmem = s_tmem;
+    volatile int *err = &s_err;
+    if (warp >= kUmCopyWarp && warp < kUmCopyWarp + kUmCopyWarps) {
+        // ---- copies: tile k into stage k mod kUmStages, 16-byte cp.async
+        // chunks spread over the copy warps' threads ----
+        constexpr int NCP = 32 * kUmCopyWarps;
+        const int ct = tid - 32 * kUmCopyWarp;
+        const int c4 = (sw + 3) / 4 * 4;
+        const int gcpr = ROWS ? c4 / 4 + 1 : sw / 4;  // 16-byte chunks of a row (per-row copies)
+        // magic divisors only for the per-row and element copies
+        const uint32_t gmag = C.g_whole ? 0u : fdiv_magic(C.g_rows ? gcpr : sw);
+        const uint32_t xmag = C.x_whole ? 0u : fdiv_magic(C.x_rows ? nt / 4 : nt);
+        const float *gf = ROWS ? Rw.val : reinterpret_cast<const float *>(g);
+        const int glen = ROWS ? Rw.R : S;  // floats per source row
+        for (int k = 0; k < ntiles; k++) {
+            const int st = k % kUmStages, bb0 = b_lo + k * kUmBT, nb = min(kUmBT, b_hi - bb0);
+            if (k >= kUmStages && !umma_bar_wait(&s_empty[st], (uint32_t)(k / kUmStages - 1) & 1u, kUmWait)) *err = 1;
+            if (*err) break;
+            float *sg = stg_g + (size_t)st * kUmBT * L.rw, *sx = stg_x + (size_t)st * kUmBT * L.xs;
+            const float *gt = gf + (size_t)bb0 * glen;
+            if (C.g_whole) {  // the tile's rows are one contiguous stretch
+                const int n16 = nb * glen / 4;
+                const uint32_t d0 = umma_saddr(sg);
+                for (int i = ct; i < n16; i += NCP) cp_async16_sa(d0 + 16u * i, gt + 4 * i);
+            } else if (C.g_rows) {
+                for (int i = ct; i < nb * gcpr; i += NCP) {
+                    const int j = (int)fdiv((uint32_t)i, gmag), q = i - j * gcpr;
+                    const float *row = gt + (size_t)j * glen;
+                    if (ROWS && q == gcpr - 1) cp_async16z(sg + j * L.rw + ow, row + Rw.ore_off + s0 / 32, true);
+                    else cp_async16z(sg + j * L.rw + 4 * q, row + s0 + 4 * q, true);
+                }
             } else {
-                cp_async4z(sg + j * L.rw + q, reinterpret_cast<const float *>(g) + b * S + s0 + q, live);
-            }
-        }
-        float *sx = s_x + (size_t)st * kTcBT * TT;
-        for (int i = tid; i < kTcBT * xcs; i += nth) {
-            const int j = (int)fdiv((uint32_t)i, xmag), q = i - j * xcs;
-            const bool live = j < nb;
-            const float *row = x + (size_t)(bb0 + (live ? j : 0)) * T + t0;
-            if (xvec) cp_async16z(sx + j * TT + 4 * q, row + 4 * q, live);
-            else cp_async4z(sx + j * TT + q, row + q, live);
-        }
-        for (int j = tid; j < kTcBT; j += nth) cp_async4z(&s_m[st * kTcBT + j], mass + bb0 + (j < nb ? j : 0), j < nb);
-    };
-    issue(0);
-    asm volatile("cp.async.commit_group;" ::: "memory");
-    float dO[TT / 8][4], dV[TT / 8][4];
-#pragma unroll
-    for (int n = 0; n < TT / 8; n++)
-#pragma unroll
-        for (int c = 0; c < 4; c++) dO[n][c] = dV[n][c] = 0.0f;
-    const float c1 = E.pf * E.rf, pcm = E.pcf + E.mcf, mcn = -E.mcf;
-    const uint32_t one = __float_as_uint(1.0f);
-    for (int k = 0; k < ntiles; k++) {
-        if (k + 1 < ntiles) issue(k + 1);
-        asm volatile("cp.async.commit_group;" ::: "memory");
-        asm volatile("cp.async.wait_group 1;" ::: "memory");  // tile k has landed
-        __syncthreads();
-        const int st = k % kTcStages, nb = min(kTcBT, b_hi - (b_lo + k * kTcBT));
-        const float *sg = s_g + (size_t)st * kTcBT * L.rw;
-        // the tile's y = x m (and, for model rows, x) split into TF32 pieces in
-        // fragment order: 16-byte word ((q TT + t) 4 + i) holds, for K step q
-        // and period t, hi and lo of blocks 8q + i and 8q + i + 4 (consecutive
-        // threads write consecutive words); zero-filled rows give y = 0
-        {
-            const float *sx = s_x + (size_t)st * kTcBT * TT;
-            const uint32_t *sm = s_m + st * kTcBT;
-            uint4 *y4 = reinterpret_cast<uint4 *>(s_yw), *x4 = reinterpret_cast<uint4 *>(s_xw);
-            for (int u = tid; u < (kTcBT / 8) * TT * 4; u += nth) {
-                const int i = u & 3, qt = u >> 2, q = qt / TT, t = qt - q * TT;
-                const int j0 = 8 * q + i, j1 = j0 + 4;
-                const float x0 = sx[j0 * TT + t], x1 = sx[j1 * TT + t];
-                uint4 o;
-                tf32_split(x0 * (float)sm[j0], o.x, o.z);
-                tf32_split(x1 * (float)sm[j1], o.y, o.w);
-                y4[u] = o;
-                if (ROWS) {
-                    tf32_split(x0, o.x, o.z);
-                    tf32_split(x1, o.y, o.w);
-                    x4[u] = o;
+                for (int i = ct; i < nb * sw; i += NCP) {
+                    const int j = (int)fdiv((uint32_t)i, gmag), q = i - j * sw;
+                    cp_async4z(sg + j * L.rw + q, gt + (size_t)j * glen + s0 + q, true);
                 }
             }
+            const float *xt = x + (size_t)bb0 * T;
+            if (C.x_whole) {
+                const int n16 = nb * T / 4;
+                const uint32_t d0 = umma_saddr(sx);
+                for (int i = ct; i < n16; i += NCP) cp_async16_sa(d0 + 16u * i, xt + 4 * i);
+            } else if (C.x_rows) {
+                const int xcpr = nt / 4;
+                for (int i = ct; i < nb * xcpr; i += NCP) {
+                    const int j = (int)fdiv((uint32_t)i, xmag), q = i - j * xcpr;
+                    cp_async16z(sx + j * L.xs + 4 * q, xt + (size_t)j * T + t0 + 4 * q, true);
+                }
+            } else {
+                for (int i = ct; i < nb * nt; i += NCP) {
+                    const int j = (int)fdiv((uint32_t)i, xmag), q = i - j * nt;
+                    cp_async4z(sx + j * L.xs + q, xt + (size_t)j * T + t0 + q, true);
+                }
+            }
+            if (ct < kUmBT) cp_async4z(&stg_m[st * kUmBT + ct], mass + bb0 + (ct < nb ? ct : 0), ct < nb);
+            cp_async_arrive(&s_full[st]);
         }
-        __syncthreads();
-        if (m0 < sw) {
+        asm volatile("cp.async.wait_all;" ::: "memory");  // nothing lands in shared memory after the CTA ends
+    } else if (warp < kUmAWarps + kUmBWarps) {
+        // ---- operands: A warps (thread (m, h) = scenario row m, quarter h of
+        // the blocks), B warps (lane n = period n, half h of the blocks) ----
+        const bool isA = warp < kUmAWarps;
+        const int row_id = isA ? (tid & (kUmM - 1)) : lane;
+        const int h = isA ? warp / 4 : warp - kUmAWarps;  // A: quarter, B: half
+        const int base = (((row_id >> 3) * KC) * 8 + (row_id & 7)) * 4;  // B: chunk c at base + 32 c
+        const float c1 = E.pf * E.rf, pcm = E.pcf + E.mcf, mcn = -E.mcf;
+        const uint32_t one = __float_as_uint(1.0f);
+        // A: this warp's lanes (32 (warp mod 4) ..) and quarter of the columns
+        const uint32_t ta0 = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + kUmACol + 8u * (isA ? h : 0);
+        for (int k = 0; k < ntiles; k++) {
+            const int st = k % kUmStages, bsel = k % kUmBufs, nb = min(kUmBT, b_hi - (b_lo + k * kUmBT));
+            bool ok = umma_bar_wait(&s_full[st], (uint32_t)(k / kUmStages) & 1u, kUmWait);
+            if (ok && k >= kUmBufs) ok = umma_bar_wait(&s_opempty[bsel], (uint32_t)(k / kUmBufs - 1) & 1u, kUmWait);
+            if (!ok) *err = 1;
+            if (__any_sync(0xffffffffu, *err != 0)) break;  // warp-uniform: tcgen05.st is warp-collective
+            umma_fence_after();
+            if (isA) {
+                // A row m only enters D row m, and D rows past the scenario
+                // tile are never read: those rows take whatever the stage holds.
+                // Blocks past the range (the ragged last tile) enter as zeros.
+                const float *sg = stg_g + (size_t)st * kUmBT * L.rw + (size_t)(8 * h) * L.rw + row_id;
+                float gvs[8];
+                uint32_t ows[ROWS ? 8 : 1];
 #pragma unroll
-            for (int hh = 0; hh < kTcBT / (8 * kTcGroups); hh++) {
-                const int q = kTcGroups * hh + grp, k8 = 8 * q;  // this group's K step
-                if (k8 >= nb) break;
-                // A: operands of (scenario m0 + gid (+8), block k8 + tig (+4))
-                uint32_t vh[4], vl[4], oa[4];
+                for (int i = 0; i < 8; i++) {
+                    gvs[i] = sg[i * L.rw];
+                    if (ROWS) ows[i] = __float_as_uint(sg[i * L.rw + ow - row_id + (row_id >> 5)]);
+                }
+                uint32_t hi[8], lo[8], o[8];
+                const int nlive = nb - 8 * h;  // >= 8 except in the ragged last tile
 #pragma unroll
-                for (int a = 0; a < 4; a++) {
-                    const int mm = m0 + gid + ((a & 1) ? 8 : 0);
-                    const float *rowp = sg + (k8 + tig + ((a & 2) ? 4 : 0)) * L.rw;
-                    const float gv = rowp[mm];
+                for (int i = 0; i < 8; i++) {
+                    const float gv = gvs[i];
                     bool ore;
                     float val;
                     if (ROWS) {
+                        ore = (ows[ROWS ? i : 0] >> (row_id & 31)) & 1u;
                         val = gv;
-                        ore = (__float_as_uint(rowp[L.ow + (mm >> 5)]) >> (mm & 31)) & 1u;
                     } else {
                         ore = THR ? gv >= E.g_thr : relax_ore(gv, E);
                         val = ore ? fmaf(gv, c1, -pcm) : mcn;
                     }
-                    tf32_split(val, vh[a], vl[a]);
-                    oa[a] = ore ? one : 0u;
-                }
-                const uint4 *yb = s_y + (q * TT + gid) * 4 + tig;
-                const uint4 *xb = s_xs + (q * TT + gid) * 4 + tig;
-#pragma unroll
-                for (int n = 0; n < TT / 8; n++) {
-                    // B: y (x) of (block k8 + tig (+4), period 8n + gid)
-                    const uint4 yv = yb[32 * n];
-                    const uint32_t yh[2] = {yv.x, yv.y}, yl[2] = {yv.z, yv.w};
-                    if (ROWS) {
-                        const uint4 xv = xb[32 * n];
-                        const uint32_t xh[2] = {xv.x, xv.y}, xl[2] = {xv.z, xv.w};
-                        mma_tf32(dV[n], vh, xh);
-                        mma_tf32(dV[n], vh, xl);
-                        mma_tf32(dV[n], vl, xh);
-                    } else {
-                        mma_tf32(dV[n], vh, yh);
-                        mma_tf32(dV[n], vh, yl);
-                        mma_tf32(dV[n], vl, yh);
+                    if (nlive < 8 && i >= nlive) {
+                        ore = false;
+                        val = 0.0f;
                     }
-                    mma_tf32(dO[n], oa, yh);
-                    mma_tf32(dO[n], oa, yl);
+                    tf32_split(val, hi[i], lo[i]);
+                    o[i] = ore ? one : 0u;
+                }
+                const uint32_t ta = ta0 + (uint32_t)(bsel * 3 * kUmBT);
+                umma_st8(ta, hi);
+                umma_st8(ta + kUmBT, lo);
+                umma_st8(ta + 2 * kUmBT, o);
+                umma_wait_st();
+            } else if (row_id < N) {
+                const float *sx = stg_x + (size_t)st * kUmBT * L.xs + row_id;
+                const uint32_t *smm = stg_m + st * kUmBT;
+                float *B0 = opB + (size_t)bsel * (ROWS ? 4 : 2) * N * kUmBT + base, *B1 = B0 + N * kUmBT;
+                float *B2 = B1 + N * kUmBT, *B3 = B2 + N * kUmBT;
+                float xvs[4 * KH], mvs[4 * KH];
+#pragma unroll
+                for (int i = 0; i < 4 * KH; i++) {
+                    const int j = 4 * KH * h + i;
+                    xvs[i] = j < nb ? sx[j * L.xs] : 0.0f;  // B row n only enters D column n (n >= nt unread)
+                    mvs[i] = (float)smm[j];
+                }
+#pragma unroll
+                for (int cc = 0; cc < KH; cc++) {
+                    const int c = h * KH + cc;
+                    uint32_t yh[4], yl[4], xh[4], xl[4];
+#pragma unroll
+                    for (int e = 0; e < 4; e++) {
+                        const float xv = xvs[4 * cc + e];
+                        tf32_split(xv * mvs[4 * cc + e], yh[e], yl[e]);
+                        if (ROWS) tf32_split(xv, xh[e], xl[e]);
+                    }
+                    *reinterpret_cast<uint4 *>(B0 + 32 * c) = make_uint4(yh[0], yh[1], yh[2], yh[3]);
+                    *reinterpret_cast<uint4 *>(B1 + 32 * c) = make_uint4(yl[0], yl[1], yl[2], yl[3]);
+                    if (ROWS) {
+                        *reinterpret_cast<uint4 *>(B2 + 32 * c) = make_uint4(xh[0], xh[1], xh[2], xh[3]);
+                        *reinterpret_cast<uint4 *>(B3 + 32 * c) = make_uint4(xl[0], xl[1], xl[2], xl[3]);
+                    }
+                }
+            }
+            if (isA) umma_fence_before();  // tensor-memory stores -> the MMA thread
+            else umma_fence_operands();    // shared-memory stores -> the tensor core
+            mbar_arrive(&s_empty[st]);
+            mbar_arrive(&s_opfull[bsel]);
+        }
+    } else if (warp == kUmMmaWarp && lane == 0) {
+        // ---- products: one lane issues every MMA of the CTA ----
+        for (int k = 0; k < ntiles; k++) {
+            const int bsel = k % kUmBufs, nb = min(kUmBT, b_hi - (b_lo + k * kUmBT));
+            if (!umma_bar_wait(&s_opfull[bsel], (uint32_t)(k / kUmBufs) & 1u, kUmWait)) *err = 1;
+            if (*err) break;
+            umma_fence_after();
+            const float *B0 = opB + (size_t)bsel * (ROWS ? 4 : 2) * N * kUmBT;
+            const uint32_t a0 = tmem + kUmACol + (uint32_t)(bsel * 3 * kUmBT), a1 = a0 + kUmBT, a2 = a1 + kUmBT;
+            const uint32_t b0 = umma_saddr(B0), b2 = b0 + 8u * N * kUmBT;
+#pragma unroll
+            for (int s = 0; s < kUmBT / 8; s++) {
+                if (8 * s >= nb) break;  // K steps past the range's last block add nothing
+                // the first product into each set overwrites it
+                const uint32_t acc = (k > 0 || s > 1) ? 1u : 0u, so = 256u * s, ka = 8u * s;
+                const uint32_t dVh = tmem + (uint32_t)(s & 1) * SETC, dO = dVh + 2 * N, dVl = dVh + 4 * N;
+                const uint64_t dBy = umma_sdesc(b0 + so, 128, KC * 128);               // [yh | yl], 2 N rows
+                const uint64_t dBx = ROWS ? umma_sdesc(b2 + so, 128, KC * 128) : dBy;  // [xh | xl]
+                const uint64_t dBxh = umma_sdesc((ROWS ? b2 : b0) + so, 128, KC * 128);  // xh (yh), N rows
+                umma_tf32_ta(dVh, a0 + ka, dBx, IDESC2, acc);
+                umma_tf32_ta(dO, a2 + ka, dBy, IDESC2, acc);
+                umma_tf32_ta(dVl, a1 + ka, dBxh, IDESC1, acc);
+            }
+            umma_commit(&s_opempty[bsel]);
+        }
+    }
+    // ---- the CTA's partial: warp w reads tensor-memory lanes 32 (w mod 4),
+    // columns 16 (w / 4) .. + 15 of the accumulators ----
+    if (warp < kUmAWarps) {
+        bool ok = *err == 0;
+        if (ntiles > 0 && ok &&
+            !umma_bar_wait(&s_opempty[(ntiles - 1) % kUmBufs], (uint32_t)((ntiles - 1) / kUmBufs) & 1u, kUmWait))
+            ok = false;
+        ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld is warp-collective
+        if (!ok && lane == 0) atomicOr(status, kStTimeout);
+        umma_fence_after();
+        const int m = 32 * (warp & 3) + lane, hc = warp >> 2;
+        // the odd set holds products unless the range is one tile of at most 8 blocks
+        const int nsets = (ntiles > 1 || b_hi - b_lo > 8) ? 2 : 1;
+        if (16 * hc < N) {
+            const bool have = ntiles > 0 && ok;
+            float v[16], o[16];
+            if (have) {
+                const uint32_t base = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + 16u * hc;
+                float a[16], b[16], c[16];
+                for (int q = 0; q < 16; q++) v[q] = o[q] = 0.0f;
+                for (int set = 0; set < nsets; set++) {
+                    const uint32_t sb = base + (uint32_t)set * SETC;
+                    umma_ld16(sb, a);          // vh yh
+                    umma_ld16(sb + N, b);      // vh yl
+                    umma_ld16(sb + 4 * N, c);  // vl yh
+#pragma unroll
+                    for (int q = 0; q < 16; q++) v[q] += (a[q] + b[q]) + c[q];
+                    umma_ld16(sb + 2 * N, a);  // o yh
+                    umma_ld16(sb + 3 * N, b);  // o yl
+#pragma unroll
+                    for (int q = 0; q < 16; q++) o[q] += a[q] + b[q];
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 16; q++) {
+                const int t = 16 * hc + q;
+                if (m < sw && t < nt) {
+                    const size_t at = ((size_t)r * T + t0 + t) * S + s0 + m;
+                    part_v[at] = have ? v[q] : 0.0f;
+                    part_o[at] = have ? o[q] : 0.0f;
                 }
             }
         }
-        __syncthreads();  // stage k % kTcStages and the split tiles are refilled next
     }
-    asm volatile("cp.async.wait_all;" ::: "memory");
+    umma_fence_before();
     __syncthreads();
-    // the groups' sums added as (0 + 1) + (2 + 3) through two buffers over
-    // the idle shared memory: [2][W][32][TT / 8][8]
-    const int wl = warp - grp * W;
-    float *red = sm_tc;
-    auto put = [&](int buf) {
-        float *my = red + (((size_t)buf * W + wl) * 32 + lane) * (TT / 8) * 8;
-#pragma unroll
-        for (int n = 0; n < TT / 8; n++)
-#pragma unroll
-            for (int c = 0; c < 4; c++) {
-                my[n * 8 + c] = dO[n][c];
-                my[n * 8 + 4 + c] = dV[n][c];
-            }
-    };
-    auto add = [&](int buf) {
-        const float *oth = red + (((size_t)buf * W + wl) * 32 + lane) * (TT / 8) * 8;
-#pragma unroll
-        for (int n = 0; n < TT / 8; n++)
-#pragma unroll
-            for (int c = 0; c < 4; c++) {
-                dO[n][c] += oth[n * 8 + c];
-                dV[n][c] += oth[n * 8 + 4 + c];
-            }
-    };
-    if (kTcGroups == 4) {
-        if (grp & 1) put(grp >> 1);
-        __syncthreads();
-        if (!(grp & 1)) add(grp >> 1);
-        __syncthreads();
-        if (grp == 2) put(0);
-    } else {
-        if (grp == 1) put(0);
-    }
-    __syncthreads();
-    if (grp == 0 && m0 < sw) {
-        add(0);
-        // D[scenario m0 + gid (+8)][period 8n + 2 tig (+1)]; V carries the
-        // factor m_b inside y for caller grades
-#pragma unroll
-        for (int n = 0; n < TT / 8; n++)
-#pragma unroll
-            for (int c = 0; c < 4; c++) {
-                const int mm = m0 + gid + (c >= 2 ? 8 : 0), j = 8 * n + 2 * tig + (c & 1);
-                if (mm < sw && j < nt) {
-                    part_o[((size_t)r * T + t0 + j) * S + s0 + mm] = dO[n][c];
-                    part_v[((size_t)r * T + t0 + j) * S + s0 + mm] = dV[n][c];
-                }
-            }
-    }
+    if (warp == 0) umma_dealloc(tmem, kUmNCols);
 }
 
-template <typename G>
-using FwdFn = void (*)(const float *, const G *, RelaxRows, const uint32_t *, int32_t, int32_t, int32_t, int32_t,
-                       RelaxEcon, int32_t, int32_t, float *, float *);
-
-template <typename G>
-static FwdFn<G> fwd_fn(int tt, bool thr) {
-    if (thr) return tt == 8 ? k_relax_fwd_tc<G, 8, true> : (tt == 16 ? k_relax_fwd_tc<G, 16, true> : k_relax_fwd_tc<G, 24, true>);
-    return tt == 8 ? k_relax_fwd_tc<G, 8, false> : (tt == 16 ? k_relax_fwd_tc<G, 16, false> : k_relax_fwd_tc<G, 24, false>);
-}
-
-template <typename G>
-static mm_status relax_fwd_launch(const float *x, const G *g, RelaxRows Rw, const uint32_t *mass, int32_t B, int32_t S,
-                                  int32_t T, RelaxEcon E, float *part_o, float *part_v, int nr, cudaStream_t st) {
+// CTAs per scenario tile of the forward: one per SM (each owns a range of
+// blocks and writes one partial), at least one 32-block tile each.
+static int relax_fwd_ctas(const mm_model *m, int B, int S) {
     const int zs = (S + kFwdSW - 1) / kFwdSW;
-    const int threads = 32 * kTcGroups * ((std::min(S, kFwdSW) + 15) / 16);  // each group: a warp per 16 scenarios
-    const int vec = (S % 4 == 0 && ((uintptr_t)g & 15u) == 0) ? 1 : 0;
-    const int xvec = (T % 4 == 0 && ((uintptr_t)x & 15u) == 0) ? 1 : 0;  // period tiles start at multiples of 4
-    static_assert(kRelaxTile % 8 == 0, "period tiles must start at multiples of 8 floats");
-    for (int tb = 0; tb < T; tb += kRelaxTile) {
-        const int tt = (std::min(kRelaxTile, T - tb) + 7) / 8 * 8;
-        const size_t smem = fwd_layout(std::min(S, kFwdSW), tt, sizeof(G) == sizeof(double)).floats * sizeof(float);
-        const FwdFn<G> fn = fwd_fn<G>(tt, E.use_thr != 0);
+    return std::max(1, std::min((B + kUmBT - 1) / kUmBT, std::max(1, m->num_sms / zs)));
+}
+
+template <typename G>
+static mm_status relax_fwd_launch(const mm_model *m, const float *x, const G *g, RelaxRows Rw, const uint32_t *mass,
+                                  int32_t B, int32_t S, int32_t T, RelaxEcon E, float *part_o, float *part_v, int nr,
+                                  cudaStream_t st) {
+    const int zs = (S + kFwdSW - 1) / kFwdSW;
+    constexpr bool rows = sizeof(G) == sizeof(double);
+    UmCopy C;
+    if (rows) {
+        if (((uintptr_t)Rw.val & 15u) != 0 || Rw.R % 4 != 0 || Rw.ore_off % 4 != 0) return MM_ERR_INVALID_ARG;
+        C.g_rows = 1;
+    } else {
+        C.g_rows = (S % 4 == 0 && ((uintptr_t)g & 15u) == 0) ? 1 : 0;
+    }
+    C.g_whole = C.g_rows && zs == 1;
+    C.x_rows = (T % 4 == 0 && ((uintptr_t)x & 15u) == 0) ? 1 : 0;  // period tiles start at multiples of 32
+    for (int tb = 0; tb < T; tb += 32) {
+        const int N = T - tb <= 16 ? 16 : 32;
+        C.x_whole = C.x_rows && T <= N;
+        // at least half of an SM's shared memory: one CTA per SM, which owns all of its tensor memory
+        const size_t smem = std::max<size_t>(um_layout(std::min(S, kFwdSW), zs, N, T, Rw.R, rows).floats * sizeof(float),
+                                             116u << 10);
+        using Fn = void (*)(const float *, const G *, RelaxRows, const uint32_t *, int32_t, int32_t, int32_t, int32_t,
+                            RelaxEcon, UmCopy, float *, float *, uint32_t *);
+        Fn fn;
+        if (E.use_thr) fn = N == 16 ? k_relax_fwd_umma<G, 16, true> : k_relax_fwd_umma<G, 32, true>;
+        else fn = N == 16 ? k_relax_fwd_umma<G, 16, false> : k_relax_fwd_umma<G, 32, false>;
         MM_CUDA_TRY(cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
                     "forward smem");
-        fn<<<dim3((unsigned)nr, 1, (unsigned)zs), threads, smem, st>>>(x, g, Rw, mass, B, S, T, tb, E, vec, xvec,
-                                                                       part_o, part_v);
-        mm_status r = check_launch("k_relax_fwd_tc");
+        fn<<<dim3((unsigned)nr, 1, (unsigned)zs), kUmThreads, smem, st>>>(x, g, Rw, mass, B, S, T, tb, E, C, part_o,
+                                                                          part_v, m->status);
+        mm_status r = check_launch("k_relax_fwd_umma");
         if (r != MM_OK) return r;
     }
     return MM_OK;
@@ -425,9 +548,9 @@ __device__ __forceinline__ void relax_merge(float &s, float &c, float s2, float 
 //   1. O[t][s] and V[t][s] for the CTA's 32 scenarios of period t from the
 //      range partials: warp w adds ranges w, w + kFinWarps, ... by compensated
 //      FP32 sums (each load reads 32 consecutive floats of one partial; all of
-//      a lane's loads are in flight together), and warp 0 merges the warp sums
-//      in warp order (deterministic; the error is about one FP32 rounding of
-//      the total, no FP64 on the long sums);
+//      a lane's loads are in flight together), and warps 0 (O) and 1 (V)
+//      merge the warp sums in warp order (deterministic; the error is about
+//      one FP32 rounding of the total, no FP64 on the long sums);
 //   2. the FP64 checkpoint O[t][s] and term[t][s] = d_t (V - P_t(O)), with
 //      (Q_t - O) / m_ref formed in FP64 and the two softplus branches in FP32;
 //   3. the last CTA (release-acquire ticket) forms every NPV_s = sum_t
@@ -438,23 +561,27 @@ __device__ __forceinline__ void relax_merge(float &s, float &c, float s2, float 
 // weights per unit upstream gradient, 1/S - lambda (NPV_s - mean) / (S std)
 // (step 3), both FP32, so a backward pass on these outputs needs no
 // coefficient launch.
-// Many small CTAs keep the FP64 work (a small fraction of the FP32 rate on
-// this part) spread over the SMs; after the ticket only one round of loads
-// and short FP64 chains remain.
+// A warp-wide FP64 instruction issues about every 16 clocks per SM on this
+// part, so step 3 spends FP64 only where there are scenarios: the trees skip
+// the additions of the zero padding past T (exact, so the sums are those of
+// the full trees) and warps without scenarios skip the reductions.  A split
+// of step 3 over one CTA per chunk and a second ticket measured slower: the
+// extra fence, ticket and load round trips cost more than the FP64 saved.
 constexpr int kFinWarps = 16;
-constexpr int kFinBatch = 20;  // partial loads in flight per lane and array
+constexpr int kFinBatch = 10;  // partial loads in flight per lane and array
 
 __device__ __forceinline__ float relax_softplus_f(float bz) { return fmaxf(bz, 0.0f) + log1pf(expf(-fabsf(bz))); }
 
-// sum of q[0 .. 31] by a fixed pairwise tree
-__device__ __forceinline__ double relax_tree32(const double (&q)[32]) {
+// sum of q[0 .. 31] by a fixed pairwise tree, q[i] = 0 for i >= n: pairs of
+// two padding zeros are not added (x + 0 = x, so the result is the full tree's)
+__device__ __forceinline__ double relax_tree32(const double (&q)[32], int n) {
     double a[16];
 #pragma unroll
-    for (int u = 0; u < 16; u++) a[u] = q[2 * u] + q[2 * u + 1];
+    for (int u = 0; u < 16; u++) a[u] = 2 * u + 1 < n ? q[2 * u] + q[2 * u + 1] : q[2 * u];
 #pragma unroll
-    for (int w = 8; w > 0; w >>= 1)
+    for (int w = 8, span = 2; w > 0; w >>= 1, span <<= 1)  // a[v] covers q[span v .. span v + span - 1]
 #pragma unroll
-        for (int u = 0; u < w; u++) a[u] = a[2 * u] + a[2 * u + 1];
+        for (int u = 0; u < w; u++) a[u] = (2 * u + 1) * span < n ? a[2 * u] + a[2 * u + 1] : a[2 * u];
     return a[0];
 }
 
@@ -467,6 +594,7 @@ __global__ void __launch_bounds__(32 * kFinWarps, 1) k_relax_finish(const float 
                                                                 double *__restrict__ J, float *__restrict__ dp_out,
                                                                 float *__restrict__ wt_out) {
     __shared__ float s_sum[2][kFinWarps][32], s_cmp[2][kFinWarps][32];  // [O / V][warp][lane]
+    __shared__ float s_vm[2][32];                                         // V merged by warp 1: (sum, compensation)
     __shared__ double s_red[2][kFinWarps];
     __shared__ double s_mv[2];
     __shared__ int s_last;
@@ -478,6 +606,8 @@ __global__ void __launch_bounds__(32 * kFinWarps, 1) k_relax_finish(const float 
     // start staging its grades now; it waits for this grid before it reads
     // anything this grid writes
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    // the period's inputs are not written by the forward: read before the wait
+    const double Qt = (double)target[t], dt = disc[t];
     // launched as a programmatic dependent of the forward contraction: wait
     // until its grid has completed and its partials are visible
     asm volatile("griddepcontrol.wait;" ::: "memory");
@@ -492,10 +622,11 @@ __global__ void __launch_bounds__(32 * kFinWarps, 1) k_relax_finish(const float 
                 b[u] = c < nr ? __ldcg(part_v + (size_t)c * TS + col) : 0.0f;
             }
 #pragma unroll
-            for (int u = 0; u < kFinBatch; u++) {
-                relax_neumaier(so, co, a[u]);
-                relax_neumaier(sv, cv, b[u]);
-            }
+            for (int u = 0; u < kFinBatch; u++)
+                if (c0 + kFinWarps * u < nr) {  // warp-uniform: only the ranges that exist
+                    relax_neumaier(so, co, a[u]);
+                    relax_neumaier(sv, cv, b[u]);
+                }
         }
     }
     s_sum[0][warp][lane] = so;
@@ -503,18 +634,28 @@ __global__ void __launch_bounds__(32 * kFinWarps, 1) k_relax_finish(const float 
     s_sum[1][warp][lane] = sv;
     s_cmp[1][warp][lane] = cv;
     __syncthreads();
-    if (warp == 0) {
-        for (int w = 1; w < kFinWarps; w++) {
-            relax_merge(so, co, s_sum[0][w][lane], s_cmp[0][w][lane]);
-            relax_merge(sv, cv, s_sum[1][w][lane], s_cmp[1][w][lane]);
+    if (warp < 2) {  // warp 0 merges O, warp 1 merges V, each in warp order
+        float sm = s_sum[warp][0][lane], cm = s_cmp[warp][0][lane];
+        for (int w = 1; w < kFinWarps; w++) relax_merge(sm, cm, s_sum[warp][w][lane], s_cmp[warp][w][lane]);
+        if (warp == 1) {
+            s_vm[0][lane] = sm;
+            s_vm[1][lane] = cm;
+        } else {
+            so = sm;
+            co = cm;
         }
+    }
+    __syncthreads();
+    if (warp == 0) {
         if (s < S) {
+            sv = s_vm[0][lane];
+            cv = s_vm[1][lane];
             const double O = (double)so + (double)co, V = (double)sv + (double)cv;
             o_out[col] = O;
-            const float bz = (float)E.beta * (float)(((double)target[t] - O) * E.inv_mref);
+            const float bz = (float)E.beta * (float)((Qt - O) * E.inv_mref);
             const float pen = (float)(E.a * E.m_ref * E.inv_beta) * relax_softplus_f(bz) +
                               (float)(E.e * E.m_ref * E.inv_beta) * relax_softplus_f(-bz);
-            term[col] = disc[t] * (V - (double)pen);
+            term[col] = dt * (V - (double)pen);
             // P_t'(O) for the adjoint: -a sigma(beta (Q - O) / m_ref) + e sigma(beta (O - Q) / m_ref)
             dp_out[col] = -(float)E.a / (1.0f + expf(-bz)) + (float)E.e / (1.0f + expf(bz));
         }
@@ -527,7 +668,9 @@ __global__ void __launch_bounds__(32 * kFinWarps, 1) k_relax_finish(const float 
     __threadfence();
     // the last CTA: NPV_s for every scenario (32 periods at a time, all loads
     // in flight, each batch by a fixed pairwise tree, the batch sums in period
-    // order), then (sum, sum of squares) by fixed trees over lanes and warps
+    // order), then (sum, sum of squares) by fixed trees over lanes and warps;
+    // warps past the last scenario hold zeros and skip the FP64 work
+    const int nw = min(kFinWarps, (S + 31) / 32);  // warps holding scenarios (of the first pass)
     double x1 = 0.0, x2 = 0.0;
     for (int sc = threadIdx.x; sc < S; sc += blockDim.x) {
         double acc = 0.0;
@@ -535,16 +678,18 @@ __global__ void __launch_bounds__(32 * kFinWarps, 1) k_relax_finish(const float 
             double q[32];
 #pragma unroll
             for (int u = 0; u < 32; u++) q[u] = t0 + u < T ? __ldcg(term + (size_t)(t0 + u) * S + sc) : 0.0;
-            acc += relax_tree32(q);
+            acc += relax_tree32(q, T - t0);
         }
         npv[sc] = acc;
         x1 += acc;
         x2 += acc * acc;
     }
+    if (warp < nw) {
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        x1 += __shfl_xor_sync(0xffffffffu, x1, off);
-        x2 += __shfl_xor_sync(0xffffffffu, x2, off);
+        for (int off = 16; off > 0; off >>= 1) {
+            x1 += __shfl_xor_sync(0xffffffffu, x1, off);
+            x2 += __shfl_xor_sync(0xffffffffu, x2, off);
+        }
     }
     if (lane == 0) {
         s_red[0][warp] = x1;
@@ -552,11 +697,13 @@ __global__ void __launch_bounds__(32 * kFinWarps, 1) k_relax_finish(const float 
     }
     __syncthreads();
     if (warp == 0) {
-        double y1 = lane < kFinWarps ? s_red[0][lane] : 0.0, y2 = lane < kFinWarps ? s_red[1][lane] : 0.0;
+        double y1 = lane < nw ? s_red[0][lane] : 0.0, y2 = lane < nw ? s_red[1][lane] : 0.0;
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
-            y1 += __shfl_xor_sync(0xffffffffu, y1, off);
-            y2 += __shfl_xor_sync(0xffffffffu, y2, off);
+            if (off < nw) {  // lanes >= nw hold zeros: the levels above add only zeros
+                y1 += __shfl_xor_sync(0xffffffffu, y1, off);
+                y2 += __shfl_xor_sync(0xffffffffu, y2, off);
+            }
         }
         if (lane == 0) {
             const double mean = y1 * E.inv_S;
@@ -1115,10 +1262,9 @@ mm_status mm_relaxed_forward(mm_model *m, const float *x_dev, const float *g_dev
     const int B = m->B, S = m->S, T = m->T;
     const RelaxEcon E = relax_econ(m, beta, m_ref);
     const RelaxRows Rw{m->val, m->R, m->ore_off};
-    // block ranges: MM_RELAX_CTAS_PER_SM CTAs per SM over the scenario tiles,
-    // at least one staged tile each
-    const int zs = (S + kFwdSW - 1) / kFwdSW;
-    const int nr = std::max(1, std::min((B + kTcBT - 1) / kTcBT, std::max(1, MM_RELAX_CTAS_PER_SM * m->num_sms / zs)));
+    // block ranges: one forward CTA per SM over the scenario tiles, whole
+    // 32-block tiles each
+    const int nr = relax_fwd_ctas(m, B, S);
     const size_t TS = (size_t)T * S;
     // the adjoint's coefficients: P_t'(O) [T][S], then w_s / gJ [S]
     if (m->relax_coef_floats < TS + S) {
@@ -1136,8 +1282,8 @@ mm_status mm_relaxed_forward(mm_model *m, const float *x_dev, const float *g_dev
     if (st != MM_OK) return st;
     float *part_o = m->relax_scratch, *part_v = part_o + (size_t)nr * TS;
     double *term = reinterpret_cast<double *>(part_v + (size_t)nr * TS);
-    st = g_dev ? relax_fwd_launch<float>(x_dev, g_dev, Rw, m->mass, B, S, T, E, part_o, part_v, nr, m->stream)
-               : relax_fwd_launch<double>(x_dev, m->grade, Rw, m->mass, B, S, T, E, part_o, part_v, nr, m->stream);
+    st = g_dev ? relax_fwd_launch<float>(m, x_dev, g_dev, Rw, m->mass, B, S, T, E, part_o, part_v, nr, m->stream)
+               : relax_fwd_launch<double>(m, x_dev, m->grade, Rw, m->mass, B, S, T, E, part_o, part_v, nr, m->stream);
     if (st != MM_OK) return st;
     // the finish launches as a programmatic dependent of the forward grid, so
     // its launch overlaps the forward's tail
