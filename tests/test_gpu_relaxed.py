@@ -94,6 +94,24 @@ def test_relaxed_small_vs_oracle(S, T):
     check_close(gg, r["gg"], r["floor_g"], "dJ/dg")
 
 
+@pytest.mark.parametrize("grid,S,T", [((5, 5, 4), 37, 17), ((5, 5, 4), 100, 20), ((1, 1, 1), 9, 5), ((3, 3, 1), 100, 20)])
+def test_relaxed_ragged_block_ranges(grid, S, T):
+    """Block counts that leave the forward's last range short: 100 blocks end
+    in a 4-block tile (one K step, the odd accumulator set unused), a single
+    block, and 9 blocks in one CTA (one tile, two K steps)."""
+    p = tiny_problem(*grid, S=S, T=T, seed=3 * S + T, target_blocks=2)
+    x = W.relaxed_x(p.B, p.T, 2)
+    g = p.grade.astype(np.float32)
+    m = mm().Model.from_problem(p)
+    J, npv, ot, gx, gg = run(m, x, g)
+    r = reference(p, x, g)
+    assert J == pytest.approx(r["J"], rel=TOL)
+    np.testing.assert_allclose(ot, r["O"], rtol=1e-6, atol=1e-3)
+    np.testing.assert_allclose(npv, r["npv"], rtol=TOL)
+    check_close(gx, r["gx"], r["floor_x"], "dJ/dx")
+    check_close(gg, r["gg"], r["floor_g"], "dJ/dg")
+
+
 @pytest.mark.parametrize("S,T", [(12, 6), (200, 30), (1024, 30), (12, 254)])
 def test_relaxed_model_grades_path(S, T):
     """g = NULL: the model's own FP64 grades (value rows and ore words staged
