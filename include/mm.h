@@ -345,9 +345,10 @@ mm_status mm_batch_get_chain(const mm_batch *b, int32_t chain, int32_t *team, in
  * 512 .. 16384 x CTAs per SM {max, max - 1}), keeping the fastest; (2) for
  * each scenario count among the chains, every other team width that fits
  * (mm_batch_set_chain), kept only when more than 1 % faster than the best so
- * far; (3) L1 prefetch distances 0..2 for all chains, kept the same way.
- * Returns the tile and the best mean time (outputs may be NULL); the chosen
- * team widths and distance are read with mm_batch_get_chain.  Synchronous;
+ * far; (3) for each scenario count, L1 prefetch distances 0..2 for its
+ * chains, kept the same way.  Returns the tile and the best mean time
+ * (outputs may be NULL); the chosen team widths and distances are read with
+ * mm_batch_get_chain.  Synchronous;
  * only for batches created with apply = 0 (MM_ERR_STATE otherwise), since it
  * runs the batch many times. */
 mm_status mm_batch_autotune(mm_batch *b, int32_t reps, int32_t *moves_per_item, int32_t *ctas_per_sm,

@@ -527,7 +527,8 @@ class Batch:
 
     def autotune(self, reps: int = 3, cache: Optional[str] = None):
         """mm_batch_autotune: tile shape, then team width per scenario count,
-        then prefetch distance.  Returns (moves per item, CTAs per SM, best ms).
+        then prefetch distance per scenario count.  Returns (moves per item,
+        CTAs per SM, best ms).
 
         cache: a JSON file of earlier choices (default: $MM_BATCH_TUNE_CACHE,
         none when unset).  Each chain's team width and prefetch distance are

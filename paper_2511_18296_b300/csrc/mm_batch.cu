@@ -13,7 +13,7 @@
 // when asked, applies the chain's best move with the single-model apply code.
 // Nothing in the launch allocates or synchronises with the host, so a run can
 // be captured into a CUDA graph; the tile shape (moves per item, CTAs per SM)
-// and each scenario class's team width and the prefetch distance are chosen by
+// and each scenario class's team width and prefetch distance are chosen by
 // mm_batch_autotune.
 #include <algorithm>
 #include <vector>
@@ -506,12 +506,19 @@ mm_status mm_batch_autotune(mm_batch *b, int32_t reps, int32_t *moves_per_item, 
         for (int c = 0; c < b->n_chains && st == MM_OK; c++)
             if (b->S[c] == S) st = mm_batch_set_chain(b, c, keep, b->chains[c].E.prefetch);
     }
-    // 3. L1 prefetch distance (evaluation batches ahead), all chains
-    if (st == MM_OK) {
-        int keep = b->chains[0].E.prefetch;
+    // 3. L1 prefetch distance (evaluation batches ahead) per scenario class,
+    //    the other classes unchanged: a class whose rows stay in L2 loses by
+    //    prefetching, one whose rows come from DRAM may gain; kept only if it
+    //    beats the best time so far by more than 1 %
+    for (int S : classes) {
+        if (st != MM_OK) break;
+        int keep = -1;
+        for (int c = 0; c < b->n_chains; c++)
+            if (b->S[c] == S) keep = b->chains[c].E.prefetch;
         for (int pf = 0; pf <= 2 && st == MM_OK; pf++) {
             if (pf == keep) continue;
-            for (int c = 0; c < b->n_chains && st == MM_OK; c++) st = mm_batch_set_chain(b, c, b->team[c], pf);
+            for (int c = 0; c < b->n_chains && st == MM_OK; c++)
+                if (b->S[c] == S) st = mm_batch_set_chain(b, c, b->team[c], pf);
             float ms = 0.0f;
             if (st == MM_OK) st = batch_time(b, reps, e0, e1, &ms);
             if (st == MM_OK && ms < best * 0.99f) {
@@ -519,7 +526,8 @@ mm_status mm_batch_autotune(mm_batch *b, int32_t reps, int32_t *moves_per_item, 
                 keep = pf;
             }
         }
-        for (int c = 0; c < b->n_chains && st == MM_OK; c++) st = mm_batch_set_chain(b, c, b->team[c], keep);
+        for (int c = 0; c < b->n_chains && st == MM_OK; c++)
+            if (b->S[c] == S) st = mm_batch_set_chain(b, c, b->team[c], keep);
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
