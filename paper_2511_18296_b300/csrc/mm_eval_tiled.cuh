@@ -872,7 +872,7 @@ template <int TEAM, int QMAX, bool KAHAN, bool DELTA, int KF, bool TAIL, bool TO
           int NW = kEvalThreads / 32>
 __device__ __forceinline__ void eval_warp_range(const EvalArgs &A, EvalSharedT<NW> &sh, const float *tab, const float *s_dd,
                                                 const int64_t *s_mined, const uint64_t *s_cap, int64_t r0, int64_t r1,
-                                                uint64_t &wtk) {
+                                                uint64_t &wtk, const int2 *first = nullptr) {
     constexpr int CH = kChunk;
     constexpr int TPW = 32 / TEAM;
     const int T1 = A.T + 1;
@@ -884,11 +884,12 @@ __device__ __forceinline__ void eval_warp_range(const EvalArgs &A, EvalSharedT<N
     const float invS = 1.0f / (float)S;
     const size_t pin_off = (size_t)T1 * A.S_pad;
     const uint32_t lt_mask = (1u << lane) - 1u;
+    // the first chunk's moves (first: loaded by the caller before its set-up)
     int2 mv[2];
 #pragma unroll
     for (int h = 0; h < 2; h++) {
         const int64_t i = r0 + h * 32 + lane;
-        mv[h] = i < r1 ? load_move(A, i) : make_int2(0, -1);
+        mv[h] = first ? first[h] : (i < r1 ? load_move(A, i) : make_int2(0, -1));
     }
     for (int64_t c0 = r0; c0 < r1; c0 += CH) {
         // ---- decode: two moves per lane ----
@@ -1037,6 +1038,18 @@ __global__ void __launch_bounds__(NT, NT == kEvalThreads ? MM_EVAL_MINB : 1) k_e
     uint64_t *s_cap = reinterpret_cast<uint64_t *>(s_mined + T1);              // [T+1]
 
     const int tid = threadIdx.x;
+    // contiguous, balanced range of moves for each warp; its first moves'
+    // loads go out before the set-up below, so their latency overlaps it
+    const int warp = tid >> 5;
+    const int64_t nwarps = (int64_t)gridDim.x * NW;
+    const int64_t gw = (int64_t)blockIdx.x * NW + warp;
+    const int64_t r0 = gw * A.n / nwarps, r1 = (gw + 1) * A.n / nwarps;
+    int2 first[2];
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+        const int64_t i = r0 + h * 32 + (tid & 31);
+        first[h] = i < r1 ? load_move(A, i) : make_int2(0, -1);
+    }
     __shared__ uint32_t s_fin;  // TOPK: warps of this CTA that have finished evaluating
     if (TOPK && tid == 0) s_fin = 0u;
     if (TSM) {
@@ -1052,15 +1065,9 @@ __global__ void __launch_bounds__(NT, NT == kEvalThreads ? MM_EVAL_MINB : 1) k_e
     }
     __syncthreads();
     const float *tab = TSM ? s_tab : A.tab;
-
-    // contiguous, balanced range of moves for each warp
-    const int warp = tid >> 5;
-    const int64_t nwarps = (int64_t)gridDim.x * NW;
-    const int64_t gw = (int64_t)blockIdx.x * NW + warp;
-    const int64_t r0 = gw * A.n / nwarps, r1 = (gw + 1) * A.n / nwarps;
     uint64_t wtk = 0;  // this warp's best 32 candidate keys (TOPK)
     eval_warp_range<TEAM, QMAX, KAHAN, DELTA, KF, TAIL, TOPK, SIG, NW>(A, sh, tab, A.dd_smem ? s_dd : A.ddt,
-                                                                       s_mined, s_cap, r0, r1, wtk);
+                                                                       s_mined, s_cap, r0, r1, wtk, first);
     if constexpr (TOPK) step_finish<NW>(A.tail, wtk, sh.best, su, &s_fin);
 }
 
