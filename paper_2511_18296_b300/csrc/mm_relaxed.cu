@@ -251,6 +251,61 @@ __global__ void __launch_bounds__(kUmThreads, 1) k_relax_fwd_umma(const float *_
     float *opB = sm_um + L.opB;
     const int nt = min(N, T - t0);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    // ---- copies (warps kUmCopyWarp ..): tile k into stage k mod kUmStages,
+    // 16-byte cp.async chunks spread over the copy warps' threads ----
+    const bool is_copy = warp >= kUmCopyWarp && warp < kUmCopyWarp + kUmCopyWarps;
+    constexpr int NCP = 32 * kUmCopyWarps;
+    const int ct = tid - 32 * kUmCopyWarp;
+    const int c4 = (sw + 3) / 4 * 4;
+    const int gcpr = ROWS ? c4 / 4 + 1 : sw / 4;  // 16-byte chunks of a row (per-row copies)
+    // magic divisors only for the per-row and element copies
+    const uint32_t gmag = (!is_copy || C.g_whole) ? 0u : fdiv_magic(C.g_rows ? gcpr : sw);
+    const uint32_t xmag = (!is_copy || C.x_whole) ? 0u : fdiv_magic(C.x_rows ? nt / 4 : nt);
+    const float *gf = ROWS ? Rw.val : reinterpret_cast<const float *>(g);
+    const int glen = ROWS ? Rw.R : S;  // floats per source row
+    auto issue_tile = [&](int k) {
+        const int st = k % kUmStages, bb0 = b_lo + k * kUmBT, nb = min(kUmBT, b_hi - bb0);
+        float *sg = stg_g + (size_t)st * kUmBT * L.rw, *sx = stg_x + (size_t)st * kUmBT * L.xs;
+        const float *gt = gf + (size_t)bb0 * glen;
+        if (C.g_whole) {  // the tile's rows are one contiguous stretch
+            const int n16 = nb * glen / 4;
+            const uint32_t d0 = umma_saddr(sg);
+            for (int i = ct; i < n16; i += NCP) cp_async16_sa(d0 + 16u * i, gt + 4 * i);
+        } else if (C.g_rows) {
+            for (int i = ct; i < nb * gcpr; i += NCP) {
+                const int j = (int)fdiv((uint32_t)i, gmag), q = i - j * gcpr;
+                const float *row = gt + (size_t)j * glen;
+                if (ROWS && q == gcpr - 1) cp_async16z(sg + j * L.rw + ow, row + Rw.ore_off + s0 / 32, true);
+                else cp_async16z(sg + j * L.rw + 4 * q, row + s0 + 4 * q, true);
+            }
+        } else {
+            for (int i = ct; i < nb * sw; i += NCP) {
+                const int j = (int)fdiv((uint32_t)i, gmag), q = i - j * sw;
+                cp_async4z(sg + j * L.rw + q, gt + (size_t)j * glen + s0 + q, true);
+            }
+        }
+        const float *xt = x + (size_t)bb0 * T;
+        if (C.x_whole) {
+            const int n16 = nb * T / 4;
+            const uint32_t d0 = umma_saddr(sx);
+            for (int i = ct; i < n16; i += NCP) cp_async16_sa(d0 + 16u * i, xt + 4 * i);
+        } else if (C.x_rows) {
+            const int xcpr = nt / 4;
+            for (int i = ct; i < nb * xcpr; i += NCP) {
+                const int j = (int)fdiv((uint32_t)i, xmag), q = i - j * xcpr;
+                cp_async16z(sx + j * L.xs + 4 * q, xt + (size_t)j * T + t0 + 4 * q, true);
+            }
+        } else {
+            for (int i = ct; i < nb * nt; i += NCP) {
+                const int j = (int)fdiv((uint32_t)i, xmag), q = i - j * nt;
+                cp_async4z(sx + j * L.xs + q, xt + (size_t)j * T + t0 + q, true);
+            }
+        }
+        if (ct < kUmBT) cp_async4z(&stg_m[st * kUmBT + ct], mass + bb0 + (ct < nb ? ct : 0), ct < nb);
+    };
+    // tile 0's copies go out before the set-up below (they need no barrier;
+    // the stage's arrival comes after it), so their latency overlaps it
+    if (is_copy && ntiles > 0) issue_tile(0);
     if (tid == 0) {
         for (int i = 0; i < kUmStages; i++) {
             umma_bar_init(&s_full[i], 32 * kUmCopyWarps);  // one cp.async arrival per copy thread
@@ -269,60 +324,13 @@ __global__ void __launch_bounds__(kUmThreads, 1) k_relax_fwd_umma(const float *_
     umma_fence_after();
     const uint32_t tmem = s_tmem;
     volatile int *err = &s_err;
-    if (warp >= kUmCopyWarp && warp < kUmCopyWarp + kUmCopyWarps) {
-        // ---- copies: tile k into stage k mod kUmStages, 16-byte cp.async
-        // chunks spread over the copy warps' threads ----
-        constexpr int NCP = 32 * kUmCopyWarps;
-        const int ct = tid - 32 * kUmCopyWarp;
-        const int c4 = (sw + 3) / 4 * 4;
-        const int gcpr = ROWS ? c4 / 4 + 1 : sw / 4;  // 16-byte chunks of a row (per-row copies)
-        // magic divisors only for the per-row and element copies
-        const uint32_t gmag = C.g_whole ? 0u : fdiv_magic(C.g_rows ? gcpr : sw);
-        const uint32_t xmag = C.x_whole ? 0u : fdiv_magic(C.x_rows ? nt / 4 : nt);
-        const float *gf = ROWS ? Rw.val : reinterpret_cast<const float *>(g);
-        const int glen = ROWS ? Rw.R : S;  // floats per source row
+    if (is_copy) {
         for (int k = 0; k < ntiles; k++) {
-            const int st = k % kUmStages, bb0 = b_lo + k * kUmBT, nb = min(kUmBT, b_hi - bb0);
+            const int st = k % kUmStages;
             if (k >= kUmStages && !umma_bar_wait(&s_empty[st], (uint32_t)(k / kUmStages - 1) & 1u, kUmWait)) *err = 1;
             if (*err) break;
-            float *sg = stg_g + (size_t)st * kUmBT * L.rw, *sx = stg_x + (size_t)st * kUmBT * L.xs;
-            const float *gt = gf + (size_t)bb0 * glen;
-            if (C.g_whole) {  // the tile's rows are one contiguous stretch
-                const int n16 = nb * glen / 4;
-                const uint32_t d0 = umma_saddr(sg);
-                for (int i = ct; i < n16; i += NCP) cp_async16_sa(d0 + 16u * i, gt + 4 * i);
-            } else if (C.g_rows) {
-                for (int i = ct; i < nb * gcpr; i += NCP) {
-                    const int j = (int)fdiv((uint32_t)i, gmag), q = i - j * gcpr;
-                    const float *row = gt + (size_t)j * glen;
-                    if (ROWS && q == gcpr - 1) cp_async16z(sg + j * L.rw + ow, row + Rw.ore_off + s0 / 32, true);
-                    else cp_async16z(sg + j * L.rw + 4 * q, row + s0 + 4 * q, true);
-                }
-            } else {
-                for (int i = ct; i < nb * sw; i += NCP) {
-                    const int j = (int)fdiv((uint32_t)i, gmag), q = i - j * sw;
-                    cp_async4z(sg + j * L.rw + q, gt + (size_t)j * glen + s0 + q, true);
-                }
-            }
-            const float *xt = x + (size_t)bb0 * T;
-            if (C.x_whole) {
-                const int n16 = nb * T / 4;
-                const uint32_t d0 = umma_saddr(sx);
-                for (int i = ct; i < n16; i += NCP) cp_async16_sa(d0 + 16u * i, xt + 4 * i);
-            } else if (C.x_rows) {
-                const int xcpr = nt / 4;
-                for (int i = ct; i < nb * xcpr; i += NCP) {
-                    const int j = (int)fdiv((uint32_t)i, xmag), q = i - j * xcpr;
-                    cp_async16z(sx + j * L.xs + 4 * q, xt + (size_t)j * T + t0 + 4 * q, true);
-                }
-            } else {
-                for (int i = ct; i < nb * nt; i += NCP) {
-                    const int j = (int)fdiv((uint32_t)i, xmag), q = i - j * nt;
-                    cp_async4z(sx + j * L.xs + q, xt + (size_t)j * T + t0 + q, true);
-                }
-            }
-            if (ct < kUmBT) cp_async4z(&stg_m[st * kUmBT + ct], mass + bb0 + (ct < nb ? ct : 0), ct < nb);
-            cp_async_arrive(&s_full[st]);
+            if (k > 0) issue_tile(k);
+            cp_async_arrive(&s_full[st]);  // when this thread's copies so far (tile k's and earlier) have landed
         }
         asm volatile("cp.async.wait_all;" ::: "memory");  // nothing lands in shared memory after the CTA ends
     } else if (warp < kUmAWarps + kUmBWarps) {
