@@ -440,9 +440,10 @@ mm_status mm_get_metal(mm_model *m, double *metal_host);
  *
  * mm_relaxed_forward: x_dev[B][T] FP32 -> *J_dev, npv_dev[S] and ore_t_dev[T][S]
  * (FP64, device).  ore_t_dev is the per-period checkpoint O[t][s] that the
- * adjoint reads.  Products and each CTA's sums over its range of blocks in
- * FP32, the ranges' sums added by compensated FP32 in a fixed order, the
- * penalty, NPV_s and J in FP64 (deterministic).
+ * adjoint reads.  The products run on the tensor cores as TF32 with every
+ * FP32 operand split into hi + lo (FP32-accurate), accumulated in FP32 over
+ * each CTA's range of blocks; the ranges' sums are added by compensated FP32
+ * in a fixed order, the penalty, NPV_s and J in FP64 (deterministic).
  * mm_relaxed_backward: given the forward's npv_dev and ore_t_dev and the
  * upstream gradient *gJ_dev (FP64, device), writes gx_dev[B][T] = dJ/dx and,
  * if gg_dev is not NULL, gg_dev[B][S] = dJ/dg (FP32, device).  Where every
