@@ -124,6 +124,10 @@ struct mm_model {
     int test_stall = 0;              // test-only (MM_TEST_STALL_BULK_WAIT at create): every bulk-copy stage
                                      // expects 16 bytes it never receives and waits about 1 ms, so the
                                      // evaluator's timeout path runs without any fault
+    int test_stall_relax = 0;        // test-only (MM_TEST_STALL_RELAXED at create), one-shot: the next relaxed
+                                     // forward's stage barriers expect one arrival nobody makes and every wait
+                                     // of that launch gives up after about 1 ms, so its timeout path runs
+                                     // without any fault
     int step_max_ctas = 0;
     void *step_event = nullptr;      // cudaEvent_t recorded between the step's two launches (timing hook)
     float *shadow32 = nullptr;       // FP32 shadow accumulators: metal [T][S], contrib [T][S], npv [S]

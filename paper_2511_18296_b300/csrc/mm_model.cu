@@ -512,6 +512,7 @@ mm_status mm_model_create(const mm_model_desc *d, mm_model **out) {
     // test-only: the bulk-copy evaluator's stages wait for bytes that never
     // come (every copy it issues still lands), so its bounded wait runs out
     if (const char *st = std::getenv("MM_TEST_STALL_BULK_WAIT")) m->test_stall = (*st && *st != '0') ? 1 : 0;
+    if (const char *st = std::getenv("MM_TEST_STALL_RELAXED")) m->test_stall_relax = (*st && *st != '0') ? 1 : 0;
     m->S_pad = (S + 7) / 8 * 8;
     m->W = (S + 31) / 32;
     m->ore_off = 4 * ((S + 3) / 4);

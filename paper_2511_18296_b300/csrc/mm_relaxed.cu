@@ -224,7 +224,8 @@ __global__ void __launch_bounds__(kUmThreads, 1) k_relax_fwd_umma(const float *_
                                                                    RelaxRows Rw, const uint32_t *__restrict__ mass,
                                                                    int32_t B, int32_t S, int32_t T, int32_t t0,
                                                                    RelaxEcon E, UmCopy C, float *__restrict__ part_o,
-                                                                   float *__restrict__ part_v, uint32_t *status) {
+                                                                   float *__restrict__ part_v, uint32_t *status,
+                                                                   int32_t stall, long long wait) {
     constexpr bool ROWS = sizeof(G) == sizeof(double);
     constexpr int KC = kUmBT / 4;  // 16-byte chunks of an operand row
     constexpr int KH = KC / 2;     // chunks per half tile
@@ -308,7 +309,8 @@ __global__ void __launch_bounds__(kUmThreads, 1) k_relax_fwd_umma(const float *_
     if (is_copy && ntiles > 0) issue_tile(0);
     if (tid == 0) {
         for (int i = 0; i < kUmStages; i++) {
-            umma_bar_init(&s_full[i], 32 * kUmCopyWarps);  // one cp.async arrival per copy thread
+            // one cp.async arrival per copy thread (test-only stall: one more, which never comes)
+            umma_bar_init(&s_full[i], 32 * kUmCopyWarps + (stall ? 1 : 0));
             umma_bar_init(&s_empty[i], NPREP);
         }
         for (int i = 0; i < kUmBufs; i++) {
@@ -327,7 +329,7 @@ __global__ void __launch_bounds__(kUmThreads, 1) k_relax_fwd_umma(const float *_
     if (is_copy) {
         for (int k = 0; k < ntiles; k++) {
             const int st = k % kUmStages;
-            if (k >= kUmStages && !umma_bar_wait(&s_empty[st], (uint32_t)(k / kUmStages - 1) & 1u, kUmWait)) *err = 1;
+            if (k >= kUmStages && !umma_bar_wait(&s_empty[st], (uint32_t)(k / kUmStages - 1) & 1u, wait)) *err = 1;
             if (*err) break;
             if (k > 0) issue_tile(k);
             cp_async_arrive(&s_full[st]);  // when this thread's copies so far (tile k's and earlier) have landed
@@ -346,8 +348,8 @@ __global__ void __launch_bounds__(kUmThreads, 1) k_relax_fwd_umma(const float *_
         const uint32_t ta0 = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + kUmACol + 8u * (isA ? h : 0);
         for (int k = 0; k < ntiles; k++) {
             const int st = k % kUmStages, bsel = k % kUmBufs, nb = min(kUmBT, b_hi - (b_lo + k * kUmBT));
-            bool ok = umma_bar_wait(&s_full[st], (uint32_t)(k / kUmStages) & 1u, kUmWait);
-            if (ok && k >= kUmBufs) ok = umma_bar_wait(&s_opempty[bsel], (uint32_t)(k / kUmBufs - 1) & 1u, kUmWait);
+            bool ok = umma_bar_wait(&s_full[st], (uint32_t)(k / kUmStages) & 1u, wait);
+            if (ok && k >= kUmBufs) ok = umma_bar_wait(&s_opempty[bsel], (uint32_t)(k / kUmBufs - 1) & 1u, wait);
             if (!ok) *err = 1;
             if (__any_sync(0xffffffffu, *err != 0)) break;  // warp-uniform: tcgen05.st is warp-collective
             umma_fence_after();
@@ -428,7 +430,7 @@ __global__ void __launch_bounds__(kUmThreads, 1) k_relax_fwd_umma(const float *_
         // ---- products: one lane issues every MMA of the CTA ----
         for (int k = 0; k < ntiles; k++) {
             const int bsel = k % kUmBufs, nb = min(kUmBT, b_hi - (b_lo + k * kUmBT));
-            if (!umma_bar_wait(&s_opfull[bsel], (uint32_t)(k / kUmBufs) & 1u, kUmWait)) *err = 1;
+            if (!umma_bar_wait(&s_opfull[bsel], (uint32_t)(k / kUmBufs) & 1u, wait)) *err = 1;
             if (*err) break;
             umma_fence_after();
             const float *B0 = opB + (size_t)bsel * (ROWS ? 4 : 2) * N * kUmBT;
@@ -455,7 +457,7 @@ __global__ void __launch_bounds__(kUmThreads, 1) k_relax_fwd_umma(const float *_
     if (warp < kUmAWarps) {
         bool ok = *err == 0;
         if (ntiles > 0 && ok &&
-            !umma_bar_wait(&s_opempty[(ntiles - 1) % kUmBufs], (uint32_t)((ntiles - 1) / kUmBufs) & 1u, kUmWait))
+            !umma_bar_wait(&s_opempty[(ntiles - 1) % kUmBufs], (uint32_t)((ntiles - 1) / kUmBufs) & 1u, wait))
             ok = false;
         ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld is warp-collective
         if (!ok && lane == 0) atomicOr(status, kStTimeout);
@@ -509,7 +511,8 @@ static int relax_fwd_ctas(const mm_model *m, int B, int S) {
 template <typename G>
 static mm_status relax_fwd_launch(const mm_model *m, const float *x, const G *g, RelaxRows Rw, const uint32_t *mass,
                                   int32_t B, int32_t S, int32_t T, RelaxEcon E, float *part_o, float *part_v, int nr,
-                                  cudaStream_t st) {
+                                  cudaStream_t st, int stall) {
+    const long long wait = stall ? 2000000LL : kUmWait;  // test-only stall: about 1 ms
     const int zs = (S + kFwdSW - 1) / kFwdSW;
     constexpr bool rows = sizeof(G) == sizeof(double);
     UmCopy C;
@@ -528,14 +531,14 @@ static mm_status relax_fwd_launch(const mm_model *m, const float *x, const G *g,
         const size_t smem = std::max<size_t>(um_layout(std::min(S, kFwdSW), zs, N, T, Rw.R, rows).floats * sizeof(float),
                                              116u << 10);
         using Fn = void (*)(const float *, const G *, RelaxRows, const uint32_t *, int32_t, int32_t, int32_t, int32_t,
-                            RelaxEcon, UmCopy, float *, float *, uint32_t *);
+                            RelaxEcon, UmCopy, float *, float *, uint32_t *, int32_t, long long);
         Fn fn;
         if (E.use_thr) fn = N == 16 ? k_relax_fwd_umma<G, 16, true> : k_relax_fwd_umma<G, 32, true>;
         else fn = N == 16 ? k_relax_fwd_umma<G, 16, false> : k_relax_fwd_umma<G, 32, false>;
         MM_CUDA_TRY(cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
                     "forward smem");
         fn<<<dim3((unsigned)nr, 1, (unsigned)zs), kUmThreads, smem, st>>>(x, g, Rw, mass, B, S, T, tb, E, C, part_o,
-                                                                          part_v, m->status);
+                                                                          part_v, m->status, stall, wait);
         mm_status r = check_launch("k_relax_fwd_umma");
         if (r != MM_OK) return r;
     }
@@ -1292,8 +1295,11 @@ mm_status mm_relaxed_forward(mm_model *m, const float *x_dev, const float *g_dev
     if (st != MM_OK) return st;
     float *part_o = m->relax_scratch, *part_v = part_o + (size_t)nr * TS;
     double *term = reinterpret_cast<double *>(part_v + (size_t)nr * TS);
-    st = g_dev ? relax_fwd_launch<float>(m, x_dev, g_dev, Rw, m->mass, B, S, T, E, part_o, part_v, nr, m->stream)
-               : relax_fwd_launch<double>(m, x_dev, m->grade, Rw, m->mass, B, S, T, E, part_o, part_v, nr, m->stream);
+    const int stall = m->test_stall_relax;  // test-only, one-shot
+    m->test_stall_relax = 0;
+    st = g_dev ? relax_fwd_launch<float>(m, x_dev, g_dev, Rw, m->mass, B, S, T, E, part_o, part_v, nr, m->stream, stall)
+               : relax_fwd_launch<double>(m, x_dev, m->grade, Rw, m->mass, B, S, T, E, part_o, part_v, nr, m->stream,
+                                          stall);
     if (st != MM_OK) return st;
     // the finish launches as a programmatic dependent of the forward grid, so
     // its launch overlaps the forward's tail

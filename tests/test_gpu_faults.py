@@ -5,8 +5,10 @@ call) and leaves the model usable; an allocation cap (host-side injection,
 MM_ALLOC_CAP_BYTES) turns model creation into MM_ERR_OOM with nothing left
 allocated; a bounded device wait made to run out (test-only mode, set at
 model creation: the bulk-copy stages expect bytes that never come, every copy
-issued still lands) returns MM_ERR_TIMEOUT at the next synchronising call and
-leaves the model usable.  Nothing here traps, faults or hangs the GPU."""
+issued still lands; or the relaxed forward's stage barriers expect one
+arrival that never comes) returns MM_ERR_TIMEOUT at the next synchronising
+call and leaves the model usable.  Nothing here traps, faults or hangs the
+GPU."""
 
 import ctypes as C
 import os
@@ -134,4 +136,37 @@ def test_bulk_copy_wait_runs_out_and_the_model_stays_usable(monkeypatch):
     ref = O.OracleModel(p).eval_incremental(p.x0, p.moves)
     assert np.array_equal(f.cpu().numpy(), ref["flag"])
     assert_close_floor(s.cpu().numpy(), ref["score"], ref["floor"], what="scores after the timeout")
+    m.npv()
+
+
+def test_relaxed_forward_wait_runs_out_and_the_model_stays_usable(monkeypatch):
+    """With MM_TEST_STALL_RELAXED set at model creation the next relaxed
+    forward's stage barriers expect one arrival that no thread makes, and
+    every wait of that launch gives up after about 1 ms: the copy warps wait
+    for their copies (they all land), no product is issued, the tensor memory
+    is released.  The next synchronising call reports MM_ERR_TIMEOUT once; the
+    mode is one-shot, so the same model's next forward matches the float64
+    oracle."""
+    mm = _mm()
+    from test_gpu_relaxed import TOL, reference
+    from helpers import tiny_problem
+    p = tiny_problem(8, 8, 4, S=100, T=20, seed=11, target_blocks=8)
+    x = W.relaxed_x(p.B, p.T, 2)
+    g = p.grade.astype(np.float32)
+    monkeypatch.setenv("MM_TEST_STALL_RELAXED", "1")
+    m = mm.Model.from_problem(p)
+    monkeypatch.delenv("MM_TEST_STALL_RELAXED")
+    m.schedule_set(p.x0)  # for the synchronising npv calls below
+    xt = torch.as_tensor(x, device="cuda")
+    gt = torch.as_tensor(g, device="cuda")
+    m.relaxed_forward(xt, gt)
+    with pytest.raises(mm.MMError) as e:
+        m.npv()
+    assert e.value.status == TIMEOUT
+    m.npv()  # reported once, then cleared
+    J, npv, ot = m.relaxed_forward(xt, gt)
+    torch.cuda.synchronize()
+    r = reference(p, x, g)
+    assert float(J.cpu()[0]) == pytest.approx(r["J"], rel=TOL)
+    np.testing.assert_allclose(npv.cpu().numpy(), r["npv"], rtol=TOL)
     m.npv()
