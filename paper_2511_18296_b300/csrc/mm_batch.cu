@@ -72,13 +72,33 @@ struct BatchArgs {
 
 constexpr int kBatchMaxT = 64;  // chains with more periods are not batched (tables staged per item)
 
+// The CTA's current item: its chain's evaluator arguments and small tables,
+// and the evaluator's per-warp lists.  At namespace scope so that each
+// evaluator shape below, a separate (not inlined) function, addresses them as
+// shared memory.
+__shared__ EvalShared b_sh;
+__shared__ __align__(16) EvalArgs b_A;
+__shared__ float b_dd[(kBatchMaxT + 1) * (kBatchMaxT + 1)];
+__shared__ int64_t b_mined[kBatchMaxT + 1];
+__shared__ uint64_t b_cap[kBatchMaxT + 1];
+
+// One evaluator shape over the calling warp's moves [r0, r1) of the current
+// item; returns the warp's top-32 keys.  Not inlined: compiled together, the
+// nine shapes need more registers than the kernel's occupancy allows, and
+// each alone needs fewer.
+template <int TEAM, int QMAX, int KF, bool TAIL>
+static __device__ __noinline__ uint64_t batch_range(int64_t r0, int64_t r1) {
+    uint64_t wtk = 0;
+    eval_warp_range<TEAM, QMAX, false, false, KF, TAIL, true>(b_A, b_sh, b_A.tab, b_dd, b_mined, b_cap, r0, r1, wtk);
+    return wtk;
+}
+
 __global__ void __launch_bounds__(kEvalThreads, MM_EVAL_MINB) k_batch_eval(BatchArgs B) {
     constexpr int NW = kEvalThreads / 32;
-    __shared__ EvalShared sh;
-    __shared__ __align__(16) EvalArgs sA;
-    __shared__ float s_dd[(kBatchMaxT + 1) * (kBatchMaxT + 1)];
-    __shared__ int64_t s_mined[kBatchMaxT + 1];
-    __shared__ uint64_t s_cap[kBatchMaxT + 1];
+    EvalArgs &sA = b_A;
+    float *s_dd = b_dd;
+    int64_t *s_mined = b_mined;
+    uint64_t *s_cap = b_cap;
     __shared__ uint64_t s_wl[NW][32];
     __shared__ __align__(16) float s_apply_tab[kApplyTabMax];
     __shared__ int s_item, s_last, s_best;
@@ -107,44 +127,17 @@ __global__ void __launch_bounds__(kEvalThreads, MM_EVAL_MINB) k_batch_eval(Batch
         // this warp's share of the item's moves
         const int64_t len = I.r1 - I.r0;
         const int64_t r0 = I.r0 + warp * len / NW, r1 = I.r0 + (warp + 1) * len / NW;
-        uint64_t wtk = 0;
+        uint64_t wtk;
         switch (C->variant) {
-            case kBvT4K1:
-                eval_warp_range<4, 1, false, false, 1, false, true>(sA, sh, sA.tab, s_dd, s_mined, s_cap, r0,
-                                                                    r1, wtk);
-                break;
-            case kBvT4K2:
-                eval_warp_range<4, 1, false, false, 2, false, true>(sA, sh, sA.tab, s_dd, s_mined, s_cap, r0,
-                                                                    r1, wtk);
-                break;
-            case kBvT4K3:
-                eval_warp_range<4, 1, false, false, 3, false, true>(sA, sh, sA.tab, s_dd, s_mined, s_cap, r0,
-                                                                    r1, wtk);
-                break;
-            case kBvT4K4:
-                eval_warp_range<4, 1, false, false, 4, false, true>(sA, sh, sA.tab, s_dd, s_mined, s_cap, r0,
-                                                                    r1, wtk);
-                break;
-            case kBvT8K3T:
-                eval_warp_range<8, 1, false, false, 3, true, true>(sA, sh, sA.tab, s_dd, s_mined, s_cap, r0,
-                                                                   r1, wtk);
-                break;
-            case kBvG4:
-                eval_warp_range<4, 4, false, false, 0, false, true>(sA, sh, sA.tab, s_dd, s_mined, s_cap, r0,
-                                                                    r1, wtk);
-                break;
-            case kBvG8:
-                eval_warp_range<8, 4, false, false, 0, false, true>(sA, sh, sA.tab, s_dd, s_mined, s_cap, r0,
-                                                                    r1, wtk);
-                break;
-            case kBvG16:
-                eval_warp_range<16, 4, false, false, 0, false, true>(sA, sh, sA.tab, s_dd, s_mined, s_cap, r0,
-                                                                     r1, wtk);
-                break;
-            default:
-                eval_warp_range<32, 8, false, false, 0, false, true>(sA, sh, sA.tab, s_dd, s_mined, s_cap,
-                                                                     r0, r1, wtk);
-                break;
+            case kBvT4K1: wtk = batch_range<4, 1, 1, false>(r0, r1); break;
+            case kBvT4K2: wtk = batch_range<4, 1, 2, false>(r0, r1); break;
+            case kBvT4K3: wtk = batch_range<4, 1, 3, false>(r0, r1); break;
+            case kBvT4K4: wtk = batch_range<4, 1, 4, false>(r0, r1); break;
+            case kBvT8K3T: wtk = batch_range<8, 1, 3, true>(r0, r1); break;
+            case kBvG4: wtk = batch_range<4, 4, 0, false>(r0, r1); break;
+            case kBvG8: wtk = batch_range<8, 4, 0, false>(r0, r1); break;
+            case kBvG16: wtk = batch_range<16, 4, 0, false>(r0, r1); break;
+            default: wtk = batch_range<32, 8, 0, false>(r0, r1); break;
         }
         const int32_t list0 = C->list0, n_items = C->n_items;
         step_publish(B.lists + (size_t)(list0 + I.item) * 32, wtk);
