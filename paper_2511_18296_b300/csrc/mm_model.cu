@@ -129,15 +129,17 @@ __global__ void k_base_arcs(int32_t B, const uint32_t *__restrict__ blk, uint32_
 // consecutive blocks of one period (chunk table built on the host); thread s
 // sums scenario s over the chunk's blocks, eight blocks' loads in flight at a
 // time: ore tonnage (integer), metal m_b * g[b][s] of ore blocks (FP64, block
-// order) and, in thread 0, the mined tonnage.  k_accum_reduce: thread s of
-// period t adds the period's chunk partials in chunk order.  Deterministic:
-// the same schedule always gives the same bits.
+// order) and, in thread 0, the mined tonnage.  k_accum_reduce: for period t
+// and 32 scenarios, warp u adds every eighth chunk partial from chunk u on, in
+// chunk order, and the eight warps' sums are added in a fixed tree.
+// Deterministic: the same schedule always gives the same bits.
 __global__ void __launch_bounds__(128) k_accum_part(const int4 *__restrict__ chunk, const int32_t *__restrict__ order,
                                                     const uint32_t *__restrict__ mass, const float *__restrict__ val,
                                                     int32_t R, int32_t ore_off, const double *__restrict__ grade,
                                                     int32_t S, int64_t *__restrict__ p_ore, double *__restrict__ p_met,
                                                     int64_t *__restrict__ p_mass) {
     const int4 c = chunk[blockIdx.x];  // (period, begin, end, 0)
+    int64_t mt = 0;                    // the chunk's mined tonnage (thread 0, in its s = 0 pass)
     for (int s = threadIdx.x; s < S; s += blockDim.x) {
         int64_t o = 0;
         double g = 0.0;
@@ -158,43 +160,74 @@ __global__ void __launch_bounds__(128) k_accum_part(const int4 *__restrict__ chu
                 }
             }
 #pragma unroll
-            for (int u = 0; u < 8; u++)
+            for (int u = 0; u < 8; u++) {
+                if (s == 0) mt += mb[u];  // 0 past the chunk's end
                 if (ob[u]) {
                     o += mb[u];
                     g = __dadd_rn(g, __dmul_rn((double)mb[u], gb[u]));
                 }
+            }
         }
         p_ore[(int64_t)blockIdx.x * S + s] = o;
         p_met[(int64_t)blockIdx.x * S + s] = g;
     }
-    if (threadIdx.x == 0) {
-        int64_t mt = 0;
-        for (int32_t k = c.y; k < c.z; k++) mt += __ldg(mass + __ldg(order + k));
-        p_mass[blockIdx.x] = mt;
-    }
+    if (threadIdx.x == 0) p_mass[blockIdx.x] = mt;
 }
 
-__global__ void k_accum_reduce(const int32_t *__restrict__ cbase, const int64_t *__restrict__ p_ore,
-                               const double *__restrict__ p_met, const int64_t *__restrict__ p_mass, int32_t S,
-                               int64_t *__restrict__ minedT, int64_t *__restrict__ oreT, double *__restrict__ metal) {
+__global__ void __launch_bounds__(256) k_accum_reduce(const int32_t *__restrict__ cbase,
+                                                      const int64_t *__restrict__ p_ore,
+                                                      const double *__restrict__ p_met,
+                                                      const int64_t *__restrict__ p_mass, int32_t S,
+                                                      int64_t *__restrict__ minedT, int64_t *__restrict__ oreT,
+                                                      double *__restrict__ metal) {
+    __shared__ int64_t s_o[8][32];
+    __shared__ double s_g[8][32];
     const int t = blockIdx.x;
-    const int s = blockIdx.y * blockDim.x + threadIdx.x;
+    const int j = threadIdx.x & 31, u = threadIdx.x >> 5;  // scenario lane, chunk subset (warp)
+    const int s = blockIdx.y * 32 + j;
     const int32_t c0 = cbase[t], c1 = cbase[t + 1];
+    // warp u: chunks c0 + u, c0 + u + 8, ... in chunk order, four loads in flight
+    int64_t o = 0;
+    double g = 0.0;
     if (s < S) {
-        int64_t o = 0;
-        double g = 0.0;
-        for (int32_t c = c0; c < c1; c++) {
-            o += p_ore[(int64_t)c * S + s];
-            g = __dadd_rn(g, p_met[(int64_t)c * S + s]);
+        for (int32_t c = c0 + u; c < c1; c += 32) {
+            int64_t ob[4];
+            double gb[4];
+#pragma unroll
+            for (int v = 0; v < 4; v++) {
+                const int32_t cc = c + 8 * v;
+                ob[v] = cc < c1 ? p_ore[(int64_t)cc * S + s] : 0;
+                gb[v] = cc < c1 ? p_met[(int64_t)cc * S + s] : 0.0;
+            }
+#pragma unroll
+            for (int v = 0; v < 4; v++)
+                if (c + 8 * v < c1) {
+                    o += ob[v];
+                    g = __dadd_rn(g, gb[v]);
+                }
         }
-        oreT[(int64_t)t * S + s] = o;
-        metal[(int64_t)t * S + s] = g;
     }
-    if (blockIdx.y == 0 && threadIdx.x == 0) {
-        int64_t mt = 0;
-        for (int32_t c = c0; c < c1; c++) mt += p_mass[c];
-        minedT[t] = mt;
+    s_o[u][j] = o;
+    s_g[u][j] = g;
+    // the period's mined tonnage: warp 0 of the first scenario group (exact integers)
+    int64_t mt = 0;
+    if (blockIdx.y == 0 && u == 0) {
+        for (int32_t c = c0 + j; c < c1; c += 32) mt += p_mass[c];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) mt += __shfl_down_sync(0xffffffffu, mt, off);
     }
+    __syncthreads();
+    if (u == 0 && s < S) {
+        // the eight subsets' sums in a fixed tree
+        const double a0 = __dadd_rn(s_g[0][j], s_g[1][j]), a1 = __dadd_rn(s_g[2][j], s_g[3][j]);
+        const double a2 = __dadd_rn(s_g[4][j], s_g[5][j]), a3 = __dadd_rn(s_g[6][j], s_g[7][j]);
+        int64_t ot = 0;
+#pragma unroll
+        for (int k = 0; k < 8; k++) ot += s_o[k][j];
+        oreT[(int64_t)t * S + s] = ot;
+        metal[(int64_t)t * S + s] = __dadd_rn(__dadd_rn(a0, a1), __dadd_rn(a2, a3));
+    }
+    if (blockIdx.y == 0 && threadIdx.x == 0) minedT[t] = mt;
 }
 
 __global__ void k_tables(int32_t S, int32_t S_pad, int32_t T, const int64_t *__restrict__ oreT,
@@ -736,7 +769,7 @@ mm_status mm_schedule_set(mm_model *m, const uint8_t *period, int *base_feasible
                                                              m->ore_off, m->grade, S, m->accum_ore, m->accum_met,
                                                              m->accum_mass);
         if ((st = check_launch("k_accum_part")) != MM_OK) return done(st);
-        k_accum_reduce<<<dim3(T, (S + 127) / 128), 128, 0, s>>>(m->accum_cbase, m->accum_ore, m->accum_met,
+        k_accum_reduce<<<dim3(T, (S + 31) / 32), 256, 0, s>>>(m->accum_cbase, m->accum_ore, m->accum_met,
                                                                 m->accum_mass, S, m->minedT, m->oreT, m->metal);
         if ((st = check_launch("k_accum_reduce")) != MM_OK) return done(st);
     } else {
