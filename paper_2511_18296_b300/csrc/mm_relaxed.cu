@@ -685,7 +685,8 @@ __global__ void __launch_bounds__(32 * kFinWarps, 1) k_relax_finish(const float 
     // warps past the last scenario hold zeros and skip the FP64 work
     const int nw = min(kFinWarps, (S + 31) / 32);  // warps holding scenarios (of the first pass)
     double x1 = 0.0, x2 = 0.0;
-    for (int sc = threadIdx.x; sc < S; sc += blockDim.x) {
+    double mine0 = 0.0, mine1 = 0.0;  // this thread's first two NPV_s, kept for the weights below
+    for (int sc = threadIdx.x, r = 0; sc < S; sc += blockDim.x, r++) {
         double acc = 0.0;
         for (int t0 = 0; t0 < T; t0 += 32) {
             double q[32];
@@ -694,6 +695,8 @@ __global__ void __launch_bounds__(32 * kFinWarps, 1) k_relax_finish(const float 
             acc += relax_tree32(q, T - t0);
         }
         npv[sc] = acc;
+        if (r == 0) mine0 = acc;
+        else if (r == 1) mine1 = acc;
         x1 += acc;
         x2 += acc * acc;
     }
@@ -730,8 +733,8 @@ __global__ void __launch_bounds__(32 * kFinWarps, 1) k_relax_finish(const float 
     }
     __syncthreads();
     // the adjoint's scenario weights per unit gJ: 1/S - lambda (NPV_s - mean) / (S std)
-    for (int sc = threadIdx.x; sc < S; sc += blockDim.x)
-        wt_out[sc] = (float)(E.inv_S - s_mv[1] * (npv[sc] - s_mv[0]));
+    for (int sc = threadIdx.x, r = 0; sc < S; sc += blockDim.x, r++)
+        wt_out[sc] = (float)(E.inv_S - s_mv[1] * ((r == 0 ? mine0 : (r == 1 ? mine1 : __ldcg(npv + sc))) - s_mv[0]));
 }
 
 // Adjoint coefficients: w_s = gJ (1/S - lambda (NPV_s - mean) / (S std))
