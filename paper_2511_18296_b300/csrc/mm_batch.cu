@@ -4,7 +4,7 @@
 //
 // The queue is a list of items (chain, range of that chain's moves), ordered
 // largest estimated cost first.  Every CTA of the persistent grid takes the next
-// item with one atomicAdd, stages the chain's small tables in shared memory,
+// item with one atomicAdd (drawn together with its previous item's ticket), stages the chain's small tables in shared memory,
 // evaluates the range with the same per-warp evaluator as the single-model
 // path (its compile-time-shaped form where the chain's scenario count has one,
 // the run-time-shaped form otherwise), and publishes the range's 32 best keys.
@@ -103,10 +103,10 @@ __global__ void __launch_bounds__(kEvalThreads, MM_EVAL_MINB) k_batch_eval(Batch
     __shared__ __align__(16) float s_apply_tab[kApplyTabMax];
     __shared__ int s_item, s_last, s_best;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) s_item = (int)atomicAdd(B.next, 1u);
+    __syncthreads();
+    int it = s_item;
     for (;;) {
-        if (tid == 0) s_item = (int)atomicAdd(B.next, 1u);
-        __syncthreads();
-        const int it = s_item;
         if (it >= B.n_items) break;
         const BatchItem I = B.items[it];
         const ChainDev *C = B.chains + I.chain;
@@ -144,8 +144,12 @@ __global__ void __launch_bounds__(kEvalThreads, MM_EVAL_MINB) k_batch_eval(Batch
         // ticket: the CTA completing the chain's last item finishes the chain
         __threadfence();
         __syncthreads();
-        if (tid == 0) s_last = atomicAdd(B.next + 1 + I.chain, 1u) == (uint32_t)(n_items - 1);
+        if (tid == 0) {
+            s_last = atomicAdd(B.next + 1 + I.chain, 1u) == (uint32_t)(n_items - 1);
+            s_item = (int)atomicAdd(B.next, 1u);  // the next item, drawn beside the ticket
+        }
         __syncthreads();
+        const int next = s_item;
         if (s_last) {
             __threadfence();
             const uint64_t t = block_merge_lists<NW>(B.lists + (size_t)list0 * 32, n_items, s_wl);
@@ -162,6 +166,7 @@ __global__ void __launch_bounds__(kEvalThreads, MM_EVAL_MINB) k_batch_eval(Batch
             }
         }
         __syncthreads();  // shared state is reused by the next item
+        it = next;
     }
 }
 

@@ -296,3 +296,32 @@ def test_batch_autotune_cache_installs_stored_shapes(small, tmp_path):
         if shapes[c][0] == default_team(probs[c].S):
             check_chain(m, mv, o, 4)
     b2.close()
+
+
+def test_batch_wide_scenario_shapes():
+    """The run-time-shaped evaluators of 8, 16 and 32 lanes as chains' default
+    shapes (S = 70, 200, 300: the single model's team widths 8, 16, 32), each
+    in its own non-inlined function inside the batched kernel: every chain gets
+    the single-model bits and top k, and one is checked against the oracle."""
+    specs = W.batched_chain_specs(3, base_seed=900)
+    probs = []
+    for spec, (side, S, n) in zip(specs, ((9, 70, 1500), (8, 200, 1100), (7, 300, 777))):
+        spec = dict(spec, nx=side, ny=side, nz=side, S=S, n_moves=n)
+        spec["cap_blocks"] = int(np.ceil(1.12 * side ** 3 / spec["T"]))
+        spec["target_blocks"] = int(round(0.393 * spec["cap_blocks"]))
+        probs.append(W.chain_problem(spec))
+    assert [default_team(p.S) for p in probs] == [8, 16, 32]
+    models = models_for(probs)
+    mvs = [moves_of(p) for p in probs]
+    b = mm().Batch(list(zip(models, mvs)), k=16)
+    for tile, ctas in ((256, 0), (1 << 20, 0)):
+        b.set_tile(tile, ctas)
+        b.run()
+        torch.cuda.synchronize()
+        for m, mv, o in zip(models, mvs, b.out):
+            check_chain(m, mv, o, 16)
+    p = probs[2]
+    inc = O.OracleModel(p).eval_incremental(p.x0, p.moves)
+    assert np.array_equal(b.out[2]["feas"].cpu().numpy(), inc["flag"])
+    assert_close_floor(b.out[2]["score"].cpu().numpy(), inc["score"], inc["floor"], what="S = 300 chain")
+    b.close()
