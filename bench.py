@@ -744,7 +744,7 @@ def gpu_arm(args):
     # its batch of moves from pinned host memory and reads its result (the
     # top-k and count) back to pinned host memory.  Double-buffered, as a
     # search loop runs it: batch k+1 is copied on a copy stream while step k
-    # computes, step k's result is read back on the copy stream too (so the
+    # computes, step k's result is read back on a third stream (so the
     # compute stream never waits on a transfer), and the host does not wait on
     # each step (stream order and events keep the buffers safe); the L2 flush
     # stays inside every step (on the compute stream, before the step), so it
@@ -764,6 +764,10 @@ def gpu_arm(args):
     outs_h = [torch.empty(2 * TOPK + 1, dtype=torch.int32).pin_memory() for _ in range(2)]
     bufs = [torch.empty_like(moves_h, device=dev) for _ in range(2)]
     copy_stream = torch.cuda.Stream(device=dev)
+    # the readback has a stream of its own: queued on the copy stream, the
+    # next batch's copy would wait behind it (the next-but-one batch's copy
+    # can start only once the step two back has finished)
+    read_stream = torch.cuda.Stream(device=dev)
     copied = [torch.cuda.Event() for _ in range(2)]  # batch k is on the device
     freed = [torch.cuda.Event() for _ in range(2)]   # step k no longer reads its batch buffer
     done = [torch.cuda.Event() for _ in range(2)]    # step k's outputs are written
@@ -793,10 +797,10 @@ def gpu_arm(args):
             done[b].record(stream)
             if k + 1 < steps:
                 issue_copy(k + 1)
-            with torch.cuda.stream(copy_stream):
-                copy_stream.wait_event(done[b])
+            with torch.cuda.stream(read_stream):
+                read_stream.wait_event(done[b])
                 outs_h[b].copy_(o, non_blocking=True)
-                read[b].record(copy_stream)
+                read[b].record(read_stream)
         torch.cuda.synchronize()
         return m.last_apply()[1]  # NPV mean after the last step's move
 
@@ -917,8 +921,8 @@ def gpu_arm(args):
                           "the step's launch; apply on device)" if packed else
                           "pinned host moves -> mm_search_step (apply on device)")
                          + " -> top-k and count to pinned host memory every step; "
-                         "double-buffered (batch k+1 copied and step k-1's result read back on a second stream while "
-                         "step k runs), the host not waiting on each step; L2 flush inside each step; NPV statistics "
+                         "double-buffered (batch k+1 copied on a copy stream and step k-1's result read back on a third "
+                         "stream while step k runs), the host not waiting on each step; L2 flush inside each step; NPV statistics "
                          "read after the last step")},
         "gpu_launches": (1 if S <= 768 else 2) * K,  # per step: the evaluation launch (top-k and apply inside when S <= 768)
         "clocks": clocks,
