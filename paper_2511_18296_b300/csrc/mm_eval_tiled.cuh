@@ -752,7 +752,9 @@ union EvalSmemStep {
 //      draws the final ticket (acquire-release; nobody waits).
 //   2. The CTA that draws the last number ranks the lists' heads (only lists
 //      whose heads rank among the 32 best can hold one of the 32 best keys),
-//      merges those lists (a tree of warp merges), writes the top k, applies
+//      selects the 32 best keys of those lists (the keys no smaller than the
+//      32nd head, each ranked against the others; a tree of warp merges when
+//      there are many), writes the top k, applies
 //      the structural part of the best move from its record (tonnage, schedule
 //      words, penalty tables: all the next evaluation reads) and leaves the
 //      move's FP64 part due in *pending (or clears *pending without an apply).
@@ -767,7 +769,7 @@ static __device__ __noinline__ void step_finish(const StepTail &T, uint64_t wtk,
     __shared__ uint64_t s_heads[256];  // grids of up to 256 CTAs (one per SM)
     __shared__ int s_slot[32];
     __shared__ int4 s_best_inf;
-    __shared__ int s_last, s_best;
+    __shared__ int s_last, s_best, s_ncand;
     const StepLists &L = T.L;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     uint32_t order = 0u;
@@ -820,18 +822,53 @@ static __device__ __noinline__ void step_finish(const StepTail &T, uint64_t wtk,
                 if (r == 0) s_best_inf = my_inf;  // the best key heads its CTA's list
             }
         }
+        if (tid == 0) s_ncand = 0;
         __syncthreads();
-        // warp w < 16 merges the lists of ranks 2w and 2w + 1, then a tree
         const int nc = min(nonempty, 32);
-        t = 0ull;
-        if (warp < 16) {
-            const uint64_t a = 2 * warp < nc ? __ldcg(L.cta + (size_t)s_slot[2 * warp] * 32 + lane) : 0ull;
-            const uint64_t b = 2 * warp + 1 < nc ? __ldcg(L.cta + (size_t)s_slot[2 * warp + 1] * 32 + lane) : 0ull;
-            t = warp_topk_merge(a, b);
-            s_wl[warp][lane] = t;
+        // With 32 lists selected, their 32 heads are keys at least as large as
+        // the smallest of them (tau), so the 32 best keys are all >= tau: they
+        // are found among the keys >= tau of the selected lists (few, unless
+        // many keys lie close together), each ranked by comparison with the
+        // others.  With fewer lists every key is a candidate.  Too many
+        // candidates for the staging (s_wl, free again here) fall back to a
+        // merge tree; both give the same sorted 32 keys (keys are unique).
+        const uint64_t tau = nc == 32 ? s_heads[s_slot[31]] : 1ull;
+        uint64_t *s_cand = &s_wl[0][0];
+        constexpr int kCandMax = NW * 32 < 256 ? NW * 32 : 256;
+        for (int r = warp; r < nc; r += NW) {
+            const uint64_t key = __ldcg(L.cta + (size_t)s_slot[r] * 32 + lane);
+            const uint32_t m = __ballot_sync(0xffffffffu, key >= tau);
+            int base = 0;
+            if (lane == 0 && m) base = atomicAdd(&s_ncand, __popc(m));
+            const int pos = __shfl_sync(0xffffffffu, base, 0) + __popc(m & ((1u << lane) - 1u));
+            if (key >= tau && pos < kCandMax) s_cand[pos] = key;
         }
         __syncthreads();
-        t = tree_merge<(NW < 16 ? NW : 16), false>(t, s_wl, nullptr);
+        const int ncand = s_ncand;
+        __syncthreads();  // every thread has read the count before the tree may reuse s_wl
+        if (ncand <= kCandMax) {
+            uint64_t *s_out = s_heads;  // the heads are no longer read
+            if (tid < ncand) {
+                const uint64_t key = s_cand[tid];
+                int r = 0;
+                for (int j = 0; j < ncand; j++) r += s_cand[j] > key ? 1 : 0;
+                if (r < 32) s_out[r] = key;
+            }
+            if (tid >= ncand && tid < 32) s_out[tid] = 0ull;
+            __syncthreads();
+            t = warp == 0 ? s_out[lane] : 0ull;
+        } else {
+            // warp w < 16 merges the lists of ranks 2w and 2w + 1, then a tree
+            t = 0ull;
+            if (warp < 16) {
+                const uint64_t a = 2 * warp < nc ? __ldcg(L.cta + (size_t)s_slot[2 * warp] * 32 + lane) : 0ull;
+                const uint64_t b = 2 * warp + 1 < nc ? __ldcg(L.cta + (size_t)s_slot[2 * warp + 1] * 32 + lane) : 0ull;
+                t = warp_topk_merge(a, b);
+                s_wl[warp][lane] = t;
+            }
+            __syncthreads();
+            t = tree_merge<(NW < 16 ? NW : 16), false>(t, s_wl, nullptr);
+        }
         inf = s_best_inf;
     } else {
         t = block_merge_lists_info<NW>(L.cta, L.cinf, G, s_wl, s_inf, inf);
