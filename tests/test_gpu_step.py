@@ -280,3 +280,48 @@ def test_step_in_launch_apply_up_to_768_scenarios(S):
     fresh = mm.Model.from_problem(p)
     fresh.schedule_set(a.schedule_get())
     np.testing.assert_allclose(a.npv()[0], fresh.npv()[0], rtol=1e-12, atol=1e-3)
+
+
+def _tie_batch(p, n, kind, seed=11):
+    """A batch whose scores tie (one or two feasible moves repeated), or
+    whose feasible moves are a scattered few among infeasible ones."""
+    inc = O.OracleModel(p).eval_incremental(p.x0, p.moves[:4096])
+    feas = np.flatnonzero((inc["flag"] != 0) & (inc["mean"] != 0.0))
+    infeas = np.flatnonzero(inc["flag"] == 0)
+    rng = np.random.default_rng(seed)
+    if kind == "same":
+        return np.repeat(p.moves[feas[:1]], n, axis=0)
+    if kind == "two":
+        pick = feas[:2][rng.integers(0, 2, n)]
+        return p.moves[pick].copy()
+    # "sparse": 20 feasible moves at random places among infeasible ones
+    mv = p.moves[infeas[rng.integers(0, len(infeas), n)]].copy()
+    at = rng.choice(n, 20, replace=False)
+    mv[at] = p.moves[feas[:20]]
+    return mv
+
+
+@pytest.mark.parametrize("name,n,kind", [("plain_50k", 262_144, "same"), ("plain_50k", 262_144, "two"),
+                                         ("plain_50k", 262_144, "sparse"), ("plain_4k", 20_000, "same"),
+                                         ("plain_4k", 20_000, "sparse")])
+@pytest.mark.parametrize("k", [1, 32])
+def test_step_tied_scores_and_few_lists(name, n, kind, k):
+    """The launch's last CTA selects the 32 best keys from the keys no smaller
+    than the 32nd list head, or from every key when fewer than 32 CTA lists
+    are non-empty, and falls back to a merge tree when too many keys qualify.
+    Tied scores (keys differing only in the move index) drive the fallback,
+    a few scattered feasible moves leave most CTA lists empty: both must give
+    the separate calls' selection (ties by index) and the same apply."""
+    p = W.config(name)
+    mv = torch.as_tensor(_tie_batch(p, n, kind), device="cuda")
+    a, b = _pair(p)
+    for _ in range(2):
+        ra = a.search_step(mv, k=k, apply=True)
+        rb = _separate(b, mv, k, True)
+        c = _compare(ra, rb, k)
+        s, f = ra[0].cpu().numpy(), ra[1].cpu().numpy()
+        ri, _ = O.topk(s.astype(np.float64), f, k)
+        assert len(ri) == c and np.array_equal(ra[2].cpu().numpy()[:c], ri)
+        assert a.last_apply() == b.last_apply()
+    assert np.array_equal(a.schedule_get(), b.schedule_get())
+    assert np.array_equal(a.npv()[0], b.npv()[0])
