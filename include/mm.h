@@ -234,8 +234,8 @@ mm_status mm_topk(mm_model *m, const float *score_dev, const uint8_t *feasible_d
  * 768 threads per SM (mm_set_tile's ctas_per_sm does not apply to it); each
  * warp keeps its 32 best keys in registers (warp shuffles), each CTA merges
  * its warps' lists and publishes one list, and the CTA that finishes last
- * (a ticket, no waiting) ranks the lists' heads, merges the lists that can
- * hold one of the 32 best keys and writes the top k.  When S <= 768 that
+ * (a ticket, no waiting) ranks the lists' heads, selects the 32 best keys
+ * from the lists that can hold one of them and writes the top k.  When S <= 768 that
  * final CTA also applies the best move from the record the evaluation kept of
  * it (its blocks and periods): the tonnage, schedule words and penalty tables
  * (everything the next evaluation reads) in this launch, the move's FP64
