@@ -488,16 +488,17 @@ def stress_form(stream, flush, reps: int = 20, n_accept: int = 1000):
     # drift: FP64 running totals beside their FP32 shadow over n_accept applies
     m.set_fp32_shadow(True)
     m.schedule_set(p.x0)
-    accepted = steps = 0
+    accepted = steps = improving = 0
     with torch.cuda.stream(stream):
         while accepted < n_accept and steps < n_accept + n_accept // 5:
             m.eval_moves(mv, score=score, feas=feas, want_mean=False, kahan=True)
             m.topk(score, feas, 1, idx=idx[:1], top=top[:1], count=cnt)
             m.apply_best(mv, idx[:1], cnt)
-            accepted += m.last_apply()[0]
+            accepted += m.last_apply()[0]  # a feasible no-op counts as applied
+            improving += int(cnt[0].item() > 0 and top[0].item() > 0.0)
             steps += 1
     x = m.schedule_get()
-    drift_in = (p, x, m.npv()[0], m.fp32_shadow_npv(), accepted)
+    drift_in = (p, x, m.npv()[0], m.fp32_shadow_npv(), accepted, improving)
     m.close()
     alg = algorithmic_bytes(p.moves, p.S)
     peaks, which = measured_peaks()
@@ -512,7 +513,7 @@ def stress_form(stream, flush, reps: int = 20, n_accept: int = 1000):
             "step_ms": step_ms, "step_time": stats(times["step"]), "step_desc": "mm_search_step: evaluate + top-32 + apply the best move, one launch",
             "value": evals / (step_ms * 1e-3), "unit": UNIT,
             "peak_source": f"{which} (MEASURED_PEAKS.json hbm_gbs)",
-            "accepted_moves": accepted, "steps": steps}, drift_in
+            "accepted_moves": accepted, "improving_moves": improving, "steps": steps}, drift_in
 
 
 def shard_arm(args, p, world: int, rank: int, dev):
@@ -825,11 +826,14 @@ def gpu_arm(args):
     N_APPLY = 1000
     m.set_fp32_shadow(True)
     m.schedule_set(p.x0)
+    n_improving = torch.zeros(1, dtype=torch.int64, device=dev)
     with torch.cuda.stream(stream):
         for _ in range(N_APPLY):
             m.search_step(moves_d, k=TOPK, apply=True, score=score, feas=feas, idx=idx, top=top, count=cnt)
+            n_improving += ((cnt[:1] > 0) & (top[:1] > 0.0)).to(torch.int64)  # the step changed the schedule
     stream.synchronize()
     drift_gpu = (m.schedule_get(), m.npv()[0], m.fp32_shadow_npv())
+    n_improving = int(n_improving.item())
     m.set_fp32_shadow(False)
 
 
@@ -947,12 +951,14 @@ def gpu_arm(args):
         line["accuracy"] = accuracy_report(p, acc_sel, acc_gpu)
         line["accuracy"]["full_batch_plain"] = full_batch_accuracy(p, *acc_full)
         line["precision_form"]["drift"] = drift_report(p, *drift_gpu, n_apply=N_APPLY)
+        line["precision_form"]["drift"]["improving_moves"] = n_improving
         if stress_in is not None:
-            ps, xs, n64, n32, acc = stress_in
+            ps, xs, n64, n32, acc, imp = stress_in
             line["stress_form"]["drift"] = drift_report(
                 ps, xs, n64, n32, n_apply=acc,
                 workload="the 400,000-block model: accepted moves (compensated sums, best feasible move of the "
                          "batch) applied on the device from the initial schedule")
+            line["stress_form"]["drift"]["improving_moves"] = imp
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
