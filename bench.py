@@ -471,20 +471,23 @@ def stress_form(stream, flush, reps: int = 20, n_accept: int = 1000):
     timer = StepTimer(stream, flush, R=reps)
     times = {}
 
-    def time_fn(fn, name):
+    def time_fn(fn, name, R=None, reset=False):
         with torch.cuda.stream(stream):
             fn()
         stream.synchronize()
-        ge = timer.graph([fn])
+        ge = timer.graph([fn], R=R)
         timer.warm(ge)
         m.schedule_set(p.x0)
-        times[name] = timer.run(ge, reps)
+        times[name] = timer.run(ge, reps, between=(lambda: m.schedule_set(p.x0)) if reset else None)
         return float(np.mean(times[name]))
 
     plain_ms = time_fn(lambda: m.eval_moves(mv, score=score, feas=feas, want_mean=False), "eval")
     kahan_ms = time_fn(lambda: m.eval_moves(mv, score=score, feas=feas, want_mean=False, kahan=True), "kahan")
+    # from the initial schedule the batch's best move improves the NPV for a
+    # few steps only (then it is a no-op): graphs of 5 steps, the schedule
+    # reset between replays, so that every timed step applies a move
     step_ms = time_fn(lambda: m.search_step(mv, k=TOPK, apply=True, score=score, feas=feas, idx=idx, top=top,
-                                            count=cnt), "step")
+                                            count=cnt), "step", R=5, reset=True)
     # drift: FP64 running totals beside their FP32 shadow over n_accept applies
     m.set_fp32_shadow(True)
     m.schedule_set(p.x0)
